@@ -1,0 +1,283 @@
+"""CPU oracle for the LUDA compaction job -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package. The product path (``paper_2004_03054_b300``) never does.
+
+The arithmetic lives in ``luda_oracle.c`` (plain C, single-threaded); this module only
+marshals arguments through ctypes. See that file's header for what is computed and which
+part of the paper each step follows (LUDA, §II-A Phases 1-3).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "luda_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CORRUPTION = -2
+ERR_NOT_SUPPORTED = -3
+ERR_OOM = -4
+ERR_DUPLICATE_KEY = -7
+F_STRICT_DUP = 1
+MAX_SEQ = (1 << 56) - 1
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (plain -O2, no vectorisation pragmas)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Table(C.Structure):
+    _fields_ = [("data", C.POINTER(C.c_uint8)), ("size", C.c_uint64), ("n_entries", C.c_uint64),
+                ("smallest", C.POINTER(C.c_uint8)), ("smallest_len", C.c_uint32),
+                ("largest", C.POINTER(C.c_uint8)), ("largest_len", C.c_uint32)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("tables", C.POINTER(_Table)), ("n_tables", C.c_uint32),
+                ("n_in_entries", C.c_uint64), ("n_dropped", C.c_uint64)]
+
+
+class _Read(C.Structure):
+    _fields_ = [("keys", C.POINTER(C.c_uint8)), ("koff", C.POINTER(C.c_uint64)),
+                ("vals", C.POINTER(C.c_uint8)), ("voff", C.POINTER(C.c_uint64)), ("n", C.c_uint64),
+                ("n_blocks", C.c_uint64), ("blk_off", C.POINTER(C.c_uint64)),
+                ("blk_size", C.POINTER(C.c_uint64)), ("blk_last", C.POINTER(C.c_uint64)),
+                ("index_keys_ok", C.c_uint32), ("layout_ok", C.c_uint32),
+                ("filter_off", C.c_uint64), ("filter_size", C.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        u8p, u64p = C.POINTER(C.c_uint8), C.POINTER(C.c_uint64)
+        L.ora_crc32c.restype = C.c_uint32
+        L.ora_crc32c.argtypes = [C.c_void_p, C.c_uint64]
+        L.ora_crc32c_bitwise.restype = C.c_uint32
+        L.ora_crc32c_bitwise.argtypes = [C.c_void_p, C.c_uint64]
+        L.ora_mask.restype = C.c_uint32
+        L.ora_mask.argtypes = [C.c_uint32]
+        L.ora_unmask.restype = C.c_uint32
+        L.ora_unmask.argtypes = [C.c_uint32]
+        L.ora_murmur3_32.restype = C.c_uint32
+        L.ora_murmur3_32.argtypes = [C.c_void_p, C.c_uint64, C.c_uint32]
+        L.ora_put_varint.restype = C.c_uint32
+        L.ora_put_varint.argtypes = [C.c_void_p, C.c_uint64]
+        L.ora_get_varint64.restype = C.c_uint64
+        L.ora_get_varint64.argtypes = [C.c_void_p, C.c_uint64, u64p]
+        L.ora_encode_block.restype = C.c_int
+        L.ora_encode_block.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
+                                       C.c_uint32, C.c_void_p, C.c_uint64, u64p]
+        L.ora_compact.restype = C.c_int
+        L.ora_compact.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32, C.c_uint64,
+                                  C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(C.POINTER(_Result))]
+        L.ora_build.restype = C.c_int
+        L.ora_build.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
+                                C.POINTER(C.POINTER(_Result))]
+        L.ora_free_result.argtypes = [C.POINTER(_Result)]
+        L.ora_read_table.restype = C.c_int
+        L.ora_read_table.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.POINTER(_Read))]
+        L.ora_free_read.argtypes = [C.POINTER(_Read)]
+        L.ora_bloom_may_contain.restype = C.c_int
+        L.ora_bloom_may_contain.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64]
+        L.ora_last_detail.restype = C.c_char_p
+        del u8p
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int:
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    raise TypeError(type(a))
+
+
+def _u8(b) -> np.ndarray:
+    if isinstance(b, np.ndarray):
+        return np.ascontiguousarray(b, dtype=np.uint8)
+    return np.frombuffer(bytes(b), dtype=np.uint8) if len(b) else np.zeros(1, np.uint8)[:0]
+
+
+def crc32c(data: bytes) -> int:
+    a = _u8(data)
+    return lib().ora_crc32c(a.ctypes.data, len(a))
+
+
+def crc32c_bitwise(data: bytes) -> int:
+    a = _u8(data)
+    return lib().ora_crc32c_bitwise(a.ctypes.data, len(a))
+
+
+def mask(c: int) -> int:
+    return lib().ora_mask(c)
+
+
+def unmask(m: int) -> int:
+    return lib().ora_unmask(m)
+
+
+def murmur3_32(data: bytes, seed: int = 0) -> int:
+    a = _u8(data)
+    return lib().ora_murmur3_32(a.ctypes.data, len(a), seed)
+
+
+def put_varint(v: int) -> bytes:
+    buf = (C.c_uint8 * 10)()
+    n = lib().ora_put_varint(buf, v)
+    return bytes(buf[:n])
+
+
+def get_varint64(data: bytes):
+    """(value, bytes consumed); consumed == 0 means malformed."""
+    a = _u8(data)
+    v = C.c_uint64()
+    n = lib().ora_get_varint64(a.ctypes.data, len(a), C.byref(v))
+    return v.value, int(n)
+
+
+def _blob(items):
+    offs = np.zeros(len(items) + 1, np.uint64)
+    if items:
+        offs[1:] = np.cumsum([len(x) for x in items], dtype=np.uint64)
+    blob = np.frombuffer(b"".join(items), np.uint8) if items else np.zeros(0, np.uint8)
+    return np.ascontiguousarray(blob), offs
+
+
+def encode_block(entries, restart_interval: int) -> bytes:
+    """Contents of one block holding raw (key, value) entries (no trailer)."""
+    kb, ko = _blob([k for k, _ in entries])
+    vb, vo = _blob([v for _, v in entries])
+    cap = sum(len(k) + len(v) + 15 for k, v in entries) + 4 * (len(entries) + 1) + 16
+    out = np.zeros(cap, np.uint8)
+    n = C.c_uint64()
+    rc = lib().ora_encode_block(kb.ctypes.data, ko.ctypes.data, vb.ctypes.data, vo.ctypes.data, len(entries),
+                                restart_interval, out.ctypes.data, cap, C.byref(n))
+    if rc:
+        raise ValueError(f"encode_block rc={rc}")
+    return out[: n.value].tobytes()
+
+
+@dataclass
+class Table:
+    data: bytes
+    n_entries: int
+    smallest: bytes
+    largest: bytes
+
+
+@dataclass
+class Result:
+    status: int
+    tables: list
+    n_in_entries: int = 0
+    n_dropped: int = 0
+    detail: str = ""
+
+
+def _take(rc, res_p) -> Result:
+    L = lib()
+    if rc != OK:
+        return Result(rc, [], detail=L.ora_last_detail().decode(errors="replace"))
+    r = res_p.contents
+    tables = []
+    for i in range(r.n_tables):
+        t = r.tables[i]
+        tables.append(Table(C.string_at(t.data, t.size), int(t.n_entries),
+                            C.string_at(t.smallest, t.smallest_len), C.string_at(t.largest, t.largest_len)))
+    out = Result(OK, tables, int(r.n_in_entries), int(r.n_dropped))
+    L.ora_free_result(res_p)
+    return out
+
+
+def compact(inputs, smallest_snapshot: int = MAX_SEQ, bottommost: bool = False, block_size: int = 4096,
+            restart_interval: int = 16, bloom_bits_per_key: int = 10, target_file_size: int = 2 << 20,
+            flags: int = 0) -> Result:
+    """Compact input tables (listed newest first) into new tables."""
+    arrs = [_u8(x) for x in inputs]
+    ptrs = (C.c_void_p * max(1, len(arrs)))(*[a.ctypes.data for a in arrs])
+    sizes = (C.c_uint64 * max(1, len(arrs)))(*[len(a) for a in arrs])
+    res = C.POINTER(_Result)()
+    rc = lib().ora_compact(ptrs, sizes, len(arrs), smallest_snapshot, int(bool(bottommost)), block_size,
+                           restart_interval, bloom_bits_per_key, target_file_size, flags, C.byref(res))
+    return _take(rc, res)
+
+
+def build_tables(run, block_size: int = 4096, restart_interval: int = 16, bloom_bits_per_key: int = 10,
+                 target_file_size: int = (1 << 64) - 1) -> Result:
+    """Build tables from one sorted run (a ``workloads.Run``): the memtable-flush path."""
+    ukeys = np.ascontiguousarray(run.ukeys, np.uint8)
+    ukoff = np.ascontiguousarray(run.ukoff, np.uint64)
+    seqs = np.ascontiguousarray(run.seqs, np.uint64)
+    types = np.ascontiguousarray(run.types, np.uint8)
+    vals = np.ascontiguousarray(run.vals, np.uint8)
+    voff = np.ascontiguousarray(run.voff, np.uint64)
+    res = C.POINTER(_Result)()
+    rc = lib().ora_build(ukeys.ctypes.data, ukoff.ctypes.data, seqs.ctypes.data, types.ctypes.data,
+                         vals.ctypes.data, voff.ctypes.data, len(seqs), block_size, restart_interval,
+                         bloom_bits_per_key, target_file_size, C.byref(res))
+    return _take(rc, res)
+
+
+@dataclass
+class ReadTable:
+    keys: list          # internal keys
+    values: list
+    n_blocks: int
+    blk_off: list
+    blk_size: list
+    blk_last: list
+    index_keys_ok: bool
+    layout_ok: bool
+    filter: bytes       # filter block contents (bitmap || k)
+
+
+def read_table(data: bytes):
+    """(status, ReadTable | None, detail)."""
+    a = _u8(data)
+    r = C.POINTER(_Read)()
+    L = lib()
+    rc = L.ora_read_table(a.ctypes.data, len(a), C.byref(r))
+    if rc != OK:
+        return rc, None, L.ora_last_detail().decode(errors="replace")
+    t = r.contents
+    n = int(t.n)
+    koff = np.ctypeslib.as_array(t.koff, shape=(n + 1,)).copy()
+    voff = np.ctypeslib.as_array(t.voff, shape=(n + 1,)).copy()
+    kb = C.string_at(t.keys, int(koff[-1])) if koff[-1] else b""
+    vb = C.string_at(t.vals, int(voff[-1])) if voff[-1] else b""
+    nb = int(t.n_blocks)
+    out = ReadTable(
+        keys=[kb[koff[i]:koff[i + 1]] for i in range(n)],
+        values=[vb[voff[i]:voff[i + 1]] for i in range(n)],
+        n_blocks=nb,
+        blk_off=[int(t.blk_off[i]) for i in range(nb)],
+        blk_size=[int(t.blk_size[i]) for i in range(nb)],
+        blk_last=[int(t.blk_last[i]) for i in range(nb)],
+        index_keys_ok=bool(t.index_keys_ok), layout_ok=bool(t.layout_ok),
+        filter=bytes(a[int(t.filter_off): int(t.filter_off) + int(t.filter_size)]),
+    )
+    L.ora_free_read(r)
+    return OK, out, ""
+
+
+def bloom_may_contain(filter_contents: bytes, ukey: bytes) -> bool:
+    f = _u8(filter_contents)
+    k = _u8(ukey)
+    return bool(lib().ora_bloom_may_contain(f.ctypes.data, len(f), k.ctypes.data, len(k)))
