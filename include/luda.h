@@ -1,0 +1,190 @@
+/*
+ * luda.h -- C ABI of libluda.so: SSTable compaction on one NVIDIA B300 (sm_103a).
+ *
+ * The operation is the compaction job of LUDA (arXiv 2004.03054): decode the selected
+ * input tables (§II-A Phase 1 "Unpack": verify each data block's checksum, restore full
+ * keys from shared prefixes), merge and sort all pairs by internal key and drop stale
+ * and deleted versions (§II-A Phase 2 "(Delete and) Sort"), then pack the survivors
+ * into new tables: data blocks cut by size, shared-prefix keys, checksums, index and
+ * bloom filter (§II-A Phase 3 "Pack"; §III-C kernels unpack / shared_key / encode /
+ * filter). The table format is this library's written LevelDB-style format: LEB128
+ * varints, prefix-compressed keys with restart points, masked CRC-32C block trailers,
+ * an unshortened index, a per-table MurmurHash3 bloom filter, no block compression.
+ *
+ * Every step runs in this library's CUDA kernels. There is no CPU fallback: a call on a
+ * machine without a usable GPU returns LUDA_ERR_CUDA.
+ *
+ * Conventions, all entry points:
+ *   - Inputs are caller-owned and never modified. Inputs of one job are listed newest
+ *     first (level-0 tables newest to oldest, then the next level's tables in key order);
+ *     on identical internal keys the earlier input wins.
+ *   - Outputs are library-owned until luda_outputs_free. On any error *out holds no
+ *     tables (all-or-nothing), `status` holds the error, and luda_last_error_detail()
+ *     names the input and byte offset when the error is in an input.
+ *   - Device pointers must stay readable up to the next 16-byte boundary past their end
+ *     (every cudaMalloc / PyTorch CUDA allocation is).
+ *   - Calls are thread-compatible: concurrent calls must use distinct streams.
+ */
+#ifndef LUDA_H
+#define LUDA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LUDA_API __attribute__((visibility("default")))
+#else
+#define LUDA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LUDA_OK = 0,
+  LUDA_ERR_INVALID_ARG = -1,   /* bad option, NULL pointer, unsorted run given to luda_build */
+  LUDA_ERR_CORRUPTION = -2,    /* checksum, varint, offsets, footer, magic or key order */
+  LUDA_ERR_NOT_SUPPORTED = -3, /* a block whose type byte is not 0 (compressed) */
+  LUDA_ERR_OOM = -4,           /* device or pinned host allocation failed */
+  LUDA_ERR_CUDA = -5,          /* a CUDA runtime call failed (no GPU, launch error) */
+  LUDA_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
+  LUDA_ERR_DUPLICATE_KEY = -7, /* identical internal keys in two inputs, with LUDA_F_STRICT_DUP */
+  LUDA_ERR_PLAN_MISMATCH = -8  /* a plan was re-run on inputs whose sizes changed */
+} luda_status;
+
+/* options.flags */
+#define LUDA_F_STRICT_DUP 1u /* identical internal keys across inputs are an error */
+#define LUDA_F_TRACE 2u      /* record per-stage device times (luda_outputs.stage_ms) */
+
+/* One input table. For the device entry points `data` is a device pointer. */
+typedef struct {
+  const uint8_t* data;
+  uint64_t size;
+  int32_t level;        /* informational */
+  uint64_t file_number; /* informational */
+} luda_input;
+
+/* Device allocator hook (e.g. PyTorch's caching allocator). NULL = cudaMallocAsync on
+ * the call's stream. `stream` is a cudaStream_t. */
+typedef void* (*luda_alloc_fn)(size_t bytes, void* ctx, void* stream);
+typedef void (*luda_free_fn)(void* ptr, void* ctx, void* stream);
+
+typedef struct {
+  uint32_t block_size;          /* T: a data block is closed once its size reaches T (>= 1) */
+  uint32_t restart_interval;    /* R: every R-th entry of a block is a restart (1..65535) */
+  uint32_t bloom_bits_per_key;  /* bloom filter bits per entry (1..64); k = bpk*69/100 probes */
+  uint64_t target_file_size;    /* a table is finished once its data blocks reach this (>= 1) */
+  int32_t bottommost;           /* drop tombstones visible at the snapshot (single-job calls) */
+  uint32_t flags;               /* LUDA_F_* */
+  luda_alloc_fn dev_alloc;
+  luda_free_fn dev_free;
+  void* alloc_ctx;
+  void* stream;                 /* cudaStream_t; NULL = the legacy default stream */
+} luda_options;
+
+/* Defaults: T = 4096, R = 16, bpk = 10, target = 2 MiB, not bottommost, no flags. */
+LUDA_API void luda_options_default(luda_options* o);
+
+/* One output table. `data` is a host pointer for the host entry points and a device
+ * pointer for the *_device ones; `smallest`/`largest` (internal keys) are always host
+ * pointers. */
+typedef struct {
+  uint8_t* data;
+  uint64_t size;
+  uint64_t n_entries;
+  uint8_t* smallest;
+  uint32_t smallest_len;
+  uint8_t* largest;
+  uint32_t largest_len;
+} luda_table;
+
+#define LUDA_N_STAGES 8
+
+typedef struct {
+  luda_table* tables;
+  uint32_t n_tables;
+  int32_t status;               /* luda_status of this job */
+  uint64_t n_in_entries;        /* entries decoded from the inputs */
+  uint64_t n_dropped;           /* entries removed by the drop rule */
+  double ms_h2d, ms_device, ms_d2h;
+  double stage_ms[LUDA_N_STAGES]; /* with LUDA_F_TRACE: scan, decode, sort, gc, cut, encode, meta, d2h-meta */
+  void* _priv;                  /* library bookkeeping: do not touch */
+} luda_outputs;
+
+/* ---- single compaction job ------------------------------------------------------------
+ * luda_compact: inputs[].data are host pointers (pinned memory gives the fastest copies);
+ *   the library copies them to the device (timed in ms_h2d), compacts, and copies the new
+ *   tables back into library-owned pinned host memory (ms_d2h).
+ * luda_compact_device: inputs[].data are device pointers on opts->stream; the new tables
+ *   stay on the device in one library-owned allocation.
+ * `level` is the output level (recorded only); `smallest_snapshot` is the oldest sequence
+ *   number any reader may still see ((1<<56)-1 when there are no snapshots). */
+LUDA_API luda_status luda_compact(const luda_input* inputs, uint32_t n_inputs, int32_t level, uint64_t smallest_snapshot,
+                         const luda_options* opts, luda_outputs* out);
+LUDA_API luda_status luda_compact_device(const luda_input* inputs, uint32_t n_inputs, int32_t level,
+                                uint64_t smallest_snapshot, const luda_options* opts, luda_outputs* out);
+
+/* ---- many independent jobs in one launch sequence ------------------------------------ */
+typedef struct {
+  const luda_input* inputs;   /* device pointers */
+  uint32_t n_inputs;
+  int32_t level;
+  uint64_t smallest_snapshot;
+  int32_t bottommost;
+} luda_job;
+
+/* Compacts n_jobs jobs together: every kernel of the pipeline runs once over all jobs'
+ * work. outs[j] receives job j's tables (device pointers) and status; a corrupt job fails
+ * alone. Returns LUDA_OK when the batch ran (check each outs[j].status), else the error
+ * that stopped the whole batch. */
+LUDA_API luda_status luda_batch_compact_device(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts,
+                                      luda_outputs* outs);
+
+/* ---- plans: a batch sized once, captured in a CUDA graph, replayed --------------------
+ * luda_plan_create runs the sizing pass on the jobs' device inputs, allocates every
+ * buffer and captures the whole pipeline (decode to footers, all jobs) into one CUDA
+ * graph. luda_plan_run replays it on `stream`; every replay redoes all the work from the
+ * input bytes and checks on the device that the sizes still match the plan
+ * (LUDA_ERR_PLAN_MISMATCH otherwise). The inputs must stay valid and unchanged in size
+ * for the plan's life. luda_plan_outputs gives each job's tables from the last run
+ * (device pointers into the plan, valid until the next run or destroy). */
+typedef struct luda_plan luda_plan;
+LUDA_API luda_status luda_plan_create(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts, luda_plan** plan);
+LUDA_API luda_status luda_plan_run(luda_plan* plan, void* stream);
+LUDA_API luda_status luda_plan_outputs(luda_plan* plan, luda_outputs* outs);
+LUDA_API void luda_plan_destroy(luda_plan* plan);
+
+/* ---- table builder (memtable flush) ---------------------------------------------------
+ * Packs one run of entries already in increasing internal-key order (user key ascending;
+ * for equal user keys, sequence descending) into tables, cutting files at the target
+ * size, with the same encoder as a compaction. ukeys/vals are concatenated bytes with
+ * n+1 offsets; types 1 = put, 0 = delete; seqs < 2^56. Unsorted input is
+ * LUDA_ERR_INVALID_ARG. luda_build takes host arrays and returns host tables;
+ * luda_build_device takes device arrays and returns device tables. */
+typedef struct {
+  const uint8_t* ukeys;
+  const uint64_t* ukoff;
+  const uint64_t* seqs;
+  const uint8_t* types;
+  const uint8_t* vals;
+  const uint64_t* voff;
+  uint64_t n;
+} luda_run;
+
+LUDA_API luda_status luda_build(const luda_run* run, const luda_options* opts, luda_outputs* out);
+LUDA_API luda_status luda_build_device(const luda_run* run, const luda_options* opts, luda_outputs* out);
+
+/* Frees everything an entry point stored in *out (host and device memory). */
+LUDA_API void luda_outputs_free(luda_outputs* out);
+
+LUDA_API const char* luda_strerror(luda_status s);
+/* Thread-local text for the last error of this thread's last call ("" if none). */
+LUDA_API const char* luda_last_error_detail(void);
+/* Library version string. */
+LUDA_API const char* luda_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LUDA_H */

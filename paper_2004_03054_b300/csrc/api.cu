@@ -1,0 +1,1031 @@
+// api.cu -- host orchestration of the compaction pipeline and the C ABI of libluda.so.
+//
+// A call runs the three phases of a compaction (LUDA §II-A; Fig. 3 of §III-A without the
+// host-side sort of steps 4-6, which stays on the device here) for one or many jobs:
+//   sizing    footers and index blocks (one host read of per-input block counts), then
+//             per-block CRC/structure checks and entry counts (one host read of per-input
+//             record and key-byte totals, which size every later buffer);
+//   execute   decode, merge, drop rule, sizes, block cut, file cut, layout, encode, bloom,
+//             index/metaindex/footer -- launched back to back with no host round trip;
+//   collect   one read of the counts, then the per-table metadata and boundary keys.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "luda.h"
+
+using namespace luda;
+
+namespace {
+
+thread_local char t_detail[512];
+
+void set_detail(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_detail, sizeof t_detail, fmt, ap);
+  va_end(ap);
+}
+
+// ---- per-device CRC tables ----------------------------------------------------------------
+struct DevTables {
+  uint32_t* slice = nullptr;
+  uint32_t* shift = nullptr;
+};
+std::mutex g_mu;
+DevTables g_tabs[128];
+
+luda_status get_tabs(CrcTabs* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+    set_detail("no usable CUDA device");
+    return LUDA_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevTables& t = g_tabs[dev];
+  if (!t.slice) {
+    std::vector<uint32_t> slice(1024), shift(size_t(kShiftTables) * 1024);
+    if (!make_crc_tables(slice.data(), shift.data())) {
+      set_detail("crc table generation failed");
+      return LUDA_ERR_CUDA;
+    }
+    uint32_t *ds = nullptr, *dh = nullptr;
+    if (cudaMalloc(&ds, slice.size() * 4) != cudaSuccess || cudaMalloc(&dh, shift.size() * 4) != cudaSuccess ||
+        cudaMemcpy(ds, slice.data(), slice.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dh, shift.data(), shift.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(ds);
+      cudaFree(dh);
+      set_detail("could not upload crc tables: %s", cudaGetErrorString(cudaGetLastError()));
+      return LUDA_ERR_CUDA;
+    }
+    t.slice = ds;
+    t.shift = dh;
+  }
+  out->slice = t.slice;
+  out->shift = t.shift;
+  return LUDA_OK;
+}
+
+// ---- memory -------------------------------------------------------------------------------
+struct DevMem {
+  const luda_options* o;
+  cudaStream_t st;
+  void* get(size_t n) const {
+    if (n == 0) n = 256;
+    if (o && o->dev_alloc) return o->dev_alloc(n, o->alloc_ctx, st);
+    void* p = nullptr;
+    return cudaMallocAsync(&p, n, st) == cudaSuccess ? p : nullptr;
+  }
+  void put(void* p) const {
+    if (!p) return;
+    if (o && o->dev_free) o->dev_free(p, o->alloc_ctx, st);
+    else cudaFreeAsync(p, st);
+  }
+};
+
+// Bump layout over one allocation: measure, allocate, then hand out pointers.
+struct Layout {
+  size_t off = 0;
+  uint8_t* base = nullptr;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T) + 16;
+    return p;
+  }
+};
+
+// Owner of the memory behind one or more luda_outputs (shared by the jobs of a batch).
+struct Holder {
+  std::atomic<int> refs{1};
+  void* dev = nullptr;
+  luda_free_fn dev_free = nullptr;
+  void* ctx = nullptr;
+  uint8_t* pinned = nullptr;
+  size_t pinned_cap = 0;
+};
+
+// A small cache of pinned host buffers for table images (cudaHostAlloc is slow).
+std::mutex g_pin_mu;
+std::vector<std::pair<uint8_t*, size_t>> g_pin_free;
+
+uint8_t* pinned_get(size_t n, size_t* cap) {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    for (size_t i = 0; i < g_pin_free.size(); ++i)
+      if (g_pin_free[i].second >= n) {
+        auto pr = g_pin_free[i];
+        g_pin_free.erase(g_pin_free.begin() + long(i));
+        *cap = pr.second;
+        return pr.first;
+      }
+  }
+  void* p = nullptr;
+  const size_t want = n < 4096 ? 4096 : n;
+  if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+  *cap = want;
+  return static_cast<uint8_t*>(p);
+}
+
+void pinned_put(uint8_t* p, size_t cap) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.emplace_back(p, cap);
+  while (g_pin_free.size() > 2) {
+    cudaFreeHost(g_pin_free.front().first);
+    g_pin_free.erase(g_pin_free.begin());
+  }
+}
+
+void holder_release(Holder* h) {
+  if (!h) return;
+  if (--h->refs > 0) return;
+  if (h->dev) {
+    if (h->dev_free) h->dev_free(h->dev, h->ctx, nullptr);
+    else cudaFree(h->dev);
+  }
+  pinned_put(h->pinned, h->pinned_cap);
+  delete h;
+}
+
+struct OutPriv {
+  Holder* holder;
+  uint8_t* keys;
+};
+
+luda_status opts_check(const luda_options* o, Fmt* fmt) {
+  if (!o) {
+    set_detail("options pointer is NULL");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  if (o->block_size < 1 || o->restart_interval < 1 || o->restart_interval > 65535 || o->bloom_bits_per_key < 1 ||
+      o->bloom_bits_per_key > 64 || o->target_file_size < 1) {
+    set_detail("invalid options: block_size=%u restart_interval=%u bloom_bits_per_key=%u target=%llu",
+               o->block_size, o->restart_interval, o->bloom_bits_per_key,
+               (unsigned long long)o->target_file_size);
+    return LUDA_ERR_INVALID_ARG;
+  }
+  uint32_t k = o->bloom_bits_per_key * 69 / 100;
+  if (k < 1) k = 1;
+  if (k > 30) k = 30;
+  *fmt = Fmt{o->block_size, o->restart_interval, o->bloom_bits_per_key, k, o->target_file_size};
+  return LUDA_OK;
+}
+
+luda_status cuda_fail(cudaError_t e, const char* where) {
+  set_detail("%s: %s", where, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? LUDA_ERR_OOM : LUDA_ERR_CUDA;
+}
+
+#define CK(expr)                                          \
+  do {                                                    \
+    cudaError_t e_ = (expr);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr);   \
+  } while (0)
+
+luda_status err_status(const DErr& e, uint32_t job, uint32_t n_jobs) {
+  if (e.code == 0) return LUDA_OK;
+  if (e.input != ~0u)
+    set_detail("job %u of %u: input %u, byte offset %llu: %s", job, n_jobs, e.input, (unsigned long long)e.where,
+               luda_strerror(luda_status(e.code)));
+  else
+    set_detail("job %u of %u: %s (position %llu)", job, n_jobs, luda_strerror(luda_status(e.code)),
+               (unsigned long long)e.where);
+  return luda_status(e.code);
+}
+
+// ---- the pack stages, shared by compaction and build --------------------------------------
+struct PackBufs {
+  uint32_t *surv, *lcp, *sd, *dr, *next, *bpos, *blk_start, *fnext, *fpos, *file_start, *blk_file, *ie;
+  uint8_t *sflags, *fflags;
+  uint64_t *P, *bsz, *disk, *C, *IX, *fsize, *foff, *bmw, *bmoff, *klens, *koff;
+  FileDesc* files;
+  FileMeta* meta;
+  uint32_t* bitmap;
+  uint8_t* keybuf;
+  void *scan_tmp, *stitch_tmp;
+};
+
+void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t key_cap) {
+  b.surv = L.take<uint32_t>(cap + 1);
+  b.lcp = L.take<uint32_t>(cap + 1);
+  b.sd = L.take<uint32_t>(cap + 1);
+  b.dr = L.take<uint32_t>(cap + 1);
+  b.next = L.take<uint32_t>(cap + 1);
+  b.bpos = L.take<uint32_t>(cap + 1);
+  b.blk_start = L.take<uint32_t>(cap + 1);
+  b.fnext = L.take<uint32_t>(cap + 1);
+  b.fpos = L.take<uint32_t>(cap + 1);
+  b.file_start = L.take<uint32_t>(cap + 1);
+  b.blk_file = L.take<uint32_t>(cap + 1);
+  b.ie = L.take<uint32_t>(cap + 1);
+  b.sflags = L.take<uint8_t>(cap + 1);
+  b.fflags = L.take<uint8_t>(cap + 1);
+  b.P = L.take<uint64_t>(cap + 1);
+  b.bsz = L.take<uint64_t>(cap + 1);
+  b.disk = L.take<uint64_t>(cap + 1);
+  b.C = L.take<uint64_t>(cap + 1);
+  b.IX = L.take<uint64_t>(cap + 1);
+  b.fsize = L.take<uint64_t>(cap + 1);
+  b.foff = L.take<uint64_t>(cap + 1);
+  b.bmw = L.take<uint64_t>(cap + 1);
+  b.bmoff = L.take<uint64_t>(cap + 1);
+  b.klens = L.take<uint64_t>(cap + 1);
+  b.koff = L.take<uint64_t>(cap + 1);
+  b.files = L.take<FileDesc>(cap + 1);
+  b.meta = L.take<FileMeta>(cap + 1);
+  b.bitmap = L.take<uint32_t>(bm_cap + 1);
+  b.keybuf = L.take<uint8_t>(key_cap + 1);
+  b.scan_tmp = L.take<uint8_t>(scan_temp_bytes(cap + 1));
+  b.stitch_tmp = L.take<uint8_t>(stitch_temp_bytes(cap + 1));
+}
+
+// Survivors are in b.surv and cnt->n_surv is set; jobs[] hold surv ranges.
+luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DErr* errs, uint32_t cap, Recs recs,
+                     const uint8_t* arena, Fmt fmt, uint8_t* out, uint64_t out_cap, uint64_t bm_cap, CrcTabs tabs,
+                     cudaStream_t st) {
+  launch_sizes(b.surv, cnt, cap, jobs, n_jobs, recs, arena, b.lcp, b.sd, b.dr, st);
+  CK((exclusive_scan<uint32_t, uint64_t>(b.sd, b.P, cap, &cnt->n_surv, b.scan_tmp, st)));
+  launch_block_next(b.P, b.dr, cnt, cap, jobs, n_jobs, fmt, b.next, st);
+  launch_stitch(b.next, &cnt->n_surv, cap, b.sflags, b.stitch_tmp, st);
+  CK((exclusive_scan<uint8_t, uint32_t>(b.sflags, b.bpos, cap, &cnt->n_surv, b.scan_tmp, st)));
+  launch_compact_flags(b.sflags, b.bpos, &cnt->n_surv, cap, b.blk_start, &cnt->nb, st);
+  launch_job_blocks(jobs, n_jobs, b.bpos, st);
+  launch_block_sizes(b.blk_start, cnt, cap, b.P, b.dr, fmt, b.bsz, b.disk, st);
+  CK((exclusive_scan<uint64_t, uint64_t>(b.disk, b.C, cap, &cnt->nb, b.scan_tmp, st)));
+  launch_file_next(b.C, cnt, cap, jobs, n_jobs, fmt, b.fnext, st);
+  launch_stitch(b.fnext, &cnt->nb, cap, b.fflags, b.stitch_tmp, st);
+  CK((exclusive_scan<uint8_t, uint32_t>(b.fflags, b.fpos, cap, &cnt->nb, b.scan_tmp, st)));
+  launch_compact_flags(b.fflags, b.fpos, &cnt->nb, cap, b.file_start, &cnt->nf, st);
+  launch_job_files(jobs, n_jobs, b.fpos, st);
+  launch_block_file(b.fpos, cnt, cap, b.blk_file, st);
+  launch_index_sizes(b.blk_start, b.bsz, b.C, b.blk_file, b.file_start, cnt, cap, b.surv, recs, b.ie, st);
+  CK((exclusive_scan<uint32_t, uint64_t>(b.ie, b.IX, cap, &cnt->nb, b.scan_tmp, st)));
+  launch_file_layout(b.file_start, cnt, cap, b.blk_start, b.C, b.IX, fmt, jobs, n_jobs, b.files, b.fsize, b.bmw, st);
+  CK((exclusive_scan<uint64_t, uint64_t>(b.fsize, b.foff, cap, &cnt->nf, b.scan_tmp, st)));
+  CK((exclusive_scan<uint64_t, uint64_t>(b.bmw, b.bmoff, cap, &cnt->nf, b.scan_tmp, st)));
+  launch_file_offsets(b.files, cnt, cap, b.foff, b.bmoff, jobs, n_jobs, out_cap, bm_cap, errs, st);
+  launch_zero_bitmap(b.bitmap, cnt, bm_cap, st);
+  launch_encode(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena, fmt,
+                out, out_cap, tabs, st);
+  launch_bloom(b.surv, cnt, cap, b.blk_file, b.blk_start, b.files, recs, arena, fmt, b.bitmap, out_cap, bm_cap, st);
+  launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, out, out_cap,
+                     st);
+  launch_file_finish(b.files, cnt, cap, b.bitmap, b.surv, recs, fmt, out, out_cap, tabs, b.meta, st);
+  launch_key_lens(b.meta, cnt, cap, b.klens, st);
+  CK((exclusive_scan<uint64_t, uint64_t>(b.klens, b.koff, cap, &cnt->nf, b.scan_tmp, st)));
+  launch_key_gather(b.meta, cnt, cap, b.koff, b.files, b.surv, recs, arena, b.keybuf, st);
+  CK(cudaGetLastError());
+  return LUDA_OK;
+}
+
+Recs recs_layout(Layout& L, uint32_t n) {
+  Recs r;
+  r.pfx = L.take<uint64_t>(n + 1);
+  r.koff = L.take<uint64_t>(n + 1);
+  r.klen = L.take<uint32_t>(n + 1);
+  r.tr = L.take<uint64_t>(n + 1);
+  r.vptr = L.take<uint64_t>(n + 1);
+  r.vlen = L.take<uint32_t>(n + 1);
+  r.src = L.take<uint32_t>(n + 1);
+  return r;
+}
+
+// Collect: counts -> metadata and keys -> per-job luda_outputs.
+struct Collected {
+  Counts cnt;
+  std::vector<JobDev> jobs;
+  std::vector<DErr> errs;
+  std::vector<FileMeta> meta;
+  std::vector<uint8_t> keys;
+};
+
+luda_status collect(const Counts* d_cnt, const JobDev* d_jobs, const DErr* d_errs, const PackBufs& b, uint32_t n_jobs,
+                    Collected* c, cudaStream_t st) {
+  c->jobs.resize(n_jobs);
+  c->errs.resize(n_jobs);
+  CK(cudaMemcpyAsync(&c->cnt, d_cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(c->jobs.data(), d_jobs, sizeof(JobDev) * n_jobs, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(c->errs.data(), d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  c->meta.resize(c->cnt.nf);
+  c->keys.resize(c->cnt.key_bytes + 1);
+  if (c->cnt.nf) {
+    CK(cudaMemcpyAsync(c->meta.data(), b.meta, sizeof(FileMeta) * c->cnt.nf, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->keys.data(), b.keybuf, c->cnt.key_bytes, cudaMemcpyDeviceToHost, st));
+  }
+  return LUDA_OK;
+}
+
+void fill_outputs(const Collected& c, uint32_t n_jobs, uint8_t* out_base, Holder* h, luda_outputs* outs) {
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    luda_outputs& o = outs[j];
+    const JobDev& jd = c.jobs[j];
+    o.n_in_entries = jd.rec_end - jd.rec_begin;
+    if (o.status != LUDA_OK) continue;
+    const uint32_t nf = jd.file_end - jd.file_begin;
+    o.n_dropped = o.n_in_entries - (jd.surv_end - jd.surv_begin);
+    o.n_tables = nf;
+    uint64_t kb = 0;
+    for (uint32_t f = jd.file_begin; f < jd.file_end; ++f) kb += c.meta[f].small_len + c.meta[f].large_len;
+    o.tables = static_cast<luda_table*>(calloc(nf ? nf : 1, sizeof(luda_table)));
+    uint8_t* keys = static_cast<uint8_t*>(malloc(kb ? kb : 1));
+    uint64_t kp = 0;
+    for (uint32_t f = jd.file_begin; f < jd.file_end; ++f) {
+      const FileMeta& m = c.meta[f];
+      luda_table& t = o.tables[f - jd.file_begin];
+      t.data = out_base + m.off;
+      t.size = m.size;
+      t.n_entries = m.n_entries;
+      memcpy(keys + kp, c.keys.data() + m.small_koff, m.small_len);
+      t.smallest = keys + kp;
+      t.smallest_len = m.small_len;
+      kp += m.small_len;
+      memcpy(keys + kp, c.keys.data() + m.large_koff, m.large_len);
+      t.largest = keys + kp;
+      t.largest_len = m.large_len;
+      kp += m.large_len;
+    }
+    OutPriv* p = new OutPriv{h, keys};
+    ++h->refs;
+    o._priv = p;
+  }
+}
+
+struct HostJob {
+  const luda_input* inputs;
+  uint32_t n_inputs;
+  uint64_t snapshot;
+  int32_t bottommost;
+};
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  bool on = false;
+  void start(cudaStream_t st) {
+    on = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+    if (on) cudaEventRecord(a, st);
+  }
+  void stop(cudaStream_t st) {
+    if (on) cudaEventRecord(b, st);
+  }
+  double ms() {
+    float v = 0;
+    if (on && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&v, a, b);
+    return v;
+  }
+  ~Timer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+// The whole compaction for n_jobs jobs whose inputs are device pointers. On return
+// outs[j] hold device (or, with host_out, pinned host) tables.
+luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_options* o, cudaStream_t st,
+                           luda_outputs* outs, bool host_out, double* ms_device, double* ms_d2h) {
+  Fmt fmt;
+  luda_status rc = opts_check(o, &fmt);
+  if (rc) return rc;
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    memset(&outs[j], 0, sizeof(luda_outputs));
+    if (jobs[j].n_inputs && !jobs[j].inputs) {
+      set_detail("job %u: inputs is NULL", j);
+      return LUDA_ERR_INVALID_ARG;
+    }
+    for (uint32_t i = 0; i < jobs[j].n_inputs; ++i)
+      if (!jobs[j].inputs[i].data && jobs[j].inputs[i].size) {
+        set_detail("job %u input %u: data is NULL", j, i);
+        return LUDA_ERR_INVALID_ARG;
+      }
+  }
+  CrcTabs tabs;
+  if ((rc = get_tabs(&tabs))) return rc;
+  const DevMem mem{o, st};
+  Timer tdev;
+  tdev.start(st);
+
+  // ---- sizing: footers -------------------------------------------------------------------
+  std::vector<DInput> hin;
+  std::vector<uint64_t> job_in_bytes(n_jobs, 0);
+  std::vector<uint32_t> job_in_first(n_jobs + 1, 0);
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    job_in_first[j] = uint32_t(hin.size());
+    for (uint32_t i = 0; i < jobs[j].n_inputs; ++i) {
+      DInput d{};
+      d.data = jobs[j].inputs[i].data;
+      d.size = jobs[j].inputs[i].size;
+      d.job = j;
+      d.local = i;
+      hin.push_back(d);
+      job_in_bytes[j] += d.size;
+    }
+  }
+  job_in_first[n_jobs] = uint32_t(hin.size());
+  const uint32_t N = uint32_t(hin.size());
+
+  Layout LA;
+  DInput* d_in = LA.take<DInput>(N + 1);
+  DErr* d_errs = LA.take<DErr>(n_jobs + 1);
+  JobDev* d_jobs = LA.take<JobDev>(n_jobs + 1);
+  uint32_t* d_in_blk_first = LA.take<uint32_t>(N + 1);
+  Counts* d_cnt = LA.take<Counts>(1);
+  uint8_t* bufA = static_cast<uint8_t*>(mem.get(LA.off));
+  if (!bufA) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
+  {
+    const size_t used = LA.off;
+    LA = Layout{};
+    LA.base = bufA;
+    d_in = LA.take<DInput>(N + 1);
+    d_errs = LA.take<DErr>(n_jobs + 1);
+    d_jobs = LA.take<JobDev>(n_jobs + 1);
+    d_in_blk_first = LA.take<uint32_t>(N + 1);
+    d_cnt = LA.take<Counts>(1);
+    (void)used;
+  }
+  struct Guard {
+    const DevMem& m;
+    std::vector<void*> ps;
+    ~Guard() {
+      for (void* p : ps) m.put(p);
+    }
+  } guard{mem, {bufA}};
+
+  CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * (n_jobs + 1), st));
+  CK(cudaMemsetAsync(d_cnt, 0, sizeof(Counts), st));
+  if (N) CK(cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
+  launch_footers(d_in, N, d_errs, tabs, st);
+  CK(cudaGetLastError());
+  if (N) CK(cudaMemcpyAsync(hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<uint32_t> in_blk_first(N + 1, 0);
+  uint64_t NB64 = 0;
+  for (uint32_t i = 0; i < N; ++i) {
+    hin[i].blk_first = uint32_t(NB64);
+    in_blk_first[i] = uint32_t(NB64);
+    NB64 += hin[i].nblk;
+  }
+  in_blk_first[N] = uint32_t(NB64);
+  if (NB64 >= (1ull << 31)) {
+    set_detail("too many data blocks in one call (%llu)", (unsigned long long)NB64);
+    return LUDA_ERR_INVALID_ARG;
+  }
+  const uint32_t NB = uint32_t(NB64);
+  if (N) {
+    CK(cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_in_blk_first, in_blk_first.data(), sizeof(uint32_t) * (N + 1), cudaMemcpyHostToDevice, st));
+  }
+
+  // ---- sizing: block scan ------------------------------------------------------------------
+  Layout LB;
+  auto layoutB = [&](Layout& L, BlockDesc*& blocks, uint32_t*& nrec, uint64_t*& kbytes, uint32_t*& rec_first,
+                     uint64_t*& key_first, uint32_t*& in_rec, uint64_t*& in_key, void*& tmp) {
+    blocks = L.take<BlockDesc>(NB + 1);
+    nrec = L.take<uint32_t>(NB + 1);
+    kbytes = L.take<uint64_t>(NB + 1);
+    rec_first = L.take<uint32_t>(NB + 1);
+    key_first = L.take<uint64_t>(NB + 1);
+    in_rec = L.take<uint32_t>(N + 1);
+    in_key = L.take<uint64_t>(N + 1);
+    tmp = L.take<uint8_t>(scan_temp_bytes(NB + 1));
+  };
+  BlockDesc* d_blocks;
+  uint32_t *d_nrec, *d_rec_first, *d_in_rec;
+  uint64_t *d_kbytes, *d_key_first, *d_in_key;
+  void* d_tmpB;
+  layoutB(LB, d_blocks, d_nrec, d_kbytes, d_rec_first, d_key_first, d_in_rec, d_in_key, d_tmpB);
+  uint8_t* bufB = static_cast<uint8_t*>(mem.get(LB.off));
+  if (!bufB) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
+  guard.ps.push_back(bufB);
+  LB = Layout{};
+  LB.base = bufB;
+  layoutB(LB, d_blocks, d_nrec, d_kbytes, d_rec_first, d_key_first, d_in_rec, d_in_key, d_tmpB);
+
+  launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
+  launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, tabs, st);
+  launch_zero_failed(d_blocks, NB, d_errs, d_nrec, d_kbytes, st);
+  CK((exclusive_scan<uint32_t, uint32_t>(d_nrec, d_rec_first, NB, nullptr, d_tmpB, st)));
+  CK((exclusive_scan<uint64_t, uint64_t>(d_kbytes, d_key_first, NB, nullptr, d_tmpB, st)));
+  launch_input_ranges(d_in, N, d_rec_first, d_key_first, d_in_rec, d_in_key, st);
+  CK(cudaGetLastError());
+  std::vector<uint32_t> in_rec(N + 1);
+  std::vector<uint64_t> in_key(N + 1);
+  std::vector<DErr> herr(n_jobs + 1);
+  CK(cudaMemcpyAsync(in_rec.data(), d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(in_key.data(), d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(herr.data(), d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+
+  const uint32_t n_rec = in_rec[N];
+  const uint64_t K = in_key[N];
+  std::vector<JobDev> hjobs(n_jobs);
+  uint64_t out_cap = 4096, bm_cap = 64;
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    JobDev& jd = hjobs[j];
+    memset(&jd, 0, sizeof jd);
+    jd.snapshot = jobs[j].snapshot;
+    jd.bottommost = jobs[j].bottommost ? 1u : 0u;
+    jd.flags = o->flags;
+    jd.rec_begin = in_rec[job_in_first[j]];
+    jd.rec_end = in_rec[job_in_first[j + 1]];
+    const uint64_t nj = jd.rec_end - jd.rec_begin;
+    const uint64_t kj = in_key[job_in_first[j + 1]] - in_key[job_in_first[j]];
+    // Output bound: data <= K + V + 24n; index <= K + 31n + 9 per table; filter, metaindex and
+    // footer <= n*bpk/8 + 116 per table; tables <= n.
+    out_cap += 2 * kj + job_in_bytes[j] + 200 * nj + 256;
+    bm_cap += nj * fmt.bpk / 32 + 5 * nj + 8;
+  }
+  // merge schedule: each input is a sorted run; merge neighbours pairwise until one run per job
+  struct Run {
+    uint32_t b, n;
+  };
+  std::vector<std::vector<Run>> runs(n_jobs);
+  for (uint32_t j = 0; j < n_jobs; ++j)
+    for (uint32_t i = job_in_first[j]; i < job_in_first[j + 1]; ++i)
+      if (in_rec[i + 1] > in_rec[i]) runs[j].push_back(Run{in_rec[i], in_rec[i + 1] - in_rec[i]});
+  std::vector<MergeSpan> spans;
+  std::vector<uint32_t> pass_span0, pass_nspans, pass_ntiles;
+  uint32_t max_tiles = 1;
+  while (true) {
+    bool more = false;
+    for (auto& r : runs) more |= r.size() > 1;
+    if (!more) break;
+    pass_span0.push_back(uint32_t(spans.size()));
+    uint32_t tiles = 0;
+    for (auto& r : runs) {
+      std::vector<Run> nr;
+      for (size_t k = 0; k < r.size(); k += 2) {
+        MergeSpan sp{r[k].b, r[k].n, k + 1 < r.size() ? r[k + 1].n : 0u, tiles};
+        tiles += (sp.a_len + sp.b_len + kMergeTile - 1) / kMergeTile;
+        spans.push_back(sp);
+        nr.push_back(Run{sp.a_begin, sp.a_len + sp.b_len});
+      }
+      r.swap(nr);
+    }
+    pass_nspans.push_back(uint32_t(spans.size()) - pass_span0.back());
+    pass_ntiles.push_back(tiles);
+    if (tiles > max_tiles) max_tiles = tiles;
+  }
+
+  // ---- execute -------------------------------------------------------------------------------
+  const uint32_t cap = n_rec;
+  const uint64_t key_cap = 2 * K + 64;
+  Layout LC;
+  Recs recs;
+  uint8_t* d_arena;
+  uint32_t *d_ord0, *d_ord1, *d_keep, *d_pos, *d_co;
+  uint64_t *d_pfx0, *d_pfx1;
+  MergeSpan* d_spans;
+  PackBufs pb;
+  auto layoutC = [&](Layout& L) {
+    recs = recs_layout(L, n_rec);
+    d_arena = L.take<uint8_t>(K + 16);
+    d_ord0 = L.take<uint32_t>(n_rec + 1);
+    d_ord1 = L.take<uint32_t>(n_rec + 1);
+    d_pfx0 = L.take<uint64_t>(n_rec + 1);
+    d_pfx1 = L.take<uint64_t>(n_rec + 1);
+    d_keep = L.take<uint32_t>(n_rec + 1);
+    d_pos = L.take<uint32_t>(n_rec + 1);
+    d_co = L.take<uint32_t>(max_tiles + 1);
+    d_spans = L.take<MergeSpan>(spans.size() + 1);
+    pack_layout(L, pb, cap, bm_cap, key_cap);
+  };
+  layoutC(LC);
+  uint8_t* bufC = static_cast<uint8_t*>(mem.get(LC.off));
+  if (!bufC) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
+  guard.ps.push_back(bufC);
+  LC = Layout{};
+  LC.base = bufC;
+  layoutC(LC);
+  uint8_t* d_out = static_cast<uint8_t*>(mem.get(out_cap));
+  if (!d_out) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
+  bool out_owned = false;
+  struct OutGuard {
+    const DevMem& m;
+    uint8_t* p;
+    bool* owned;
+    ~OutGuard() {
+      if (!*owned) m.put(p);
+    }
+  } out_guard{mem, d_out, &out_owned};
+
+  Counts hc{};
+  hc.n_rec = n_rec;
+  CK(cudaMemcpyAsync(d_cnt, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_jobs, hjobs.data(), sizeof(JobDev) * n_jobs, cudaMemcpyHostToDevice, st));
+  if (!spans.empty())
+    CK(cudaMemcpyAsync(d_spans, spans.data(), sizeof(MergeSpan) * spans.size(), cudaMemcpyHostToDevice, st));
+
+  launch_decode(d_blocks, NB, d_in, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
+  launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
+  launch_sort_init(d_ord0, d_pfx0, recs.pfx, n_rec, st);
+  uint32_t* src_o = d_ord0;
+  uint32_t* dst_o = d_ord1;
+  uint64_t* src_p = d_pfx0;
+  uint64_t* dst_p = d_pfx1;
+  for (size_t p = 0; p < pass_span0.size(); ++p) {
+    launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], d_co, src_o, src_p, dst_o, dst_p, recs,
+                      d_arena, st);
+    std::swap(src_o, dst_o);
+    std::swap(src_p, dst_p);
+  }
+  launch_gc_flags(src_o, n_rec, d_jobs, n_jobs, recs, d_arena, d_keep, d_errs, st);
+  CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
+  launch_gc_compact(src_o, d_keep, d_pos, n_rec, pb.surv, st);
+  launch_job_surv(d_jobs, n_jobs, d_pos, n_rec, d_cnt, st);
+  CK(cudaGetLastError());
+  if ((rc = run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap, tabs, st)))
+    return rc;
+  tdev.stop(st);
+
+  // ---- collect -------------------------------------------------------------------------------
+  Collected col;
+  if ((rc = collect(d_cnt, d_jobs, d_errs, pb, n_jobs, &col, st))) return rc;
+  Holder* h = new Holder();
+  uint8_t* base = d_out;
+  double d2h = 0;
+  if (host_out) {
+    h->pinned = pinned_get(col.cnt.out_bytes + 16, &h->pinned_cap);
+    if (!h->pinned) {
+      holder_release(h);
+      return cuda_fail(cudaErrorMemoryAllocation, "pinned host allocation");
+    }
+    Timer t;
+    t.start(st);
+    if (col.cnt.out_bytes)
+      if (cudaMemcpyAsync(h->pinned, d_out, col.cnt.out_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        holder_release(h);
+        return cuda_fail(cudaGetLastError(), "copy of the new tables to the host");
+      }
+    t.stop(st);
+    d2h = t.ms();
+    base = h->pinned;
+  } else {
+    h->dev = d_out;
+    h->dev_free = o->dev_free;
+    h->ctx = o->alloc_ctx;
+    out_owned = true;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    holder_release(h);
+    return cuda_fail(cudaGetLastError(), "stream synchronize");
+  }
+  const double dev_ms = tdev.ms();
+  if (ms_device) *ms_device = dev_ms;
+  if (ms_d2h) *ms_d2h = d2h;
+  luda_status first = LUDA_OK;
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    outs[j].status = err_status(col.errs[j], j, n_jobs);
+    if (outs[j].status && !first) first = luda_status(outs[j].status);
+  }
+  fill_outputs(col, n_jobs, base, h, outs);
+  holder_release(h);
+  if (first) {
+    // keep the detail of the first failing job
+    for (uint32_t j = 0; j < n_jobs; ++j)
+      if (outs[j].status) {
+        err_status(col.errs[j], j, n_jobs);
+        break;
+      }
+  }
+  return LUDA_OK;
+}
+
+
+// Build tables from one sorted run (memtable flush): records straight from the run's
+// arrays, then the same pack stages as a compaction.
+luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, luda_outputs* out, bool host_out) {
+  Fmt fmt;
+  luda_status rc = opts_check(o, &fmt);
+  if (rc) return rc;
+  memset(out, 0, sizeof *out);
+  if (!run) {
+    set_detail("run is NULL");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  const uint64_t n64 = run->n;
+  if (n64 >= (1ull << 31)) {
+    set_detail("run too large (%llu entries)", (unsigned long long)n64);
+    return LUDA_ERR_INVALID_ARG;
+  }
+  if (!run->ukoff || !run->voff || (n64 && (!run->ukeys || !run->seqs || !run->types || !run->vals))) {
+    set_detail("run arrays are NULL");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  const uint32_t n = uint32_t(n64);
+  CrcTabs tabs;
+  if ((rc = get_tabs(&tabs))) return rc;
+  const cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+  const DevMem mem{o, st};
+  uint64_t ku = 0, vb = 0;
+  if (host_in) {
+    ku = run->ukoff[n];
+    vb = run->voff[n];
+  } else {
+    CK(cudaMemcpyAsync(&ku, run->ukoff + n, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&vb, run->voff + n, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  const uint64_t K = ku + 8ull * n;
+  const uint64_t out_cap = 2 * K + vb + 200ull * n + 4096;
+  const uint64_t bm_cap = uint64_t(n) * fmt.bpk / 32 + 5ull * n + 64;
+  Layout L;
+  Recs recs;
+  uint8_t *arena, *h_ukeys, *h_types, *h_vals;
+  uint64_t *h_ukoff, *h_seqs, *h_voff;
+  DErr* d_err;
+  JobDev* d_job;
+  Counts* d_cnt;
+  PackBufs pb;
+  auto lay = [&](Layout& l) {
+    recs = recs_layout(l, n);
+    arena = l.take<uint8_t>(K + 16);
+    d_err = l.take<DErr>(1);
+    d_job = l.take<JobDev>(1);
+    d_cnt = l.take<Counts>(1);
+    pack_layout(l, pb, n, bm_cap, 2 * K + 64);
+    if (host_in) {
+      h_ukeys = l.take<uint8_t>(ku + 16);
+      h_ukoff = l.take<uint64_t>(n + 1);
+      h_seqs = l.take<uint64_t>(n + 1);
+      h_types = l.take<uint8_t>(n + 1);
+      h_vals = l.take<uint8_t>(vb + 16);
+      h_voff = l.take<uint64_t>(n + 1);
+    }
+  };
+  lay(L);
+  uint8_t* buf = static_cast<uint8_t*>(mem.get(L.off));
+  if (!buf) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
+  uint8_t* d_out = static_cast<uint8_t*>(mem.get(out_cap));
+  if (!d_out) {
+    mem.put(buf);
+    return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
+  }
+  bool out_owned = false;
+  struct G {
+    const DevMem& m;
+    uint8_t* a;
+    uint8_t* b;
+    bool* owned;
+    ~G() {
+      m.put(a);
+      if (!*owned) m.put(b);
+    }
+  } g{mem, buf, d_out, &out_owned};
+  L = Layout{};
+  L.base = buf;
+  lay(L);
+  const uint8_t *ukeys = run->ukeys, *types = run->types, *vals = run->vals;
+  const uint64_t *ukoff = run->ukoff, *seqs = run->seqs, *voff = run->voff;
+  Timer th;
+  th.start(st);
+  if (host_in) {
+    if (ku) CK(cudaMemcpyAsync(h_ukeys, run->ukeys, ku, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h_ukoff, run->ukoff, 8ull * (n + 1), cudaMemcpyHostToDevice, st));
+    if (n) {
+      CK(cudaMemcpyAsync(h_seqs, run->seqs, 8ull * n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(h_types, run->types, n, cudaMemcpyHostToDevice, st));
+    }
+    if (vb) CK(cudaMemcpyAsync(h_vals, run->vals, vb, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h_voff, run->voff, 8ull * (n + 1), cudaMemcpyHostToDevice, st));
+    ukeys = h_ukeys;
+    types = h_types;
+    vals = h_vals;
+    ukoff = h_ukoff;
+    seqs = h_seqs;
+    voff = h_voff;
+  }
+  th.stop(st);
+  Timer td;
+  td.start(st);
+  JobDev jd{};
+  jd.rec_end = n;
+  jd.surv_end = n;
+  Counts hc{};
+  hc.n_rec = n;
+  hc.n_surv = n;
+  CK(cudaMemsetAsync(d_err, 0, sizeof(DErr), st));
+  CK(cudaMemcpyAsync(d_job, &jd, sizeof jd, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_cnt, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+  launch_build_records(ukeys, ukoff, seqs, types, vals, voff, n, recs, arena, pb.surv, d_err, st);
+  launch_build_check(recs, arena, n, d_err, st);
+  CK(cudaGetLastError());
+  if ((rc = run_pack(pb, d_cnt, d_job, 1, d_err, n, recs, arena, fmt, d_out, out_cap, bm_cap, tabs, st))) return rc;
+  td.stop(st);
+  Collected col;
+  if ((rc = collect(d_cnt, d_job, d_err, pb, 1, &col, st))) return rc;
+  Holder* h = new Holder();
+  uint8_t* base = d_out;
+  double d2h = 0;
+  if (host_out) {
+    h->pinned = pinned_get(col.cnt.out_bytes + 16, &h->pinned_cap);
+    if (!h->pinned) {
+      holder_release(h);
+      return cuda_fail(cudaErrorMemoryAllocation, "pinned host allocation");
+    }
+    Timer t;
+    t.start(st);
+    if (col.cnt.out_bytes) CK(cudaMemcpyAsync(h->pinned, d_out, col.cnt.out_bytes, cudaMemcpyDeviceToHost, st));
+    t.stop(st);
+    d2h = t.ms();
+    base = h->pinned;
+  } else {
+    h->dev = d_out;
+    h->dev_free = o->dev_free;
+    h->ctx = o->alloc_ctx;
+    out_owned = true;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    holder_release(h);
+    return cuda_fail(cudaGetLastError(), "stream synchronize");
+  }
+  out->status = err_status(col.errs[0], 0, 1);
+  fill_outputs(col, 1, base, h, out);
+  holder_release(h);
+  out->n_in_entries = n;
+  out->n_dropped = 0;
+  out->ms_h2d = host_in ? th.ms() : 0;
+  out->ms_device = td.ms();
+  out->ms_d2h = d2h;
+  if (out->status) {
+    const luda_status s = luda_status(out->status);
+    luda_outputs_free(out);
+    out->status = s;
+    return s;
+  }
+  return LUDA_OK;
+}
+
+}  // namespace
+
+// =========================================================================================
+extern "C" {
+
+void luda_options_default(luda_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->block_size = 4096;
+  o->restart_interval = 16;
+  o->bloom_bits_per_key = 10;
+  o->target_file_size = 2ull << 20;
+}
+
+const char* luda_strerror(luda_status s) {
+  switch (s) {
+    case LUDA_OK: return "ok";
+    case LUDA_ERR_INVALID_ARG: return "invalid argument";
+    case LUDA_ERR_CORRUPTION: return "corrupt input table";
+    case LUDA_ERR_NOT_SUPPORTED: return "not supported (compressed block)";
+    case LUDA_ERR_OOM: return "out of memory";
+    case LUDA_ERR_CUDA: return "CUDA error";
+    case LUDA_ERR_TIMEOUT: return "device wait timed out";
+    case LUDA_ERR_DUPLICATE_KEY: return "duplicate internal key";
+    case LUDA_ERR_PLAN_MISMATCH: return "plan no longer matches its inputs";
+  }
+  return "unknown status";
+}
+
+const char* luda_last_error_detail(void) { return t_detail; }
+
+const char* luda_version(void) { return "luda-b300 0.1 (sm_103a)"; }
+
+void luda_outputs_free(luda_outputs* out) {
+  if (!out) return;
+  OutPriv* p = static_cast<OutPriv*>(out->_priv);
+  if (p) {
+    free(p->keys);
+    holder_release(p->holder);
+    delete p;
+  }
+  free(out->tables);
+  memset(out, 0, sizeof *out);
+}
+
+luda_status luda_batch_compact_device(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts,
+                                      luda_outputs* outs) {
+  t_detail[0] = 0;
+  if ((!jobs && n_jobs) || !outs) {
+    set_detail("jobs or outs is NULL");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  std::vector<HostJob> hj(n_jobs);
+  for (uint32_t j = 0; j < n_jobs; ++j) hj[j] = HostJob{jobs[j].inputs, jobs[j].n_inputs, jobs[j].smallest_snapshot,
+                                                        jobs[j].bottommost};
+  const cudaStream_t st = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
+  double ms = 0;
+  luda_status rc = run_compaction(hj.data(), n_jobs, opts, st, outs, false, &ms, nullptr);
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    if (rc) outs[j].status = rc;
+    outs[j].ms_device = ms;
+  }
+  return rc;
+}
+
+luda_status luda_compact_device(const luda_input* inputs, uint32_t n_inputs, int32_t level, uint64_t smallest_snapshot,
+                                const luda_options* opts, luda_outputs* out) {
+  (void)level;
+  t_detail[0] = 0;
+  if (!out || (!inputs && n_inputs) || !opts) {
+    set_detail("NULL argument");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  HostJob hj{inputs, n_inputs, smallest_snapshot, opts->bottommost};
+  const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+  double ms = 0;
+  luda_status rc = run_compaction(&hj, 1, opts, st, out, false, &ms, nullptr);
+  if (rc) {
+    out->status = rc;
+    return rc;
+  }
+  out->ms_device = ms;
+  if (out->status) {
+    const luda_status s = luda_status(out->status);
+    luda_outputs_free(out);
+    out->status = s;
+    return s;
+  }
+  return LUDA_OK;
+}
+
+luda_status luda_compact(const luda_input* inputs, uint32_t n_inputs, int32_t level, uint64_t smallest_snapshot,
+                         const luda_options* opts, luda_outputs* out) {
+  (void)level;
+  t_detail[0] = 0;
+  if (!out || (!inputs && n_inputs) || !opts) {
+    set_detail("NULL argument");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  memset(out, 0, sizeof *out);
+  const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+  const DevMem mem{opts, st};
+  // one device arena for all inputs, each at a 256-byte boundary
+  std::vector<uint64_t> off(n_inputs + 1, 0);
+  for (uint32_t i = 0; i < n_inputs; ++i) {
+    if (!inputs[i].data && inputs[i].size) {
+      set_detail("input %u: data is NULL", i);
+      return LUDA_ERR_INVALID_ARG;
+    }
+    off[i + 1] = (off[i] + inputs[i].size + 255) & ~uint64_t(255);
+  }
+  CrcTabs tabs;
+  luda_status rc = get_tabs(&tabs);
+  if (rc) return rc;
+  uint8_t* arena = static_cast<uint8_t*>(mem.get(off[n_inputs] + 256));
+  if (!arena) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
+  std::vector<luda_input> din(n_inputs);
+  Timer th;
+  th.start(st);
+  for (uint32_t i = 0; i < n_inputs; ++i) {
+    din[i] = inputs[i];
+    din[i].data = arena + off[i];
+    if (inputs[i].size &&
+        cudaMemcpyAsync(arena + off[i], inputs[i].data, inputs[i].size, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      mem.put(arena);
+      return cuda_fail(cudaGetLastError(), "copy of the inputs to the device");
+    }
+  }
+  th.stop(st);
+  HostJob hj{din.data(), n_inputs, smallest_snapshot, opts->bottommost};
+  double ms = 0, d2h = 0;
+  rc = run_compaction(&hj, 1, opts, st, out, true, &ms, &d2h);
+  const double h2d = th.ms();
+  mem.put(arena);
+  cudaStreamSynchronize(st);
+  if (rc) {
+    out->status = rc;
+    return rc;
+  }
+  out->ms_h2d = h2d;
+  out->ms_device = ms;
+  out->ms_d2h = d2h;
+  if (out->status) {
+    const luda_status s = luda_status(out->status);
+    luda_outputs_free(out);
+    out->status = s;
+    return s;
+  }
+  return LUDA_OK;
+}
+
+luda_status luda_build(const luda_run* run, const luda_options* opts, luda_outputs* out) {
+  t_detail[0] = 0;
+  if (!out) return LUDA_ERR_INVALID_ARG;
+  return run_build(run, true, opts, out, true);
+}
+
+luda_status luda_build_device(const luda_run* run, const luda_options* opts, luda_outputs* out) {
+  t_detail[0] = 0;
+  if (!out) return LUDA_ERR_INVALID_ARG;
+  return run_build(run, false, opts, out, false);
+}
+
+}  // extern "C"

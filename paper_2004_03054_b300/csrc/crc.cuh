@@ -1,0 +1,122 @@
+// crc.cuh -- warp-parallel CRC-32C (Castagnoli) for block trailers.
+//
+// Block checksums are verified per data block when unpacking and computed per block when
+// packing (LUDA §II-A Phases 1 and 3; §III-C "unpack" and "encode" kernels). Reflected
+// polynomial 0x82F63B78, init and final XOR 0xFFFFFFFF.
+//
+// Method (linear-algebra view of a CRC, e.g. as used for combining CRCs of
+// concatenated messages):
+//   * Let F(M) be the register after feeding M into a zero register. F is linear over
+//     GF(2) and F(A || B) = Z_|B|(F(A)) xor F(B), where Z_L is the linear map "feed L zero
+//     bytes" (multiplication by x^{8L} modulo the polynomial).
+//   * Leading zero bytes do not change F, so the message is widened to whole aligned
+//     16-byte words by zero bytes in front; the trailing pad of p zero bytes is removed
+//     with the inverse map Z_{-p}.
+//   * Starting the register at 0xFFFFFFFF equals XOR-ing 0xFF into the first four message
+//     bytes with a zero register (valid for messages of at least 4 bytes).
+//   * Each lane folds an equal, contiguous run of aligned words (slicing-by-4 tables in
+//     shared memory); a 5-level butterfly joins neighbouring runs with Z_{run length},
+//     applied with four 256-entry lookup tables per shift length.
+// The tables are generated on the host from the polynomial (crc_tables.cu).
+#pragma once
+
+#include <cstdint>
+
+namespace luda {
+
+// Shift tables: index j in [0, 32) shifts by 16 << j bytes; index 32 + (p - 1) for p in
+// [1, 16) applies the inverse shift by p bytes. Each table: 4 x 256 words.
+constexpr int kShiftPow = 32;
+constexpr int kShiftInv = 15;
+constexpr int kShiftTables = kShiftPow + kShiftInv;
+
+struct CrcTabs {
+  const uint32_t* slice;  // 4 x 256: slice[k*256 + v] = register after k+1 byte steps of v
+  const uint32_t* shift;  // kShiftTables x 4 x 256
+};
+
+// One 4-byte step with slicing-by-4 tables in shared memory.
+__device__ __forceinline__ uint32_t crc_step4(uint32_t crc, uint32_t w, const uint32_t* sT) {
+  crc ^= w;
+  return sT[768 + (crc & 0xFFu)] ^ sT[512 + ((crc >> 8) & 0xFFu)] ^ sT[256 + ((crc >> 16) & 0xFFu)] ^
+         sT[crc >> 24];
+}
+
+__device__ __forceinline__ uint32_t crc_shift(const uint32_t* tab, uint32_t v) {
+  return __ldg(tab + (v & 0xFFu)) ^ __ldg(tab + 256 + ((v >> 8) & 0xFFu)) ^
+         __ldg(tab + 512 + ((v >> 16) & 0xFFu)) ^ __ldg(tab + 768 + (v >> 24));
+}
+
+// Bytes of a little-endian word at byte address q that fall outside [ps, pe) become 0;
+// bytes inside [ps, ps + 4) are complemented (the register init).
+__device__ __forceinline__ uint32_t crc_fix_word(uint32_t w, uintptr_t q, uintptr_t ps, uintptr_t pe) {
+  uint32_t keep = 0, flip = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const uintptr_t x = q + b;
+    if (x >= ps && x < pe) {
+      keep |= 0xFFu << (8 * b);
+      if (x < ps + 4) flip |= 0xFFu << (8 * b);
+    }
+  }
+  return (w & keep) ^ flip;
+}
+
+// Standard CRC-32C of the n bytes at p (generic address: global or shared memory).
+// All 32 lanes of the warp must call it with the same arguments; every lane gets the
+// result. The 16-byte words that contain p[0..n) are read whole (bytes outside are
+// ignored), so the memory around the range must be readable to the next 16-byte bounds.
+// `sT` is the slicing table (1024 words) staged in shared memory by the caller.
+static __device__ __noinline__ uint32_t warp_crc32c(const uint8_t* p, uint64_t n, const uint32_t* sT, const CrcTabs tabs) {
+  const uint32_t lane = threadIdx.x & 31u;
+  if (n < 16) {  // short message: lane 0 alone, byte at a time
+    uint32_t c = 0xFFFFFFFFu;
+    if (lane == 0)
+      for (uint64_t i = 0; i < n; ++i) c = sT[(c ^ p[i]) & 0xFFu] ^ (c >> 8);
+    c = __shfl_sync(0xFFFFFFFFu, c, 0);
+    return c ^ 0xFFFFFFFFu;
+  }
+  const uintptr_t ps = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t pe = ps + n;
+  const uintptr_t a0 = ps & ~uintptr_t(15);
+  const uintptr_t a1 = (pe + 15) & ~uintptr_t(15);
+  const uint32_t pad = uint32_t(a1 - pe);
+  const int64_t W = int64_t((a1 - a0) >> 4);
+  uint32_t j = 0;
+  while ((int64_t(32) << j) < W) ++j;
+  const int64_t cw = int64_t(1) << j;
+  int64_t w0 = W - cw * int64_t(32 - lane);
+  const int64_t w1 = w0 + cw;
+  if (w0 < 0) w0 = 0;
+  uint32_t crc = 0;
+#pragma unroll 1
+  for (int64_t w = w0; w < w1; ++w) {
+    const uintptr_t q = a0 + (uintptr_t(w) << 4);
+    uint4 v = *reinterpret_cast<const uint4*>(q);
+    if (q < ps + 4 || q + 16 > pe) {
+      v.x = crc_fix_word(v.x, q, ps, pe);
+      v.y = crc_fix_word(v.y, q + 4, ps, pe);
+      v.z = crc_fix_word(v.z, q + 8, ps, pe);
+      v.w = crc_fix_word(v.w, q + 12, ps, pe);
+    }
+    crc = crc_step4(crc, v.x, sT);
+    crc = crc_step4(crc, v.y, sT);
+    crc = crc_step4(crc, v.z, sT);
+    crc = crc_step4(crc, v.w, sT);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const uint32_t other = __shfl_xor_sync(0xFFFFFFFFu, crc, 1u << k);
+    const uint32_t* tab = tabs.shift + size_t(j + k) * 1024;
+    crc = (lane & (1u << k)) ? (crc_shift(tab, other) ^ crc) : (crc_shift(tab, crc) ^ other);
+  }
+  if (pad) crc = crc_shift(tabs.shift + size_t(kShiftPow + pad - 1) * 1024, crc);
+  return crc ^ 0xFFFFFFFFu;
+}
+
+// Stage the slicing table into shared memory (1024 words), whole CTA.
+__device__ __forceinline__ void load_slice_table(uint32_t* sT, const CrcTabs tabs) {
+  for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) sT[i] = __ldg(tabs.slice + i);
+}
+
+}  // namespace luda

@@ -1,0 +1,354 @@
+// decode.cu -- Phase 1 "Unpack" (LUDA §II-A; §III-C "unpack" kernel, Fig. 4a).
+//
+// Per input table: parse the footer and verify the index block. Per data block (there
+// are no data dependencies among data blocks, §III-C): verify the trailer CRC and the
+// block structure, count entries, then restore every full key from the shared prefixes
+// into a key arena and emit one record per entry. Values are not copied: a record keeps
+// the device address of its value inside the input table, so values move exactly once,
+// from the input straight into the output block (the paper's "lazy value movement" of
+// §III-D taken one step further).
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace luda {
+
+namespace {
+
+__device__ __forceinline__ bool handle_ok(uint64_t off, uint64_t size, uint64_t limit) {
+  return off <= limit && size <= limit - off && uint64_t(kTrailer) <= limit - off - size;
+}
+
+// One warp per input: footer, index block CRC and type, index restart count.
+__global__ void __launch_bounds__(32) k_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcTabs tabs) {
+  __shared__ uint32_t sT[1024];
+  load_slice_table(sT, tabs);
+  __syncthreads();
+  const uint32_t lane = lane_id();
+  for (uint32_t i = blockIdx.x; i < n_inputs; i += gridDim.x) {
+    const uint8_t* f = in[i].data;
+    const uint64_t size = in[i].size;
+    DErr* e = errs + in[i].job;
+    const uint32_t local = in[i].local;
+    uint64_t ioff = 0, isize = 0;
+    int ok = 0;
+    if (lane == 0) {
+      if (size >= kFooter && ld_u64(f + size - 8) == kMagic) {
+        const uint8_t* p = f + size - kFooter;
+        const uint8_t* end = p + 40;
+        uint64_t moff = 0, msize = 0;
+        uint32_t a = get_varint<64>(p, end, &moff);
+        if (a) a = (p += a, get_varint<64>(p, end, &msize));
+        if (a) a = (p += a, get_varint<64>(p, end, &ioff));
+        if (a) a = (p += a, get_varint<64>(p, end, &isize));
+        const uint64_t limit = size - kFooter;
+        ok = a && handle_ok(moff, msize, limit) && handle_ok(ioff, isize, limit);
+      }
+      if (!ok) report(e, E_CORRUPT, local, size);
+    }
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    ioff = __shfl_sync(0xFFFFFFFFu, ioff, 0);
+    isize = __shfl_sync(0xFFFFFFFFu, isize, 0);
+    uint32_t nblk = 0;
+    if (ok) {
+      const uint32_t got = warp_crc32c(f + ioff, isize + 1, sT, tabs);
+      if (lane == 0) {
+        const uint32_t want = crc_unmask(ld_u32(f + ioff + isize + 1));
+        if (got != want) {
+          report(e, E_CORRUPT, local, ioff);
+        } else if (f[ioff + isize] != 0) {
+          report(e, E_NOTSUP, local, ioff);
+        } else {
+          const uint64_t nr = isize >= 4 ? ld_u32(f + ioff + isize - 4) : 0;
+          if (nr >= 1 && nr <= (isize - 4) / 4) nblk = uint32_t(nr);
+          else report(e, E_CORRUPT, local, ioff);
+        }
+      }
+    }
+    if (lane == 0) {
+      in[i].idx_off = ioff;
+      in[i].idx_size = isize;
+      in[i].nblk = nblk;
+    }
+  }
+}
+
+// One thread per data block: its index entry (restart interval 1, so every entry starts
+// a restart segment and all decode independently) gives the block handle.
+__global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs,
+                                const uint32_t* __restrict__ in_blk_first, uint32_t n_blocks,
+                                BlockDesc* __restrict__ blocks, DErr* errs) {
+  for (uint64_t g = gtid(); g < n_blocks; g += gstride()) {
+    uint32_t lo = 0, hi = n_inputs;  // last input with blk_first <= g
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (in_blk_first[mid] <= g) lo = mid;
+      else hi = mid;
+    }
+    const DInput d = in[lo];
+    const uint32_t k = uint32_t(g - in_blk_first[lo]);
+    BlockDesc out{nullptr, 0, 0, lo, d.job};
+    const uint8_t* ib = d.data + d.idx_off;
+    const uint64_t rstart = d.idx_size - 4 - 4ull * d.nblk;
+    const uint64_t s = ld_u32(ib + rstart + 4ull * k);
+    const uint64_t e = k + 1 < d.nblk ? ld_u32(ib + rstart + 4ull * (k + 1)) : rstart;
+    bool ok = !(k == 0 && s != 0) && s < e && e <= rstart;
+    if (ok) {
+      const uint8_t* p = ib + s;
+      const uint8_t* end = ib + e;
+      uint64_t shared = 0, nonshared = 0, vlen = 0;
+      uint32_t a = get_varint<32>(p, end, &shared);
+      if (a) a = (p += a, get_varint<32>(p, end, &nonshared));
+      if (a) a = (p += a, get_varint<32>(p, end, &vlen));
+      if (a) p += a;
+      ok = a && shared == 0 && nonshared <= uint64_t(end - p) && vlen <= uint64_t(end - p) - nonshared;
+      if (ok) {
+        p += nonshared;
+        ok = p + vlen == end;
+      }
+      uint64_t off = 0, size = 0;
+      if (ok) {
+        const uint8_t* vend = p + vlen;
+        uint32_t b = get_varint<64>(p, vend, &off);
+        if (b) b = (p += b, get_varint<64>(p, vend, &size));
+        ok = b && p + b == vend && handle_ok(off, size, d.size - kFooter);
+      }
+      if (ok) {
+        out.ptr = d.data + off;
+        out.size = size;
+        out.off = off;
+      }
+    }
+    if (!ok) report(errs + d.job, E_CORRUPT, d.local, d.idx_off + rstart + 4ull * k);
+    blocks[g] = out;
+  }
+}
+
+// Walk one restart segment [s, e) of a data block: headers only. Returns false on a
+// structure violation; adds entries and key bytes.
+__device__ __forceinline__ bool walk_segment(const uint8_t* base, uint64_t s, uint64_t e, uint32_t* cnt,
+                                             uint64_t* kbytes) {
+  const uint8_t* p = base + s;
+  const uint8_t* end = base + e;
+  uint64_t prev = 0;
+  bool first = true;
+  while (p < end) {
+    uint64_t shared, nonshared, vlen;
+    uint32_t a = get_varint<32>(p, end, &shared);
+    if (!a) return false;
+    p += a;
+    a = get_varint<32>(p, end, &nonshared);
+    if (!a) return false;
+    p += a;
+    a = get_varint<32>(p, end, &vlen);
+    if (!a) return false;
+    p += a;
+    if ((first && shared != 0) || shared > prev) return false;
+    if (nonshared > uint64_t(end - p) || vlen > uint64_t(end - p) - nonshared) return false;
+    const uint64_t klen = shared + nonshared;
+    if (klen < 8) return false;
+    p += nonshared + vlen;
+    prev = klen;
+    first = false;
+    *cnt += 1;
+    *kbytes += klen;
+  }
+  return true;
+}
+
+// One warp per data block: CRC, type, structure; entry and key-byte counts.
+__global__ void __launch_bounds__(256) k_block_scan(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
+                                                    const DInput* __restrict__ in, uint32_t* __restrict__ nrec,
+                                                    uint64_t* __restrict__ kbytes, DErr* errs, CrcTabs tabs) {
+  __shared__ uint32_t sT[1024];
+  load_slice_table(sT, tabs);
+  __syncthreads();
+  const uint32_t lane = lane_id();
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t g = gtid() / 32; g < n_blocks; g += warps) {
+    const BlockDesc b = blocks[g];
+    DErr* e = errs + b.job;
+    uint32_t cnt = 0;
+    uint64_t kb = 0;
+    if (b.ptr != nullptr && *(volatile int32_t*)&e->code == 0) {
+      const uint32_t got = warp_crc32c(b.ptr, b.size + 1, sT, tabs);
+      const uint32_t want = crc_unmask(ld_u32(b.ptr + b.size + 1));
+      const uint32_t local = in[b.input].local;
+      if (got != want) {
+        if (lane == 0) report(e, E_CORRUPT, local, b.off);
+      } else if (b.ptr[b.size] != 0) {
+        if (lane == 0) report(e, E_NOTSUP, local, b.off);
+      } else {
+        const uint64_t nr = b.size >= 4 ? ld_u32(b.ptr + b.size - 4) : 0;
+        bool bad = !(nr >= 1 && nr <= (b.size - 4) / 4);
+        if (!bad) {
+          const uint64_t rstart = b.size - 4 - 4 * nr;
+          const uint8_t* rs = b.ptr + rstart;
+          for (uint64_t k = lane; k < nr && !bad; k += 32) {
+            const uint64_t s = ld_u32(rs + 4 * k);
+            const uint64_t en = k + 1 < nr ? ld_u32(rs + 4 * (k + 1)) : rstart;
+            if ((k == 0 && s != 0) || s >= en || en > rstart) bad = true;
+            else if (!walk_segment(b.ptr, s, en, &cnt, &kb)) bad = true;
+          }
+        }
+        bad = __any_sync(0xFFFFFFFFu, bad);
+        if (bad) {
+          if (lane == 0) report(e, E_CORRUPT, local, b.off);
+          cnt = 0;
+          kb = 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+      cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, d);
+      kb += __shfl_xor_sync(0xFFFFFFFFu, kb, d);
+    }
+    if (lane == 0) {
+      nrec[g] = cnt;
+      kbytes[g] = kb;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_excl(T v, T* total) {
+  const uint32_t lane = lane_id();
+  T x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T o = __shfl_up_sync(0xFFFFFFFFu, x, d);
+    if (lane >= uint32_t(d)) x += o;
+  }
+  *total = __shfl_sync(0xFFFFFFFFu, x, 31);
+  return x - v;
+}
+
+// One warp per data block, one lane per restart segment: rebuild the keys and emit
+// records at the block's scanned offsets.
+__global__ void __launch_bounds__(256) k_decode(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
+                                                const DInput* __restrict__ in, const uint32_t* __restrict__ rec_first,
+                                                const uint64_t* __restrict__ key_first, Recs recs,
+                                                uint8_t* __restrict__ arena, DErr* errs) {
+  const uint32_t lane = lane_id();
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t g = gtid() / 32; g < n_blocks; g += warps) {
+    const BlockDesc b = blocks[g];
+    DErr* e = errs + b.job;
+    if (b.ptr == nullptr || *(volatile int32_t*)&e->code != 0) continue;
+    const uint64_t nr = ld_u32(b.ptr + b.size - 4);
+    const uint64_t rstart = b.size - 4 - 4 * nr;
+    const uint8_t* rs = b.ptr + rstart;
+    uint64_t rec_base = rec_first[g];
+    uint64_t key_base = key_first[g];
+    const uint32_t local = in[b.input].local;
+    for (uint64_t k0 = 0; k0 < nr; k0 += 32) {
+      const uint64_t k = k0 + lane;
+      uint64_t s = 0, en = 0;
+      uint32_t cnt = 0;
+      uint64_t kb = 0;
+      if (k < nr) {
+        s = ld_u32(rs + 4 * k);
+        en = k + 1 < nr ? ld_u32(rs + 4 * (k + 1)) : rstart;
+        walk_segment(b.ptr, s, en, &cnt, &kb);
+      }
+      uint32_t cnt_tot;
+      uint64_t kb_tot;
+      const uint32_t my_rec = warp_excl<uint32_t>(cnt, &cnt_tot);
+      const uint64_t my_key = warp_excl<uint64_t>(kb, &kb_tot);
+      if (k < nr) {
+        const uint8_t* p = b.ptr + s;
+        const uint8_t* end = b.ptr + en;
+        uint64_t rec = rec_base + my_rec;
+        uint64_t kpos = key_base + my_key;
+        uint64_t prev_kpos = 0;
+        bool bad = false;
+        while (p < end) {
+          uint64_t shared, nonshared, vlen;
+          p += get_varint<32>(p, end, &shared);
+          p += get_varint<32>(p, end, &nonshared);
+          p += get_varint<32>(p, end, &vlen);
+          uint8_t* kd = arena + kpos;
+          for (uint64_t t = 0; t < shared; ++t) kd[t] = arena[prev_kpos + t];
+          for (uint64_t t = 0; t < nonshared; ++t) kd[shared + t] = p[t];
+          p += nonshared;
+          const uint32_t klen = uint32_t(shared + nonshared);
+          const uint64_t tr = ld_u64(kd + klen - 8);
+          if ((tr & 0xFF) > 1) bad = true;
+          recs.pfx[rec] = key_prefix(kd, klen - 8);
+          recs.koff[rec] = kpos;
+          recs.klen[rec] = klen;
+          recs.tr[rec] = tr;
+          recs.vptr[rec] = reinterpret_cast<uint64_t>(p);
+          recs.vlen[rec] = uint32_t(vlen);
+          recs.src[rec] = b.input;
+          p += vlen;
+          prev_kpos = kpos;
+          kpos += klen;
+          ++rec;
+        }
+        if (bad) report(e, E_CORRUPT, local, b.off);
+      }
+      rec_base += cnt_tot;
+      key_base += kb_tot;
+    }
+  }
+}
+
+__global__ void k_zero_failed(const BlockDesc* __restrict__ blocks, uint32_t n_blocks, const DErr* __restrict__ errs,
+                              uint32_t* __restrict__ nrec, uint64_t* __restrict__ kbytes) {
+  for (uint64_t g = gtid(); g < n_blocks; g += gstride())
+    if (errs[blocks[g].job].code != 0) {
+      nrec[g] = 0;
+      kbytes[g] = 0;
+    }
+}
+
+__global__ void k_input_ranges(const DInput* __restrict__ in, uint32_t n_inputs, const uint32_t* __restrict__ rec_first,
+                               const uint64_t* __restrict__ key_first, uint32_t* __restrict__ in_rec,
+                               uint64_t* __restrict__ in_key) {
+  for (uint64_t i = gtid(); i <= n_inputs; i += gstride()) {
+    const uint32_t blk =
+        i < n_inputs ? in[i].blk_first : (n_inputs ? in[n_inputs - 1].blk_first + in[n_inputs - 1].nblk : 0);
+    in_rec[i] = rec_first[blk];
+    in_key[i] = key_first[blk];
+  }
+}
+
+}  // namespace
+
+void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cudaStream_t st) {
+  if (!n_inputs) return;
+  k_footers<<<grid_for(n_inputs, 1, 4096), 32, 0, st>>>(in, n_inputs, errs, tabs);
+}
+
+void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
+                          BlockDesc* blocks, DErr* errs, cudaStream_t st) {
+  if (!n_blocks) return;
+  k_index_entries<<<grid_for(n_blocks, 256), 256, 0, st>>>(in, n_inputs, in_blk_first, n_blocks, blocks, errs);
+}
+
+void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
+                       uint64_t* kbytes, DErr* errs, CrcTabs tabs, cudaStream_t st) {
+  if (!n_blocks) return;
+  k_block_scan<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, tabs);
+}
+
+void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* rec_first,
+                   const uint64_t* key_first, Recs recs, uint8_t* arena, DErr* errs, cudaStream_t st) {
+  if (!n_blocks) return;
+  k_decode<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, rec_first, key_first, recs, arena, errs);
+}
+
+void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,
+                        uint64_t* kbytes, cudaStream_t st) {
+  if (!n_blocks) return;
+  k_zero_failed<<<grid_for(n_blocks, 256), 256, 0, st>>>(blocks, n_blocks, errs, nrec, kbytes);
+}
+
+void launch_input_ranges(const DInput* in, uint32_t n_inputs, const uint32_t* rec_first, const uint64_t* key_first,
+                         uint32_t* in_rec, uint64_t* in_key, cudaStream_t st) {
+  k_input_ranges<<<grid_for(n_inputs + 1, 256), 256, 0, st>>>(in, n_inputs, rec_first, key_first, in_rec, in_key);
+}
+
+}  // namespace luda

@@ -1,0 +1,189 @@
+// internal.cuh -- data structures and kernel launchers shared by the pipeline stages.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "crc.cuh"
+
+namespace luda {
+
+// ---- batch description ----------------------------------------------------------------
+struct DInput {
+  const uint8_t* data;  // device address of the table image
+  uint64_t size;
+  uint32_t job;         // owning job
+  uint32_t local;       // index of the input within its job (error reports)
+  uint64_t idx_off;     // index block handle, set by the footer kernel
+  uint64_t idx_size;
+  uint32_t nblk;        // data blocks listed in the index, set by the footer kernel
+  uint32_t blk_first;   // first global data-block id, set by the host
+};
+
+struct BlockDesc {
+  const uint8_t* ptr;   // block contents
+  uint64_t size;        // contents size (trailer excluded)
+  uint64_t off;         // offset within its input (error reports)
+  uint32_t input;       // global input index
+  uint32_t job;
+};
+
+struct JobDev {
+  uint64_t snapshot;
+  uint32_t bottommost;
+  uint32_t flags;
+  uint32_t rec_begin, rec_end;    // decoded records (set by the host after sizing)
+  uint32_t surv_begin, surv_end;  // survivors (device)
+  uint32_t blk_begin, blk_end;    // output data blocks (device)
+  uint32_t file_begin, file_end;  // output tables (device)
+  uint64_t n_in;                  // entries decoded
+  uint64_t out_bytes;             // bytes of this job's tables (device)
+};
+
+struct FileDesc {
+  uint64_t off;          // offset of the table image in the output arena
+  uint64_t size;         // image size
+  uint64_t data_size;    // data blocks with trailers
+  uint64_t filter_size;  // filter contents (bitmap + k)
+  uint64_t meta_off, meta_size;
+  uint64_t index_off, index_size;
+  uint64_t bm_word;      // first 32-bit word of this table's bitmap in the scratch
+  uint32_t blk_begin, blk_end;  // output data blocks
+  uint32_t ent_begin, ent_end;  // survivor positions
+  uint32_t job;
+  uint32_t pad;
+  uint64_t bm_bits;      // filter bits
+};
+
+struct Fmt {
+  uint32_t T;       // block size threshold
+  uint32_t R;       // restart interval
+  uint32_t bpk;     // bloom bits per key
+  uint32_t k;       // bloom probes
+  uint64_t target;  // target file size
+};
+
+// Device-side counts of the stages whose sizes only the device knows.
+struct Counts {
+  uint32_t n_rec;     // decoded records (host-set)
+  uint32_t n_surv;    // survivors of the drop rule
+  uint32_t nb;        // output data blocks
+  uint32_t nf;        // output tables
+  uint64_t out_bytes; // bytes of all table images
+  uint64_t bm_words;  // bloom bitmap words
+  uint64_t key_bytes; // gathered smallest/largest key bytes
+};
+
+// Per-output-table summary copied to the host at the end.
+struct FileMeta {
+  uint64_t off, size, n_entries;
+  uint64_t small_koff, large_koff;  // in the key gather buffer
+  uint32_t small_len, large_len;
+  uint32_t job, pad;
+};
+
+// ---- launch geometry --------------------------------------------------------------------
+inline unsigned grid_for(uint64_t work, unsigned per_cta, unsigned max_ctas = kSms * 16) {
+  uint64_t g = (work + per_cta - 1) / per_cta;
+  if (g < 1) g = 1;
+  if (g > max_ctas) g = max_ctas;
+  return unsigned(g);
+}
+
+// ---- scan.cu ----------------------------------------------------------------------------
+uint64_t scan_temp_bytes(uint64_t n);
+template <typename In, typename Out>
+cudaError_t exclusive_scan(const In* in, Out* out, uint64_t cap, const uint32_t* count, void* temp,
+                           cudaStream_t st);
+
+// ---- crc_tables.cu ------------------------------------------------------------------------
+bool make_crc_tables(uint32_t* slice, uint32_t* shift);
+
+// ---- decode.cu ---------------------------------------------------------------------------
+void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cudaStream_t st);
+void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
+                          BlockDesc* blocks, DErr* errs, cudaStream_t st);
+void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
+                       uint64_t* kbytes, DErr* errs, CrcTabs tabs, cudaStream_t st);
+void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,
+                        uint64_t* kbytes, cudaStream_t st);
+void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* rec_first,
+                   const uint64_t* key_first, Recs recs, uint8_t* arena, DErr* errs, cudaStream_t st);
+void launch_input_ranges(const DInput* in, uint32_t n_inputs, const uint32_t* rec_first,
+                         const uint64_t* key_first, uint32_t* in_rec, uint64_t* in_key, cudaStream_t st);
+
+// ---- sort.cu -----------------------------------------------------------------------------
+struct MergeSpan {
+  uint32_t a_begin;  // first position of run A (run B follows it)
+  uint32_t a_len;
+  uint32_t b_len;
+  uint32_t tile_first;  // first tile id of this merge
+};
+constexpr uint32_t kMergeTile = 1024;
+
+void launch_check_order(Recs recs, const uint8_t* arena, uint32_t n_rec, const DInput* in, DErr* errs,
+                        cudaStream_t st);
+void launch_sort_init(uint32_t* ord, uint64_t* opfx, const uint64_t* pfx, uint32_t n, cudaStream_t st);
+void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* corank,
+                       const uint32_t* src_ord, const uint64_t* src_pfx, uint32_t* dst_ord, uint64_t* dst_pfx,
+                       Recs recs, const uint8_t* arena, cudaStream_t st);
+void launch_gc_flags(const uint32_t* ord, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, Recs recs,
+                     const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st);
+void launch_gc_compact(const uint32_t* ord, const uint32_t* keep, const uint32_t* pos, uint32_t n_rec,
+                       uint32_t* surv, cudaStream_t st);
+void launch_job_surv(JobDev* jobs, uint32_t n_jobs, const uint32_t* pos, uint32_t n_rec, Counts* cnt,
+                     cudaStream_t st);
+
+// ---- pack.cu -----------------------------------------------------------------------------
+void launch_sizes(const uint32_t* surv, const Counts* cnt, uint32_t cap, const JobDev* jobs, uint32_t n_jobs,
+                  Recs recs, const uint8_t* arena, uint32_t* lcp, uint32_t* sd, uint32_t* dr, cudaStream_t st);
+void launch_block_next(const uint64_t* P, const uint32_t* dr, const Counts* cnt, uint32_t cap, const JobDev* jobs,
+                       uint32_t n_jobs, Fmt fmt, uint32_t* next, cudaStream_t st);
+uint64_t stitch_temp_bytes(uint32_t cap);
+void launch_stitch(const uint32_t* next, const uint32_t* n_dev, uint32_t cap, uint8_t* flags, void* temp,
+                   cudaStream_t st);
+void launch_compact_flags(const uint8_t* flags, const uint32_t* pos, const uint32_t* n_dev, uint32_t cap,
+                          uint32_t* starts, uint32_t* total_out, cudaStream_t st);
+void launch_job_blocks(JobDev* jobs, uint32_t n_jobs, const uint32_t* bpos, cudaStream_t st);
+void launch_block_sizes(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* P,
+                        const uint32_t* dr, Fmt fmt, uint64_t* bsz, uint64_t* disk, cudaStream_t st);
+void launch_file_next(const uint64_t* C, const Counts* cnt, uint32_t cap, const JobDev* jobs, uint32_t n_jobs,
+                      Fmt fmt, uint32_t* next, cudaStream_t st);
+void launch_job_files(JobDev* jobs, uint32_t n_jobs, const uint32_t* fpos, cudaStream_t st);
+void launch_block_file(const uint32_t* fpos, const Counts* cnt, uint32_t cap, uint32_t* blk_file, cudaStream_t st);
+void launch_index_sizes(const uint32_t* blk_start, const uint64_t* bsz, const uint64_t* C, const uint32_t* blk_file,
+                        const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* surv, Recs recs,
+                        uint32_t* ie, cudaStream_t st);
+void launch_file_layout(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_start,
+                        const uint64_t* C, const uint64_t* IX, Fmt fmt, const JobDev* jobs, uint32_t n_jobs,
+                        FileDesc* files, uint64_t* fsize, uint64_t* bmwords, cudaStream_t st);
+void launch_file_offsets(FileDesc* files, Counts* cnt, uint32_t cap, const uint64_t* foff, const uint64_t* bmoff,
+                         JobDev* jobs, uint32_t n_jobs, uint64_t out_cap, uint64_t bm_cap, DErr* errs,
+                         cudaStream_t st);
+void launch_zero_bitmap(uint32_t* bitmap, const Counts* cnt, uint64_t cap_words, cudaStream_t st);
+void launch_encode(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
+                   const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
+                   const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
+                   Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs, cudaStream_t st);
+void launch_bloom(const uint32_t* surv, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
+                  const uint32_t* blk_start, const FileDesc* files, Recs recs, const uint8_t* arena, Fmt fmt,
+                  uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st);
+void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* bsz,
+                        const uint64_t* C, const uint64_t* IX, const uint32_t* blk_file, const FileDesc* files,
+                        const uint32_t* surv, Recs recs, const uint8_t* arena, uint8_t* out, uint64_t out_cap,
+                        cudaStream_t st);
+void launch_file_finish(const FileDesc* files, const Counts* cnt, uint32_t cap, const uint32_t* bitmap,
+                        const uint32_t* surv, Recs recs, Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs,
+                        FileMeta* meta, cudaStream_t st);
+void launch_key_lens(const FileMeta* meta, const Counts* cnt, uint32_t cap, uint64_t* lens, cudaStream_t st);
+void launch_key_gather(FileMeta* meta, Counts* cnt, uint32_t cap, const uint64_t* koff, const FileDesc* files,
+                       const uint32_t* surv, Recs recs, const uint8_t* arena, uint8_t* keybuf, cudaStream_t st);
+
+// ---- build path (memtable flush) ----------------------------------------------------------
+void launch_build_records(const uint8_t* ukeys, const uint64_t* ukoff, const uint64_t* seqs, const uint8_t* types,
+                          const uint8_t* vals, const uint64_t* voff, uint32_t n, Recs recs, uint8_t* arena,
+                          uint32_t* surv, DErr* err, cudaStream_t st);
+void launch_build_check(Recs recs, const uint8_t* arena, uint32_t n, DErr* err, cudaStream_t st);
+
+}  // namespace luda

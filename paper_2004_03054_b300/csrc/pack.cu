@@ -1,0 +1,834 @@
+// pack.cu -- Phase 3 "Pack" (LUDA §II-A; §III-C "shared_key", "encode" and "filter"
+// kernels, Fig. 4b).
+//
+//   sizes      per survivor: shared prefix with its predecessor (the "shared keys part")
+//              and its encoded size in delta form and in restart form
+//   block cut  the greedy builder rule "close the block once its size estimate reaches
+//              the block size" made parallel: next(i) (where a block starting at entry i
+//              ends) for every i from prefix sums, then the chain 0, next(0), ... is
+//              stitched tile by tile (speculate each tile's entry, fix mispredictions)
+//   file cut   the same over blocks with the target file size
+//   encode     one CTA per data block: headers, key deltas, values gathered straight from
+//              the input tables, restart array, CRC trailer; no data exchange between
+//              blocks (§III-C)
+//   filter     per-table bloom bitmap built with atomics, then written with its trailer
+//   index, metaindex, footer per table.
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace luda {
+
+namespace {
+
+__device__ __forceinline__ uint32_t find_last_le(const uint32_t* a, uint32_t n, uint32_t v) {
+  // largest i in [0, n) with a[i] <= v (a non-decreasing, a[0] <= v)
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t job_of_surv(const JobDev* jobs, uint32_t n_jobs, uint32_t s) {
+  uint32_t lo = 0, hi = n_jobs;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (jobs[mid].surv_begin <= s) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t job_of_block(const JobDev* jobs, uint32_t n_jobs, uint32_t b) {
+  uint32_t lo = 0, hi = n_jobs;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (jobs[mid].blk_begin <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_sizes(const uint32_t* __restrict__ surv, const Counts* __restrict__ cnt,
+                        const JobDev* __restrict__ jobs, uint32_t n_jobs, Recs recs, const uint8_t* __restrict__ arena,
+                        uint32_t* __restrict__ lcp, uint32_t* __restrict__ sd, uint32_t* __restrict__ dr) {
+  const uint32_t n = cnt->n_surv;
+  for (uint64_t s = gtid(); s < n; s += gstride()) {
+    const uint32_t j = job_of_surv(jobs, n_jobs, uint32_t(s));
+    const uint32_t x = surv[s];
+    const uint32_t klen = recs.klen[x], vlen = recs.vlen[x];
+    uint32_t l = 0;
+    if (s > jobs[j].surv_begin) {
+      const uint32_t y = surv[s - 1];
+      const uint32_t m = min(klen, recs.klen[y]);
+      const uint8_t* a = arena + recs.koff[x];
+      const uint8_t* b = arena + recs.koff[y];
+      while (l < m && a[l] == b[l]) ++l;
+    }
+    const uint32_t d = varint_size(l) + varint_size(klen - l) + varint_size(vlen) + (klen - l) + vlen;
+    const uint32_t r = 1 + varint_size(klen) + varint_size(vlen) + klen + vlen;
+    lcp[s] = l;
+    sd[s] = d;
+    dr[s] = r - d;
+  }
+}
+
+// next(i) = 1 + min{j >= i : E(i, j) >= T}, capped at the job's end, with
+// E(i, j) = P[j+1] - P[i] + sum of dr over the restarts i, i+R, ... <= j + 4*ceil((j-i+1)/R) + 4.
+__global__ void k_block_next(const uint64_t* __restrict__ P, const uint32_t* __restrict__ dr,
+                             const Counts* __restrict__ cnt, const JobDev* __restrict__ jobs, uint32_t n_jobs, Fmt fmt,
+                             uint32_t* __restrict__ next) {
+  const uint64_t T = fmt.T, R = fmt.R;
+  const uint32_t n = cnt->n_surv;
+  for (uint64_t i = gtid(); i < n; i += gstride()) {
+    const uint64_t e = jobs[job_of_surv(jobs, n_jobs, uint32_t(i))].surv_end;
+    const uint64_t base = P[i];
+    uint64_t rs = 0;
+    uint64_t res = e;
+    for (uint64_t g = 0;; ++g) {
+      const uint64_t gs = i + g * R;
+      rs += dr[gs];
+      const uint64_t ge = min(gs + R, e) - 1;
+      const uint64_t fixed = rs + 4 * (g + 1) + 4 - base;
+      if (P[ge + 1] + fixed >= T) {
+        uint64_t j = gs;
+        while (P[j + 1] + fixed < T) ++j;
+        res = j + 1;
+        break;
+      }
+      if (ge + 1 >= e) break;
+    }
+    next[i] = uint32_t(res);
+  }
+}
+
+// ---- chain stitching --------------------------------------------------------------------
+constexpr uint32_t kStitchTile = 2048;
+constexpr uint32_t kStitchChunk = 2048;
+
+__global__ void __launch_bounds__(128) k_stitch_tiles(const uint32_t* __restrict__ next,
+                                                      const uint32_t* __restrict__ n_dev,
+                                                      uint8_t* __restrict__ flags, uint32_t* __restrict__ entry,
+                                                      uint32_t* __restrict__ exitp) {
+  __shared__ uint32_t s_prev[kStitchTile], s_cur[kStitchTile];
+  __shared__ uint8_t gm[kStitchTile], tm[kStitchTile];
+  __shared__ uint32_t s_conv;
+  const uint32_t n = *n_dev;
+  const uint32_t n_tiles = (n + kStitchTile - 1) / kStitchTile;
+  for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const uint32_t L = t * kStitchTile;
+    const uint32_t U = min(n, L + kStitchTile);
+    const uint32_t PL = t ? L - kStitchTile : 0;
+    for (uint32_t i = threadIdx.x; i < kStitchTile; i += blockDim.x) {
+      s_cur[i] = L + i < U ? next[L + i] : n;
+      s_prev[i] = t ? next[PL + i] : n;
+      gm[i] = 0;
+      tm[i] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t a = 0;
+      if (t) {
+        uint32_t h = PL;
+        while (h < L) h = s_prev[h - PL];
+        a = h;
+      }
+      uint32_t g = L;
+      while (g < U) {
+        gm[g - L] = 1;
+        g = s_cur[g - L];
+      }
+      uint32_t conv, ex;
+      if (a >= U) {
+        conv = U;
+        ex = a;
+      } else {
+        uint32_t x = a;
+        while (x < U && !gm[x - L]) {
+          tm[x - L] = 1;
+          x = s_cur[x - L];
+        }
+        if (x < U) {
+          conv = x;
+          ex = g;
+        } else {
+          conv = U;
+          ex = x;
+        }
+      }
+      entry[t] = a;
+      exitp[t] = ex;
+      s_conv = conv;
+    }
+    __syncthreads();
+    const uint32_t conv = s_conv;
+    for (uint32_t i = L + threadIdx.x; i < U; i += blockDim.x)
+      flags[i] = uint8_t(tm[i - L] | (gm[i - L] && i >= conv));
+    __syncthreads();
+  }
+}
+
+// Single CTA: walk the tiles in order; where a tile was computed from a wrong entry,
+// redo it from the true one (until the true chain meets the tile's flagged chain).
+__global__ void __launch_bounds__(256) k_stitch_fix(const uint32_t* __restrict__ next,
+                                                    const uint32_t* __restrict__ n_dev, uint8_t* __restrict__ flags,
+                                                    const uint32_t* __restrict__ entry,
+                                                    const uint32_t* __restrict__ exitp) {
+  const uint32_t n = *n_dev;
+  const uint32_t n_tiles = (n + kStitchTile - 1) / kStitchTile;
+  __shared__ uint32_t s_entry[kStitchChunk], s_exit[kStitchChunk];
+  __shared__ uint32_t s_list[kStitchTile];
+  __shared__ uint32_t s_cur, s_t, s_nl, s_clear_end;
+  if (threadIdx.x == 0) s_cur = 0;
+  for (uint32_t t0 = 0; t0 < n_tiles; t0 += kStitchChunk) {
+    const uint32_t tend = min(n_tiles, t0 + kStitchChunk);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < tend - t0; i += blockDim.x) {
+      s_entry[i] = entry[t0 + i];
+      s_exit[i] = exitp[t0 + i];
+    }
+    __syncthreads();
+    uint32_t t = t0;
+    while (true) {
+      if (threadIdx.x == 0) {
+        uint32_t c = s_cur, tt = t;
+        while (tt < tend && c == s_entry[tt - t0]) c = s_exit[(tt++) - t0];
+        s_cur = c;
+        s_t = tt;
+        if (tt < tend) {
+          const uint32_t L = tt * kStitchTile, U = min(n, L + kStitchTile);
+          uint32_t x = c, nl = 0;
+          while (x < U && !flags[x]) {
+            s_list[nl++] = x;
+            x = next[x];
+          }
+          if (x < U) {  // met the tile's chain: everything from x on is right
+            s_clear_end = x;
+            s_cur = s_exit[tt - t0];
+          } else {
+            s_clear_end = U;
+            s_cur = x;
+          }
+          s_nl = nl;
+        }
+      }
+      __syncthreads();
+      t = s_t;
+      if (t >= tend) break;
+      const uint32_t L = t * kStitchTile;
+      for (uint32_t i = L + threadIdx.x; i < s_clear_end; i += blockDim.x) flags[i] = 0;
+      __syncthreads();
+      for (uint32_t k = threadIdx.x; k < s_nl; k += blockDim.x) flags[s_list[k]] = 1;
+      ++t;
+      __syncthreads();
+    }
+  }
+}
+
+// starts[pos[i]] = i for flagged i, starts[total] = n; *total_out = total.
+__global__ void k_compact_flags(const uint8_t* __restrict__ flags, const uint32_t* __restrict__ pos,
+                                const uint32_t* __restrict__ n_dev, uint32_t* __restrict__ starts,
+                                uint32_t* __restrict__ total_out) {
+  const uint32_t n = *n_dev;
+  for (uint64_t i = gtid(); i < n; i += gstride())
+    if (flags[i]) starts[pos[i]] = uint32_t(i);
+  if (gtid() == 0) {
+    starts[pos[n]] = n;
+    *total_out = pos[n];
+  }
+}
+
+__global__ void k_job_blocks(JobDev* jobs, uint32_t n_jobs, const uint32_t* __restrict__ bpos) {
+  for (uint64_t j = gtid(); j < n_jobs; j += gstride()) {
+    jobs[j].blk_begin = bpos[jobs[j].surv_begin];
+    jobs[j].blk_end = bpos[jobs[j].surv_end];
+  }
+}
+
+__global__ void k_job_files(JobDev* jobs, uint32_t n_jobs, const uint32_t* __restrict__ fpos) {
+  for (uint64_t j = gtid(); j < n_jobs; j += gstride()) {
+    jobs[j].file_begin = fpos[jobs[j].blk_begin];
+    jobs[j].file_end = fpos[jobs[j].blk_end];
+  }
+}
+
+// Contents size of block [s, e): exact, equal to the builder's estimate at its close.
+__global__ void k_block_sizes(const uint32_t* __restrict__ start, const Counts* __restrict__ cnt,
+                              const uint64_t* __restrict__ P, const uint32_t* __restrict__ dr, Fmt fmt,
+                              uint64_t* __restrict__ bsz, uint64_t* __restrict__ disk) {
+  const uint32_t nb = cnt->nb;
+  for (uint64_t b = gtid(); b < nb; b += gstride()) {
+    const uint32_t s = start[b], e = start[b + 1];
+    uint64_t sz = P[e] - P[s];
+    uint64_t nr = 0;
+    for (uint64_t k = s; k < e; k += fmt.R, ++nr) sz += dr[k];
+    sz += 4 * nr + 4;
+    bsz[b] = sz;
+    disk[b] = sz + kTrailer;
+  }
+}
+
+// File cut: a table ends after the block that brings its data bytes to >= target.
+__global__ void k_file_next(const uint64_t* __restrict__ C, const Counts* __restrict__ cnt,
+                            const JobDev* __restrict__ jobs, uint32_t n_jobs, Fmt fmt, uint32_t* __restrict__ next) {
+  const uint32_t nb = cnt->nb;
+  for (uint64_t b = gtid(); b < nb; b += gstride()) {
+    const uint32_t be = jobs[job_of_block(jobs, n_jobs, uint32_t(b))].blk_end;
+    const uint64_t base = C[b];
+    uint32_t lo = uint32_t(b), hi = be;  // first b' in [b, be) with C[b'+1] - base >= target
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (C[mid + 1] - base >= fmt.target) hi = mid;
+      else lo = mid + 1;
+    }
+    next[b] = lo < be ? lo + 1 : be;
+  }
+}
+
+__global__ void k_block_file(const uint32_t* __restrict__ fpos, const Counts* __restrict__ cnt,
+                             uint32_t* __restrict__ blk_file) {
+  const uint32_t nb = cnt->nb;
+  for (uint64_t b = gtid(); b < nb; b += gstride()) blk_file[b] = fpos[b + 1] - 1;
+}
+
+__global__ void k_index_sizes(const uint32_t* __restrict__ start, const uint64_t* __restrict__ bsz,
+                              const uint64_t* __restrict__ C, const uint32_t* __restrict__ blk_file,
+                              const uint32_t* __restrict__ file_start, const Counts* __restrict__ cnt,
+                              const uint32_t* __restrict__ surv, Recs recs, uint32_t* __restrict__ ie) {
+  const uint32_t nb = cnt->nb;
+  for (uint64_t b = gtid(); b < nb; b += gstride()) {
+    const uint32_t fb0 = file_start[blk_file[b]];
+    const uint64_t off = C[b] - C[fb0];
+    const uint32_t klen = recs.klen[surv[start[b + 1] - 1]];
+    const uint32_t hlen = varint_size(off) + varint_size(bsz[b]);
+    ie[b] = 1 + varint_size(klen) + varint_size(hlen) + klen + hlen;
+  }
+}
+
+__global__ void k_file_layout(const uint32_t* __restrict__ file_start, const Counts* __restrict__ cnt,
+                              const uint32_t* __restrict__ start,
+                              const uint64_t* __restrict__ C, const uint64_t* __restrict__ IX, Fmt fmt,
+                              const JobDev* __restrict__ jobs, uint32_t n_jobs, FileDesc* __restrict__ files,
+                              uint64_t* __restrict__ fsize, uint64_t* __restrict__ bmwords) {
+  const uint32_t nf = cnt->nf;
+  for (uint64_t f = gtid(); f < nf; f += gstride()) {
+    const uint32_t fb0 = file_start[f], fb1 = file_start[f + 1];
+    const uint32_t e0 = start[fb0], e1 = start[fb1];
+    FileDesc d{};
+    d.blk_begin = fb0;
+    d.blk_end = fb1;
+    d.ent_begin = e0;
+    d.ent_end = e1;
+    d.job = job_of_block(jobs, n_jobs, fb0);
+    d.data_size = C[fb1] - C[fb0];
+    uint64_t bits = uint64_t(e1 - e0) * fmt.bpk;
+    if (bits < 64) bits = 64;
+    const uint64_t bytes = (bits + 7) / 8;
+    d.bm_bits = bytes * 8;
+    d.filter_size = bytes + 1;
+    const uint32_t hf = varint_size(d.data_size) + varint_size(d.filter_size);
+    d.meta_size = 3 + 17 + hf + 8;
+    d.meta_off = d.data_size + d.filter_size + kTrailer;
+    d.index_size = (IX[fb1] - IX[fb0]) + 4ull * (fb1 - fb0) + 4;
+    d.index_off = d.meta_off + d.meta_size + kTrailer;
+    d.size = d.index_off + d.index_size + kTrailer + kFooter;
+    files[f] = d;
+    fsize[f] = d.size;
+    bmwords[f] = (bytes + 3) / 4;
+  }
+}
+
+__global__ void k_file_offsets(FileDesc* files, Counts* cnt, const uint64_t* __restrict__ foff,
+                               const uint64_t* __restrict__ bmoff, JobDev* jobs, uint32_t n_jobs, uint64_t out_cap,
+                               uint64_t bm_cap, DErr* errs) {
+  const uint32_t nf = cnt->nf;
+  for (uint64_t f = gtid(); f < nf; f += gstride()) {
+    files[f].off = foff[f];
+    files[f].bm_word = bmoff[f];
+  }
+  for (uint64_t j = gtid(); j < n_jobs; j += gstride()) {
+    jobs[j].out_bytes = foff[jobs[j].file_end] - foff[jobs[j].file_begin];
+    if (foff[nf] > out_cap || bmoff[nf] > bm_cap) report(errs + j, E_OOM, ~0u, foff[nf]);
+  }
+  if (gtid() == 0) {
+    cnt->out_bytes = foff[nf];
+    cnt->bm_words = bmoff[nf];
+  }
+}
+
+__global__ void k_zero_words(uint32_t* __restrict__ w, const Counts* __restrict__ cnt, uint64_t cap) {
+  const uint64_t n = cnt->bm_words < cap ? cnt->bm_words : cap;
+  for (uint64_t i = gtid(); i < n; i += gstride()) w[i] = 0;
+}
+
+// ---- encode -------------------------------------------------------------------------------
+constexpr int kEncThreads = 128;
+
+__global__ void __launch_bounds__(kEncThreads) k_encode(const uint32_t* __restrict__ start,
+                                                        const Counts* __restrict__ cnt,
+                                                        const uint32_t* __restrict__ blk_file,
+                                                        const FileDesc* __restrict__ files,
+                                                        const uint64_t* __restrict__ C, const uint64_t* __restrict__ bsz,
+                                                        const uint32_t* __restrict__ surv,
+                                                        const uint32_t* __restrict__ lcp,
+                                                        const uint32_t* __restrict__ sd,
+                                                        const uint32_t* __restrict__ dr, Recs recs,
+                                                        const uint8_t* __restrict__ arena, Fmt fmt,
+                                                        uint8_t* __restrict__ out, uint64_t out_cap, CrcTabs tabs) {
+  __shared__ uint32_t sT[1024];
+  __shared__ uint64_t s_off[kEncThreads];
+  __shared__ uint64_t s_wsum[kEncThreads / 32];
+  load_slice_table(sT, tabs);
+  __syncthreads();
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t R = fmt.R;
+  const uint32_t nb = cnt->nb;
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const uint32_t s = start[b], e = start[b + 1], m = e - s;
+    const FileDesc F = files[blk_file[b]];
+    if (F.off + F.size > out_cap) continue;
+    uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
+    const uint64_t contents = bsz[b];
+    const uint64_t nr = (m + R - 1) / R;
+    const uint64_t rbase = contents - 4 * nr - 4;
+    uint64_t base = 0;
+    for (uint32_t r0 = 0; r0 < m; r0 += kEncThreads) {
+      const uint32_t k = r0 + tid;
+      uint64_t sz = 0;
+      if (k < m) sz = sd[s + k] + ((k % R) == 0 ? dr[s + k] : 0u);
+      // CTA exclusive scan of sz
+      uint64_t x = sz;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t o = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= uint32_t(d)) x += o;
+      }
+      if (lane == 31) s_wsum[warp] = x;
+      __syncthreads();
+      uint64_t before = 0, total = 0;
+      for (uint32_t w = 0; w < kEncThreads / 32; ++w) {
+        if (w < warp) before += s_wsum[w];
+        total += s_wsum[w];
+      }
+      s_off[tid] = base + before + x - sz;
+      __syncthreads();
+      const uint32_t cnt = min(uint32_t(kEncThreads), m - r0);
+      for (uint32_t kk = warp; kk < cnt; kk += kEncThreads / 32) {
+        const uint32_t kb = r0 + kk;
+        const uint32_t xi = surv[s + kb];
+        const uint32_t klen = recs.klen[xi], vlen = recs.vlen[xi];
+        const bool restart = (kb % R) == 0;
+        const uint32_t shared = restart ? 0u : lcp[s + kb];
+        const uint32_t nonshared = klen - shared;
+        const uint64_t eoff = s_off[kk];
+        uint8_t* ep = dst + eoff;
+        uint32_t h = 0;
+        if (lane == 0) {
+          h = put_varint(ep, shared);
+          h += put_varint(ep + h, nonshared);
+          h += put_varint(ep + h, vlen);
+          if (restart) st_u32(dst + rbase + 4ull * (kb / R), uint32_t(eoff));
+        }
+        h = __shfl_sync(0xFFFFFFFFu, h, 0);
+        const uint8_t* ks = arena + recs.koff[xi] + shared;
+        for (uint32_t t = lane; t < nonshared; t += 32) ep[h + t] = ks[t];
+        const uint8_t* vs = reinterpret_cast<const uint8_t*>(recs.vptr[xi]);
+        uint8_t* vd = ep + h + nonshared;
+        for (uint32_t t = lane; t < vlen; t += 32) vd[t] = vs[t];
+      }
+      base += total;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      st_u32(dst + contents - 4, uint32_t(nr));
+      dst[contents] = 0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t crc = warp_crc32c(dst, contents + 1, sT, tabs);
+      if (lane == 0) st_u32(dst + contents + 1, crc_mask(crc));
+    }
+    __syncthreads();
+  }
+}
+
+// MurmurHash3 x86_32 (Appleby, public domain), from its published description.
+__device__ __forceinline__ uint32_t rotl(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }
+
+__device__ uint32_t murmur3_32(const uint8_t* p, uint32_t n, uint32_t seed) {
+  const uint32_t c1 = 0xcc9e2d51u, c2 = 0x1b873593u;
+  uint32_t h = seed;
+  const uint32_t nb = n >> 2;
+  for (uint32_t i = 0; i < nb; ++i) {
+    uint32_t k = ld_u32(p + 4 * i);
+    k *= c1;
+    k = rotl(k, 15);
+    k *= c2;
+    h ^= k;
+    h = rotl(h, 13);
+    h = h * 5u + 0xe6546b64u;
+  }
+  const uint8_t* t = p + 4 * nb;
+  uint32_t k = 0;
+  switch (n & 3) {
+    case 3: k ^= uint32_t(t[2]) << 16; [[fallthrough]];
+    case 2: k ^= uint32_t(t[1]) << 8; [[fallthrough]];
+    case 1:
+      k ^= t[0];
+      k *= c1;
+      k = rotl(k, 15);
+      k *= c2;
+      h ^= k;
+  }
+  h ^= n;
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__global__ void k_bloom(const uint32_t* __restrict__ surv, const Counts* __restrict__ cnt,
+                        const uint32_t* __restrict__ blk_file, const uint32_t* __restrict__ start,
+                        const FileDesc* __restrict__ files, Recs recs, const uint8_t* __restrict__ arena, Fmt fmt,
+                        uint32_t* __restrict__ bitmap, uint64_t out_cap, uint64_t bm_cap) {
+  const uint32_t n = cnt->n_surv, nb = cnt->nb;
+  if (cnt->out_bytes > out_cap || cnt->bm_words > bm_cap) return;
+  for (uint64_t s = gtid(); s < n; s += gstride()) {
+    const uint32_t b = find_last_le(start, nb, uint32_t(s));
+    const FileDesc F = files[blk_file[b]];
+    const uint32_t x = surv[s];
+    uint32_t h = murmur3_32(arena + recs.koff[x], recs.klen[x] - 8, 0);
+    const uint32_t d = (h >> 17) | (h << 15);
+    uint32_t* bm = bitmap + F.bm_word;
+    for (uint32_t j = 0; j < fmt.k; ++j) {
+      const uint64_t bit = h % F.bm_bits;
+      atomicOr(bm + (bit >> 5), 1u << (bit & 31));
+      h += d;
+    }
+  }
+}
+
+__global__ void k_index_write(const uint32_t* __restrict__ start, const Counts* __restrict__ cnt,
+                              const uint64_t* __restrict__ bsz,
+                              const uint64_t* __restrict__ C, const uint64_t* __restrict__ IX,
+                              const uint32_t* __restrict__ blk_file, const FileDesc* __restrict__ files,
+                              const uint32_t* __restrict__ surv, Recs recs, const uint8_t* __restrict__ arena,
+                              uint8_t* __restrict__ out, uint64_t out_cap) {
+  const uint32_t nb = cnt->nb;
+  for (uint64_t b = gtid(); b < nb; b += gstride()) {
+    const FileDesc F = files[blk_file[b]];
+    if (F.off + F.size > out_cap) continue;
+    uint8_t* ib = out + F.off + F.index_off;
+    const uint32_t fb0 = F.blk_begin, fb1 = F.blk_end;
+    const uint64_t eoff = IX[b] - IX[fb0];
+    const uint32_t x = surv[start[b + 1] - 1];
+    const uint32_t klen = recs.klen[x];
+    const uint64_t off = C[b] - C[fb0], size = bsz[b];
+    const uint32_t hlen = varint_size(off) + varint_size(size);
+    uint8_t* p = ib + eoff;
+    *p++ = 0;
+    p += put_varint(p, klen);
+    p += put_varint(p, hlen);
+    const uint8_t* k = arena + recs.koff[x];
+    for (uint32_t t = 0; t < klen; ++t) p[t] = k[t];
+    p += klen;
+    p += put_varint(p, off);
+    put_varint(p, size);
+    st_u32(ib + (IX[fb1] - IX[fb0]) + 4ull * (b - fb0), uint32_t(eoff));
+  }
+}
+
+// One warp per table: filter block, metaindex block, index block trailer, footer.
+__global__ void __launch_bounds__(32) k_file_finish(const FileDesc* __restrict__ files,
+                                                    const Counts* __restrict__ cnt,
+                                                    const uint32_t* __restrict__ bitmap,
+                                                    const uint32_t* __restrict__ surv, Recs recs, Fmt fmt,
+                                                    uint8_t* __restrict__ out, uint64_t out_cap, CrcTabs tabs,
+                                                    FileMeta* __restrict__ meta) {
+  __shared__ uint32_t sT[1024];
+  load_slice_table(sT, tabs);
+  __syncthreads();
+  const uint32_t lane = lane_id();
+  const uint32_t nf = cnt->nf;
+  for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
+    const FileDesc F = files[f];
+    if (F.off + F.size > out_cap) continue;
+    uint8_t* base = out + F.off;
+    // filter: bitmap bytes, k, type
+    uint8_t* fp = base + F.data_size;
+    const uint64_t bytes = F.filter_size - 1;
+    const uint32_t* bm = bitmap + F.bm_word;
+    for (uint64_t i = lane; i < bytes; i += 32) fp[i] = uint8_t(bm[i >> 2] >> (8 * (i & 3)));
+    if (lane == 0) {
+      fp[bytes] = uint8_t(fmt.k);
+      fp[bytes + 1] = 0;
+      // metaindex: one entry "filter.luda.bloom" -> filter handle, restart interval 1
+      uint8_t* mp = base + F.meta_off;
+      uint8_t hbuf[20];
+      uint32_t hl = put_varint(hbuf, F.data_size);
+      hl += put_varint(hbuf + hl, F.filter_size);
+      uint32_t q = 0;
+      mp[q++] = 0;
+      mp[q++] = 17;
+      mp[q++] = uint8_t(hl);
+      const char name[] = "filter.luda.bloom";
+      for (int i = 0; i < 17; ++i) mp[q++] = uint8_t(name[i]);
+      for (uint32_t i = 0; i < hl; ++i) mp[q++] = hbuf[i];
+      st_u32(mp + q, 0);
+      st_u32(mp + q + 4, 1);
+      mp[F.meta_size] = 0;
+      // index block: restart count and type
+      uint8_t* ip = base + F.index_off;
+      st_u32(ip + F.index_size - 4, F.blk_end - F.blk_begin);
+      ip[F.index_size] = 0;
+    }
+    __syncwarp();
+    const uint32_t cf = warp_crc32c(fp, F.filter_size + 1, sT, tabs);
+    const uint32_t cm = warp_crc32c(base + F.meta_off, F.meta_size + 1, sT, tabs);
+    const uint32_t ci = warp_crc32c(base + F.index_off, F.index_size + 1, sT, tabs);
+    if (lane == 0) {
+      st_u32(fp + F.filter_size + 1, crc_mask(cf));
+      st_u32(base + F.meta_off + F.meta_size + 1, crc_mask(cm));
+      st_u32(base + F.index_off + F.index_size + 1, crc_mask(ci));
+      uint8_t* ft = base + F.size - kFooter;
+      uint32_t q = put_varint(ft, F.meta_off);
+      q += put_varint(ft + q, F.meta_size);
+      q += put_varint(ft + q, F.index_off);
+      q += put_varint(ft + q, F.index_size);
+      while (q < 40) ft[q++] = 0;
+      for (int i = 0; i < 8; ++i) ft[40 + i] = uint8_t(kMagic >> (8 * i));
+      FileMeta mt{};
+      mt.off = F.off;
+      mt.size = F.size;
+      mt.n_entries = F.ent_end - F.ent_begin;
+      mt.small_len = recs.klen[surv[F.ent_begin]];
+      mt.large_len = recs.klen[surv[F.ent_end - 1]];
+      mt.job = F.job;
+      meta[f] = mt;
+    }
+  }
+}
+
+__global__ void k_key_lens(const FileMeta* __restrict__ meta, const Counts* __restrict__ cnt,
+                           uint64_t* __restrict__ lens) {
+  const uint32_t nf = cnt->nf;
+  for (uint64_t f = gtid(); f < nf; f += gstride()) lens[f] = uint64_t(meta[f].small_len) + meta[f].large_len;
+}
+
+__global__ void k_key_gather(FileMeta* meta, Counts* cnt, const uint64_t* __restrict__ koff,
+                             const FileDesc* __restrict__ files, const uint32_t* __restrict__ surv, Recs recs,
+                             const uint8_t* __restrict__ arena, uint8_t* __restrict__ keybuf) {
+  const uint32_t nf = cnt->nf;
+  if (gtid() == 0) cnt->key_bytes = koff[nf];
+  for (uint64_t f = gtid(); f < nf; f += gstride()) {
+    const FileDesc F = files[f];
+    const uint32_t a = surv[F.ent_begin], z = surv[F.ent_end - 1];
+    const uint64_t o = koff[f];
+    const uint32_t la = recs.klen[a], lz = recs.klen[z];
+    for (uint32_t i = 0; i < la; ++i) keybuf[o + i] = arena[recs.koff[a] + i];
+    for (uint32_t i = 0; i < lz; ++i) keybuf[o + la + i] = arena[recs.koff[z] + i];
+    meta[f].small_koff = o;
+    meta[f].large_koff = o + la;
+  }
+}
+
+// ---- build path ------------------------------------------------------------------------
+__global__ void k_build_records(const uint8_t* __restrict__ ukeys, const uint64_t* __restrict__ ukoff,
+                                const uint64_t* __restrict__ seqs, const uint8_t* __restrict__ types,
+                                const uint8_t* __restrict__ vals, const uint64_t* __restrict__ voff, uint32_t n,
+                                Recs recs, uint8_t* __restrict__ arena, uint32_t* __restrict__ surv, DErr* err) {
+  for (uint64_t i = gtid(); i < n; i += gstride()) {
+    const uint64_t u0 = ukoff[i], ulen = ukoff[i + 1] - u0;
+    const uint64_t kpos = u0 + 8 * i;
+    const uint64_t seq = seqs[i];
+    const uint32_t ty = types[i];
+    if (seq >= (1ull << 56) || ty > 1) report(err, E_INVALID, ~0u, i);
+    const uint64_t tr = (seq << 8) | (ty & 0xFFu);
+    uint8_t* kd = arena + kpos;
+    for (uint64_t t = 0; t < ulen; ++t) kd[t] = ukeys[u0 + t];
+    for (int t = 0; t < 8; ++t) kd[ulen + t] = uint8_t(tr >> (8 * t));
+    recs.pfx[i] = key_prefix(kd, uint32_t(ulen));
+    recs.koff[i] = kpos;
+    recs.klen[i] = uint32_t(ulen + 8);
+    recs.tr[i] = tr;
+    recs.vptr[i] = reinterpret_cast<uint64_t>(vals + voff[i]);
+    recs.vlen[i] = uint32_t(voff[i + 1] - voff[i]);
+    recs.src[i] = 0;
+    surv[i] = uint32_t(i);
+  }
+}
+
+__global__ void k_build_check(Recs recs, const uint8_t* __restrict__ arena, uint32_t n, DErr* err) {
+  for (uint64_t i = gtid() + 1; i < n; i += gstride()) {
+    const uint32_t a = uint32_t(i - 1), b = uint32_t(i);
+    // strictly increasing internal keys
+    int c;
+    const uint64_t pa = recs.pfx[a], pb = recs.pfx[b];
+    if (pa != pb) {
+      c = pa < pb ? -1 : 1;
+    } else {
+      const uint32_t la = recs.klen[a] - 8, lb = recs.klen[b] - 8;
+      const uint8_t* ka = arena + recs.koff[a];
+      const uint8_t* kb = arena + recs.koff[b];
+      const uint32_t m = la < lb ? la : lb;
+      c = 0;
+      for (uint32_t t = 8; t < m && !c; ++t)
+        if (ka[t] != kb[t]) c = ka[t] < kb[t] ? -1 : 1;
+      if (!c && la != lb) c = la < lb ? -1 : 1;
+      if (!c) {
+        const uint64_t ta = recs.tr[a], tb = recs.tr[b];
+        c = ta == tb ? 0 : (ta > tb ? -1 : 1);
+      }
+    }
+    if (c >= 0) report(err, E_INVALID, ~0u, i);
+  }
+}
+
+}  // namespace
+
+void launch_sizes(const uint32_t* surv, const Counts* cnt, uint32_t cap, const JobDev* jobs, uint32_t n_jobs,
+                  Recs recs, const uint8_t* arena, uint32_t* lcp, uint32_t* sd, uint32_t* dr, cudaStream_t st) {
+  if (!cap) return;
+  k_sizes<<<grid_for(cap, 256), 256, 0, st>>>(surv, cnt, jobs, n_jobs, recs, arena, lcp, sd, dr);
+}
+
+void launch_block_next(const uint64_t* P, const uint32_t* dr, const Counts* cnt, uint32_t cap, const JobDev* jobs,
+                       uint32_t n_jobs, Fmt fmt, uint32_t* next, cudaStream_t st) {
+  if (!cap) return;
+  k_block_next<<<grid_for(cap, 256), 256, 0, st>>>(P, dr, cnt, jobs, n_jobs, fmt, next);
+}
+
+uint64_t stitch_temp_bytes(uint32_t cap) {
+  const uint64_t tiles = (uint64_t(cap) + kStitchTile - 1) / kStitchTile;
+  return 2 * tiles * sizeof(uint32_t) + 256;
+}
+
+void launch_stitch(const uint32_t* next, const uint32_t* n_dev, uint32_t cap, uint8_t* flags, void* temp,
+                   cudaStream_t st) {
+  if (!cap) return;
+  const uint32_t tiles = (cap + kStitchTile - 1) / kStitchTile;
+  uint32_t* entry = static_cast<uint32_t*>(temp);
+  uint32_t* exitp = entry + tiles;
+  k_stitch_tiles<<<grid_for(tiles, 1, kSms * 8), 128, 0, st>>>(next, n_dev, flags, entry, exitp);
+  k_stitch_fix<<<1, 256, 0, st>>>(next, n_dev, flags, entry, exitp);
+}
+
+void launch_compact_flags(const uint8_t* flags, const uint32_t* pos, const uint32_t* n_dev, uint32_t cap,
+                          uint32_t* starts, uint32_t* total_out, cudaStream_t st) {
+  k_compact_flags<<<grid_for(cap, 256), 256, 0, st>>>(flags, pos, n_dev, starts, total_out);
+}
+
+void launch_job_blocks(JobDev* jobs, uint32_t n_jobs, const uint32_t* bpos, cudaStream_t st) {
+  k_job_blocks<<<grid_for(n_jobs, 128), 128, 0, st>>>(jobs, n_jobs, bpos);
+}
+
+void launch_block_sizes(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* P,
+                        const uint32_t* dr, Fmt fmt, uint64_t* bsz, uint64_t* disk, cudaStream_t st) {
+  if (!cap) return;
+  k_block_sizes<<<grid_for(cap, 256), 256, 0, st>>>(blk_start, cnt, P, dr, fmt, bsz, disk);
+}
+
+void launch_file_next(const uint64_t* C, const Counts* cnt, uint32_t cap, const JobDev* jobs, uint32_t n_jobs,
+                      Fmt fmt, uint32_t* next, cudaStream_t st) {
+  if (!cap) return;
+  k_file_next<<<grid_for(cap, 256), 256, 0, st>>>(C, cnt, jobs, n_jobs, fmt, next);
+}
+
+void launch_job_files(JobDev* jobs, uint32_t n_jobs, const uint32_t* fpos, cudaStream_t st) {
+  k_job_files<<<grid_for(n_jobs, 128), 128, 0, st>>>(jobs, n_jobs, fpos);
+}
+
+void launch_block_file(const uint32_t* fpos, const Counts* cnt, uint32_t cap, uint32_t* blk_file, cudaStream_t st) {
+  if (!cap) return;
+  k_block_file<<<grid_for(cap, 256), 256, 0, st>>>(fpos, cnt, blk_file);
+}
+
+void launch_index_sizes(const uint32_t* blk_start, const uint64_t* bsz, const uint64_t* C, const uint32_t* blk_file,
+                        const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* surv, Recs recs,
+                        uint32_t* ie, cudaStream_t st) {
+  if (!cap) return;
+  k_index_sizes<<<grid_for(cap, 256), 256, 0, st>>>(blk_start, bsz, C, blk_file, file_start, cnt, surv, recs, ie);
+}
+
+void launch_file_layout(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_start,
+                        const uint64_t* C, const uint64_t* IX, Fmt fmt, const JobDev* jobs, uint32_t n_jobs,
+                        FileDesc* files, uint64_t* fsize, uint64_t* bmwords, cudaStream_t st) {
+  if (!cap) return;
+  k_file_layout<<<grid_for(cap, 128), 128, 0, st>>>(file_start, cnt, blk_start, C, IX, fmt, jobs, n_jobs, files,
+                                                    fsize, bmwords);
+}
+
+void launch_file_offsets(FileDesc* files, Counts* cnt, uint32_t cap, const uint64_t* foff, const uint64_t* bmoff,
+                         JobDev* jobs, uint32_t n_jobs, uint64_t out_cap, uint64_t bm_cap, DErr* errs,
+                         cudaStream_t st) {
+  k_file_offsets<<<grid_for(cap > n_jobs ? cap : n_jobs, 128), 128, 0, st>>>(files, cnt, foff, bmoff, jobs, n_jobs,
+                                                                             out_cap, bm_cap, errs);
+}
+
+void launch_zero_bitmap(uint32_t* bitmap, const Counts* cnt, uint64_t cap_words, cudaStream_t st) {
+  if (!cap_words) return;
+  k_zero_words<<<grid_for(cap_words, 256), 256, 0, st>>>(bitmap, cnt, cap_words);
+}
+
+void launch_encode(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
+                   const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
+                   const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
+                   Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs, cudaStream_t st) {
+  if (!cap) return;
+  k_encode<<<grid_for(cap, 1, kSms * 16), kEncThreads, 0, st>>>(blk_start, cnt, blk_file, files, C, bsz, surv, lcp,
+                                                                sd, dr, recs, arena, fmt, out, out_cap, tabs);
+}
+
+void launch_bloom(const uint32_t* surv, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
+                  const uint32_t* blk_start, const FileDesc* files, Recs recs, const uint8_t* arena, Fmt fmt,
+                  uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st) {
+  if (!cap) return;
+  k_bloom<<<grid_for(cap, 256), 256, 0, st>>>(surv, cnt, blk_file, blk_start, files, recs, arena, fmt, bitmap,
+                                              out_cap, bm_cap);
+}
+
+void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* bsz,
+                        const uint64_t* C, const uint64_t* IX, const uint32_t* blk_file, const FileDesc* files,
+                        const uint32_t* surv, Recs recs, const uint8_t* arena, uint8_t* out, uint64_t out_cap,
+                        cudaStream_t st) {
+  if (!cap) return;
+  k_index_write<<<grid_for(cap, 128), 128, 0, st>>>(blk_start, cnt, bsz, C, IX, blk_file, files, surv, recs, arena,
+                                                    out, out_cap);
+}
+
+void launch_file_finish(const FileDesc* files, const Counts* cnt, uint32_t cap, const uint32_t* bitmap,
+                        const uint32_t* surv, Recs recs, Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs,
+                        FileMeta* meta, cudaStream_t st) {
+  if (!cap) return;
+  k_file_finish<<<grid_for(cap, 1, kSms * 16), 32, 0, st>>>(files, cnt, bitmap, surv, recs, fmt, out, out_cap, tabs,
+                                                            meta);
+}
+
+void launch_key_lens(const FileMeta* meta, const Counts* cnt, uint32_t cap, uint64_t* lens, cudaStream_t st) {
+  if (!cap) return;
+  k_key_lens<<<grid_for(cap, 128), 128, 0, st>>>(meta, cnt, lens);
+}
+
+void launch_key_gather(FileMeta* meta, Counts* cnt, uint32_t cap, const uint64_t* koff, const FileDesc* files,
+                       const uint32_t* surv, Recs recs, const uint8_t* arena, uint8_t* keybuf, cudaStream_t st) {
+  k_key_gather<<<grid_for(cap ? cap : 1, 128), 128, 0, st>>>(meta, cnt, koff, files, surv, recs, arena, keybuf);
+}
+
+void launch_build_records(const uint8_t* ukeys, const uint64_t* ukoff, const uint64_t* seqs, const uint8_t* types,
+                          const uint8_t* vals, const uint64_t* voff, uint32_t n, Recs recs, uint8_t* arena,
+                          uint32_t* surv, DErr* err, cudaStream_t st) {
+  if (!n) return;
+  k_build_records<<<grid_for(n, 256), 256, 0, st>>>(ukeys, ukoff, seqs, types, vals, voff, n, recs, arena, surv, err);
+}
+
+void launch_build_check(Recs recs, const uint8_t* arena, uint32_t n, DErr* err, cudaStream_t st) {
+  if (n < 2) return;
+  k_build_check<<<grid_for(n, 256), 256, 0, st>>>(recs, arena, n, err);
+}
+
+}  // namespace luda

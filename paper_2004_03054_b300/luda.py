@@ -1,0 +1,277 @@
+"""ctypes binding of libluda.so (argument marshalling only; every step runs in the
+library's CUDA kernels).
+
+The library must have been built (``python -m paper_2004_03054_b300.build``); loading
+fails loudly otherwise. PyTorch is used for device memory and the current stream only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libluda.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CORRUPTION = -2
+ERR_NOT_SUPPORTED = -3
+ERR_OOM = -4
+ERR_CUDA = -5
+ERR_TIMEOUT = -6
+ERR_DUPLICATE_KEY = -7
+ERR_PLAN_MISMATCH = -8
+F_STRICT_DUP = 1
+F_TRACE = 2
+MAX_SEQ = (1 << 56) - 1
+
+
+class Input(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("size", C.c_uint64), ("level", C.c_int32), ("file_number", C.c_uint64)]
+
+
+class Options(C.Structure):
+    _fields_ = [("block_size", C.c_uint32), ("restart_interval", C.c_uint32), ("bloom_bits_per_key", C.c_uint32),
+                ("target_file_size", C.c_uint64), ("bottommost", C.c_int32), ("flags", C.c_uint32),
+                ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p),
+                ("stream", C.c_void_p)]
+
+
+class Table(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("size", C.c_uint64), ("n_entries", C.c_uint64),
+                ("smallest", C.c_void_p), ("smallest_len", C.c_uint32),
+                ("largest", C.c_void_p), ("largest_len", C.c_uint32)]
+
+
+class Outputs(C.Structure):
+    _fields_ = [("tables", C.POINTER(Table)), ("n_tables", C.c_uint32), ("status", C.c_int32),
+                ("n_in_entries", C.c_uint64), ("n_dropped", C.c_uint64), ("ms_h2d", C.c_double),
+                ("ms_device", C.c_double), ("ms_d2h", C.c_double), ("stage_ms", C.c_double * 8),
+                ("_priv", C.c_void_p)]
+
+
+class Job(C.Structure):
+    _fields_ = [("inputs", C.POINTER(Input)), ("n_inputs", C.c_uint32), ("level", C.c_int32),
+                ("smallest_snapshot", C.c_uint64), ("bottommost", C.c_int32)]
+
+
+class RunArrays(C.Structure):
+    _fields_ = [("ukeys", C.c_void_p), ("ukoff", C.c_void_p), ("seqs", C.c_void_p), ("types", C.c_void_p),
+                ("vals", C.c_void_p), ("voff", C.c_void_p), ("n", C.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libluda.so; raises if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libluda.so not built ({_LIB_PATH}); run python -m paper_2004_03054_b300.build")
+        L = C.CDLL(_LIB_PATH)
+        st = C.c_int
+        L.luda_options_default.argtypes = [C.POINTER(Options)]
+        L.luda_compact.restype = st
+        L.luda_compact.argtypes = [C.POINTER(Input), C.c_uint32, C.c_int32, C.c_uint64, C.POINTER(Options),
+                                   C.POINTER(Outputs)]
+        L.luda_compact_device.restype = st
+        L.luda_compact_device.argtypes = L.luda_compact.argtypes
+        L.luda_batch_compact_device.restype = st
+        L.luda_batch_compact_device.argtypes = [C.POINTER(Job), C.c_uint32, C.POINTER(Options), C.POINTER(Outputs)]
+        L.luda_build.restype = st
+        L.luda_build.argtypes = [C.POINTER(RunArrays), C.POINTER(Options), C.POINTER(Outputs)]
+        L.luda_build_device.restype = st
+        L.luda_build_device.argtypes = L.luda_build.argtypes
+        L.luda_outputs_free.argtypes = [C.POINTER(Outputs)]
+        L.luda_strerror.restype = C.c_char_p
+        L.luda_strerror.argtypes = [C.c_int]
+        L.luda_last_error_detail.restype = C.c_char_p
+        L.luda_version.restype = C.c_char_p
+        for name in ("luda_plan_create", "luda_plan_run", "luda_plan_outputs", "luda_plan_destroy"):
+            if hasattr(L, name):
+                getattr(L, name).restype = st
+        if hasattr(L, "luda_plan_create"):
+            L.luda_plan_create.argtypes = [C.POINTER(Job), C.c_uint32, C.POINTER(Options), C.POINTER(C.c_void_p)]
+            L.luda_plan_run.argtypes = [C.c_void_p, C.c_void_p]
+            L.luda_plan_outputs.argtypes = [C.c_void_p, C.POINTER(Outputs)]
+            L.luda_plan_destroy.argtypes = [C.c_void_p]
+            L.luda_plan_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def options(block_size=4096, restart_interval=16, bloom_bits_per_key=10, target_file_size=2 << 20,
+            bottommost=False, flags=0, stream=None) -> Options:
+    o = Options()
+    lib().luda_options_default(C.byref(o))
+    o.block_size, o.restart_interval, o.bloom_bits_per_key = block_size, restart_interval, bloom_bits_per_key
+    o.target_file_size, o.bottommost, o.flags = target_file_size, int(bool(bottommost)), flags
+    o.stream = stream
+    return o
+
+
+def job_options(job, **kw) -> Options:
+    """Options of a workloads.Job."""
+    return options(job.block_size, job.restart_interval, job.bloom_bits_per_key, job.target_file_size,
+                   job.bottommost, **kw)
+
+
+def strerror(s: int) -> str:
+    return lib().luda_strerror(s).decode()
+
+
+def last_error_detail() -> str:
+    return lib().luda_last_error_detail().decode(errors="replace")
+
+
+def current_stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class Result:
+    status: int
+    tables: list = field(default_factory=list)      # bytes (host) or torch uint8 tensors (device)
+    smallest: list = field(default_factory=list)
+    largest: list = field(default_factory=list)
+    n_entries: list = field(default_factory=list)
+    n_in_entries: int = 0
+    n_dropped: int = 0
+    ms_h2d: float = 0.0
+    ms_device: float = 0.0
+    ms_d2h: float = 0.0
+    detail: str = ""
+
+
+class _CudaView:
+    """Exposes a device byte range through __cuda_array_interface__ (zero copy)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "|u1", "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+def device_bytes(ptr: int, n: int):
+    """A torch uint8 CUDA tensor copy of n bytes at device address ptr."""
+    import torch
+    if n == 0:
+        return torch.empty(0, dtype=torch.uint8, device="cuda")
+    return torch.as_tensor(_CudaView(ptr, n), device="cuda").clone()
+
+
+def _take(rc: int, out: Outputs, device: bool) -> Result:
+    res = Result(int(out.status) if rc == OK else rc, detail=last_error_detail() if rc or out.status else "")
+    res.n_in_entries, res.n_dropped = int(out.n_in_entries), int(out.n_dropped)
+    res.ms_h2d, res.ms_device, res.ms_d2h = out.ms_h2d, out.ms_device, out.ms_d2h
+    if rc == OK and out.status == OK:
+        for i in range(out.n_tables):
+            t = out.tables[i]
+            if device:
+                res.tables.append(device_bytes(t.data, t.size))
+            else:
+                res.tables.append(C.string_at(t.data, t.size))
+            res.smallest.append(C.string_at(t.smallest, t.smallest_len))
+            res.largest.append(C.string_at(t.largest, t.largest_len))
+            res.n_entries.append(int(t.n_entries))
+    lib().luda_outputs_free(C.byref(out))
+    return res
+
+
+def _u8(b) -> np.ndarray:
+    if isinstance(b, np.ndarray):
+        return np.ascontiguousarray(b, dtype=np.uint8)
+    return np.frombuffer(bytes(b), dtype=np.uint8)
+
+
+def compact(inputs, smallest_snapshot: int = MAX_SEQ, level: int = 1, opts: Options | None = None) -> Result:
+    """Host entry point: inputs are host byte strings / uint8 arrays (listed newest first)."""
+    arrs = [_u8(x) for x in inputs]
+    ins = (Input * max(1, len(arrs)))()
+    for i, a in enumerate(arrs):
+        ins[i].data, ins[i].size = a.ctypes.data, len(a)
+    o = opts or options()
+    out = Outputs()
+    rc = lib().luda_compact(ins, len(arrs), level, smallest_snapshot, C.byref(o), C.byref(out))
+    return _take(rc, out, device=False)
+
+
+def compact_device(inputs, smallest_snapshot: int = MAX_SEQ, level: int = 1, opts: Options | None = None,
+                   copy_out: bool = True):
+    """Device entry point: inputs are torch uint8 CUDA tensors. Returns a Result whose
+    tables are torch CUDA tensors (copies); with copy_out=False returns (rc, Outputs) and
+    the caller must call free_outputs."""
+    ins = (Input * max(1, len(inputs)))()
+    for i, t in enumerate(inputs):
+        ins[i].data, ins[i].size = t.data_ptr(), t.numel()
+    o = opts or options()
+    if o.stream is None:
+        o.stream = current_stream()
+    out = Outputs()
+    rc = lib().luda_compact_device(ins, len(inputs), level, smallest_snapshot, C.byref(o), C.byref(out))
+    if not copy_out:
+        return rc, out
+    return _take(rc, out, device=True)
+
+
+def free_outputs(out: Outputs) -> None:
+    lib().luda_outputs_free(C.byref(out))
+
+
+def batch_compact_device(jobs, opts: Options | None = None, copy_out: bool = True):
+    """jobs: list of (inputs: [torch CUDA uint8 tensors], smallest_snapshot, bottommost)."""
+    ins_keep = []
+    js = (Job * max(1, len(jobs)))()
+    for j, (inputs, snap, bottom) in enumerate(jobs):
+        ins = (Input * max(1, len(inputs)))()
+        for i, t in enumerate(inputs):
+            ins[i].data, ins[i].size = t.data_ptr(), t.numel()
+        ins_keep.append(ins)
+        js[j].inputs = C.cast(ins, C.POINTER(Input))
+        js[j].n_inputs, js[j].smallest_snapshot, js[j].bottommost = len(inputs), snap, int(bool(bottom))
+    o = opts or options()
+    if o.stream is None:
+        o.stream = current_stream()
+    outs = (Outputs * max(1, len(jobs)))()
+    rc = lib().luda_batch_compact_device(js, len(jobs), C.byref(o), outs)
+    if not copy_out:
+        return rc, outs
+    return rc, [_take(rc, outs[j], device=True) for j in range(len(jobs))]
+
+
+def _run_arrays(run, device: bool):
+    if device:
+        import torch
+        keep = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+                (run.ukeys, run.ukoff, run.seqs, run.types, run.vals, run.voff)]
+        ptrs = [t.data_ptr() for t in keep]
+    else:
+        keep = [np.ascontiguousarray(a) for a in (run.ukeys, run.ukoff, run.seqs, run.types, run.vals, run.voff)]
+        ptrs = [a.ctypes.data for a in keep]
+    ra = RunArrays(*ptrs, run.n)
+    return ra, keep
+
+
+def build(run, opts: Options | None = None) -> Result:
+    """Pack one sorted run (a workloads.Run) into tables; host arrays in, bytes out."""
+    ra, keep = _run_arrays(run, device=False)
+    o = opts or options(target_file_size=(1 << 64) - 1)
+    out = Outputs()
+    rc = lib().luda_build(C.byref(ra), C.byref(o), C.byref(out))
+    del keep
+    return _take(rc, out, device=False)
+
+
+def build_device(run, opts: Options | None = None) -> Result:
+    """Pack one sorted run on the device; tables come back as torch CUDA tensors."""
+    ra, keep = _run_arrays(run, device=True)
+    o = opts or options(target_file_size=(1 << 64) - 1)
+    if o.stream is None:
+        o.stream = current_stream()
+    out = Outputs()
+    rc = lib().luda_build_device(C.byref(ra), C.byref(o), C.byref(out))
+    del keep
+    return _take(rc, out, device=True)
