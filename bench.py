@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: SSTable compaction throughput (compaction input MiB/s) on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--scale S]
+
+One step = one full compaction job through libluda's C ABI: decode and verify every
+input data block, merge, drop rule, block/file cut, encode with CRC trailers, bloom
+filter, index/metaindex/footer of every new table. The workload is the large job: 4
+overlapping 64 MiB L0 tables + 12 L1 tables (~1 GiB of input, 8-64 B keys sharing 0-24 B
+prefixes, 1 KiB values, 10% overwrites, 3% deletions, 16 KiB blocks, restart interval 16,
+10 bits/key bloom, 64 MiB target files), synthetic and seeded. Its input tables are built
+on the GPU by the library's own table builder and stay resident in HBM; at 1 GiB they
+are far larger than the 126 MB L2, so no flush is needed between steps.
+
+`value` is device-resident input MiB/s over all ranks; `e2e` is the same metric through
+luda_compact with pinned host buffers (host-to-device copy of the inputs and
+device-to-host copy of the new tables inside the timed region). Multi-GPU is replicas
+only: each rank compacts its own copy of the job; nothing is exchanged.
+
+`--impl reference` times the CPU oracle (the plain single-threaded C compactor used by
+the tests) on a bounded sample of the same workload; it is the baseline arm.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MiB = float(1 << 20)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6400.0)), "measured"
+    return 6400.0, "fallback"
+
+
+# ---- clocks during the timed region -------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.time(), ln.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        sm, mx, reasons = [], [], set()
+        for ts, ln in self.lines:
+            if not (t0 - 0.15 <= ts <= t1 + 0.15):
+                continue
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- our arm ------------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2004_03054_b300 import luda
+    from paper_2004_03054_b300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    L = luda.lib()
+    job = W.config3(seed=3, scale=args.scale)
+    # inputs: the library's own builder packs each run into one table, kept on the device
+    inputs = []
+    for r in job.inputs:
+        res = luda.build_device(r, luda.options(job.block_size, job.restart_interval, job.bloom_bits_per_key,
+                                                (1 << 64) - 1))
+        if res.status != 0 or len(res.tables) != 1:
+            raise RuntimeError(f"input build failed: {res.status} {res.detail}")
+        inputs.append(res.tables[0])
+    in_bytes = sum(t.numel() for t in inputs)
+    ins = (luda.Input * len(inputs))()
+    for i, t in enumerate(inputs):
+        ins[i].data, ins[i].size = t.data_ptr(), t.numel()
+    stream = torch.cuda.current_stream()
+    opts = luda.job_options(job, flags=luda.F_TRACE, stream=C.c_void_p(stream.cuda_stream))
+
+    def step():
+        out = luda.Outputs()
+        rc = L.luda_compact_device(ins, len(inputs), job.level, job.smallest_snapshot, C.byref(opts),
+                                   C.byref(out))
+        if rc != 0:
+            raise RuntimeError(f"compaction failed: {rc} {luda.last_error_detail()}")
+        info = (sum(out.tables[i].size for i in range(out.n_tables)), out.n_tables, list(out.stage_ms),
+                list(out.stage_bytes), int(out.n_in_entries), int(out.n_dropped))
+        L.luda_outputs_free(C.byref(out))
+        return info
+
+    for _ in range(args.warmup):
+        out_bytes, n_tables, *_ = step()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else str(local))
+    sampler.start()
+    time.sleep(0.3)
+    l0 = luda.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    torch.cuda.nvtx.range_push("timed")
+    e0.record(stream)
+    stages, sbytes = [], []
+    for _ in range(args.steps):
+        out_bytes, n_tables, sm, sb, n_in, n_drop = step()
+        stages.append(sm)
+        sbytes.append(sb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    t1 = time.time()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = luda.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    time.sleep(0.2)
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * in_bytes / MiB / (ms / 1e3)
+
+    # dominant kernel: block scan [1] (CRC verify of every input block) vs encode [5]
+    peak, peak_kind = _peaks()
+    avg = [statistics.mean(s[i] for s in stages) for i in range(8)]
+    cand = {1: "k_block_scan", 5: "k_encode"}
+    dom = max(cand, key=lambda i: avg[i])
+    dom_bytes = sbytes[-1][dom]
+    achieved = dom_bytes / (avg[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": cand[dom], "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
+                "bytes_per_launch": dom_bytes, "ms_per_launch": round(avg[dom], 4),
+                "traffic": args.traffic}
+    path_gbs = (in_bytes + out_bytes) / (ms / 1e3) / 1e9
+    stage_names = ["sizing", "block_scan", "decode", "sort", "gc_cut_layout", "encode", "meta", "device_span"]
+
+    # end to end: luda_compact with pinned host inputs, new tables back in pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.empty(t.numel(), dtype=torch.uint8, pin_memory=True) for t in inputs]
+        for h, t in zip(host, inputs):
+            h.copy_(t)
+        hins = (luda.Input * len(host))()
+        for i, h in enumerate(host):
+            hins[i].data, hins[i].size = h.data_ptr(), h.numel()
+        hopts = luda.job_options(job, stream=C.c_void_p(stream.cuda_stream))
+        d2h = 0
+
+        def hstep():
+            out = luda.Outputs()
+            rc = L.luda_compact(hins, len(host), job.level, job.smallest_snapshot, C.byref(hopts), C.byref(out))
+            if rc != 0:
+                raise RuntimeError(f"host compaction failed: {rc} {luda.last_error_detail()}")
+            n = sum(out.tables[i].size for i in range(out.n_tables))
+            L.luda_outputs_free(C.byref(out))
+            return n
+
+        for _ in range(2):
+            d2h = hstep()
+        torch.cuda.synchronize()
+        ke = max(3, args.steps // 10)
+        ts = time.perf_counter()
+        for _ in range(ke):
+            d2h = hstep()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - ts) / ke
+        if ws > 1:
+            t = torch.tensor([te], dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": round(ws * in_bytes / MiB / te, 1), "unit": "MiB/s", "h2d_bytes_per_step": in_bytes,
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(te * 1e3, 3), "steps": ke}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "compaction input MiB/s (large job, device-resident inputs)",
+        "value": round(value, 1), "unit": "MiB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic (seeded, shaped like the paper's workloads)",
+        "config": {"workload": "cfg3_large: 4 L0 + 12 L1 tables of 64 MiB, 8-64 B keys (0-24 B shared prefixes), "
+                               "1 KiB values, 10% overwrites, 3% deletes, 16 KiB blocks, R=16, bpk=10, 64 MiB files",
+                   "scale": args.scale, "input_bytes": in_bytes, "output_bytes": out_bytes, "tables_out": n_tables,
+                   "entries_in": n_in, "entries_dropped": n_drop,
+                   "l2": "inputs (1 GiB) larger than the 126 MB L2; no flush", "parallelism": f"replicas x{ws}"},
+        "roofline": roofline,
+        "path": {"bytes_in_plus_out": in_bytes + out_bytes, "achieved_gbs": round(path_gbs, 1),
+                 "frac_of_peak": round(path_gbs / peak, 4)},
+        "stage_ms": {n: round(v, 4) for n, v in zip(stage_names, avg)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args):
+    """The oracle as it stands, single-threaded, on the same job (one full run)."""
+    import oracle
+    from paper_2004_03054_b300 import workloads as W
+    scale = args.cpu_scale
+    job = W.config3(seed=3, scale=scale)
+    ins = [oracle.build_tables(r, job.block_size, job.restart_interval, job.bloom_bits_per_key,
+                               (1 << 64) - 1).tables[0].data for r in job.inputs]
+    nbytes = sum(len(x) for x in ins)
+    timing = {}
+    res = oracle.compact(ins, job.smallest_snapshot, job.bottommost, job.block_size, job.restart_interval,
+                         job.bloom_bits_per_key, job.target_file_size, timing=timing)
+    if res.status != 0:
+        raise RuntimeError("oracle failed")
+    sec = timing["seconds"]
+    return {"value": round(nbytes / MiB / sec, 2), "unit": "MiB/s", "cores": 1, "kind": "oracle",
+            "sample": f"cfg3 job at scale {scale} ({nbytes / MiB:.0f} MiB of input), one run, {sec:.2f} s",
+            "cpu": _cpu_model(), "host_cores": os.cpu_count()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ---- reference arm: the oracle ------------------------------------------------------------
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2004_03054_b300 import workloads as W
+    scale = args.ref_scale
+    job = W.config3(seed=3, scale=scale)
+    ins = [oracle.build_tables(r, job.block_size, job.restart_interval, job.bloom_bits_per_key,
+                               (1 << 64) - 1).tables[0].data for r in job.inputs]
+    nbytes = sum(len(x) for x in ins)
+
+    def step():
+        timing = {}
+        res = oracle.compact(ins, job.smallest_snapshot, job.bottommost, job.block_size, job.restart_interval,
+                             job.bloom_bits_per_key, job.target_file_size, timing=timing)
+        if res.status != 0:
+            raise RuntimeError("oracle failed")
+        return timing["seconds"]
+
+    for _ in range(args.warmup):
+        step()
+    secs = [step() for _ in range(args.steps)]
+    sec = sum(secs) / len(secs)
+    value = nbytes / MiB / sec
+    sample = f"cfg3 job at scale {scale} ({nbytes / MiB:.0f} MiB of input) per step"
+    line = {"impl": "reference", "metric": "compaction input MiB/s (large job, device-resident inputs)",
+            "value": round(value, 2), "unit": "MiB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec * 1e3, 2), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8", "data": "synthetic (seeded, shaped like the paper's workloads)",
+            "config": {"workload": "cfg3_large (bounded sample)", "scale": scale, "input_bytes": nbytes},
+            "cpu_baseline": {"value": round(value, 2), "unit": "MiB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample, "cpu": _cpu_model()},
+            "e2e": {"value": round(value, 2), "unit": "MiB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--cpu-scale", type=float, default=1.0)
+    ap.add_argument("--ref-scale", type=float, default=1 / 16)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the dominant kernel from an ncu capture (reported as is)")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

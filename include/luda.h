@@ -108,7 +108,17 @@ typedef struct {
   uint64_t n_in_entries;        /* entries decoded from the inputs */
   uint64_t n_dropped;           /* entries removed by the drop rule */
   double ms_h2d, ms_device, ms_d2h;
-  double stage_ms[LUDA_N_STAGES]; /* with LUDA_F_TRACE: scan, decode, sort, gc, cut, encode, meta, d2h-meta */
+  /* With LUDA_F_TRACE, CUDA-event times on the call's stream (ms) and algorithmic bytes:
+   *  [0] sizing (footers, index, block scan, prefix sums; includes host round trips)
+   *  [1] block-scan kernel alone: CRC-32C verify + structure of every input data block;
+   *      bytes = input data blocks with trailers (read once)
+   *  [2] decode kernel alone      [3] order check + merge sort
+   *  [4] drop rule, entry sizes, block and file cut, layout
+   *  [5] encode kernel alone: bytes = output data blocks written + survivor keys and
+   *      values read
+   *  [6] bloom, index, metaindex, footer, boundary keys   [7] whole device span */
+  double stage_ms[LUDA_N_STAGES];
+  uint64_t stage_bytes[LUDA_N_STAGES];
   void* _priv;                  /* library bookkeeping: do not touch */
 } luda_outputs;
 
@@ -183,6 +193,8 @@ LUDA_API const char* luda_strerror(luda_status s);
 LUDA_API const char* luda_last_error_detail(void);
 /* Library version string. */
 LUDA_API const char* luda_version(void);
+/* Number of CUDA kernels this library has launched in this process so far. */
+LUDA_API uint64_t luda_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import subprocess
+import time
 from dataclasses import dataclass
 
 import numpy as np
@@ -208,14 +209,19 @@ def _take(rc, res_p) -> Result:
 
 def compact(inputs, smallest_snapshot: int = MAX_SEQ, bottommost: bool = False, block_size: int = 4096,
             restart_interval: int = 16, bloom_bits_per_key: int = 10, target_file_size: int = 2 << 20,
-            flags: int = 0) -> Result:
-    """Compact input tables (listed newest first) into new tables."""
+            flags: int = 0, timing: dict | None = None) -> Result:
+    """Compact input tables (listed newest first) into new tables. When `timing` is a
+    dict, timing["seconds"] receives the wall time of the C call alone."""
     arrs = [_u8(x) for x in inputs]
     ptrs = (C.c_void_p * max(1, len(arrs)))(*[a.ctypes.data for a in arrs])
     sizes = (C.c_uint64 * max(1, len(arrs)))(*[len(a) for a in arrs])
     res = C.POINTER(_Result)()
-    rc = lib().ora_compact(ptrs, sizes, len(arrs), smallest_snapshot, int(bool(bottommost)), block_size,
-                           restart_interval, bloom_bits_per_key, target_file_size, flags, C.byref(res))
+    L = lib()
+    t0 = time.perf_counter()
+    rc = L.ora_compact(ptrs, sizes, len(arrs), smallest_snapshot, int(bool(bottommost)), block_size,
+                       restart_interval, bloom_bits_per_key, target_file_size, flags, C.byref(res))
+    if timing is not None:
+        timing["seconds"] = time.perf_counter() - t0
     return _take(rc, res)
 
 

@@ -25,6 +25,12 @@
 using namespace luda;
 
 namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+
+void luda::count_launches(uint32_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
 
 thread_local char t_detail[512];
 
@@ -68,6 +74,13 @@ luda_status get_tabs(CrcTabs* out) {
     }
     t.slice = ds;
     t.shift = dh;
+    // Keep freed stream-ordered allocations cached in the device's default pool instead of
+    // returning them to the driver at every synchronisation (a process-local setting).
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
   }
   out->slice = t.slice;
   out->shift = t.shift;
@@ -250,20 +263,23 @@ void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t
 }
 
 // Survivors are in b.surv and cnt->n_surv is set; jobs[] hold surv ranges.
+struct Trace;
+void trace_mark(Trace* t, int i, cudaStream_t st);
+
 luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DErr* errs, uint32_t cap, Recs recs,
                      const uint8_t* arena, Fmt fmt, uint8_t* out, uint64_t out_cap, uint64_t bm_cap, CrcTabs tabs,
-                     cudaStream_t st) {
+                     cudaStream_t st, Trace* tr = nullptr) {
   launch_sizes(b.surv, cnt, cap, jobs, n_jobs, recs, arena, b.lcp, b.sd, b.dr, st);
   CK((exclusive_scan<uint32_t, uint64_t>(b.sd, b.P, cap, &cnt->n_surv, b.scan_tmp, st)));
   launch_block_next(b.P, b.dr, cnt, cap, jobs, n_jobs, fmt, b.next, st);
-  launch_stitch(b.next, &cnt->n_surv, cap, b.sflags, b.stitch_tmp, st);
+  launch_stitch(b.next, &cnt->n_surv, cap, &cnt->gap_surv, jobs, n_jobs, false, b.sflags, b.stitch_tmp, st);
   CK((exclusive_scan<uint8_t, uint32_t>(b.sflags, b.bpos, cap, &cnt->n_surv, b.scan_tmp, st)));
   launch_compact_flags(b.sflags, b.bpos, &cnt->n_surv, cap, b.blk_start, &cnt->nb, st);
   launch_job_blocks(jobs, n_jobs, b.bpos, st);
   launch_block_sizes(b.blk_start, cnt, cap, b.P, b.dr, fmt, b.bsz, b.disk, st);
   CK((exclusive_scan<uint64_t, uint64_t>(b.disk, b.C, cap, &cnt->nb, b.scan_tmp, st)));
   launch_file_next(b.C, cnt, cap, jobs, n_jobs, fmt, b.fnext, st);
-  launch_stitch(b.fnext, &cnt->nb, cap, b.fflags, b.stitch_tmp, st);
+  launch_stitch(b.fnext, &cnt->nb, cap, &cnt->gap_blk, jobs, n_jobs, true, b.fflags, b.stitch_tmp, st);
   CK((exclusive_scan<uint8_t, uint32_t>(b.fflags, b.fpos, cap, &cnt->nb, b.scan_tmp, st)));
   launch_compact_flags(b.fflags, b.fpos, &cnt->nb, cap, b.file_start, &cnt->nf, st);
   launch_job_files(jobs, n_jobs, b.fpos, st);
@@ -275,8 +291,10 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   CK((exclusive_scan<uint64_t, uint64_t>(b.bmw, b.bmoff, cap, &cnt->nf, b.scan_tmp, st)));
   launch_file_offsets(b.files, cnt, cap, b.foff, b.bmoff, jobs, n_jobs, out_cap, bm_cap, errs, st);
   launch_zero_bitmap(b.bitmap, cnt, bm_cap, st);
+  trace_mark(tr, 7, st);
   launch_encode(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena, fmt,
                 out, out_cap, tabs, st);
+  trace_mark(tr, 8, st);
   launch_bloom(b.surv, cnt, cap, b.blk_file, b.blk_start, b.files, recs, arena, fmt, b.bitmap, out_cap, bm_cap, st);
   launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, out, out_cap,
                      st);
@@ -361,6 +379,34 @@ void fill_outputs(const Collected& c, uint32_t n_jobs, uint8_t* out_base, Holder
   }
 }
 
+// CUDA events at stage boundaries on the call's stream (LUDA_F_TRACE only).
+struct Trace {
+  bool on = false;
+  cudaEvent_t ev[16] = {};
+  void init(bool enable) {
+    on = enable;
+    if (on)
+      for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) on = false;
+  }
+  void mark(int i, cudaStream_t st) {
+    if (on) cudaEventRecord(ev[i], st);
+  }
+  double span(int a, int b) {
+    float v = 0;
+    if (on && cudaEventSynchronize(ev[b]) == cudaSuccess) cudaEventElapsedTime(&v, ev[a], ev[b]);
+    return v;
+  }
+  ~Trace() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+void trace_mark(Trace* t, int i, cudaStream_t st) {
+  if (t) t->mark(i, st);
+}
+
 struct HostJob {
   const luda_input* inputs;
   uint32_t n_inputs;
@@ -392,7 +438,8 @@ struct Timer {
 // The whole compaction for n_jobs jobs whose inputs are device pointers. On return
 // outs[j] hold device (or, with host_out, pinned host) tables.
 luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_options* o, cudaStream_t st,
-                           luda_outputs* outs, bool host_out, double* ms_device, double* ms_d2h) {
+                           luda_outputs* outs, bool host_out, double* ms_device, double* ms_d2h,
+                           double* stage_ms = nullptr, uint64_t* stage_bytes = nullptr) {
   Fmt fmt;
   luda_status rc = opts_check(o, &fmt);
   if (rc) return rc;
@@ -413,6 +460,9 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   const DevMem mem{o, st};
   Timer tdev;
   tdev.start(st);
+  Trace tr;
+  tr.init((o->flags & LUDA_F_TRACE) && stage_ms);
+  tr.mark(0, st);
 
   // ---- sizing: footers -------------------------------------------------------------------
   std::vector<DInput> hin;
@@ -511,7 +561,9 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   layoutB(LB, d_blocks, d_nrec, d_kbytes, d_rec_first, d_key_first, d_in_rec, d_in_key, d_tmpB);
 
   launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
-  launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, tabs, st);
+  tr.mark(1, st);
+  launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, tabs, st);
+  tr.mark(2, st);
   launch_zero_failed(d_blocks, NB, d_errs, d_nrec, d_kbytes, st);
   CK((exclusive_scan<uint32_t, uint32_t>(d_nrec, d_rec_first, NB, nullptr, d_tmpB, st)));
   CK((exclusive_scan<uint64_t, uint64_t>(d_kbytes, d_key_first, NB, nullptr, d_tmpB, st)));
@@ -523,6 +575,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   CK(cudaMemcpyAsync(in_rec.data(), d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(in_key.data(), d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(herr.data(), d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
+  tr.mark(3, st);
   CK(cudaStreamSynchronize(st));
 
   const uint32_t n_rec = in_rec[N];
@@ -618,14 +671,14 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     }
   } out_guard{mem, d_out, &out_owned};
 
-  Counts hc{};
-  hc.n_rec = n_rec;
-  CK(cudaMemcpyAsync(d_cnt, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(&d_cnt->n_rec, &n_rec, sizeof n_rec, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_jobs, hjobs.data(), sizeof(JobDev) * n_jobs, cudaMemcpyHostToDevice, st));
   if (!spans.empty())
     CK(cudaMemcpyAsync(d_spans, spans.data(), sizeof(MergeSpan) * spans.size(), cudaMemcpyHostToDevice, st));
 
+  tr.mark(4, st);
   launch_decode(d_blocks, NB, d_in, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
+  tr.mark(5, st);
   launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
   launch_sort_init(d_ord0, d_pfx0, recs.pfx, n_rec, st);
   uint32_t* src_o = d_ord0;
@@ -638,13 +691,16 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     std::swap(src_o, dst_o);
     std::swap(src_p, dst_p);
   }
+  tr.mark(6, st);
   launch_gc_flags(src_o, n_rec, d_jobs, n_jobs, recs, d_arena, d_keep, d_errs, st);
   CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
   launch_gc_compact(src_o, d_keep, d_pos, n_rec, pb.surv, st);
   launch_job_surv(d_jobs, n_jobs, d_pos, n_rec, d_cnt, st);
   CK(cudaGetLastError());
-  if ((rc = run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap, tabs, st)))
+  if ((rc = run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap, tabs, st,
+                     tr.on ? &tr : nullptr)))
     return rc;
+  tr.mark(10, st);
   tdev.stop(st);
 
   // ---- collect -------------------------------------------------------------------------------
@@ -682,6 +738,20 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   const double dev_ms = tdev.ms();
   if (ms_device) *ms_device = dev_ms;
   if (ms_d2h) *ms_d2h = d2h;
+  if (tr.on) {
+    stage_ms[0] = tr.span(0, 3);
+    stage_ms[1] = tr.span(1, 2);
+    stage_ms[2] = tr.span(4, 5);
+    stage_ms[3] = tr.span(5, 6);
+    stage_ms[4] = tr.span(6, 7);
+    stage_ms[5] = tr.span(7, 8);
+    stage_ms[6] = tr.span(8, 10);
+    stage_ms[7] = tr.span(0, 10);
+    uint64_t out_data = 0;
+    for (const FileMeta& m : col.meta) out_data += m.data_size;
+    stage_bytes[1] = col.cnt.in_data_bytes;
+    stage_bytes[5] = out_data + col.cnt.surv_kv_bytes;
+  }
   luda_status first = LUDA_OK;
   for (uint32_t j = 0; j < n_jobs; ++j) {
     outs[j].status = err_status(col.errs[j], j, n_jobs);
@@ -898,6 +968,8 @@ const char* luda_last_error_detail(void) { return t_detail; }
 
 const char* luda_version(void) { return "luda-b300 0.1 (sm_103a)"; }
 
+uint64_t luda_launch_count(void) { return g_launches.load(); }
+
 void luda_outputs_free(luda_outputs* out) {
   if (!out) return;
   OutPriv* p = static_cast<OutPriv*>(out->_priv);
@@ -941,7 +1013,7 @@ luda_status luda_compact_device(const luda_input* inputs, uint32_t n_inputs, int
   HostJob hj{inputs, n_inputs, smallest_snapshot, opts->bottommost};
   const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
   double ms = 0;
-  luda_status rc = run_compaction(&hj, 1, opts, st, out, false, &ms, nullptr);
+  luda_status rc = run_compaction(&hj, 1, opts, st, out, false, &ms, nullptr, out->stage_ms, out->stage_bytes);
   if (rc) {
     out->status = rc;
     return rc;
@@ -996,7 +1068,9 @@ luda_status luda_compact(const luda_input* inputs, uint32_t n_inputs, int32_t le
   th.stop(st);
   HostJob hj{din.data(), n_inputs, smallest_snapshot, opts->bottommost};
   double ms = 0, d2h = 0;
-  rc = run_compaction(&hj, 1, opts, st, out, true, &ms, &d2h);
+  double sms[LUDA_N_STAGES] = {};
+  uint64_t sbytes[LUDA_N_STAGES] = {};
+  rc = run_compaction(&hj, 1, opts, st, out, true, &ms, &d2h, sms, sbytes);
   const double h2d = th.ms();
   mem.put(arena);
   cudaStreamSynchronize(st);
@@ -1007,6 +1081,8 @@ luda_status luda_compact(const luda_input* inputs, uint32_t n_inputs, int32_t le
   out->ms_h2d = h2d;
   out->ms_device = ms;
   out->ms_d2h = d2h;
+  memcpy(out->stage_ms, sms, sizeof sms);
+  memcpy(out->stage_bytes, sbytes, sizeof sbytes);
   if (out->status) {
     const luda_status s = luda_status(out->status);
     luda_outputs_free(out);

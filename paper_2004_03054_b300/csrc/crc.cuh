@@ -114,6 +114,76 @@ static __device__ __noinline__ uint32_t warp_crc32c(const uint8_t* p, uint64_t n
   return crc ^ 0xFFFFFFFFu;
 }
 
+// Standard CRC-32C of n bytes at p computed by all NT threads of the CTA (NT = blockDim.x,
+// a multiple of 32, at most 1024); same method as warp_crc32c with an NT-leaf butterfly
+// (shuffles inside warps, `scratch` (>= NT/32 words of shared memory) across warps).
+// Every thread must call it; every thread gets the result.
+static __device__ __noinline__ uint32_t cta_crc32c(const uint8_t* p, uint64_t n, const uint32_t* sT,
+                                                   const CrcTabs tabs, uint32_t* scratch) {
+  const uint32_t tid = threadIdx.x, NT = blockDim.x, lane = tid & 31u, warp = tid >> 5, nw = NT >> 5;
+  if (n < 16) {
+    if (tid == 0) {
+      uint32_t c = 0xFFFFFFFFu;
+      for (uint64_t i = 0; i < n; ++i) c = sT[(c ^ p[i]) & 0xFFu] ^ (c >> 8);
+      scratch[0] = c ^ 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    const uint32_t r = scratch[0];
+    __syncthreads();
+    return r;
+  }
+  const uintptr_t ps = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t pe = ps + n;
+  const uintptr_t a0 = ps & ~uintptr_t(15);
+  const uintptr_t a1 = (pe + 15) & ~uintptr_t(15);
+  const uint32_t pad = uint32_t(a1 - pe);
+  const int64_t W = int64_t((a1 - a0) >> 4);
+  uint32_t j = 0;
+  while ((int64_t(NT) << j) < W) ++j;
+  const int64_t cw = int64_t(1) << j;
+  int64_t w0 = W - cw * int64_t(NT - tid);
+  const int64_t w1 = w0 + cw;
+  if (w0 < 0) w0 = 0;
+  uint32_t crc = 0;
+#pragma unroll 1
+  for (int64_t w = w0; w < w1; ++w) {
+    const uintptr_t q = a0 + (uintptr_t(w) << 4);
+    uint4 v = *reinterpret_cast<const uint4*>(q);
+    if (q < ps + 4 || q + 16 > pe) {
+      v.x = crc_fix_word(v.x, q, ps, pe);
+      v.y = crc_fix_word(v.y, q + 4, ps, pe);
+      v.z = crc_fix_word(v.z, q + 8, ps, pe);
+      v.w = crc_fix_word(v.w, q + 12, ps, pe);
+    }
+    crc = crc_step4(crc, v.x, sT);
+    crc = crc_step4(crc, v.y, sT);
+    crc = crc_step4(crc, v.z, sT);
+    crc = crc_step4(crc, v.w, sT);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const uint32_t other = __shfl_xor_sync(0xFFFFFFFFu, crc, 1u << k);
+    const uint32_t* tab = tabs.shift + size_t(j + k) * 1024;
+    crc = (lane & (1u << k)) ? (crc_shift(tab, other) ^ crc) : (crc_shift(tab, crc) ^ other);
+  }
+  if (lane == 0) scratch[warp] = crc;
+  __syncthreads();
+  if (warp == 0) {
+    crc = lane < nw ? scratch[lane] : 0u;
+    for (uint32_t k = 0; (1u << k) < nw; ++k) {
+      const uint32_t other = __shfl_xor_sync(0xFFFFFFFFu, crc, 1u << k);
+      const uint32_t* tab = tabs.shift + size_t(j + 5 + k) * 1024;
+      crc = (lane & (1u << k)) ? (crc_shift(tab, other) ^ crc) : (crc_shift(tab, crc) ^ other);
+    }
+    if (pad) crc = crc_shift(tabs.shift + size_t(kShiftPow + pad - 1) * 1024, crc);
+    if (lane == 0) scratch[0] = crc ^ 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  const uint32_t r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
 // Stage the slicing table into shared memory (1024 words), whole CTA.
 __device__ __forceinline__ void load_slice_table(uint32_t* sT, const CrcTabs tabs) {
   for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) sT[i] = __ldg(tabs.slice + i);

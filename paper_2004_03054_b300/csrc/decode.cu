@@ -19,20 +19,25 @@ __device__ __forceinline__ bool handle_ok(uint64_t off, uint64_t size, uint64_t 
   return off <= limit && size <= limit - off && uint64_t(kTrailer) <= limit - off - size;
 }
 
-// One warp per input: footer, index block CRC and type, index restart count.
-__global__ void __launch_bounds__(32) k_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcTabs tabs) {
+// One CTA per input: footer, index block CRC and type, index restart count.
+constexpr int kFootThreads = 256;
+
+__global__ void __launch_bounds__(kFootThreads) k_footers(DInput* in, uint32_t n_inputs, DErr* errs,
+                                                          CrcTabs tabs) {
   __shared__ uint32_t sT[1024];
+  __shared__ uint32_t s_scratch[kFootThreads / 32];
+  __shared__ uint64_t s_h[3];
   load_slice_table(sT, tabs);
   __syncthreads();
-  const uint32_t lane = lane_id();
+  const uint32_t tid = threadIdx.x;
   for (uint32_t i = blockIdx.x; i < n_inputs; i += gridDim.x) {
     const uint8_t* f = in[i].data;
     const uint64_t size = in[i].size;
     DErr* e = errs + in[i].job;
     const uint32_t local = in[i].local;
-    uint64_t ioff = 0, isize = 0;
-    int ok = 0;
-    if (lane == 0) {
+    if (tid == 0) {
+      uint64_t ioff = 0, isize = 0;
+      int ok = 0;
       if (size >= kFooter && ld_u64(f + size - 8) == kMagic) {
         const uint8_t* p = f + size - kFooter;
         const uint8_t* end = p + 40;
@@ -45,14 +50,17 @@ __global__ void __launch_bounds__(32) k_footers(DInput* in, uint32_t n_inputs, D
         ok = a && handle_ok(moff, msize, limit) && handle_ok(ioff, isize, limit);
       }
       if (!ok) report(e, E_CORRUPT, local, size);
+      s_h[0] = ok;
+      s_h[1] = ioff;
+      s_h[2] = isize;
     }
-    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
-    ioff = __shfl_sync(0xFFFFFFFFu, ioff, 0);
-    isize = __shfl_sync(0xFFFFFFFFu, isize, 0);
+    __syncthreads();
+    const bool ok = s_h[0] != 0;
+    const uint64_t ioff = s_h[1], isize = s_h[2];
     uint32_t nblk = 0;
     if (ok) {
-      const uint32_t got = warp_crc32c(f + ioff, isize + 1, sT, tabs);
-      if (lane == 0) {
+      const uint32_t got = cta_crc32c(f + ioff, isize + 1, sT, tabs, s_scratch);
+      if (tid == 0) {
         const uint32_t want = crc_unmask(ld_u32(f + ioff + isize + 1));
         if (got != want) {
           report(e, E_CORRUPT, local, ioff);
@@ -65,11 +73,12 @@ __global__ void __launch_bounds__(32) k_footers(DInput* in, uint32_t n_inputs, D
         }
       }
     }
-    if (lane == 0) {
+    if (tid == 0) {
       in[i].idx_off = ioff;
       in[i].idx_size = isize;
       in[i].nblk = nblk;
     }
+    __syncthreads();
   }
 }
 
@@ -159,7 +168,8 @@ __device__ __forceinline__ bool walk_segment(const uint8_t* base, uint64_t s, ui
 // One warp per data block: CRC, type, structure; entry and key-byte counts.
 __global__ void __launch_bounds__(256) k_block_scan(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
                                                     const DInput* __restrict__ in, uint32_t* __restrict__ nrec,
-                                                    uint64_t* __restrict__ kbytes, DErr* errs, CrcTabs tabs) {
+                                                    uint64_t* __restrict__ kbytes, DErr* errs, Counts* counts,
+                                                    CrcTabs tabs) {
   __shared__ uint32_t sT[1024];
   load_slice_table(sT, tabs);
   __syncthreads();
@@ -171,6 +181,8 @@ __global__ void __launch_bounds__(256) k_block_scan(const BlockDesc* __restrict_
     uint32_t cnt = 0;
     uint64_t kb = 0;
     if (b.ptr != nullptr && *(volatile int32_t*)&e->code == 0) {
+      if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&counts->in_data_bytes),
+                               (unsigned long long)(b.size + kTrailer));
       const uint32_t got = warp_crc32c(b.ptr, b.size + 1, sT, tabs);
       const uint32_t want = crc_unmask(ld_u32(b.ptr + b.size + 1));
       const uint32_t local = in[b.input].local;
@@ -319,36 +331,36 @@ __global__ void k_input_ranges(const DInput* __restrict__ in, uint32_t n_inputs,
 
 void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cudaStream_t st) {
   if (!n_inputs) return;
-  k_footers<<<grid_for(n_inputs, 1, 4096), 32, 0, st>>>(in, n_inputs, errs, tabs);
+  k_footers<<<grid_for(n_inputs, 1, kSms * 4), kFootThreads, 0, st>>>(in, n_inputs, errs, tabs); count_launches(1);
 }
 
 void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
                           BlockDesc* blocks, DErr* errs, cudaStream_t st) {
   if (!n_blocks) return;
-  k_index_entries<<<grid_for(n_blocks, 256), 256, 0, st>>>(in, n_inputs, in_blk_first, n_blocks, blocks, errs);
+  k_index_entries<<<grid_for(n_blocks, 256), 256, 0, st>>>(in, n_inputs, in_blk_first, n_blocks, blocks, errs); count_launches(1);
 }
 
 void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, CrcTabs tabs, cudaStream_t st) {
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, CrcTabs tabs, cudaStream_t st) {
   if (!n_blocks) return;
-  k_block_scan<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, tabs);
+  k_block_scan<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, cnt, tabs); count_launches(1);
 }
 
 void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* rec_first,
                    const uint64_t* key_first, Recs recs, uint8_t* arena, DErr* errs, cudaStream_t st) {
   if (!n_blocks) return;
-  k_decode<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, rec_first, key_first, recs, arena, errs);
+  k_decode<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, rec_first, key_first, recs, arena, errs); count_launches(1);
 }
 
 void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,
                         uint64_t* kbytes, cudaStream_t st) {
   if (!n_blocks) return;
-  k_zero_failed<<<grid_for(n_blocks, 256), 256, 0, st>>>(blocks, n_blocks, errs, nrec, kbytes);
+  k_zero_failed<<<grid_for(n_blocks, 256), 256, 0, st>>>(blocks, n_blocks, errs, nrec, kbytes); count_launches(1);
 }
 
 void launch_input_ranges(const DInput* in, uint32_t n_inputs, const uint32_t* rec_first, const uint64_t* key_first,
                          uint32_t* in_rec, uint64_t* in_key, cudaStream_t st) {
-  k_input_ranges<<<grid_for(n_inputs + 1, 256), 256, 0, st>>>(in, n_inputs, rec_first, key_first, in_rec, in_key);
+  k_input_ranges<<<grid_for(n_inputs + 1, 256), 256, 0, st>>>(in, n_inputs, rec_first, key_first, in_rec, in_key); count_launches(1);
 }
 
 }  // namespace luda

@@ -73,17 +73,24 @@ struct Counts {
   uint64_t out_bytes; // bytes of all table images
   uint64_t bm_words;  // bloom bitmap words
   uint64_t key_bytes; // gathered smallest/largest key bytes
+  uint64_t in_data_bytes;   // input data blocks with trailers (block scan)
+  uint64_t surv_kv_bytes;   // survivor keys + values (read by the encoder)
+  uint32_t gap_surv;        // largest next(i) - i of the block cut
+  uint32_t gap_blk;         // largest next(b) - b of the file cut
 };
 
 // Per-output-table summary copied to the host at the end.
 struct FileMeta {
-  uint64_t off, size, n_entries;
+  uint64_t off, size, n_entries, data_size;
   uint64_t small_koff, large_koff;  // in the key gather buffer
   uint32_t small_len, large_len;
   uint32_t job, pad;
 };
 
 // ---- launch geometry --------------------------------------------------------------------
+// Every launcher adds its kernel launches here (luda_launch_count).
+void count_launches(uint32_t n);
+
 inline unsigned grid_for(uint64_t work, unsigned per_cta, unsigned max_ctas = kSms * 16) {
   uint64_t g = (work + per_cta - 1) / per_cta;
   if (g < 1) g = 1;
@@ -105,7 +112,7 @@ void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cud
 void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
                           BlockDesc* blocks, DErr* errs, cudaStream_t st);
 void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, CrcTabs tabs, cudaStream_t st);
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, CrcTabs tabs, cudaStream_t st);
 void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,
                         uint64_t* kbytes, cudaStream_t st);
 void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* rec_first,
@@ -141,8 +148,8 @@ void launch_sizes(const uint32_t* surv, const Counts* cnt, uint32_t cap, const J
 void launch_block_next(const uint64_t* P, const uint32_t* dr, const Counts* cnt, uint32_t cap, const JobDev* jobs,
                        uint32_t n_jobs, Fmt fmt, uint32_t* next, cudaStream_t st);
 uint64_t stitch_temp_bytes(uint32_t cap);
-void launch_stitch(const uint32_t* next, const uint32_t* n_dev, uint32_t cap, uint8_t* flags, void* temp,
-                   cudaStream_t st);
+void launch_stitch(const uint32_t* next, const uint32_t* n_dev, uint32_t cap, uint32_t* gap, const JobDev* jobs,
+                   uint32_t n_jobs, bool blocks_level, uint8_t* flags, void* temp, cudaStream_t st);
 void launch_compact_flags(const uint8_t* flags, const uint32_t* pos, const uint32_t* n_dev, uint32_t cap,
                           uint32_t* starts, uint32_t* total_out, cudaStream_t st);
 void launch_job_blocks(JobDev* jobs, uint32_t n_jobs, const uint32_t* bpos, cudaStream_t st);

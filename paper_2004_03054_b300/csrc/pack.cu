@@ -56,6 +56,7 @@ __global__ void k_sizes(const uint32_t* __restrict__ surv, const Counts* __restr
                         const JobDev* __restrict__ jobs, uint32_t n_jobs, Recs recs, const uint8_t* __restrict__ arena,
                         uint32_t* __restrict__ lcp, uint32_t* __restrict__ sd, uint32_t* __restrict__ dr) {
   const uint32_t n = cnt->n_surv;
+  uint64_t kv = 0;
   for (uint64_t s = gtid(); s < n; s += gstride()) {
     const uint32_t j = job_of_surv(jobs, n_jobs, uint32_t(s));
     const uint32_t x = surv[s];
@@ -73,7 +74,13 @@ __global__ void k_sizes(const uint32_t* __restrict__ surv, const Counts* __restr
     lcp[s] = l;
     sd[s] = d;
     dr[s] = r - d;
+    kv += klen + vlen;
   }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) kv += __shfl_xor_sync(0xFFFFFFFFu, kv, o);
+  if ((threadIdx.x & 31u) == 0 && kv)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&const_cast<Counts*>(cnt)->surv_kv_bytes),
+              (unsigned long long)kv);
 }
 
 // next(i) = 1 + min{j >= i : E(i, j) >= T}, capped at the job's end, with
@@ -106,124 +113,131 @@ __global__ void k_block_next(const uint64_t* __restrict__ P, const uint32_t* __r
 }
 
 // ---- chain stitching --------------------------------------------------------------------
+// The cut points are the chain 0, next(0), next(next(0)), ... over a next[] array with
+// next(i) > i, capped at each job's end (so every job start is on the chain). Exact and
+// parallel without any convergence assumption:
+//   window path (largest step G = max(next(i) - i) <= kWinMax): the first chain node of
+//     tile t lies in [L_t, L_t + G). Each tile walks its chain from every one of those W
+//     candidates (one thread each, tile's next[] in shared memory) and records where it
+//     leaves the tile; one CTA then composes the tiles in order with table lookups in
+//     shared memory; finally every tile marks its chain from its true entry.
+//   walk path (G > kWinMax, e.g. the file cut over blocks): the chain is walked per job,
+//     jobs in parallel; such chains have few nodes.
 constexpr uint32_t kStitchTile = 2048;
-constexpr uint32_t kStitchChunk = 2048;
+constexpr uint32_t kWinMax = 256;
 
-__global__ void __launch_bounds__(128) k_stitch_tiles(const uint32_t* __restrict__ next,
-                                                      const uint32_t* __restrict__ n_dev,
-                                                      uint8_t* __restrict__ flags, uint32_t* __restrict__ entry,
-                                                      uint32_t* __restrict__ exitp) {
-  __shared__ uint32_t s_prev[kStitchTile], s_cur[kStitchTile];
-  __shared__ uint8_t gm[kStitchTile], tm[kStitchTile];
-  __shared__ uint32_t s_conv;
+__device__ __forceinline__ uint32_t win_of(uint32_t gap) { return max(32u, (gap + 31u) & ~31u); }
+
+__global__ void k_max_gap(const uint32_t* __restrict__ next, const uint32_t* __restrict__ n_dev,
+                          uint32_t* __restrict__ gap) {
   const uint32_t n = *n_dev;
+  uint32_t g = 0;
+  for (uint64_t i = gtid(); i < n; i += gstride()) g = max(g, next[i] - uint32_t(i));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) g = max(g, __shfl_xor_sync(0xFFFFFFFFu, g, o));
+  if ((threadIdx.x & 31u) == 0 && g) atomicMax(gap, g);
+}
+
+__global__ void __launch_bounds__(256) k_stitch_win(const uint32_t* __restrict__ next,
+                                                    const uint32_t* __restrict__ n_dev,
+                                                    const uint32_t* __restrict__ gap,
+                                                    uint32_t* __restrict__ exitw) {
+  __shared__ uint32_t s_next[kStitchTile];
+  if (*gap > kWinMax) return;
+  const uint32_t n = *n_dev, W = win_of(*gap);
   const uint32_t n_tiles = (n + kStitchTile - 1) / kStitchTile;
   for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const uint32_t L = t * kStitchTile;
-    const uint32_t U = min(n, L + kStitchTile);
-    const uint32_t PL = t ? L - kStitchTile : 0;
-    for (uint32_t i = threadIdx.x; i < kStitchTile; i += blockDim.x) {
-      s_cur[i] = L + i < U ? next[L + i] : n;
-      s_prev[i] = t ? next[PL + i] : n;
-      gm[i] = 0;
-      tm[i] = 0;
-    }
+    const uint32_t L = t * kStitchTile, U = min(n, L + kStitchTile);
+    for (uint32_t i = threadIdx.x; i < U - L; i += blockDim.x) s_next[i] = next[L + i];
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t a = 0;
-      if (t) {
-        uint32_t h = PL;
-        while (h < L) h = s_prev[h - PL];
-        a = h;
-      }
-      uint32_t g = L;
-      while (g < U) {
-        gm[g - L] = 1;
-        g = s_cur[g - L];
-      }
-      uint32_t conv, ex;
-      if (a >= U) {
-        conv = U;
-        ex = a;
-      } else {
-        uint32_t x = a;
-        while (x < U && !gm[x - L]) {
-          tm[x - L] = 1;
-          x = s_cur[x - L];
-        }
-        if (x < U) {
-          conv = x;
-          ex = g;
-        } else {
-          conv = U;
-          ex = x;
-        }
-      }
-      entry[t] = a;
-      exitp[t] = ex;
-      s_conv = conv;
+    for (uint32_t k = threadIdx.x; k < W; k += blockDim.x) {
+      uint32_t x = L + k;
+      while (x < U) x = s_next[x - L];
+      exitw[uint64_t(t) * kWinMax + k] = x;
     }
-    __syncthreads();
-    const uint32_t conv = s_conv;
-    for (uint32_t i = L + threadIdx.x; i < U; i += blockDim.x)
-      flags[i] = uint8_t(tm[i - L] | (gm[i - L] && i >= conv));
     __syncthreads();
   }
 }
 
-// Single CTA: walk the tiles in order; where a tile was computed from a wrong entry,
-// redo it from the true one (until the true chain meets the tile's flagged chain).
-__global__ void __launch_bounds__(256) k_stitch_fix(const uint32_t* __restrict__ next,
-                                                    const uint32_t* __restrict__ n_dev, uint8_t* __restrict__ flags,
-                                                    const uint32_t* __restrict__ entry,
-                                                    const uint32_t* __restrict__ exitp) {
-  const uint32_t n = *n_dev;
+__global__ void __launch_bounds__(256) k_stitch_combine(const uint32_t* __restrict__ exitw,
+                                                        const uint32_t* __restrict__ n_dev,
+                                                        const uint32_t* __restrict__ gap,
+                                                        uint32_t* __restrict__ entry) {
+  constexpr uint32_t kWords = 12000;  // rows held in shared memory
+  __shared__ uint32_t s_rows[kWords];
+  __shared__ uint32_t s_cur;
+  if (*gap > kWinMax) return;
+  const uint32_t n = *n_dev, W = win_of(*gap);
   const uint32_t n_tiles = (n + kStitchTile - 1) / kStitchTile;
-  __shared__ uint32_t s_entry[kStitchChunk], s_exit[kStitchChunk];
-  __shared__ uint32_t s_list[kStitchTile];
-  __shared__ uint32_t s_cur, s_t, s_nl, s_clear_end;
+  const uint32_t per = kWords / W;
   if (threadIdx.x == 0) s_cur = 0;
-  for (uint32_t t0 = 0; t0 < n_tiles; t0 += kStitchChunk) {
-    const uint32_t tend = min(n_tiles, t0 + kStitchChunk);
+  for (uint32_t t0 = 0; t0 < n_tiles; t0 += per) {
+    const uint32_t tn = min(per, n_tiles - t0);
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < tend - t0; i += blockDim.x) {
-      s_entry[i] = entry[t0 + i];
-      s_exit[i] = exitp[t0 + i];
+    for (uint32_t i = threadIdx.x; i < tn * W; i += blockDim.x) {
+      const uint32_t r = i / W, k = i - r * W;
+      s_rows[i] = exitw[uint64_t(t0 + r) * kWinMax + k];
     }
     __syncthreads();
-    uint32_t t = t0;
-    while (true) {
-      if (threadIdx.x == 0) {
-        uint32_t c = s_cur, tt = t;
-        while (tt < tend && c == s_entry[tt - t0]) c = s_exit[(tt++) - t0];
-        s_cur = c;
-        s_t = tt;
-        if (tt < tend) {
-          const uint32_t L = tt * kStitchTile, U = min(n, L + kStitchTile);
-          uint32_t x = c, nl = 0;
-          while (x < U && !flags[x]) {
-            s_list[nl++] = x;
-            x = next[x];
-          }
-          if (x < U) {  // met the tile's chain: everything from x on is right
-            s_clear_end = x;
-            s_cur = s_exit[tt - t0];
-          } else {
-            s_clear_end = U;
-            s_cur = x;
-          }
-          s_nl = nl;
-        }
+    if (threadIdx.x == 0) {
+      uint32_t c = s_cur;
+      for (uint32_t r = 0; r < tn; ++r) {
+        const uint32_t L = (t0 + r) * kStitchTile;
+        entry[t0 + r] = c;
+        if (c < n) c = s_rows[r * W + (c - L)];
       }
-      __syncthreads();
-      t = s_t;
-      if (t >= tend) break;
-      const uint32_t L = t * kStitchTile;
-      for (uint32_t i = L + threadIdx.x; i < s_clear_end; i += blockDim.x) flags[i] = 0;
-      __syncthreads();
-      for (uint32_t k = threadIdx.x; k < s_nl; k += blockDim.x) flags[s_list[k]] = 1;
-      ++t;
-      __syncthreads();
+      s_cur = c;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_stitch_mark(const uint32_t* __restrict__ next,
+                                                     const uint32_t* __restrict__ n_dev,
+                                                     const uint32_t* __restrict__ gap,
+                                                     const uint32_t* __restrict__ entry,
+                                                     uint8_t* __restrict__ flags) {
+  __shared__ uint32_t s_next[kStitchTile];
+  __shared__ uint8_t s_flag[kStitchTile];
+  if (*gap > kWinMax) return;
+  const uint32_t n = *n_dev;
+  const uint32_t n_tiles = (n + kStitchTile - 1) / kStitchTile;
+  for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const uint32_t L = t * kStitchTile, U = min(n, L + kStitchTile);
+    for (uint32_t i = threadIdx.x; i < U - L; i += blockDim.x) {
+      s_next[i] = next[L + i];
+      s_flag[i] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t x = entry[t];
+      while (x < U) {
+        s_flag[x - L] = 1;
+        x = s_next[x - L];
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < U - L; i += blockDim.x) flags[L + i] = s_flag[i];
+    __syncthreads();
+  }
+}
+
+// Walk path: one warp per job; lane 0 follows the chain over global next[].
+__global__ void k_stitch_walk(const uint32_t* __restrict__ next, const uint32_t* __restrict__ gap,
+                              const JobDev* __restrict__ jobs, uint32_t n_jobs, bool blocks_level,
+                              uint8_t* __restrict__ flags) {
+  if (*gap <= kWinMax) return;
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t j = gtid() / 32; j < n_jobs; j += warps) {
+    const uint32_t b = blocks_level ? jobs[j].blk_begin : jobs[j].surv_begin;
+    const uint32_t e = blocks_level ? jobs[j].blk_end : jobs[j].surv_end;
+    for (uint32_t i = b + lane_id(); i < e; i += 32) flags[i] = 0;
+    __syncwarp();
+    if (lane_id() == 0) {
+      uint32_t x = b;
+      while (x < e) {
+        flags[x] = 1;
+        x = next[x];
+      }
     }
   }
 }
@@ -365,7 +379,33 @@ __global__ void k_zero_words(uint32_t* __restrict__ w, const Counts* __restrict_
 }
 
 // ---- encode -------------------------------------------------------------------------------
-constexpr int kEncThreads = 128;
+// One CTA per data block. The block image is assembled in shared memory at the same
+// 16-byte phase as its destination, so the final store is whole aligned 16-byte words
+// (bytes only at the two ragged ends). Values are gathered from the input tables with
+// aligned 4-byte loads joined by funnel shifts; the CRC trailer is computed by the whole
+// CTA from shared memory. A block larger than the shared buffer is written straight to
+// global memory instead (same bytes).
+constexpr int kEncThreads = 256;
+constexpr uint32_t kEncBuf = 64 * 1024;
+
+// Copy n bytes from global src (any alignment) to dst (any alignment), one warp.
+__device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, uint32_t n, uint32_t lane) {
+  uint32_t head = (4u - (uint32_t(reinterpret_cast<uintptr_t>(dst)) & 3u)) & 3u;
+  if (head > n) head = n;
+  if (lane < head) dst[lane] = src[lane];
+  const uint32_t nw = (n - head) >> 2;
+  const uint8_t* s = src + head;
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst + head);
+  const uint32_t sh = (uint32_t(reinterpret_cast<uintptr_t>(s)) & 3u) * 8u;
+  const uint32_t* sa = reinterpret_cast<const uint32_t*>(reinterpret_cast<uintptr_t>(s) & ~uintptr_t(3));
+  if (sh == 0) {
+    for (uint32_t k = lane; k < nw; k += 32) d[k] = __ldg(sa + k);
+  } else {
+    for (uint32_t k = lane; k < nw; k += 32) d[k] = __funnelshift_r(__ldg(sa + k), __ldg(sa + k + 1), sh);
+  }
+  const uint32_t done = head + 4 * nw;
+  if (lane < n - done) dst[done + lane] = src[done + lane];
+}
 
 __global__ void __launch_bounds__(kEncThreads) k_encode(const uint32_t* __restrict__ start,
                                                         const Counts* __restrict__ cnt,
@@ -378,12 +418,15 @@ __global__ void __launch_bounds__(kEncThreads) k_encode(const uint32_t* __restri
                                                         const uint32_t* __restrict__ dr, Recs recs,
                                                         const uint8_t* __restrict__ arena, Fmt fmt,
                                                         uint8_t* __restrict__ out, uint64_t out_cap, CrcTabs tabs) {
+  extern __shared__ uint4 s_dyn[];
   __shared__ uint32_t sT[1024];
-  __shared__ uint64_t s_off[kEncThreads];
-  __shared__ uint64_t s_wsum[kEncThreads / 32];
+  __shared__ uint32_t s_off[kEncThreads];
+  __shared__ uint32_t s_wsum[kEncThreads / 32];
+  __shared__ uint32_t s_scratch[kEncThreads / 32];
   load_slice_table(sT, tabs);
   __syncthreads();
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  constexpr uint32_t nwarps = kEncThreads / 32;
   const uint32_t R = fmt.R;
   const uint32_t nb = cnt->nb;
   for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
@@ -392,66 +435,83 @@ __global__ void __launch_bounds__(kEncThreads) k_encode(const uint32_t* __restri
     if (F.off + F.size > out_cap) continue;
     uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
     const uint64_t contents = bsz[b];
-    const uint64_t nr = (m + R - 1) / R;
-    const uint64_t rbase = contents - 4 * nr - 4;
-    uint64_t base = 0;
+    const uint32_t nr = (m + R - 1) / R;
+    const uint64_t rbase = contents - 4ull * nr - 4;
+    const uint32_t phase = uint32_t(reinterpret_cast<uintptr_t>(dst) & 15u);
+    const bool in_smem = contents + kTrailer + 16 <= kEncBuf;
+    uint8_t* img = in_smem ? reinterpret_cast<uint8_t*>(s_dyn) + phase : dst;
+    uint32_t base = 0;
     for (uint32_t r0 = 0; r0 < m; r0 += kEncThreads) {
       const uint32_t k = r0 + tid;
-      uint64_t sz = 0;
+      uint32_t sz = 0;
       if (k < m) sz = sd[s + k] + ((k % R) == 0 ? dr[s + k] : 0u);
-      // CTA exclusive scan of sz
-      uint64_t x = sz;
+      uint32_t x = sz;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        const uint64_t o = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, x, d);
         if (lane >= uint32_t(d)) x += o;
       }
       if (lane == 31) s_wsum[warp] = x;
       __syncthreads();
-      uint64_t before = 0, total = 0;
-      for (uint32_t w = 0; w < kEncThreads / 32; ++w) {
-        if (w < warp) before += s_wsum[w];
-        total += s_wsum[w];
+      uint32_t before = 0, total = 0;
+#pragma unroll
+      for (uint32_t w = 0; w < nwarps; ++w) {
+        const uint32_t v = s_wsum[w];
+        before += w < warp ? v : 0u;
+        total += v;
       }
       s_off[tid] = base + before + x - sz;
       __syncthreads();
-      const uint32_t cnt = min(uint32_t(kEncThreads), m - r0);
-      for (uint32_t kk = warp; kk < cnt; kk += kEncThreads / 32) {
+      const uint32_t cnt_r = min(uint32_t(kEncThreads), m - r0);
+      for (uint32_t kk = warp; kk < cnt_r; kk += nwarps) {
         const uint32_t kb = r0 + kk;
         const uint32_t xi = surv[s + kb];
         const uint32_t klen = recs.klen[xi], vlen = recs.vlen[xi];
         const bool restart = (kb % R) == 0;
         const uint32_t shared = restart ? 0u : lcp[s + kb];
         const uint32_t nonshared = klen - shared;
-        const uint64_t eoff = s_off[kk];
-        uint8_t* ep = dst + eoff;
-        uint32_t h = 0;
+        const uint32_t eoff = s_off[kk];
+        uint8_t* ep = img + eoff;
+        const uint32_t h = varint_size(shared) + varint_size(nonshared) + varint_size(vlen);
         if (lane == 0) {
-          h = put_varint(ep, shared);
-          h += put_varint(ep + h, nonshared);
-          h += put_varint(ep + h, vlen);
-          if (restart) st_u32(dst + rbase + 4ull * (kb / R), uint32_t(eoff));
+          uint32_t q = put_varint(ep, shared);
+          q += put_varint(ep + q, nonshared);
+          put_varint(ep + q, vlen);
+          if (restart) st_u32(img + rbase + 4ull * (kb / R), eoff);
         }
-        h = __shfl_sync(0xFFFFFFFFu, h, 0);
         const uint8_t* ks = arena + recs.koff[xi] + shared;
         for (uint32_t t = lane; t < nonshared; t += 32) ep[h + t] = ks[t];
-        const uint8_t* vs = reinterpret_cast<const uint8_t*>(recs.vptr[xi]);
-        uint8_t* vd = ep + h + nonshared;
-        for (uint32_t t = lane; t < vlen; t += 32) vd[t] = vs[t];
+        warp_copy(ep + h + nonshared, reinterpret_cast<const uint8_t*>(recs.vptr[xi]), vlen, lane);
       }
       base += total;
       __syncthreads();
     }
     if (tid == 0) {
-      st_u32(dst + contents - 4, uint32_t(nr));
-      dst[contents] = 0;
+      st_u32(img + contents - 4, nr);
+      img[contents] = 0;
     }
     __syncthreads();
-    if (warp == 0) {
-      const uint32_t crc = warp_crc32c(dst, contents + 1, sT, tabs);
-      if (lane == 0) st_u32(dst + contents + 1, crc_mask(crc));
-    }
+    const uint32_t crc = cta_crc32c(img, contents + 1, sT, tabs, s_scratch);
+    if (tid == 0) st_u32(img + contents + 1, crc_mask(crc));
     __syncthreads();
+    if (in_smem) {
+      // aligned 16-byte words of [dst, dst + len) at the same phase in shared memory
+      const uint64_t len = contents + kTrailer;
+      const uint64_t nq = (phase + len + 15) >> 4;
+      uint4* gq = reinterpret_cast<uint4*>(dst - phase);
+      for (uint64_t q = tid; q < nq; q += kEncThreads) {
+        const uint64_t lo = q * 16, hi = lo + 16;
+        if (lo >= phase && hi <= phase + len) {
+          gq[q] = s_dyn[q];
+        } else {
+          const uint8_t* sb = reinterpret_cast<const uint8_t*>(s_dyn);
+          uint8_t* gb = dst - phase;
+          for (uint64_t i = lo; i < hi; ++i)
+            if (i >= phase && i < phase + len) gb[i] = sb[i];
+        }
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -543,28 +603,30 @@ __global__ void k_index_write(const uint32_t* __restrict__ start, const Counts* 
   }
 }
 
-// One warp per table: filter block, metaindex block, index block trailer, footer.
-__global__ void __launch_bounds__(32) k_file_finish(const FileDesc* __restrict__ files,
-                                                    const Counts* __restrict__ cnt,
-                                                    const uint32_t* __restrict__ bitmap,
-                                                    const uint32_t* __restrict__ surv, Recs recs, Fmt fmt,
-                                                    uint8_t* __restrict__ out, uint64_t out_cap, CrcTabs tabs,
-                                                    FileMeta* __restrict__ meta) {
+// One CTA per table: filter block, metaindex block, index block trailer, footer.
+constexpr int kFinThreads = 256;
+
+__global__ void __launch_bounds__(kFinThreads) k_file_finish(const FileDesc* __restrict__ files,
+                                                             const Counts* __restrict__ cnt,
+                                                             const uint32_t* __restrict__ bitmap,
+                                                             const uint32_t* __restrict__ surv, Recs recs, Fmt fmt,
+                                                             uint8_t* __restrict__ out, uint64_t out_cap,
+                                                             CrcTabs tabs, FileMeta* __restrict__ meta) {
   __shared__ uint32_t sT[1024];
+  __shared__ uint32_t s_scratch[kFinThreads / 32];
   load_slice_table(sT, tabs);
   __syncthreads();
-  const uint32_t lane = lane_id();
+  const uint32_t tid = threadIdx.x;
   const uint32_t nf = cnt->nf;
   for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
     const FileDesc F = files[f];
     if (F.off + F.size > out_cap) continue;
     uint8_t* base = out + F.off;
-    // filter: bitmap bytes, k, type
     uint8_t* fp = base + F.data_size;
     const uint64_t bytes = F.filter_size - 1;
     const uint32_t* bm = bitmap + F.bm_word;
-    for (uint64_t i = lane; i < bytes; i += 32) fp[i] = uint8_t(bm[i >> 2] >> (8 * (i & 3)));
-    if (lane == 0) {
+    for (uint64_t i = tid; i < bytes; i += kFinThreads) fp[i] = uint8_t(bm[i >> 2] >> (8 * (i & 3)));
+    if (tid == 0) {
       fp[bytes] = uint8_t(fmt.k);
       fp[bytes + 1] = 0;
       // metaindex: one entry "filter.luda.bloom" -> filter handle, restart interval 1
@@ -587,11 +649,11 @@ __global__ void __launch_bounds__(32) k_file_finish(const FileDesc* __restrict__
       st_u32(ip + F.index_size - 4, F.blk_end - F.blk_begin);
       ip[F.index_size] = 0;
     }
-    __syncwarp();
-    const uint32_t cf = warp_crc32c(fp, F.filter_size + 1, sT, tabs);
-    const uint32_t cm = warp_crc32c(base + F.meta_off, F.meta_size + 1, sT, tabs);
-    const uint32_t ci = warp_crc32c(base + F.index_off, F.index_size + 1, sT, tabs);
-    if (lane == 0) {
+    __syncthreads();
+    const uint32_t cf = cta_crc32c(fp, F.filter_size + 1, sT, tabs, s_scratch);
+    const uint32_t cm = cta_crc32c(base + F.meta_off, F.meta_size + 1, sT, tabs, s_scratch);
+    const uint32_t ci = cta_crc32c(base + F.index_off, F.index_size + 1, sT, tabs, s_scratch);
+    if (tid == 0) {
       st_u32(fp + F.filter_size + 1, crc_mask(cf));
       st_u32(base + F.meta_off + F.meta_size + 1, crc_mask(cm));
       st_u32(base + F.index_off + F.index_size + 1, crc_mask(ci));
@@ -606,11 +668,13 @@ __global__ void __launch_bounds__(32) k_file_finish(const FileDesc* __restrict__
       mt.off = F.off;
       mt.size = F.size;
       mt.n_entries = F.ent_end - F.ent_begin;
+      mt.data_size = F.data_size;
       mt.small_len = recs.klen[surv[F.ent_begin]];
       mt.large_len = recs.klen[surv[F.ent_end - 1]];
       mt.job = F.job;
       meta[f] = mt;
     }
+    __syncthreads();
   }
 }
 
@@ -694,65 +758,69 @@ __global__ void k_build_check(Recs recs, const uint8_t* __restrict__ arena, uint
 void launch_sizes(const uint32_t* surv, const Counts* cnt, uint32_t cap, const JobDev* jobs, uint32_t n_jobs,
                   Recs recs, const uint8_t* arena, uint32_t* lcp, uint32_t* sd, uint32_t* dr, cudaStream_t st) {
   if (!cap) return;
-  k_sizes<<<grid_for(cap, 256), 256, 0, st>>>(surv, cnt, jobs, n_jobs, recs, arena, lcp, sd, dr);
+  k_sizes<<<grid_for(cap, 256), 256, 0, st>>>(surv, cnt, jobs, n_jobs, recs, arena, lcp, sd, dr); count_launches(1);
 }
 
 void launch_block_next(const uint64_t* P, const uint32_t* dr, const Counts* cnt, uint32_t cap, const JobDev* jobs,
                        uint32_t n_jobs, Fmt fmt, uint32_t* next, cudaStream_t st) {
   if (!cap) return;
-  k_block_next<<<grid_for(cap, 256), 256, 0, st>>>(P, dr, cnt, jobs, n_jobs, fmt, next);
+  k_block_next<<<grid_for(cap, 256), 256, 0, st>>>(P, dr, cnt, jobs, n_jobs, fmt, next); count_launches(1);
 }
 
 uint64_t stitch_temp_bytes(uint32_t cap) {
   const uint64_t tiles = (uint64_t(cap) + kStitchTile - 1) / kStitchTile;
-  return 2 * tiles * sizeof(uint32_t) + 256;
+  return (tiles * kWinMax + tiles + 64) * sizeof(uint32_t) + 256;
 }
 
-void launch_stitch(const uint32_t* next, const uint32_t* n_dev, uint32_t cap, uint8_t* flags, void* temp,
-                   cudaStream_t st) {
+void launch_stitch(const uint32_t* next, const uint32_t* n_dev, uint32_t cap, uint32_t* gap, const JobDev* jobs,
+                   uint32_t n_jobs, bool blocks_level, uint8_t* flags, void* temp, cudaStream_t st) {
   if (!cap) return;
   const uint32_t tiles = (cap + kStitchTile - 1) / kStitchTile;
-  uint32_t* entry = static_cast<uint32_t*>(temp);
-  uint32_t* exitp = entry + tiles;
-  k_stitch_tiles<<<grid_for(tiles, 1, kSms * 8), 128, 0, st>>>(next, n_dev, flags, entry, exitp);
-  k_stitch_fix<<<1, 256, 0, st>>>(next, n_dev, flags, entry, exitp);
+  uint32_t* exitw = static_cast<uint32_t*>(temp);
+  uint32_t* entry = exitw + uint64_t(tiles) * kWinMax;
+  k_max_gap<<<grid_for(cap, 256), 256, 0, st>>>(next, n_dev, gap); count_launches(1);
+  k_stitch_win<<<grid_for(tiles, 1, kSms * 8), 256, 0, st>>>(next, n_dev, gap, exitw); count_launches(1);
+  k_stitch_combine<<<1, 256, 0, st>>>(exitw, n_dev, gap, entry); count_launches(1);
+  k_stitch_mark<<<grid_for(tiles, 1, kSms * 8), 128, 0, st>>>(next, n_dev, gap, entry, flags); count_launches(1);
+  k_stitch_walk<<<grid_for(n_jobs, 8, kSms * 8), 256, 0, st>>>(next, gap, jobs, n_jobs, blocks_level, flags);
+  count_launches(1);
 }
 
 void launch_compact_flags(const uint8_t* flags, const uint32_t* pos, const uint32_t* n_dev, uint32_t cap,
                           uint32_t* starts, uint32_t* total_out, cudaStream_t st) {
-  k_compact_flags<<<grid_for(cap, 256), 256, 0, st>>>(flags, pos, n_dev, starts, total_out);
+  k_compact_flags<<<grid_for(cap, 256), 256, 0, st>>>(flags, pos, n_dev, starts, total_out); count_launches(1);
 }
 
 void launch_job_blocks(JobDev* jobs, uint32_t n_jobs, const uint32_t* bpos, cudaStream_t st) {
-  k_job_blocks<<<grid_for(n_jobs, 128), 128, 0, st>>>(jobs, n_jobs, bpos);
+  k_job_blocks<<<grid_for(n_jobs, 128), 128, 0, st>>>(jobs, n_jobs, bpos); count_launches(1);
 }
 
 void launch_block_sizes(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* P,
                         const uint32_t* dr, Fmt fmt, uint64_t* bsz, uint64_t* disk, cudaStream_t st) {
   if (!cap) return;
-  k_block_sizes<<<grid_for(cap, 256), 256, 0, st>>>(blk_start, cnt, P, dr, fmt, bsz, disk);
+  k_block_sizes<<<grid_for(cap, 256), 256, 0, st>>>(blk_start, cnt, P, dr, fmt, bsz, disk); count_launches(1);
 }
 
 void launch_file_next(const uint64_t* C, const Counts* cnt, uint32_t cap, const JobDev* jobs, uint32_t n_jobs,
                       Fmt fmt, uint32_t* next, cudaStream_t st) {
   if (!cap) return;
-  k_file_next<<<grid_for(cap, 256), 256, 0, st>>>(C, cnt, jobs, n_jobs, fmt, next);
+  k_file_next<<<grid_for(cap, 256), 256, 0, st>>>(C, cnt, jobs, n_jobs, fmt, next); count_launches(1);
 }
 
 void launch_job_files(JobDev* jobs, uint32_t n_jobs, const uint32_t* fpos, cudaStream_t st) {
-  k_job_files<<<grid_for(n_jobs, 128), 128, 0, st>>>(jobs, n_jobs, fpos);
+  k_job_files<<<grid_for(n_jobs, 128), 128, 0, st>>>(jobs, n_jobs, fpos); count_launches(1);
 }
 
 void launch_block_file(const uint32_t* fpos, const Counts* cnt, uint32_t cap, uint32_t* blk_file, cudaStream_t st) {
   if (!cap) return;
-  k_block_file<<<grid_for(cap, 256), 256, 0, st>>>(fpos, cnt, blk_file);
+  k_block_file<<<grid_for(cap, 256), 256, 0, st>>>(fpos, cnt, blk_file); count_launches(1);
 }
 
 void launch_index_sizes(const uint32_t* blk_start, const uint64_t* bsz, const uint64_t* C, const uint32_t* blk_file,
                         const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* surv, Recs recs,
                         uint32_t* ie, cudaStream_t st) {
   if (!cap) return;
-  k_index_sizes<<<grid_for(cap, 256), 256, 0, st>>>(blk_start, bsz, C, blk_file, file_start, cnt, surv, recs, ie);
+  k_index_sizes<<<grid_for(cap, 256), 256, 0, st>>>(blk_start, bsz, C, blk_file, file_start, cnt, surv, recs, ie); count_launches(1);
 }
 
 void launch_file_layout(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_start,
@@ -760,19 +828,19 @@ void launch_file_layout(const uint32_t* file_start, const Counts* cnt, uint32_t 
                         FileDesc* files, uint64_t* fsize, uint64_t* bmwords, cudaStream_t st) {
   if (!cap) return;
   k_file_layout<<<grid_for(cap, 128), 128, 0, st>>>(file_start, cnt, blk_start, C, IX, fmt, jobs, n_jobs, files,
-                                                    fsize, bmwords);
+                                                    fsize, bmwords); count_launches(1);
 }
 
 void launch_file_offsets(FileDesc* files, Counts* cnt, uint32_t cap, const uint64_t* foff, const uint64_t* bmoff,
                          JobDev* jobs, uint32_t n_jobs, uint64_t out_cap, uint64_t bm_cap, DErr* errs,
                          cudaStream_t st) {
   k_file_offsets<<<grid_for(cap > n_jobs ? cap : n_jobs, 128), 128, 0, st>>>(files, cnt, foff, bmoff, jobs, n_jobs,
-                                                                             out_cap, bm_cap, errs);
+                                                                             out_cap, bm_cap, errs); count_launches(1);
 }
 
 void launch_zero_bitmap(uint32_t* bitmap, const Counts* cnt, uint64_t cap_words, cudaStream_t st) {
   if (!cap_words) return;
-  k_zero_words<<<grid_for(cap_words, 256), 256, 0, st>>>(bitmap, cnt, cap_words);
+  k_zero_words<<<grid_for(cap_words, 256), 256, 0, st>>>(bitmap, cnt, cap_words); count_launches(1);
 }
 
 void launch_encode(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
@@ -780,8 +848,11 @@ void launch_encode(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, c
                    const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
                    Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs, cudaStream_t st) {
   if (!cap) return;
-  k_encode<<<grid_for(cap, 1, kSms * 16), kEncThreads, 0, st>>>(blk_start, cnt, blk_file, files, C, bsz, surv, lcp,
-                                                                sd, dr, recs, arena, fmt, out, out_cap, tabs);
+  cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kEncBuf));
+  k_encode<<<grid_for(cap, 1, kSms * 3), kEncThreads, kEncBuf, st>>>(blk_start, cnt, blk_file, files, C, bsz, surv,
+                                                                     lcp, sd, dr, recs, arena, fmt, out, out_cap,
+                                                                     tabs);
+  count_launches(1);
 }
 
 void launch_bloom(const uint32_t* surv, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
@@ -789,7 +860,7 @@ void launch_bloom(const uint32_t* surv, const Counts* cnt, uint32_t cap, const u
                   uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st) {
   if (!cap) return;
   k_bloom<<<grid_for(cap, 256), 256, 0, st>>>(surv, cnt, blk_file, blk_start, files, recs, arena, fmt, bitmap,
-                                              out_cap, bm_cap);
+                                              out_cap, bm_cap); count_launches(1);
 }
 
 void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* bsz,
@@ -798,37 +869,37 @@ void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t c
                         cudaStream_t st) {
   if (!cap) return;
   k_index_write<<<grid_for(cap, 128), 128, 0, st>>>(blk_start, cnt, bsz, C, IX, blk_file, files, surv, recs, arena,
-                                                    out, out_cap);
+                                                    out, out_cap); count_launches(1);
 }
 
 void launch_file_finish(const FileDesc* files, const Counts* cnt, uint32_t cap, const uint32_t* bitmap,
                         const uint32_t* surv, Recs recs, Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs,
                         FileMeta* meta, cudaStream_t st) {
   if (!cap) return;
-  k_file_finish<<<grid_for(cap, 1, kSms * 16), 32, 0, st>>>(files, cnt, bitmap, surv, recs, fmt, out, out_cap, tabs,
-                                                            meta);
+  k_file_finish<<<grid_for(cap, 1, kSms * 4), kFinThreads, 0, st>>>(files, cnt, bitmap, surv, recs, fmt, out,
+                                                                    out_cap, tabs, meta); count_launches(1);
 }
 
 void launch_key_lens(const FileMeta* meta, const Counts* cnt, uint32_t cap, uint64_t* lens, cudaStream_t st) {
   if (!cap) return;
-  k_key_lens<<<grid_for(cap, 128), 128, 0, st>>>(meta, cnt, lens);
+  k_key_lens<<<grid_for(cap, 128), 128, 0, st>>>(meta, cnt, lens); count_launches(1);
 }
 
 void launch_key_gather(FileMeta* meta, Counts* cnt, uint32_t cap, const uint64_t* koff, const FileDesc* files,
                        const uint32_t* surv, Recs recs, const uint8_t* arena, uint8_t* keybuf, cudaStream_t st) {
-  k_key_gather<<<grid_for(cap ? cap : 1, 128), 128, 0, st>>>(meta, cnt, koff, files, surv, recs, arena, keybuf);
+  k_key_gather<<<grid_for(cap ? cap : 1, 128), 128, 0, st>>>(meta, cnt, koff, files, surv, recs, arena, keybuf); count_launches(1);
 }
 
 void launch_build_records(const uint8_t* ukeys, const uint64_t* ukoff, const uint64_t* seqs, const uint8_t* types,
                           const uint8_t* vals, const uint64_t* voff, uint32_t n, Recs recs, uint8_t* arena,
                           uint32_t* surv, DErr* err, cudaStream_t st) {
   if (!n) return;
-  k_build_records<<<grid_for(n, 256), 256, 0, st>>>(ukeys, ukoff, seqs, types, vals, voff, n, recs, arena, surv, err);
+  k_build_records<<<grid_for(n, 256), 256, 0, st>>>(ukeys, ukoff, seqs, types, vals, voff, n, recs, arena, surv, err); count_launches(1);
 }
 
 void launch_build_check(Recs recs, const uint8_t* arena, uint32_t n, DErr* err, cudaStream_t st) {
   if (n < 2) return;
-  k_build_check<<<grid_for(n, 256), 256, 0, st>>>(recs, arena, n, err);
+  k_build_check<<<grid_for(n, 256), 256, 0, st>>>(recs, arena, n, err); count_launches(1);
 }
 
 }  // namespace luda

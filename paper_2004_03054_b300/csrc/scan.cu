@@ -111,16 +111,16 @@ cudaError_t exclusive_scan(const In* in, Out* out, uint64_t cap, const uint32_t*
   if (cap == 0) return cudaMemsetAsync(out, 0, sizeof(Out), st);
   const uint64_t t = tiles_of(cap);
   if (t == 1) {
-    k_tile_scan<In, Out><<<1, kScanThreads, 0, st>>>(in, cap, count, out, nullptr);
+    k_tile_scan<In, Out><<<1, kScanThreads, 0, st>>>(in, cap, count, out, nullptr); count_launches(1);
     return cudaGetLastError();
   }
   uint64_t* sums = static_cast<uint64_t*>(temp);
   uint64_t* offs = sums + t;
   void* rest = offs + t + 1;
-  k_tile_reduce<In><<<unsigned(t), kScanThreads, 0, st>>>(in, cap, count, sums);
+  k_tile_reduce<In><<<unsigned(t), kScanThreads, 0, st>>>(in, cap, count, sums); count_launches(1);
   cudaError_t e = exclusive_scan<uint64_t, uint64_t>(sums, offs, t, nullptr, rest, st);
   if (e != cudaSuccess) return e;
-  k_tile_scan<In, Out><<<unsigned(t), kScanThreads, 0, st>>>(in, cap, count, out, offs);
+  k_tile_scan<In, Out><<<unsigned(t), kScanThreads, 0, st>>>(in, cap, count, out, offs); count_launches(1);
   return cudaGetLastError();
 }
 

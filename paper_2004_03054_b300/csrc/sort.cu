@@ -205,12 +205,12 @@ __global__ void k_job_surv(JobDev* jobs, uint32_t n_jobs, const uint32_t* __rest
 void launch_check_order(Recs recs, const uint8_t* arena, uint32_t n_rec, const DInput* in, DErr* errs,
                         cudaStream_t st) {
   if (n_rec < 2) return;
-  k_check_order<<<grid_for(n_rec, 256), 256, 0, st>>>(recs, arena, n_rec, in, errs);
+  k_check_order<<<grid_for(n_rec, 256), 256, 0, st>>>(recs, arena, n_rec, in, errs); count_launches(1);
 }
 
 void launch_sort_init(uint32_t* ord, uint64_t* opfx, const uint64_t* pfx, uint32_t n, cudaStream_t st) {
   if (!n) return;
-  k_sort_init<<<grid_for(n, 256), 256, 0, st>>>(ord, opfx, pfx, n);
+  k_sort_init<<<grid_for(n, 256), 256, 0, st>>>(ord, opfx, pfx, n); count_launches(1);
 }
 
 void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* corank_buf,
@@ -218,27 +218,27 @@ void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tile
                        Recs recs, const uint8_t* arena, cudaStream_t st) {
   if (!n_tiles) return;
   k_merge_partition<<<grid_for(n_tiles, 128), 128, 0, st>>>(spans, n_spans, n_tiles, corank_buf, src_ord, src_pfx,
-                                                            recs, arena);
+                                                            recs, arena); count_launches(1);
   k_merge_tiles<<<grid_for(n_tiles, 1, kSms * 8), kMergeThreads, 0, st>>>(spans, n_spans, n_tiles, corank_buf,
                                                                           src_ord, src_pfx, dst_ord, dst_pfx, recs,
-                                                                          arena);
+                                                                          arena); count_launches(1);
 }
 
 void launch_gc_flags(const uint32_t* ord, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, Recs recs,
                      const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st) {
   if (!n_rec) return;
-  k_gc_flags<<<grid_for(n_rec, 256), 256, 0, st>>>(ord, n_rec, jobs, n_jobs, recs, arena, keep, errs);
+  k_gc_flags<<<grid_for(n_rec, 256), 256, 0, st>>>(ord, n_rec, jobs, n_jobs, recs, arena, keep, errs); count_launches(1);
 }
 
 void launch_gc_compact(const uint32_t* ord, const uint32_t* keep, const uint32_t* pos, uint32_t n_rec,
                        uint32_t* surv, cudaStream_t st) {
   if (!n_rec) return;
-  k_gc_compact<<<grid_for(n_rec, 256), 256, 0, st>>>(ord, keep, pos, n_rec, surv);
+  k_gc_compact<<<grid_for(n_rec, 256), 256, 0, st>>>(ord, keep, pos, n_rec, surv); count_launches(1);
 }
 
 void launch_job_surv(JobDev* jobs, uint32_t n_jobs, const uint32_t* pos, uint32_t n_rec, Counts* cnt,
                      cudaStream_t st) {
-  k_job_surv<<<grid_for(n_jobs, 128), 128, 0, st>>>(jobs, n_jobs, pos, n_rec, cnt);
+  k_job_surv<<<grid_for(n_jobs, 128), 128, 0, st>>>(jobs, n_jobs, pos, n_rec, cnt); count_launches(1);
 }
 
 }  // namespace luda

@@ -49,7 +49,7 @@ class Outputs(C.Structure):
     _fields_ = [("tables", C.POINTER(Table)), ("n_tables", C.c_uint32), ("status", C.c_int32),
                 ("n_in_entries", C.c_uint64), ("n_dropped", C.c_uint64), ("ms_h2d", C.c_double),
                 ("ms_device", C.c_double), ("ms_d2h", C.c_double), ("stage_ms", C.c_double * 8),
-                ("_priv", C.c_void_p)]
+                ("stage_bytes", C.c_uint64 * 8), ("_priv", C.c_void_p)]
 
 
 class Job(C.Structure):
@@ -90,6 +90,7 @@ def lib():
         L.luda_strerror.argtypes = [C.c_int]
         L.luda_last_error_detail.restype = C.c_char_p
         L.luda_version.restype = C.c_char_p
+        L.luda_launch_count.restype = C.c_uint64
         for name in ("luda_plan_create", "luda_plan_run", "luda_plan_outputs", "luda_plan_destroy"):
             if hasattr(L, name):
                 getattr(L, name).restype = st
@@ -119,6 +120,11 @@ def job_options(job, **kw) -> Options:
                    job.bottommost, **kw)
 
 
+def launch_count() -> int:
+    """Kernels libluda has launched in this process."""
+    return int(lib().luda_launch_count())
+
+
 def strerror(s: int) -> str:
     return lib().luda_strerror(s).decode()
 
@@ -144,6 +150,8 @@ class Result:
     ms_h2d: float = 0.0
     ms_device: float = 0.0
     ms_d2h: float = 0.0
+    stage_ms: list = field(default_factory=list)
+    stage_bytes: list = field(default_factory=list)
     detail: str = ""
 
 
@@ -167,6 +175,7 @@ def _take(rc: int, out: Outputs, device: bool) -> Result:
     res = Result(int(out.status) if rc == OK else rc, detail=last_error_detail() if rc or out.status else "")
     res.n_in_entries, res.n_dropped = int(out.n_in_entries), int(out.n_dropped)
     res.ms_h2d, res.ms_device, res.ms_d2h = out.ms_h2d, out.ms_device, out.ms_d2h
+    res.stage_ms, res.stage_bytes = list(out.stage_ms), [int(x) for x in out.stage_bytes]
     if rc == OK and out.status == OK:
         for i in range(out.n_tables):
             t = out.tables[i]
