@@ -219,7 +219,7 @@ luda_status err_status(const DErr& e, uint32_t job, uint32_t n_jobs) {
 // ---- the pack stages, shared by compaction and build --------------------------------------
 struct PackBufs {
   uint32_t *surv, *lcp, *sd, *dr, *next, *bpos, *blk_start, *fnext, *fpos, *file_start, *blk_file, *ie;
-  uint8_t *sflags, *fflags;
+  uint8_t *sflags, *fflags, *enc_done;
   uint64_t *P, *bsz, *disk, *C, *IX, *fsize, *foff, *bmw, *bmoff, *klens, *koff;
   FileDesc* files;
   FileMeta* meta;
@@ -243,6 +243,7 @@ void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t
   b.ie = L.take<uint32_t>(cap + 1);
   b.sflags = L.take<uint8_t>(cap + 1);
   b.fflags = L.take<uint8_t>(cap + 1);
+  b.enc_done = L.take<uint8_t>(cap + 1);
   b.P = L.take<uint64_t>(cap + 1);
   b.bsz = L.take<uint64_t>(cap + 1);
   b.disk = L.take<uint64_t>(cap + 1);
@@ -293,7 +294,7 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   launch_zero_bitmap(b.bitmap, cnt, bm_cap, st);
   trace_mark(tr, 7, st);
   launch_encode(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena, fmt,
-                out, out_cap, tabs, st);
+                out, out_cap, b.enc_done, tabs, st);
   trace_mark(tr, 8, st);
   launch_bloom(b.surv, cnt, cap, b.blk_file, b.blk_start, b.files, recs, arena, fmt, b.bitmap, out_cap, bm_cap, st);
   launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, out, out_cap,
@@ -537,9 +538,11 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
 
   // ---- sizing: block scan ------------------------------------------------------------------
   Layout LB;
+  uint16_t* d_hdr;
   auto layoutB = [&](Layout& L, BlockDesc*& blocks, uint32_t*& nrec, uint64_t*& kbytes, uint32_t*& rec_first,
                      uint64_t*& key_first, uint32_t*& in_rec, uint64_t*& in_key, void*& tmp) {
     blocks = L.take<BlockDesc>(NB + 1);
+    d_hdr = L.take<uint16_t>(uint64_t(NB) * kHdrMax + 1);
     nrec = L.take<uint32_t>(NB + 1);
     kbytes = L.take<uint64_t>(NB + 1);
     rec_first = L.take<uint32_t>(NB + 1);
@@ -562,7 +565,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
 
   launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
   tr.mark(1, st);
-  launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, tabs, st);
+  launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, tabs, st);
   tr.mark(2, st);
   launch_zero_failed(d_blocks, NB, d_errs, d_nrec, d_kbytes, st);
   CK((exclusive_scan<uint32_t, uint32_t>(d_nrec, d_rec_first, NB, nullptr, d_tmpB, st)));
@@ -641,7 +644,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   PackBufs pb;
   auto layoutC = [&](Layout& L) {
     recs = recs_layout(L, n_rec);
-    d_arena = L.take<uint8_t>(K + 16);
+    d_arena = L.take<uint8_t>(K + 64);
     d_ord0 = L.take<uint32_t>(n_rec + 1);
     d_ord1 = L.take<uint32_t>(n_rec + 1);
     d_pfx0 = L.take<uint64_t>(n_rec + 1);
@@ -677,7 +680,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     CK(cudaMemcpyAsync(d_spans, spans.data(), sizeof(MergeSpan) * spans.size(), cudaMemcpyHostToDevice, st));
 
   tr.mark(4, st);
-  launch_decode(d_blocks, NB, d_in, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
+  launch_decode(d_blocks, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
   tr.mark(5, st);
   launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
   launch_sort_init(d_ord0, d_pfx0, recs.pfx, n_rec, st);
@@ -818,7 +821,7 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
   PackBufs pb;
   auto lay = [&](Layout& l) {
     recs = recs_layout(l, n);
-    arena = l.take<uint8_t>(K + 16);
+    arena = l.take<uint8_t>(K + 64);
     d_err = l.take<DErr>(1);
     d_job = l.take<JobDev>(1);
     d_cnt = l.take<Counts>(1);

@@ -96,6 +96,18 @@ bool make_crc_tables(uint32_t* slice, uint32_t* shift) {
     to_tables(z, shift + size_t(j) * 1024);
     z = mul(z, z);
   }
+  Mat z496 = z1;  // Z_1^496 by square-and-multiply
+  {
+    Mat acc;
+    for (int i = 0; i < 32; ++i) acc.col[i] = 1u << i;
+    Mat base = z1;
+    for (uint32_t e = 496; e; e >>= 1) {
+      if (e & 1u) acc = mul(acc, base);
+      base = mul(base, base);
+    }
+    z496 = acc;
+  }
+  to_tables(z496, shift + size_t(kShift496) * 1024);
   Mat inv;
   if (!invert(z1, &inv)) return false;
   Mat zp = inv;

@@ -134,14 +134,17 @@ __global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs
 }
 
 // Walk one restart segment [s, e) of a data block: headers only. Returns false on a
-// structure violation; adds entries and key bytes.
+// structure violation; adds entries and key bytes. With `offs`, writes each entry's offset.
 __device__ __forceinline__ bool walk_segment(const uint8_t* base, uint64_t s, uint64_t e, uint32_t* cnt,
-                                             uint64_t* kbytes) {
+                                             uint64_t* kbytes, uint16_t* offs = nullptr, uint32_t cap = 0) {
   const uint8_t* p = base + s;
   const uint8_t* end = base + e;
   uint64_t prev = 0;
   bool first = true;
+  uint32_t rec = 0;
   while (p < end) {
+    if (offs && rec < cap) offs[rec] = uint16_t(p - base);
+    ++rec;
     uint64_t shared, nonshared, vlen;
     uint32_t a = get_varint<32>(p, end, &shared);
     if (!a) return false;
@@ -165,13 +168,21 @@ __device__ __forceinline__ bool walk_segment(const uint8_t* base, uint64_t s, ui
   return true;
 }
 
-// One warp per data block: CRC, type, structure; entry and key-byte counts.
-__global__ void __launch_bounds__(256) k_block_scan(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
-                                                    const DInput* __restrict__ in, uint32_t* __restrict__ nrec,
-                                                    uint64_t* __restrict__ kbytes, DErr* errs, Counts* counts,
-                                                    CrcTabs tabs) {
-  __shared__ uint32_t sT[1024];
-  load_slice_table(sT, tabs);
+// One warp per data block: CRC, type, structure; entry and key-byte counts. 1024-thread
+// CTAs, one per SM, with lane-replicated CRC tables (conflict-free lookups).
+constexpr int kScanWarps = 32;
+constexpr uint32_t kScanSmem = (kRepWords + 1024) * 4;
+
+__global__ void __launch_bounds__(kScanWarps * 32, 1) k_block_scan(const BlockDesc* __restrict__ blocks,
+                                                                   uint32_t n_blocks, const DInput* __restrict__ in,
+                                                                   uint32_t* __restrict__ nrec,
+                                                                   uint64_t* __restrict__ kbytes, DErr* errs,
+                                                                   Counts* counts, uint16_t* __restrict__ hdr_tab,
+                                                                   CrcTabs tabs) {
+  extern __shared__ uint32_t s_scan[];
+  uint32_t* sTr = s_scan;
+  uint32_t* sZ = s_scan + kRepWords;
+  load_rep_tables(sTr, sZ, tabs);
   __syncthreads();
   const uint32_t lane = lane_id();
   const uint64_t warps = gstride() / 32;
@@ -183,7 +194,7 @@ __global__ void __launch_bounds__(256) k_block_scan(const BlockDesc* __restrict_
     if (b.ptr != nullptr && *(volatile int32_t*)&e->code == 0) {
       if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&counts->in_data_bytes),
                                (unsigned long long)(b.size + kTrailer));
-      const uint32_t got = warp_crc32c(b.ptr, b.size + 1, sT, tabs);
+      const uint32_t got = warp_crc32c_il(b.ptr, b.size + 1, smem_addr(sTr), smem_addr(sZ), tabs);
       const uint32_t want = crc_unmask(ld_u32(b.ptr + b.size + 1));
       const uint32_t local = in[b.input].local;
       if (got != want) {
@@ -200,7 +211,9 @@ __global__ void __launch_bounds__(256) k_block_scan(const BlockDesc* __restrict_
             const uint64_t s = ld_u32(rs + 4 * k);
             const uint64_t en = k + 1 < nr ? ld_u32(rs + 4 * (k + 1)) : rstart;
             if ((k == 0 && s != 0) || s >= en || en > rstart) bad = true;
-            else if (!walk_segment(b.ptr, s, en, &cnt, &kb)) bad = true;
+            else if (!walk_segment(b.ptr, s, en, &cnt, &kb, nr == 1 && b.size < 65536 ? hdr_tab + g * kHdrMax : nullptr,
+                                   kHdrMax))
+              bad = true;
           }
         }
         bad = __any_sync(0xFFFFFFFFu, bad);
@@ -208,6 +221,36 @@ __global__ void __launch_bounds__(256) k_block_scan(const BlockDesc* __restrict_
           if (lane == 0) report(e, E_CORRUPT, local, b.off);
           cnt = 0;
           kb = 0;
+        } else if (b.size < 65536 && nr > 1) {
+          // entry offsets for the decoder (blocks of at most kHdrMax entries), segments in
+          // groups of 32 so that each group's entries are placed after the previous group's
+          const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, cnt);
+          if (total <= kHdrMax) {
+            const uint64_t rstart = b.size - 4 - 4 * nr;
+            const uint8_t* rs = b.ptr + rstart;
+            uint32_t run = 0;
+            for (uint64_t k0 = 0; k0 < nr; k0 += 32) {
+              const uint64_t k = k0 + lane;
+              uint64_t s = 0, en = 0, kk = 0;
+              uint32_t c = 0;
+              if (k < nr) {
+                s = ld_u32(rs + 4 * k);
+                en = k + 1 < nr ? ld_u32(rs + 4 * (k + 1)) : rstart;
+                walk_segment(b.ptr, s, en, &c, &kk);
+              }
+              uint32_t xs = c;
+#pragma unroll
+              for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, xs, d);
+                if (lane >= uint32_t(d)) xs += o;
+              }
+              if (k < nr) {
+                uint32_t c2 = 0;
+                walk_segment(b.ptr, s, en, &c2, &kk, hdr_tab + g * kHdrMax + run + xs - c, kHdrMax);
+              }
+              run += __shfl_sync(0xFFFFFFFFu, xs, 31);
+            }
+          }
         }
       }
     }
@@ -223,23 +266,53 @@ __global__ void __launch_bounds__(256) k_block_scan(const BlockDesc* __restrict_
   }
 }
 
-template <typename T>
-__device__ __forceinline__ T warp_excl(T v, T* total) {
-  const uint32_t lane = lane_id();
-  T x = v;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const T o = __shfl_up_sync(0xFFFFFFFFu, x, d);
-    if (lane >= uint32_t(d)) x += o;
+// One warp per data block. With the block's entry offsets from the scan (at most kHdrMax
+// entries, keys of at most 128 bytes), all headers are parsed at once (lane per entry)
+// and the keys are rebuilt entry by entry with lanes as byte positions: lane t keeps byte
+// t (t + 32, ...) of the current key in registers, takes the new bytes from the entry's
+// key delta, and stores the whole key with coalesced byte stores. Other blocks are
+// decoded by lane 0 alone, walking the segments in order.
+constexpr uint32_t kDecSlots = 4;  // key bytes per lane: 128-byte keys
+
+__device__ void decode_walk(const BlockDesc& b, uint64_t rec, uint64_t kpos, Recs& recs, uint8_t* arena, bool* bad) {
+  const uint64_t nr = ld_u32(b.ptr + b.size - 4);
+  const uint64_t rstart = b.size - 4 - 4 * nr;
+  const uint8_t* rs = b.ptr + rstart;
+  for (uint64_t k = 0; k < nr; ++k) {
+    const uint8_t* p = b.ptr + ld_u32(rs + 4 * k);
+    const uint8_t* end = b.ptr + (k + 1 < nr ? ld_u32(rs + 4 * (k + 1)) : rstart);
+    uint64_t prev_kpos = 0;
+    while (p < end) {
+      uint64_t shared, nonshared, vlen;
+      p += get_varint<32>(p, end, &shared);
+      p += get_varint<32>(p, end, &nonshared);
+      p += get_varint<32>(p, end, &vlen);
+      uint8_t* kd = arena + kpos;
+      for (uint64_t t = 0; t < shared; ++t) kd[t] = arena[prev_kpos + t];
+      for (uint64_t t = 0; t < nonshared; ++t) kd[shared + t] = p[t];
+      p += nonshared;
+      const uint32_t klen = uint32_t(shared + nonshared);
+      const uint64_t tr = ld_u64(kd + klen - 8);
+      if ((tr & 0xFF) > 1) *bad = true;
+      recs.pfx[rec] = key_prefix(kd, klen - 8);
+      recs.koff[rec] = kpos;
+      recs.klen[rec] = klen;
+      recs.tr[rec] = tr;
+      recs.vptr[rec] = reinterpret_cast<uint64_t>(p);
+      recs.vlen[rec] = uint32_t(vlen);
+      recs.src[rec] = b.input;
+      p += vlen;
+      prev_kpos = kpos;
+      kpos += klen;
+      ++rec;
+    }
   }
-  *total = __shfl_sync(0xFFFFFFFFu, x, 31);
-  return x - v;
 }
 
-// One warp per data block, one lane per restart segment: rebuild the keys and emit
-// records at the block's scanned offsets.
 __global__ void __launch_bounds__(256) k_decode(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
-                                                const DInput* __restrict__ in, const uint32_t* __restrict__ rec_first,
+                                                const DInput* __restrict__ in, const uint32_t* __restrict__ nrec,
+                                                const uint16_t* __restrict__ hdr_tab,
+                                                const uint32_t* __restrict__ rec_first,
                                                 const uint64_t* __restrict__ key_first, Recs recs,
                                                 uint8_t* __restrict__ arena, DErr* errs) {
   const uint32_t lane = lane_id();
@@ -248,62 +321,88 @@ __global__ void __launch_bounds__(256) k_decode(const BlockDesc* __restrict__ bl
     const BlockDesc b = blocks[g];
     DErr* e = errs + b.job;
     if (b.ptr == nullptr || *(volatile int32_t*)&e->code != 0) continue;
-    const uint64_t nr = ld_u32(b.ptr + b.size - 4);
-    const uint64_t rstart = b.size - 4 - 4 * nr;
-    const uint8_t* rs = b.ptr + rstart;
-    uint64_t rec_base = rec_first[g];
-    uint64_t key_base = key_first[g];
-    const uint32_t local = in[b.input].local;
-    for (uint64_t k0 = 0; k0 < nr; k0 += 32) {
-      const uint64_t k = k0 + lane;
-      uint64_t s = 0, en = 0;
-      uint32_t cnt = 0;
-      uint64_t kb = 0;
-      if (k < nr) {
-        s = ld_u32(rs + 4 * k);
-        en = k + 1 < nr ? ld_u32(rs + 4 * (k + 1)) : rstart;
-        walk_segment(b.ptr, s, en, &cnt, &kb);
-      }
-      uint32_t cnt_tot;
-      uint64_t kb_tot;
-      const uint32_t my_rec = warp_excl<uint32_t>(cnt, &cnt_tot);
-      const uint64_t my_key = warp_excl<uint64_t>(kb, &kb_tot);
-      if (k < nr) {
-        const uint8_t* p = b.ptr + s;
-        const uint8_t* end = b.ptr + en;
-        uint64_t rec = rec_base + my_rec;
-        uint64_t kpos = key_base + my_key;
-        uint64_t prev_kpos = 0;
-        bool bad = false;
-        while (p < end) {
-          uint64_t shared, nonshared, vlen;
-          p += get_varint<32>(p, end, &shared);
-          p += get_varint<32>(p, end, &nonshared);
-          p += get_varint<32>(p, end, &vlen);
-          uint8_t* kd = arena + kpos;
-          for (uint64_t t = 0; t < shared; ++t) kd[t] = arena[prev_kpos + t];
-          for (uint64_t t = 0; t < nonshared; ++t) kd[shared + t] = p[t];
-          p += nonshared;
-          const uint32_t klen = uint32_t(shared + nonshared);
-          const uint64_t tr = ld_u64(kd + klen - 8);
-          if ((tr & 0xFF) > 1) bad = true;
-          recs.pfx[rec] = key_prefix(kd, klen - 8);
-          recs.koff[rec] = kpos;
-          recs.klen[rec] = klen;
-          recs.tr[rec] = tr;
-          recs.vptr[rec] = reinterpret_cast<uint64_t>(p);
-          recs.vlen[rec] = uint32_t(vlen);
-          recs.src[rec] = b.input;
-          p += vlen;
-          prev_kpos = kpos;
-          kpos += klen;
-          ++rec;
+    const uint32_t nent = nrec[g];
+    const uint64_t rec0 = rec_first[g], key0 = key_first[g];
+    bool bad = false;
+    bool tab = nent <= kHdrMax && b.size < 65536;
+    // lane-per-entry header parse (entries lane and lane + 32)
+    uint32_t sh[2] = {0, 0}, ns[2] = {0, 0}, kl[2] = {0, 0}, dp[2] = {0, 0};
+    if (tab) {
+      bool long_key = false;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t k = lane + 32 * h;
+        if (k < nent) {
+          const uint8_t* p = b.ptr + hdr_tab[g * kHdrMax + k];
+          const uint8_t* end = b.ptr + b.size;
+          uint64_t s_, n_, v_;
+          p += get_varint<32>(p, end, &s_);
+          p += get_varint<32>(p, end, &n_);
+          p += get_varint<32>(p, end, &v_);
+          sh[h] = uint32_t(s_);
+          ns[h] = uint32_t(n_);
+          kl[h] = uint32_t(s_ + n_);
+          dp[h] = uint32_t(p - b.ptr);
+          long_key |= kl[h] > 32 * kDecSlots;
+          recs.vptr[rec0 + k] = reinterpret_cast<uint64_t>(p + n_);
+          recs.vlen[rec0 + k] = uint32_t(v_);
+          recs.klen[rec0 + k] = kl[h];
+          recs.src[rec0 + k] = b.input;
         }
-        if (bad) report(e, E_CORRUPT, local, b.off);
       }
-      rec_base += cnt_tot;
-      key_base += kb_tot;
+      tab = !__any_sync(0xFFFFFFFFu, long_key);
     }
+    if (!tab) {
+      if (lane == 0) decode_walk(b, rec0, key0, recs, arena, &bad);
+      bad = __any_sync(0xFFFFFFFFu, bad);
+      if (bad && lane == 0) report(e, E_CORRUPT, in[b.input].local, b.off);
+      continue;
+    }
+    // key offsets: exclusive scan of key lengths over the (up to 64) entries
+    uint32_t x0 = kl[0], x1 = kl[1];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o0 = __shfl_up_sync(0xFFFFFFFFu, x0, d), o1 = __shfl_up_sync(0xFFFFFFFFu, x1, d);
+      if (lane >= uint32_t(d)) {
+        x0 += o0;
+        x1 += o1;
+      }
+    }
+    const uint32_t tot0 = __shfl_sync(0xFFFFFFFFu, x0, 31);
+    const uint32_t ko[2] = {x0 - kl[0], tot0 + x1 - kl[1]};
+    uint8_t cur[kDecSlots] = {0, 0, 0, 0};
+    for (uint32_t k = 0; k < nent; ++k) {
+      const uint32_t src = k & 31u, h = k >> 5;
+      const uint32_t shared = __shfl_sync(0xFFFFFFFFu, h ? sh[1] : sh[0], src);
+      const uint32_t klen = __shfl_sync(0xFFFFFFFFu, h ? kl[1] : kl[0], src);
+      const uint32_t dpos = __shfl_sync(0xFFFFFFFFu, h ? dp[1] : dp[0], src);
+      const uint32_t kof = __shfl_sync(0xFFFFFFFFu, h ? ko[1] : ko[0], src);
+      uint8_t* kd = arena + key0 + kof;
+      uint64_t pf = 0, tr = 0;
+#pragma unroll
+      for (uint32_t s = 0; s < kDecSlots; ++s) {
+        const uint32_t t = lane + 32 * s;
+        if (t < klen) {
+          if (t >= shared) cur[s] = b.ptr[dpos + t - shared];
+          kd[t] = cur[s];
+          if (t < 8 && t < klen - 8) pf |= uint64_t(cur[s]) << (8 * (7 - t));
+          if (t >= klen - 8) tr |= uint64_t(cur[s]) << (8 * (t - (klen - 8)));
+        }
+      }
+#pragma unroll
+      for (int d = 16; d; d >>= 1) {
+        pf |= __shfl_xor_sync(0xFFFFFFFFu, pf, d);
+        tr |= __shfl_xor_sync(0xFFFFFFFFu, tr, d);
+      }
+      if (lane == 0) {
+        if ((tr & 0xFF) > 1) bad = true;
+        recs.pfx[rec0 + k] = pf;
+        recs.tr[rec0 + k] = tr;
+        recs.koff[rec0 + k] = key0 + kof;
+      }
+    }
+    bad = __any_sync(0xFFFFFFFFu, bad);
+    if (bad && lane == 0) report(e, E_CORRUPT, in[b.input].local, b.off);
   }
 }
 
@@ -341,15 +440,22 @@ void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* i
 }
 
 void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, Counts* cnt, CrcTabs tabs, cudaStream_t st) {
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, CrcTabs tabs, cudaStream_t st) {
   if (!n_blocks) return;
-  k_block_scan<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, cnt, tabs); count_launches(1);
+  cudaFuncSetAttribute(k_block_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kScanSmem));
+  k_block_scan<<<grid_for(n_blocks, kScanWarps, kSms), kScanWarps * 32, kScanSmem, st>>>(blocks, n_blocks, in, nrec,
+                                                                                         kbytes, errs, cnt, hdr_tab,
+                                                                                         tabs);
+  count_launches(1);
 }
 
-void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* rec_first,
-                   const uint64_t* key_first, Recs recs, uint8_t* arena, DErr* errs, cudaStream_t st) {
+void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,
+                   const uint16_t* hdr_tab, const uint32_t* rec_first, const uint64_t* key_first, Recs recs,
+                   uint8_t* arena, DErr* errs, cudaStream_t st) {
   if (!n_blocks) return;
-  k_decode<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, rec_first, key_first, recs, arena, errs); count_launches(1);
+  k_decode<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, nrec, hdr_tab, rec_first, key_first, recs,
+                                                  arena, errs);
+  count_launches(1);
 }
 
 void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,

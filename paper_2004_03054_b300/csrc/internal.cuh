@@ -111,12 +111,14 @@ bool make_crc_tables(uint32_t* slice, uint32_t* shift);
 void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cudaStream_t st);
 void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
                           BlockDesc* blocks, DErr* errs, cudaStream_t st);
+constexpr uint32_t kHdrMax = 64;  // entry offsets recorded per block for the decoder
 void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, Counts* cnt, CrcTabs tabs, cudaStream_t st);
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, CrcTabs tabs, cudaStream_t st);
 void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,
                         uint64_t* kbytes, cudaStream_t st);
-void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* rec_first,
-                   const uint64_t* key_first, Recs recs, uint8_t* arena, DErr* errs, cudaStream_t st);
+void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,
+                   const uint16_t* hdr_tab, const uint32_t* rec_first, const uint64_t* key_first, Recs recs,
+                   uint8_t* arena, DErr* errs, cudaStream_t st);
 void launch_input_ranges(const DInput* in, uint32_t n_inputs, const uint32_t* rec_first,
                          const uint64_t* key_first, uint32_t* in_rec, uint64_t* in_key, cudaStream_t st);
 
@@ -172,7 +174,7 @@ void launch_zero_bitmap(uint32_t* bitmap, const Counts* cnt, uint64_t cap_words,
 void launch_encode(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                    const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
                    const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
-                   Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs, cudaStream_t st);
+                   Fmt fmt, uint8_t* out, uint64_t out_cap, uint8_t* done, CrcTabs tabs, cudaStream_t st);
 void launch_bloom(const uint32_t* surv, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                   const uint32_t* blk_start, const FileDesc* files, Recs recs, const uint8_t* arena, Fmt fmt,
                   uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st);

@@ -387,6 +387,7 @@ __global__ void k_zero_words(uint32_t* __restrict__ w, const Counts* __restrict_
 // global memory instead (same bytes).
 constexpr int kEncThreads = 256;
 constexpr uint32_t kEncBuf = 64 * 1024;
+constexpr uint32_t kEncMaxEnt = 40;  // blocks of up to this many entries take the warp encoder
 
 // Copy n bytes from global src (any alignment) to dst (any alignment), one warp.
 __device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, uint32_t n, uint32_t lane) {
@@ -407,7 +408,7 @@ __device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, uint
   if (lane < n - done) dst[done + lane] = src[done + lane];
 }
 
-__global__ void __launch_bounds__(kEncThreads) k_encode(const uint32_t* __restrict__ start,
+__global__ void __launch_bounds__(kEncThreads) k_encode_big(const uint32_t* __restrict__ start,
                                                         const Counts* __restrict__ cnt,
                                                         const uint32_t* __restrict__ blk_file,
                                                         const FileDesc* __restrict__ files,
@@ -417,7 +418,8 @@ __global__ void __launch_bounds__(kEncThreads) k_encode(const uint32_t* __restri
                                                         const uint32_t* __restrict__ sd,
                                                         const uint32_t* __restrict__ dr, Recs recs,
                                                         const uint8_t* __restrict__ arena, Fmt fmt,
-                                                        uint8_t* __restrict__ out, uint64_t out_cap, CrcTabs tabs) {
+                                                        uint8_t* __restrict__ out, uint64_t out_cap,
+                                                        const uint8_t* __restrict__ done, CrcTabs tabs) {
   extern __shared__ uint4 s_dyn[];
   __shared__ uint32_t sT[1024];
   __shared__ uint32_t s_off[kEncThreads];
@@ -431,6 +433,7 @@ __global__ void __launch_bounds__(kEncThreads) k_encode(const uint32_t* __restri
   const uint32_t nb = cnt->nb;
   for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
     const uint32_t s = start[b], e = start[b + 1], m = e - s;
+    if (done[b]) continue;  // the warp encoder took it
     const FileDesc F = files[blk_file[b]];
     if (F.off + F.size > out_cap) continue;
     uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
@@ -512,6 +515,255 @@ __global__ void __launch_bounds__(kEncThreads) k_encode(const uint32_t* __restri
       }
       __syncthreads();
     }
+  }
+}
+
+
+// ---- warp encoder ---------------------------------------------------------------------------
+// Two kernels. k_encode writes the bytes of every data block of at most kEncMaxEnt
+// entries, one warp per block and no staging buffer: the block is cut into 16-byte chunks
+// aligned in global memory. Chunks inside one value ("value chunks") are copied in rounds
+// where lane l of round r owns chunk Q - 32 * (rounds - r) + l (512 contiguous bytes per
+// round): two aligned 16-byte loads from the input table, funnel shifts, one aligned
+// 16-byte store, with loads two rounds ahead. The other chunks (headers, key deltas,
+// restart array, ragged ends) are written byte by byte first, one lane per entry so that
+// all of a block's boundary loads are in flight together. Without CRC tables the kernel
+// holds little shared memory and runs 64 warps per SM.
+// k_block_crc then computes each block's masked CRC-32C trailer (interleaved warp CRC,
+// lane-replicated tables). Blocks the warp encoder cannot take go to k_encode_big.
+constexpr int kEncWarps = 32;
+constexpr uint32_t kEncMapWords = 96;  // bitmap words: chunks per block <= 3072 (48 KiB)
+
+struct EncEnt {
+  uint32_t eoff, voff, vlen, nsh, shr, pad;
+  uint64_t vptr, kptr;
+};
+
+struct EncWarp {
+  EncEnt ent[kEncMaxEnt + 1];
+  uint32_t map[kEncMapWords];
+};
+
+constexpr uint32_t kEncSmem = kEncWarps * uint32_t(sizeof(EncWarp));
+
+__device__ __forceinline__ uint32_t vbyte(uint32_t v, uint32_t j) {
+  return ((v >> (7 * j)) & 0x7Fu) | (j + 1 < varint_size(v) ? 0x80u : 0u);
+}
+
+__device__ __forceinline__ uint32_t u4_byte(uint4 v, uint32_t u) {  // byte u (< 16) of v
+  const uint32_t w = u < 8 ? (u < 4 ? v.x : v.y) : (u < 12 ? v.z : v.w);
+  return (w >> (8 * (u & 3))) & 0xFFu;
+}
+
+// Bytes [sh, sh + 16) of the 32 bytes a || b, with selects (no divergent branches).
+__device__ __forceinline__ uint4 shift32(uint4 a, uint4 b, uint32_t sh) {
+  const bool s2 = (sh & 8u) != 0, s1 = (sh & 4u) != 0;
+  const uint32_t x0 = s2 ? a.z : a.x, x1 = s2 ? a.w : a.y, x2 = s2 ? b.x : a.z;
+  const uint32_t x3 = s2 ? b.y : a.w, x4 = s2 ? b.z : b.x, x5 = s2 ? b.w : b.y;
+  const uint32_t y0 = s1 ? x1 : x0, y1 = s1 ? x2 : x1, y2 = s1 ? x3 : x2, y3 = s1 ? x4 : x3, y4 = s1 ? x5 : x4;
+  const uint32_t bs = (sh & 3u) * 8u;
+  return make_uint4(__funnelshift_r(y0, y1, bs), __funnelshift_r(y1, y2, bs), __funnelshift_r(y2, y3, bs),
+                    __funnelshift_r(y3, y4, bs));
+}
+
+__device__ __forceinline__ uint4 load16(const uint8_t* src) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
+  const uint32_t sh = uint32_t(reinterpret_cast<uintptr_t>(src) & 15u);
+  const uint4 u0 = __ldg(reinterpret_cast<const uint4*>(a));
+  if (sh == 0) return u0;
+  return shift32(u0, __ldg(reinterpret_cast<const uint4*>(a + 16)), sh);
+}
+
+__device__ __forceinline__ void map_range(uint32_t* map, int64_t a, int64_t b) {  // set bits [a, b]
+  for (int64_t q = a; q <= b; ++q) atomicOr(map + (q >> 5), 1u << (q & 31));
+}
+
+__global__ void __launch_bounds__(kEncWarps * 32, 1) k_encode(const uint32_t* __restrict__ start,
+                                                               const Counts* __restrict__ cnt,
+                                                               const uint32_t* __restrict__ blk_file,
+                                                               const FileDesc* __restrict__ files,
+                                                               const uint64_t* __restrict__ C,
+                                                               const uint64_t* __restrict__ bsz,
+                                                               const uint32_t* __restrict__ surv,
+                                                               const uint32_t* __restrict__ lcp, Recs recs,
+                                                               const uint8_t* __restrict__ arena, Fmt fmt,
+                                                               uint8_t* __restrict__ out, uint64_t out_cap,
+                                                               uint8_t* __restrict__ done) {
+  extern __shared__ uint32_t s_enc[];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  EncWarp& Wp = reinterpret_cast<EncWarp*>(s_enc)[warp];
+  EncEnt* E = Wp.ent;
+  const uint32_t R = fmt.R;
+  const uint32_t nb = cnt->nb;
+  const uint32_t total_warps = gridDim.x * kEncWarps;
+  for (uint32_t b = blockIdx.x * kEncWarps + warp; b < nb; b += total_warps) {
+    const uint32_t s = start[b], m = start[b + 1] - s;
+    if (lane == 0) done[b] = 0;
+    if (m > kEncMaxEnt) continue;
+    const FileDesc F = files[blk_file[b]];
+    if (F.off + F.size > out_cap) continue;
+    uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
+    const uint64_t contents = bsz[b];
+    const uint64_t msg = contents + 1;  // contents and type byte
+    const uint32_t phase = uint32_t(reinterpret_cast<uintptr_t>(dst) & 15u);
+    const int64_t Q = int64_t((phase + msg + 15) >> 4);
+    if (Q > int64_t(kEncMapWords) * 32) continue;
+    // entry layout
+    uint32_t carry = 0;
+    for (uint32_t k0 = 0; k0 < m; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      uint32_t size = 0, vlen = 0, shr = 0, nsh = 0, hl = 0;
+      uint64_t vptr = 0, kptr = 0;
+      if (k < m) {
+        const uint32_t x = surv[s + k];
+        const uint32_t klen = recs.klen[x];
+        vlen = recs.vlen[x];
+        shr = (k % R) == 0 ? 0u : lcp[s + k];
+        nsh = klen - shr;
+        hl = varint_size(shr) + varint_size(nsh) + varint_size(vlen);
+        size = hl + nsh + vlen;
+        vptr = recs.vptr[x];
+        kptr = reinterpret_cast<uint64_t>(arena + recs.koff[x] + shr);
+      }
+      uint32_t xs = size;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, xs, d);
+        if (lane >= uint32_t(d)) xs += o;
+      }
+      const uint32_t eoff = carry + xs - size;
+      if (k < m) E[k] = EncEnt{eoff, eoff + hl + nsh, vlen, nsh, shr, 0, vptr, kptr};
+      carry += __shfl_sync(0xFFFFFFFFu, xs, 31);
+    }
+    const uint32_t ent_end = carry;
+    const uint32_t nr = (m + R - 1) / R;
+    // boundary-chunk bitmap
+    const uint32_t words = uint32_t((Q + 31) >> 5);
+    for (uint32_t w = lane; w < words; w += 32) Wp.map[w] = 0;
+    if (lane == 0) E[m].eoff = ent_end;
+    __syncwarp();
+    for (uint32_t k = lane; k < m; k += 32)
+      map_range(Wp.map, (int64_t(E[k].eoff) + phase) >> 4, (int64_t(E[k].voff) - 1 + phase) >> 4);
+    if (lane == 0) map_range(Wp.map, (int64_t(ent_end) + phase) >> 4, Q - 1);
+    __syncwarp();
+    uint8_t* A0 = dst - phase;
+    // boundary bytes, one lane per entry: header, key delta, value head and tail
+    for (uint32_t k = lane; k < m; k += 32) {
+      const EncEnt en = E[k];
+      const uint32_t s0 = varint_size(en.shr), s1 = varint_size(en.nsh), s2 = varint_size(en.vlen);
+      const uint32_t hl = s0 + s1 + s2;
+      const uint8_t* kp = reinterpret_cast<const uint8_t*>(en.kptr);
+      const uint8_t* vp = reinterpret_cast<const uint8_t*>(en.vptr);
+      const int64_t v0 = en.voff, v1 = int64_t(en.voff) + en.vlen;
+      const int64_t head_end = min(v1, ((v0 + phase + 15) & ~int64_t(15)) - phase);
+      const int64_t tail_beg = max(head_end, ((v1 + phase) & ~int64_t(15)) - phase);
+      uint4 hv = make_uint4(0, 0, 0, 0), tv = hv;
+      const int64_t w0 = en.vlen >= 16 ? int64_t(en.vlen) - 16 : 0;  // tail window inside the value
+      if (head_end > v0) hv = load16(vp);
+      if (v1 > tail_beg) tv = load16(vp + w0);
+      uint8_t* ep = dst + en.eoff;
+      uint32_t q = put_varint(ep, en.shr);
+      q += put_varint(ep + q, en.nsh);
+      put_varint(ep + q, en.vlen);
+      // key delta: 16-byte loads issued ahead of the byte stores (keys up to 80 bytes in
+      // one batch; longer keys continue 16 bytes at a time)
+      {
+        uint4 k0 = make_uint4(0, 0, 0, 0), k1 = k0, k2 = k0, k3 = k0, k4 = k0;
+        const uint32_t n = en.nsh;
+        if (n > 0) k0 = load16(kp);
+        if (n > 16) k1 = load16(kp + 16);
+        if (n > 32) k2 = load16(kp + 32);
+        if (n > 48) k3 = load16(kp + 48);
+        if (n > 64) k4 = load16(kp + 64);
+        uint8_t* kd = ep + hl;
+        for (uint32_t t = 0; t < n && t < 80; ++t) {
+          const uint4 kv = t < 16 ? k0 : t < 32 ? k1 : t < 48 ? k2 : t < 64 ? k3 : k4;
+          kd[t] = uint8_t(u4_byte(kv, t & 15u));
+        }
+        for (uint32_t t0 = 80; t0 < n; t0 += 16) {
+          const uint4 kv = load16(kp + t0);
+          for (uint32_t u = 0; u < 16 && t0 + u < n; ++u) kd[t0 + u] = uint8_t(u4_byte(kv, u));
+        }
+      }
+      for (int64_t i = v0; i < head_end; ++i) dst[i] = uint8_t(u4_byte(hv, uint32_t(i - v0)));
+      for (int64_t i = tail_beg; i < v1; ++i) dst[i] = uint8_t(u4_byte(tv, uint32_t(i - v0 - w0)));
+    }
+    for (uint64_t t = lane; t < 4ull * nr; t += 32)  // restart array
+      dst[ent_end + t] = uint8_t(E[(t >> 2) * R].eoff >> (8 * (t & 3)));
+    if (lane == 0) {
+      st_u32(dst + contents - 4, nr);
+      dst[contents] = 0;
+    }
+    // value chunks, in rounds; loads run two rounds ahead of the stores
+    const int64_t rounds = (Q + 31) >> 5;
+    uint32_t cur = 0;
+    auto fetch = [&](int64_t r, uint4& u0, uint4& u1, uint32_t& sh, bool& val) {
+      const int64_t q = Q - 32 * (rounds - r) + lane;
+      val = false;
+      if (q < 0 || (Wp.map[q >> 5] & (1u << (q & 31)))) return;
+      const int64_t lo = q * 16 - int64_t(phase);
+      while (cur + 1 < m && E[cur + 1].eoff <= uint64_t(lo)) ++cur;
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(E[cur].vptr) + (lo - E[cur].voff);
+      const uintptr_t a = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
+      sh = uint32_t(reinterpret_cast<uintptr_t>(src) & 15u);
+      u0 = __ldg(reinterpret_cast<const uint4*>(a));
+      u1 = sh ? __ldg(reinterpret_cast<const uint4*>(a + 16)) : u0;
+      val = true;
+    };
+    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
+    uint32_t ash = 0, bsh = 0;
+    bool aval = false, bval = false;
+    if (rounds > 0) fetch(0, a0, a1, ash, aval);
+    if (rounds > 1) fetch(1, b0, b1, bsh, bval);
+    for (int64_t r = 0; r < rounds; ++r) {
+      uint4 c0 = make_uint4(0, 0, 0, 0), c1 = c0;
+      uint32_t csh = 0;
+      bool cval = false;
+      if (r + 2 < rounds) fetch(r + 2, c0, c1, csh, cval);
+      if (aval) {
+        const int64_t q = Q - 32 * (rounds - r) + lane;
+        *reinterpret_cast<uint4*>(A0 + q * 16) = ash ? shift32(a0, a1, ash) : a0;
+      }
+      a0 = b0;
+      a1 = b1;
+      ash = bsh;
+      aval = bval;
+      b0 = c0;
+      b1 = c1;
+      bsh = csh;
+      bval = cval;
+    }
+    if (lane == 0) done[b] = 1;
+  }
+}
+
+// Masked CRC-32C trailers of the blocks k_encode wrote (done[b] = 1): one warp per block,
+// the block re-read from global memory (mostly L2).
+constexpr int kCrcWarps = 32;
+constexpr uint32_t kCrcSmem = (kRepWords + 1024) * 4;
+
+__global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(const Counts* __restrict__ cnt,
+                                                                  const uint32_t* __restrict__ blk_file,
+                                                                  const FileDesc* __restrict__ files,
+                                                                  const uint64_t* __restrict__ C,
+                                                                  const uint64_t* __restrict__ bsz,
+                                                                  uint8_t* __restrict__ out, uint64_t out_cap,
+                                                                  const uint8_t* __restrict__ done, CrcTabs tabs) {
+  extern __shared__ uint32_t s_crc[];
+  load_rep_tables(s_crc, s_crc + kRepWords, tabs);
+  __syncthreads();
+  const uint32_t tb0 = smem_addr(s_crc), zb = smem_addr(s_crc + kRepWords);
+  const uint32_t lane = lane_id();
+  const uint32_t nb = cnt->nb;
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t b = gtid() / 32; b < nb; b += warps) {
+    if (!done[b]) continue;
+    const FileDesc F = files[blk_file[b]];
+    if (F.off + F.size > out_cap) continue;
+    uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
+    const uint64_t contents = bsz[b];
+    const uint32_t crc = warp_crc32c_il(dst, contents + 1, tb0, zb, tabs);
+    if (lane == 0) st_u32(dst + contents + 1, crc_mask(crc));
   }
 }
 
@@ -846,12 +1098,19 @@ void launch_zero_bitmap(uint32_t* bitmap, const Counts* cnt, uint64_t cap_words,
 void launch_encode(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                    const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
                    const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
-                   Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs, cudaStream_t st) {
+                   Fmt fmt, uint8_t* out, uint64_t out_cap, uint8_t* done, CrcTabs tabs, cudaStream_t st) {
   if (!cap) return;
-  cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kEncBuf));
-  k_encode<<<grid_for(cap, 1, kSms * 3), kEncThreads, kEncBuf, st>>>(blk_start, cnt, blk_file, files, C, bsz, surv,
-                                                                     lcp, sd, dr, recs, arena, fmt, out, out_cap,
-                                                                     tabs);
+  cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kEncSmem));
+  k_encode<<<kSms, kEncWarps * 32, kEncSmem, st>>>(blk_start, cnt, blk_file, files, C, bsz, surv, lcp, recs,
+                                                       arena, fmt, out, out_cap, done);
+  count_launches(1);
+  cudaFuncSetAttribute(k_block_crc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCrcSmem));
+  k_block_crc<<<kSms, kCrcWarps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done, tabs);
+  count_launches(1);
+  cudaFuncSetAttribute(k_encode_big, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kEncBuf));
+  k_encode_big<<<grid_for(cap, 1, kSms * 3), kEncThreads, kEncBuf, st>>>(blk_start, cnt, blk_file, files, C, bsz,
+                                                                         surv, lcp, sd, dr, recs, arena, fmt, out,
+                                                                         out_cap, done, tabs);
   count_launches(1);
 }
 
