@@ -185,6 +185,39 @@ typedef struct {
 LUDA_API luda_status luda_build(const luda_run* run, const luda_options* opts, luda_outputs* out);
 LUDA_API luda_status luda_build_device(const luda_run* run, const luda_options* opts, luda_outputs* out);
 
+/* ---- table check without allocation ----------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that cannot
+ * allocate device memory when they need to check a table: code running inside a custom
+ * allocator or memory-pool callback (a nested cudaMalloc would re-enter it), storage
+ * engines that reserve all device memory at start-up, and paths that cannot afford an
+ * allocation's implicit synchronisation.
+ *
+ * luda_check_table_noalloc verifies one table on the device exactly as a compaction
+ * reads it -- footer, index block, and every data block's CRC-32C, type byte and
+ * structure -- and counts its entries. `table` is a device pointer to `size` bytes on
+ * `stream` (a cudaStream_t, NULL = legacy default). It calls no cudaMalloc, cudaFree or
+ * other allocating routine: its scratch is a static device array of about 2.7 MiB that
+ * every GPU loading the library holds until the process exits, limited to tables of at
+ * most LUDA_NOALLOC_MAX_BLOCKS data blocks (larger tables: LUDA_ERR_INVALID_ARG with a
+ * message naming the limit). The scratch is shared by all calls and keeps the last
+ * call's contents; each call clears what it needs. Calls that overlap on the GPU race:
+ * serialise them. The first call on a device (with that device current) looks up the
+ * scratch with cudaGetSymbolAddress and uploads CRC tables with cudaMemcpyToSymbol;
+ * make that first call before any stream capture. Returns the table's status (also in
+ * out->status); on a corrupt table out->bad_offset is the byte offset of the fault. */
+#define LUDA_NOALLOC_MAX_BLOCKS 16384u
+
+typedef struct {
+  int32_t status;       /* luda_status */
+  uint32_t n_blocks;    /* data blocks listed in the index */
+  uint64_t n_entries;   /* entries in all data blocks (valid when status == LUDA_OK) */
+  uint64_t data_bytes;  /* data block bytes including trailers (valid when LUDA_OK) */
+  uint64_t bad_offset;  /* byte offset of the fault when status is an error */
+} luda_table_check;
+
+LUDA_API luda_status luda_check_table_noalloc(const uint8_t* table, uint64_t size, void* stream,
+                                              luda_table_check* out);
+
 /* Frees everything an entry point stored in *out (host and device memory). */
 LUDA_API void luda_outputs_free(luda_outputs* out);
 

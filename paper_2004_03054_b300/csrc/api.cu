@@ -41,6 +41,12 @@ void set_detail(const char* fmt, ...) {
   va_end(ap);
 }
 
+}  // namespace
+
+void luda::set_error_detail(const char* text) { snprintf(t_detail, sizeof t_detail, "%s", text); }
+
+namespace {
+
 // ---- per-device CRC tables ----------------------------------------------------------------
 struct DevTables {
   uint32_t* slice = nullptr;

@@ -90,6 +90,8 @@ struct FileMeta {
 // ---- launch geometry --------------------------------------------------------------------
 // Every launcher adds its kernel launches here (luda_launch_count).
 void count_launches(uint32_t n);
+// Sets the calling thread's luda_last_error_detail() text.
+void set_error_detail(const char* text);
 
 inline unsigned grid_for(uint64_t work, unsigned per_cta, unsigned max_ctas = kSms * 16) {
   uint64_t g = (work + per_cta - 1) / per_cta;

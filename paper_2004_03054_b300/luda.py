@@ -57,6 +57,11 @@ class Job(C.Structure):
                 ("smallest_snapshot", C.c_uint64), ("bottommost", C.c_int32)]
 
 
+class TableCheck(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_blocks", C.c_uint32), ("n_entries", C.c_uint64),
+                ("data_bytes", C.c_uint64), ("bad_offset", C.c_uint64)]
+
+
 class RunArrays(C.Structure):
     _fields_ = [("ukeys", C.c_void_p), ("ukoff", C.c_void_p), ("seqs", C.c_void_p), ("types", C.c_void_p),
                 ("vals", C.c_void_p), ("voff", C.c_void_p), ("n", C.c_uint64)]
@@ -91,6 +96,8 @@ def lib():
         L.luda_last_error_detail.restype = C.c_char_p
         L.luda_version.restype = C.c_char_p
         L.luda_launch_count.restype = C.c_uint64
+        L.luda_check_table_noalloc.restype = st
+        L.luda_check_table_noalloc.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(TableCheck)]
         for name in ("luda_plan_create", "luda_plan_run", "luda_plan_outputs", "luda_plan_destroy"):
             if hasattr(L, name):
                 getattr(L, name).restype = st
@@ -262,6 +269,15 @@ def _run_arrays(run, device: bool):
         ptrs = [a.ctypes.data for a in keep]
     ra = RunArrays(*ptrs, run.n)
     return ra, keep
+
+
+def check_table_noalloc(table, stream=None) -> TableCheck:
+    """Verify one table (torch uint8 CUDA tensor) with the entry point that allocates no
+    device memory; returns the filled luda_table_check."""
+    out = TableCheck()
+    lib().luda_check_table_noalloc(C.c_void_p(table.data_ptr()), table.numel(),
+                                   stream if stream is not None else current_stream(), C.byref(out))
+    return out
 
 
 def build(run, opts: Options | None = None) -> Result:
