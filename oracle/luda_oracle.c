@@ -7,9 +7,9 @@
  * code, header, table or constant generator with the CUDA path.
  *
  * The method (LUDA, arXiv 2004.03054, §II-A "LSM-tree Compaction") is exact: a
- * compaction decodes the input tables (Phase 1 "Unpack"), merges and sorts all pairs and
- * drops stale and deleted ones (Phase 2 "(Delete and) Sort"), and packs the survivors into
- * new tables with data blocks, checksums, an index and a bloom filter (Phase 3 "Pack").
+ * compaction decodes the input tables (Phase 1, unpack), orders all pairs by key and
+ * removes stale and deleted ones (Phase 2, delete and sort), and packs the survivors into
+ * new tables with data blocks, checksums, an index and a bloom filter (Phase 3, pack).
  * The paper defers the byte layout to LevelDB; the layout used here is the written
  * LevelDB-style format of this project (varints, prefix-compressed keys with restart
  * points, masked CRC32C trailers, full-key index, per-table bloom filter, no
@@ -61,8 +61,8 @@ const char* ora_last_detail(void) { return g_detail; }
 
 /* ------------------------------------------------------------------------------------
  * CRC-32C (Castagnoli), reflected polynomial 0x82F63B78, init and final XOR 0xFFFFFFFF.
- * Block checksums: §II-A ("a checksum ... is used for the shared keys and value part")
- * and §III-C (the encode kernel "calculate[s] the checksum ... for each data block").
+ * Every data block carries a checksum over its keys and values (§II-A), computed per
+ * block when packing (§III-C, encode kernel) and verified when unpacking.
  * ------------------------------------------------------------------------------------ */
 #define ORA_CRC_POLY 0x82F63B78u
 

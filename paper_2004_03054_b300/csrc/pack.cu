@@ -1,7 +1,7 @@
 // pack.cu -- Phase 3 "Pack" (LUDA §II-A; §III-C "shared_key", "encode" and "filter"
 // kernels, Fig. 4b).
 //
-//   sizes      per survivor: shared prefix with its predecessor (the "shared keys part")
+//   sizes      per survivor: shared prefix with its predecessor (the prefix-compressed key)
 //              and its encoded size in delta form and in restart form
 //   block cut  the greedy builder rule "close the block once its size estimate reaches
 //              the block size" made parallel: next(i) (where a block starting at entry i

@@ -3,9 +3,8 @@
 Every version of every user key goes into a Python dict. Per key, the versions are taken
 newest first and LevelDB's compaction rule is applied directly: a version is dropped when
 a newer version of the same key is visible at the smallest snapshot, or when it is a
-tombstone visible at that snapshot and the job is bottommost (LUDA §II-A, Phase 2
-"(Delete and) Sort": "merges and sorts all key value pairs and drops those marked with
-delete"). The result is the expected entry list in output order.
+tombstone visible at that snapshot and the job is bottommost (LUDA §II-A, Phase 2: pairs
+are merged in key order and deleted or stale ones are removed). The result is the expected entry list in output order.
 """
 from __future__ import annotations
 
