@@ -599,6 +599,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     jd.flags = o->flags;
     jd.rec_begin = in_rec[job_in_first[j]];
     jd.rec_end = in_rec[job_in_first[j + 1]];
+    jd.in_first = job_in_first[j];
     const uint64_t nj = jd.rec_end - jd.rec_begin;
     const uint64_t kj = in_key[job_in_first[j + 1]] - in_key[job_in_first[j]];
     // Output bound: data <= K + V + 24n; index <= K + 31n + 9 per table; filter, metaindex and
@@ -944,6 +945,295 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
   return LUDA_OK;
 }
 
+
+// ---- plans: sized once, captured in one CUDA graph, replayed -------------------------------
+struct PlanImpl {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  uint32_t n_jobs = 0;
+  uint64_t launches = 0;
+  std::vector<void*> bufs;
+  // device state the collect step reads
+  Counts* d_cnt = nullptr;
+  JobDev* d_jobs = nullptr;
+  DErr* d_errs = nullptr;
+  PackBufs pb{};
+  uint8_t* d_out = nullptr;
+  bool ran = false;
+  ~PlanImpl() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (done) cudaEventDestroy(done);
+    if (st) cudaStreamSynchronize(st);
+    for (void* p : bufs) cudaFree(p);
+    if (st) cudaStreamDestroy(st);
+  }
+};
+
+luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options* o, PlanImpl* P) {
+  Fmt fmt;
+  luda_status rc = opts_check(o, &fmt);
+  if (rc) return rc;
+  CrcTabs tabs;
+  if ((rc = get_tabs(&tabs))) return rc;
+  CK(cudaGetDevice(&P->device));
+  CK(cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&P->done, cudaEventDisableTiming));
+  cudaStream_t st = P->st;
+  P->n_jobs = n_jobs;
+  auto alloc = [&](size_t n) -> uint8_t* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, n ? n : 256) != cudaSuccess) return nullptr;
+    P->bufs.push_back(p);
+    return static_cast<uint8_t*>(p);
+  };
+  // inputs
+  std::vector<DInput> hin;
+  std::vector<uint64_t> job_in_bytes(n_jobs, 0);
+  std::vector<uint32_t> job_in_first(n_jobs + 1, 0);
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    job_in_first[j] = uint32_t(hin.size());
+    if (jobs[j].n_inputs && !jobs[j].inputs) {
+      set_detail("job %u: inputs is NULL", j);
+      return LUDA_ERR_INVALID_ARG;
+    }
+    for (uint32_t i = 0; i < jobs[j].n_inputs; ++i) {
+      DInput d{};
+      d.data = jobs[j].inputs[i].data;
+      d.size = jobs[j].inputs[i].size;
+      if (!d.data && d.size) {
+        set_detail("job %u input %u: data is NULL", j, i);
+        return LUDA_ERR_INVALID_ARG;
+      }
+      d.job = j;
+      d.local = i;
+      hin.push_back(d);
+      job_in_bytes[j] += d.size;
+    }
+  }
+  job_in_first[n_jobs] = uint32_t(hin.size());
+  const uint32_t N = uint32_t(hin.size());
+  Layout LA;
+  DInput* d_in;
+  DErr* d_errs;
+  JobDev* d_jobs;
+  uint32_t *d_in_blk_first, *d_plan_nblk, *d_nrec_const;
+  Counts* d_cnt;
+  auto layA = [&](Layout& L) {
+    d_in = L.take<DInput>(N + 1);
+    d_errs = L.take<DErr>(n_jobs + 1);
+    d_jobs = L.take<JobDev>(n_jobs + 1);
+    d_in_blk_first = L.take<uint32_t>(N + 1);
+    d_plan_nblk = L.take<uint32_t>(N + 1);
+    d_nrec_const = L.take<uint32_t>(1);
+    d_cnt = L.take<Counts>(1);
+  };
+  layA(LA);
+  LA.base = alloc(LA.off);
+  if (!LA.base) return cuda_fail(cudaErrorMemoryAllocation, "plan allocation");
+  LA.off = 0;
+  layA(LA);
+  CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * (n_jobs + 1), st));
+  CK(cudaMemsetAsync(d_cnt, 0, sizeof(Counts), st));
+  if (N) CK(cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
+  launch_footers(d_in, N, d_errs, tabs, st);
+  if (N) CK(cudaMemcpyAsync(hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<uint32_t> in_blk_first(N + 1, 0), plan_nblk(N + 1, 0);
+  uint64_t NB64 = 0;
+  for (uint32_t i = 0; i < N; ++i) {
+    hin[i].blk_first = uint32_t(NB64);
+    in_blk_first[i] = uint32_t(NB64);
+    plan_nblk[i] = hin[i].nblk;
+    NB64 += hin[i].nblk;
+  }
+  in_blk_first[N] = uint32_t(NB64);
+  if (NB64 >= (1ull << 31)) {
+    set_detail("too many data blocks in one plan");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  const uint32_t NB = uint32_t(NB64);
+  if (N) {
+    CK(cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_in_blk_first, in_blk_first.data(), sizeof(uint32_t) * (N + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_plan_nblk, plan_nblk.data(), sizeof(uint32_t) * (N + 1), cudaMemcpyHostToDevice, st));
+  }
+  Layout LB;
+  BlockDesc* d_blocks;
+  uint32_t *d_nrec, *d_rec_first, *d_in_rec, *d_plan_nrec;
+  uint64_t *d_kbytes, *d_key_first, *d_in_key, *d_plan_kbytes;
+  uint16_t* d_hdr;
+  void* d_tmpB;
+  auto layB = [&](Layout& L) {
+    d_blocks = L.take<BlockDesc>(NB + 1);
+    d_hdr = L.take<uint16_t>(uint64_t(NB) * kHdrMax + 1);
+    d_nrec = L.take<uint32_t>(NB + 1);
+    d_kbytes = L.take<uint64_t>(NB + 1);
+    d_plan_nrec = L.take<uint32_t>(NB + 1);
+    d_plan_kbytes = L.take<uint64_t>(NB + 1);
+    d_rec_first = L.take<uint32_t>(NB + 1);
+    d_key_first = L.take<uint64_t>(NB + 1);
+    d_in_rec = L.take<uint32_t>(N + 1);
+    d_in_key = L.take<uint64_t>(N + 1);
+    d_tmpB = L.take<uint8_t>(scan_temp_bytes(NB + 1));
+  };
+  layB(LB);
+  LB.base = alloc(LB.off);
+  if (!LB.base) return cuda_fail(cudaErrorMemoryAllocation, "plan allocation");
+  LB.off = 0;
+  layB(LB);
+  launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
+  launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, tabs, st);
+  launch_zero_failed(d_blocks, NB, d_errs, d_nrec, d_kbytes, st);
+  if (NB) {
+    CK(cudaMemcpyAsync(d_plan_nrec, d_nrec, sizeof(uint32_t) * NB, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(d_plan_kbytes, d_kbytes, sizeof(uint64_t) * NB, cudaMemcpyDeviceToDevice, st));
+  }
+  CK((exclusive_scan<uint32_t, uint32_t>(d_nrec, d_rec_first, NB, nullptr, d_tmpB, st)));
+  CK((exclusive_scan<uint64_t, uint64_t>(d_kbytes, d_key_first, NB, nullptr, d_tmpB, st)));
+  launch_input_ranges(d_in, N, d_rec_first, d_key_first, d_in_rec, d_in_key, st);
+  CK(cudaGetLastError());
+  std::vector<uint32_t> in_rec(N + 1);
+  std::vector<uint64_t> in_key(N + 1);
+  CK(cudaMemcpyAsync(in_rec.data(), d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(in_key.data(), d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint32_t n_rec = in_rec[N];
+  const uint64_t K = in_key[N];
+  std::vector<JobDev> hjobs(n_jobs);
+  uint64_t out_cap = 4096, bm_cap = 64;
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    JobDev& jd = hjobs[j];
+    memset(&jd, 0, sizeof jd);
+    jd.snapshot = jobs[j].smallest_snapshot;
+    jd.bottommost = jobs[j].bottommost ? 1u : 0u;
+    jd.flags = o->flags;
+    jd.rec_begin = in_rec[job_in_first[j]];
+    jd.rec_end = in_rec[job_in_first[j + 1]];
+    jd.in_first = job_in_first[j];
+    const uint64_t nj = jd.rec_end - jd.rec_begin;
+    const uint64_t kj = in_key[job_in_first[j + 1]] - in_key[job_in_first[j]];
+    out_cap += 2 * kj + job_in_bytes[j] + 200 * nj + 256;
+    bm_cap += nj * fmt.bpk / 32 + 5 * nj + 8;
+  }
+  // merge schedule (as in run_compaction)
+  struct Run {
+    uint32_t b, n;
+  };
+  std::vector<std::vector<Run>> runs(n_jobs);
+  for (uint32_t j = 0; j < n_jobs; ++j)
+    for (uint32_t i = job_in_first[j]; i < job_in_first[j + 1]; ++i)
+      if (in_rec[i + 1] > in_rec[i]) runs[j].push_back(Run{in_rec[i], in_rec[i + 1] - in_rec[i]});
+  std::vector<MergeSpan> spans;
+  std::vector<uint32_t> pass_span0, pass_nspans, pass_ntiles;
+  uint32_t max_tiles = 1;
+  while (true) {
+    bool more = false;
+    for (auto& r : runs) more |= r.size() > 1;
+    if (!more) break;
+    pass_span0.push_back(uint32_t(spans.size()));
+    uint32_t tiles = 0;
+    for (auto& r : runs) {
+      std::vector<Run> nr;
+      for (size_t k = 0; k < r.size(); k += 2) {
+        MergeSpan sp{r[k].b, r[k].n, k + 1 < r.size() ? r[k + 1].n : 0u, tiles};
+        tiles += (sp.a_len + sp.b_len + kMergeTile - 1) / kMergeTile;
+        spans.push_back(sp);
+        nr.push_back(Run{sp.a_begin, sp.a_len + sp.b_len});
+      }
+      r.swap(nr);
+    }
+    pass_nspans.push_back(uint32_t(spans.size()) - pass_span0.back());
+    pass_ntiles.push_back(tiles);
+    if (tiles > max_tiles) max_tiles = tiles;
+  }
+  const uint32_t cap = n_rec;
+  Layout LC;
+  Recs recs;
+  uint8_t* d_arena;
+  uint32_t *d_ord0, *d_ord1, *d_keep, *d_pos, *d_co;
+  uint64_t *d_pfx0, *d_pfx1;
+  MergeSpan* d_spans;
+  PackBufs pb;
+  auto layC = [&](Layout& L) {
+    recs = recs_layout(L, n_rec);
+    d_arena = L.take<uint8_t>(K + 64);
+    d_ord0 = L.take<uint32_t>(n_rec + 1);
+    d_ord1 = L.take<uint32_t>(n_rec + 1);
+    d_pfx0 = L.take<uint64_t>(n_rec + 1);
+    d_pfx1 = L.take<uint64_t>(n_rec + 1);
+    d_keep = L.take<uint32_t>(n_rec + 1);
+    d_pos = L.take<uint32_t>(n_rec + 1);
+    d_co = L.take<uint32_t>(max_tiles + 1);
+    d_spans = L.take<MergeSpan>(spans.size() + 1);
+    pack_layout(L, pb, cap, bm_cap, 2 * K + 64);
+  };
+  layC(LC);
+  LC.base = alloc(LC.off);
+  if (!LC.base) return cuda_fail(cudaErrorMemoryAllocation, "plan allocation");
+  LC.off = 0;
+  layC(LC);
+  uint8_t* d_out = alloc(out_cap);
+  if (!d_out) return cuda_fail(cudaErrorMemoryAllocation, "plan allocation");
+  CK(cudaMemcpyAsync(d_jobs, hjobs.data(), sizeof(JobDev) * n_jobs, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_nrec_const, &n_rec, sizeof n_rec, cudaMemcpyHostToDevice, st));
+  if (!spans.empty())
+    CK(cudaMemcpyAsync(d_spans, spans.data(), sizeof(MergeSpan) * spans.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  // ---- capture the whole pipeline --------------------------------------------------------
+  const uint64_t l0 = g_launches.load();
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  auto body = [&]() -> luda_status {
+    CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * (n_jobs + 1), st));
+    CK(cudaMemsetAsync(d_cnt, 0, sizeof(Counts), st));
+    CK(cudaMemcpyAsync(&d_cnt->n_rec, d_nrec_const, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    launch_footers(d_in, N, d_errs, tabs, st);
+    launch_plan_checks(d_in, N, d_plan_nblk, d_errs, st);
+    launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
+    launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, tabs, st);
+    launch_plan_check_recs(d_blocks, NB, d_nrec, d_kbytes, d_plan_nrec, d_plan_kbytes, d_in, d_errs, st);
+    launch_decode(d_blocks, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
+    launch_plan_sanitize(recs, n_rec, d_jobs, n_jobs, d_errs, d_arena, st);
+    launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
+    launch_sort_init(d_ord0, d_pfx0, recs.pfx, n_rec, st);
+    uint32_t* src_o = d_ord0;
+    uint32_t* dst_o = d_ord1;
+    uint64_t* src_p = d_pfx0;
+    uint64_t* dst_p = d_pfx1;
+    for (size_t p = 0; p < pass_span0.size(); ++p) {
+      launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], d_co, src_o, src_p, dst_o, dst_p,
+                        recs, d_arena, st);
+      std::swap(src_o, dst_o);
+      std::swap(src_p, dst_p);
+    }
+    launch_gc_flags(src_o, n_rec, d_jobs, n_jobs, recs, d_arena, d_keep, d_errs, st);
+    CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
+    launch_gc_compact(src_o, d_keep, d_pos, n_rec, pb.surv, st);
+    launch_job_surv(d_jobs, n_jobs, d_pos, n_rec, d_cnt, st);
+    return run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap, tabs, st);
+  };
+  luda_status brc = body();
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(st, &g);
+  if (brc) {
+    if (g) cudaGraphDestroy(g);
+    return brc;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce, "stream capture");
+  P->graph = g;
+  CK(cudaGraphInstantiate(&P->exec, g, 0));
+  P->launches = g_launches.load() - l0;
+  P->d_cnt = d_cnt;
+  P->d_jobs = d_jobs;
+  P->d_errs = d_errs;
+  P->pb = pb;
+  P->d_out = d_out;
+  return LUDA_OK;
+}
+
 }  // namespace
 
 // =========================================================================================
@@ -1112,5 +1402,63 @@ luda_status luda_build_device(const luda_run* run, const luda_options* opts, lud
   if (!out) return LUDA_ERR_INVALID_ARG;
   return run_build(run, false, opts, out, false);
 }
+
+luda_status luda_plan_create(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts, luda_plan** plan) {
+  t_detail[0] = 0;
+  if (!plan || (!jobs && n_jobs) || !opts) {
+    set_detail("NULL argument");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  *plan = nullptr;
+  PlanImpl* P = new PlanImpl();
+  const luda_status rc = plan_build(jobs, n_jobs, opts, P);
+  if (rc) {
+    delete P;
+    return rc;
+  }
+  *plan = reinterpret_cast<luda_plan*>(P);
+  return LUDA_OK;
+}
+
+luda_status luda_plan_run(luda_plan* plan, void* stream) {
+  t_detail[0] = 0;
+  if (!plan) return LUDA_ERR_INVALID_ARG;
+  PlanImpl* P = reinterpret_cast<PlanImpl*>(plan);
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGraphLaunch(P->exec, st);
+  if (e == cudaSuccess) e = cudaEventRecord(P->done, st);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  g_launches.fetch_add(P->launches, std::memory_order_relaxed);
+  P->ran = true;
+  return LUDA_OK;
+}
+
+luda_status luda_plan_outputs(luda_plan* plan, luda_outputs* outs) {
+  t_detail[0] = 0;
+  if (!plan || !outs) return LUDA_ERR_INVALID_ARG;
+  PlanImpl* P = reinterpret_cast<PlanImpl*>(plan);
+  for (uint32_t j = 0; j < P->n_jobs; ++j) memset(&outs[j], 0, sizeof(luda_outputs));
+  if (!P->ran) {
+    set_detail("luda_plan_outputs before luda_plan_run");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaEventSynchronize(P->done);
+  if (e != cudaSuccess) return cuda_fail(e, "waiting for the plan");
+  Collected col;
+  luda_status rc = collect(P->d_cnt, P->d_jobs, P->d_errs, P->pb, P->n_jobs, &col, P->st);
+  if (rc) return rc;
+  if ((e = cudaStreamSynchronize(P->st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  Holder* h = new Holder();  // the plan owns the table memory; outputs only reference it
+  luda_status first = LUDA_OK;
+  for (uint32_t j = 0; j < P->n_jobs; ++j) {
+    outs[j].status = err_status(col.errs[j], j, P->n_jobs);
+    if (outs[j].status && !first) first = luda_status(outs[j].status);
+  }
+  fill_outputs(col, P->n_jobs, P->d_out, h, outs);
+  holder_release(h);
+  return LUDA_OK;
+}
+
+void luda_plan_destroy(luda_plan* plan) { delete reinterpret_cast<PlanImpl*>(plan); }
 
 }  // extern "C"

@@ -97,6 +97,11 @@ __global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs
     const DInput d = in[lo];
     const uint32_t k = uint32_t(g - in_blk_first[lo]);
     BlockDesc out{nullptr, 0, 0, lo, d.job};
+    if (k >= d.nblk) {  // only when a replayed plan sees fewer blocks than it was sized for
+      report(errs + d.job, E_PLAN, d.local, d.idx_off);
+      blocks[g] = out;
+      continue;
+    }
     const uint8_t* ib = d.data + d.idx_off;
     const uint64_t rstart = d.idx_size - 4 - 4ull * d.nblk;
     const uint64_t s = ld_u32(ib + rstart + 4ull * k);
@@ -426,7 +431,41 @@ __global__ void k_input_ranges(const DInput* __restrict__ in, uint32_t n_inputs,
   }
 }
 
+// Plans: a replay must see the block counts the plan was sized for.
+__global__ void k_plan_check_blocks(DInput* in, uint32_t n_inputs, const uint32_t* __restrict__ plan_nblk, DErr* errs) {
+  for (uint64_t i = gtid(); i < n_inputs; i += gstride())
+    if (in[i].nblk != plan_nblk[i]) {
+      report(errs + in[i].job, E_PLAN, in[i].local, in[i].size);
+      in[i].nblk = 0;
+    }
+}
+
+// ... and the entry and key-byte counts of every block.
+__global__ void k_plan_check_recs(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
+                                  const uint32_t* __restrict__ nrec, const uint64_t* __restrict__ kbytes,
+                                  const uint32_t* __restrict__ plan_nrec, const uint64_t* __restrict__ plan_kbytes,
+                                  const DInput* __restrict__ in, DErr* errs) {
+  for (uint64_t g = gtid(); g < n_blocks; g += gstride())
+    if (nrec[g] != plan_nrec[g] || kbytes[g] != plan_kbytes[g])
+      report(errs + blocks[g].job, E_PLAN, in[blocks[g].input].local, blocks[g].off);
+}
+
 }  // namespace
+
+void launch_plan_checks(DInput* in, uint32_t n_inputs, const uint32_t* plan_nblk, DErr* errs, cudaStream_t st) {
+  if (!n_inputs) return;
+  k_plan_check_blocks<<<grid_for(n_inputs, 128), 128, 0, st>>>(in, n_inputs, plan_nblk, errs);
+  count_launches(1);
+}
+
+void launch_plan_check_recs(const BlockDesc* blocks, uint32_t n_blocks, const uint32_t* nrec, const uint64_t* kbytes,
+                            const uint32_t* plan_nrec, const uint64_t* plan_kbytes, const DInput* in, DErr* errs,
+                            cudaStream_t st) {
+  if (!n_blocks) return;
+  k_plan_check_recs<<<grid_for(n_blocks, 256), 256, 0, st>>>(blocks, n_blocks, nrec, kbytes, plan_nrec, plan_kbytes,
+                                                             in, errs);
+  count_launches(1);
+}
 
 void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cudaStream_t st) {
   if (!n_inputs) return;

@@ -39,6 +39,8 @@ struct JobDev {
   uint32_t file_begin, file_end;  // output tables (device)
   uint64_t n_in;                  // entries decoded
   uint64_t out_bytes;             // bytes of this job's tables (device)
+  uint32_t in_first;              // first global input index of the job
+  uint32_t pad;
 };
 
 struct FileDesc {
@@ -124,6 +126,11 @@ void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in,
 void launch_input_ranges(const DInput* in, uint32_t n_inputs, const uint32_t* rec_first,
                          const uint64_t* key_first, uint32_t* in_rec, uint64_t* in_key, cudaStream_t st);
 
+void launch_plan_checks(DInput* in, uint32_t n_inputs, const uint32_t* plan_nblk, DErr* errs, cudaStream_t st);
+void launch_plan_check_recs(const BlockDesc* blocks, uint32_t n_blocks, const uint32_t* nrec, const uint64_t* kbytes,
+                            const uint32_t* plan_nrec, const uint64_t* plan_kbytes, const DInput* in, DErr* errs,
+                            cudaStream_t st);
+
 // ---- sort.cu -----------------------------------------------------------------------------
 struct MergeSpan {
   uint32_t a_begin;  // first position of run A (run B follows it)
@@ -135,6 +142,8 @@ constexpr uint32_t kMergeTile = 1024;
 
 void launch_check_order(Recs recs, const uint8_t* arena, uint32_t n_rec, const DInput* in, DErr* errs,
                         cudaStream_t st);
+void launch_plan_sanitize(Recs recs, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, const DErr* errs,
+                          const uint8_t* arena, cudaStream_t st);
 void launch_sort_init(uint32_t* ord, uint64_t* opfx, const uint64_t* pfx, uint32_t n, cudaStream_t st);
 void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* corank,
                        const uint32_t* src_ord, const uint64_t* src_pfx, uint32_t* dst_ord, uint64_t* dst_pfx,

@@ -200,7 +200,31 @@ __global__ void k_job_surv(JobDev* jobs, uint32_t n_jobs, const uint32_t* __rest
   if (gtid() == 0) cnt->n_surv = pos[n_rec];
 }
 
+// Plans: records of a job that failed before decode are left undefined; give them a
+// harmless value (an 8-byte key at arena offset 0, no value) so later kernels stay in bounds.
+__global__ void k_plan_sanitize(Recs recs, uint32_t n_rec, const JobDev* __restrict__ jobs, uint32_t n_jobs,
+                                const DErr* errs, const uint8_t* __restrict__ arena) {
+  for (uint64_t p = gtid(); p < n_rec; p += gstride()) {
+    const uint32_t j = find_job(jobs, n_jobs, uint32_t(p), false);
+    if (errs[j].code == 0) continue;
+    recs.pfx[p] = 0;
+    recs.koff[p] = 0;
+    recs.klen[p] = 8;
+    recs.tr[p] = 0;
+    recs.vptr[p] = reinterpret_cast<uint64_t>(arena);
+    recs.vlen[p] = 0;
+    recs.src[p] = jobs[j].in_first;
+  }
+}
+
 }  // namespace
+
+void launch_plan_sanitize(Recs recs, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, const DErr* errs,
+                          const uint8_t* arena, cudaStream_t st) {
+  if (!n_rec) return;
+  k_plan_sanitize<<<grid_for(n_rec, 256), 256, 0, st>>>(recs, n_rec, jobs, n_jobs, errs, arena);
+  count_launches(1);
+}
 
 void launch_check_order(Recs recs, const uint8_t* arena, uint32_t n_rec, const DInput* in, DErr* errs,
                         cudaStream_t st) {

@@ -239,23 +239,70 @@ def free_outputs(out: Outputs) -> None:
 
 def batch_compact_device(jobs, opts: Options | None = None, copy_out: bool = True):
     """jobs: list of (inputs: [torch CUDA uint8 tensors], smallest_snapshot, bottommost)."""
-    ins_keep = []
-    js = (Job * max(1, len(jobs)))()
-    for j, (inputs, snap, bottom) in enumerate(jobs):
-        ins = (Input * max(1, len(inputs)))()
-        for i, t in enumerate(inputs):
-            ins[i].data, ins[i].size = t.data_ptr(), t.numel()
-        ins_keep.append(ins)
-        js[j].inputs = C.cast(ins, C.POINTER(Input))
-        js[j].n_inputs, js[j].smallest_snapshot, js[j].bottommost = len(inputs), snap, int(bool(bottom))
+    js, keep = _jobs_array(jobs)
     o = opts or options()
     if o.stream is None:
         o.stream = current_stream()
     outs = (Outputs * max(1, len(jobs)))()
     rc = lib().luda_batch_compact_device(js, len(jobs), C.byref(o), outs)
+    del keep
     if not copy_out:
         return rc, outs
     return rc, [_take(rc, outs[j], device=True) for j in range(len(jobs))]
+
+
+def _jobs_array(jobs):
+    """jobs: list of (inputs: [torch CUDA uint8 tensors], smallest_snapshot, bottommost)."""
+    keep = []
+    js = (Job * max(1, len(jobs)))()
+    for j, (inputs, snap, bottom) in enumerate(jobs):
+        ins = (Input * max(1, len(inputs)))()
+        for i, t in enumerate(inputs):
+            ins[i].data, ins[i].size = t.data_ptr(), t.numel()
+        keep.append(ins)
+        js[j].inputs = C.cast(ins, C.POINTER(Input))
+        js[j].n_inputs, js[j].smallest_snapshot, js[j].bottommost = len(inputs), snap, int(bool(bottom))
+    return js, keep
+
+
+class Plan:
+    """A batch of jobs sized once and captured in a CUDA graph (luda_plan_*). The input
+    tensors must stay alive and unchanged in size while the plan exists."""
+
+    def __init__(self, jobs, opts: Options | None = None):
+        self._js, self._keep = _jobs_array(jobs)
+        self._inputs = [t for inputs, _, _ in jobs for t in inputs]
+        self.n_jobs = len(jobs)
+        self.opts = opts or options()
+        self.handle = C.c_void_p()
+        rc = lib().luda_plan_create(self._js, len(jobs), C.byref(self.opts), C.byref(self.handle))
+        if rc != OK:
+            raise RuntimeError(f"luda_plan_create: {strerror(rc)}: {last_error_detail()}")
+
+    def run(self, stream=None) -> None:
+        rc = lib().luda_plan_run(self.handle, stream if stream is not None else current_stream())
+        if rc != OK:
+            raise RuntimeError(f"luda_plan_run: {strerror(rc)}: {last_error_detail()}")
+
+    def outputs(self, copy_out: bool = True):
+        outs = (Outputs * max(1, self.n_jobs))()
+        rc = lib().luda_plan_outputs(self.handle, outs)
+        if rc != OK:
+            raise RuntimeError(f"luda_plan_outputs: {strerror(rc)}: {last_error_detail()}")
+        if not copy_out:
+            return outs
+        return [_take(OK, outs[j], device=True) for j in range(self.n_jobs)]
+
+    def close(self) -> None:
+        if self.handle:
+            lib().luda_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _run_arrays(run, device: bool):
