@@ -254,9 +254,122 @@ def run_ours(args, ws, rank, local):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if not args.no_batched:
+        line["batched"] = batched(args, stream)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
+
+
+def batched(args, stream):
+    """The batched workload: 256 independent jobs (per-job input lognormal 256 KiB-64 MiB,
+    16-32 B keys, 32 B-4 KiB values, 4 KiB blocks, 2 MiB tables), run three ways on the
+    same device-resident inputs: one luda_compact_device call per job (the plain per-job
+    launch), one luda_batch_compact_device call for all jobs, and a plan (sized once,
+    captured in one CUDA graph) replayed. Reports input MiB/s for each and, for the
+    per-job launch, p50/p99 job latency."""
+    import torch
+    from paper_2004_03054_b300 import luda
+    from paper_2004_03054_b300 import workloads as W
+
+    L = luda.lib()
+    jobs = W.config4(seed=4, scale=args.batch_scale, n_jobs=args.batch_jobs)
+    o = jobs[0]
+    dev_jobs = []
+    for job in jobs:
+        ins = []
+        for r in job.inputs:
+            res = luda.build_device(r, luda.options(o.block_size, o.restart_interval, o.bloom_bits_per_key,
+                                                    (1 << 64) - 1))
+            if res.status != 0 or len(res.tables) != 1:
+                raise RuntimeError(f"input build failed: {res.status} {res.detail}")
+            ins.append(res.tables[0])
+        dev_jobs.append((ins, job.smallest_snapshot, job.bottommost))
+    in_bytes = sum(t.numel() for ins, _, _ in dev_jobs for t in ins)
+    opts = luda.options(o.block_size, o.restart_interval, o.bloom_bits_per_key, o.target_file_size,
+                        stream=C.c_void_p(stream.cuda_stream))
+    arrays = []
+    for ins, _, _ in dev_jobs:
+        a = (luda.Input * len(ins))()
+        for i, t in enumerate(ins):
+            a[i].data, a[i].size = t.data_ptr(), t.numel()
+        arrays.append(a)
+
+    def per_job(lat=None):
+        for j, (ins, snap, bottom) in enumerate(dev_jobs):
+            if lat is not None:
+                ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev[0].record(stream)
+            out = luda.Outputs()
+            jo = luda.Options.from_buffer_copy(opts)
+            jo.bottommost = int(bool(bottom))
+            rc = L.luda_compact_device(arrays[j], len(ins), o.level, snap, C.byref(jo), C.byref(out))
+            if rc != 0:
+                raise RuntimeError(f"job {j}: {rc} {luda.last_error_detail()}")
+            L.luda_outputs_free(C.byref(out))
+            if lat is not None:
+                ev[1].record(stream)
+                lat.append(ev)
+
+    js, keep = luda._jobs_array(dev_jobs)
+    outs = (luda.Outputs * len(dev_jobs))()
+
+    def batch():
+        rc = L.luda_batch_compact_device(js, len(dev_jobs), C.byref(opts), outs)
+        if rc != 0:
+            raise RuntimeError(f"batch: {rc} {luda.last_error_detail()}")
+        for j in range(len(dev_jobs)):
+            if outs[j].status != 0:
+                raise RuntimeError(f"batch job {j}: {outs[j].status}")
+            L.luda_outputs_free(C.byref(outs[j]))
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    k, w = args.batch_steps, max(1, args.batch_warmup)
+    l0 = luda.launch_count()
+    for _ in range(w):
+        per_job()
+    lat = []
+    ms_job = timed(lambda: per_job(lat), k)
+    lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
+    for _ in range(w):
+        batch()
+    ms_batch = timed(batch, k)
+    plan = luda.Plan(dev_jobs, opts)
+    for _ in range(w):
+        plan.run(C.c_void_p(stream.cuda_stream))
+    c0 = luda.launch_count()
+    ms_plan = timed(lambda: plan.run(C.c_void_p(stream.cuda_stream)), k)
+    plan_launches = (luda.launch_count() - c0) // k
+    pouts = plan.outputs(copy_out=False)
+    bad = [j for j in range(len(dev_jobs)) if pouts[j].status != 0]
+    plan.close()
+    if bad:
+        raise RuntimeError(f"plan jobs failed: {bad[:5]}")
+    del keep
+
+    def q(p):
+        return round(lat_ms[min(len(lat_ms) - 1, int(p * len(lat_ms)))], 3)
+
+    mib = in_bytes / MiB
+    return {"workload": f"cfg4_batched: {len(dev_jobs)} jobs, input lognormal 256 KiB-64 MiB per job "
+                        "(16-32 B keys, 32 B-4 KiB values, 4 KiB blocks, 2 MiB tables)",
+            "jobs": len(dev_jobs), "input_bytes": in_bytes, "steps": k, "warmup": w,
+            "per_job": {"value": round(mib / (ms_job / 1e3), 1), "unit": "MiB/s", "ms_per_step": round(ms_job, 3),
+                        "job_latency_ms": {"p50": q(0.50), "p99": q(0.99), "max": round(lat_ms[-1], 3)}},
+            "batch_call": {"value": round(mib / (ms_batch / 1e3), 1), "unit": "MiB/s",
+                           "ms_per_step": round(ms_batch, 3)},
+            "plan_replay": {"value": round(mib / (ms_plan / 1e3), 1), "unit": "MiB/s",
+                            "ms_per_step": round(ms_plan, 3), "gpu_launches_per_replay": plan_launches},
+            "gpu_launches_total": luda.launch_count() - l0}
 
 
 def cpu_baseline(args):
@@ -338,6 +451,11 @@ def main():
     ap.add_argument("--ref-scale", type=float, default=1 / 16)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-jobs", type=int, default=256)
+    ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--batch-warmup", type=int, default=3)
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture (reported as is)")
     args = ap.parse_args()
