@@ -256,6 +256,8 @@ def run_ours(args, ws, rank, local):
     }
     if not args.no_batched:
         line["batched"] = batched(args, stream)
+    if not args.no_served:
+        line["served"] = served(args)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
@@ -372,6 +374,36 @@ def batched(args, stream):
             "gpu_launches_total": luda.launch_count() - l0}
 
 
+def served(args):
+    """The served workload: a simulated 7-level LSM tree (64 MiB memtables, L0 trigger 4,
+    fanout 10, 64 MiB tables, 4 KiB blocks) fed by a seeded Poisson write stream (16 B
+    keys, half uniform and half zipf(0.99), 256 B values). Compaction jobs go to a
+    luda_server with continuous batching under a 40 GB HBM budget; the same stream is then
+    served by a one-slot server (the plain per-job launch, first in first out). Reports
+    compaction input MiB/s over the run's wall time and p50/p99 job latency."""
+    from paper_2004_03054_b300 import lsm as L
+    from paper_2004_03054_b300 import workloads as W
+
+    out = {"workload": f"cfg5_served: {args.serve_memtables} memtables of 64 MiB, Poisson writes at "
+                       f"{args.serve_rate:.0f}/s, 16 B keys (50% uniform, 50% zipf 0.99), 256 B values, "
+                       "L0 trigger 4, fanout 10, 64 MiB tables, 40 GB budget"}
+    for name, slots in (("continuous", args.serve_slots), ("per_job_fifo", 1)):
+        stream = W.config5_stream(seed=5, n_memtables=args.serve_memtables, write_rate=args.serve_rate)
+        rep = L.serve(stream, n_slots=slots, hbm_budget=40 * 10**9, pace=True)
+        out[name] = {"slots": slots, "jobs": rep.jobs, "failed": rep.failed,
+                     "value": round(rep.compaction_in_bytes / MiB / rep.wall_s, 1), "unit": "MiB/s",
+                     "wall_s": round(rep.wall_s, 3), "compaction_in_bytes": rep.compaction_in_bytes,
+                     "written_bytes": rep.written_bytes,
+                     "job_latency_ms": {"p50": round(rep.pct(0.5), 3), "p99": round(rep.pct(0.99), 3),
+                                        "max": round(max(rep.latencies_ms, default=0), 3)},
+                     "admit_wait_ms_p99": round(sorted(rep.admit_wait_ms)[int(0.99 * (len(rep.admit_wait_ms) - 1))]
+                                                if rep.admit_wait_ms else 0, 3),
+                     "running_peak": rep.running_peak, "budget_peak_bytes": rep.budget_peak,
+                     "write_stall_s": round(rep.stall_s, 3),
+                     "level_bytes": rep.level_bytes}
+    return out
+
+
 def cpu_baseline(args):
     """The oracle as it stands, single-threaded, on the same job (one full run)."""
     import oracle
@@ -452,6 +484,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--serve-memtables", type=int, default=40)
+    ap.add_argument("--serve-rate", type=float, default=8e6, help="writes per second of the served stream")
+    ap.add_argument("--serve-slots", type=int, default=6)
     ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--batch-steps", type=int, default=5)

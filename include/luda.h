@@ -165,6 +165,66 @@ LUDA_API luda_status luda_plan_run(luda_plan* plan, void* stream);
 LUDA_API luda_status luda_plan_outputs(luda_plan* plan, luda_outputs* outs);
 LUDA_API void luda_plan_destroy(luda_plan* plan);
 
+/* ---- serving: continuous batching of compaction jobs ----------------------------------
+ * A server takes compaction jobs as they arise (for example from an LSM tree whose tables
+ * stay resident in device memory) and runs up to n_slots of them at once, each on its own
+ * CUDA stream driven by its own host thread, so that the jobs' kernels overlap on the GPU.
+ * A job that a slot has taken first runs its sizing pass (footers, index, block scan);
+ * it is then admitted only when the device bytes it will hold at its peak fit in
+ * hbm_budget together with those of the jobs already admitted. Admission is first come,
+ * first served; a job larger than the whole budget is admitted once no other job holds
+ * any. The sizing pass's own buffers (well under 1% of the inputs for blocks of 4 KiB or
+ * more) are not counted. A job's new tables (device memory) leave the budget when it
+ * completes; the caller owns them from luda_server_wait on.
+ *
+ * Results do not depend on the mix: each job's tables are byte-identical to those of
+ * luda_compact_device on the same inputs.
+ *
+ * luda_server_submit copies the job description (the luda_input array too); the input
+ * tables themselves must stay valid until the job completes. luda_server_next returns the
+ * ticket of a completed job that no luda_server_next has returned yet (LUDA_ERR_TIMEOUT if
+ * none completes within timeout_ms; timeout_ms < 0 waits without limit).
+ * luda_server_wait waits for one ticket (same timeout rule), moves its tables into *out
+ * (free with luda_outputs_free) and fills *stats (may be NULL); the ticket is then gone.
+ * It returns the job's status, or LUDA_ERR_TIMEOUT when the job has not completed in
+ * time (the ticket then stays valid; no job itself ends with LUDA_ERR_TIMEOUT). luda_server_destroy waits for every submitted job to
+ * complete, frees the tables no one collected and ends the slots' threads. Submit, next
+ * and wait may be called from any host thread. */
+typedef struct luda_server luda_server;
+
+typedef struct {
+  uint32_t n_slots;        /* jobs that may run at once (1..64) */
+  uint64_t hbm_budget;     /* device bytes the admitted jobs may hold at once (> 0) */
+  luda_options opts;       /* format options of every job; opts.stream is ignored and
+                              opts.bottommost is replaced by each job's own flag */
+} luda_server_config;
+
+typedef struct {
+  double queue_ms;         /* submit -> a slot took the job */
+  double admit_wait_ms;    /* end of sizing -> admitted */
+  double run_ms;           /* a slot took the job -> completed */
+  double latency_ms;       /* submit -> completed */
+  uint64_t reserved_bytes; /* peak device bytes the job was admitted with */
+  uint64_t input_bytes;    /* sum of the job's input table sizes */
+  uint32_t slot;           /* the slot (stream) that ran it */
+  uint32_t running_at_admit; /* admitted jobs, this one included, when it was admitted */
+} luda_job_stats;
+
+typedef struct {
+  uint64_t submitted, completed, failed;
+  uint64_t budget_peak;    /* highest sum of admitted jobs' reserved bytes */
+  uint32_t running_peak;   /* most jobs admitted at once */
+  uint32_t pad;
+} luda_server_stats;
+
+LUDA_API luda_status luda_server_create(const luda_server_config* cfg, luda_server** server);
+LUDA_API luda_status luda_server_submit(luda_server* server, const luda_job* job, uint64_t* ticket);
+LUDA_API luda_status luda_server_next(luda_server* server, int64_t timeout_ms, uint64_t* ticket);
+LUDA_API luda_status luda_server_wait(luda_server* server, uint64_t ticket, int64_t timeout_ms, luda_outputs* out,
+                                      luda_job_stats* stats);
+LUDA_API luda_status luda_server_stats_get(luda_server* server, luda_server_stats* stats);
+LUDA_API void luda_server_destroy(luda_server* server);
+
 /* ---- table builder (memtable flush) ---------------------------------------------------
  * Packs one run of entries already in increasing internal-key order (user key ascending;
  * for equal user keys, sequence descending) into tables, cutting files at the target

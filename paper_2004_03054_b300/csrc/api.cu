@@ -446,7 +446,7 @@ struct Timer {
 // outs[j] hold device (or, with host_out, pinned host) tables.
 luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_options* o, cudaStream_t st,
                            luda_outputs* outs, bool host_out, double* ms_device, double* ms_d2h,
-                           double* stage_ms = nullptr, uint64_t* stage_bytes = nullptr) {
+                           double* stage_ms = nullptr, uint64_t* stage_bytes = nullptr, AdmitGate* gate = nullptr) {
   Fmt fmt;
   luda_status rc = opts_check(o, &fmt);
   if (rc) return rc;
@@ -663,6 +663,10 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     pack_layout(L, pb, cap, bm_cap, key_cap);
   };
   layoutC(LC);
+  if (gate && !gate->admit(LA.off + LB.off + LC.off + out_cap)) {
+    set_detail("the job was not admitted (server shutting down)");
+    return LUDA_ERR_OOM;
+  }
   uint8_t* bufC = static_cast<uint8_t*>(mem.get(LC.off));
   if (!bufC) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
   guard.ps.push_back(bufC);
@@ -1235,6 +1239,31 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
 }
 
 }  // namespace
+
+luda_status luda::compact_job_device(const luda_job& job, const luda_options* opts, luda_outputs* out,
+                                     AdmitGate* gate) {
+  t_detail[0] = 0;
+  if (!out || (!job.inputs && job.n_inputs) || !opts) {
+    set_detail("NULL argument");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  HostJob hj{job.inputs, job.n_inputs, job.smallest_snapshot, job.bottommost};
+  const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+  double ms = 0;
+  luda_status rc = run_compaction(&hj, 1, opts, st, out, false, &ms, nullptr, out->stage_ms, out->stage_bytes, gate);
+  if (rc) {
+    out->status = rc;
+    return rc;
+  }
+  out->ms_device = ms;
+  if (out->status) {
+    const luda_status s = luda_status(out->status);
+    luda_outputs_free(out);
+    out->status = s;
+    return s;
+  }
+  return LUDA_OK;
+}
 
 // =========================================================================================
 extern "C" {

@@ -6,6 +6,7 @@
 
 #include "common.cuh"
 #include "crc.cuh"
+#include "luda.h"
 
 namespace luda {
 
@@ -205,5 +206,17 @@ void launch_build_records(const uint8_t* ukeys, const uint64_t* ukoff, const uin
                           const uint8_t* vals, const uint64_t* voff, uint32_t n, Recs recs, uint8_t* arena,
                           uint32_t* surv, DErr* err, cudaStream_t st);
 void launch_build_check(Recs recs, const uint8_t* arena, uint32_t n, DErr* err, cudaStream_t st);
+
+// ---- host runtime ------------------------------------------------------------------------
+// Admission hook of a compaction: called once per call, after the sizing pass and before
+// the large allocations, with the device bytes the call holds at its peak (sizing buffers,
+// records and sort buffers, output arena). It may block; false abandons the call.
+struct AdmitGate {
+  virtual bool admit(uint64_t bytes) = 0;
+  virtual ~AdmitGate() = default;
+};
+
+// One job on opts->stream with device inputs (luda_compact_device plus an admission gate).
+luda_status compact_job_device(const luda_job& job, const luda_options* opts, luda_outputs* out, AdmitGate* gate);
 
 }  // namespace luda

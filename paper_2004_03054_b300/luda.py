@@ -57,6 +57,21 @@ class Job(C.Structure):
                 ("smallest_snapshot", C.c_uint64), ("bottommost", C.c_int32)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("n_slots", C.c_uint32), ("hbm_budget", C.c_uint64), ("opts", Options)]
+
+
+class JobStats(C.Structure):
+    _fields_ = [("queue_ms", C.c_double), ("admit_wait_ms", C.c_double), ("run_ms", C.c_double),
+                ("latency_ms", C.c_double), ("reserved_bytes", C.c_uint64), ("input_bytes", C.c_uint64),
+                ("slot", C.c_uint32), ("running_at_admit", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("budget_peak", C.c_uint64), ("running_peak", C.c_uint32), ("pad", C.c_uint32)]
+
+
 class TableCheck(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_blocks", C.c_uint32), ("n_entries", C.c_uint64),
                 ("data_bytes", C.c_uint64), ("bad_offset", C.c_uint64)]
@@ -98,15 +113,25 @@ def lib():
         L.luda_launch_count.restype = C.c_uint64
         L.luda_check_table_noalloc.restype = st
         L.luda_check_table_noalloc.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(TableCheck)]
-        for name in ("luda_plan_create", "luda_plan_run", "luda_plan_outputs", "luda_plan_destroy"):
-            if hasattr(L, name):
-                getattr(L, name).restype = st
-        if hasattr(L, "luda_plan_create"):
-            L.luda_plan_create.argtypes = [C.POINTER(Job), C.c_uint32, C.POINTER(Options), C.POINTER(C.c_void_p)]
-            L.luda_plan_run.argtypes = [C.c_void_p, C.c_void_p]
-            L.luda_plan_outputs.argtypes = [C.c_void_p, C.POINTER(Outputs)]
-            L.luda_plan_destroy.argtypes = [C.c_void_p]
-            L.luda_plan_destroy.restype = None
+        for name in ("luda_plan_create", "luda_plan_run", "luda_plan_outputs"):
+            getattr(L, name).restype = st
+        L.luda_plan_create.argtypes = [C.POINTER(Job), C.c_uint32, C.POINTER(Options), C.POINTER(C.c_void_p)]
+        L.luda_plan_run.argtypes = [C.c_void_p, C.c_void_p]
+        L.luda_plan_outputs.argtypes = [C.c_void_p, C.POINTER(Outputs)]
+        L.luda_plan_destroy.argtypes = [C.c_void_p]
+        L.luda_plan_destroy.restype = None
+        L.luda_server_create.restype = st
+        L.luda_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]
+        L.luda_server_submit.restype = st
+        L.luda_server_submit.argtypes = [C.c_void_p, C.POINTER(Job), C.POINTER(C.c_uint64)]
+        L.luda_server_next.restype = st
+        L.luda_server_next.argtypes = [C.c_void_p, C.c_int64, C.POINTER(C.c_uint64)]
+        L.luda_server_wait.restype = st
+        L.luda_server_wait.argtypes = [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(Outputs), C.POINTER(JobStats)]
+        L.luda_server_stats_get.restype = st
+        L.luda_server_stats_get.argtypes = [C.c_void_p, C.POINTER(ServerStats)]
+        L.luda_server_destroy.restype = None
+        L.luda_server_destroy.argtypes = [C.c_void_p]
         _lib = L
     return _lib
 
@@ -297,6 +322,82 @@ class Plan:
         if self.handle:
             lib().luda_plan_destroy(self.handle)
             self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching of compaction jobs (luda_server_*): up to n_slots jobs run at
+    once, each on its own stream, admitted under an HBM budget. Input tables are CUDA
+    uint8 tensors (or (device pointer, size) pairs) that must stay alive until their job
+    completes; the server keeps a reference to tensors until the job is collected."""
+
+    def __init__(self, n_slots: int, hbm_budget: int, opts: Options | None = None):
+        cfg = ServerConfig()
+        cfg.n_slots, cfg.hbm_budget = n_slots, hbm_budget
+        cfg.opts = opts or options()
+        self.handle = C.c_void_p()
+        rc = lib().luda_server_create(C.byref(cfg), C.byref(self.handle))
+        if rc != OK:
+            raise RuntimeError(f"luda_server_create: {strerror(rc)}: {last_error_detail()}")
+        self._keep = {}
+
+    def submit(self, inputs, smallest_snapshot: int = MAX_SEQ, bottommost: bool = False, level: int = 1) -> int:
+        ins = (Input * max(1, len(inputs)))()
+        for i, t in enumerate(inputs):
+            if isinstance(t, tuple):
+                ins[i].data, ins[i].size = t
+            else:
+                ins[i].data, ins[i].size = t.data_ptr(), t.numel()
+        job = Job()
+        job.inputs = C.cast(ins, C.POINTER(Input))
+        job.n_inputs, job.level = len(inputs), level
+        job.smallest_snapshot, job.bottommost = smallest_snapshot, int(bool(bottommost))
+        ticket = C.c_uint64()
+        rc = lib().luda_server_submit(self.handle, C.byref(job), C.byref(ticket))
+        if rc != OK:
+            raise RuntimeError(f"luda_server_submit: {strerror(rc)}: {last_error_detail()}")
+        self._keep[ticket.value] = list(inputs)
+        return ticket.value
+
+    def next(self, timeout_ms: int = -1):
+        """Ticket of a completed, not yet announced job, or None on timeout."""
+        t = C.c_uint64()
+        rc = lib().luda_server_next(self.handle, timeout_ms, C.byref(t))
+        if rc == ERR_TIMEOUT:
+            return None
+        if rc != OK:
+            raise RuntimeError(f"luda_server_next: {strerror(rc)}")
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1, copy_out: bool = True):
+        """(Result or raw Outputs, JobStats) of a job; the ticket is then gone."""
+        if ticket not in self._keep:
+            raise KeyError(f"unknown or already collected ticket {ticket}")
+        out, stats = Outputs(), JobStats()
+        rc = lib().luda_server_wait(self.handle, ticket, timeout_ms, C.byref(out), C.byref(stats))
+        if rc == ERR_TIMEOUT:
+            raise TimeoutError(f"ticket {ticket} not done")
+        self._keep.pop(ticket, None)
+        if not copy_out:
+            out.status = rc
+            return out, stats
+        return _take(rc, out, device=True), stats
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        lib().luda_server_stats_get(self.handle, C.byref(st))
+        return st
+
+    def close(self) -> None:
+        if self.handle:
+            lib().luda_server_destroy(self.handle)
+            self.handle = C.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -22,6 +22,9 @@ Configs (sizes at ``scale=1``):
     1 KiB values; 10% overwrites; 3% deletions; 16 KiB blocks, 64 MiB files.
   4 batch of 256 jobs, per-job input lognormal (median 4 MiB, sigma 1.2) clipped to
     [256 KiB, 64 MiB]; 16-32 B keys; 32 B-4 KiB values; 10% overwrites; 3% deletions.
+  5 served: a write stream for a simulated LSM tree (``config5_stream``): Poisson
+    arrivals, 16 B keys (half uniform, half zipf(0.99) over a 2^24-key universe), 256 B
+    values, no deletions, cut into 64 MiB memtables.
 """
 from __future__ import annotations
 
@@ -295,6 +298,49 @@ def config4(seed: int = 4, scale: float = 1.0, n_jobs: int = 256) -> list:
     sizes = np.clip(sizes, 256 * 1024, 64 * MiB) * scale
     sizes = np.maximum(sizes, 16 * 1024).astype(np.int64)
     return [config4_job(rng, int(s), f"cfg4_job{j}", seed) for j, s in enumerate(sizes.tolist())]
+
+
+@dataclass
+class Memtable:
+    """One memtable's worth of writes in arrival order. User key i is
+    u64_be(hi[i]) || u64_be(lo[i]); sequence numbers increase with arrival; every write is a
+    put of a 256-byte value (the values themselves are drawn by the consumer, e.g. as
+    slices of a random pool)."""
+    t_full: float        # stream time (s) at which the memtable is full
+    hi: np.ndarray       # uint64 [n]
+    lo: np.ndarray       # uint64 [n]
+    seqs: np.ndarray     # uint64 [n]
+    value_len: int = 256
+
+    @property
+    def n(self) -> int:
+        return len(self.seqs)
+
+
+def config5_stream(seed: int = 5, n_memtables: int = 24, memtable_bytes: int = 64 * MiB,
+                   write_rate: float = 8e6, value_len: int = 256, universe_bits: int = 24, zipf_s: float = 0.99,
+                   first_seq: int = 1):
+    """Seeded Poisson write stream (rate `write_rate` writes/s) cut into memtables of
+    `memtable_bytes` (key + value + 8 bytes of sequence/type per write). Half of the keys
+    are uniform 16-byte strings, half are zipf(`zipf_s`) draws over 2^universe_bits keys
+    u64_be(splitmix64(r)) || u64_be(r)."""
+    rng = np.random.default_rng(seed)
+    per = max(1, memtable_bytes // (16 + value_len + 8))
+    cdf = _zipf_cdf(1 << universe_bits, zipf_s)
+    t, seq = 0.0, first_seq
+    for _ in range(n_memtables):
+        t += float(rng.gamma(per, 1.0 / write_rate))   # sum of `per` exponential gaps
+        hi = rng.integers(0, 1 << 63, size=per, dtype=np.uint64) * np.uint64(2) + \
+            rng.integers(0, 2, size=per, dtype=np.uint64)
+        lo = rng.integers(0, 1 << 63, size=per, dtype=np.uint64) * np.uint64(2) + \
+            rng.integers(0, 2, size=per, dtype=np.uint64)
+        z = rng.random(per) < 0.5
+        r = np.searchsorted(cdf, rng.random(int(z.sum()))).astype(np.uint64)
+        hi[z] = _splitmix64(r)
+        lo[z] = r
+        seqs = np.arange(seq, seq + per, dtype=np.uint64)
+        seq += per
+        yield Memtable(t, hi, lo, seqs, value_len)
 
 
 CONFIGS = {1: config1, 2: config2, 3: config3}
