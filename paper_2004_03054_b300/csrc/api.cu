@@ -226,6 +226,8 @@ luda_status err_status(const DErr& e, uint32_t job, uint32_t n_jobs) {
 struct PackBufs {
   uint32_t *surv, *lcp, *sd, *dr, *next, *bpos, *blk_start, *fnext, *fpos, *file_start, *blk_file, *ie;
   uint8_t *sflags, *fflags, *enc_done;
+  EncDesc* ed;
+  uint32_t* big;
   uint64_t *P, *bsz, *disk, *C, *IX, *fsize, *foff, *bmw, *bmoff, *klens, *koff;
   FileDesc* files;
   FileMeta* meta;
@@ -250,6 +252,8 @@ void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t
   b.sflags = L.take<uint8_t>(cap + 1);
   b.fflags = L.take<uint8_t>(cap + 1);
   b.enc_done = L.take<uint8_t>(cap + 1);
+  b.ed = L.take<EncDesc>(cap + 1);
+  b.big = L.take<uint32_t>(cap + 1);
   b.P = L.take<uint64_t>(cap + 1);
   b.bsz = L.take<uint64_t>(cap + 1);
   b.disk = L.take<uint64_t>(cap + 1);
@@ -276,7 +280,7 @@ void trace_mark(Trace* t, int i, cudaStream_t st);
 luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DErr* errs, uint32_t cap, Recs recs,
                      const uint8_t* arena, Fmt fmt, uint8_t* out, uint64_t out_cap, uint64_t bm_cap, CrcTabs tabs,
                      cudaStream_t st, Trace* tr = nullptr) {
-  launch_sizes(b.surv, cnt, cap, jobs, n_jobs, recs, arena, b.lcp, b.sd, b.dr, st);
+  launch_sizes(b.surv, cnt, cap, jobs, n_jobs, recs, arena, b.lcp, b.sd, b.dr, b.ed, st);
   CK((exclusive_scan<uint32_t, uint64_t>(b.sd, b.P, cap, &cnt->n_surv, b.scan_tmp, st)));
   launch_block_next(b.P, b.dr, cnt, cap, jobs, n_jobs, fmt, b.next, st);
   launch_stitch(b.next, &cnt->n_surv, cap, &cnt->gap_surv, jobs, n_jobs, false, b.sflags, b.stitch_tmp, st);
@@ -299,8 +303,8 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   launch_file_offsets(b.files, cnt, cap, b.foff, b.bmoff, jobs, n_jobs, out_cap, bm_cap, errs, st);
   launch_zero_bitmap(b.bitmap, cnt, bm_cap, st);
   trace_mark(tr, 7, st);
-  launch_encode(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena, fmt,
-                out, out_cap, b.enc_done, tabs, st);
+  launch_encode(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, b.ed, recs, arena,
+                fmt, fmt.max_kv, out, out_cap, b.enc_done, b.big, errs, tabs, st);
   trace_mark(tr, 8, st);
   launch_bloom(b.surv, cnt, cap, b.blk_file, b.blk_start, b.files, recs, arena, fmt, b.bitmap, out_cap, bm_cap, st);
   launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, out, out_cap,
@@ -584,6 +588,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   CK(cudaMemcpyAsync(in_rec.data(), d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(in_key.data(), d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(herr.data(), d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&fmt.max_kv, &d_cnt->max_kv, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   tr.mark(3, st);
   CK(cudaStreamSynchronize(st));
 
@@ -1104,6 +1109,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   std::vector<uint64_t> in_key(N + 1);
   CK(cudaMemcpyAsync(in_rec.data(), d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(in_key.data(), d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&fmt.max_kv, &d_cnt->max_kv, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const uint32_t n_rec = in_rec[N];
   const uint64_t K = in_key[N];

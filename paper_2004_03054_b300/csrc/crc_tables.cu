@@ -71,6 +71,17 @@ void to_tables(const Mat& m, uint32_t* tab) {
     for (uint32_t v = 0; v < 256; ++v) tab[b * 256 + v] = apply(m, v << (8 * b));
 }
 
+Mat power(const Mat& m, uint32_t e) {  // m^e by square-and-multiply
+  Mat acc;
+  for (int i = 0; i < 32; ++i) acc.col[i] = 1u << i;
+  Mat base = m;
+  for (; e; e >>= 1) {
+    if (e & 1u) acc = mul(acc, base);
+    base = mul(base, base);
+  }
+  return acc;
+}
+
 }  // namespace
 
 // Fills `slice` (1024 words) and `shift` (kShiftTables * 1024 words).
@@ -96,18 +107,7 @@ bool make_crc_tables(uint32_t* slice, uint32_t* shift) {
     to_tables(z, shift + size_t(j) * 1024);
     z = mul(z, z);
   }
-  Mat z496 = z1;  // Z_1^496 by square-and-multiply
-  {
-    Mat acc;
-    for (int i = 0; i < 32; ++i) acc.col[i] = 1u << i;
-    Mat base = z1;
-    for (uint32_t e = 496; e; e >>= 1) {
-      if (e & 1u) acc = mul(acc, base);
-      base = mul(base, base);
-    }
-    z496 = acc;
-  }
-  to_tables(z496, shift + size_t(kShift496) * 1024);
+  to_tables(power(z1, 992), shift + size_t(kShift992) * 1024);
   Mat inv;
   if (!invert(z1, &inv)) return false;
   Mat zp = inv;

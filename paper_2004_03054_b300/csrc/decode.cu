@@ -138,137 +138,145 @@ __global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs
   }
 }
 
-// Walk one restart segment [s, e) of a data block: headers only. Returns false on a
-// structure violation; adds entries and key bytes. With `offs`, writes each entry's offset.
-__device__ __forceinline__ bool walk_segment(const uint8_t* base, uint64_t s, uint64_t e, uint32_t* cnt,
-                                             uint64_t* kbytes, uint16_t* offs = nullptr, uint32_t cap = 0) {
-  const uint8_t* p = base + s;
-  const uint8_t* end = base + e;
-  uint64_t prev = 0;
-  bool first = true;
-  uint32_t rec = 0;
-  while (p < end) {
-    if (offs && rec < cap) offs[rec] = uint16_t(p - base);
-    ++rec;
-    uint64_t shared, nonshared, vlen;
-    uint32_t a = get_varint<32>(p, end, &shared);
-    if (!a) return false;
-    p += a;
-    a = get_varint<32>(p, end, &nonshared);
-    if (!a) return false;
-    p += a;
-    a = get_varint<32>(p, end, &vlen);
-    if (!a) return false;
-    p += a;
-    if ((first && shared != 0) || shared > prev) return false;
-    if (nonshared > uint64_t(end - p) || vlen > uint64_t(end - p) - nonshared) return false;
-    const uint64_t klen = shared + nonshared;
-    if (klen < 8) return false;
-    p += nonshared + vlen;
-    prev = klen;
-    first = false;
-    *cnt += 1;
-    *kbytes += klen;
-  }
-  return true;
-}
+// ---- block scan: checksum verify and structure walk ----------------------------------------
+// k_block_verify: one warp per data block recomputes the CRC-32C of contents || type byte
+// (32-byte lane spans, lane-replicated tables, 1024-thread CTAs, one per SM) and checks
+// the type byte. k_block_walk: one thread per data block walks the restart segments in
+// order (the entries' offsets depend on the previous entries' headers, so a block's walk is
+// sequential; blocks run in parallel), checks the structure, counts entries and key bytes
+// and records the first kHdrMax entry offsets for the decoder. Each header is read from one
+// 16-byte window (two aligned 8-byte loads; tables are readable up to 16 bytes past any
+// entry, since at least the trailer and footer follow every data block).
+constexpr int kVerifyWarps = 32;
+constexpr uint32_t kVerifySmem = (kRepWords + 1024) * 4;
 
-// One warp per data block: CRC, type, structure; entry and key-byte counts. 1024-thread
-// CTAs, one per SM, with lane-replicated CRC tables (conflict-free lookups).
-constexpr int kScanWarps = 32;
-constexpr uint32_t kScanSmem = (kRepWords + 1024) * 4;
-
-__global__ void __launch_bounds__(kScanWarps * 32, 1) k_block_scan(const BlockDesc* __restrict__ blocks,
-                                                                   uint32_t n_blocks, const DInput* __restrict__ in,
-                                                                   uint32_t* __restrict__ nrec,
-                                                                   uint64_t* __restrict__ kbytes, DErr* errs,
-                                                                   Counts* counts, uint16_t* __restrict__ hdr_tab,
-                                                                   CrcTabs tabs) {
-  extern __shared__ uint32_t s_scan[];
-  uint32_t* sTr = s_scan;
-  uint32_t* sZ = s_scan + kRepWords;
-  load_rep_tables(sTr, sZ, tabs);
+__global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_block_verify(const BlockDesc* __restrict__ blocks,
+                                                                       uint32_t n_blocks,
+                                                                       const DInput* __restrict__ in, DErr* errs,
+                                                                       CrcTabs tabs) {
+  extern __shared__ uint32_t s_ver[];
+  load_rep_tables992(s_ver, s_ver + kRepWords, tabs);
   __syncthreads();
   const uint32_t lane = lane_id();
+  const uint32_t tl = smem_addr(s_ver) + lane * 4u, tz = smem_addr(s_ver + kRepWords);
   const uint64_t warps = gstride() / 32;
   for (uint64_t g = gtid() / 32; g < n_blocks; g += warps) {
+    const BlockDesc b = blocks[g];
+    DErr* e = errs + b.job;
+    if (b.ptr == nullptr || *(volatile int32_t*)&e->code != 0) continue;
+    const uint32_t got = warp_crc32c_u32(b.ptr, b.size + 1, tl, tz, tabs);
+    if (lane == 0) {
+      const uint32_t want = crc_unmask(ld_u32(b.ptr + b.size + 1));
+      if (got != want) report(e, E_CORRUPT, in[b.input].local, b.off);
+      else if (b.ptr[b.size] != 0) report(e, E_NOTSUP, in[b.input].local, b.off);
+    }
+  }
+}
+
+// Byte i (< 16) of the 16-byte window w0 | w1 << 64.
+__device__ __forceinline__ uint32_t win_byte(uint64_t w0, uint64_t w1, uint32_t i) {
+  return uint32_t((i < 8 ? w0 >> (8 * i) : w1 >> (8 * (i - 8))) & 0xFFu);
+}
+
+// Parses the three varint32 header fields of the entry at p (p < end). Returns the header
+// length, or 0 on a malformed or out-of-range varint.
+__device__ __forceinline__ uint32_t read_header(const uint8_t* p, const uint8_t* end, uint32_t* f) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(7);
+  const uint32_t o = uint32_t(reinterpret_cast<uintptr_t>(p) & 7u);
+  const uint64_t u0 = *reinterpret_cast<const uint64_t*>(a), u1 = *reinterpret_cast<const uint64_t*>(a + 8);
+  const uint64_t w0 = o ? (u0 >> (8 * o)) | (u1 << (64 - 8 * o)) : u0;
+  const uint64_t w1 = u1 >> (8 * o);
+  const uint32_t have = 16u - o;  // window bytes starting at p
+  const uint64_t room = uint64_t(end - p);
+  uint32_t pos = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    uint64_t v = 0;
+    uint32_t i = 0;
+    for (;; ++i) {
+      if (i == 5 || pos >= room) return 0;
+      const uint32_t byte = pos < have ? win_byte(w0, w1, pos) : p[pos];
+      ++pos;
+      v |= uint64_t(byte & 0x7Fu) << (7 * i);
+      if (!(byte & 0x80u)) break;
+    }
+    if (v > 0xFFFFFFFFull) return 0;
+    f[k] = uint32_t(v);
+  }
+  return pos;
+}
+
+__global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
+                                                    const DInput* __restrict__ in, uint32_t* __restrict__ nrec,
+                                                    uint64_t* __restrict__ kbytes, DErr* errs, Counts* counts,
+                                                    uint16_t* __restrict__ hdr_tab) {
+  unsigned long long data_bytes = 0;
+  uint32_t max_kv = 0;
+  for (uint64_t g = gtid(); g < n_blocks; g += gstride()) {
     const BlockDesc b = blocks[g];
     DErr* e = errs + b.job;
     uint32_t cnt = 0;
     uint64_t kb = 0;
     if (b.ptr != nullptr && *(volatile int32_t*)&e->code == 0) {
-      if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&counts->in_data_bytes),
-                               (unsigned long long)(b.size + kTrailer));
-      const uint32_t got = warp_crc32c_il(b.ptr, b.size + 1, smem_addr(sTr), smem_addr(sZ), tabs);
-      const uint32_t want = crc_unmask(ld_u32(b.ptr + b.size + 1));
-      const uint32_t local = in[b.input].local;
-      if (got != want) {
-        if (lane == 0) report(e, E_CORRUPT, local, b.off);
-      } else if (b.ptr[b.size] != 0) {
-        if (lane == 0) report(e, E_NOTSUP, local, b.off);
-      } else {
-        const uint64_t nr = b.size >= 4 ? ld_u32(b.ptr + b.size - 4) : 0;
-        bool bad = !(nr >= 1 && nr <= (b.size - 4) / 4);
-        if (!bad) {
-          const uint64_t rstart = b.size - 4 - 4 * nr;
-          const uint8_t* rs = b.ptr + rstart;
-          for (uint64_t k = lane; k < nr && !bad; k += 32) {
-            const uint64_t s = ld_u32(rs + 4 * k);
-            const uint64_t en = k + 1 < nr ? ld_u32(rs + 4 * (k + 1)) : rstart;
-            if ((k == 0 && s != 0) || s >= en || en > rstart) bad = true;
-            else if (!walk_segment(b.ptr, s, en, &cnt, &kb, nr == 1 && b.size < 65536 ? hdr_tab + g * kHdrMax : nullptr,
-                                   kHdrMax))
+      data_bytes += b.size + kTrailer;
+      const uint64_t nr = b.size >= 4 ? ld_u32(b.ptr + b.size - 4) : 0;
+      bool bad = !(nr >= 1 && nr <= (b.size - 4) / 4);
+      if (!bad) {
+        const uint64_t rstart = b.size - 4 - 4 * nr;
+        const uint8_t* rs = b.ptr + rstart;
+        uint16_t* offs = b.size < 65536 ? hdr_tab + g * kHdrMax : nullptr;
+        uint64_t s = ld_u32(rs);
+        bad = s != 0;
+        for (uint64_t k = 0; k < nr && !bad; ++k) {
+          const uint64_t en = k + 1 < nr ? ld_u32(rs + 4 * (k + 1)) : rstart;
+          if (s >= en || en > rstart) {
+            bad = true;
+            break;
+          }
+          const uint8_t* p = b.ptr + s;
+          const uint8_t* end = b.ptr + en;
+          uint64_t prev = 0;
+          bool first = true;
+          while (p < end) {
+            if (offs && cnt < kHdrMax) offs[cnt] = uint16_t(p - b.ptr);
+            uint32_t f[3];
+            const uint32_t hl = read_header(p, end, f);
+            if (!hl) {
               bad = true;
-          }
-        }
-        bad = __any_sync(0xFFFFFFFFu, bad);
-        if (bad) {
-          if (lane == 0) report(e, E_CORRUPT, local, b.off);
-          cnt = 0;
-          kb = 0;
-        } else if (b.size < 65536 && nr > 1) {
-          // entry offsets for the decoder (blocks of at most kHdrMax entries), segments in
-          // groups of 32 so that each group's entries are placed after the previous group's
-          const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, cnt);
-          if (total <= kHdrMax) {
-            const uint64_t rstart = b.size - 4 - 4 * nr;
-            const uint8_t* rs = b.ptr + rstart;
-            uint32_t run = 0;
-            for (uint64_t k0 = 0; k0 < nr; k0 += 32) {
-              const uint64_t k = k0 + lane;
-              uint64_t s = 0, en = 0, kk = 0;
-              uint32_t c = 0;
-              if (k < nr) {
-                s = ld_u32(rs + 4 * k);
-                en = k + 1 < nr ? ld_u32(rs + 4 * (k + 1)) : rstart;
-                walk_segment(b.ptr, s, en, &c, &kk);
-              }
-              uint32_t xs = c;
-#pragma unroll
-              for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, xs, d);
-                if (lane >= uint32_t(d)) xs += o;
-              }
-              if (k < nr) {
-                uint32_t c2 = 0;
-                walk_segment(b.ptr, s, en, &c2, &kk, hdr_tab + g * kHdrMax + run + xs - c, kHdrMax);
-              }
-              run += __shfl_sync(0xFFFFFFFFu, xs, 31);
+              break;
             }
+            p += hl;
+            const uint64_t shared = f[0], nonshared = f[1], vlen = f[2];
+            if ((first && shared != 0) || shared > prev || nonshared > uint64_t(end - p) ||
+                vlen > uint64_t(end - p) - nonshared || shared + nonshared < 8) {
+              bad = true;
+              break;
+            }
+            p += nonshared + vlen;
+            prev = shared + nonshared;
+            max_kv = max(max_kv, uint32_t(prev + vlen));
+            first = false;
+            cnt += 1;
+            kb += prev;
           }
+          s = en;
         }
       }
+      if (bad) {
+        report(e, E_CORRUPT, in[b.input].local, b.off);
+        cnt = 0;
+        kb = 0;
+      }
     }
-#pragma unroll
-    for (int d = 16; d; d >>= 1) {
-      cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, d);
-      kb += __shfl_xor_sync(0xFFFFFFFFu, kb, d);
-    }
-    if (lane == 0) {
-      nrec[g] = cnt;
-      kbytes[g] = kb;
-    }
+    nrec[g] = cnt;
+    kbytes[g] = kb;
   }
+#pragma unroll
+  for (int d = 16; d; d >>= 1) data_bytes += __shfl_xor_sync(0xFFFFFFFFu, data_bytes, d);
+  if ((threadIdx.x & 31u) == 0 && data_bytes)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&counts->in_data_bytes), data_bytes);
+  max_kv = __reduce_max_sync(0xFFFFFFFFu, max_kv);
+  if ((threadIdx.x & 31u) == 0 && max_kv) atomicMax(&counts->max_kv, max_kv);
 }
 
 // One warp per data block. With the block's entry offsets from the scan (at most kHdrMax
@@ -481,11 +489,11 @@ void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* i
 void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
                        uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, CrcTabs tabs, cudaStream_t st) {
   if (!n_blocks) return;
-  cudaFuncSetAttribute(k_block_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kScanSmem));
-  k_block_scan<<<grid_for(n_blocks, kScanWarps, kSms), kScanWarps * 32, kScanSmem, st>>>(blocks, n_blocks, in, nrec,
-                                                                                         kbytes, errs, cnt, hdr_tab,
-                                                                                         tabs);
-  count_launches(1);
+  cudaFuncSetAttribute(k_block_verify, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kVerifySmem));
+  k_block_verify<<<grid_for(n_blocks, kVerifyWarps, kSms), kVerifyWarps * 32, kVerifySmem, st>>>(blocks, n_blocks,
+                                                                                                 in, errs, tabs);
+  k_block_walk<<<grid_for(n_blocks, 256), 256, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, cnt, hdr_tab);
+  count_launches(2);
 }
 
 void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,

@@ -65,6 +65,8 @@ struct Fmt {
   uint32_t bpk;     // bloom bits per key
   uint32_t k;       // bloom probes
   uint64_t target;  // target file size
+  uint32_t max_kv;  // largest internal key + value length of the inputs (0: unknown)
+  uint32_t pad;
 };
 
 // Device-side counts of the stages whose sizes only the device knows.
@@ -80,6 +82,15 @@ struct Counts {
   uint64_t surv_kv_bytes;   // survivor keys + values (read by the encoder)
   uint32_t gap_surv;        // largest next(i) - i of the block cut
   uint32_t gap_blk;         // largest next(b) - b of the file cut
+  uint32_t big_blocks;      // data blocks left to the CTA-per-block encoder
+  uint32_t max_kv;          // largest internal key + value length in the inputs (block walk)
+};
+
+// Per survivor, in survivor order: what the encoder reads of its record.
+struct EncDesc {
+  uint64_t kptr;  // device address of the full internal key (key arena)
+  uint64_t vptr;  // device address of the value (input table)
+  uint32_t klen, vlen;
 };
 
 // Per-output-table summary copied to the host at the end.
@@ -158,7 +169,8 @@ void launch_job_surv(JobDev* jobs, uint32_t n_jobs, const uint32_t* pos, uint32_
 
 // ---- pack.cu -----------------------------------------------------------------------------
 void launch_sizes(const uint32_t* surv, const Counts* cnt, uint32_t cap, const JobDev* jobs, uint32_t n_jobs,
-                  Recs recs, const uint8_t* arena, uint32_t* lcp, uint32_t* sd, uint32_t* dr, cudaStream_t st);
+                  Recs recs, const uint8_t* arena, uint32_t* lcp, uint32_t* sd, uint32_t* dr, EncDesc* ed,
+                  cudaStream_t st);
 void launch_block_next(const uint64_t* P, const uint32_t* dr, const Counts* cnt, uint32_t cap, const JobDev* jobs,
                        uint32_t n_jobs, Fmt fmt, uint32_t* next, cudaStream_t st);
 uint64_t stitch_temp_bytes(uint32_t cap);
@@ -183,10 +195,11 @@ void launch_file_offsets(FileDesc* files, Counts* cnt, uint32_t cap, const uint6
                          JobDev* jobs, uint32_t n_jobs, uint64_t out_cap, uint64_t bm_cap, DErr* errs,
                          cudaStream_t st);
 void launch_zero_bitmap(uint32_t* bitmap, const Counts* cnt, uint64_t cap_words, cudaStream_t st);
-void launch_encode(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
+void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                    const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
-                   const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
-                   Fmt fmt, uint8_t* out, uint64_t out_cap, uint8_t* done, CrcTabs tabs, cudaStream_t st);
+                   const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, const EncDesc* ed, Recs recs,
+                   const uint8_t* arena, Fmt fmt, uint32_t max_kv, uint8_t* out, uint64_t out_cap, uint8_t* done,
+                   uint32_t* big, DErr* errs, CrcTabs tabs, cudaStream_t st);
 void launch_bloom(const uint32_t* surv, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                   const uint32_t* blk_start, const FileDesc* files, Recs recs, const uint8_t* arena, Fmt fmt,
                   uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st);

@@ -54,7 +54,8 @@ __device__ __forceinline__ uint32_t job_of_block(const JobDev* jobs, uint32_t n_
 
 __global__ void k_sizes(const uint32_t* __restrict__ surv, const Counts* __restrict__ cnt,
                         const JobDev* __restrict__ jobs, uint32_t n_jobs, Recs recs, const uint8_t* __restrict__ arena,
-                        uint32_t* __restrict__ lcp, uint32_t* __restrict__ sd, uint32_t* __restrict__ dr) {
+                        uint32_t* __restrict__ lcp, uint32_t* __restrict__ sd, uint32_t* __restrict__ dr,
+                        EncDesc* __restrict__ ed) {
   const uint32_t n = cnt->n_surv;
   uint64_t kv = 0;
   for (uint64_t s = gtid(); s < n; s += gstride()) {
@@ -74,6 +75,7 @@ __global__ void k_sizes(const uint32_t* __restrict__ surv, const Counts* __restr
     lcp[s] = l;
     sd[s] = d;
     dr[s] = r - d;
+    ed[s] = EncDesc{reinterpret_cast<uint64_t>(arena + recs.koff[x]), recs.vptr[x], klen, vlen};
     kv += klen + vlen;
   }
 #pragma unroll
@@ -387,7 +389,6 @@ __global__ void k_zero_words(uint32_t* __restrict__ w, const Counts* __restrict_
 // global memory instead (same bytes).
 constexpr int kEncThreads = 256;
 constexpr uint32_t kEncBuf = 64 * 1024;
-constexpr uint32_t kEncMaxEnt = 40;  // blocks of up to this many entries take the warp encoder
 
 // Copy n bytes from global src (any alignment) to dst (any alignment), one warp.
 __device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, uint32_t n, uint32_t lane) {
@@ -419,7 +420,8 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_big(const uint32_t* __re
                                                         const uint32_t* __restrict__ dr, Recs recs,
                                                         const uint8_t* __restrict__ arena, Fmt fmt,
                                                         uint8_t* __restrict__ out, uint64_t out_cap,
-                                                        const uint8_t* __restrict__ done, CrcTabs tabs) {
+                                                        const uint32_t* __restrict__ big, CrcTabs tabs) {
+  if (blockIdx.x >= cnt->big_blocks) return;
   extern __shared__ uint4 s_dyn[];
   __shared__ uint32_t sT[1024];
   __shared__ uint32_t s_off[kEncThreads];
@@ -430,10 +432,10 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_big(const uint32_t* __re
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   constexpr uint32_t nwarps = kEncThreads / 32;
   const uint32_t R = fmt.R;
-  const uint32_t nb = cnt->nb;
-  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+  const uint32_t n_big = cnt->big_blocks;
+  for (uint32_t i = blockIdx.x; i < n_big; i += gridDim.x) {
+    const uint32_t b = big[i];
     const uint32_t s = start[b], e = start[b + 1], m = e - s;
-    if (done[b]) continue;  // the warp encoder took it
     const FileDesc F = files[blk_file[b]];
     if (F.off + F.size > out_cap) continue;
     uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
@@ -519,41 +521,78 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_big(const uint32_t* __re
 }
 
 
-// ---- warp encoder ---------------------------------------------------------------------------
-// Two kernels. k_encode writes the bytes of every data block of at most kEncMaxEnt
-// entries, one warp per block and no staging buffer: the block is cut into 16-byte chunks
-// aligned in global memory. Chunks inside one value ("value chunks") are copied in rounds
-// where lane l of round r owns chunk Q - 32 * (rounds - r) + l (512 contiguous bytes per
-// round): two aligned 16-byte loads from the input table, funnel shifts, one aligned
-// 16-byte store, with loads two rounds ahead. The other chunks (headers, key deltas,
-// restart array, ragged ends) are written byte by byte first, one lane per entry so that
-// all of a block's boundary loads are in flight together. Without CRC tables the kernel
-// holds little shared memory and runs 64 warps per SM.
-// k_block_crc then computes each block's masked CRC-32C trailer (interleaved warp CRC,
-// lane-replicated tables). Blocks the warp encoder cannot take go to k_encode_big.
-constexpr int kEncWarps = 32;
-constexpr uint32_t kEncMapWords = 96;  // bitmap words: chunks per block <= 3072 (48 KiB)
+// ---- staged encoder (TMA) -------------------------------------------------------------------
+// A CTA of kStgThreads threads encodes one data block at a time and keeps the next block's
+// bytes in flight:
+//   prepare(b): one thread per entry reads the survivor's descriptor (survivor order,
+//     coalesced) and its shared-prefix length; a CTA scan places every entry in the block
+//     and in a staging buffer; each entry's key delta and value are fetched into the
+//     staging buffer by bulk asynchronous copies (cp.async.bulk, completion counted in
+//     bytes on the buffer's mbarrier) as whole aligned 16-byte ranges.
+//   consume(b): the block image is assembled in shared memory at its destination's
+//     16-byte phase: headers, key deltas, value edges, restart array and type byte
+//     bytewise; every 16-byte image word inside one value comes from the staging buffer
+//     with funnel shifts. The aligned middle of the image leaves in one bulk store
+//     (cp.async.bulk shared -> global); the ragged ends with byte stores.
+// Two staging buffers and one image buffer per CTA; several CTAs per SM. Blocks with more
+// than kStgMaxEnt entries or larger than the buffers go to k_encode_big. The CRC trailer is
+// written afterwards by k_block_crc.
+constexpr uint32_t kStgThreads = 256;
+constexpr uint32_t kStgWarps = kStgThreads / 32;
+constexpr uint32_t kStgMaxEnt = 128;
+constexpr uint32_t kStgHead = 16 + 2 * kStgMaxEnt * 32 + 64;  // mbarriers, entry tables, scan scratch
 
-struct EncEnt {
-  uint32_t eoff, voff, vlen, nsh, shr, pad;
-  uint64_t vptr, kptr;
+struct StgEnt {
+  uint32_t eoff;  // entry offset in the block
+  uint32_t shr, nsh, vlen;
+  uint32_t ks;    // staging offset of the key delta's first byte
+  uint32_t vs;    // staging offset of the value's first byte
+  uint32_t vb;    // block offset of the value's first byte
+  uint32_t pad;
 };
 
-struct EncWarp {
-  EncEnt ent[kEncMaxEnt + 1];
-  uint32_t map[kEncMapWords];
-};
-
-constexpr uint32_t kEncSmem = kEncWarps * uint32_t(sizeof(EncWarp));
-
-__device__ __forceinline__ uint32_t vbyte(uint32_t v, uint32_t j) {
-  return ((v >> (7 * j)) & 0x7Fu) | (j + 1 < varint_size(v) ? 0x80u : 0u);
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
 }
-
-__device__ __forceinline__ uint32_t u4_byte(uint4 v, uint32_t u) {  // byte u (< 16) of v
-  const uint32_t w = u < 8 ? (u < 4 ? v.x : v.y) : (u < 12 ? v.z : v.w);
-  return (w >> (8 * (u & 3))) & 0xFFu;
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase with the given parity: false once a second has passed.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  if (mbar_try_wait(a, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(a, parity)) return true;
+    if (global_ns() - t0 > 1000000000ull) return false;
+  }
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Bytes [sh, sh + 16) of the 32 bytes a || b, with selects (no divergent branches).
 __device__ __forceinline__ uint4 shift32(uint4 a, uint4 b, uint32_t sh) {
@@ -566,175 +605,229 @@ __device__ __forceinline__ uint4 shift32(uint4 a, uint4 b, uint32_t sh) {
                     __funnelshift_r(y3, y4, bs));
 }
 
-__device__ __forceinline__ uint4 load16(const uint8_t* src) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
-  const uint32_t sh = uint32_t(reinterpret_cast<uintptr_t>(src) & 15u);
-  const uint4 u0 = __ldg(reinterpret_cast<const uint4*>(a));
-  if (sh == 0) return u0;
-  return shift32(u0, __ldg(reinterpret_cast<const uint4*>(a + 16)), sh);
+__device__ __forceinline__ uint32_t hdr_len(uint32_t shr, uint32_t nsh, uint32_t vlen) {
+  return varint_size(shr) + varint_size(nsh) + varint_size(vlen);
 }
 
-__device__ __forceinline__ void map_range(uint32_t* map, int64_t a, int64_t b) {  // set bits [a, b]
-  for (int64_t q = a; q <= b; ++q) atomicOr(map + (q >> 5), 1u << (q & 31));
-}
+// Per-block state kept in registers (the same in every thread of the CTA).
+struct StgBlk {
+  uint32_t b;         // block index
+  uint32_t m;         // entries
+  uint32_t state;     // 0 none, 1 loads in flight, 2 skipped
+  uint32_t phase;     // destination address mod 16
+  uint64_t contents;  // block contents size (without the 5-byte trailer)
+  uint8_t* dst;       // block start in the output
+};
 
-__global__ void __launch_bounds__(kEncWarps * 32, 1) k_encode(const uint32_t* __restrict__ start,
-                                                               const Counts* __restrict__ cnt,
-                                                               const uint32_t* __restrict__ blk_file,
-                                                               const FileDesc* __restrict__ files,
-                                                               const uint64_t* __restrict__ C,
-                                                               const uint64_t* __restrict__ bsz,
-                                                               const uint32_t* __restrict__ surv,
-                                                               const uint32_t* __restrict__ lcp, Recs recs,
-                                                               const uint8_t* __restrict__ arena, Fmt fmt,
-                                                               uint8_t* __restrict__ out, uint64_t out_cap,
-                                                               uint8_t* __restrict__ done) {
-  extern __shared__ uint32_t s_enc[];
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  EncWarp& Wp = reinterpret_cast<EncWarp*>(s_enc)[warp];
-  EncEnt* E = Wp.ent;
+__global__ void __launch_bounds__(kStgThreads) k_encode_stg(const uint32_t* __restrict__ start,
+                                                            Counts* __restrict__ cnt,
+                                                            const uint32_t* __restrict__ blk_file,
+                                                            const FileDesc* __restrict__ files,
+                                                            const uint64_t* __restrict__ C,
+                                                            const uint64_t* __restrict__ bsz,
+                                                            const uint32_t* __restrict__ lcp,
+                                                            const EncDesc* __restrict__ ed, Fmt fmt,
+                                                            uint8_t* __restrict__ out, uint64_t out_cap,
+                                                            uint8_t* __restrict__ done, uint32_t* __restrict__ big,
+                                                            DErr* errs, uint32_t S, uint32_t I) {
+  extern __shared__ __align__(128) uint8_t s_stg[];
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t sbase = smem_addr(s_stg);
+  const uint32_t mbar0 = sbase, mbar1 = sbase + 8;
+  StgEnt* ents = reinterpret_cast<StgEnt*>(s_stg + 16);             // [2][kStgMaxEnt]
+  uint32_t* scratch = reinterpret_cast<uint32_t*>(s_stg + 16 + 2 * kStgMaxEnt * 32);  // [16]
+  uint8_t* stage = s_stg + ((kStgHead + 127) & ~127u);              // [2][S]
+  uint8_t* img = stage + 2 * size_t(S);                             // [I + 16]
+  const uint32_t stage_a = smem_addr(stage), img_a = smem_addr(img);
   const uint32_t R = fmt.R;
   const uint32_t nb = cnt->nb;
-  const uint32_t total_warps = gridDim.x * kEncWarps;
-  for (uint32_t b = blockIdx.x * kEncWarps + warp; b < nb; b += total_warps) {
-    const uint32_t s = start[b], m = start[b + 1] - s;
-    if (lane == 0) done[b] = 0;
-    if (m > kEncMaxEnt) continue;
-    const FileDesc F = files[blk_file[b]];
-    if (F.off + F.size > out_cap) continue;
-    uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
-    const uint64_t contents = bsz[b];
-    const uint64_t msg = contents + 1;  // contents and type byte
-    const uint32_t phase = uint32_t(reinterpret_cast<uintptr_t>(dst) & 15u);
-    const int64_t Q = int64_t((phase + msg + 15) >> 4);
-    if (Q > int64_t(kEncMapWords) * 32) continue;
-    // entry layout
-    uint32_t carry = 0;
-    for (uint32_t k0 = 0; k0 < m; k0 += 32) {
-      const uint32_t k = k0 + lane;
-      uint32_t size = 0, vlen = 0, shr = 0, nsh = 0, hl = 0;
-      uint64_t vptr = 0, kptr = 0;
-      if (k < m) {
-        const uint32_t x = surv[s + k];
-        const uint32_t klen = recs.klen[x];
-        vlen = recs.vlen[x];
-        shr = (k % R) == 0 ? 0u : lcp[s + k];
-        nsh = klen - shr;
-        hl = varint_size(shr) + varint_size(nsh) + varint_size(vlen);
-        size = hl + nsh + vlen;
-        vptr = recs.vptr[x];
-        kptr = reinterpret_cast<uint64_t>(arena + recs.koff[x] + shr);
-      }
-      uint32_t xs = size;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, xs, d);
-        if (lane >= uint32_t(d)) xs += o;
-      }
-      const uint32_t eoff = carry + xs - size;
-      if (k < m) E[k] = EncEnt{eoff, eoff + hl + nsh, vlen, nsh, shr, 0, vptr, kptr};
-      carry += __shfl_sync(0xFFFFFFFFu, xs, 31);
-    }
-    const uint32_t ent_end = carry;
-    const uint32_t nr = (m + R - 1) / R;
-    // boundary-chunk bitmap
-    const uint32_t words = uint32_t((Q + 31) >> 5);
-    for (uint32_t w = lane; w < words; w += 32) Wp.map[w] = 0;
-    if (lane == 0) E[m].eoff = ent_end;
-    __syncwarp();
-    for (uint32_t k = lane; k < m; k += 32)
-      map_range(Wp.map, (int64_t(E[k].eoff) + phase) >> 4, (int64_t(E[k].voff) - 1 + phase) >> 4);
-    if (lane == 0) map_range(Wp.map, (int64_t(ent_end) + phase) >> 4, Q - 1);
-    __syncwarp();
-    uint8_t* A0 = dst - phase;
-    // boundary bytes, one lane per entry: header, key delta, value head and tail
-    for (uint32_t k = lane; k < m; k += 32) {
-      const EncEnt en = E[k];
-      const uint32_t s0 = varint_size(en.shr), s1 = varint_size(en.nsh), s2 = varint_size(en.vlen);
-      const uint32_t hl = s0 + s1 + s2;
-      const uint8_t* kp = reinterpret_cast<const uint8_t*>(en.kptr);
-      const uint8_t* vp = reinterpret_cast<const uint8_t*>(en.vptr);
-      const int64_t v0 = en.voff, v1 = int64_t(en.voff) + en.vlen;
-      const int64_t head_end = min(v1, ((v0 + phase + 15) & ~int64_t(15)) - phase);
-      const int64_t tail_beg = max(head_end, ((v1 + phase) & ~int64_t(15)) - phase);
-      uint4 hv = make_uint4(0, 0, 0, 0), tv = hv;
-      const int64_t w0 = en.vlen >= 16 ? int64_t(en.vlen) - 16 : 0;  // tail window inside the value
-      if (head_end > v0) hv = load16(vp);
-      if (v1 > tail_beg) tv = load16(vp + w0);
-      uint8_t* ep = dst + en.eoff;
-      uint32_t q = put_varint(ep, en.shr);
-      q += put_varint(ep + q, en.nsh);
-      put_varint(ep + q, en.vlen);
-      // key delta: 16-byte loads issued ahead of the byte stores (keys up to 80 bytes in
-      // one batch; longer keys continue 16 bytes at a time)
-      {
-        uint4 k0 = make_uint4(0, 0, 0, 0), k1 = k0, k2 = k0, k3 = k0, k4 = k0;
-        const uint32_t n = en.nsh;
-        if (n > 0) k0 = load16(kp);
-        if (n > 16) k1 = load16(kp + 16);
-        if (n > 32) k2 = load16(kp + 32);
-        if (n > 48) k3 = load16(kp + 48);
-        if (n > 64) k4 = load16(kp + 64);
-        uint8_t* kd = ep + hl;
-        for (uint32_t t = 0; t < n && t < 80; ++t) {
-          const uint4 kv = t < 16 ? k0 : t < 32 ? k1 : t < 48 ? k2 : t < 64 ? k3 : k4;
-          kd[t] = uint8_t(u4_byte(kv, t & 15u));
-        }
-        for (uint32_t t0 = 80; t0 < n; t0 += 16) {
-          const uint4 kv = load16(kp + t0);
-          for (uint32_t u = 0; u < 16 && t0 + u < n; ++u) kd[t0 + u] = uint8_t(u4_byte(kv, u));
-        }
-      }
-      for (int64_t i = v0; i < head_end; ++i) dst[i] = uint8_t(u4_byte(hv, uint32_t(i - v0)));
-      for (int64_t i = tail_beg; i < v1; ++i) dst[i] = uint8_t(u4_byte(tv, uint32_t(i - v0 - w0)));
-    }
-    for (uint64_t t = lane; t < 4ull * nr; t += 32)  // restart array
-      dst[ent_end + t] = uint8_t(E[(t >> 2) * R].eoff >> (8 * (t & 3)));
-    if (lane == 0) {
-      st_u32(dst + contents - 4, nr);
-      dst[contents] = 0;
-    }
-    // value chunks, in rounds; loads run two rounds ahead of the stores
-    const int64_t rounds = (Q + 31) >> 5;
-    uint32_t cur = 0;
-    auto fetch = [&](int64_t r, uint4& u0, uint4& u1, uint32_t& sh, bool& val) {
-      const int64_t q = Q - 32 * (rounds - r) + lane;
-      val = false;
-      if (q < 0 || (Wp.map[q >> 5] & (1u << (q & 31)))) return;
-      const int64_t lo = q * 16 - int64_t(phase);
-      while (cur + 1 < m && E[cur + 1].eoff <= uint64_t(lo)) ++cur;
-      const uint8_t* src = reinterpret_cast<const uint8_t*>(E[cur].vptr) + (lo - E[cur].voff);
-      const uintptr_t a = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
-      sh = uint32_t(reinterpret_cast<uintptr_t>(src) & 15u);
-      u0 = __ldg(reinterpret_cast<const uint4*>(a));
-      u1 = sh ? __ldg(reinterpret_cast<const uint4*>(a + 16)) : u0;
-      val = true;
-    };
-    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
-    uint32_t ash = 0, bsh = 0;
-    bool aval = false, bval = false;
-    if (rounds > 0) fetch(0, a0, a1, ash, aval);
-    if (rounds > 1) fetch(1, b0, b1, bsh, bval);
-    for (int64_t r = 0; r < rounds; ++r) {
-      uint4 c0 = make_uint4(0, 0, 0, 0), c1 = c0;
-      uint32_t csh = 0;
-      bool cval = false;
-      if (r + 2 < rounds) fetch(r + 2, c0, c1, csh, cval);
-      if (aval) {
-        const int64_t q = Q - 32 * (rounds - r) + lane;
-        *reinterpret_cast<uint4*>(A0 + q * 16) = ash ? shift32(a0, a1, ash) : a0;
-      }
-      a0 = b0;
-      a1 = b1;
-      ash = bsh;
-      aval = bval;
-      b0 = c0;
-      b1 = c1;
-      bsh = csh;
-      bval = cval;
-    }
-    if (lane == 0) done[b] = 1;
+  if (tid == 0) {
+    mbar_init(mbar0, 1);
+    mbar_init(mbar1, 1);
+    fence_proxy_async();
   }
+  __syncthreads();
+  uint32_t parity[2] = {0, 0};
+
+  auto prepare = [&](uint32_t b, uint32_t st, StgBlk& B) {
+    B.b = b;
+    B.state = 2;
+    const uint32_t s0 = start[b], m = start[b + 1] - s0;
+    B.m = m;
+    const FileDesc F = files[blk_file[b]];
+    B.contents = bsz[b];
+    B.dst = out + F.off + (C[b] - C[F.blk_begin]);
+    B.phase = uint32_t(reinterpret_cast<uintptr_t>(B.dst) & 15u);
+    if (F.off + F.size > out_cap) {
+      if (tid == 0) done[b] = 0;
+      return;
+    }
+    bool fits = m <= kStgMaxEnt && B.phase + B.contents + 1 <= I;
+    // entry layout: one thread per entry
+    uint32_t esz = 0, ssz = 0, shr = 0, nsh = 0, vlen = 0, kc = 0, vc = 0;
+    uint64_t kp = 0, vp = 0;
+    if (fits && tid < m) {
+      const EncDesc d = ed[s0 + tid];
+      shr = (tid % R) == 0 ? 0u : lcp[s0 + tid];
+      nsh = d.klen - shr;
+      vlen = d.vlen;
+      kp = d.kptr + shr;
+      vp = d.vptr;
+      kc = nsh ? uint32_t(((kp + nsh + 15) & ~uint64_t(15)) - (kp & ~uint64_t(15))) : 0u;
+      vc = vlen ? uint32_t(((vp + vlen + 15) & ~uint64_t(15)) - (vp & ~uint64_t(15))) : 0u;
+      esz = hdr_len(shr, nsh, vlen) + nsh + vlen;
+      ssz = kc + vc;
+    }
+    // CTA exclusive scan of (esz, ssz)
+    uint32_t xe = esz, xs = ssz;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t oe = __shfl_up_sync(0xFFFFFFFFu, xe, d), os = __shfl_up_sync(0xFFFFFFFFu, xs, d);
+      if (lane >= uint32_t(d)) {
+        xe += oe;
+        xs += os;
+      }
+    }
+    __syncthreads();  // scratch reuse
+    if (lane == 31) {
+      scratch[warp] = xe;
+      scratch[kStgWarps + warp] = xs;
+    }
+    __syncthreads();
+    uint32_t be = 0, bs = 0, te = 0, ts = 0;
+#pragma unroll
+    for (uint32_t w = 0; w < kStgWarps; ++w) {
+      const uint32_t ve = scratch[w], vs = scratch[kStgWarps + w];
+      if (w < warp) {
+        be += ve;
+        bs += vs;
+      }
+      te += ve;
+      ts += vs;
+    }
+    fits = fits && ts <= S;
+    if (!fits) {
+      if (tid == 0) {
+        done[b] = 0;
+        big[atomicAdd(&cnt->big_blocks, 1u)] = b;
+      }
+      return;
+    }
+    const uint32_t soff = bs + xs - ssz;
+    if (tid < m) {
+      StgEnt e;
+      e.eoff = be + xe - esz;
+      e.shr = shr;
+      e.nsh = nsh;
+      e.vlen = vlen;
+      e.ks = soff + uint32_t(kp & 15u);
+      e.vs = soff + kc + uint32_t(vp & 15u);
+      e.vb = e.eoff + esz - vlen;
+      e.pad = 0;
+      ents[st * kStgMaxEnt + tid] = e;
+    }
+    const uint32_t mb = st ? mbar1 : mbar0;
+    if (tid == 0) mbar_arrive_expect_tx(mb, ts);
+    __syncthreads();
+    if (tid < m) {
+      const uint32_t dst0 = stage_a + st * S + soff;
+      if (kc) bulk_load(dst0, reinterpret_cast<const void*>(kp & ~uint64_t(15)), kc, mb);
+      if (vc) bulk_load(dst0 + kc, reinterpret_cast<const void*>(vp & ~uint64_t(15)), vc, mb);
+    }
+    B.state = 1;
+  };
+
+  // returns false when the block's copies did not complete in time (the kernel then stops)
+  auto consume = [&](uint32_t st, const StgBlk& B) -> bool {
+    if (B.state != 1) return true;
+    const uint32_t mb = st ? mbar1 : mbar0;
+    bool ok = true;
+    if (tid == 0) {
+      ok = mbar_wait(mb, parity[st]);
+      bulk_wait_read_all();  // the previous image has left shared memory
+    }
+    if (!__syncthreads_and(ok)) {
+      const FileDesc F = files[blk_file[B.b]];
+      if (tid == 0) report(errs + F.job, E_TIMEOUT, 0, B.b);
+      return false;
+    }
+    parity[st] ^= 1u;
+    const StgEnt* E = ents + st * kStgMaxEnt;
+    const uint8_t* stg = stage + st * size_t(S);
+    const uint32_t P = B.phase, m = B.m;
+    const uint32_t contents = uint32_t(B.contents), msg = contents + 1;
+    const uint32_t nr = (m + R - 1) / R;
+    const uint32_t rbase = contents - 4 - 4 * nr;
+    // headers
+    if (tid < m) {
+      const StgEnt e = E[tid];
+      uint8_t* p = img + P + e.eoff;
+      uint32_t q = put_varint(p, e.shr);
+      q += put_varint(p + q, e.nsh);
+      put_varint(p + q, e.vlen);
+    }
+    // key delta and value: one warp per entry; 16-byte image words inside the value from
+    // the staging buffer with funnel shifts, the value's ragged ends and the key bytewise
+    for (uint32_t k = warp; k < m; k += kStgWarps) {
+      const StgEnt e = E[k];
+      const uint32_t v0 = P + e.vb, v1 = v0 + e.vlen;  // image positions of the value
+      const uint32_t kd = v0 - e.nsh;
+      for (uint32_t t = lane; t < e.nsh; t += 32) img[kd + t] = stg[e.ks + t];
+      const uint32_t h1 = min((v0 + 15) & ~15u, v1), t0 = max(v1 & ~15u, h1);
+      if (lane < h1 - v0) img[v0 + lane] = stg[e.vs + lane];
+      if (lane < v1 - t0) img[t0 + lane] = stg[e.vs + (t0 - v0) + lane];
+      const uint32_t dsrc = e.vs - v0;  // staging offset = image position + dsrc
+      for (uint32_t w = h1 + 16 * lane; w + 16 <= t0; w += 512) {
+        const uint32_t src = w + dsrc;
+        const uint4* q = reinterpret_cast<const uint4*>(stg + (src & ~15u));
+        const uint32_t sh = src & 15u;
+        const uint4 u0 = q[0];
+        *reinterpret_cast<uint4*>(img + w) = sh ? shift32(u0, q[1], sh) : u0;
+      }
+    }
+    // restart array, restart count, type byte
+    for (uint32_t t = tid; t < 4 * nr; t += kStgThreads)
+      img[P + rbase + t] = uint8_t(E[(t >> 2) * R].eoff >> (8 * (t & 3u)));
+    if (tid < 4) img[P + contents - 4 + tid] = uint8_t(nr >> (8 * tid));
+    if (tid == 4) img[P + contents] = 0;
+    fence_proxy_async();
+    __syncthreads();
+    // store: aligned middle in bulk, ragged ends bytewise
+    const uint32_t i0 = (P + 15) & ~15u, i1 = (P + msg) & ~15u;
+    uint8_t* g = B.dst - P;  // 16-byte aligned
+    if (i1 > i0) {
+      if (tid == 0) {
+        bulk_store(g + i0, img_a + i0, i1 - i0);
+        bulk_commit();
+      }
+      if (tid >= 32 && tid < 32 + (i0 - P)) g[P + (tid - 32)] = img[P + (tid - 32)];
+      if (tid >= 64 && tid < 64 + (P + msg - i1)) g[i1 + (tid - 64)] = img[i1 + (tid - 64)];
+    } else {
+      for (uint32_t t = tid; t < msg; t += kStgThreads) g[P + t] = img[P + t];
+    }
+    if (tid == 0) done[B.b] = 1;
+    return true;
+  };
+
+  StgBlk cur{}, nxt{};
+  uint32_t st = 0;
+  uint32_t b = blockIdx.x;
+  if (b < nb) prepare(b, 0, cur);
+  for (; b < nb; b += gridDim.x) {
+    const uint32_t bn = b + gridDim.x;
+    nxt.state = 0;
+    if (bn < nb) prepare(bn, st ^ 1u, nxt);
+    if (!consume(st, cur)) {
+      // a copy never completed: wait (bounded) for what is still in flight, then stop
+      if (nxt.state == 1) mbar_wait(st ? mbar0 : mbar1, parity[st ^ 1u]);
+      mbar_wait(st ? mbar1 : mbar0, parity[st]);
+      break;
+    }
+    __syncthreads();
+    cur = nxt;
+    st ^= 1u;
+  }
+  if (tid == 0) bulk_wait_all();
 }
 
 // Masked CRC-32C trailers of the blocks k_encode wrote (done[b] = 1): one warp per block,
@@ -750,10 +843,10 @@ __global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(const Counts* _
                                                                   uint8_t* __restrict__ out, uint64_t out_cap,
                                                                   const uint8_t* __restrict__ done, CrcTabs tabs) {
   extern __shared__ uint32_t s_crc[];
-  load_rep_tables(s_crc, s_crc + kRepWords, tabs);
+  load_rep_tables992(s_crc, s_crc + kRepWords, tabs);
   __syncthreads();
-  const uint32_t tb0 = smem_addr(s_crc), zb = smem_addr(s_crc + kRepWords);
   const uint32_t lane = lane_id();
+  const uint32_t tl = smem_addr(s_crc) + lane * 4u, tz = smem_addr(s_crc + kRepWords);
   const uint32_t nb = cnt->nb;
   const uint64_t warps = gstride() / 32;
   for (uint64_t b = gtid() / 32; b < nb; b += warps) {
@@ -762,7 +855,7 @@ __global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(const Counts* _
     if (F.off + F.size > out_cap) continue;
     uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
     const uint64_t contents = bsz[b];
-    const uint32_t crc = warp_crc32c_il(dst, contents + 1, tb0, zb, tabs);
+    const uint32_t crc = warp_crc32c_u32(dst, contents + 1, tl, tz, tabs);
     if (lane == 0) st_u32(dst + contents + 1, crc_mask(crc));
   }
 }
@@ -1008,9 +1101,10 @@ __global__ void k_build_check(Recs recs, const uint8_t* __restrict__ arena, uint
 }  // namespace
 
 void launch_sizes(const uint32_t* surv, const Counts* cnt, uint32_t cap, const JobDev* jobs, uint32_t n_jobs,
-                  Recs recs, const uint8_t* arena, uint32_t* lcp, uint32_t* sd, uint32_t* dr, cudaStream_t st) {
+                  Recs recs, const uint8_t* arena, uint32_t* lcp, uint32_t* sd, uint32_t* dr, EncDesc* ed,
+                  cudaStream_t st) {
   if (!cap) return;
-  k_sizes<<<grid_for(cap, 256), 256, 0, st>>>(surv, cnt, jobs, n_jobs, recs, arena, lcp, sd, dr); count_launches(1);
+  k_sizes<<<grid_for(cap, 256), 256, 0, st>>>(surv, cnt, jobs, n_jobs, recs, arena, lcp, sd, dr, ed); count_launches(1);
 }
 
 void launch_block_next(const uint64_t* P, const uint32_t* dr, const Counts* cnt, uint32_t cap, const JobDev* jobs,
@@ -1095,22 +1189,39 @@ void launch_zero_bitmap(uint32_t* bitmap, const Counts* cnt, uint64_t cap_words,
   k_zero_words<<<grid_for(cap_words, 256), 256, 0, st>>>(bitmap, cnt, cap_words); count_launches(1);
 }
 
-void launch_encode(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
+// Buffer bytes of the staged encoder. A block's contents are below T plus its last entry,
+// and an entry is at most key + value + 11 bytes (max_kv: largest key + value length of the
+// inputs, 0 when unknown); staging adds up to 30 bytes of alignment per entry.
+static void stg_sizes(uint32_t T, uint32_t max_kv, uint32_t* S, uint32_t* I) {
+  uint64_t img = uint64_t(T) + (max_kv ? uint64_t(max_kv) + 11 : uint64_t(T)) + 64;
+  uint64_t stage = img + (T / 4 > 1024 ? T / 4 : 1024);
+  img = (img + 127) & ~uint64_t(127);
+  stage = (stage + 127) & ~uint64_t(127);
+  *I = uint32_t(img > 64 * 1024 ? 64 * 1024 : img);
+  *S = uint32_t(stage > 64 * 1024 ? 64 * 1024 : stage);
+}
+
+void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                    const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
-                   const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
-                   Fmt fmt, uint8_t* out, uint64_t out_cap, uint8_t* done, CrcTabs tabs, cudaStream_t st) {
+                   const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, const EncDesc* ed, Recs recs,
+                   const uint8_t* arena, Fmt fmt, uint32_t max_kv, uint8_t* out, uint64_t out_cap, uint8_t* done,
+                   uint32_t* big, DErr* errs, CrcTabs tabs, cudaStream_t st) {
   if (!cap) return;
-  cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kEncSmem));
-  k_encode<<<kSms, kEncWarps * 32, kEncSmem, st>>>(blk_start, cnt, blk_file, files, C, bsz, surv, lcp, recs,
-                                                       arena, fmt, out, out_cap, done);
+  uint32_t S, I;
+  stg_sizes(fmt.T, max_kv, &S, &I);
+  const uint32_t smem = ((kStgHead + 127) & ~127u) + 2 * S + I + 16;
+  uint32_t per_sm = (227u * 1024u) / (smem + 1024u);
+  per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+  cudaFuncSetAttribute(k_encode_stg, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  k_encode_stg<<<kSms * per_sm, kStgThreads, smem, st>>>(blk_start, cnt, blk_file, files, C, bsz, lcp, ed, fmt, out,
+                                                          out_cap, done, big, errs, S, I);
   count_launches(1);
   cudaFuncSetAttribute(k_block_crc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCrcSmem));
   k_block_crc<<<kSms, kCrcWarps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done, tabs);
   count_launches(1);
   cudaFuncSetAttribute(k_encode_big, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kEncBuf));
-  k_encode_big<<<grid_for(cap, 1, kSms * 3), kEncThreads, kEncBuf, st>>>(blk_start, cnt, blk_file, files, C, bsz,
-                                                                         surv, lcp, sd, dr, recs, arena, fmt, out,
-                                                                         out_cap, done, tabs);
+  k_encode_big<<<kSms, kEncThreads, kEncBuf, st>>>(blk_start, cnt, blk_file, files, C, bsz, surv, lcp, sd, dr, recs,
+                                                   arena, fmt, out, out_cap, big, tabs);
   count_launches(1);
 }
 
