@@ -522,25 +522,25 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_big(const uint32_t* __re
 
 
 // ---- staged encoder (TMA) -------------------------------------------------------------------
-// A CTA of kStgThreads threads encodes one data block at a time and keeps the next block's
-// bytes in flight:
-//   prepare(b): one thread per entry reads the survivor's descriptor (survivor order,
-//     coalesced) and its shared-prefix length; a CTA scan places every entry in the block
-//     and in a staging buffer; each entry's key delta and value are fetched into the
-//     staging buffer by bulk asynchronous copies (cp.async.bulk, completion counted in
-//     bytes on the buffer's mbarrier) as whole aligned 16-byte ranges.
-//   consume(b): the block image is assembled in shared memory at its destination's
-//     16-byte phase: headers, key deltas, value edges, restart array and type byte
-//     bytewise; every 16-byte image word inside one value comes from the staging buffer
-//     with funnel shifts. The aligned middle of the image leaves in one bulk store
-//     (cp.async.bulk shared -> global); the ragged ends with byte stores.
-// Two staging buffers and one image buffer per CTA; several CTAs per SM. Blocks with more
-// than kStgMaxEnt entries or larger than the buffers go to k_encode_big. The CRC trailer is
-// written afterwards by k_block_crc.
-constexpr uint32_t kStgThreads = 256;
-constexpr uint32_t kStgWarps = kStgThreads / 32;
+// A CTA encodes data blocks b = blockIdx.x, + gridDim.x, ... with one producer warp and
+// kStgConsumers consumer warps, two staging slots in flight:
+//   producer: one lane per entry reads the survivor's descriptor (survivor order,
+//     coalesced) and its shared-prefix length; a warp scan places every entry in the block
+//     and in the slot's staging buffer; each entry's key delta and value are fetched into
+//     the staging buffer by bulk asynchronous copies (cp.async.bulk, completion counted
+//     in bytes on the slot's "full" mbarrier) as whole aligned 16-byte ranges. It refills
+//     a slot once the consumers release it on the slot's "empty" mbarrier.
+//   consumers: assemble the block image in shared memory at its destination's 16-byte
+//     phase: headers, key deltas, value edges, restart array and type byte bytewise; every
+//     16-byte image word inside one value comes from the staging buffer with funnel
+//     shifts (one warp per entry). The aligned middle of the image leaves in one bulk
+//     store (cp.async.bulk shared -> global); the ragged ends with byte stores.
+// Blocks with more than kStgMaxEnt entries or larger than the buffers go to k_encode_big.
+// The CRC trailer is written afterwards by k_block_crc.
+constexpr uint32_t kStgConsumers = 8;
+constexpr uint32_t kStgThreads = 32 * (kStgConsumers + 1);
+constexpr uint32_t kStgCons = 32 * kStgConsumers;  // consumer threads
 constexpr uint32_t kStgMaxEnt = 128;
-constexpr uint32_t kStgHead = 16 + 2 * kStgMaxEnt * 32 + 64;  // mbarriers, entry tables, scan scratch
 
 struct StgEnt {
   uint32_t eoff;  // entry offset in the block
@@ -550,6 +550,20 @@ struct StgEnt {
   uint32_t vb;    // block offset of the value's first byte
   uint32_t pad;
 };
+
+struct StgInfo {     // one slot's block, written by the producer before "full" completes
+  uint64_t dst;      // block start in the output
+  uint32_t b, m;
+  uint32_t contents, phase;
+  uint32_t state;    // 1 staged, 2 nothing to do (sent to k_encode_big or out of range)
+  uint32_t pad;
+};
+
+// shared memory: 4 mbarriers | 2 StgInfo | entries [2][kStgMaxEnt] | sources [2][kStgMaxEnt]
+constexpr uint32_t kStgOffInfo = 32;
+constexpr uint32_t kStgOffEnt = kStgOffInfo + 2 * 32;
+constexpr uint32_t kStgOffSrc = kStgOffEnt + 2 * kStgMaxEnt * 32;
+constexpr uint32_t kStgHead = kStgOffSrc + 2 * kStgMaxEnt * 16;
 
 __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
@@ -609,15 +623,20 @@ __device__ __forceinline__ uint32_t hdr_len(uint32_t shr, uint32_t nsh, uint32_t
   return varint_size(shr) + varint_size(nsh) + varint_size(vlen);
 }
 
-// Per-block state kept in registers (the same in every thread of the CTA).
-struct StgBlk {
-  uint32_t b;         // block index
-  uint32_t m;         // entries
-  uint32_t state;     // 0 none, 1 loads in flight, 2 skipped
-  uint32_t phase;     // destination address mod 16
-  uint64_t contents;  // block contents size (without the 5-byte trailer)
-  uint8_t* dst;       // block start in the output
-};
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kStgCons) : "memory"); }
+// Barrier of the consumer threads that also ANDs a predicate across them.
+__device__ __forceinline__ bool consumers_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(r)
+      : "r"(uint32_t(v)), "n"(kStgCons)
+      : "memory");
+  return r != 0;
+}
 
 __global__ void __launch_bounds__(kStgThreads) k_encode_stg(const uint32_t* __restrict__ start,
                                                             Counts* __restrict__ cnt,
@@ -633,201 +652,209 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(const uint32_t* __re
   extern __shared__ __align__(128) uint8_t s_stg[];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint32_t sbase = smem_addr(s_stg);
-  const uint32_t mbar0 = sbase, mbar1 = sbase + 8;
-  StgEnt* ents = reinterpret_cast<StgEnt*>(s_stg + 16);             // [2][kStgMaxEnt]
-  uint32_t* scratch = reinterpret_cast<uint32_t*>(s_stg + 16 + 2 * kStgMaxEnt * 32);  // [16]
-  uint8_t* stage = s_stg + ((kStgHead + 127) & ~127u);              // [2][S]
-  uint8_t* img = stage + 2 * size_t(S);                             // [I + 16]
+  // mbarriers: full[0], full[1], empty[0], empty[1]
+  auto full = [&](uint32_t sl) { return sbase + 8 * sl; };
+  auto empty = [&](uint32_t sl) { return sbase + 16 + 8 * sl; };
+  StgInfo* info = reinterpret_cast<StgInfo*>(s_stg + kStgOffInfo);
+  StgEnt* ents = reinterpret_cast<StgEnt*>(s_stg + kStgOffEnt);
+  uint64_t* srcs = reinterpret_cast<uint64_t*>(s_stg + kStgOffSrc);
+  uint8_t* stage = s_stg + ((kStgHead + 127) & ~127u);  // [2][S]
+  uint8_t* img = stage + 2 * size_t(S);                  // [I + 16]
   const uint32_t stage_a = smem_addr(stage), img_a = smem_addr(img);
   const uint32_t R = fmt.R;
   const uint32_t nb = cnt->nb;
   if (tid == 0) {
-    mbar_init(mbar0, 1);
-    mbar_init(mbar1, 1);
+    mbar_init(full(0), 1);
+    mbar_init(full(1), 1);
+    mbar_init(empty(0), 1);
+    mbar_init(empty(1), 1);
     fence_proxy_async();
   }
   __syncthreads();
-  uint32_t parity[2] = {0, 0};
 
-  auto prepare = [&](uint32_t b, uint32_t st, StgBlk& B) {
-    B.b = b;
-    B.state = 2;
-    const uint32_t s0 = start[b], m = start[b + 1] - s0;
-    B.m = m;
-    const FileDesc F = files[blk_file[b]];
-    B.contents = bsz[b];
-    B.dst = out + F.off + (C[b] - C[F.blk_begin]);
-    B.phase = uint32_t(reinterpret_cast<uintptr_t>(B.dst) & 15u);
-    if (F.off + F.size > out_cap) {
-      if (tid == 0) done[b] = 0;
-      return;
-    }
-    bool fits = m <= kStgMaxEnt && B.phase + B.contents + 1 <= I;
-    // entry layout: one thread per entry
-    uint32_t esz = 0, ssz = 0, shr = 0, nsh = 0, vlen = 0, kc = 0, vc = 0;
-    uint64_t kp = 0, vp = 0;
-    if (fits && tid < m) {
-      const EncDesc d = ed[s0 + tid];
-      shr = (tid % R) == 0 ? 0u : lcp[s0 + tid];
-      nsh = d.klen - shr;
-      vlen = d.vlen;
-      kp = d.kptr + shr;
-      vp = d.vptr;
-      kc = nsh ? uint32_t(((kp + nsh + 15) & ~uint64_t(15)) - (kp & ~uint64_t(15))) : 0u;
-      vc = vlen ? uint32_t(((vp + vlen + 15) & ~uint64_t(15)) - (vp & ~uint64_t(15))) : 0u;
-      esz = hdr_len(shr, nsh, vlen) + nsh + vlen;
-      ssz = kc + vc;
-    }
-    // CTA exclusive scan of (esz, ssz)
-    uint32_t xe = esz, xs = ssz;
+  __shared__ uint32_t s_fills[2], s_used[2];
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    uint32_t j = 0;
+    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x, ++j) {
+      const uint32_t sl = j & 1u;
+      if (j >= 2 && !mbar_wait(empty(sl), ((j >> 1) - 1) & 1u)) {
+        if (lane == 0) report(errs + files[blk_file[b]].job, E_TIMEOUT, 0, b);
+        break;
+      }
+      StgInfo inf{};
+      const uint32_t s0 = start[b], m = start[b + 1] - s0;
+      const FileDesc F = files[blk_file[b]];
+      inf.b = b;
+      inf.m = m;
+      inf.contents = uint32_t(bsz[b]);
+      uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
+      inf.dst = reinterpret_cast<uint64_t>(dst);
+      inf.phase = uint32_t(reinterpret_cast<uintptr_t>(dst) & 15u);
+      inf.state = 2;
+      bool fits = F.off + F.size <= out_cap && m <= kStgMaxEnt && inf.phase + inf.contents + 1 <= I;
+      uint32_t ce = 0, cs = 0;  // running entry / staging offsets
+      StgEnt* E = ents + sl * kStgMaxEnt;
+      uint64_t* SRC = srcs + sl * 2 * kStgMaxEnt;
+      for (uint32_t k0 = 0; fits && k0 < m; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        uint32_t esz = 0, ssz = 0, shr = 0, nsh = 0, vlen = 0, kc = 0;
+        uint64_t kp = 0, vp = 0;
+        if (k < m) {
+          const EncDesc d = ed[s0 + k];
+          shr = (k % R) == 0 ? 0u : lcp[s0 + k];
+          nsh = d.klen - shr;
+          vlen = d.vlen;
+          kp = d.kptr + shr;
+          vp = d.vptr;
+          kc = nsh ? uint32_t(((kp + nsh + 15) & ~uint64_t(15)) - (kp & ~uint64_t(15))) : 0u;
+          const uint32_t vc = vlen ? uint32_t(((vp + vlen + 15) & ~uint64_t(15)) - (vp & ~uint64_t(15))) : 0u;
+          esz = hdr_len(shr, nsh, vlen) + nsh + vlen;
+          ssz = kc + vc;
+        }
+        uint32_t xe = esz, xs = ssz;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t oe = __shfl_up_sync(0xFFFFFFFFu, xe, d), os = __shfl_up_sync(0xFFFFFFFFu, xs, d);
-      if (lane >= uint32_t(d)) {
-        xe += oe;
-        xs += os;
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t oe = __shfl_up_sync(0xFFFFFFFFu, xe, d), os = __shfl_up_sync(0xFFFFFFFFu, xs, d);
+          if (lane >= uint32_t(d)) {
+            xe += oe;
+            xs += os;
+          }
+        }
+        if (k < m) {
+          StgEnt e;
+          e.eoff = ce + xe - esz;
+          const uint32_t soff = cs + xs - ssz;
+          e.shr = shr;
+          e.nsh = nsh;
+          e.vlen = vlen;
+          e.ks = soff + uint32_t(kp & 15u);
+          e.vs = soff + kc + uint32_t(vp & 15u);
+          e.vb = e.eoff + esz - vlen;
+          e.pad = 0;
+          E[k] = e;
+          SRC[2 * k] = kp;
+          SRC[2 * k + 1] = vp;
+        }
+        ce += __shfl_sync(0xFFFFFFFFu, xe, 31);
+        cs += __shfl_sync(0xFFFFFFFFu, xs, 31);
+        fits = cs <= S;
+      }
+      if (fits) inf.state = 1;
+      if (lane == 0) {
+        if (!fits) {
+          done[b] = 0;
+          if (F.off + F.size <= out_cap) big[atomicAdd(&cnt->big_blocks, 1u)] = b;
+        }
+        info[sl] = inf;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive_expect_tx(full(sl), fits ? cs : 0u);
+      __syncwarp();
+      if (fits) {
+        const uint32_t dst0 = stage_a + sl * S;
+        for (uint32_t k = lane; k < m; k += 32) {
+          const StgEnt e = E[k];
+          const uint64_t kp = SRC[2 * k], vp = SRC[2 * k + 1];
+          const uint32_t kb = uint32_t(kp & 15u), vb = uint32_t(vp & 15u);
+          if (e.nsh) {
+            const uint32_t kc = (kb + e.nsh + 15) & ~15u;
+            bulk_load(dst0 + e.ks - kb, reinterpret_cast<const void*>(kp - kb), kc, full(sl));
+          }
+          if (e.vlen) {
+            const uint32_t vc = (vb + e.vlen + 15) & ~15u;
+            bulk_load(dst0 + e.vs - vb, reinterpret_cast<const void*>(vp - vb), vc, full(sl));
+          }
+        }
       }
     }
-    __syncthreads();  // scratch reuse
-    if (lane == 31) {
-      scratch[warp] = xe;
-      scratch[kStgWarps + warp] = xs;
+    if (lane == 0) {
+      s_fills[0] = (j + 1) >> 1;  // fills of slot 0 and slot 1
+      s_fills[1] = j >> 1;
     }
-    __syncthreads();
-    uint32_t be = 0, bs = 0, te = 0, ts = 0;
-#pragma unroll
-    for (uint32_t w = 0; w < kStgWarps; ++w) {
-      const uint32_t ve = scratch[w], vs = scratch[kStgWarps + w];
-      if (w < warp) {
-        be += ve;
-        bs += vs;
-      }
-      te += ve;
-      ts += vs;
-    }
-    fits = fits && ts <= S;
-    if (!fits) {
-      if (tid == 0) {
-        done[b] = 0;
-        big[atomicAdd(&cnt->big_blocks, 1u)] = b;
-      }
-      return;
-    }
-    const uint32_t soff = bs + xs - ssz;
-    if (tid < m) {
-      StgEnt e;
-      e.eoff = be + xe - esz;
-      e.shr = shr;
-      e.nsh = nsh;
-      e.vlen = vlen;
-      e.ks = soff + uint32_t(kp & 15u);
-      e.vs = soff + kc + uint32_t(vp & 15u);
-      e.vb = e.eoff + esz - vlen;
-      e.pad = 0;
-      ents[st * kStgMaxEnt + tid] = e;
-    }
-    const uint32_t mb = st ? mbar1 : mbar0;
-    if (tid == 0) mbar_arrive_expect_tx(mb, ts);
-    __syncthreads();
-    if (tid < m) {
-      const uint32_t dst0 = stage_a + st * S + soff;
-      if (kc) bulk_load(dst0, reinterpret_cast<const void*>(kp & ~uint64_t(15)), kc, mb);
-      if (vc) bulk_load(dst0 + kc, reinterpret_cast<const void*>(vp & ~uint64_t(15)), vc, mb);
-    }
-    B.state = 1;
-  };
+  }
 
-  // returns false when the block's copies did not complete in time (the kernel then stops)
-  auto consume = [&](uint32_t st, const StgBlk& B) -> bool {
-    if (B.state != 1) return true;
-    const uint32_t mb = st ? mbar1 : mbar0;
-    bool ok = true;
-    if (tid == 0) {
-      ok = mbar_wait(mb, parity[st]);
-      bulk_wait_read_all();  // the previous image has left shared memory
-    }
-    if (!__syncthreads_and(ok)) {
-      const FileDesc F = files[blk_file[B.b]];
-      if (tid == 0) report(errs + F.job, E_TIMEOUT, 0, B.b);
-      return false;
-    }
-    parity[st] ^= 1u;
-    const StgEnt* E = ents + st * kStgMaxEnt;
-    const uint8_t* stg = stage + st * size_t(S);
-    const uint32_t P = B.phase, m = B.m;
-    const uint32_t contents = uint32_t(B.contents), msg = contents + 1;
-    const uint32_t nr = (m + R - 1) / R;
-    const uint32_t rbase = contents - 4 - 4 * nr;
-    // headers
-    if (tid < m) {
-      const StgEnt e = E[tid];
-      uint8_t* p = img + P + e.eoff;
-      uint32_t q = put_varint(p, e.shr);
-      q += put_varint(p + q, e.nsh);
-      put_varint(p + q, e.vlen);
-    }
-    // key delta and value: one warp per entry; 16-byte image words inside the value from
-    // the staging buffer with funnel shifts, the value's ragged ends and the key bytewise
-    for (uint32_t k = warp; k < m; k += kStgWarps) {
-      const StgEnt e = E[k];
-      const uint32_t v0 = P + e.vb, v1 = v0 + e.vlen;  // image positions of the value
-      const uint32_t kd = v0 - e.nsh;
-      for (uint32_t t = lane; t < e.nsh; t += 32) img[kd + t] = stg[e.ks + t];
-      const uint32_t h1 = min((v0 + 15) & ~15u, v1), t0 = max(v1 & ~15u, h1);
-      if (lane < h1 - v0) img[v0 + lane] = stg[e.vs + lane];
-      if (lane < v1 - t0) img[t0 + lane] = stg[e.vs + (t0 - v0) + lane];
-      const uint32_t dsrc = e.vs - v0;  // staging offset = image position + dsrc
-      for (uint32_t w = h1 + 16 * lane; w + 16 <= t0; w += 512) {
-        const uint32_t src = w + dsrc;
-        const uint4* q = reinterpret_cast<const uint4*>(stg + (src & ~15u));
-        const uint32_t sh = src & 15u;
-        const uint4 u0 = q[0];
-        *reinterpret_cast<uint4*>(img + w) = sh ? shift32(u0, q[1], sh) : u0;
-      }
-    }
-    // restart array, restart count, type byte
-    for (uint32_t t = tid; t < 4 * nr; t += kStgThreads)
-      img[P + rbase + t] = uint8_t(E[(t >> 2) * R].eoff >> (8 * (t & 3u)));
-    if (tid < 4) img[P + contents - 4 + tid] = uint8_t(nr >> (8 * tid));
-    if (tid == 4) img[P + contents] = 0;
-    fence_proxy_async();
-    __syncthreads();
-    // store: aligned middle in bulk, ragged ends bytewise
-    const uint32_t i0 = (P + 15) & ~15u, i1 = (P + msg) & ~15u;
-    uint8_t* g = B.dst - P;  // 16-byte aligned
-    if (i1 > i0) {
-      if (tid == 0) {
-        bulk_store(g + i0, img_a + i0, i1 - i0);
-        bulk_commit();
-      }
-      if (tid >= 32 && tid < 32 + (i0 - P)) g[P + (tid - 32)] = img[P + (tid - 32)];
-      if (tid >= 64 && tid < 64 + (P + msg - i1)) g[i1 + (tid - 64)] = img[i1 + (tid - 64)];
-    } else {
-      for (uint32_t t = tid; t < msg; t += kStgThreads) g[P + t] = img[P + t];
-    }
-    if (tid == 0) done[B.b] = 1;
-    return true;
-  };
-
-  StgBlk cur{}, nxt{};
-  uint32_t st = 0;
-  uint32_t b = blockIdx.x;
-  if (b < nb) prepare(b, 0, cur);
-  for (; b < nb; b += gridDim.x) {
-    const uint32_t bn = b + gridDim.x;
-    nxt.state = 0;
-    if (bn < nb) prepare(bn, st ^ 1u, nxt);
-    if (!consume(st, cur)) {
-      // a copy never completed: wait (bounded) for what is still in flight, then stop
-      if (nxt.state == 1) mbar_wait(st ? mbar0 : mbar1, parity[st ^ 1u]);
-      mbar_wait(st ? mbar1 : mbar0, parity[st]);
+  // ---------------- consumers ----------------
+  const uint32_t ct = tid - 32, cw = warp - 1;  // consumer thread / warp index
+  uint32_t j = 0;
+  for (uint32_t b = blockIdx.x; warp != 0 && b < nb; b += gridDim.x, ++j) {
+    const uint32_t sl = j & 1u;
+    if (!consumers_all(mbar_wait(full(sl), (j >> 1) & 1u))) {
+      if (ct == 0) report(errs + files[blk_file[b]].job, E_TIMEOUT, 0, b);
       break;
     }
-    __syncthreads();
-    cur = nxt;
-    st ^= 1u;
+    const StgInfo inf = info[sl];
+    if (inf.state == 1) {
+      if (ct == 0) bulk_wait_read_all();  // the previous image has left shared memory
+      consumers_sync();
+      const StgEnt* E = ents + sl * kStgMaxEnt;
+      const uint8_t* stg = stage + sl * size_t(S);
+      const uint32_t P = inf.phase, m = inf.m;
+      const uint32_t contents = inf.contents, msg = contents + 1;
+      const uint32_t nr = (m + R - 1) / R;
+      const uint32_t rbase = contents - 4 - 4 * nr;
+      if (ct < m) {  // headers
+        const StgEnt e = E[ct];
+        uint8_t* p = img + P + e.eoff;
+        uint32_t q = put_varint(p, e.shr);
+        q += put_varint(p + q, e.nsh);
+        put_varint(p + q, e.vlen);
+      }
+      // key delta and value: one warp per entry; 16-byte image words inside the value from
+      // the staging buffer with funnel shifts, the value's ragged ends and the key bytewise
+      for (uint32_t k = cw; k < m; k += kStgConsumers) {
+        const StgEnt e = E[k];
+        const uint32_t v0 = P + e.vb, v1 = v0 + e.vlen;  // image positions of the value
+        const uint32_t kd = v0 - e.nsh;
+        for (uint32_t t = lane; t < e.nsh; t += 32) img[kd + t] = stg[e.ks + t];
+        const uint32_t h1 = min((v0 + 15) & ~15u, v1), t0 = max(v1 & ~15u, h1);
+        if (lane < h1 - v0) img[v0 + lane] = stg[e.vs + lane];
+        if (lane < v1 - t0) img[t0 + lane] = stg[e.vs + (t0 - v0) + lane];
+        const uint32_t dsrc = e.vs - v0;  // staging offset = image position + dsrc
+        for (uint32_t w = h1 + 16 * lane; w + 16 <= t0; w += 512) {
+          const uint32_t src = w + dsrc;
+          const uint4* q = reinterpret_cast<const uint4*>(stg + (src & ~15u));
+          const uint32_t sh = src & 15u;
+          const uint4 u0 = q[0];
+          *reinterpret_cast<uint4*>(img + w) = sh ? shift32(u0, q[1], sh) : u0;
+        }
+      }
+      for (uint32_t t = ct; t < 4 * nr; t += kStgCons)  // restart array
+        img[P + rbase + t] = uint8_t(E[(t >> 2) * R].eoff >> (8 * (t & 3u)));
+      if (ct < 4) img[P + contents - 4 + ct] = uint8_t(nr >> (8 * ct));
+      if (ct == 4) img[P + contents] = 0;
+      fence_proxy_async();
+      consumers_sync();  // image complete; the slot's staging buffer is no longer read
+      if (ct == 0) mbar_arrive(empty(sl));
+      // store: aligned middle in bulk, ragged ends bytewise
+      const uint32_t i0 = (P + 15) & ~15u, i1 = (P + msg) & ~15u;
+      uint8_t* g = reinterpret_cast<uint8_t*>(inf.dst) - P;  // 16-byte aligned
+      if (i1 > i0) {
+        if (ct == 0) {
+          bulk_store(g + i0, img_a + i0, i1 - i0);
+          bulk_commit();
+        }
+        if (ct >= 32 && ct < 32 + (i0 - P)) g[P + (ct - 32)] = img[P + (ct - 32)];
+        if (ct >= 64 && ct < 64 + (P + msg - i1)) g[i1 + (ct - 64)] = img[i1 + (ct - 64)];
+      } else {
+        for (uint32_t t = ct; t < msg; t += kStgCons) g[P + t] = img[P + t];
+      }
+      if (ct == 0) done[inf.b] = 1;
+    } else {
+      consumers_sync();  // every consumer has read the slot's info
+      if (ct == 0) mbar_arrive(empty(sl));
+    }
   }
-  if (tid == 0) bulk_wait_all();
+  if (tid == 32) {
+    bulk_wait_all();
+    s_used[0] = (j + 1) >> 1;  // slots consumed (or abandoned) by the consumers
+    s_used[1] = j >> 1;
+  }
+  __syncthreads();
+  // after a timeout, let copies still in flight land before the CTA exits (bounded)
+  if (tid == 0)
+    for (uint32_t sl = 0; sl < 2; ++sl)
+      if (s_fills[sl] > s_used[sl]) mbar_wait(full(sl), (s_fills[sl] - 1) & 1u);
 }
 
 // Masked CRC-32C trailers of the blocks k_encode wrote (done[b] = 1): one warp per block,
