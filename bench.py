@@ -183,10 +183,10 @@ def run_ours(args, ws, rank, local):
         ms = float(t.item())
     value = ws * in_bytes / MiB / (ms / 1e3)
 
-    # dominant kernel: block scan [1] (CRC verify of every input block) vs encode [5]
+    # dominant kernel: block scan [1] (CRC verify and walk of every input block) vs encode [5]
     peak, peak_kind = _peaks()
     avg = [statistics.mean(s[i] for s in stages) for i in range(8)]
-    cand = {1: "k_block_scan", 5: "k_encode"}
+    cand = {1: "block scan (k_block_verify + k_block_walk)", 5: "k_encode_stg"}
     dom = max(cand, key=lambda i: avg[i])
     dom_bytes = sbytes[-1][dom]
     achieved = dom_bytes / (avg[dom] / 1e3) / 1e9

@@ -114,9 +114,10 @@ typedef struct {
    *      bytes = input data blocks with trailers (read once)
    *  [2] decode kernel alone      [3] order check + merge sort
    *  [4] drop rule, entry sizes, block and file cut, layout
-   *  [5] encode kernel alone: bytes = output data blocks written + survivor keys and
-   *      values read
-   *  [6] bloom, index, metaindex, footer, boundary keys   [7] whole device span */
+   *  [5] encode kernel alone (block images without their CRC): bytes = output data
+   *      blocks written + survivor keys and values read
+   *  [6] data block CRC trailers, bloom, index, metaindex, footer, boundary keys
+   *  [7] whole device span */
   double stage_ms[LUDA_N_STAGES];
   uint64_t stage_bytes[LUDA_N_STAGES];
   void* _priv;                  /* library bookkeeping: do not touch */

@@ -227,6 +227,7 @@ struct PackBufs {
   uint32_t *surv, *lcp, *sd, *dr, *next, *bpos, *blk_start, *fnext, *fpos, *file_start, *blk_file, *ie;
   uint8_t *sflags, *fflags, *enc_done;
   EncDesc* ed;
+  BlkEnc* bd;
   uint32_t* big;
   uint64_t *P, *bsz, *disk, *C, *IX, *fsize, *foff, *bmw, *bmoff, *klens, *koff;
   FileDesc* files;
@@ -253,6 +254,7 @@ void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t
   b.fflags = L.take<uint8_t>(cap + 1);
   b.enc_done = L.take<uint8_t>(cap + 1);
   b.ed = L.take<EncDesc>(cap + 1);
+  b.bd = L.take<BlkEnc>(cap + 1);
   b.big = L.take<uint32_t>(cap + 1);
   b.P = L.take<uint64_t>(cap + 1);
   b.bsz = L.take<uint64_t>(cap + 1);
@@ -303,9 +305,12 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   launch_file_offsets(b.files, cnt, cap, b.foff, b.bmoff, jobs, n_jobs, out_cap, bm_cap, errs, st);
   launch_zero_bitmap(b.bitmap, cnt, bm_cap, st);
   trace_mark(tr, 7, st);
-  launch_encode(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, b.ed, recs, arena,
+  launch_encode(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, b.ed, b.bd, recs,
+                arena,
                 fmt, fmt.max_kv, out, out_cap, b.enc_done, b.big, errs, tabs, st);
   trace_mark(tr, 8, st);
+  launch_encode_finish(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
+                       fmt, out, out_cap, b.enc_done, b.big, tabs, st);
   launch_bloom(b.surv, cnt, cap, b.blk_file, b.blk_start, b.files, recs, arena, fmt, b.bitmap, out_cap, bm_cap, st);
   launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, out, out_cap,
                      st);
@@ -651,7 +656,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   Recs recs;
   uint8_t* d_arena;
   uint32_t *d_ord0, *d_ord1, *d_keep, *d_pos, *d_co;
-  uint64_t *d_pfx0, *d_pfx1;
+  MKey *d_pfx0, *d_pfx1;
   MergeSpan* d_spans;
   PackBufs pb;
   auto layoutC = [&](Layout& L) {
@@ -659,8 +664,8 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     d_arena = L.take<uint8_t>(K + 64);
     d_ord0 = L.take<uint32_t>(n_rec + 1);
     d_ord1 = L.take<uint32_t>(n_rec + 1);
-    d_pfx0 = L.take<uint64_t>(n_rec + 1);
-    d_pfx1 = L.take<uint64_t>(n_rec + 1);
+    d_pfx0 = L.take<MKey>(n_rec + 1);
+    d_pfx1 = L.take<MKey>(n_rec + 1);
     d_keep = L.take<uint32_t>(n_rec + 1);
     d_pos = L.take<uint32_t>(n_rec + 1);
     d_co = L.take<uint32_t>(max_tiles + 1);
@@ -699,11 +704,11 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   launch_decode(d_blocks, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
   tr.mark(5, st);
   launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
-  launch_sort_init(d_ord0, d_pfx0, recs.pfx, n_rec, st);
+  launch_sort_init(d_ord0, d_pfx0, recs, d_arena, n_rec, st);
   uint32_t* src_o = d_ord0;
   uint32_t* dst_o = d_ord1;
-  uint64_t* src_p = d_pfx0;
-  uint64_t* dst_p = d_pfx1;
+  MKey* src_p = d_pfx0;
+  MKey* dst_p = d_pfx1;
   for (size_t p = 0; p < pass_span0.size(); ++p) {
     launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], d_co, src_o, src_p, dst_o, dst_p, recs,
                       d_arena, st);
@@ -1165,7 +1170,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   Recs recs;
   uint8_t* d_arena;
   uint32_t *d_ord0, *d_ord1, *d_keep, *d_pos, *d_co;
-  uint64_t *d_pfx0, *d_pfx1;
+  MKey *d_pfx0, *d_pfx1;
   MergeSpan* d_spans;
   PackBufs pb;
   auto layC = [&](Layout& L) {
@@ -1173,8 +1178,8 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     d_arena = L.take<uint8_t>(K + 64);
     d_ord0 = L.take<uint32_t>(n_rec + 1);
     d_ord1 = L.take<uint32_t>(n_rec + 1);
-    d_pfx0 = L.take<uint64_t>(n_rec + 1);
-    d_pfx1 = L.take<uint64_t>(n_rec + 1);
+    d_pfx0 = L.take<MKey>(n_rec + 1);
+    d_pfx1 = L.take<MKey>(n_rec + 1);
     d_keep = L.take<uint32_t>(n_rec + 1);
     d_pos = L.take<uint32_t>(n_rec + 1);
     d_co = L.take<uint32_t>(max_tiles + 1);
@@ -1208,11 +1213,11 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     launch_decode(d_blocks, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
     launch_plan_sanitize(recs, n_rec, d_jobs, n_jobs, d_errs, d_arena, st);
     launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
-    launch_sort_init(d_ord0, d_pfx0, recs.pfx, n_rec, st);
+    launch_sort_init(d_ord0, d_pfx0, recs, d_arena, n_rec, st);
     uint32_t* src_o = d_ord0;
     uint32_t* dst_o = d_ord1;
-    uint64_t* src_p = d_pfx0;
-    uint64_t* dst_p = d_pfx1;
+    MKey* src_p = d_pfx0;
+    MKey* dst_p = d_pfx1;
     for (size_t p = 0; p < pass_span0.size(); ++p) {
       launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], d_co, src_o, src_p, dst_o, dst_p,
                         recs, d_arena, st);

@@ -131,24 +131,46 @@ struct Recs {
   uint32_t* src;    // batch-global input index (order check)
 };
 
+// 8 key bytes at p as a big-endian word; bytes at index >= avail read as 0. p may have any
+// alignment: two aligned 8-byte loads (the key arena is padded past its end).
+__device__ __forceinline__ uint64_t key_word(const uint8_t* p, uint32_t avail) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uint64_t* q = reinterpret_cast<const uint64_t*>(a & ~uintptr_t(7));
+  const uint32_t sh = uint32_t(a & 7u) * 8u;
+  uint64_t w = q[0];
+  if (sh) w = (w >> sh) | (q[1] << (64 - sh));
+  if (avail < 8) w &= avail ? (~0ull >> (64 - 8 * avail)) : 0ull;
+  const uint32_t lo = uint32_t(w), hi = uint32_t(w >> 32);
+  return (uint64_t(__byte_perm(lo, 0, 0x0123)) << 32) | __byte_perm(hi, 0, 0x0123);
+}
+
+// Internal key order from byte `from` of the user keys on, given that the bytes before it
+// are equal (zero-padded): user key bytes (8 at a time), proper prefix first, then trailer
+// descending, then record id ascending (input index, then position; 0 for a == b).
+__device__ __forceinline__ int cmp_tail(const Recs& r, const uint8_t* arena, uint32_t a, uint32_t b, uint32_t from,
+                                        bool by_id = true) {
+  const uint32_t la = r.klen[a] - 8, lb = r.klen[b] - 8;
+  const uint8_t* ka = arena + r.koff[a];
+  const uint8_t* kb = arena + r.koff[b];
+  const uint32_t m = la < lb ? la : lb;
+  for (uint32_t i = from; i < m; i += 8) {
+    const uint64_t wa = key_word(ka + i, m - i), wb = key_word(kb + i, m - i);
+    if (wa != wb) return wa < wb ? -1 : 1;
+  }
+  if (la != lb) return la < lb ? -1 : 1;
+  const uint64_t ta = r.tr[a], tb = r.tr[b];
+  if (ta != tb) return ta > tb ? -1 : 1;
+  if (!by_id || a == b) return 0;
+  return a < b ? -1 : 1;
+}
+
 // Internal key order on records: user key ascending (memcmp, proper prefix first), then
 // trailer descending, then record id ascending (input index, then position).
 __device__ __forceinline__ int cmp_rec(const Recs& r, const uint8_t* arena, uint32_t a, uint64_t pa, uint32_t b,
                                        uint64_t pb) {
   if (pa != pb) return pa < pb ? -1 : 1;
   if (a == b) return 0;
-  const uint32_t la = r.klen[a] - 8, lb = r.klen[b] - 8;
-  const uint8_t* ka = arena + r.koff[a];
-  const uint8_t* kb = arena + r.koff[b];
-  const uint32_t m = la < lb ? la : lb;
-  for (uint32_t i = 8; i < m; ++i) {
-    const uint8_t x = ka[i], y = kb[i];
-    if (x != y) return x < y ? -1 : 1;
-  }
-  if (la != lb) return la < lb ? -1 : 1;
-  const uint64_t ta = r.tr[a], tb = r.tr[b];
-  if (ta != tb) return ta > tb ? -1 : 1;
-  return a < b ? -1 : 1;
+  return cmp_tail(r, arena, a, b, 8);
 }
 
 // User keys equal?
@@ -157,8 +179,8 @@ __device__ __forceinline__ bool same_user_key(const Recs& r, const uint8_t* aren
   const uint32_t l = r.klen[a] - 8;
   const uint8_t* ka = arena + r.koff[a];
   const uint8_t* kb = arena + r.koff[b];
-  for (uint32_t i = 8; i < l; ++i)
-    if (ka[i] != kb[i]) return false;
+  for (uint32_t i = 8; i < l; i += 8)
+    if (key_word(ka + i, l - i) != key_word(kb + i, l - i)) return false;
   return true;
 }
 

@@ -86,6 +86,20 @@ struct Counts {
   uint32_t max_kv;          // largest internal key + value length in the inputs (block walk)
 };
 
+// Merge key of a record: the first 16 bytes of its user key as two big-endian words
+// (zero-padded).
+struct MKey {
+  uint64_t h0, h1;
+};
+
+// Per output data block: where and what the encoder writes.
+struct BlkEnc {
+  uint64_t dst;       // byte offset of the block in the output arena
+  uint32_t s0, m;     // first survivor, entries
+  uint32_t contents;  // contents size (without the trailer)
+  uint32_t job;       // job index; bit 31: outside the output arena (skip)
+};
+
 // Per survivor, in survivor order: what the encoder reads of its record.
 struct EncDesc {
   uint64_t kptr;  // device address of the full internal key (key arena)
@@ -156,10 +170,10 @@ void launch_check_order(Recs recs, const uint8_t* arena, uint32_t n_rec, const D
                         cudaStream_t st);
 void launch_plan_sanitize(Recs recs, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, const DErr* errs,
                           const uint8_t* arena, cudaStream_t st);
-void launch_sort_init(uint32_t* ord, uint64_t* opfx, const uint64_t* pfx, uint32_t n, cudaStream_t st);
+void launch_sort_init(uint32_t* ord, MKey* okey, Recs recs, const uint8_t* arena, uint32_t n, cudaStream_t st);
 void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* corank,
-                       const uint32_t* src_ord, const uint64_t* src_pfx, uint32_t* dst_ord, uint64_t* dst_pfx,
-                       Recs recs, const uint8_t* arena, cudaStream_t st);
+                       const uint32_t* src_ord, const MKey* src_key, uint32_t* dst_ord, MKey* dst_key, Recs recs,
+                       const uint8_t* arena, cudaStream_t st);
 void launch_gc_flags(const uint32_t* ord, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, Recs recs,
                      const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st);
 void launch_gc_compact(const uint32_t* ord, const uint32_t* keep, const uint32_t* pos, uint32_t n_rec,
@@ -197,9 +211,16 @@ void launch_file_offsets(FileDesc* files, Counts* cnt, uint32_t cap, const uint6
 void launch_zero_bitmap(uint32_t* bitmap, const Counts* cnt, uint64_t cap_words, cudaStream_t st);
 void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                    const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
-                   const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, const EncDesc* ed, Recs recs,
+                   const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, const EncDesc* ed, BlkEnc* bd,
+                   Recs recs,
                    const uint8_t* arena, Fmt fmt, uint32_t max_kv, uint8_t* out, uint64_t out_cap, uint8_t* done,
                    uint32_t* big, DErr* errs, CrcTabs tabs, cudaStream_t st);
+// CRC trailers of the staged encoder's blocks, and the blocks it left (CTA per block).
+void launch_encode_finish(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
+                          const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
+                          const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs,
+                          const uint8_t* arena, Fmt fmt, uint8_t* out, uint64_t out_cap, const uint8_t* done,
+                          const uint32_t* big, CrcTabs tabs, cudaStream_t st);
 void launch_bloom(const uint32_t* surv, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                   const uint32_t* blk_start, const FileDesc* files, Recs recs, const uint8_t* arena, Fmt fmt,
                   uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st);

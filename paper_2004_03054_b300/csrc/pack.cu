@@ -638,12 +638,26 @@ __device__ __forceinline__ bool consumers_all(bool v) {
   return r != 0;
 }
 
-__global__ void __launch_bounds__(kStgThreads) k_encode_stg(const uint32_t* __restrict__ start,
-                                                            Counts* __restrict__ cnt,
-                                                            const uint32_t* __restrict__ blk_file,
-                                                            const FileDesc* __restrict__ files,
-                                                            const uint64_t* __restrict__ C,
-                                                            const uint64_t* __restrict__ bsz,
+// Per block: destination offset, entries and size for the encoder (one thread per block).
+__global__ void k_block_enc(const uint32_t* __restrict__ start, const Counts* __restrict__ cnt,
+                            const uint32_t* __restrict__ blk_file, const FileDesc* __restrict__ files,
+                            const uint64_t* __restrict__ C, const uint64_t* __restrict__ bsz, uint64_t out_cap,
+                            BlkEnc* __restrict__ bd) {
+  const uint32_t nb = cnt->nb;
+  for (uint64_t b = gtid(); b < nb; b += gstride()) {
+    const FileDesc F = files[blk_file[b]];
+    BlkEnc d;
+    d.dst = F.off + (C[b] - C[F.blk_begin]);
+    d.s0 = start[b];
+    d.m = start[b + 1] - d.s0;
+    d.contents = uint32_t(bsz[b]);
+    d.job = F.job | (F.off + F.size > out_cap ? 0x80000000u : 0u);
+    bd[b] = d;
+  }
+}
+
+__global__ void __launch_bounds__(kStgThreads) k_encode_stg(Counts* __restrict__ cnt,
+                                                            const BlkEnc* __restrict__ bd,
                                                             const uint32_t* __restrict__ lcp,
                                                             const EncDesc* __restrict__ ed, Fmt fmt,
                                                             uint8_t* __restrict__ out, uint64_t out_cap,
@@ -676,23 +690,35 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(const uint32_t* __re
   if (warp == 0) {
     // ---------------- producer ----------------
     uint32_t j = 0;
+    BlkEnc pre{};  // lane l holds the descriptor of block b + l * gridDim.x of the current batch of 32
     for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x, ++j) {
       const uint32_t sl = j & 1u;
+      if ((j & 31u) == 0) {
+        const uint64_t bl = uint64_t(b) + uint64_t(lane) * gridDim.x;
+        if (bl < nb) pre = bd[bl];
+      }
+      const uint32_t src_lane = j & 31u;
+      BlkEnc D;
+      D.dst = __shfl_sync(0xFFFFFFFFu, pre.dst, src_lane);
+      D.s0 = __shfl_sync(0xFFFFFFFFu, pre.s0, src_lane);
+      D.m = __shfl_sync(0xFFFFFFFFu, pre.m, src_lane);
+      D.contents = __shfl_sync(0xFFFFFFFFu, pre.contents, src_lane);
+      D.job = __shfl_sync(0xFFFFFFFFu, pre.job, src_lane);
       if (j >= 2 && !mbar_wait(empty(sl), ((j >> 1) - 1) & 1u)) {
-        if (lane == 0) report(errs + files[blk_file[b]].job, E_TIMEOUT, 0, b);
+        if (lane == 0) report(errs + (D.job & 0x7FFFFFFFu), E_TIMEOUT, 0, b);
         break;
       }
       StgInfo inf{};
-      const uint32_t s0 = start[b], m = start[b + 1] - s0;
-      const FileDesc F = files[blk_file[b]];
+      const uint32_t s0 = D.s0, m = D.m;
       inf.b = b;
       inf.m = m;
-      inf.contents = uint32_t(bsz[b]);
-      uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
+      inf.contents = D.contents;
+      uint8_t* dst = out + D.dst;
       inf.dst = reinterpret_cast<uint64_t>(dst);
       inf.phase = uint32_t(reinterpret_cast<uintptr_t>(dst) & 15u);
       inf.state = 2;
-      bool fits = F.off + F.size <= out_cap && m <= kStgMaxEnt && inf.phase + inf.contents + 1 <= I;
+      const bool in_range = (D.job & 0x80000000u) == 0;
+      bool fits = in_range && m <= kStgMaxEnt && inf.phase + inf.contents + 1 <= I;
       uint32_t ce = 0, cs = 0;  // running entry / staging offsets
       StgEnt* E = ents + sl * kStgMaxEnt;
       uint64_t* SRC = srcs + sl * 2 * kStgMaxEnt;
@@ -744,7 +770,7 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(const uint32_t* __re
       if (lane == 0) {
         if (!fits) {
           done[b] = 0;
-          if (F.off + F.size <= out_cap) big[atomicAdd(&cnt->big_blocks, 1u)] = b;
+          if (in_range) big[atomicAdd(&cnt->big_blocks, 1u)] = b;
         }
         info[sl] = inf;
       }
@@ -780,7 +806,7 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(const uint32_t* __re
   for (uint32_t b = blockIdx.x; warp != 0 && b < nb; b += gridDim.x, ++j) {
     const uint32_t sl = j & 1u;
     if (!consumers_all(mbar_wait(full(sl), (j >> 1) & 1u))) {
-      if (ct == 0) report(errs + files[blk_file[b]].job, E_TIMEOUT, 0, b);
+      if (ct == 0) report(errs + (bd[b].job & 0x7FFFFFFFu), E_TIMEOUT, 0, b);
       break;
     }
     const StgInfo inf = info[sl];
@@ -1230,8 +1256,9 @@ static void stg_sizes(uint32_t T, uint32_t max_kv, uint32_t* S, uint32_t* I) {
 
 void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                    const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
-                   const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, const EncDesc* ed, Recs recs,
-                   const uint8_t* arena, Fmt fmt, uint32_t max_kv, uint8_t* out, uint64_t out_cap, uint8_t* done,
+                   const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, const EncDesc* ed, BlkEnc* bd,
+                   Recs recs, const uint8_t* arena, Fmt fmt, uint32_t max_kv, uint8_t* out, uint64_t out_cap,
+                   uint8_t* done,
                    uint32_t* big, DErr* errs, CrcTabs tabs, cudaStream_t st) {
   if (!cap) return;
   uint32_t S, I;
@@ -1240,9 +1267,17 @@ void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const u
   uint32_t per_sm = (227u * 1024u) / (smem + 1024u);
   per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
   cudaFuncSetAttribute(k_encode_stg, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  k_encode_stg<<<kSms * per_sm, kStgThreads, smem, st>>>(blk_start, cnt, blk_file, files, C, bsz, lcp, ed, fmt, out,
-                                                          out_cap, done, big, errs, S, I);
-  count_launches(1);
+  k_block_enc<<<grid_for(cap, 256), 256, 0, st>>>(blk_start, cnt, blk_file, files, C, bsz, out_cap, bd);
+  k_encode_stg<<<kSms * per_sm, kStgThreads, smem, st>>>(cnt, bd, lcp, ed, fmt, out, out_cap, done, big, errs, S, I);
+  count_launches(2);
+}
+
+void launch_encode_finish(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
+                          const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
+                          const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs,
+                          const uint8_t* arena, Fmt fmt, uint8_t* out, uint64_t out_cap, const uint8_t* done,
+                          const uint32_t* big, CrcTabs tabs, cudaStream_t st) {
+  if (!cap) return;
   cudaFuncSetAttribute(k_block_crc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCrcSmem));
   k_block_crc<<<kSms, kCrcWarps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done, tabs);
   count_launches(1);

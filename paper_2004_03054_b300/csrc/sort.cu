@@ -22,15 +22,17 @@ namespace {
 __device__ __forceinline__ int cmp_ikey(const Recs& r, const uint8_t* arena, uint32_t a, uint32_t b) {
   const uint64_t pa = r.pfx[a], pb = r.pfx[b];
   if (pa != pb) return pa < pb ? -1 : 1;
-  const uint32_t la = r.klen[a] - 8, lb = r.klen[b] - 8;
-  const uint8_t* ka = arena + r.koff[a];
-  const uint8_t* kb = arena + r.koff[b];
-  const uint32_t m = la < lb ? la : lb;
-  for (uint32_t i = 8; i < m; ++i)
-    if (ka[i] != kb[i]) return ka[i] < kb[i] ? -1 : 1;
-  if (la != lb) return la < lb ? -1 : 1;
-  const uint64_t ta = r.tr[a], tb = r.tr[b];
-  return ta == tb ? 0 : (ta > tb ? -1 : 1);
+  return cmp_tail(r, arena, a, b, 8, false);
+}
+
+// Merge key: the first 16 bytes of the user key (big-endian words, zero-padded); ties on
+// it are resolved from the key arena.
+__device__ __forceinline__ int cmp_mkey(const Recs& r, const uint8_t* arena, uint32_t a, const MKey& ka, uint32_t b,
+                                        const MKey& kb) {
+  if (ka.h0 != kb.h0) return ka.h0 < kb.h0 ? -1 : 1;
+  if (ka.h1 != kb.h1) return ka.h1 < kb.h1 ? -1 : 1;
+  if (a == b) return 0;
+  return cmp_tail(r, arena, a, b, 16);
 }
 
 __global__ void k_check_order(Recs recs, const uint8_t* __restrict__ arena, uint32_t n_rec,
@@ -45,25 +47,26 @@ __global__ void k_check_order(Recs recs, const uint8_t* __restrict__ arena, uint
   }
 }
 
-__global__ void k_sort_init(uint32_t* __restrict__ ord, uint64_t* __restrict__ opfx, const uint64_t* __restrict__ pfx,
-                            uint32_t n) {
+__global__ void k_sort_init(uint32_t* __restrict__ ord, MKey* __restrict__ okey, Recs recs,
+                            const uint8_t* __restrict__ arena, uint32_t n) {
   for (uint64_t i = gtid(); i < n; i += gstride()) {
     ord[i] = uint32_t(i);
-    opfx[i] = pfx[i];
+    const uint32_t ul = recs.klen[i] - 8;
+    okey[i] = MKey{recs.pfx[i], key_word(arena + recs.koff[i] + 8, ul > 8 ? ul - 8 : 0u)};
   }
 }
 
 // Co-rank of output position d in the merge of A (len na) and B (len nb): the number of
 // A elements among the first d outputs.
-__device__ __forceinline__ uint32_t corank(uint32_t d, const uint32_t* A, const uint64_t* Ap, uint32_t na,
-                                           const uint32_t* B, const uint64_t* Bp, uint32_t nb, const Recs& recs,
+__device__ __forceinline__ uint32_t corank(uint32_t d, const uint32_t* A, const MKey* Ap, uint32_t na,
+                                           const uint32_t* B, const MKey* Bp, uint32_t nb, const Recs& recs,
                                            const uint8_t* arena) {
   uint32_t lo = d > nb ? d - nb : 0;
   uint32_t hi = d < na ? d : na;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
     const uint32_t bj = d - mid - 1;
-    if (cmp_rec(recs, arena, A[mid], Ap[mid], B[bj], Bp[bj]) < 0) lo = mid + 1;
+    if (cmp_mkey(recs, arena, A[mid], Ap[mid], B[bj], Bp[bj]) < 0) lo = mid + 1;
     else hi = mid;
   }
   return lo;
@@ -81,7 +84,7 @@ __device__ __forceinline__ uint32_t find_span(const MergeSpan* spans, uint32_t n
 
 __global__ void k_merge_partition(const MergeSpan* __restrict__ spans, uint32_t n_spans, uint32_t n_tiles,
                                   uint32_t* __restrict__ co, const uint32_t* __restrict__ ord,
-                                  const uint64_t* __restrict__ pfx, Recs recs, const uint8_t* __restrict__ arena) {
+                                  const MKey* __restrict__ pfx, Recs recs, const uint8_t* __restrict__ arena) {
   for (uint64_t t = gtid(); t < n_tiles; t += gstride()) {
     const MergeSpan sp = spans[find_span(spans, n_spans, uint32_t(t))];
     const uint32_t d = uint32_t(t - sp.tile_first) * kMergeTile;
@@ -97,12 +100,12 @@ constexpr int kMergeItems = kMergeTile / kMergeThreads;
 __global__ void __launch_bounds__(kMergeThreads) k_merge_tiles(const MergeSpan* __restrict__ spans, uint32_t n_spans,
                                                                uint32_t n_tiles, const uint32_t* __restrict__ co,
                                                                const uint32_t* __restrict__ src_ord,
-                                                               const uint64_t* __restrict__ src_pfx,
+                                                               const MKey* __restrict__ src_pfx,
                                                                uint32_t* __restrict__ dst_ord,
-                                                               uint64_t* __restrict__ dst_pfx, Recs recs,
+                                                               MKey* __restrict__ dst_pfx, Recs recs,
                                                                const uint8_t* __restrict__ arena) {
   __shared__ uint32_t s_ord[kMergeTile];
-  __shared__ uint64_t s_pfx[kMergeTile];
+  __shared__ MKey s_pfx[kMergeTile];
   for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const uint32_t si = find_span(spans, n_spans, t);
     const MergeSpan sp = spans[si];
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_tiles(const MergeSpan* 
         bool take_a;
         if (a >= na) take_a = false;
         else if (ib >= nb) take_a = true;
-        else take_a = cmp_rec(recs, arena, s_ord[a], s_pfx[a], s_ord[na + ib], s_pfx[na + ib]) < 0;
+        else take_a = cmp_mkey(recs, arena, s_ord[a], s_pfx[a], s_ord[na + ib], s_pfx[na + ib]) < 0;
         if (take_a) {
           dst_ord[out] = s_ord[a];
           dst_pfx[out] = s_pfx[a];
@@ -232,13 +235,13 @@ void launch_check_order(Recs recs, const uint8_t* arena, uint32_t n_rec, const D
   k_check_order<<<grid_for(n_rec, 256), 256, 0, st>>>(recs, arena, n_rec, in, errs); count_launches(1);
 }
 
-void launch_sort_init(uint32_t* ord, uint64_t* opfx, const uint64_t* pfx, uint32_t n, cudaStream_t st) {
+void launch_sort_init(uint32_t* ord, MKey* okey, Recs recs, const uint8_t* arena, uint32_t n, cudaStream_t st) {
   if (!n) return;
-  k_sort_init<<<grid_for(n, 256), 256, 0, st>>>(ord, opfx, pfx, n); count_launches(1);
+  k_sort_init<<<grid_for(n, 256), 256, 0, st>>>(ord, okey, recs, arena, n); count_launches(1);
 }
 
 void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* corank_buf,
-                       const uint32_t* src_ord, const uint64_t* src_pfx, uint32_t* dst_ord, uint64_t* dst_pfx,
+                       const uint32_t* src_ord, const MKey* src_pfx, uint32_t* dst_ord, MKey* dst_pfx,
                        Recs recs, const uint8_t* arena, cudaStream_t st) {
   if (!n_tiles) return;
   k_merge_partition<<<grid_for(n_tiles, 128), 128, 0, st>>>(spans, n_spans, n_tiles, corank_buf, src_ord, src_pfx,
