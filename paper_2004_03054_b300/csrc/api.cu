@@ -93,6 +93,52 @@ luda_status get_tabs(CrcTabs* out) {
   return LUDA_OK;
 }
 
+// ---- side stream --------------------------------------------------------------------------
+// Work that does not feed the main chain of a compaction runs on a second stream of the
+// calling thread: the checksums of the input data blocks (overlapping decode, merge, drop
+// rule and cuts) and of the output data blocks (overlapping bloom, index and footers).
+// Forks and joins are events, so the same code is captured into plans' graphs.
+struct Side {
+  int dev = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev[4] = {};
+};
+thread_local Side t_side;
+
+luda_status get_side(Side** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    set_detail("no usable CUDA device");
+    return LUDA_ERR_CUDA;
+  }
+  Side& sd = t_side;
+  if (sd.dev != dev) {
+    if (sd.s) {
+      cudaStreamDestroy(sd.s);
+      for (cudaEvent_t& e : sd.ev) cudaEventDestroy(e);
+    }
+    sd = Side{};
+    if (cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking) != cudaSuccess) {
+      set_detail("cudaStreamCreateWithFlags failed");
+      return LUDA_ERR_CUDA;
+    }
+    for (cudaEvent_t& e : sd.ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        set_detail("cudaEventCreateWithFlags failed");
+        return LUDA_ERR_CUDA;
+      }
+    sd.dev = dev;
+  }
+  *out = &sd;
+  return LUDA_OK;
+}
+
+// `to` waits for the work queued so far on `from` (event slot e of the side stream).
+cudaError_t fork_join(Side* sd, int e, cudaStream_t from, cudaStream_t to) {
+  cudaError_t r = cudaEventRecord(sd->ev[e], from);
+  return r == cudaSuccess ? cudaStreamWaitEvent(to, sd->ev[e], 0) : r;
+}
+
 // ---- memory -------------------------------------------------------------------------------
 struct DevMem {
   const luda_options* o;
@@ -228,6 +274,7 @@ struct PackBufs {
   uint8_t *sflags, *fflags, *enc_done;
   EncDesc* ed;
   BlkEnc* bd;
+  CrcMsg* fmsg;
   uint32_t* big;
   uint64_t *P, *bsz, *disk, *C, *IX, *fsize, *foff, *bmw, *bmoff, *klens, *koff;
   FileDesc* files;
@@ -255,6 +302,7 @@ void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t
   b.enc_done = L.take<uint8_t>(cap + 1);
   b.ed = L.take<EncDesc>(cap + 1);
   b.bd = L.take<BlkEnc>(cap + 1);
+  b.fmsg = L.take<CrcMsg>(3 * uint64_t(cap) + 3);
   b.big = L.take<uint32_t>(cap + 1);
   b.P = L.take<uint64_t>(cap + 1);
   b.bsz = L.take<uint64_t>(cap + 1);
@@ -281,7 +329,7 @@ void trace_mark(Trace* t, int i, cudaStream_t st);
 
 luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DErr* errs, uint32_t cap, Recs recs,
                      const uint8_t* arena, Fmt fmt, uint8_t* out, uint64_t out_cap, uint64_t bm_cap, CrcTabs tabs,
-                     cudaStream_t st, Trace* tr = nullptr) {
+                     cudaStream_t st, Side* side, Trace* tr = nullptr) {
   launch_sizes(b.surv, cnt, cap, jobs, n_jobs, recs, arena, b.lcp, b.sd, b.dr, b.ed, st);
   CK((exclusive_scan<uint32_t, uint64_t>(b.sd, b.P, cap, &cnt->n_surv, b.scan_tmp, st)));
   launch_block_next(b.P, b.dr, cnt, cap, jobs, n_jobs, fmt, b.next, st);
@@ -309,12 +357,16 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
                 arena,
                 fmt, fmt.max_kv, out, out_cap, b.enc_done, b.big, errs, tabs, st);
   trace_mark(tr, 8, st);
-  launch_encode_finish(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
-                       fmt, out, out_cap, b.enc_done, b.big, tabs, st);
+  // data block trailers on the side stream (joined by the caller through event slot 3)
+  CK(fork_join(side, 2, st, side->s));
+  launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, side->s);
+  CK(cudaEventRecord(side->ev[3], side->s));
+  launch_encode_big(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
+                    fmt, out, out_cap, b.big, tabs, st);
   launch_bloom(b.surv, cnt, cap, b.blk_file, b.blk_start, b.files, recs, arena, fmt, b.bitmap, out_cap, bm_cap, st);
   launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, out, out_cap,
                      st);
-  launch_file_finish(b.files, cnt, cap, b.bitmap, b.surv, recs, fmt, out, out_cap, tabs, b.meta, st);
+  launch_file_finish(b.files, cnt, cap, b.bitmap, b.surv, recs, fmt, out, out_cap, tabs, b.fmsg, b.meta, st);
   launch_key_lens(b.meta, cnt, cap, b.klens, st);
   CK((exclusive_scan<uint64_t, uint64_t>(b.klens, b.koff, cap, &cnt->nf, b.scan_tmp, st)));
   launch_key_gather(b.meta, cnt, cap, b.koff, b.files, b.surv, recs, arena, b.keybuf, st);
@@ -343,14 +395,20 @@ struct Collected {
   std::vector<uint8_t> keys;
 };
 
+// d_errs holds 2 * (n_jobs + 1) entries: the main chain's errors, then the input checksum
+// errors; a checksum error takes precedence (the inputs are verified before anything is
+// read from them in the method's order).
 luda_status collect(const Counts* d_cnt, const JobDev* d_jobs, const DErr* d_errs, const PackBufs& b, uint32_t n_jobs,
                     Collected* c, cudaStream_t st) {
   c->jobs.resize(n_jobs);
-  c->errs.resize(n_jobs);
+  c->errs.resize(2 * (n_jobs + 1));
   CK(cudaMemcpyAsync(&c->cnt, d_cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(c->jobs.data(), d_jobs, sizeof(JobDev) * n_jobs, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(c->errs.data(), d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(c->errs.data(), d_errs, sizeof(DErr) * 2 * (n_jobs + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  for (uint32_t j = 0; j < n_jobs; ++j)
+    if (c->errs[n_jobs + 1 + j].code) c->errs[j] = c->errs[n_jobs + 1 + j];
+  c->errs.resize(n_jobs);
   c->meta.resize(c->cnt.nf);
   c->keys.resize(c->cnt.key_bytes + 1);
   if (c->cnt.nf) {
@@ -501,10 +559,11 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
 
   Layout LA;
   DInput* d_in = LA.take<DInput>(N + 1);
-  DErr* d_errs = LA.take<DErr>(n_jobs + 1);
+  DErr* d_errs = LA.take<DErr>(2 * (n_jobs + 1));  // main chain, then input checksums
   JobDev* d_jobs = LA.take<JobDev>(n_jobs + 1);
   uint32_t* d_in_blk_first = LA.take<uint32_t>(N + 1);
   Counts* d_cnt = LA.take<Counts>(1);
+  CrcMsg* d_msgs = LA.take<CrcMsg>(N + 1);
   uint8_t* bufA = static_cast<uint8_t*>(mem.get(LA.off));
   if (!bufA) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
   {
@@ -512,10 +571,11 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     LA = Layout{};
     LA.base = bufA;
     d_in = LA.take<DInput>(N + 1);
-    d_errs = LA.take<DErr>(n_jobs + 1);
+    d_errs = LA.take<DErr>(2 * (n_jobs + 1));
     d_jobs = LA.take<JobDev>(n_jobs + 1);
     d_in_blk_first = LA.take<uint32_t>(N + 1);
     d_cnt = LA.take<Counts>(1);
+    d_msgs = LA.take<CrcMsg>(N + 1);
     (void)used;
   }
   struct Guard {
@@ -526,10 +586,10 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     }
   } guard{mem, {bufA}};
 
-  CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * (n_jobs + 1), st));
+  CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * 2 * (n_jobs + 1), st));
   CK(cudaMemsetAsync(d_cnt, 0, sizeof(Counts), st));
   if (N) CK(cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
-  launch_footers(d_in, N, d_errs, tabs, st);
+  launch_footers(d_in, N, d_errs, d_msgs, tabs, st);
   CK(cudaGetLastError());
   if (N) CK(cudaMemcpyAsync(hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -579,8 +639,16 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   layoutB(LB, d_blocks, d_nrec, d_kbytes, d_rec_first, d_key_first, d_in_rec, d_in_key, d_tmpB);
 
   launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
+  // input checksums on the side stream, joined before the results are collected
+  Side* side = nullptr;
+  if ((rc = get_side(&side))) return rc;
+  CK(fork_join(side, 0, st, side->s));
+  tr.mark(11, side->s);
+  launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, side->s);
+  tr.mark(12, side->s);
+  CK(cudaEventRecord(side->ev[1], side->s));
   tr.mark(1, st);
-  launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, tabs, st);
+  launch_block_walk(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, st);
   tr.mark(2, st);
   launch_zero_failed(d_blocks, NB, d_errs, d_nrec, d_kbytes, st);
   CK((exclusive_scan<uint32_t, uint32_t>(d_nrec, d_rec_first, NB, nullptr, d_tmpB, st)));
@@ -710,7 +778,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   MKey* src_p = d_pfx0;
   MKey* dst_p = d_pfx1;
   for (size_t p = 0; p < pass_span0.size(); ++p) {
-    launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], d_co, src_o, src_p, dst_o, dst_p, recs,
+    launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], src_o, src_p, dst_o, dst_p, recs,
                       d_arena, st);
     std::swap(src_o, dst_o);
     std::swap(src_p, dst_p);
@@ -722,8 +790,10 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   launch_job_surv(d_jobs, n_jobs, d_pos, n_rec, d_cnt, st);
   CK(cudaGetLastError());
   if ((rc = run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap, tabs, st,
-                     tr.on ? &tr : nullptr)))
+                     side, tr.on ? &tr : nullptr)))
     return rc;
+  CK(cudaStreamWaitEvent(st, side->ev[1], 0));
+  CK(cudaStreamWaitEvent(st, side->ev[3], 0));
   tr.mark(10, st);
   tdev.stop(st);
 
@@ -764,7 +834,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   if (ms_d2h) *ms_d2h = d2h;
   if (tr.on) {
     stage_ms[0] = tr.span(0, 3);
-    stage_ms[1] = tr.span(1, 2);
+    stage_ms[1] = tr.span(11, 12) + tr.span(1, 2);  // checksum kernel (side stream) + walk
     stage_ms[2] = tr.span(4, 5);
     stage_ms[3] = tr.span(5, 6);
     stage_ms[4] = tr.span(6, 7);
@@ -843,7 +913,7 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
   auto lay = [&](Layout& l) {
     recs = recs_layout(l, n);
     arena = l.take<uint8_t>(K + 64);
-    d_err = l.take<DErr>(1);
+    d_err = l.take<DErr>(4);  // main chain and input checksums (collect's layout)
     d_job = l.take<JobDev>(1);
     d_cnt = l.take<Counts>(1);
     pack_layout(l, pb, n, bm_cap, 2 * K + 64);
@@ -907,13 +977,17 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
   Counts hc{};
   hc.n_rec = n;
   hc.n_surv = n;
-  CK(cudaMemsetAsync(d_err, 0, sizeof(DErr), st));
+  CK(cudaMemsetAsync(d_err, 0, sizeof(DErr) * 4, st));
   CK(cudaMemcpyAsync(d_job, &jd, sizeof jd, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_cnt, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
   launch_build_records(ukeys, ukoff, seqs, types, vals, voff, n, recs, arena, pb.surv, d_err, st);
   launch_build_check(recs, arena, n, d_err, st);
   CK(cudaGetLastError());
-  if ((rc = run_pack(pb, d_cnt, d_job, 1, d_err, n, recs, arena, fmt, d_out, out_cap, bm_cap, tabs, st))) return rc;
+  Side* side = nullptr;
+  if ((rc = get_side(&side))) return rc;
+  if ((rc = run_pack(pb, d_cnt, d_job, 1, d_err, n, recs, arena, fmt, d_out, out_cap, bm_cap, tabs, st, side)))
+    return rc;
+  CK(cudaStreamWaitEvent(st, side->ev[3], 0));
   td.stop(st);
   Collected col;
   if ((rc = collect(d_cnt, d_job, d_err, pb, 1, &col, st))) return rc;
@@ -1036,24 +1110,26 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   JobDev* d_jobs;
   uint32_t *d_in_blk_first, *d_plan_nblk, *d_nrec_const;
   Counts* d_cnt;
+  CrcMsg* d_msgs;
   auto layA = [&](Layout& L) {
     d_in = L.take<DInput>(N + 1);
-    d_errs = L.take<DErr>(n_jobs + 1);
+    d_errs = L.take<DErr>(2 * (n_jobs + 1));
     d_jobs = L.take<JobDev>(n_jobs + 1);
     d_in_blk_first = L.take<uint32_t>(N + 1);
     d_plan_nblk = L.take<uint32_t>(N + 1);
     d_nrec_const = L.take<uint32_t>(1);
     d_cnt = L.take<Counts>(1);
+    d_msgs = L.take<CrcMsg>(N + 1);
   };
   layA(LA);
   LA.base = alloc(LA.off);
   if (!LA.base) return cuda_fail(cudaErrorMemoryAllocation, "plan allocation");
   LA.off = 0;
   layA(LA);
-  CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * (n_jobs + 1), st));
+  CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * 2 * (n_jobs + 1), st));
   CK(cudaMemsetAsync(d_cnt, 0, sizeof(Counts), st));
   if (N) CK(cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
-  launch_footers(d_in, N, d_errs, tabs, st);
+  launch_footers(d_in, N, d_errs, d_msgs, tabs, st);
   if (N) CK(cudaMemcpyAsync(hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   std::vector<uint32_t> in_blk_first(N + 1, 0), plan_nblk(N + 1, 0);
@@ -1199,16 +1275,21 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     CK(cudaMemcpyAsync(d_spans, spans.data(), sizeof(MergeSpan) * spans.size(), cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   // ---- capture the whole pipeline --------------------------------------------------------
+  Side* side = nullptr;
+  if ((rc = get_side(&side))) return rc;
   const uint64_t l0 = g_launches.load();
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   auto body = [&]() -> luda_status {
-    CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * (n_jobs + 1), st));
+    CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * 2 * (n_jobs + 1), st));
     CK(cudaMemsetAsync(d_cnt, 0, sizeof(Counts), st));
     CK(cudaMemcpyAsync(&d_cnt->n_rec, d_nrec_const, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
-    launch_footers(d_in, N, d_errs, tabs, st);
+    launch_footers(d_in, N, d_errs, d_msgs, tabs, st);
     launch_plan_checks(d_in, N, d_plan_nblk, d_errs, st);
     launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
-    launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, tabs, st);
+    CK(fork_join(side, 0, st, side->s));
+    launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, side->s);
+    CK(cudaEventRecord(side->ev[1], side->s));
+    launch_block_walk(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, st);
     launch_plan_check_recs(d_blocks, NB, d_nrec, d_kbytes, d_plan_nrec, d_plan_kbytes, d_in, d_errs, st);
     launch_decode(d_blocks, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
     launch_plan_sanitize(recs, n_rec, d_jobs, n_jobs, d_errs, d_arena, st);
@@ -1219,7 +1300,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     MKey* src_p = d_pfx0;
     MKey* dst_p = d_pfx1;
     for (size_t p = 0; p < pass_span0.size(); ++p) {
-      launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], d_co, src_o, src_p, dst_o, dst_p,
+      launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], src_o, src_p, dst_o, dst_p,
                         recs, d_arena, st);
       std::swap(src_o, dst_o);
       std::swap(src_p, dst_p);
@@ -1228,7 +1309,12 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
     launch_gc_compact(src_o, d_keep, d_pos, n_rec, pb.surv, st);
     launch_job_surv(d_jobs, n_jobs, d_pos, n_rec, d_cnt, st);
-    return run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap, tabs, st);
+    luda_status prc = run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap,
+                               tabs, st, side);
+    if (prc) return prc;
+    CK(cudaStreamWaitEvent(st, side->ev[1], 0));
+    CK(cudaStreamWaitEvent(st, side->ev[3], 0));
+    return LUDA_OK;
   };
   luda_status brc = body();
   cudaGraph_t g = nullptr;

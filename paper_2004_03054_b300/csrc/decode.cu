@@ -19,66 +19,63 @@ __device__ __forceinline__ bool handle_ok(uint64_t off, uint64_t size, uint64_t 
   return off <= limit && size <= limit - off && uint64_t(kTrailer) <= limit - off - size;
 }
 
-// One CTA per input: footer, index block CRC and type, index restart count.
-constexpr int kFootThreads = 256;
-
-__global__ void __launch_bounds__(kFootThreads) k_footers(DInput* in, uint32_t n_inputs, DErr* errs,
-                                                          CrcTabs tabs) {
-  __shared__ uint32_t sT[1024];
-  __shared__ uint32_t s_scratch[kFootThreads / 32];
-  __shared__ uint64_t s_h[3];
-  load_slice_table(sT, tabs);
-  __syncthreads();
-  const uint32_t tid = threadIdx.x;
-  for (uint32_t i = blockIdx.x; i < n_inputs; i += gridDim.x) {
+// One thread per input: parse the footer (magic, metaindex and index handles) and queue the
+// index block (contents and type byte) for the multi-warp checksum.
+__global__ void k_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs) {
+  for (uint64_t i = gtid(); i < n_inputs; i += gstride()) {
     const uint8_t* f = in[i].data;
     const uint64_t size = in[i].size;
     DErr* e = errs + in[i].job;
     const uint32_t local = in[i].local;
-    if (tid == 0) {
-      uint64_t ioff = 0, isize = 0;
-      int ok = 0;
-      if (size >= kFooter && ld_u64(f + size - 8) == kMagic) {
-        const uint8_t* p = f + size - kFooter;
-        const uint8_t* end = p + 40;
-        uint64_t moff = 0, msize = 0;
-        uint32_t a = get_varint<64>(p, end, &moff);
-        if (a) a = (p += a, get_varint<64>(p, end, &msize));
-        if (a) a = (p += a, get_varint<64>(p, end, &ioff));
-        if (a) a = (p += a, get_varint<64>(p, end, &isize));
-        const uint64_t limit = size - kFooter;
-        ok = a && handle_ok(moff, msize, limit) && handle_ok(ioff, isize, limit);
-      }
-      if (!ok) report(e, E_CORRUPT, local, size);
-      s_h[0] = ok;
-      s_h[1] = ioff;
-      s_h[2] = isize;
+    uint64_t ioff = 0, isize = 0;
+    int ok = 0;
+    if (size >= kFooter && ld_u64(f + size - 8) == kMagic) {
+      const uint8_t* p = f + size - kFooter;
+      const uint8_t* end = p + 40;
+      uint64_t moff = 0, msize = 0;
+      uint32_t a = get_varint<64>(p, end, &moff);
+      if (a) a = (p += a, get_varint<64>(p, end, &msize));
+      if (a) a = (p += a, get_varint<64>(p, end, &ioff));
+      if (a) a = (p += a, get_varint<64>(p, end, &isize));
+      const uint64_t limit = size - kFooter;
+      ok = a && handle_ok(moff, msize, limit) && handle_ok(ioff, isize, limit);
     }
-    __syncthreads();
-    const bool ok = s_h[0] != 0;
-    const uint64_t ioff = s_h[1], isize = s_h[2];
-    uint32_t nblk = 0;
+    CrcMsg m{};
     if (ok) {
-      const uint32_t got = cta_crc32c(f + ioff, isize + 1, sT, tabs, s_scratch);
-      if (tid == 0) {
-        const uint32_t want = crc_unmask(ld_u32(f + ioff + isize + 1));
-        if (got != want) {
-          report(e, E_CORRUPT, local, ioff);
-        } else if (f[ioff + isize] != 0) {
-          report(e, E_NOTSUP, local, ioff);
-        } else {
-          const uint64_t nr = isize >= 4 ? ld_u32(f + ioff + isize - 4) : 0;
-          if (nr >= 1 && nr <= (isize - 4) / 4) nblk = uint32_t(nr);
-          else report(e, E_CORRUPT, local, ioff);
-        }
+      m.p = f + ioff;
+      m.n = isize + 1;
+      m.out = const_cast<uint8_t*>(f + ioff + isize + 1);
+      m.where = ioff;
+      m.job = in[i].job;
+      m.local = local;
+      m.verify = 1;
+    } else {
+      report(e, E_CORRUPT, local, size);
+      ioff = isize = 0;
+    }
+    msgs[i] = m;
+    in[i].idx_off = ioff;
+    in[i].idx_size = isize;
+    in[i].nblk = ok ? 1u : 0u;  // provisional: footer parsed
+  }
+}
+
+// After the index checksums: type byte and restart count give the number of data blocks.
+__global__ void k_footers_finish(DInput* in, uint32_t n_inputs, DErr* errs) {
+  for (uint64_t i = gtid(); i < n_inputs; i += gstride()) {
+    const DInput d = in[i];
+    uint32_t nblk = 0;
+    if (d.nblk && *(volatile int32_t*)&errs[d.job].code == 0) {
+      const uint8_t* f = d.data;
+      if (f[d.idx_off + d.idx_size] != 0) {
+        report(errs + d.job, E_NOTSUP, d.local, d.idx_off);
+      } else {
+        const uint64_t nr = d.idx_size >= 4 ? ld_u32(f + d.idx_off + d.idx_size - 4) : 0;
+        if (nr >= 1 && nr <= (d.idx_size - 4) / 4) nblk = uint32_t(nr);
+        else report(errs + d.job, E_CORRUPT, d.local, d.idx_off);
       }
     }
-    if (tid == 0) {
-      in[i].idx_off = ioff;
-      in[i].idx_size = isize;
-      in[i].nblk = nblk;
-    }
-    __syncthreads();
+    in[i].nblk = nblk;
   }
 }
 
@@ -152,8 +149,8 @@ constexpr uint32_t kVerifySmem = (kRepWords + 1024) * 4;
 
 __global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_block_verify(const BlockDesc* __restrict__ blocks,
                                                                        uint32_t n_blocks,
-                                                                       const DInput* __restrict__ in, DErr* errs,
-                                                                       CrcTabs tabs) {
+                                                                       const DInput* __restrict__ in,
+                                                                       const DErr* errs, DErr* verr, CrcTabs tabs) {
   extern __shared__ uint32_t s_ver[];
   load_rep_tables992(s_ver, s_ver + kRepWords, tabs);
   __syncthreads();
@@ -162,8 +159,9 @@ __global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_block_verify(const Blo
   const uint64_t warps = gstride() / 32;
   for (uint64_t g = gtid() / 32; g < n_blocks; g += warps) {
     const BlockDesc b = blocks[g];
-    DErr* e = errs + b.job;
-    if (b.ptr == nullptr || *(volatile int32_t*)&e->code != 0) continue;
+    DErr* e = verr + b.job;
+    if (b.ptr == nullptr || *(volatile const int32_t*)&errs[b.job].code != 0 || *(volatile int32_t*)&e->code != 0)
+      continue;
     const uint32_t got = warp_crc32c_u32(b.ptr, b.size + 1, tl, tz, tabs);
     if (lane == 0) {
       const uint32_t want = crc_unmask(ld_u32(b.ptr + b.size + 1));
@@ -475,9 +473,13 @@ void launch_plan_check_recs(const BlockDesc* blocks, uint32_t n_blocks, const ui
   count_launches(1);
 }
 
-void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cudaStream_t st) {
+void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs, CrcTabs tabs, cudaStream_t st) {
   if (!n_inputs) return;
-  k_footers<<<grid_for(n_inputs, 1, kSms * 4), kFootThreads, 0, st>>>(in, n_inputs, errs, tabs); count_launches(1);
+  k_footers<<<grid_for(n_inputs, 128), 128, 0, st>>>(in, n_inputs, errs, msgs);
+  count_launches(1);
+  launch_msg_crc(msgs, nullptr, n_inputs, n_inputs, errs, tabs, st);
+  k_footers_finish<<<grid_for(n_inputs, 128), 128, 0, st>>>(in, n_inputs, errs);
+  count_launches(1);
 }
 
 void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
@@ -486,14 +488,26 @@ void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* i
   k_index_entries<<<grid_for(n_blocks, 256), 256, 0, st>>>(in, n_inputs, in_blk_first, n_blocks, blocks, errs); count_launches(1);
 }
 
-void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, CrcTabs tabs, cudaStream_t st) {
+void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const DErr* errs, DErr* verr,
+                         CrcTabs tabs, cudaStream_t st) {
   if (!n_blocks) return;
   cudaFuncSetAttribute(k_block_verify, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kVerifySmem));
   k_block_verify<<<grid_for(n_blocks, kVerifyWarps, kSms), kVerifyWarps * 32, kVerifySmem, st>>>(blocks, n_blocks,
-                                                                                                 in, errs, tabs);
+                                                                                                 in, errs, verr, tabs);
+  count_launches(1);
+}
+
+void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st) {
+  if (!n_blocks) return;
   k_block_walk<<<grid_for(n_blocks, 256), 256, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, cnt, hdr_tab);
-  count_launches(2);
+  count_launches(1);
+}
+
+void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, CrcTabs tabs, cudaStream_t st) {
+  launch_block_verify(blocks, n_blocks, in, errs, errs, tabs, st);
+  launch_block_walk(blocks, n_blocks, in, nrec, kbytes, errs, cnt, hdr_tab, st);
 }
 
 void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,

@@ -86,10 +86,23 @@ struct Counts {
   uint32_t max_kv;          // largest internal key + value length in the inputs (block walk)
 };
 
-// Merge key of a record: the first 16 bytes of its user key as two big-endian words
+// One message for the multi-warp CRC (index and filter blocks): n bytes at p (contents and
+// type byte); the masked CRC is written to out, or with verify compared with the one
+// stored at out (a mismatch is reported for job / local input at byte offset where).
+struct CrcMsg {
+  const uint8_t* p;
+  uint64_t n;
+  uint8_t* out;
+  uint64_t where;
+  uint32_t job, local;
+  uint32_t verify;
+  uint32_t acc;  // XOR of the chunks' shifted registers (zero when queued)
+};
+
+// Merge key of a record: the first 32 bytes of its user key as four big-endian words
 // (zero-padded).
 struct MKey {
-  uint64_t h0, h1;
+  uint64_t h[4];
 };
 
 // Per output data block: where and what the encoder writes.
@@ -138,12 +151,20 @@ cudaError_t exclusive_scan(const In* in, Out* out, uint64_t cap, const uint32_t*
 bool make_crc_tables(uint32_t* slice, uint32_t* shift);
 
 // ---- decode.cu ---------------------------------------------------------------------------
-void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cudaStream_t st);
+// Footers and index block checksums of n_inputs tables; msgs: n_inputs entries of scratch.
+void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs, CrcTabs tabs, cudaStream_t st);
 void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
                           BlockDesc* blocks, DErr* errs, cudaStream_t st);
 constexpr uint32_t kHdrMax = 64;  // entry offsets recorded per block for the decoder
 void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
                        uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, CrcTabs tabs, cudaStream_t st);
+// The two halves of launch_block_scan, for callers that run them on different streams:
+// checksum and type byte (errors into verr; blocks of jobs failed in errs or verr are
+// skipped), and the structure walk with entry counts.
+void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const DErr* errs, DErr* verr,
+                         CrcTabs tabs, cudaStream_t st);
+void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st);
 void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,
                         uint64_t* kbytes, cudaStream_t st);
 void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,
@@ -171,9 +192,9 @@ void launch_check_order(Recs recs, const uint8_t* arena, uint32_t n_rec, const D
 void launch_plan_sanitize(Recs recs, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, const DErr* errs,
                           const uint8_t* arena, cudaStream_t st);
 void launch_sort_init(uint32_t* ord, MKey* okey, Recs recs, const uint8_t* arena, uint32_t n, cudaStream_t st);
-void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* corank,
-                       const uint32_t* src_ord, const MKey* src_key, uint32_t* dst_ord, MKey* dst_key, Recs recs,
-                       const uint8_t* arena, cudaStream_t st);
+void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, const uint32_t* src_ord,
+                       const MKey* src_key, uint32_t* dst_ord, MKey* dst_key, Recs recs, const uint8_t* arena,
+                       cudaStream_t st);
 void launch_gc_flags(const uint32_t* ord, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, Recs recs,
                      const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st);
 void launch_gc_compact(const uint32_t* ord, const uint32_t* keep, const uint32_t* pos, uint32_t n_rec,
@@ -215,12 +236,15 @@ void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const u
                    Recs recs,
                    const uint8_t* arena, Fmt fmt, uint32_t max_kv, uint8_t* out, uint64_t out_cap, uint8_t* done,
                    uint32_t* big, DErr* errs, CrcTabs tabs, cudaStream_t st);
-// CRC trailers of the staged encoder's blocks, and the blocks it left (CTA per block).
-void launch_encode_finish(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
-                          const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
-                          const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs,
-                          const uint8_t* arena, Fmt fmt, uint8_t* out, uint64_t out_cap, const uint8_t* done,
-                          const uint32_t* big, CrcTabs tabs, cudaStream_t st);
+// CRC trailers of the staged encoder's blocks (done[b] = 1).
+void launch_block_crc(const Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,
+                      const uint64_t* C, const uint64_t* bsz, uint8_t* out, uint64_t out_cap, const uint8_t* done,
+                      CrcTabs tabs, cudaStream_t st);
+// The blocks the staged encoder left, one CTA per block (bytes and CRC trailer).
+void launch_encode_big(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
+                       const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
+                       const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
+                       Fmt fmt, uint8_t* out, uint64_t out_cap, const uint32_t* big, CrcTabs tabs, cudaStream_t st);
 void launch_bloom(const uint32_t* surv, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                   const uint32_t* blk_start, const FileDesc* files, Recs recs, const uint8_t* arena, Fmt fmt,
                   uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st);
@@ -230,7 +254,7 @@ void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t c
                         cudaStream_t st);
 void launch_file_finish(const FileDesc* files, const Counts* cnt, uint32_t cap, const uint32_t* bitmap,
                         const uint32_t* surv, Recs recs, Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs,
-                        FileMeta* meta, cudaStream_t st);
+                        CrcMsg* msgs, FileMeta* meta, cudaStream_t st);
 void launch_key_lens(const FileMeta* meta, const Counts* cnt, uint32_t cap, uint64_t* lens, cudaStream_t st);
 void launch_key_gather(FileMeta* meta, Counts* cnt, uint32_t cap, const uint64_t* koff, const FileDesc* files,
                        const uint32_t* surv, Recs recs, const uint8_t* arena, uint8_t* keybuf, cudaStream_t st);
@@ -240,6 +264,11 @@ void launch_build_records(const uint8_t* ukeys, const uint64_t* ukoff, const uin
                           const uint8_t* vals, const uint64_t* voff, uint32_t n, Recs recs, uint8_t* arena,
                           uint32_t* surv, DErr* err, cudaStream_t st);
 void launch_build_check(Recs recs, const uint8_t* arena, uint32_t n, DErr* err, cudaStream_t st);
+
+// CRC of messages msgs[0 .. (*count) * mult) (count may be NULL: mult messages); max_msgs
+// bounds the grid.
+void launch_msg_crc(CrcMsg* msgs, const uint32_t* count, uint32_t mult, uint32_t max_msgs, DErr* errs, CrcTabs tabs,
+                    cudaStream_t st);
 
 // ---- host runtime ------------------------------------------------------------------------
 // Admission hook of a compaction: called once per call, after the sizing pass and before

@@ -36,6 +36,7 @@ constexpr uint32_t kNaMaxBlocks = LUDA_NOALLOC_MAX_BLOCKS;
 struct NaScratch {
   DInput in;
   DErr err;
+  CrcMsg msg;
   Counts cnt;
   unsigned long long entries;
   uint32_t blk_first[2];
@@ -139,7 +140,7 @@ luda_status luda_check_table_noalloc(const uint8_t* table, uint64_t size, void* 
   din.data = table;
   din.size = size;
   NA_CK(cudaMemcpyAsync(&S->in, &din, sizeof din, cudaMemcpyHostToDevice, st));
-  launch_footers(&S->in, 1, &S->err, dev->tabs, st);
+  launch_footers(&S->in, 1, &S->err, &S->msg, dev->tabs, st);
   NA_CK(cudaGetLastError());
   NA_CK(cudaMemcpyAsync(&din, &S->in, sizeof din, cudaMemcpyDeviceToHost, st));
   NA_CK(cudaStreamSynchronize(st));

@@ -1002,77 +1002,97 @@ __global__ void k_index_write(const uint32_t* __restrict__ start, const Counts* 
 }
 
 // One CTA per table: filter block, metaindex block, index block trailer, footer.
-constexpr int kFinThreads = 256;
 
-__global__ void __launch_bounds__(kFinThreads) k_file_finish(const FileDesc* __restrict__ files,
-                                                             const Counts* __restrict__ cnt,
-                                                             const uint32_t* __restrict__ bitmap,
-                                                             const uint32_t* __restrict__ surv, Recs recs, Fmt fmt,
-                                                             uint8_t* __restrict__ out, uint64_t out_cap,
-                                                             CrcTabs tabs, FileMeta* __restrict__ meta) {
-  __shared__ uint32_t sT[1024];
-  __shared__ uint32_t s_scratch[kFinThreads / 32];
-  load_slice_table(sT, tabs);
-  __syncthreads();
-  const uint32_t tid = threadIdx.x;
+// Filter bitmaps into the tables: one thread per 32-bit bitmap word of all tables.
+__global__ void k_filter_copy(const FileDesc* __restrict__ files, const Counts* __restrict__ cnt,
+                              const uint32_t* __restrict__ bitmap, uint8_t* __restrict__ out, uint64_t out_cap) {
   const uint32_t nf = cnt->nf;
-  for (uint32_t f = blockIdx.x; f < nf; f += gridDim.x) {
-    const FileDesc F = files[f];
+  const uint64_t nw = cnt->bm_words;
+  for (uint64_t w = gtid(); w < nw; w += gstride()) {
+    uint32_t lo = 0, hi = nf;  // last table whose bitmap starts at or before w
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (files[mid].bm_word <= w) lo = mid;
+      else hi = mid;
+    }
+    const FileDesc F = files[lo];
     if (F.off + F.size > out_cap) continue;
+    const uint64_t i = 4 * (w - F.bm_word), bytes = F.filter_size - 1;
+    if (i >= bytes) continue;
+    const uint32_t v = bitmap[w];
+    uint8_t* fp = out + F.off + F.data_size + i;
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)
+      if (i + k < bytes) fp[k] = uint8_t(v >> (8 * k));
+  }
+}
+
+// One thread per table: probe count byte, metaindex, index restart count, footer, the three
+// block checksums queued for the multi-warp CRC, and the table's summary.
+__global__ void k_file_finish(const FileDesc* __restrict__ files, const Counts* __restrict__ cnt,
+                              const uint32_t* __restrict__ surv, Recs recs, Fmt fmt, uint8_t* __restrict__ out,
+                              uint64_t out_cap, CrcMsg* __restrict__ msgs, FileMeta* __restrict__ meta) {
+  const uint32_t nf = cnt->nf;
+  for (uint64_t f = gtid(); f < nf; f += gstride()) {
+    const FileDesc F = files[f];
+    if (F.off + F.size > out_cap) {
+      msgs[3 * f] = msgs[3 * f + 1] = msgs[3 * f + 2] = CrcMsg{};
+      continue;
+    }
     uint8_t* base = out + F.off;
     uint8_t* fp = base + F.data_size;
     const uint64_t bytes = F.filter_size - 1;
-    const uint32_t* bm = bitmap + F.bm_word;
-    for (uint64_t i = tid; i < bytes; i += kFinThreads) fp[i] = uint8_t(bm[i >> 2] >> (8 * (i & 3)));
-    if (tid == 0) {
-      fp[bytes] = uint8_t(fmt.k);
-      fp[bytes + 1] = 0;
-      // metaindex: one entry "filter.luda.bloom" -> filter handle, restart interval 1
-      uint8_t* mp = base + F.meta_off;
-      uint8_t hbuf[20];
-      uint32_t hl = put_varint(hbuf, F.data_size);
-      hl += put_varint(hbuf + hl, F.filter_size);
-      uint32_t q = 0;
-      mp[q++] = 0;
-      mp[q++] = 17;
-      mp[q++] = uint8_t(hl);
-      const char name[] = "filter.luda.bloom";
-      for (int i = 0; i < 17; ++i) mp[q++] = uint8_t(name[i]);
-      for (uint32_t i = 0; i < hl; ++i) mp[q++] = hbuf[i];
-      st_u32(mp + q, 0);
-      st_u32(mp + q + 4, 1);
-      mp[F.meta_size] = 0;
-      // index block: restart count and type
-      uint8_t* ip = base + F.index_off;
-      st_u32(ip + F.index_size - 4, F.blk_end - F.blk_begin);
-      ip[F.index_size] = 0;
-    }
-    __syncthreads();
-    const uint32_t cf = cta_crc32c(fp, F.filter_size + 1, sT, tabs, s_scratch);
-    const uint32_t cm = cta_crc32c(base + F.meta_off, F.meta_size + 1, sT, tabs, s_scratch);
-    const uint32_t ci = cta_crc32c(base + F.index_off, F.index_size + 1, sT, tabs, s_scratch);
-    if (tid == 0) {
-      st_u32(fp + F.filter_size + 1, crc_mask(cf));
-      st_u32(base + F.meta_off + F.meta_size + 1, crc_mask(cm));
-      st_u32(base + F.index_off + F.index_size + 1, crc_mask(ci));
-      uint8_t* ft = base + F.size - kFooter;
-      uint32_t q = put_varint(ft, F.meta_off);
-      q += put_varint(ft + q, F.meta_size);
-      q += put_varint(ft + q, F.index_off);
-      q += put_varint(ft + q, F.index_size);
-      while (q < 40) ft[q++] = 0;
-      for (int i = 0; i < 8; ++i) ft[40 + i] = uint8_t(kMagic >> (8 * i));
-      FileMeta mt{};
-      mt.off = F.off;
-      mt.size = F.size;
-      mt.n_entries = F.ent_end - F.ent_begin;
-      mt.data_size = F.data_size;
-      mt.small_len = recs.klen[surv[F.ent_begin]];
-      mt.large_len = recs.klen[surv[F.ent_end - 1]];
-      mt.job = F.job;
-      meta[f] = mt;
-    }
-    __syncthreads();
+    fp[bytes] = uint8_t(fmt.k);
+    fp[bytes + 1] = 0;
+    // metaindex: one entry "filter.luda.bloom" -> filter handle, restart interval 1
+    uint8_t* mp = base + F.meta_off;
+    uint8_t hbuf[20];
+    uint32_t hl = put_varint(hbuf, F.data_size);
+    hl += put_varint(hbuf + hl, F.filter_size);
+    uint32_t q = 0;
+    mp[q++] = 0;
+    mp[q++] = 17;
+    mp[q++] = uint8_t(hl);
+    const char name[] = "filter.luda.bloom";
+    for (int i = 0; i < 17; ++i) mp[q++] = uint8_t(name[i]);
+    for (uint32_t i = 0; i < hl; ++i) mp[q++] = hbuf[i];
+    st_u32(mp + q, 0);
+    st_u32(mp + q + 4, 1);
+    mp[F.meta_size] = 0;
+    // index block: restart count and type
+    uint8_t* ip = base + F.index_off;
+    st_u32(ip + F.index_size - 4, F.blk_end - F.blk_begin);
+    ip[F.index_size] = 0;
+    // block checksums: filter, metaindex, index
+    CrcMsg m{};
+    m.p = fp;
+    m.n = F.filter_size + 1;
+    m.out = fp + F.filter_size + 1;
+    msgs[3 * f] = m;
+    m.p = base + F.meta_off;
+    m.n = F.meta_size + 1;
+    m.out = base + F.meta_off + F.meta_size + 1;
+    msgs[3 * f + 1] = m;
+    m.p = base + F.index_off;
+    m.n = F.index_size + 1;
+    m.out = base + F.index_off + F.index_size + 1;
+    msgs[3 * f + 2] = m;
+    uint8_t* ft = base + F.size - kFooter;
+    q = put_varint(ft, F.meta_off);
+    q += put_varint(ft + q, F.meta_size);
+    q += put_varint(ft + q, F.index_off);
+    q += put_varint(ft + q, F.index_size);
+    while (q < 40) ft[q++] = 0;
+    for (int i = 0; i < 8; ++i) ft[40 + i] = uint8_t(kMagic >> (8 * i));
+    FileMeta mt{};
+    mt.off = F.off;
+    mt.size = F.size;
+    mt.n_entries = F.ent_end - F.ent_begin;
+    mt.data_size = F.data_size;
+    mt.small_len = recs.klen[surv[F.ent_begin]];
+    mt.large_len = recs.klen[surv[F.ent_end - 1]];
+    mt.job = F.job;
+    meta[f] = mt;
   }
 }
 
@@ -1272,15 +1292,20 @@ void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const u
   count_launches(2);
 }
 
-void launch_encode_finish(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
-                          const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
-                          const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs,
-                          const uint8_t* arena, Fmt fmt, uint8_t* out, uint64_t out_cap, const uint8_t* done,
-                          const uint32_t* big, CrcTabs tabs, cudaStream_t st) {
+void launch_block_crc(const Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,
+                      const uint64_t* C, const uint64_t* bsz, uint8_t* out, uint64_t out_cap, const uint8_t* done,
+                      CrcTabs tabs, cudaStream_t st) {
   if (!cap) return;
   cudaFuncSetAttribute(k_block_crc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCrcSmem));
   k_block_crc<<<kSms, kCrcWarps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done, tabs);
   count_launches(1);
+}
+
+void launch_encode_big(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
+                       const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
+                       const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
+                       Fmt fmt, uint8_t* out, uint64_t out_cap, const uint32_t* big, CrcTabs tabs, cudaStream_t st) {
+  if (!cap) return;
   cudaFuncSetAttribute(k_encode_big, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kEncBuf));
   k_encode_big<<<kSms, kEncThreads, kEncBuf, st>>>(blk_start, cnt, blk_file, files, C, bsz, surv, lcp, sd, dr, recs,
                                                    arena, fmt, out, out_cap, big, tabs);
@@ -1306,10 +1331,12 @@ void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t c
 
 void launch_file_finish(const FileDesc* files, const Counts* cnt, uint32_t cap, const uint32_t* bitmap,
                         const uint32_t* surv, Recs recs, Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs,
-                        FileMeta* meta, cudaStream_t st) {
+                        CrcMsg* msgs, FileMeta* meta, cudaStream_t st) {
   if (!cap) return;
-  k_file_finish<<<grid_for(cap, 1, kSms * 4), kFinThreads, 0, st>>>(files, cnt, bitmap, surv, recs, fmt, out,
-                                                                    out_cap, tabs, meta); count_launches(1);
+  k_filter_copy<<<kSms * 4, 256, 0, st>>>(files, cnt, bitmap, out, out_cap);
+  k_file_finish<<<grid_for(cap, 128, kSms), 128, 0, st>>>(files, cnt, surv, recs, fmt, out, out_cap, msgs, meta);
+  count_launches(2);
+  launch_msg_crc(msgs, &cnt->nf, 3, 3 * cap, nullptr, tabs, st);
 }
 
 void launch_key_lens(const FileMeta* meta, const Counts* cnt, uint32_t cap, uint64_t* lens, cudaStream_t st) {

@@ -25,14 +25,15 @@ __device__ __forceinline__ int cmp_ikey(const Recs& r, const uint8_t* arena, uin
   return cmp_tail(r, arena, a, b, 8, false);
 }
 
-// Merge key: the first 16 bytes of the user key (big-endian words, zero-padded); ties on
+// Merge key: the first 32 bytes of the user key (big-endian words, zero-padded); ties on
 // it are resolved from the key arena.
 __device__ __forceinline__ int cmp_mkey(const Recs& r, const uint8_t* arena, uint32_t a, const MKey& ka, uint32_t b,
                                         const MKey& kb) {
-  if (ka.h0 != kb.h0) return ka.h0 < kb.h0 ? -1 : 1;
-  if (ka.h1 != kb.h1) return ka.h1 < kb.h1 ? -1 : 1;
+#pragma unroll
+  for (int w = 0; w < 4; ++w)
+    if (ka.h[w] != kb.h[w]) return ka.h[w] < kb.h[w] ? -1 : 1;
   if (a == b) return 0;
-  return cmp_tail(r, arena, a, b, 16);
+  return cmp_tail(r, arena, a, b, 32);
 }
 
 __global__ void k_check_order(Recs recs, const uint8_t* __restrict__ arena, uint32_t n_rec,
@@ -52,21 +53,63 @@ __global__ void k_sort_init(uint32_t* __restrict__ ord, MKey* __restrict__ okey,
   for (uint64_t i = gtid(); i < n; i += gstride()) {
     ord[i] = uint32_t(i);
     const uint32_t ul = recs.klen[i] - 8;
-    okey[i] = MKey{recs.pfx[i], key_word(arena + recs.koff[i] + 8, ul > 8 ? ul - 8 : 0u)};
+    const uint8_t* k = arena + recs.koff[i];
+    MKey m;
+    m.h[0] = recs.pfx[i];
+#pragma unroll
+    for (uint32_t w = 1; w < 4; ++w) m.h[w] = key_word(k + 8 * w, ul > 8 * w ? ul - 8 * w : 0u);
+    okey[i] = m;
   }
 }
 
-// Co-rank of output position d in the merge of A (len na) and B (len nb): the number of
-// A elements among the first d outputs.
-__device__ __forceinline__ uint32_t corank(uint32_t d, const uint32_t* A, const MKey* Ap, uint32_t na,
-                                           const uint32_t* B, const MKey* Bp, uint32_t nb, const Recs& recs,
-                                           const uint8_t* arena) {
+constexpr int kMergeThreads = 128;
+constexpr int kMergeItems = kMergeTile / kMergeThreads;
+
+// Co-rank of output position d in the merge of A and B, found by the whole CTA: while the
+// candidate range is wider than the CTA, every thread tests one of kMergeThreads evenly
+// spaced split points ("A[i] goes before B[d-1-i]" is true up to the answer, then false)
+// and the count of true tests narrows the range (about three rounds for a million
+// elements, instead of twenty dependent steps of a binary search).
+__device__ uint32_t corank_cta(uint32_t d, const uint32_t* A, const MKey* Ak, uint32_t na, const uint32_t* B,
+                               const MKey* Bk, uint32_t nb, const Recs& recs, const uint8_t* arena) {
+  uint32_t lo = d > nb ? d - nb : 0;
+  uint32_t hi = d < na ? d : na;
+  const uint32_t t = threadIdx.x;
+  while (hi > lo) {
+    const uint32_t span = hi - lo;
+    if (span <= uint32_t(kMergeThreads)) {
+      const uint32_t i = lo + t;
+      bool p = false;
+      if (t < span) p = cmp_mkey(recs, arena, A[i], Ak[i], B[d - i - 1], Bk[d - i - 1]) < 0;
+      return lo + uint32_t(__syncthreads_count(p));
+    }
+    const uint32_t step = (span + kMergeThreads) / (kMergeThreads + 1);
+    const uint32_t i = lo + (t + 1) * step - 1;
+    bool p = false;
+    if (i < hi) p = cmp_mkey(recs, arena, A[i], Ak[i], B[d - i - 1], Bk[d - i - 1]) < 0;
+    const uint32_t c = uint32_t(__syncthreads_count(p));
+    // tests 0..c-1 were true: the answer is past test c-1; test c (if any) was false or
+    // past hi: the answer is at most its index
+    const uint32_t nlo = c ? lo + c * step : lo;
+    if (c < uint32_t(kMergeThreads)) {
+      const uint32_t nhi = lo + (c + 1) * step - 1;
+      hi = nhi < hi ? nhi : hi;
+    }
+    lo = nlo;
+  }
+  return lo;
+}
+
+// Co-rank inside shared memory (binary search, one thread).
+__device__ __forceinline__ uint32_t corank_smem(uint32_t d, const uint32_t* A, const MKey* Ak, uint32_t na,
+                                                const uint32_t* B, const MKey* Bk, uint32_t nb, const Recs& recs,
+                                                const uint8_t* arena) {
   uint32_t lo = d > nb ? d - nb : 0;
   uint32_t hi = d < na ? d : na;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
     const uint32_t bj = d - mid - 1;
-    if (cmp_mkey(recs, arena, A[mid], Ap[mid], B[bj], Bp[bj]) < 0) lo = mid + 1;
+    if (cmp_mkey(recs, arena, A[mid], Ak[mid], B[bj], Bk[bj]) < 0) lo = mid + 1;
     else hi = mid;
   }
   return lo;
@@ -82,69 +125,49 @@ __device__ __forceinline__ uint32_t find_span(const MergeSpan* spans, uint32_t n
   return lo;
 }
 
-__global__ void k_merge_partition(const MergeSpan* __restrict__ spans, uint32_t n_spans, uint32_t n_tiles,
-                                  uint32_t* __restrict__ co, const uint32_t* __restrict__ ord,
-                                  const MKey* __restrict__ pfx, Recs recs, const uint8_t* __restrict__ arena) {
-  for (uint64_t t = gtid(); t < n_tiles; t += gstride()) {
-    const MergeSpan sp = spans[find_span(spans, n_spans, uint32_t(t))];
-    const uint32_t d = uint32_t(t - sp.tile_first) * kMergeTile;
-    const uint32_t* A = ord + sp.a_begin;
-    co[t] = corank(d, A, pfx + sp.a_begin, sp.a_len, A + sp.a_len, pfx + sp.a_begin + sp.a_len, sp.b_len, recs,
-                   arena);
-  }
-}
-
-constexpr int kMergeThreads = 128;
-constexpr int kMergeItems = kMergeTile / kMergeThreads;
-
-__global__ void __launch_bounds__(kMergeThreads) k_merge_tiles(const MergeSpan* __restrict__ spans, uint32_t n_spans,
-                                                               uint32_t n_tiles, const uint32_t* __restrict__ co,
-                                                               const uint32_t* __restrict__ src_ord,
-                                                               const MKey* __restrict__ src_pfx,
-                                                               uint32_t* __restrict__ dst_ord,
-                                                               MKey* __restrict__ dst_pfx, Recs recs,
-                                                               const uint8_t* __restrict__ arena) {
+// One CTA per output tile of kMergeTile elements: co-rank both ends of the tile, stage
+// the tile's parts of A and B in shared memory, then each thread co-ranks its kMergeItems
+// outputs there and merges them.
+__global__ void __launch_bounds__(kMergeThreads) k_merge(const MergeSpan* __restrict__ spans, uint32_t n_spans,
+                                                         uint32_t n_tiles, const uint32_t* __restrict__ src_ord,
+                                                         const MKey* __restrict__ src_key,
+                                                         uint32_t* __restrict__ dst_ord, MKey* __restrict__ dst_key,
+                                                         Recs recs, const uint8_t* __restrict__ arena) {
   __shared__ uint32_t s_ord[kMergeTile];
-  __shared__ MKey s_pfx[kMergeTile];
+  __shared__ MKey s_key[kMergeTile];
   for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const uint32_t si = find_span(spans, n_spans, t);
-    const MergeSpan sp = spans[si];
+    const MergeSpan sp = spans[find_span(spans, n_spans, t)];
     const uint32_t total = sp.a_len + sp.b_len;
     const uint32_t d0 = (t - sp.tile_first) * kMergeTile;
     const uint32_t d1 = min(d0 + kMergeTile, total);
-    const uint32_t last_tile = (si + 1 < n_spans ? spans[si + 1].tile_first : n_tiles) - 1;
-    const uint32_t i0 = co[t];
-    const uint32_t i1 = t < last_tile ? co[t + 1] : sp.a_len;
+    const uint32_t* A = src_ord + sp.a_begin;
+    const MKey* Ak = src_key + sp.a_begin;
+    const uint32_t* B = A + sp.a_len;
+    const MKey* Bk = Ak + sp.a_len;
+    const uint32_t i0 = corank_cta(d0, A, Ak, sp.a_len, B, Bk, sp.b_len, recs, arena);
+    const uint32_t i1 = d1 == total ? sp.a_len : corank_cta(d1, A, Ak, sp.a_len, B, Bk, sp.b_len, recs, arena);
     const uint32_t j0 = d0 - i0, j1 = d1 - i1;
     const uint32_t na = i1 - i0, nb = j1 - j0;
-    const uint32_t a_base = sp.a_begin + i0, b_base = sp.a_begin + sp.a_len + j0;
     for (uint32_t x = threadIdx.x; x < na + nb; x += blockDim.x) {
-      const uint32_t src = x < na ? a_base + x : b_base + (x - na);
-      s_ord[x] = src_ord[src];
-      s_pfx[x] = src_pfx[src];
+      const uint32_t src = x < na ? i0 + x : sp.a_len + j0 + (x - na);
+      s_ord[x] = A[src];
+      s_key[x] = Ak[src];
     }
     __syncthreads();
     const uint32_t dd = threadIdx.x * kMergeItems;
     if (dd < na + nb) {
-      const uint32_t ia = corank(dd, s_ord, s_pfx, na, s_ord + na, s_pfx + na, nb, recs, arena);
-      uint32_t ib = dd - ia;
-      uint32_t a = ia;
+      const uint32_t ia = corank_smem(dd, s_ord, s_key, na, s_ord + na, s_key + na, nb, recs, arena);
+      uint32_t a = ia, ib = dd - ia;
       const uint32_t cnt = min(uint32_t(kMergeItems), na + nb - dd);
       uint32_t out = sp.a_begin + d0 + dd;
       for (uint32_t k = 0; k < cnt; ++k, ++out) {
         bool take_a;
         if (a >= na) take_a = false;
         else if (ib >= nb) take_a = true;
-        else take_a = cmp_mkey(recs, arena, s_ord[a], s_pfx[a], s_ord[na + ib], s_pfx[na + ib]) < 0;
-        if (take_a) {
-          dst_ord[out] = s_ord[a];
-          dst_pfx[out] = s_pfx[a];
-          ++a;
-        } else {
-          dst_ord[out] = s_ord[na + ib];
-          dst_pfx[out] = s_pfx[na + ib];
-          ++ib;
-        }
+        else take_a = cmp_mkey(recs, arena, s_ord[a], s_key[a], s_ord[na + ib], s_key[na + ib]) < 0;
+        const uint32_t x = take_a ? a++ : na + ib++;
+        dst_ord[out] = s_ord[x];
+        dst_key[out] = s_key[x];
       }
     }
     __syncthreads();
@@ -240,15 +263,13 @@ void launch_sort_init(uint32_t* ord, MKey* okey, Recs recs, const uint8_t* arena
   k_sort_init<<<grid_for(n, 256), 256, 0, st>>>(ord, okey, recs, arena, n); count_launches(1);
 }
 
-void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* corank_buf,
-                       const uint32_t* src_ord, const MKey* src_pfx, uint32_t* dst_ord, MKey* dst_pfx,
-                       Recs recs, const uint8_t* arena, cudaStream_t st) {
+void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, const uint32_t* src_ord,
+                       const MKey* src_key, uint32_t* dst_ord, MKey* dst_key, Recs recs, const uint8_t* arena,
+                       cudaStream_t st) {
   if (!n_tiles) return;
-  k_merge_partition<<<grid_for(n_tiles, 128), 128, 0, st>>>(spans, n_spans, n_tiles, corank_buf, src_ord, src_pfx,
-                                                            recs, arena); count_launches(1);
-  k_merge_tiles<<<grid_for(n_tiles, 1, kSms * 8), kMergeThreads, 0, st>>>(spans, n_spans, n_tiles, corank_buf,
-                                                                          src_ord, src_pfx, dst_ord, dst_pfx, recs,
-                                                                          arena); count_launches(1);
+  k_merge<<<grid_for(n_tiles, 1, kSms * 8), kMergeThreads, 0, st>>>(spans, n_spans, n_tiles, src_ord, src_key,
+                                                                    dst_ord, dst_key, recs, arena);
+  count_launches(1);
 }
 
 void launch_gc_flags(const uint32_t* ord, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, Recs recs,

@@ -207,3 +207,24 @@ def test_bad_options():
     for kw in (dict(block_size=0), dict(restart_interval=0), dict(bloom_bits_per_key=0), dict(target_file_size=0)):
         res = luda.compact_device([], opts=luda.options(**kw))
         assert res.status == luda.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_skewed_runs(seed):
+    """Inputs whose key ranges barely overlap (most of one run sorts before the other):
+    the merge's co-rank search then finds its split at the far end of the range."""
+    rng = np.random.default_rng(700 + seed)
+    n_a, n_b = int(rng.integers(3000, 20000)), int(rng.integers(500, 8000))
+    keys = np.sort(rng.choice(1 << 30, size=n_a + n_b, replace=False)).astype(np.uint64)
+    over = int(rng.integers(0, 40))
+    a_keys = keys[:n_a]
+    b_keys = np.concatenate([keys[n_a - over:n_a] + np.uint64(1), keys[n_a:]]) if over else keys[n_a:]
+    b_keys = np.unique(b_keys)
+    runs = []
+    for level, ks in ((1, b_keys), (2, a_keys)):
+        m = len(ks)
+        seqs = rng.permutation(np.arange(1, m + 1, dtype=np.uint64)) + np.uint64(10**6 if level == 1 else 0)
+        runs.append(W._make_run(W._fixed_keys(ks), seqs, W._types(rng, m, 0.02), rng.integers(0, 64, size=m), rng,
+                                level))
+    job = W.Job(f"skew{seed}", seed, runs, W.MAX_SEQ, False, 4096, 16, 10, 1 << 20)
+    check_job(job)
