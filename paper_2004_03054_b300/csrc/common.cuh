@@ -144,6 +144,15 @@ __device__ __forceinline__ uint64_t key_word(const uint8_t* p, uint32_t avail) {
   return (uint64_t(__byte_perm(lo, 0, 0x0123)) << 32) | __byte_perm(hi, 0, 0x0123);
 }
 
+// 8 bytes at p (any alignment) as a little-endian word: two aligned 8-byte loads.
+__device__ __forceinline__ uint64_t le_word(const uint8_t* p) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uint64_t* q = reinterpret_cast<const uint64_t*>(a & ~uintptr_t(7));
+  const uint32_t sh = uint32_t(a & 7u) * 8u;
+  const uint64_t w = q[0];
+  return sh ? (w >> sh) | (q[1] << (64 - sh)) : w;
+}
+
 // Internal key order from byte `from` of the user keys on, given that the bytes before it
 // are equal (zero-padded): user key bytes (8 at a time), proper prefix first, then trailer
 // descending, then record id ascending (input index, then position; 0 for a == b).

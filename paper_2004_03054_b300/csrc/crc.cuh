@@ -213,19 +213,19 @@ __device__ __forceinline__ uint32_t crc_fix_word32(uint32_t w, uint32_t q, uint3
 // arithmetic. Between rounds a lane register moves past the other lanes' 992 bytes with
 // Z_992; the lanes are joined with Z_{32 * 2^k} (k < 5), the trailing pad is removed with
 // the inverse shift. Only 16-byte words inside [p & ~15, end rounded up] are loaded.
-// kStd = false gives the bare register F(M) instead: fed from a zero register, without the
-// init and the final complement (for joining chunks of one message).
-template <bool kStd = true>
+// kInit = false starts from a zero register instead of 0xFFFFFFFF and kFinal = false skips
+// the final complement (for chunks of one message: the first chunk carries the init, the
+// register of the whole message is complemented once after joining).
+template <bool kInit = true, bool kFinal = true>
 static __device__ __noinline__ uint32_t warp_crc32c_u32(const uint8_t* p, uint64_t n, uint32_t tl, uint32_t tz,
                                                         const CrcTabs tabs) {
   const uint32_t lane = threadIdx.x & 31u;
-  constexpr uint32_t kXor = kStd ? 0xFFFFFFFFu : 0u;
   if (n < 16) {
-    uint32_t c = kXor;
+    uint32_t c = kInit ? 0xFFFFFFFFu : 0u;
     if (lane == 0)
       for (uint64_t i = 0; i < n; ++i) c = lds_off<0u>(tl + ((c ^ p[i]) & 0xFFu) * 128u) ^ (c >> 8);
     c = __shfl_sync(0xFFFFFFFFu, c, 0);
-    return c ^ kXor;
+    return kFinal ? c ^ 0xFFFFFFFFu : c;
   }
   const uintptr_t ps = reinterpret_cast<uintptr_t>(p);
   const uintptr_t pe = ps + n;
@@ -254,14 +254,14 @@ static __device__ __noinline__ uint32_t warp_crc32c_u32(const uint8_t* p, uint64
     if (u >= 0) {
       const uint32_t q = uint32_t(u) * 32u;
       if (q < lo + 4 || q + 32 > hi) {
-        x0.x = crc_fix_word32<kStd>(x0.x, q, lo, hi);
-        x0.y = crc_fix_word32<kStd>(x0.y, q + 4, lo, hi);
-        x0.z = crc_fix_word32<kStd>(x0.z, q + 8, lo, hi);
-        x0.w = crc_fix_word32<kStd>(x0.w, q + 12, lo, hi);
-        y0.x = crc_fix_word32<kStd>(y0.x, q + 16, lo, hi);
-        y0.y = crc_fix_word32<kStd>(y0.y, q + 20, lo, hi);
-        y0.z = crc_fix_word32<kStd>(y0.z, q + 24, lo, hi);
-        y0.w = crc_fix_word32<kStd>(y0.w, q + 28, lo, hi);
+        x0.x = crc_fix_word32<kInit>(x0.x, q, lo, hi);
+        x0.y = crc_fix_word32<kInit>(x0.y, q + 4, lo, hi);
+        x0.z = crc_fix_word32<kInit>(x0.z, q + 8, lo, hi);
+        x0.w = crc_fix_word32<kInit>(x0.w, q + 12, lo, hi);
+        y0.x = crc_fix_word32<kInit>(y0.x, q + 16, lo, hi);
+        y0.y = crc_fix_word32<kInit>(y0.y, q + 20, lo, hi);
+        y0.z = crc_fix_word32<kInit>(y0.z, q + 24, lo, hi);
+        y0.w = crc_fix_word32<kInit>(y0.w, q + 28, lo, hi);
       }
       acc = crc_unit32(crc_z992(acc, tz), x0, y0, tl);
     }
@@ -275,7 +275,7 @@ static __device__ __noinline__ uint32_t warp_crc32c_u32(const uint8_t* p, uint64
     acc = (lane & (1u << k)) ? (crc_shift(tab, other) ^ acc) : (crc_shift(tab, acc) ^ other);
   }
   if (pad) acc = crc_shift(tabs.shift + size_t(kShiftPow + pad - 1) * 1024, acc);
-  return acc ^ kXor;
+  return kFinal ? acc ^ 0xFFFFFFFFu : acc;
 }
 
 // Z_L(v): the register v moved past L zero bytes (L mod 16 single-byte steps, then the

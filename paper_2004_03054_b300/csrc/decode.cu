@@ -344,19 +344,17 @@ __global__ void __launch_bounds__(256) k_decode(const BlockDesc* __restrict__ bl
       for (int h = 0; h < 2; ++h) {
         const uint32_t k = lane + 32 * h;
         if (k < nent) {
+          // the walk already validated this header (16-byte window read)
           const uint8_t* p = b.ptr + hdr_tab[g * kHdrMax + k];
-          const uint8_t* end = b.ptr + b.size;
-          uint64_t s_, n_, v_;
-          p += get_varint<32>(p, end, &s_);
-          p += get_varint<32>(p, end, &n_);
-          p += get_varint<32>(p, end, &v_);
-          sh[h] = uint32_t(s_);
-          ns[h] = uint32_t(n_);
-          kl[h] = uint32_t(s_ + n_);
+          uint32_t f[3] = {0, 0, 0};
+          p += read_header(p, b.ptr + b.size, f);
+          sh[h] = f[0];
+          ns[h] = f[1];
+          kl[h] = f[0] + f[1];
           dp[h] = uint32_t(p - b.ptr);
           long_key |= kl[h] > 32 * kDecSlots;
-          recs.vptr[rec0 + k] = reinterpret_cast<uint64_t>(p + n_);
-          recs.vlen[rec0 + k] = uint32_t(v_);
+          recs.vptr[rec0 + k] = reinterpret_cast<uint64_t>(p + f[1]);
+          recs.vlen[rec0 + k] = f[2];
           recs.klen[rec0 + k] = kl[h];
           recs.src[rec0 + k] = b.input;
         }
@@ -389,27 +387,29 @@ __global__ void __launch_bounds__(256) k_decode(const BlockDesc* __restrict__ bl
       const uint32_t dpos = __shfl_sync(0xFFFFFFFFu, h ? dp[1] : dp[0], src);
       const uint32_t kof = __shfl_sync(0xFFFFFFFFu, h ? ko[1] : ko[0], src);
       uint8_t* kd = arena + key0 + kof;
-      uint64_t pf = 0, tr = 0;
 #pragma unroll
       for (uint32_t s = 0; s < kDecSlots; ++s) {
         const uint32_t t = lane + 32 * s;
         if (t < klen) {
           if (t >= shared) cur[s] = b.ptr[dpos + t - shared];
           kd[t] = cur[s];
-          if (t < 8 && t < klen - 8) pf |= uint64_t(cur[s]) << (8 * (7 - t));
-          if (t >= klen - 8) tr |= uint64_t(cur[s]) << (8 * (t - (klen - 8)));
         }
       }
+    }
+    __syncwarp();  // the warp's key bytes are visible to all its lanes
+    // per entry (lane): user-key prefix and trailer read back from the rebuilt key
 #pragma unroll
-      for (int d = 16; d; d >>= 1) {
-        pf |= __shfl_xor_sync(0xFFFFFFFFu, pf, d);
-        tr |= __shfl_xor_sync(0xFFFFFFFFu, tr, d);
-      }
-      if (lane == 0) {
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t k = lane + 32 * h;
+      if (k < nent) {
+        const uint8_t* kd = arena + key0 + ko[h];
+        const uint32_t ul = kl[h] - 8;
+        const uint64_t pf = key_word(kd, ul < 8 ? ul : 8u);
+        const uint64_t tr = le_word(kd + ul);
         if ((tr & 0xFF) > 1) bad = true;
         recs.pfx[rec0 + k] = pf;
         recs.tr[rec0 + k] = tr;
-        recs.koff[rec0 + k] = key0 + kof;
+        recs.koff[rec0 + k] = key0 + ko[h];
       }
     }
     bad = __any_sync(0xFFFFFFFFu, bad);

@@ -4,13 +4,14 @@
 // A message is cut into at most kMsgMaxChunks chunks of at least 4 KiB, and every chunk of
 // every message goes to its own warp, so a handful of quarter-megabyte blocks spread over
 // the whole GPU (a fixed number of chunk slots per message keeps the mapping free of any
-// prefix sum; empty slots are skipped). A warp computes its chunk's bare register F(chunk)
-// (fed from a zero register, no init and no final complement) with the interleaved warp
-// CRC, moves it past the bytes that follow the chunk in the message and XORs it into the
-// message's accumulator; by linearity over GF(2)
-//   F(M) = XOR_c Z_{bytes after chunk c}(F(chunk c)),
-//   CRC(M) = F(M) xor Z_n(0xFFFFFFFF) xor 0xFFFFFFFF,
-// where Z_L moves a register past L zero bytes. A second kernel finishes each message.
+// prefix sum; empty slots are skipped). A warp computes its chunk's register without the
+// final complement, the first chunk from the init register 0xFFFFFFFF and the others from
+// a zero register, moves it past the bytes that follow the chunk in the message and XORs it
+// into the message's accumulator. By linearity over GF(2) the accumulator is then the
+// register of the whole message,
+//   XOR_c Z_{bytes after chunk c}(R(chunk c)),
+// where Z_L moves a register past L zero bytes; a second kernel complements it and writes
+// (or checks) the masked trailer.
 #include <cstdint>
 
 #include "internal.cuh"
@@ -47,7 +48,8 @@ __global__ void __launch_bounds__(kMsgWarps * 32, 1) k_msg_chunks(CrcMsg* __rest
     const uint64_t a = uint64_t(c) * chunk;
     if (a >= M.n) continue;
     const uint64_t len = M.n - a < chunk ? M.n - a : chunk;
-    const uint32_t raw = warp_crc32c_u32<false>(M.p + a, len, tl, tz, tabs);
+    const uint32_t raw = c == 0 ? warp_crc32c_u32<true, false>(M.p, len, tl, tz, tabs)
+                                : warp_crc32c_u32<false, false>(M.p + a, len, tl, tz, tabs);
     if (lane == 0) atomicXor(&msgs[m].acc, crc_zeros(raw, M.n - a - len, tabs));
   }
 }
@@ -58,7 +60,7 @@ __global__ void k_msg_finish(const CrcMsg* __restrict__ msgs, const uint32_t* __
   for (uint64_t m = gtid(); m < n_msgs; m += gstride()) {
     const CrcMsg M = msgs[m];
     if (M.p == nullptr) continue;
-    const uint32_t crc = M.acc ^ crc_zeros(0xFFFFFFFFu, M.n, tabs) ^ 0xFFFFFFFFu;
+    const uint32_t crc = M.acc ^ 0xFFFFFFFFu;
     if (M.verify) {
       if (crc_unmask(ld_u32(M.out)) != crc) report(errs + M.job, E_CORRUPT, M.local, M.where);
     } else {
@@ -74,7 +76,7 @@ void launch_msg_crc(CrcMsg* msgs, const uint32_t* count, uint32_t mult, uint32_t
   if (!max_msgs) return;
   cudaFuncSetAttribute(k_msg_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMsgSmem));
   k_msg_chunks<<<kSms, kMsgWarps * 32, kMsgSmem, st>>>(msgs, count, mult, tabs);
-  k_msg_finish<<<grid_for(max_msgs, 128), 128, 0, st>>>(msgs, count, mult, errs, tabs);
+  k_msg_finish<<<grid_for(max_msgs, 128, kSms), 128, 0, st>>>(msgs, count, mult, errs, tabs);
   count_launches(2);
 }
 

@@ -64,11 +64,20 @@ __global__ void k_sizes(const uint32_t* __restrict__ surv, const Counts* __restr
     const uint32_t klen = recs.klen[x], vlen = recs.vlen[x];
     uint32_t l = 0;
     if (s > jobs[j].surv_begin) {
+      // common prefix of the two internal keys, 8 bytes at a time
       const uint32_t y = surv[s - 1];
       const uint32_t m = min(klen, recs.klen[y]);
       const uint8_t* a = arena + recs.koff[x];
       const uint8_t* b = arena + recs.koff[y];
-      while (l < m && a[l] == b[l]) ++l;
+      while (l < m) {
+        const uint32_t avail = m - l < 8 ? m - l : 8u;
+        const uint64_t d = key_word(a + l, avail) ^ key_word(b + l, avail);
+        if (d) {
+          l += uint32_t(__clzll(d)) >> 3;
+          break;
+        }
+        l += avail;
+      }
     }
     const uint32_t d = varint_size(l) + varint_size(klen - l) + varint_size(vlen) + (klen - l) + vlen;
     const uint32_t r = 1 + varint_size(klen) + varint_size(vlen) + klen + vlen;

@@ -1,4 +1,5 @@
-// scan.cu -- device-wide exclusive prefix sums (reduce, scan the tile sums, down-sweep).
+// scan.cu -- device-wide exclusive prefix sums (reduce, then down-sweep; the tile sums are
+// scanned recursively only when there are many tiles).
 //
 // out[i] = in[0] + ... + in[i-1] for i in [0, n], so out[n] is the total. Used for record
 // offsets, survivor positions, block starts, byte offsets of blocks and files.
@@ -91,6 +92,43 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_scan(const In* __restrict
   if (base < n && base + kScanItems >= n) out[n] = run;  // the thread holding the last item
 }
 
+// As k_tile_scan, with the tile's offset summed from the tile sums by the CTA itself (one
+// launch fewer than scanning the sums; used while the tile count is small).
+template <typename In, typename Out>
+__global__ void __launch_bounds__(kScanThreads) k_tile_scan_sums(const In* __restrict__ in, uint64_t cap,
+                                                                 const uint32_t* __restrict__ count,
+                                                                 Out* __restrict__ out,
+                                                                 const uint64_t* __restrict__ sums) {
+  const uint64_t n = count ? *count : cap;
+  if (n == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = Out(0);
+    return;
+  }
+  if (uint64_t(blockIdx.x) * kScanTile >= n) return;
+  uint64_t part = 0;
+  for (uint32_t i = threadIdx.x; i < blockIdx.x; i += kScanThreads) part += sums[i];
+  uint64_t offset;
+  cta_excl_scan<uint64_t>(part, &offset);
+  const uint64_t base = uint64_t(blockIdx.x) * kScanTile + uint64_t(threadIdx.x) * kScanItems;
+  Out v[kScanItems];
+  Out s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < n ? Out(in[base + k]) : Out(0);
+    s += v[k];
+  }
+  Out total;
+  Out run = cta_excl_scan<Out>(s, &total) + Out(offset);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (base < n && base + kScanItems >= n) out[n] = run;
+}
+
+constexpr uint64_t kScanFusedTiles = 2048;
+
 }  // namespace
 
 uint64_t scan_temp_bytes(uint64_t n) {
@@ -118,6 +156,11 @@ cudaError_t exclusive_scan(const In* in, Out* out, uint64_t cap, const uint32_t*
   uint64_t* offs = sums + t;
   void* rest = offs + t + 1;
   k_tile_reduce<In><<<unsigned(t), kScanThreads, 0, st>>>(in, cap, count, sums); count_launches(1);
+  if (t <= kScanFusedTiles) {
+    k_tile_scan_sums<In, Out><<<unsigned(t), kScanThreads, 0, st>>>(in, cap, count, out, sums);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   cudaError_t e = exclusive_scan<uint64_t, uint64_t>(sums, offs, t, nullptr, rest, st);
   if (e != cudaSuccess) return e;
   k_tile_scan<In, Out><<<unsigned(t), kScanThreads, 0, st>>>(in, cap, count, out, offs); count_launches(1);
