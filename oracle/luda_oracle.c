@@ -698,13 +698,13 @@ typedef struct {
   uint64_t* off;
   uint64_t* size;
   uint64_t n, cap;
+  buf_t keys;       /* index keys, back to back */
+  uint64_t* kend;   /* end of index key b in `keys` */
 } index_ctx;
 
 static int index_cb(void* vctx, const uint8_t* key, uint64_t klen, const uint8_t* val, uint64_t vlen,
                     int at_restart) {
   index_ctx* c = (index_ctx*)vctx;
-  (void)key;
-  (void)klen;
   uint64_t off, size;
   uint32_t a, b;
   if (!at_restart) goto bad; /* restart interval 1: every entry starts its own segment */
@@ -720,10 +720,15 @@ static int index_cb(void* vctx, const uint8_t* key, uint64_t klen, const uint8_t
     uint64_t* q2 = (uint64_t*)realloc(c->size, cap * sizeof(uint64_t));
     if (!q2) return ORA_ERR_OOM;
     c->size = q2;
+    uint64_t* q3 = (uint64_t*)realloc(c->kend, cap * sizeof(uint64_t));
+    if (!q3) return ORA_ERR_OOM;
+    c->kend = q3;
     c->cap = cap;
   }
+  if (buf_put(&c->keys, key, klen)) return ORA_ERR_OOM;
   c->off[c->n] = off;
   c->size[c->n] = size;
+  c->kend[c->n] = c->keys.n;
   c->n++;
   return ORA_OK;
 bad:
@@ -782,17 +787,29 @@ static int decode_input(const uint8_t* f, uint64_t fsize, uint32_t input, ents_t
   int rc = read_footer(f, fsize, input, &moff, &msize, &ioff, &isize);
   if (rc) return rc;
   if ((rc = read_block(f, fsize, ioff, isize, "index", input))) return rc;
-  index_ctx ic = {f, fsize, input, NULL, NULL, 0, 0};
+  index_ctx ic = {f, fsize, input, NULL, NULL, 0, 0, {0}, NULL};
   buf_t key = {0};
   rc = walk_block(f + ioff, isize, &key, index_cb, &ic, "index", input, ioff);
   uint64_t first = es->n;
   data_ctx dc = {es, input, 0};
   for (uint64_t b = 0; rc == ORA_OK && b < ic.n; b++) {
+    const uint64_t before = es->n;
     rc = read_block(f, fsize, ic.off[b], ic.size[b], "data", input);
     if (rc == ORA_OK) rc = walk_block(f + ic.off[b], ic.size[b], &key, data_cb, &dc, "data", input, ic.off[b]);
+    /* R9: the index key of a data block is that block's last internal key */
+    if (rc == ORA_OK) {
+      const uint64_t k0 = b ? ic.kend[b - 1] : 0, kl = ic.kend[b] - k0;
+      const ent_t* last = es->n > before ? &es->e[es->n - 1] : NULL;
+      if (!last || last->klen != kl || memcmp(es->keys.p + last->koff, ic.keys.p + k0, kl) != 0) {
+        detail("input %u: index key of data block %llu is not its last key", input, (unsigned long long)b);
+        rc = ORA_ERR_CORRUPTION;
+      }
+    }
   }
   free(ic.off);
   free(ic.size);
+  free(ic.kend);
+  free(ic.keys.p);
   free(key.p);
   for (uint64_t i = first + 1; rc == ORA_OK && i < es->n; i++) {
     const ent_t* a = &es->e[i - 1];

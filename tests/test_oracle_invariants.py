@@ -150,14 +150,15 @@ def test_out_of_order_input_is_corruption():
     run = W._make_run([b"b", b"a"], np.array([1, 2], np.uint64), np.array([1, 1], np.uint8),
                       np.array([1, 1]), rng, 0)
     assert oracle.build_tables(run).status == oracle.ERR_INVALID_ARG   # the builder refuses
-    contents = oracle.encode_block([(b"b" + struct.pack("<Q", 1 << 8 | 1), b"x"),
-                                    (b"a" + struct.pack("<Q", 2 << 8 | 1), b"y")], 16)
-    res = oracle.compact([_single_block_table(contents)])
-    assert res.status == oracle.ERR_CORRUPTION
+    last = b"a" + struct.pack("<Q", 2 << 8 | 1)
+    contents = oracle.encode_block([(b"b" + struct.pack("<Q", 1 << 8 | 1), b"x"), (last, b"y")], 16)
+    res = oracle.compact([_single_block_table(contents, last)])
+    assert res.status == oracle.ERR_CORRUPTION and "out of order" in res.detail
 
 
-def _single_block_table(contents, index_key=b"z" * 9):
-    """A minimal table around one data block's contents (filter empty-ish, valid CRCs)."""
+def _single_block_table(contents, index_key):
+    """A minimal table around one data block's contents (filter empty-ish, valid CRCs);
+    index_key is the block's index entry key (the format wants its last internal key)."""
     def blk(c):
         return c + b"\x00" + struct.pack("<I", oracle.mask(oracle.crc32c(c + b"\x00")))
     data = blk(contents)
@@ -177,12 +178,22 @@ def _single_block_table(contents, index_key=b"z" * 9):
 
 
 def test_hand_made_table_is_valid():
-    contents = oracle.encode_block([(b"a" + struct.pack("<Q", 2 << 8 | 1), b"y"),
-                                    (b"b" + struct.pack("<Q", 1 << 8 | 1), b"x")], 16)
-    img = _single_block_table(contents)
+    last = b"b" + struct.pack("<Q", 1 << 8 | 1)
+    contents = oracle.encode_block([(b"a" + struct.pack("<Q", 2 << 8 | 1), b"y"), (last, b"x")], 16)
+    img = _single_block_table(contents, last)
     res = oracle.compact([img])
     assert res.status == 0 and len(res.tables) == 1
     assert res.tables[0].n_entries == 2
+
+
+@pytest.mark.parametrize("index_key", [b"z" * 9, b"b" + struct.pack("<Q", 2 << 8 | 1), b"a" * 9, b"b" * 9])
+def test_index_key_must_be_last_key(index_key):
+    """R9: an index entry whose key is not its block's last internal key (checksums intact)
+    makes the table corrupt."""
+    contents = oracle.encode_block([(b"a" + struct.pack("<Q", 2 << 8 | 1), b"y"),
+                                    (b"b" + struct.pack("<Q", 1 << 8 | 1), b"x")], 16)
+    res = oracle.compact([_single_block_table(contents, index_key)])
+    assert res.status == oracle.ERR_CORRUPTION and "index key" in res.detail
 
 
 def test_duplicate_internal_key_across_inputs():
