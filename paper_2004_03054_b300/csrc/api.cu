@@ -10,6 +10,7 @@
 //   collect   one read of the counts, then the per-table metadata and boundary keys.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -509,6 +510,103 @@ struct Timer {
   }
 };
 
+// ---- merge schedule ----------------------------------------------------------------------
+// Runs of each job (position ranges, in order) are merged pairwise until one is left. A
+// pass merges adjacent runs that sit in the same buffer, smallest pairs first and only
+// pairs at most twice the smallest pair's size, so a large run (a level's tables that form
+// one run) is not dragged through every pass; merged runs move to the other buffer, the
+// others stay. When no adjacent pair shares a buffer the smallest run is moved across.
+// At the end every job's run is brought to the buffer of the largest job.
+struct MergeSched {
+  std::vector<MergeSpan> spans;
+  std::vector<uint32_t> pass_span0, pass_nspans, pass_ntiles;
+  uint32_t max_tiles = 1;
+  uint32_t final_buf = 0;
+};
+
+void merge_schedule(const std::vector<std::vector<std::pair<uint32_t, uint32_t>>>& runs_in, MergeSched* S) {
+  struct R {
+    uint32_t b, n, buf;
+  };
+  std::vector<std::vector<R>> runs(runs_in.size());
+  for (size_t j = 0; j < runs_in.size(); ++j)
+    for (const auto& r : runs_in[j])
+      if (r.second) runs[j].push_back(R{r.first, r.second, 0});
+  auto tiles_of = [](uint32_t n) { return (n + kMergeTile - 1) / kMergeTile; };
+  auto begin_pass = [&]() { S->pass_span0.push_back(uint32_t(S->spans.size())); };
+  auto end_pass = [&](uint32_t tiles) {
+    S->pass_nspans.push_back(uint32_t(S->spans.size()) - S->pass_span0.back());
+    S->pass_ntiles.push_back(tiles);
+    if (tiles > S->max_tiles) S->max_tiles = tiles;
+  };
+  while (true) {
+    bool more = false;
+    for (auto& r : runs) more |= r.size() > 1;
+    if (!more) break;
+    begin_pass();
+    uint32_t tiles = 0;
+    for (auto& r : runs) {
+      if (r.size() < 2) continue;
+      std::vector<std::pair<uint64_t, size_t>> cand;
+      for (size_t k = 0; k + 1 < r.size(); ++k)
+        if (r[k].buf == r[k + 1].buf) cand.push_back({uint64_t(r[k].n) + r[k + 1].n, k});
+      if (cand.empty()) {  // move the smallest run to the other buffer
+        size_t k = 0;
+        for (size_t i = 1; i < r.size(); ++i)
+          if (r[i].n < r[k].n) k = i;
+        S->spans.push_back(MergeSpan{r[k].b, r[k].n, 0, tiles, r[k].buf, 0});
+        tiles += tiles_of(r[k].n);
+        r[k].buf ^= 1u;
+        continue;
+      }
+      std::stable_sort(cand.begin(), cand.end(),
+                       [](const std::pair<uint64_t, size_t>& a, const std::pair<uint64_t, size_t>& b) {
+                         return a.first < b.first;
+                       });
+      const uint64_t limit = 2 * cand[0].first;
+      std::vector<uint8_t> first(r.size(), 0), used(r.size(), 0);
+      for (const auto& c : cand) {
+        if (c.first > limit) break;
+        if (used[c.second] || used[c.second + 1]) continue;
+        used[c.second] = used[c.second + 1] = 1;
+        first[c.second] = 1;
+      }
+      std::vector<R> nr;
+      for (size_t k = 0; k < r.size(); ++k) {
+        if (first[k]) {
+          S->spans.push_back(MergeSpan{r[k].b, r[k].n, r[k + 1].n, tiles, r[k].buf, 0});
+          tiles += tiles_of(r[k].n + r[k + 1].n);
+          nr.push_back(R{r[k].b, r[k].n + r[k + 1].n, r[k].buf ^ 1u});
+          ++k;
+        } else {
+          nr.push_back(r[k]);
+        }
+      }
+      r.swap(nr);
+    }
+    end_pass(tiles);
+  }
+  // one buffer for all jobs: the largest job's
+  uint64_t best = 0;
+  for (auto& r : runs)
+    if (r.size() == 1 && r[0].n > best) {
+      best = r[0].n;
+      S->final_buf = r[0].buf;
+    }
+  bool moves = false;
+  for (auto& r : runs) moves |= r.size() == 1 && r[0].buf != S->final_buf;
+  if (moves) {
+    begin_pass();
+    uint32_t tiles = 0;
+    for (auto& r : runs)
+      if (r.size() == 1 && r[0].buf != S->final_buf) {
+        S->spans.push_back(MergeSpan{r[0].b, r[0].n, 0, tiles, r[0].buf, 0});
+        tiles += tiles_of(r[0].n);
+      }
+    end_pass(tiles);
+  }
+}
+
 // The whole compaction for n_jobs jobs whose inputs are device pointers. On return
 // outs[j] hold device (or, with host_out, pinned host) tables.
 luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_options* o, cudaStream_t st,
@@ -564,6 +662,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   uint32_t* d_in_blk_first = LA.take<uint32_t>(N + 1);
   Counts* d_cnt = LA.take<Counts>(1);
   CrcMsg* d_msgs = LA.take<CrcMsg>(N + 1);
+  uint8_t* d_link = LA.take<uint8_t>(N + 1);
   uint8_t* bufA = static_cast<uint8_t*>(mem.get(LA.off));
   if (!bufA) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
   {
@@ -576,6 +675,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     d_in_blk_first = LA.take<uint32_t>(N + 1);
     d_cnt = LA.take<Counts>(1);
     d_msgs = LA.take<CrcMsg>(N + 1);
+    d_link = LA.take<uint8_t>(N + 1);
     (void)used;
   }
   struct Guard {
@@ -651,6 +751,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   launch_block_walk(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, st);
   tr.mark(2, st);
   launch_zero_failed(d_blocks, NB, d_errs, d_nrec, d_kbytes, st);
+  launch_run_links(d_in, N, d_blocks, d_errs, d_link, st);
   CK((exclusive_scan<uint32_t, uint32_t>(d_nrec, d_rec_first, NB, nullptr, d_tmpB, st)));
   CK((exclusive_scan<uint64_t, uint64_t>(d_kbytes, d_key_first, NB, nullptr, d_tmpB, st)));
   launch_input_ranges(d_in, N, d_rec_first, d_key_first, d_in_rec, d_in_key, st);
@@ -658,10 +759,12 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   std::vector<uint32_t> in_rec(N + 1);
   std::vector<uint64_t> in_key(N + 1);
   std::vector<DErr> herr(n_jobs + 1);
+  std::vector<uint8_t> link(N + 1, 0);
   CK(cudaMemcpyAsync(in_rec.data(), d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(in_key.data(), d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(herr.data(), d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&fmt.max_kv, &d_cnt->max_kv, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (N) CK(cudaMemcpyAsync(link.data(), d_link, N, cudaMemcpyDeviceToHost, st));
   tr.mark(3, st);
   CK(cudaStreamSynchronize(st));
 
@@ -685,37 +788,24 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     out_cap += 2 * kj + job_in_bytes[j] + 200 * nj + 256;
     bm_cap += nj * fmt.bpk / 32 + 5 * nj + 8;
   }
-  // merge schedule: each input is a sorted run; merge neighbours pairwise until one run per job
-  struct Run {
-    uint32_t b, n;
-  };
-  std::vector<std::vector<Run>> runs(n_jobs);
-  for (uint32_t j = 0; j < n_jobs; ++j)
-    for (uint32_t i = job_in_first[j]; i < job_in_first[j + 1]; ++i)
-      if (in_rec[i + 1] > in_rec[i]) runs[j].push_back(Run{in_rec[i], in_rec[i + 1] - in_rec[i]});
-  std::vector<MergeSpan> spans;
-  std::vector<uint32_t> pass_span0, pass_nspans, pass_ntiles;
-  uint32_t max_tiles = 1;
-  while (true) {
-    bool more = false;
-    for (auto& r : runs) more |= r.size() > 1;
-    if (!more) break;
-    pass_span0.push_back(uint32_t(spans.size()));
-    uint32_t tiles = 0;
-    for (auto& r : runs) {
-      std::vector<Run> nr;
-      for (size_t k = 0; k < r.size(); k += 2) {
-        MergeSpan sp{r[k].b, r[k].n, k + 1 < r.size() ? r[k + 1].n : 0u, tiles};
-        tiles += (sp.a_len + sp.b_len + kMergeTile - 1) / kMergeTile;
-        spans.push_back(sp);
-        nr.push_back(Run{sp.a_begin, sp.a_len + sp.b_len});
+  // merge schedule: linked inputs form one sorted run
+  MergeSched ms;
+  {
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> runs(n_jobs);
+    for (uint32_t j = 0; j < n_jobs; ++j)
+      for (uint32_t i = job_in_first[j]; i < job_in_first[j + 1];) {
+        uint32_t e = i;
+        while (e + 1 < job_in_first[j + 1] && link[e]) ++e;
+        runs[j].push_back({in_rec[i], in_rec[e + 1] - in_rec[i]});
+        i = e + 1;
       }
-      r.swap(nr);
-    }
-    pass_nspans.push_back(uint32_t(spans.size()) - pass_span0.back());
-    pass_ntiles.push_back(tiles);
-    if (tiles > max_tiles) max_tiles = tiles;
+    merge_schedule(runs, &ms);
   }
+  const std::vector<MergeSpan>& spans = ms.spans;
+  const std::vector<uint32_t>& pass_span0 = ms.pass_span0;
+  const std::vector<uint32_t>& pass_nspans = ms.pass_nspans;
+  const std::vector<uint32_t>& pass_ntiles = ms.pass_ntiles;
+  const uint32_t max_tiles = ms.max_tiles;
 
   // ---- execute -------------------------------------------------------------------------------
   const uint32_t cap = n_rec;
@@ -771,18 +861,13 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   tr.mark(4, st);
   launch_decode(d_blocks, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
   tr.mark(5, st);
+  launch_check_index(d_blocks, NB, d_in, d_nrec, d_rec_first, recs, d_arena, d_errs, st);
   launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
   launch_sort_init(d_ord0, d_pfx0, recs, d_arena, n_rec, st);
-  uint32_t* src_o = d_ord0;
-  uint32_t* dst_o = d_ord1;
-  MKey* src_p = d_pfx0;
-  MKey* dst_p = d_pfx1;
-  for (size_t p = 0; p < pass_span0.size(); ++p) {
-    launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], src_o, src_p, dst_o, dst_p, recs,
+  for (size_t p = 0; p < pass_span0.size(); ++p)
+    launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], d_ord0, d_pfx0, d_ord1, d_pfx1, recs,
                       d_arena, st);
-    std::swap(src_o, dst_o);
-    std::swap(src_p, dst_p);
-  }
+  uint32_t* src_o = ms.final_buf ? d_ord1 : d_ord0;
   tr.mark(6, st);
   launch_gc_flags(src_o, n_rec, d_jobs, n_jobs, recs, d_arena, d_keep, d_errs, st);
   CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
@@ -1157,6 +1242,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   uint64_t *d_kbytes, *d_key_first, *d_in_key, *d_plan_kbytes;
   uint16_t* d_hdr;
   void* d_tmpB;
+  uint8_t *d_link, *d_plan_link;
   auto layB = [&](Layout& L) {
     d_blocks = L.take<BlockDesc>(NB + 1);
     d_hdr = L.take<uint16_t>(uint64_t(NB) * kHdrMax + 1);
@@ -1168,6 +1254,8 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     d_key_first = L.take<uint64_t>(NB + 1);
     d_in_rec = L.take<uint32_t>(N + 1);
     d_in_key = L.take<uint64_t>(N + 1);
+    d_link = L.take<uint8_t>(N + 1);
+    d_plan_link = L.take<uint8_t>(N + 1);
     d_tmpB = L.take<uint8_t>(scan_temp_bytes(NB + 1));
   };
   layB(LB);
@@ -1178,6 +1266,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
   launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, tabs, st);
   launch_zero_failed(d_blocks, NB, d_errs, d_nrec, d_kbytes, st);
+  launch_run_links(d_in, N, d_blocks, d_errs, d_plan_link, st);
   if (NB) {
     CK(cudaMemcpyAsync(d_plan_nrec, d_nrec, sizeof(uint32_t) * NB, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(d_plan_kbytes, d_kbytes, sizeof(uint64_t) * NB, cudaMemcpyDeviceToDevice, st));
@@ -1188,9 +1277,11 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   CK(cudaGetLastError());
   std::vector<uint32_t> in_rec(N + 1);
   std::vector<uint64_t> in_key(N + 1);
+  std::vector<uint8_t> link(N + 1, 0);
   CK(cudaMemcpyAsync(in_rec.data(), d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(in_key.data(), d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&fmt.max_kv, &d_cnt->max_kv, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (N) CK(cudaMemcpyAsync(link.data(), d_plan_link, N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const uint32_t n_rec = in_rec[N];
   const uint64_t K = in_key[N];
@@ -1210,37 +1301,24 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     out_cap += 2 * kj + job_in_bytes[j] + 200 * nj + 256;
     bm_cap += nj * fmt.bpk / 32 + 5 * nj + 8;
   }
-  // merge schedule (as in run_compaction)
-  struct Run {
-    uint32_t b, n;
-  };
-  std::vector<std::vector<Run>> runs(n_jobs);
-  for (uint32_t j = 0; j < n_jobs; ++j)
-    for (uint32_t i = job_in_first[j]; i < job_in_first[j + 1]; ++i)
-      if (in_rec[i + 1] > in_rec[i]) runs[j].push_back(Run{in_rec[i], in_rec[i + 1] - in_rec[i]});
-  std::vector<MergeSpan> spans;
-  std::vector<uint32_t> pass_span0, pass_nspans, pass_ntiles;
-  uint32_t max_tiles = 1;
-  while (true) {
-    bool more = false;
-    for (auto& r : runs) more |= r.size() > 1;
-    if (!more) break;
-    pass_span0.push_back(uint32_t(spans.size()));
-    uint32_t tiles = 0;
-    for (auto& r : runs) {
-      std::vector<Run> nr;
-      for (size_t k = 0; k < r.size(); k += 2) {
-        MergeSpan sp{r[k].b, r[k].n, k + 1 < r.size() ? r[k + 1].n : 0u, tiles};
-        tiles += (sp.a_len + sp.b_len + kMergeTile - 1) / kMergeTile;
-        spans.push_back(sp);
-        nr.push_back(Run{sp.a_begin, sp.a_len + sp.b_len});
+  // merge schedule (as in run_compaction); replays check that the links still hold
+  MergeSched ms;
+  {
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> runs(n_jobs);
+    for (uint32_t j = 0; j < n_jobs; ++j)
+      for (uint32_t i = job_in_first[j]; i < job_in_first[j + 1];) {
+        uint32_t e = i;
+        while (e + 1 < job_in_first[j + 1] && link[e]) ++e;
+        runs[j].push_back({in_rec[i], in_rec[e + 1] - in_rec[i]});
+        i = e + 1;
       }
-      r.swap(nr);
-    }
-    pass_nspans.push_back(uint32_t(spans.size()) - pass_span0.back());
-    pass_ntiles.push_back(tiles);
-    if (tiles > max_tiles) max_tiles = tiles;
+    merge_schedule(runs, &ms);
   }
+  const std::vector<MergeSpan>& spans = ms.spans;
+  const std::vector<uint32_t>& pass_span0 = ms.pass_span0;
+  const std::vector<uint32_t>& pass_nspans = ms.pass_nspans;
+  const std::vector<uint32_t>& pass_ntiles = ms.pass_ntiles;
+  const uint32_t max_tiles = ms.max_tiles;
   const uint32_t cap = n_rec;
   Layout LC;
   Recs recs;
@@ -1291,20 +1369,17 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     CK(cudaEventRecord(side->ev[1], side->s));
     launch_block_walk(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, st);
     launch_plan_check_recs(d_blocks, NB, d_nrec, d_kbytes, d_plan_nrec, d_plan_kbytes, d_in, d_errs, st);
+    launch_run_links(d_in, N, d_blocks, d_errs, d_link, st);
+    launch_plan_check_links(d_link, d_plan_link, N, d_in, d_errs, st);
     launch_decode(d_blocks, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
     launch_plan_sanitize(recs, n_rec, d_jobs, n_jobs, d_errs, d_arena, st);
+    launch_check_index(d_blocks, NB, d_in, d_nrec, d_rec_first, recs, d_arena, d_errs, st);
     launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
     launch_sort_init(d_ord0, d_pfx0, recs, d_arena, n_rec, st);
-    uint32_t* src_o = d_ord0;
-    uint32_t* dst_o = d_ord1;
-    MKey* src_p = d_pfx0;
-    MKey* dst_p = d_pfx1;
-    for (size_t p = 0; p < pass_span0.size(); ++p) {
-      launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], src_o, src_p, dst_o, dst_p,
+    for (size_t p = 0; p < pass_span0.size(); ++p)
+      launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], d_ord0, d_pfx0, d_ord1, d_pfx1,
                         recs, d_arena, st);
-      std::swap(src_o, dst_o);
-      std::swap(src_p, dst_p);
-    }
+    uint32_t* src_o = ms.final_buf ? d_ord1 : d_ord0;
     launch_gc_flags(src_o, n_rec, d_jobs, n_jobs, recs, d_arena, d_keep, d_errs, st);
     CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
     launch_gc_compact(src_o, d_keep, d_pos, n_rec, pb.surv, st);

@@ -93,7 +93,7 @@ __global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs
     }
     const DInput d = in[lo];
     const uint32_t k = uint32_t(g - in_blk_first[lo]);
-    BlockDesc out{nullptr, 0, 0, lo, d.job};
+    BlockDesc out{nullptr, 0, 0, lo, d.job, nullptr, 0, 0};
     if (k >= d.nblk) {  // only when a replayed plan sees fewer blocks than it was sized for
       report(errs + d.job, E_PLAN, d.local, d.idx_off);
       blocks[g] = out;
@@ -113,6 +113,7 @@ __global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs
       if (a) a = (p += a, get_varint<32>(p, end, &vlen));
       if (a) p += a;
       ok = a && shared == 0 && nonshared <= uint64_t(end - p) && vlen <= uint64_t(end - p) - nonshared;
+      const uint8_t* ikey = p;
       if (ok) {
         p += nonshared;
         ok = p + vlen == end;
@@ -128,6 +129,8 @@ __global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs
         out.ptr = d.data + off;
         out.size = size;
         out.off = off;
+        out.ikey = ikey;
+        out.ilen = uint32_t(nonshared);
       }
     }
     if (!ok) report(errs + d.job, E_CORRUPT, d.local, d.idx_off + rstart + 4ull * k);
@@ -417,6 +420,65 @@ __global__ void __launch_bounds__(256) k_decode(const BlockDesc* __restrict__ bl
   }
 }
 
+// One thread per data block, after decode: the block's index key must equal its last
+// internal key (R9 of the format).
+__global__ void k_check_index(const BlockDesc* __restrict__ blocks, uint32_t n_blocks, const DInput* __restrict__ in,
+                              const uint32_t* __restrict__ nrec, const uint32_t* __restrict__ rec_first, Recs recs,
+                              const uint8_t* __restrict__ arena, DErr* errs) {
+  for (uint64_t g = gtid(); g < n_blocks; g += gstride()) {
+    const BlockDesc b = blocks[g];
+    if (b.ptr == nullptr || nrec[g] == 0 || *(volatile int32_t*)&errs[b.job].code != 0) continue;
+    const uint32_t last = rec_first[g] + nrec[g] - 1;
+    const uint32_t kl = recs.klen[last];
+    bool ok = kl == b.ilen;
+    const uint8_t* k = arena + recs.koff[last];
+    for (uint32_t i = 0; ok && i < kl; i += 8) {
+      const uint32_t avail = kl - i < 8 ? kl - i : 8u;
+      ok = key_word(k + i, avail) == key_word(b.ikey + i, avail);
+    }
+    if (!ok) report(errs + b.job, E_CORRUPT, in[b.input].local, b.off);
+  }
+}
+
+// Internal-key order of two full internal keys (user key bytes, proper prefix first, then
+// the trailer descending).
+__device__ int cmp_ikey_bytes(const uint8_t* a, uint32_t la, const uint8_t* b, uint32_t lb) {
+  const uint32_t ua = la - 8, ub = lb - 8, m = ua < ub ? ua : ub;
+  for (uint32_t i = 0; i < m; i += 8) {
+    const uint32_t avail = m - i < 8 ? m - i : 8u;
+    const uint64_t wa = key_word(a + i, avail), wb = key_word(b + i, avail);
+    if (wa != wb) return wa < wb ? -1 : 1;
+  }
+  if (ua != ub) return ua < ub ? -1 : 1;
+  const uint64_t ta = le_word(a + ua), tb = le_word(b + ub);
+  return ta == tb ? 0 : (ta > tb ? -1 : 1);
+}
+
+// One thread per input: link[i] = 1 when input i + 1 belongs to the same job and all its
+// keys follow all of input i's (its first key, read from its first data block, is above
+// input i's last key, read from input i's last index entry). Linked inputs form one sorted
+// run for the merge. The index keys are checked against the data after decode, and each
+// input's own order by the order check, so a link never rests on an unchecked key.
+__global__ void k_run_links(const DInput* __restrict__ in, uint32_t n_inputs, const BlockDesc* __restrict__ blocks,
+                            const DErr* errs, uint8_t* __restrict__ link) {
+  for (uint64_t i = gtid(); i < n_inputs; i += gstride()) {
+    uint8_t l = 0;
+    if (i + 1 < n_inputs) {
+      const DInput a = in[i], c = in[i + 1];
+      if (a.job == c.job && a.nblk && c.nblk && errs[a.job].code == 0) {
+        const BlockDesc la = blocks[a.blk_first + a.nblk - 1], fc = blocks[c.blk_first];
+        if (la.ptr && fc.ptr && la.ilen >= 8) {
+          uint32_t f[3];
+          const uint32_t hl = read_header(fc.ptr, fc.ptr + fc.size, f);
+          if (hl && f[0] == 0 && f[1] >= 8 && f[1] <= fc.size - hl)
+            l = cmp_ikey_bytes(la.ikey, la.ilen, fc.ptr + hl, f[1]) < 0;
+        }
+      }
+    }
+    link[i] = l;
+  }
+}
+
 __global__ void k_zero_failed(const BlockDesc* __restrict__ blocks, uint32_t n_blocks, const DErr* __restrict__ errs,
                               uint32_t* __restrict__ nrec, uint64_t* __restrict__ kbytes) {
   for (uint64_t g = gtid(); g < n_blocks; g += gstride())
@@ -456,7 +518,22 @@ __global__ void k_plan_check_recs(const BlockDesc* __restrict__ blocks, uint32_t
       report(errs + blocks[g].job, E_PLAN, in[blocks[g].input].local, blocks[g].off);
 }
 
+// Replay: an input that continued the previous input's run when the plan was made must
+// still do so (the captured merge schedule relies on it).
+__global__ void k_plan_check_links(const uint8_t* __restrict__ link, const uint8_t* __restrict__ plan_link,
+                                   uint32_t n_inputs, const DInput* __restrict__ in, DErr* errs) {
+  for (uint64_t i = gtid(); i < n_inputs; i += gstride())
+    if (plan_link[i] && !link[i]) report(errs + in[i].job, E_PLAN, in[i].local, 0);
+}
+
 }  // namespace
+
+void launch_plan_check_links(const uint8_t* link, const uint8_t* plan_link, uint32_t n_inputs, const DInput* in,
+                             DErr* errs, cudaStream_t st) {
+  if (!n_inputs) return;
+  k_plan_check_links<<<grid_for(n_inputs, 128), 128, 0, st>>>(link, plan_link, n_inputs, in, errs);
+  count_launches(1);
+}
 
 void launch_plan_checks(DInput* in, uint32_t n_inputs, const uint32_t* plan_nblk, DErr* errs, cudaStream_t st) {
   if (!n_inputs) return;
@@ -516,6 +593,20 @@ void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in,
   if (!n_blocks) return;
   k_decode<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, nrec, hdr_tab, rec_first, key_first, recs,
                                                   arena, errs);
+  count_launches(1);
+}
+
+void launch_check_index(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,
+                        const uint32_t* rec_first, Recs recs, const uint8_t* arena, DErr* errs, cudaStream_t st) {
+  if (!n_blocks) return;
+  k_check_index<<<grid_for(n_blocks, 256), 256, 0, st>>>(blocks, n_blocks, in, nrec, rec_first, recs, arena, errs);
+  count_launches(1);
+}
+
+void launch_run_links(const DInput* in, uint32_t n_inputs, const BlockDesc* blocks, const DErr* errs, uint8_t* link,
+                      cudaStream_t st) {
+  if (!n_inputs) return;
+  k_run_links<<<grid_for(n_inputs, 128), 128, 0, st>>>(in, n_inputs, blocks, errs, link);
   count_launches(1);
 }
 

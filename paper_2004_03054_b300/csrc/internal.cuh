@@ -28,6 +28,9 @@ struct BlockDesc {
   uint64_t off;         // offset within its input (error reports)
   uint32_t input;       // global input index
   uint32_t job;
+  const uint8_t* ikey;  // the block's index key (its last internal key, checked after decode)
+  uint32_t ilen;
+  uint32_t pad;
 };
 
 struct JobDev {
@@ -165,6 +168,13 @@ void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInpu
                          CrcTabs tabs, cudaStream_t st);
 void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
                        uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st);
+// After decode: every data block's index key equals its last internal key.
+void launch_check_index(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,
+                        const uint32_t* rec_first, Recs recs, const uint8_t* arena, DErr* errs, cudaStream_t st);
+// link[i] = 1 when input i + 1 continues input i's sorted run (same job, disjoint and in
+// order); needs the block descriptors and the inputs' blk_first.
+void launch_run_links(const DInput* in, uint32_t n_inputs, const BlockDesc* blocks, const DErr* errs, uint8_t* link,
+                      cudaStream_t st);
 void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,
                         uint64_t* kbytes, cudaStream_t st);
 void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,
@@ -177,13 +187,17 @@ void launch_plan_checks(DInput* in, uint32_t n_inputs, const uint32_t* plan_nblk
 void launch_plan_check_recs(const BlockDesc* blocks, uint32_t n_blocks, const uint32_t* nrec, const uint64_t* kbytes,
                             const uint32_t* plan_nrec, const uint64_t* plan_kbytes, const DInput* in, DErr* errs,
                             cudaStream_t st);
+void launch_plan_check_links(const uint8_t* link, const uint8_t* plan_link, uint32_t n_inputs, const DInput* in,
+                             DErr* errs, cudaStream_t st);
 
 // ---- sort.cu -----------------------------------------------------------------------------
 struct MergeSpan {
   uint32_t a_begin;  // first position of run A (run B follows it)
   uint32_t a_len;
-  uint32_t b_len;
+  uint32_t b_len;       // 0: run A is only moved to the other buffer
   uint32_t tile_first;  // first tile id of this merge
+  uint32_t src;         // buffer (0/1) holding both runs; the result goes to the other
+  uint32_t pad;
 };
 constexpr uint32_t kMergeTile = 1024;
 
@@ -192,9 +206,9 @@ void launch_check_order(Recs recs, const uint8_t* arena, uint32_t n_rec, const D
 void launch_plan_sanitize(Recs recs, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, const DErr* errs,
                           const uint8_t* arena, cudaStream_t st);
 void launch_sort_init(uint32_t* ord, MKey* okey, Recs recs, const uint8_t* arena, uint32_t n, cudaStream_t st);
-void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, const uint32_t* src_ord,
-                       const MKey* src_key, uint32_t* dst_ord, MKey* dst_key, Recs recs, const uint8_t* arena,
-                       cudaStream_t st);
+// One pass of merges; ord[b] / key[b] are the two buffers, each span names its source.
+void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* ord0, MKey* key0,
+                       uint32_t* ord1, MKey* key1, Recs recs, const uint8_t* arena, cudaStream_t st);
 void launch_gc_flags(const uint32_t* ord, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, Recs recs,
                      const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st);
 void launch_gc_compact(const uint32_t* ord, const uint32_t* keep, const uint32_t* pos, uint32_t n_rec,

@@ -1,10 +1,12 @@
 // sort.cu -- Phase 2 "(Delete and) Sort" (LUDA §II-A; §III-C, §III-D).
 //
-// Every input table is already a sorted run, so the total order is reached by merging
-// runs pairwise (merge path: each output tile finds its split of the two runs by binary
-// search, then merges it in shared memory). The paper sorted <K, V_offset> tuples on the
-// host because it found no fast GPU sort for them (§III-D "Cooperative Sort"); here the
-// tuples (record id plus an 8-byte key prefix) never leave the device.
+// Every input table is already a sorted run (and consecutive inputs whose key ranges do
+// not overlap form one run), so the total order is reached by merging runs pairwise
+// (merge path: each output tile finds its split of the two runs, then merges it in shared
+// memory). Runs that a pass does not merge stay in their buffer. The paper sorted
+// <K, V_offset> tuples on the host because it found no fast GPU sort for them (§III-D
+// "Cooperative Sort"); here the tuples (record id plus a 32-byte key head) never leave the
+// device.
 //
 // The drop rule then keeps entry i unless a newer version of the same user key is
 // visible at the smallest snapshot S, or it is a tombstone visible at S in a bottommost
@@ -129,14 +131,16 @@ __device__ __forceinline__ uint32_t find_span(const MergeSpan* spans, uint32_t n
 // the tile's parts of A and B in shared memory, then each thread co-ranks its kMergeItems
 // outputs there and merges them.
 __global__ void __launch_bounds__(kMergeThreads) k_merge(const MergeSpan* __restrict__ spans, uint32_t n_spans,
-                                                         uint32_t n_tiles, const uint32_t* __restrict__ src_ord,
-                                                         const MKey* __restrict__ src_key,
-                                                         uint32_t* __restrict__ dst_ord, MKey* __restrict__ dst_key,
-                                                         Recs recs, const uint8_t* __restrict__ arena) {
+                                                         uint32_t n_tiles, uint32_t* ord0, MKey* key0, uint32_t* ord1,
+                                                         MKey* key1, Recs recs, const uint8_t* __restrict__ arena) {
   __shared__ uint32_t s_ord[kMergeTile];
   __shared__ MKey s_key[kMergeTile];
   for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const MergeSpan sp = spans[find_span(spans, n_spans, t)];
+    const uint32_t* src_ord = sp.src ? ord1 : ord0;
+    const MKey* src_key = sp.src ? key1 : key0;
+    uint32_t* dst_ord = sp.src ? ord0 : ord1;
+    MKey* dst_key = sp.src ? key0 : key1;
     const uint32_t total = sp.a_len + sp.b_len;
     const uint32_t d0 = (t - sp.tile_first) * kMergeTile;
     const uint32_t d1 = min(d0 + kMergeTile, total);
@@ -263,12 +267,11 @@ void launch_sort_init(uint32_t* ord, MKey* okey, Recs recs, const uint8_t* arena
   k_sort_init<<<grid_for(n, 256), 256, 0, st>>>(ord, okey, recs, arena, n); count_launches(1);
 }
 
-void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, const uint32_t* src_ord,
-                       const MKey* src_key, uint32_t* dst_ord, MKey* dst_key, Recs recs, const uint8_t* arena,
-                       cudaStream_t st) {
+void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* ord0, MKey* key0,
+                       uint32_t* ord1, MKey* key1, Recs recs, const uint8_t* arena, cudaStream_t st) {
   if (!n_tiles) return;
-  k_merge<<<grid_for(n_tiles, 1, kSms * 8), kMergeThreads, 0, st>>>(spans, n_spans, n_tiles, src_ord, src_key,
-                                                                    dst_ord, dst_key, recs, arena);
+  k_merge<<<grid_for(n_tiles, 1, kSms * 8), kMergeThreads, 0, st>>>(spans, n_spans, n_tiles, ord0, key0, ord1, key1,
+                                                                    recs, arena);
   count_launches(1);
 }
 

@@ -186,11 +186,22 @@ def test_garbage_input():
 
 def test_out_of_order_input():
     from test_oracle_invariants import _single_block_table
-    contents = oracle.encode_block([(b"b" + struct.pack("<Q", 1 << 8 | 1), b"x"),
-                                    (b"a" + struct.pack("<Q", 2 << 8 | 1), b"y")], 16)
-    img = _single_block_table(contents)
+    last = b"a" + struct.pack("<Q", 2 << 8 | 1)
+    contents = oracle.encode_block([(b"b" + struct.pack("<Q", 1 << 8 | 1), b"x"), (last, b"y")], 16)
+    img = _single_block_table(contents, last)
     job = W.Job("ooo", 0, [], W.MAX_SEQ, False)
     check_job(job, [img])
+
+
+@pytest.mark.parametrize("index_key", [b"z" * 9, b"b" + struct.pack("<Q", 2 << 8 | 1), b"b" + struct.pack("<Q", 1 << 8 | 1)])
+def test_index_key_check(index_key):
+    from test_oracle_invariants import _single_block_table
+    contents = oracle.encode_block([(b"a" + struct.pack("<Q", 2 << 8 | 1), b"y"),
+                                    (b"b" + struct.pack("<Q", 1 << 8 | 1), b"x")], 16)
+    job = W.Job("ikey", 0, [], W.MAX_SEQ, False)
+    other = oracle_inputs(W.config1(seed=4, scale=1 / 128))
+    check_job(job, [_single_block_table(contents, index_key)])
+    check_job(job, other + [_single_block_table(contents, index_key)])
 
 
 # ---- host entry point ----------------------------------------------------------------------
