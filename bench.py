@@ -226,13 +226,47 @@ def run_ours(args, ws, rank, local):
         for _ in range(ke):
             d2h = hstep()
         torch.cuda.synchronize()
+        te_single = (time.perf_counter() - ts) / ke
+
+        # the same jobs through a three-slot server (luda_server_submit_host), three jobs in
+        # flight: one job's inputs go in while another computes and a third's tables come
+        # out (the server lets one job at a time copy in each direction)
+        depth = 3
+        srv = luda.Server(depth, 1 << 46, luda.job_options(job))
+
+        def pipelined(k):
+            pending = []
+            nbytes = 0
+            for _ in range(k):
+                pending.append(srv.submit(host, job.smallest_snapshot, job.bottommost, host=True))
+                if len(pending) == depth:
+                    out, _ = srv.wait(pending.pop(0), copy_out=False)
+                    if out.status != 0:
+                        raise RuntimeError(f"served host job failed: {out.status}")
+                    nbytes = sum(out.tables[i].size for i in range(out.n_tables))
+                    L.luda_outputs_free(C.byref(out))
+            for t in pending:
+                out, _ = srv.wait(t, copy_out=False)
+                nbytes = sum(out.tables[i].size for i in range(out.n_tables))
+                L.luda_outputs_free(C.byref(out))
+            return nbytes
+
+        pipelined(2 * depth)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        d2h = pipelined(ke)
+        torch.cuda.synchronize()
         te = (time.perf_counter() - ts) / ke
+        srv.close()
         if ws > 1:
-            t = torch.tensor([te], dtype=torch.float64)
+            t = torch.tensor([te, te_single], dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+            te, te_single = float(t[0].item()), float(t[1].item())
         e2e = {"value": round(ws * in_bytes / MiB / te, 1), "unit": "MiB/s", "h2d_bytes_per_step": in_bytes,
-               "d2h_bytes_per_step": d2h, "ms_per_step": round(te * 1e3, 3), "steps": ke}
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(te * 1e3, 3), "steps": ke,
+               "api": f"luda_server_submit_host, {depth} slots, {depth} jobs in flight (copies in and out overlap)",
+               "single_call": {"value": round(ws * in_bytes / MiB / te_single, 1), "unit": "MiB/s",
+                               "ms_per_step": round(te_single * 1e3, 3), "api": "luda_compact"}}
 
     if rank != 0:
         return

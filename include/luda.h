@@ -220,6 +220,12 @@ typedef struct {
 
 LUDA_API luda_status luda_server_create(const luda_server_config* cfg, luda_server** server);
 LUDA_API luda_status luda_server_submit(luda_server* server, const luda_job* job, uint64_t* ticket);
+/* As luda_server_submit, for a job whose input tables are in host memory (pinned memory
+ * gives the fastest copies): the slot copies them to the device, compacts, and copies the
+ * new tables back into library-owned pinned host memory (as luda_compact). The device
+ * copy of the inputs counts against the budget. With two or more slots the copies of
+ * different jobs overlap (one job's inputs going in while another's tables come out). */
+LUDA_API luda_status luda_server_submit_host(luda_server* server, const luda_job* job, uint64_t* ticket);
 LUDA_API luda_status luda_server_next(luda_server* server, int64_t timeout_ms, uint64_t* ticket);
 LUDA_API luda_status luda_server_wait(luda_server* server, uint64_t ticket, int64_t timeout_ms, luda_outputs* out,
                                       luda_job_stats* stats);

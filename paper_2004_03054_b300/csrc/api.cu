@@ -206,7 +206,7 @@ void pinned_put(uint8_t* p, size_t cap) {
   if (!p) return;
   std::lock_guard<std::mutex> lk(g_pin_mu);
   g_pin_free.emplace_back(p, cap);
-  while (g_pin_free.size() > 2) {
+  while (g_pin_free.size() > 4) {
     cudaFreeHost(g_pin_free.front().first);
     g_pin_free.erase(g_pin_free.begin());
   }
@@ -364,7 +364,7 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   CK(cudaEventRecord(side->ev[3], side->s));
   launch_encode_big(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
                     fmt, out, out_cap, b.big, tabs, st);
-  launch_bloom(b.surv, cnt, cap, b.blk_file, b.blk_start, b.files, recs, arena, fmt, b.bitmap, out_cap, bm_cap, st);
+  launch_bloom(b.ed, cnt, cap, b.files, fmt, b.bitmap, out_cap, bm_cap, st);
   launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, out, out_cap,
                      st);
   launch_file_finish(b.files, cnt, cap, b.bitmap, b.surv, recs, fmt, out, out_cap, tabs, b.fmsg, b.meta, st);
@@ -831,7 +831,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     pack_layout(L, pb, cap, bm_cap, key_cap);
   };
   layoutC(LC);
-  if (gate && !gate->admit(LA.off + LB.off + LC.off + out_cap)) {
+  if (gate && !gate->admit(LA.off + LB.off + LC.off + out_cap + gate->extra)) {
     set_detail("the job was not admitted (server shutting down)");
     return LUDA_ERR_OOM;
   }
@@ -895,14 +895,17 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
       return cuda_fail(cudaErrorMemoryAllocation, "pinned host allocation");
     }
     Timer t;
+    if (gate) gate->copy_begin(1);
     t.start(st);
     if (col.cnt.out_bytes)
       if (cudaMemcpyAsync(h->pinned, d_out, col.cnt.out_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        if (gate) gate->copy_end(1);
         holder_release(h);
         return cuda_fail(cudaGetLastError(), "copy of the new tables to the host");
       }
     t.stop(st);
-    d2h = t.ms();
+    d2h = t.ms();  // waits for the copy
+    if (gate) gate->copy_end(1);
     base = h->pinned;
   } else {
     h->dev = d_out;
@@ -1412,6 +1415,78 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
 
 }  // namespace
 
+luda_status luda::compact_job_host(const luda_job& job, const luda_options* opts, luda_outputs* out,
+                                   AdmitGate* gate) {
+  t_detail[0] = 0;
+  const luda_input* inputs = job.inputs;
+  const uint32_t n_inputs = job.n_inputs;
+  if (!out || (!inputs && n_inputs) || !opts) {
+    set_detail("NULL argument");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  memset(out, 0, sizeof *out);
+  const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+  const DevMem mem{opts, st};
+  // one device arena for all inputs, each at a 256-byte boundary
+  std::vector<uint64_t> off(n_inputs + 1, 0);
+  for (uint32_t i = 0; i < n_inputs; ++i) {
+    if (!inputs[i].data && inputs[i].size) {
+      set_detail("input %u: data is NULL", i);
+      return LUDA_ERR_INVALID_ARG;
+    }
+    off[i + 1] = (off[i] + inputs[i].size + 255) & ~uint64_t(255);
+  }
+  CrcTabs tabs;
+  luda_status rc = get_tabs(&tabs);
+  if (rc) return rc;
+  uint8_t* arena = static_cast<uint8_t*>(mem.get(off[n_inputs] + 256));
+  if (!arena) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
+  std::vector<luda_input> din(n_inputs);
+  Timer th;
+  if (gate) gate->copy_begin(0);
+  th.start(st);
+  for (uint32_t i = 0; i < n_inputs; ++i) {
+    din[i] = inputs[i];
+    din[i].data = arena + off[i];
+    if (inputs[i].size &&
+        cudaMemcpyAsync(arena + off[i], inputs[i].data, inputs[i].size, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      if (gate) gate->copy_end(0);
+      mem.put(arena);
+      return cuda_fail(cudaGetLastError(), "copy of the inputs to the device");
+    }
+  }
+  th.stop(st);
+  if (gate) {
+    cudaStreamSynchronize(st);
+    gate->copy_end(0);
+  }
+  HostJob hj{din.data(), n_inputs, job.smallest_snapshot, job.bottommost};
+  double ms = 0, d2h = 0;
+  double sms[LUDA_N_STAGES] = {};
+  uint64_t sbytes[LUDA_N_STAGES] = {};
+  if (gate) gate->extra = off[n_inputs] + 256;  // the device copy of the inputs counts too
+  rc = run_compaction(&hj, 1, opts, st, out, true, &ms, &d2h, sms, sbytes, gate);
+  const double h2d = th.ms();
+  mem.put(arena);
+  cudaStreamSynchronize(st);
+  if (rc) {
+    out->status = rc;
+    return rc;
+  }
+  out->ms_h2d = h2d;
+  out->ms_device = ms;
+  out->ms_d2h = d2h;
+  memcpy(out->stage_ms, sms, sizeof sms);
+  memcpy(out->stage_bytes, sbytes, sizeof sbytes);
+  if (out->status) {
+    const luda_status s = luda_status(out->status);
+    luda_outputs_free(out);
+    out->status = s;
+    return s;
+  }
+  return LUDA_OK;
+}
+
 luda_status luda::compact_job_device(const luda_job& job, const luda_options* opts, luda_outputs* out,
                                      AdmitGate* gate) {
   t_detail[0] = 0;
@@ -1530,66 +1605,13 @@ luda_status luda_compact_device(const luda_input* inputs, uint32_t n_inputs, int
 
 luda_status luda_compact(const luda_input* inputs, uint32_t n_inputs, int32_t level, uint64_t smallest_snapshot,
                          const luda_options* opts, luda_outputs* out) {
-  (void)level;
-  t_detail[0] = 0;
-  if (!out || (!inputs && n_inputs) || !opts) {
+  if (!out || !opts) {
+    t_detail[0] = 0;
     set_detail("NULL argument");
     return LUDA_ERR_INVALID_ARG;
   }
-  memset(out, 0, sizeof *out);
-  const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
-  const DevMem mem{opts, st};
-  // one device arena for all inputs, each at a 256-byte boundary
-  std::vector<uint64_t> off(n_inputs + 1, 0);
-  for (uint32_t i = 0; i < n_inputs; ++i) {
-    if (!inputs[i].data && inputs[i].size) {
-      set_detail("input %u: data is NULL", i);
-      return LUDA_ERR_INVALID_ARG;
-    }
-    off[i + 1] = (off[i] + inputs[i].size + 255) & ~uint64_t(255);
-  }
-  CrcTabs tabs;
-  luda_status rc = get_tabs(&tabs);
-  if (rc) return rc;
-  uint8_t* arena = static_cast<uint8_t*>(mem.get(off[n_inputs] + 256));
-  if (!arena) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
-  std::vector<luda_input> din(n_inputs);
-  Timer th;
-  th.start(st);
-  for (uint32_t i = 0; i < n_inputs; ++i) {
-    din[i] = inputs[i];
-    din[i].data = arena + off[i];
-    if (inputs[i].size &&
-        cudaMemcpyAsync(arena + off[i], inputs[i].data, inputs[i].size, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-      mem.put(arena);
-      return cuda_fail(cudaGetLastError(), "copy of the inputs to the device");
-    }
-  }
-  th.stop(st);
-  HostJob hj{din.data(), n_inputs, smallest_snapshot, opts->bottommost};
-  double ms = 0, d2h = 0;
-  double sms[LUDA_N_STAGES] = {};
-  uint64_t sbytes[LUDA_N_STAGES] = {};
-  rc = run_compaction(&hj, 1, opts, st, out, true, &ms, &d2h, sms, sbytes);
-  const double h2d = th.ms();
-  mem.put(arena);
-  cudaStreamSynchronize(st);
-  if (rc) {
-    out->status = rc;
-    return rc;
-  }
-  out->ms_h2d = h2d;
-  out->ms_device = ms;
-  out->ms_d2h = d2h;
-  memcpy(out->stage_ms, sms, sizeof sms);
-  memcpy(out->stage_bytes, sbytes, sizeof sbytes);
-  if (out->status) {
-    const luda_status s = luda_status(out->status);
-    luda_outputs_free(out);
-    out->status = s;
-    return s;
-  }
-  return LUDA_OK;
+  const luda_job job{inputs, n_inputs, level, smallest_snapshot, opts->bottommost};
+  return luda::compact_job_host(job, opts, out, nullptr);
 }
 
 luda_status luda_build(const luda_run* run, const luda_options* opts, luda_outputs* out) {

@@ -259,8 +259,7 @@ void launch_encode_big(const uint32_t* blk_start, Counts* cnt, uint32_t cap, con
                        const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
                        const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
                        Fmt fmt, uint8_t* out, uint64_t out_cap, const uint32_t* big, CrcTabs tabs, cudaStream_t st);
-void launch_bloom(const uint32_t* surv, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
-                  const uint32_t* blk_start, const FileDesc* files, Recs recs, const uint8_t* arena, Fmt fmt,
+void launch_bloom(const EncDesc* ed, const Counts* cnt, uint32_t cap, const FileDesc* files, Fmt fmt,
                   uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st);
 void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* bsz,
                         const uint64_t* C, const uint64_t* IX, const uint32_t* blk_file, const FileDesc* files,
@@ -289,11 +288,20 @@ void launch_msg_crc(CrcMsg* msgs, const uint32_t* count, uint32_t mult, uint32_t
 // the large allocations, with the device bytes the call holds at its peak (sizing buffers,
 // records and sort buffers, output arena). It may block; false abandons the call.
 struct AdmitGate {
+  uint64_t extra = 0;  // bytes the caller holds for the job besides the pipeline's own
   virtual bool admit(uint64_t bytes) = 0;
+  // Around the host<->device copies of a host job (dir 0: inputs in, 1: tables out); the
+  // copies are complete when copy_end is called. A server serialises each direction so
+  // that one job's inputs go in while another job's tables come out.
+  virtual void copy_begin(int dir) { (void)dir; }
+  virtual void copy_end(int dir) { (void)dir; }
   virtual ~AdmitGate() = default;
 };
 
 // One job on opts->stream with device inputs (luda_compact_device plus an admission gate).
 luda_status compact_job_device(const luda_job& job, const luda_options* opts, luda_outputs* out, AdmitGate* gate);
+// One job with host inputs: copied to the device, compacted, new tables copied back into
+// library-owned pinned host memory (luda_compact plus an admission gate).
+luda_status compact_job_host(const luda_job& job, const luda_options* opts, luda_outputs* out, AdmitGate* gate);
 
 }  // namespace luda

@@ -139,14 +139,20 @@ constexpr uint32_t kWinMax = 256;
 
 __device__ __forceinline__ uint32_t win_of(uint32_t gap) { return max(32u, (gap + 31u) & ~31u); }
 
-__global__ void k_max_gap(const uint32_t* __restrict__ next, const uint32_t* __restrict__ n_dev,
-                          uint32_t* __restrict__ gap) {
+__global__ void __launch_bounds__(256) k_max_gap(const uint32_t* __restrict__ next, const uint32_t* __restrict__ n_dev,
+                                                 uint32_t* __restrict__ gap) {
+  __shared__ uint32_t s_max[8];
   const uint32_t n = *n_dev;
   uint32_t g = 0;
   for (uint64_t i = gtid(); i < n; i += gstride()) g = max(g, next[i] - uint32_t(i));
-#pragma unroll
-  for (int o = 16; o; o >>= 1) g = max(g, __shfl_xor_sync(0xFFFFFFFFu, g, o));
-  if ((threadIdx.x & 31u) == 0 && g) atomicMax(gap, g);
+  g = __reduce_max_sync(0xFFFFFFFFu, g);
+  if ((threadIdx.x & 31u) == 0) s_max[threadIdx.x >> 5] = g;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    g = threadIdx.x < 8 ? s_max[threadIdx.x] : 0u;
+    g = __reduce_max_sync(0xFFFFFFFFu, g);
+    if (threadIdx.x == 0 && g) atomicMax(gap, g);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_stitch_win(const uint32_t* __restrict__ next,
@@ -173,11 +179,12 @@ __global__ void __launch_bounds__(256) k_stitch_win(const uint32_t* __restrict__
 __global__ void __launch_bounds__(256) k_stitch_combine(const uint32_t* __restrict__ exitw,
                                                         const uint32_t* __restrict__ n_dev,
                                                         const uint32_t* __restrict__ gap,
-                                                        uint32_t* __restrict__ entry) {
+                                                        uint32_t* __restrict__ entry,
+                                                        const uint32_t* __restrict__ done) {
   constexpr uint32_t kWords = 12000;  // rows held in shared memory
   __shared__ uint32_t s_rows[kWords];
   __shared__ uint32_t s_cur;
-  if (*gap > kWinMax) return;
+  if (*gap > kWinMax || *done) return;
   const uint32_t n = *n_dev, W = win_of(*gap);
   const uint32_t n_tiles = (n + kStitchTile - 1) / kStitchTile;
   const uint32_t per = kWords / W;
@@ -200,6 +207,63 @@ __global__ void __launch_bounds__(256) k_stitch_combine(const uint32_t* __restri
       s_cur = c;
     }
   }
+}
+
+// Parallel composition of the tiles (when all W-entry tables fit in shared memory): tile
+// t's table f_t maps the chain's entry offset in tile t to its entry offset in tile t + 1
+// (W: the chain has ended). Doubling (Hillis-Steele over function composition) turns
+// f_t into f_t o f_{t-1} o ... o f_0 in log2(tiles) rounds; tile t's entry is then
+// f_{t-1} o ... o f_0 applied to offset 0. Falls back to the sequential walk (all threads
+// return without writing, k_stitch_combine runs) when the tables do not fit.
+constexpr uint32_t kCombWords = 24576;
+constexpr uint32_t kCombSmem = 2 * kCombWords * 4;
+
+__global__ void __launch_bounds__(1024) k_stitch_compose(const uint32_t* __restrict__ exitw,
+                                                         const uint32_t* __restrict__ n_dev,
+                                                         const uint32_t* __restrict__ gap,
+                                                         uint32_t* __restrict__ entry,
+                                                         uint32_t* __restrict__ done) {
+  extern __shared__ uint32_t s_comp[];
+  if (*gap > kWinMax) return;
+  const uint32_t n = *n_dev, W = win_of(*gap);
+  const uint32_t n_tiles = (n + kStitchTile - 1) / kStitchTile;
+  if (uint64_t(n_tiles) * W > kCombWords) {
+    if (threadIdx.x == 0) *done = 0;
+    return;
+  }
+  uint32_t* A = s_comp;
+  uint32_t* B = s_comp + kCombWords;
+  for (uint32_t i = threadIdx.x; i < n_tiles * W; i += blockDim.x) {
+    const uint32_t t = i / W, k = i - t * W;
+    const uint32_t x = exitw[uint64_t(t) * kWinMax + k];
+    const uint32_t next_l = (t + 1) * kStitchTile;
+    A[i] = x < n ? x - next_l : W;  // offset in tile t + 1, or W: ended
+  }
+  __syncthreads();
+  for (uint32_t d = 1; d < n_tiles; d <<= 1) {
+    for (uint32_t i = threadIdx.x; i < n_tiles * W; i += blockDim.x) {
+      const uint32_t t = i / W;
+      if (t < d) {
+        B[i] = A[i];
+      } else {
+        const uint32_t v = A[(t - d) * W + (i - t * W)];  // through tiles t-2d+1 .. t-d
+        B[i] = v < W ? A[t * W + v] : W;
+      }
+    }
+    __syncthreads();
+    uint32_t* tmp = A;
+    A = B;
+    B = tmp;
+  }
+  for (uint32_t t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+    if (t == 0) {
+      entry[0] = 0;
+    } else {
+      const uint32_t v = A[(t - 1) * W];
+      entry[t] = v < W ? t * kStitchTile + v : n;
+    }
+  }
+  if (threadIdx.x == 0) *done = 1;
 }
 
 __global__ void __launch_bounds__(128) k_stitch_mark(const uint32_t* __restrict__ next,
@@ -241,9 +305,7 @@ __global__ void k_stitch_walk(const uint32_t* __restrict__ next, const uint32_t*
   for (uint64_t j = gtid() / 32; j < n_jobs; j += warps) {
     const uint32_t b = blocks_level ? jobs[j].blk_begin : jobs[j].surv_begin;
     const uint32_t e = blocks_level ? jobs[j].blk_end : jobs[j].surv_end;
-    for (uint32_t i = b + lane_id(); i < e; i += 32) flags[i] = 0;
-    __syncwarp();
-    if (lane_id() == 0) {
+    if (lane_id() == 0) {  // flags were cleared by the caller
       uint32_t x = b;
       while (x < e) {
         flags[x] = 1;
@@ -959,17 +1021,21 @@ __device__ uint32_t murmur3_32(const uint8_t* p, uint32_t n, uint32_t seed) {
   return h;
 }
 
-__global__ void k_bloom(const uint32_t* __restrict__ surv, const Counts* __restrict__ cnt,
-                        const uint32_t* __restrict__ blk_file, const uint32_t* __restrict__ start,
-                        const FileDesc* __restrict__ files, Recs recs, const uint8_t* __restrict__ arena, Fmt fmt,
-                        uint32_t* __restrict__ bitmap, uint64_t out_cap, uint64_t bm_cap) {
-  const uint32_t n = cnt->n_surv, nb = cnt->nb;
+__global__ void k_bloom(const EncDesc* __restrict__ ed, const Counts* __restrict__ cnt,
+                        const FileDesc* __restrict__ files, Fmt fmt, uint32_t* __restrict__ bitmap,
+                        uint64_t out_cap, uint64_t bm_cap) {
+  const uint32_t n = cnt->n_surv, nf = cnt->nf;
   if (cnt->out_bytes > out_cap || cnt->bm_words > bm_cap) return;
   for (uint64_t s = gtid(); s < n; s += gstride()) {
-    const uint32_t b = find_last_le(start, nb, uint32_t(s));
-    const FileDesc F = files[blk_file[b]];
-    const uint32_t x = surv[s];
-    uint32_t h = murmur3_32(arena + recs.koff[x], recs.klen[x] - 8, 0);
+    uint32_t lo = 0, hi = nf;  // the table holding survivor s
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (files[mid].ent_begin <= s) lo = mid;
+      else hi = mid;
+    }
+    const FileDesc F = files[lo];
+    const EncDesc e = ed[s];
+    uint32_t h = murmur3_32(reinterpret_cast<const uint8_t*>(e.kptr), e.klen - 8, 0);
     const uint32_t d = (h >> 17) | (h << 15);
     uint32_t* bm = bitmap + F.bm_word;
     for (uint32_t j = 0; j < fmt.k; ++j) {
@@ -1009,8 +1075,6 @@ __global__ void k_index_write(const uint32_t* __restrict__ start, const Counts* 
     st_u32(ib + (IX[fb1] - IX[fb0]) + 4ull * (b - fb0), uint32_t(eoff));
   }
 }
-
-// One CTA per table: filter block, metaindex block, index block trailer, footer.
 
 // Filter bitmaps into the tables: one thread per 32-bit bitmap word of all tables.
 __global__ void k_filter_copy(const FileDesc* __restrict__ files, const Counts* __restrict__ cnt,
@@ -1206,9 +1270,13 @@ void launch_stitch(const uint32_t* next, const uint32_t* n_dev, uint32_t cap, ui
   const uint32_t tiles = (cap + kStitchTile - 1) / kStitchTile;
   uint32_t* exitw = static_cast<uint32_t*>(temp);
   uint32_t* entry = exitw + uint64_t(tiles) * kWinMax;
-  k_max_gap<<<grid_for(cap, 256), 256, 0, st>>>(next, n_dev, gap); count_launches(1);
+  uint32_t* done = entry + tiles + 1;
+  k_max_gap<<<grid_for(cap, 256, kSms * 2), 256, 0, st>>>(next, n_dev, gap); count_launches(1);
+  cudaMemsetAsync(flags, 0, cap + 1, st);  // the walk path sets only the chain's flags
   k_stitch_win<<<grid_for(tiles, 1, kSms * 8), 256, 0, st>>>(next, n_dev, gap, exitw); count_launches(1);
-  k_stitch_combine<<<1, 256, 0, st>>>(exitw, n_dev, gap, entry); count_launches(1);
+  cudaFuncSetAttribute(k_stitch_compose, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCombSmem));
+  k_stitch_compose<<<1, 1024, kCombSmem, st>>>(exitw, n_dev, gap, entry, done);
+  k_stitch_combine<<<1, 256, 0, st>>>(exitw, n_dev, gap, entry, done); count_launches(2);
   k_stitch_mark<<<grid_for(tiles, 1, kSms * 8), 128, 0, st>>>(next, n_dev, gap, entry, flags); count_launches(1);
   k_stitch_walk<<<grid_for(n_jobs, 8, kSms * 8), 256, 0, st>>>(next, gap, jobs, n_jobs, blocks_level, flags);
   count_launches(1);
@@ -1321,12 +1389,11 @@ void launch_encode_big(const uint32_t* blk_start, Counts* cnt, uint32_t cap, con
   count_launches(1);
 }
 
-void launch_bloom(const uint32_t* surv, const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
-                  const uint32_t* blk_start, const FileDesc* files, Recs recs, const uint8_t* arena, Fmt fmt,
+void launch_bloom(const EncDesc* ed, const Counts* cnt, uint32_t cap, const FileDesc* files, Fmt fmt,
                   uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st) {
   if (!cap) return;
-  k_bloom<<<grid_for(cap, 256), 256, 0, st>>>(surv, cnt, blk_file, blk_start, files, recs, arena, fmt, bitmap,
-                                              out_cap, bm_cap); count_launches(1);
+  k_bloom<<<grid_for(cap, 256), 256, 0, st>>>(ed, cnt, files, fmt, bitmap, out_cap, bm_cap);
+  count_launches(1);
 }
 
 void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* bsz,

@@ -46,6 +46,7 @@ struct Ticket {
   luda_status rc = LUDA_OK;
   luda_outputs out{};
   luda_job_stats stats{};
+  bool host = false;  // inputs and outputs in host memory
   char detail[512] = {0};
   Clock::time_point t_submit, t_start, t_gate, t_admit, t_done;
 };
@@ -70,6 +71,7 @@ struct luda_server {
   uint64_t used = 0;
   uint32_t running = 0;               // admitted jobs
   bool stopping = false;
+  std::mutex copy_mu[2];              // host jobs: inputs in / tables out, one job at a time each
   luda_server_stats st{};
 };
 
@@ -97,6 +99,8 @@ struct SlotGate final : AdmitGate {
     s->cv_budget.notify_all();  // the next waiting job may fit as well
     return true;
   }
+  void copy_begin(int dir) override { s->copy_mu[dir].lock(); }
+  void copy_end(int dir) override { s->copy_mu[dir].unlock(); }
 };
 
 void slot_main(luda_server* s, uint32_t slot) {
@@ -116,7 +120,8 @@ void slot_main(luda_server* s, uint32_t slot) {
     o.stream = s->streams[slot];
     o.bottommost = t->job.bottommost;
     SlotGate gate(s, t);
-    const luda_status rc = compact_job_device(t->job, &o, &t->out, &gate);
+    const luda_status rc = t->host ? compact_job_host(t->job, &o, &t->out, &gate)
+                                   : compact_job_device(t->job, &o, &t->out, &gate);
     if (rc) snprintf(t->detail, sizeof t->detail, "%s", luda_last_error_detail());
     const Clock::time_point now = Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
@@ -183,9 +188,10 @@ luda_status luda_server_create(const luda_server_config* cfg, luda_server** serv
   return LUDA_OK;
 }
 
-luda_status luda_server_submit(luda_server* s, const luda_job* job, uint64_t* ticket) {
+static luda_status submit(luda_server* s, const luda_job* job, uint64_t* ticket, bool host) {
   if (!s || !job || !ticket || (!job->inputs && job->n_inputs)) return LUDA_ERR_INVALID_ARG;
   auto t = std::make_unique<Ticket>();
+  t->host = host;
   t->inputs.assign(job->inputs, job->inputs + job->n_inputs);
   t->job = *job;
   t->job.inputs = t->inputs.data();
@@ -200,6 +206,14 @@ luda_status luda_server_submit(luda_server* s, const luda_job* job, uint64_t* ti
   s->st.submitted += 1;
   s->cv_queue.notify_one();
   return LUDA_OK;
+}
+
+luda_status luda_server_submit(luda_server* s, const luda_job* job, uint64_t* ticket) {
+  return submit(s, job, ticket, false);
+}
+
+luda_status luda_server_submit_host(luda_server* s, const luda_job* job, uint64_t* ticket) {
+  return submit(s, job, ticket, true);
 }
 
 luda_status luda_server_next(luda_server* s, int64_t timeout_ms, uint64_t* ticket) {

@@ -124,6 +124,8 @@ def lib():
         L.luda_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]
         L.luda_server_submit.restype = st
         L.luda_server_submit.argtypes = [C.c_void_p, C.POINTER(Job), C.POINTER(C.c_uint64)]
+        L.luda_server_submit_host.restype = st
+        L.luda_server_submit_host.argtypes = [C.c_void_p, C.POINTER(Job), C.POINTER(C.c_uint64)]
         L.luda_server_next.restype = st
         L.luda_server_next.argtypes = [C.c_void_p, C.c_int64, C.POINTER(C.c_uint64)]
         L.luda_server_wait.restype = st
@@ -346,11 +348,17 @@ class Server:
             raise RuntimeError(f"luda_server_create: {strerror(rc)}: {last_error_detail()}")
         self._keep = {}
 
-    def submit(self, inputs, smallest_snapshot: int = MAX_SEQ, bottommost: bool = False, level: int = 1) -> int:
+    def submit(self, inputs, smallest_snapshot: int = MAX_SEQ, bottommost: bool = False, level: int = 1,
+               host: bool = False) -> int:
+        """inputs: CUDA uint8 tensors or (device pointer, size) pairs; with host=True, host
+        tensors (pinned for the fastest copies), numpy uint8 arrays or (host pointer, size)
+        pairs, and the job's tables come back in host memory."""
         ins = (Input * max(1, len(inputs)))()
         for i, t in enumerate(inputs):
             if isinstance(t, tuple):
                 ins[i].data, ins[i].size = t
+            elif isinstance(t, np.ndarray):
+                ins[i].data, ins[i].size = t.ctypes.data, t.nbytes
             else:
                 ins[i].data, ins[i].size = t.data_ptr(), t.numel()
         job = Job()
@@ -358,10 +366,11 @@ class Server:
         job.n_inputs, job.level = len(inputs), level
         job.smallest_snapshot, job.bottommost = smallest_snapshot, int(bool(bottommost))
         ticket = C.c_uint64()
-        rc = lib().luda_server_submit(self.handle, C.byref(job), C.byref(ticket))
+        fn = lib().luda_server_submit_host if host else lib().luda_server_submit
+        rc = fn(self.handle, C.byref(job), C.byref(ticket))
         if rc != OK:
             raise RuntimeError(f"luda_server_submit: {strerror(rc)}: {last_error_detail()}")
-        self._keep[ticket.value] = list(inputs)
+        self._keep[ticket.value] = (list(inputs), host)
         return ticket.value
 
     def next(self, timeout_ms: int = -1):
@@ -382,11 +391,11 @@ class Server:
         rc = lib().luda_server_wait(self.handle, ticket, timeout_ms, C.byref(out), C.byref(stats))
         if rc == ERR_TIMEOUT:
             raise TimeoutError(f"ticket {ticket} not done")
-        self._keep.pop(ticket, None)
+        _, host = self._keep.pop(ticket, (None, False))
         if not copy_out:
             out.status = rc
             return out, stats
-        return _take(rc, out, device=True), stats
+        return _take(rc, out, device=not host), stats
 
     def stats(self) -> ServerStats:
         st = ServerStats()

@@ -179,3 +179,21 @@ def _serve_and_capture(L, stream, check, mib, captured):
                        lsm_kw=dict(memtable_bytes=2 * mib, target_file=2 * mib, fanout=3, value_pool_bytes=64 * mib))
     finally:
         L.LSM.close = orig_close
+
+
+@pytest.mark.parametrize("n_slots", [1, 3])
+def test_server_host_jobs_equal_oracle(n_slots):
+    """Jobs with host-memory inputs: copied in, compacted and copied back by the slots;
+    the tables equal the oracle's and those of the device path."""
+    jobs = _jobs(9, seed=17)
+    ins = [oracle_inputs(j) for j in jobs]
+    want = [oracle_compact(j, x) for j, x in zip(jobs, ins)]
+    host = [[torch.frombuffer(bytearray(b), dtype=torch.uint8).pin_memory() for b in x] for x in ins]
+    srv = luda.Server(n_slots, 1 << 40, luda.options(T, R, BPK, TARGET))
+    tickets = [srv.submit(h, j.smallest_snapshot, j.bottommost, host=True) for h, j in zip(host, jobs)]
+    for j, t in enumerate(tickets):
+        res, st = srv.wait(t, timeout_ms=60_000)
+        assert res.status == want[j].status == 0, (j, res.status, res.detail)
+        assert res.tables == [x.data for x in want[j].tables], j
+        assert st.reserved_bytes >= sum(len(b) for b in ins[j])
+    srv.close()
