@@ -379,17 +379,32 @@ def batched(args, stream):
     for _ in range(w):
         batch()
     ms_batch = timed(batch, k)
-    plan = luda.Plan(dev_jobs, opts)
-    for _ in range(w):
-        plan.run(C.c_void_p(stream.cuda_stream))
-    c0 = luda.launch_count()
-    ms_plan = timed(lambda: plan.run(C.c_void_p(stream.cuda_stream)), k)
-    plan_launches = (luda.launch_count() - c0) // k
-    pouts = plan.outputs(copy_out=False)
-    bad = [j for j in range(len(dev_jobs)) if pouts[j].status != 0]
-    plan.close()
-    if bad:
-        raise RuntimeError(f"plan jobs failed: {bad[:5]}")
+    def plan_leg(o):
+        plan = luda.Plan(dev_jobs, o)
+        for _ in range(w):
+            plan.run(C.c_void_p(stream.cuda_stream))
+        c0 = luda.launch_count()
+        ms = timed(lambda: plan.run(C.c_void_p(stream.cuda_stream)), k)
+        launches = (luda.launch_count() - c0) // k
+        pouts = plan.outputs(copy_out=False)
+        bad = [j for j in range(len(dev_jobs)) if pouts[j].status != 0]
+        plan.close()
+        if bad:
+            raise RuntimeError(f"plan jobs failed: {bad[:5]}")
+        return ms, launches
+
+    ms_plan_default, _ = plan_leg(opts)
+    tuned = None
+    if not args.no_autotune:
+        from paper_2004_03054_b300 import autotune as AT
+        res = AT.tune(dev_jobs, opts, reps=3)
+        tuned = {"tuning": res.tuning, "cache": res.cache, "candidates_timed": len(res.evaluated),
+                 "search_s": round(res.seconds, 2), "tuner_best_ms": round(res.best_ms, 3),
+                 "tuner_default_ms": round(res.default_ms, 3) if res.default_ms else None,
+                 "method": "coordinate descent over luda_tuning; each candidate a plan timed by luda_autotune"}
+        ms_plan, plan_launches = plan_leg(opts.with_tuning(res.tuning))
+    else:
+        ms_plan, plan_launches = plan_leg(opts)
     del keep
 
     def q(p):
@@ -404,7 +419,11 @@ def batched(args, stream):
             "batch_call": {"value": round(mib / (ms_batch / 1e3), 1), "unit": "MiB/s",
                            "ms_per_step": round(ms_batch, 3)},
             "plan_replay": {"value": round(mib / (ms_plan / 1e3), 1), "unit": "MiB/s",
-                            "ms_per_step": round(ms_plan, 3), "gpu_launches_per_replay": plan_launches},
+                            "ms_per_step": round(ms_plan, 3), "gpu_launches_per_replay": plan_launches,
+                            "tuning": "autotuned" if tuned else "default"},
+            "plan_replay_default_tuning": {"value": round(mib / (ms_plan_default / 1e3), 1), "unit": "MiB/s",
+                                           "ms_per_step": round(ms_plan_default, 3)},
+            "autotune": tuned,
             "gpu_launches_total": luda.launch_count() - l0}
 
 
@@ -518,6 +537,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="batched leg: plan with the default launch shapes")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--serve-memtables", type=int, default=40)
     ap.add_argument("--serve-rate", type=float, default=8e6, help="writes per second of the served stream")

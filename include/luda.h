@@ -70,6 +70,29 @@ typedef struct {
 typedef void* (*luda_alloc_fn)(size_t bytes, void* ctx, void* stream);
 typedef void (*luda_free_fn)(void* ptr, void* ctx, void* stream);
 
+/* Launch shapes of the pipeline's kernels. They decide how the work is split over CTAs
+ * and never change a byte of the output: any valid tuning gives the same tables. 0 in a
+ * field means the built-in default. luda_autotune measures candidates; a caller passes
+ * the winner through luda_options.tuning. */
+typedef struct {
+  uint32_t merge_tile;          /* records per merge CTA: 512, 1024 or 2048 (default 1024) */
+  uint32_t merge_ctas_per_sm;   /* grid of each merge pass, CTAs per SM: 1..32 (default 8) */
+  uint32_t decode_warps;        /* warps per CTA of the decoder, one data block each: 1..16 (default 8) */
+  uint32_t walk_threads;        /* threads per CTA of the block walk, one block each: 32..256, multiple of 32
+                                   (default 256) */
+  uint32_t encode_ctas_per_sm;  /* staged encoder CTAs per SM: 1..8, capped by shared memory (default: as many
+                                   as fit) */
+  uint32_t elem_threads;        /* threads per CTA of the per-record and per-block kernels of the drop rule,
+                                   cut and layout stages: 64..1024, multiple of 32 (default 256) */
+  uint32_t reserved[2];         /* must be 0 */
+} luda_tuning;
+
+/* Fills the defaults (all fields 0). */
+LUDA_API void luda_tuning_default(luda_tuning* t);
+/* LUDA_OK if every field is 0 or in its range, else LUDA_ERR_INVALID_ARG with the field
+ * named in luda_last_error_detail. */
+LUDA_API luda_status luda_tuning_check(const luda_tuning* t);
+
 typedef struct {
   uint32_t block_size;          /* T: a data block is closed once its size reaches T (>= 1) */
   uint32_t restart_interval;    /* R: every R-th entry of a block is a restart (1..65535) */
@@ -81,6 +104,8 @@ typedef struct {
   luda_free_fn dev_free;
   void* alloc_ctx;
   void* stream;                 /* cudaStream_t; NULL = the legacy default stream */
+  const luda_tuning* tuning;    /* launch shapes; NULL = defaults. Read during the call (plans: during
+                                   luda_plan_create) and not kept */
 } luda_options;
 
 /* Defaults: T = 4096, R = 16, bpk = 10, target = 2 MiB, not bottommost, no flags. */
@@ -165,6 +190,19 @@ LUDA_API luda_status luda_plan_create(const luda_job* jobs, uint32_t n_jobs, con
 LUDA_API luda_status luda_plan_run(luda_plan* plan, void* stream);
 LUDA_API luda_status luda_plan_outputs(luda_plan* plan, luda_outputs* outs);
 LUDA_API void luda_plan_destroy(luda_plan* plan);
+
+/* ---- autotuner: time candidate launch shapes on a batch -------------------------------
+ * For each of the n_candidates tunings, builds a plan of the jobs with opts and that
+ * tuning, replays it once untimed and then `reps` times (>= 1) between CUDA events on the
+ * plan's stream, and writes the median replay time in ms to ms[i] (a candidate that fails
+ * gets a negative ms[i] and does not stop the others). *best receives the index of the
+ * fastest candidate. Plans are built and destroyed one at a time, so the device holds one
+ * plan's memory at most. opts->tuning is ignored. Returns LUDA_ERR_INVALID_ARG for an
+ * invalid candidate or NULL arguments, else the first error if every candidate failed,
+ * else LUDA_OK. */
+LUDA_API luda_status luda_autotune(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts,
+                                   const luda_tuning* candidates, uint32_t n_candidates, uint32_t reps, double* ms,
+                                   uint32_t* best);
 
 /* ---- serving: continuous batching of compaction jobs ----------------------------------
  * A server takes compaction jobs as they arise (for example from an LSM tree whose tables

@@ -46,6 +46,40 @@ void set_detail(const char* fmt, ...) {
 
 void luda::set_error_detail(const char* text) { snprintf(t_detail, sizeof t_detail, "%s", text); }
 
+// ---- launch shapes ----------------------------------------------------------------------------
+namespace {
+thread_local Tuning t_tuning;
+}
+
+const Tuning& luda::tuning() { return t_tuning; }
+
+bool luda::tuning_valid(const luda_tuning* t) {
+  if (!t) return true;
+  const char* bad = nullptr;
+  if (t->merge_tile && t->merge_tile != 512 && t->merge_tile != 1024 && t->merge_tile != 2048) bad = "merge_tile";
+  else if (t->merge_ctas_per_sm > 32) bad = "merge_ctas_per_sm";
+  else if (t->decode_warps > 16) bad = "decode_warps";
+  else if (t->walk_threads && (t->walk_threads > 256 || t->walk_threads % 32)) bad = "walk_threads";
+  else if (t->encode_ctas_per_sm > 8) bad = "encode_ctas_per_sm";
+  else if (t->elem_threads && (t->elem_threads < 64 || t->elem_threads > 1024 || t->elem_threads % 32))
+    bad = "elem_threads";
+  else if (t->reserved[0] || t->reserved[1]) bad = "reserved";
+  if (bad) set_detail("invalid tuning: %s", bad);
+  return bad == nullptr;
+}
+
+luda::TuningScope::TuningScope(const luda_tuning* t) : saved_(t_tuning) {
+  if (!t) return;
+  if (t->merge_tile) t_tuning.merge_tile = t->merge_tile;
+  if (t->merge_ctas_per_sm) t_tuning.merge_ctas_per_sm = t->merge_ctas_per_sm;
+  if (t->decode_warps) t_tuning.decode_warps = t->decode_warps;
+  if (t->walk_threads) t_tuning.walk_threads = t->walk_threads;
+  if (t->encode_ctas_per_sm) t_tuning.encode_ctas_per_sm = t->encode_ctas_per_sm;
+  if (t->elem_threads) t_tuning.elem_threads = t->elem_threads;
+}
+
+luda::TuningScope::~TuningScope() { t_tuning = saved_; }
+
 namespace {
 
 // ---- per-device CRC tables ----------------------------------------------------------------
@@ -240,6 +274,7 @@ luda_status opts_check(const luda_options* o, Fmt* fmt) {
                (unsigned long long)o->target_file_size);
     return LUDA_ERR_INVALID_ARG;
   }
+  if (!tuning_valid(o->tuning)) return LUDA_ERR_INVALID_ARG;
   uint32_t k = o->bloom_bits_per_key * 69 / 100;
   if (k < 1) k = 1;
   if (k > 30) k = 30;
@@ -518,6 +553,7 @@ struct Timer {
 // others stay. When no adjacent pair shares a buffer the smallest run is moved across.
 // At the end every job's run is brought to the buffer of the largest job.
 struct MergeSched {
+  uint32_t tile = 1024;  // records per merge tile (set before merge_schedule)
   std::vector<MergeSpan> spans;
   std::vector<uint32_t> pass_span0, pass_nspans, pass_ntiles;
   uint32_t max_tiles = 1;
@@ -532,7 +568,8 @@ void merge_schedule(const std::vector<std::vector<std::pair<uint32_t, uint32_t>>
   for (size_t j = 0; j < runs_in.size(); ++j)
     for (const auto& r : runs_in[j])
       if (r.second) runs[j].push_back(R{r.first, r.second, 0});
-  auto tiles_of = [](uint32_t n) { return (n + kMergeTile - 1) / kMergeTile; };
+  const uint32_t tile = S->tile;
+  auto tiles_of = [tile](uint32_t n) { return (n + tile - 1) / tile; };
   auto begin_pass = [&]() { S->pass_span0.push_back(uint32_t(S->spans.size())); };
   auto end_pass = [&](uint32_t tiles) {
     S->pass_nspans.push_back(uint32_t(S->spans.size()) - S->pass_span0.back());
@@ -615,6 +652,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   Fmt fmt;
   luda_status rc = opts_check(o, &fmt);
   if (rc) return rc;
+  const TuningScope tuned(o->tuning);
   for (uint32_t j = 0; j < n_jobs; ++j) {
     memset(&outs[j], 0, sizeof(luda_outputs));
     if (jobs[j].n_inputs && !jobs[j].inputs) {
@@ -790,6 +828,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   }
   // merge schedule: linked inputs form one sorted run
   MergeSched ms;
+  ms.tile = tuning().merge_tile;
   {
     std::vector<std::vector<std::pair<uint32_t, uint32_t>>> runs(n_jobs);
     for (uint32_t j = 0; j < n_jobs; ++j)
@@ -865,8 +904,8 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
   launch_sort_init(d_ord0, d_pfx0, recs, d_arena, n_rec, st);
   for (size_t p = 0; p < pass_span0.size(); ++p)
-    launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], d_ord0, d_pfx0, d_ord1, d_pfx1, recs,
-                      d_arena, st);
+    launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], ms.tile, d_ord0, d_pfx0, d_ord1,
+                      d_pfx1, recs, d_arena, st);
   uint32_t* src_o = ms.final_buf ? d_ord1 : d_ord0;
   tr.mark(6, st);
   launch_gc_flags(src_o, n_rec, d_jobs, n_jobs, recs, d_arena, d_keep, d_errs, st);
@@ -959,6 +998,7 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
   Fmt fmt;
   luda_status rc = opts_check(o, &fmt);
   if (rc) return rc;
+  const TuningScope tuned(o->tuning);
   memset(out, 0, sizeof *out);
   if (!run) {
     set_detail("run is NULL");
@@ -1153,6 +1193,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   Fmt fmt;
   luda_status rc = opts_check(o, &fmt);
   if (rc) return rc;
+  const TuningScope tuned(o->tuning);
   CrcTabs tabs;
   if ((rc = get_tabs(&tabs))) return rc;
   CK(cudaGetDevice(&P->device));
@@ -1306,6 +1347,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   }
   // merge schedule (as in run_compaction); replays check that the links still hold
   MergeSched ms;
+  ms.tile = tuning().merge_tile;
   {
     std::vector<std::vector<std::pair<uint32_t, uint32_t>>> runs(n_jobs);
     for (uint32_t j = 0; j < n_jobs; ++j)
@@ -1380,8 +1422,8 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
     launch_sort_init(d_ord0, d_pfx0, recs, d_arena, n_rec, st);
     for (size_t p = 0; p < pass_span0.size(); ++p)
-      launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], d_ord0, d_pfx0, d_ord1, d_pfx1,
-                        recs, d_arena, st);
+      launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], ms.tile, d_ord0, d_pfx0, d_ord1,
+                        d_pfx1, recs, d_arena, st);
     uint32_t* src_o = ms.final_buf ? d_ord1 : d_ord0;
     launch_gc_flags(src_o, n_rec, d_jobs, n_jobs, recs, d_arena, d_keep, d_errs, st);
     CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
@@ -1683,5 +1725,81 @@ luda_status luda_plan_outputs(luda_plan* plan, luda_outputs* outs) {
 }
 
 void luda_plan_destroy(luda_plan* plan) { delete reinterpret_cast<PlanImpl*>(plan); }
+
+void luda_tuning_default(luda_tuning* t) {
+  if (t) memset(t, 0, sizeof *t);
+}
+
+luda_status luda_tuning_check(const luda_tuning* t) {
+  t_detail[0] = 0;
+  if (!t) {
+    set_detail("tuning pointer is NULL");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  return tuning_valid(t) ? LUDA_OK : LUDA_ERR_INVALID_ARG;
+}
+
+luda_status luda_autotune(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts,
+                          const luda_tuning* candidates, uint32_t n_candidates, uint32_t reps, double* ms,
+                          uint32_t* best) {
+  t_detail[0] = 0;
+  if ((!jobs && n_jobs) || !opts || !candidates || !n_candidates || !reps || !ms || !best) {
+    set_detail("NULL argument, no candidates or no repetitions");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  for (uint32_t c = 0; c < n_candidates; ++c)
+    if (!tuning_valid(&candidates[c])) return LUDA_ERR_INVALID_ARG;
+  luda_status first = LUDA_OK;
+  double best_ms = -1;
+  *best = 0;
+  for (uint32_t c = 0; c < n_candidates; ++c) {
+    ms[c] = -1;
+    luda_options o = *opts;
+    o.tuning = &candidates[c];
+    luda_plan* plan = nullptr;
+    luda_status rc = luda_plan_create(jobs, n_jobs, &o, &plan);
+    std::vector<double> t;
+    if (!rc) {
+      PlanImpl* P = reinterpret_cast<PlanImpl*>(plan);
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      cudaError_t e = cudaEventCreate(&e0);
+      if (e == cudaSuccess) e = cudaEventCreate(&e1);
+      if (e == cudaSuccess) rc = luda_plan_run(plan, P->st);  // untimed: first replay
+      if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);
+      for (uint32_t r = 0; r < reps && e == cudaSuccess && !rc; ++r) {
+        e = cudaEventRecord(e0, P->st);
+        if (e == cudaSuccess) rc = luda_plan_run(plan, P->st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, P->st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float x = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+        t.push_back(x);
+      }
+      if (e != cudaSuccess && !rc) rc = cuda_fail(e, "autotune timing");
+      if (!rc) {
+        // a candidate whose jobs failed (a corrupt input) is not a valid measurement
+        std::vector<luda_outputs> outs(n_jobs ? n_jobs : 1);
+        rc = luda_plan_outputs(plan, outs.data());
+        for (uint32_t j = 0; j < n_jobs && !rc; ++j)
+          if (outs[j].status) rc = luda_status(outs[j].status);
+        for (uint32_t j = 0; j < n_jobs; ++j) luda_outputs_free(&outs[j]);
+      }
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      luda_plan_destroy(plan);
+    }
+    if (rc) {
+      if (!first) first = rc;
+      continue;
+    }
+    std::sort(t.begin(), t.end());
+    ms[c] = t[t.size() / 2];
+    if (best_ms < 0 || ms[c] < best_ms) {
+      best_ms = ms[c];
+      *best = c;
+    }
+  }
+  return best_ms < 0 ? first : LUDA_OK;
+}
 
 }  // extern "C"

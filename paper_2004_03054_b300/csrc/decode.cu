@@ -323,7 +323,7 @@ __device__ void decode_walk(const BlockDesc& b, uint64_t rec, uint64_t kpos, Rec
   }
 }
 
-__global__ void __launch_bounds__(256) k_decode(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
+__global__ void __launch_bounds__(512) k_decode(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
                                                 const DInput* __restrict__ in, const uint32_t* __restrict__ nrec,
                                                 const uint16_t* __restrict__ hdr_tab,
                                                 const uint32_t* __restrict__ rec_first,
@@ -577,7 +577,8 @@ void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInpu
 void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
                        uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st) {
   if (!n_blocks) return;
-  k_block_walk<<<grid_for(n_blocks, 256), 256, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, cnt, hdr_tab);
+  const unsigned t = tuning().walk_threads;
+  k_block_walk<<<grid_for(n_blocks, t), t, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, cnt, hdr_tab);
   count_launches(1);
 }
 
@@ -591,7 +592,8 @@ void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in,
                    const uint16_t* hdr_tab, const uint32_t* rec_first, const uint64_t* key_first, Recs recs,
                    uint8_t* arena, DErr* errs, cudaStream_t st) {
   if (!n_blocks) return;
-  k_decode<<<grid_for(n_blocks, 8), 256, 0, st>>>(blocks, n_blocks, in, nrec, hdr_tab, rec_first, key_first, recs,
+  const unsigned w = tuning().decode_warps;
+  k_decode<<<grid_for(n_blocks, w), w * 32, 0, st>>>(blocks, n_blocks, in, nrec, hdr_tab, rec_first, key_first, recs,
                                                   arena, errs);
   count_launches(1);
 }

@@ -144,6 +144,33 @@ inline unsigned grid_for(uint64_t work, unsigned per_cta, unsigned max_ctas = kS
   return unsigned(g);
 }
 
+// ---- launch shapes (luda_tuning) ----------------------------------------------------------
+// The launchers read the calling thread's current tuning; an entry point installs the
+// caller's (luda_options.tuning) for its duration with a TuningScope. Defaults resolved:
+struct Tuning {
+  uint32_t merge_tile = 1024;
+  uint32_t merge_ctas_per_sm = 8;
+  uint32_t decode_warps = 8;
+  uint32_t walk_threads = 256;
+  uint32_t encode_ctas_per_sm = 0;  // 0: as many as shared memory allows
+  uint32_t elem_threads = 256;
+};
+const Tuning& tuning();
+// Range check of a luda_tuning (0 = default); sets the error detail on failure.
+bool tuning_valid(const luda_tuning* t);
+class TuningScope {
+ public:
+  explicit TuningScope(const luda_tuning* t);  // t must be valid (or NULL)
+  ~TuningScope();
+  TuningScope(const TuningScope&) = delete;
+  TuningScope& operator=(const TuningScope&) = delete;
+
+ private:
+  Tuning saved_;
+};
+// CTA size of the per-record and per-block kernels of the drop rule, cut and layout stages.
+inline unsigned elem_threads() { return tuning().elem_threads; }
+
 // ---- scan.cu ----------------------------------------------------------------------------
 uint64_t scan_temp_bytes(uint64_t n);
 template <typename In, typename Out>
@@ -199,7 +226,7 @@ struct MergeSpan {
   uint32_t src;         // buffer (0/1) holding both runs; the result goes to the other
   uint32_t pad;
 };
-constexpr uint32_t kMergeTile = 1024;
+constexpr uint32_t kMergeTileMax = 2048;  // merge tiles: 512, 1024 or 2048 records
 
 void launch_check_order(Recs recs, const uint8_t* arena, uint32_t n_rec, const DInput* in, DErr* errs,
                         cudaStream_t st);
@@ -207,8 +234,8 @@ void launch_plan_sanitize(Recs recs, uint32_t n_rec, const JobDev* jobs, uint32_
                           const uint8_t* arena, cudaStream_t st);
 void launch_sort_init(uint32_t* ord, MKey* okey, Recs recs, const uint8_t* arena, uint32_t n, cudaStream_t st);
 // One pass of merges; ord[b] / key[b] are the two buffers, each span names its source.
-void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* ord0, MKey* key0,
-                       uint32_t* ord1, MKey* key1, Recs recs, const uint8_t* arena, cudaStream_t st);
+void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t tile, uint32_t* ord0,
+                       MKey* key0, uint32_t* ord1, MKey* key1, Recs recs, const uint8_t* arena, cudaStream_t st);
 void launch_gc_flags(const uint32_t* ord, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, Recs recs,
                      const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st);
 void launch_gc_compact(const uint32_t* ord, const uint32_t* keep, const uint32_t* pos, uint32_t n_rec,

@@ -1250,13 +1250,13 @@ void launch_sizes(const uint32_t* surv, const Counts* cnt, uint32_t cap, const J
                   Recs recs, const uint8_t* arena, uint32_t* lcp, uint32_t* sd, uint32_t* dr, EncDesc* ed,
                   cudaStream_t st) {
   if (!cap) return;
-  k_sizes<<<grid_for(cap, 256), 256, 0, st>>>(surv, cnt, jobs, n_jobs, recs, arena, lcp, sd, dr, ed); count_launches(1);
+  k_sizes<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(surv, cnt, jobs, n_jobs, recs, arena, lcp, sd, dr, ed); count_launches(1);
 }
 
 void launch_block_next(const uint64_t* P, const uint32_t* dr, const Counts* cnt, uint32_t cap, const JobDev* jobs,
                        uint32_t n_jobs, Fmt fmt, uint32_t* next, cudaStream_t st) {
   if (!cap) return;
-  k_block_next<<<grid_for(cap, 256), 256, 0, st>>>(P, dr, cnt, jobs, n_jobs, fmt, next); count_launches(1);
+  k_block_next<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(P, dr, cnt, jobs, n_jobs, fmt, next); count_launches(1);
 }
 
 uint64_t stitch_temp_bytes(uint32_t cap) {
@@ -1284,7 +1284,7 @@ void launch_stitch(const uint32_t* next, const uint32_t* n_dev, uint32_t cap, ui
 
 void launch_compact_flags(const uint8_t* flags, const uint32_t* pos, const uint32_t* n_dev, uint32_t cap,
                           uint32_t* starts, uint32_t* total_out, cudaStream_t st) {
-  k_compact_flags<<<grid_for(cap, 256), 256, 0, st>>>(flags, pos, n_dev, starts, total_out); count_launches(1);
+  k_compact_flags<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(flags, pos, n_dev, starts, total_out); count_launches(1);
 }
 
 void launch_job_blocks(JobDev* jobs, uint32_t n_jobs, const uint32_t* bpos, cudaStream_t st) {
@@ -1294,13 +1294,13 @@ void launch_job_blocks(JobDev* jobs, uint32_t n_jobs, const uint32_t* bpos, cuda
 void launch_block_sizes(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* P,
                         const uint32_t* dr, Fmt fmt, uint64_t* bsz, uint64_t* disk, cudaStream_t st) {
   if (!cap) return;
-  k_block_sizes<<<grid_for(cap, 256), 256, 0, st>>>(blk_start, cnt, P, dr, fmt, bsz, disk); count_launches(1);
+  k_block_sizes<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(blk_start, cnt, P, dr, fmt, bsz, disk); count_launches(1);
 }
 
 void launch_file_next(const uint64_t* C, const Counts* cnt, uint32_t cap, const JobDev* jobs, uint32_t n_jobs,
                       Fmt fmt, uint32_t* next, cudaStream_t st) {
   if (!cap) return;
-  k_file_next<<<grid_for(cap, 256), 256, 0, st>>>(C, cnt, jobs, n_jobs, fmt, next); count_launches(1);
+  k_file_next<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(C, cnt, jobs, n_jobs, fmt, next); count_launches(1);
 }
 
 void launch_job_files(JobDev* jobs, uint32_t n_jobs, const uint32_t* fpos, cudaStream_t st) {
@@ -1309,14 +1309,14 @@ void launch_job_files(JobDev* jobs, uint32_t n_jobs, const uint32_t* fpos, cudaS
 
 void launch_block_file(const uint32_t* fpos, const Counts* cnt, uint32_t cap, uint32_t* blk_file, cudaStream_t st) {
   if (!cap) return;
-  k_block_file<<<grid_for(cap, 256), 256, 0, st>>>(fpos, cnt, blk_file); count_launches(1);
+  k_block_file<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(fpos, cnt, blk_file); count_launches(1);
 }
 
 void launch_index_sizes(const uint32_t* blk_start, const uint64_t* bsz, const uint64_t* C, const uint32_t* blk_file,
                         const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* surv, Recs recs,
                         uint32_t* ie, cudaStream_t st) {
   if (!cap) return;
-  k_index_sizes<<<grid_for(cap, 256), 256, 0, st>>>(blk_start, bsz, C, blk_file, file_start, cnt, surv, recs, ie); count_launches(1);
+  k_index_sizes<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(blk_start, bsz, C, blk_file, file_start, cnt, surv, recs, ie); count_launches(1);
 }
 
 void launch_file_layout(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_start,
@@ -1363,8 +1363,9 @@ void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const u
   const uint32_t smem = ((kStgHead + 127) & ~127u) + 2 * S + I + 16;
   uint32_t per_sm = (227u * 1024u) / (smem + 1024u);
   per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+  if (tuning().encode_ctas_per_sm && tuning().encode_ctas_per_sm < per_sm) per_sm = tuning().encode_ctas_per_sm;
   cudaFuncSetAttribute(k_encode_stg, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  k_block_enc<<<grid_for(cap, 256), 256, 0, st>>>(blk_start, cnt, blk_file, files, C, bsz, out_cap, bd);
+  k_block_enc<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(blk_start, cnt, blk_file, files, C, bsz, out_cap, bd);
   k_encode_stg<<<kSms * per_sm, kStgThreads, smem, st>>>(cnt, bd, lcp, ed, fmt, out, out_cap, done, big, errs, S, I);
   count_launches(2);
 }
@@ -1392,7 +1393,7 @@ void launch_encode_big(const uint32_t* blk_start, Counts* cnt, uint32_t cap, con
 void launch_bloom(const EncDesc* ed, const Counts* cnt, uint32_t cap, const FileDesc* files, Fmt fmt,
                   uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st) {
   if (!cap) return;
-  k_bloom<<<grid_for(cap, 256), 256, 0, st>>>(ed, cnt, files, fmt, bitmap, out_cap, bm_cap);
+  k_bloom<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(ed, cnt, files, fmt, bitmap, out_cap, bm_cap);
   count_launches(1);
 }
 

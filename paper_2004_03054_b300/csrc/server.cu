@@ -55,6 +55,7 @@ struct Ticket {
 
 struct luda_server {
   luda_server_config cfg{};
+  luda_tuning tuning{};               // copy of cfg.opts.tuning (cfg.opts.tuning points here)
   int device = 0;
   std::vector<cudaStream_t> streams;
   std::vector<std::thread> slots;
@@ -170,6 +171,11 @@ luda_status luda_server_create(const luda_server_config* cfg, luda_server** serv
   }
   auto s = std::make_unique<luda_server>();
   s->cfg = *cfg;
+  if (cfg->opts.tuning) {
+    if (!luda::tuning_valid(cfg->opts.tuning)) return LUDA_ERR_INVALID_ARG;
+    s->tuning = *cfg->opts.tuning;
+    s->cfg.opts.tuning = &s->tuning;
+  }
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     luda::set_error_detail("no usable CUDA device");
     return LUDA_ERR_CUDA;

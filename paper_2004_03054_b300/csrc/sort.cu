@@ -65,7 +65,6 @@ __global__ void k_sort_init(uint32_t* __restrict__ ord, MKey* __restrict__ okey,
 }
 
 constexpr int kMergeThreads = 128;
-constexpr int kMergeItems = kMergeTile / kMergeThreads;
 
 // Co-rank of output position d in the merge of A and B, found by the whole CTA: while the
 // candidate range is wider than the CTA, every thread tests one of kMergeThreads evenly
@@ -127,14 +126,17 @@ __device__ __forceinline__ uint32_t find_span(const MergeSpan* spans, uint32_t n
   return lo;
 }
 
-// One CTA per output tile of kMergeTile elements: co-rank both ends of the tile, stage
-// the tile's parts of A and B in shared memory, then each thread co-ranks its kMergeItems
-// outputs there and merges them.
+// One CTA per output tile of kTile elements: co-rank both ends of the tile, stage the
+// tile's parts of A and B in shared memory (keys first, 16-byte aligned, then the ids),
+// then each thread co-ranks its kTile / kMergeThreads outputs there and merges them.
+template <uint32_t kTile>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(const MergeSpan* __restrict__ spans, uint32_t n_spans,
                                                          uint32_t n_tiles, uint32_t* ord0, MKey* key0, uint32_t* ord1,
                                                          MKey* key1, Recs recs, const uint8_t* __restrict__ arena) {
-  __shared__ uint32_t s_ord[kMergeTile];
-  __shared__ MKey s_key[kMergeTile];
+  constexpr uint32_t kItems = kTile / kMergeThreads;
+  extern __shared__ uint4 s_merge[];
+  MKey* s_key = reinterpret_cast<MKey*>(s_merge);
+  uint32_t* s_ord = reinterpret_cast<uint32_t*>(s_key + kTile);
   for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const MergeSpan sp = spans[find_span(spans, n_spans, t)];
     const uint32_t* src_ord = sp.src ? ord1 : ord0;
@@ -142,8 +144,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const MergeSpan* __rest
     uint32_t* dst_ord = sp.src ? ord0 : ord1;
     MKey* dst_key = sp.src ? key0 : key1;
     const uint32_t total = sp.a_len + sp.b_len;
-    const uint32_t d0 = (t - sp.tile_first) * kMergeTile;
-    const uint32_t d1 = min(d0 + kMergeTile, total);
+    const uint32_t d0 = (t - sp.tile_first) * kTile;
+    const uint32_t d1 = min(d0 + kTile, total);
     const uint32_t* A = src_ord + sp.a_begin;
     const MKey* Ak = src_key + sp.a_begin;
     const uint32_t* B = A + sp.a_len;
@@ -158,11 +160,11 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const MergeSpan* __rest
       s_key[x] = Ak[src];
     }
     __syncthreads();
-    const uint32_t dd = threadIdx.x * kMergeItems;
+    const uint32_t dd = threadIdx.x * kItems;
     if (dd < na + nb) {
       const uint32_t ia = corank_smem(dd, s_ord, s_key, na, s_ord + na, s_key + na, nb, recs, arena);
       uint32_t a = ia, ib = dd - ia;
-      const uint32_t cnt = min(uint32_t(kMergeItems), na + nb - dd);
+      const uint32_t cnt = min(kItems, na + nb - dd);
       uint32_t out = sp.a_begin + d0 + dd;
       for (uint32_t k = 0; k < cnt; ++k, ++out) {
         bool take_a;
@@ -259,32 +261,44 @@ void launch_plan_sanitize(Recs recs, uint32_t n_rec, const JobDev* jobs, uint32_
 void launch_check_order(Recs recs, const uint8_t* arena, uint32_t n_rec, const DInput* in, DErr* errs,
                         cudaStream_t st) {
   if (n_rec < 2) return;
-  k_check_order<<<grid_for(n_rec, 256), 256, 0, st>>>(recs, arena, n_rec, in, errs); count_launches(1);
+  k_check_order<<<grid_for(n_rec, elem_threads()), elem_threads(), 0, st>>>(recs, arena, n_rec, in, errs); count_launches(1);
 }
 
 void launch_sort_init(uint32_t* ord, MKey* okey, Recs recs, const uint8_t* arena, uint32_t n, cudaStream_t st) {
   if (!n) return;
-  k_sort_init<<<grid_for(n, 256), 256, 0, st>>>(ord, okey, recs, arena, n); count_launches(1);
+  k_sort_init<<<grid_for(n, elem_threads()), elem_threads(), 0, st>>>(ord, okey, recs, arena, n); count_launches(1);
 }
 
-void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* ord0, MKey* key0,
-                       uint32_t* ord1, MKey* key1, Recs recs, const uint8_t* arena, cudaStream_t st) {
+template <uint32_t kTile>
+void merge_pass_t(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* ord0, MKey* key0,
+                  uint32_t* ord1, MKey* key1, Recs recs, const uint8_t* arena, cudaStream_t st) {
+  constexpr uint32_t smem = kTile * (sizeof(MKey) + sizeof(uint32_t));
+  if (smem > 48u * 1024u) cudaFuncSetAttribute(k_merge<kTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  k_merge<kTile><<<grid_for(n_tiles, 1, kSms * tuning().merge_ctas_per_sm), kMergeThreads, smem, st>>>(
+      spans, n_spans, n_tiles, ord0, key0, ord1, key1, recs, arena);
+}
+
+void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t tile, uint32_t* ord0,
+                       MKey* key0, uint32_t* ord1, MKey* key1, Recs recs, const uint8_t* arena, cudaStream_t st) {
   if (!n_tiles) return;
-  k_merge<<<grid_for(n_tiles, 1, kSms * 8), kMergeThreads, 0, st>>>(spans, n_spans, n_tiles, ord0, key0, ord1, key1,
-                                                                    recs, arena);
+  switch (tile) {
+    case 512: merge_pass_t<512>(spans, n_spans, n_tiles, ord0, key0, ord1, key1, recs, arena, st); break;
+    case 2048: merge_pass_t<2048>(spans, n_spans, n_tiles, ord0, key0, ord1, key1, recs, arena, st); break;
+    default: merge_pass_t<1024>(spans, n_spans, n_tiles, ord0, key0, ord1, key1, recs, arena, st); break;
+  }
   count_launches(1);
 }
 
 void launch_gc_flags(const uint32_t* ord, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, Recs recs,
                      const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st) {
   if (!n_rec) return;
-  k_gc_flags<<<grid_for(n_rec, 256), 256, 0, st>>>(ord, n_rec, jobs, n_jobs, recs, arena, keep, errs); count_launches(1);
+  k_gc_flags<<<grid_for(n_rec, elem_threads()), elem_threads(), 0, st>>>(ord, n_rec, jobs, n_jobs, recs, arena, keep, errs); count_launches(1);
 }
 
 void launch_gc_compact(const uint32_t* ord, const uint32_t* keep, const uint32_t* pos, uint32_t n_rec,
                        uint32_t* surv, cudaStream_t st) {
   if (!n_rec) return;
-  k_gc_compact<<<grid_for(n_rec, 256), 256, 0, st>>>(ord, keep, pos, n_rec, surv); count_launches(1);
+  k_gc_compact<<<grid_for(n_rec, elem_threads()), elem_threads(), 0, st>>>(ord, keep, pos, n_rec, surv); count_launches(1);
 }
 
 void launch_job_surv(JobDev* jobs, uint32_t n_jobs, const uint32_t* pos, uint32_t n_rec, Counts* cnt,

@@ -32,11 +32,39 @@ class Input(C.Structure):
     _fields_ = [("data", C.c_void_p), ("size", C.c_uint64), ("level", C.c_int32), ("file_number", C.c_uint64)]
 
 
+class Tuning(C.Structure):
+    """luda_tuning: launch shapes (0 = default); they never change the output bytes."""
+    _fields_ = [("merge_tile", C.c_uint32), ("merge_ctas_per_sm", C.c_uint32), ("decode_warps", C.c_uint32),
+                ("walk_threads", C.c_uint32), ("encode_ctas_per_sm", C.c_uint32), ("elem_threads", C.c_uint32),
+                ("reserved", C.c_uint32 * 2)]
+    KNOBS = ("merge_tile", "merge_ctas_per_sm", "decode_warps", "walk_threads", "encode_ctas_per_sm",
+             "elem_threads")
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k in self.KNOBS}
+
+    @classmethod
+    def of(cls, d: dict) -> "Tuning":
+        t = cls()
+        for k, v in d.items():
+            setattr(t, k, int(v))
+        return t
+
+
 class Options(C.Structure):
     _fields_ = [("block_size", C.c_uint32), ("restart_interval", C.c_uint32), ("bloom_bits_per_key", C.c_uint32),
                 ("target_file_size", C.c_uint64), ("bottommost", C.c_int32), ("flags", C.c_uint32),
                 ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_ctx", C.c_void_p),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("tuning", C.POINTER(Tuning))]
+
+    def with_tuning(self, t: "Tuning | dict | None") -> "Options":
+        """A copy of these options with launch shapes t (None: defaults); the copy keeps t alive."""
+        o = Options.from_buffer_copy(self)
+        if isinstance(t, dict):
+            t = Tuning.of(t)
+        o._tuning_ref = t
+        o.tuning = C.pointer(t) if t is not None else None
+        return o
 
 
 class Table(C.Structure):
@@ -120,6 +148,13 @@ def lib():
         L.luda_plan_outputs.argtypes = [C.c_void_p, C.POINTER(Outputs)]
         L.luda_plan_destroy.argtypes = [C.c_void_p]
         L.luda_plan_destroy.restype = None
+        L.luda_tuning_default.argtypes = [C.POINTER(Tuning)]
+        L.luda_tuning_default.restype = None
+        L.luda_tuning_check.argtypes = [C.POINTER(Tuning)]
+        L.luda_tuning_check.restype = st
+        L.luda_autotune.argtypes = [C.POINTER(Job), C.c_uint32, C.POINTER(Options), C.POINTER(Tuning), C.c_uint32,
+                                    C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_uint32)]
+        L.luda_autotune.restype = st
         L.luda_server_create.restype = st
         L.luda_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]
         L.luda_server_submit.restype = st
@@ -139,13 +174,13 @@ def lib():
 
 
 def options(block_size=4096, restart_interval=16, bloom_bits_per_key=10, target_file_size=2 << 20,
-            bottommost=False, flags=0, stream=None) -> Options:
+            bottommost=False, flags=0, stream=None, tuning=None) -> Options:
     o = Options()
     lib().luda_options_default(C.byref(o))
     o.block_size, o.restart_interval, o.bloom_bits_per_key = block_size, restart_interval, bloom_bits_per_key
     o.target_file_size, o.bottommost, o.flags = target_file_size, int(bool(bottommost)), flags
     o.stream = stream
-    return o
+    return o.with_tuning(tuning) if tuning is not None else o
 
 
 def job_options(job, **kw) -> Options:
