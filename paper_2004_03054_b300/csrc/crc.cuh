@@ -28,14 +28,12 @@
 namespace luda {
 
 // Shift tables: index j in [0, 32) shifts by 16 << j bytes; index 32 + (p - 1) for p in
-// [1, 16) applies the inverse shift by p bytes; index kShiftSkip shifts by 31 * kLaneSpan
-// bytes. Each
+// [1, 16) applies the inverse shift by p bytes; index kShift992 shifts by 992 bytes. Each
 // table: 4 x 256 words.
 constexpr int kShiftPow = 32;
 constexpr int kShiftInv = 15;
-constexpr uint32_t kLaneSpan = 32;                  // bytes a lane folds per round (warp_crc32c_u32)
-constexpr int kShiftSkip = kShiftPow + kShiftInv;  // "feed 31 * kLaneSpan zero bytes": past the other lanes
-constexpr int kShiftTables = kShiftSkip + 1;
+constexpr int kShift992 = kShiftPow + kShiftInv;  // "feed 992 zero bytes" (32-byte lane spans)
+constexpr int kShiftTables = kShift992 + 1;
 
 struct CrcTabs {
   const uint32_t* slice;  // 4 x 256: slice[k*256 + v] = register after k+1 byte steps of v
@@ -140,44 +138,32 @@ static __device__ __noinline__ uint32_t cta_crc32c(const uint8_t* p, uint64_t n,
 }
 
 // ---- lane-replicated tables: conflict-free lookups ------------------------------------------
-// Every lane has its own copy of the four slicing tables, in its own bank. The copies sit
-// in a 128 KiB region that starts at a 64 KiB-aligned shared-window address A: the word
-// for slice s, byte value v and lane l is at
-//   A + (s >> 1) * 65536 + v * 256 + (s & 1) * 128 + l * 4.
-// Bits 8..15 of that address are exactly v, so one byte permute builds it from the data
-// register (its byte k goes to bits 8..15) and a per-lane register L = A | l * 4 (bytes
-// 0, 2, 3 kept), and the slice's offset is the ld.shared immediate: a lookup is one PRMT
-// and one LDS. A kernel reserves kCrcSmem bytes of dynamic shared memory, enough to find
-// the aligned region wherever its dynamic shared memory starts, plus the four byte tables
-// of the skip shift (4 KiB, unreplicated).
-constexpr uint32_t kRepBytes = 2u * 65536u;
-constexpr uint32_t kCrcSmem = 65536u + kRepBytes + 4096u;
+// Word (t * 256 + v) * 32 + lane holds slice[t][v], so lane l always reads bank l.
+// Word (t * 256 + v) * 32 + lane holds slice[t][v]: lane l always reads bank l.
+constexpr uint32_t kRepWords = 4 * 256 * 32;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Fills the tables (whole CTA, blockDim a multiple of 32; the caller synchronises) and
-// returns this lane's L register in *tl and the address of the skip shift's tables in
-// *tz. dyn = start of the kernel's dynamic shared memory (kCrcSmem bytes).
-__device__ __forceinline__ void crc_smem_setup(uint8_t* dyn, const CrcTabs tabs, uint32_t* tl, uint32_t* tz) {
-  const uint32_t x = smem_addr(dyn);
-  const uint32_t a = (x + 0xFFFFu) & ~0xFFFFu;
-  uint32_t* rep = reinterpret_cast<uint32_t*>(dyn + (a - x));
-  uint32_t* z = a - x >= 4096u ? reinterpret_cast<uint32_t*>(dyn) : rep + kRepBytes / 4;
-  // one global load per table word, then 32 shared stores of it (lane copies in rotated
-  // order, so that the 32 threads of a warp, holding consecutive v, hit 32 banks)
+// ---- 32-byte lane spans --------------------------------------------------------------------
+// Tables in shared memory, addressed with 32-bit shared-window addresses so that every
+// lookup is one byte extract, one address multiply-add and one ld.shared with the table's
+// offset as an immediate. tl = address of this lane's column of the lane-replicated slicing
+// tables (word (t * 256 + v) * 32 + lane holds slice[t][v]); tz = address of Z_992's four
+// byte tables.
+// One global load per table word, then its 32 lane copies stored in rotated order, so that
+// the 32 threads of a warp (consecutive words) hit 32 different banks. blockDim must be a
+// multiple of 32.
+__device__ __forceinline__ void load_rep_tables992(uint32_t* sTr, uint32_t* sZ, const CrcTabs tabs) {
   const uint32_t rot = threadIdx.x & 31u;
   for (uint32_t w = threadIdx.x; w < 1024; w += blockDim.x) {
     const uint32_t val = __ldg(tabs.slice + w);
-    z[w] = __ldg(tabs.shift + size_t(kShiftSkip) * 1024 + w);
-    const uint32_t sl = w >> 8, v = w & 255u;
-    uint32_t* row = rep + (sl >> 1) * 16384u + v * 64u + (sl & 1u) * 32u;
+    sZ[w] = __ldg(tabs.shift + size_t(kShift992) * 1024 + w);
+    uint32_t* row = sTr + w * 32u;
 #pragma unroll 8
     for (uint32_t l = 0; l < 32; ++l) row[(l + rot) & 31u] = val;
   }
-  *tl = a | ((threadIdx.x & 31u) << 2);
-  *tz = smem_addr(z);
 }
 
 template <uint32_t kOff>
@@ -187,19 +173,16 @@ __device__ __forceinline__ uint32_t lds_off(uint32_t addr) {
   return v;
 }
 
-// Slice s of byte k of c, for this lane (L = tl).
-template <uint32_t kSlice, uint32_t kByte>
-__device__ __forceinline__ uint32_t rep_lookup(uint32_t c, uint32_t tl) {
-  return lds_off<(kSlice >> 1) * 65536u + (kSlice & 1u) * 128u>(__byte_perm(c, tl, 0x7604u | (kByte << 4)));
-}
-
 __device__ __forceinline__ uint32_t crc_word_rep(uint32_t c, uint32_t w, uint32_t tl) {
   c ^= w;
-  return rep_lookup<3, 0>(c, tl) ^ rep_lookup<2, 1>(c, tl) ^ rep_lookup<1, 2>(c, tl) ^ rep_lookup<0, 3>(c, tl);
+  const uint32_t t3 = lds_off<3u * 32768u>(tl + __byte_perm(c, 0, 0x4440) * 128u);
+  const uint32_t t2 = lds_off<2u * 32768u>(tl + __byte_perm(c, 0, 0x4441) * 128u);
+  const uint32_t t1 = lds_off<1u * 32768u>(tl + __byte_perm(c, 0, 0x4442) * 128u);
+  const uint32_t t0 = lds_off<0u>(tl + __byte_perm(c, 0, 0x4443) * 128u);
+  return t3 ^ t2 ^ t1 ^ t0;
 }
 
-// The register v moved past the other 31 lanes' spans (31 * kLaneSpan zero bytes).
-__device__ __forceinline__ uint32_t crc_zskip(uint32_t v, uint32_t tz) {
+__device__ __forceinline__ uint32_t crc_z992(uint32_t v, uint32_t tz) {
   return lds_off<0u>(tz + __byte_perm(v, 0, 0x4440) * 4u) ^ lds_off<1024u>(tz + __byte_perm(v, 0, 0x4441) * 4u) ^
          lds_off<2048u>(tz + __byte_perm(v, 0, 0x4442) * 4u) ^ lds_off<3072u>(tz + __byte_perm(v, 0, 0x4443) * 4u);
 }
@@ -237,11 +220,11 @@ __device__ __forceinline__ uint32_t crc_fix_word32(uint32_t w, uint32_t q, uint3
 // its end; in round r lane l folds unit U - 32 * (rounds - r) + l, so each round reads 1 KiB
 // contiguously, and the next round's two 16-byte loads are issued before this round's
 // arithmetic. Between rounds a lane register moves past the other lanes' 992 bytes with
-// the skip shift; the lanes are joined with Z_{32 * 2^k} (k < 5), the trailing pad is
-// removed with the inverse shift. Only 16-byte words inside [p & ~15, end rounded up] are
-// loaded. kInit = false starts from a zero register instead of 0xFFFFFFFF and kFinal =
-// false skips the final complement (for chunks of one message: the first chunk carries the
-// init, the register of the whole message is complemented once after joining).
+// Z_992; the lanes are joined with Z_{32 * 2^k} (k < 5), the trailing pad is removed with
+// the inverse shift. Only 16-byte words inside [p & ~15, end rounded up] are loaded.
+// kInit = false starts from a zero register instead of 0xFFFFFFFF and kFinal = false skips
+// the final complement (for chunks of one message: the first chunk carries the init, the
+// register of the whole message is complemented once after joining).
 template <bool kInit = true, bool kFinal = true>
 static __device__ __noinline__ uint32_t warp_crc32c_u32(const uint8_t* p, uint64_t n, uint32_t tl, uint32_t tz,
                                                         const CrcTabs tabs) {
@@ -249,7 +232,7 @@ static __device__ __noinline__ uint32_t warp_crc32c_u32(const uint8_t* p, uint64
   if (n < 16) {
     uint32_t c = kInit ? 0xFFFFFFFFu : 0u;
     if (lane == 0)
-      for (uint64_t i = 0; i < n; ++i) c = rep_lookup<0, 0>(c ^ p[i], tl) ^ (c >> 8);
+      for (uint64_t i = 0; i < n; ++i) c = lds_off<0u>(tl + ((c ^ p[i]) & 0xFFu) * 128u) ^ (c >> 8);
     c = __shfl_sync(0xFFFFFFFFu, c, 0);
     return kFinal ? c ^ 0xFFFFFFFFu : c;
   }
@@ -289,7 +272,7 @@ static __device__ __noinline__ uint32_t warp_crc32c_u32(const uint8_t* p, uint64
         y0.z = crc_fix_word32<kInit>(y0.z, q + 24, lo, hi);
         y0.w = crc_fix_word32<kInit>(y0.w, q + 28, lo, hi);
       }
-      acc = crc_unit32(crc_zskip(acc, tz), x0, y0, tl);
+      acc = crc_unit32(crc_z992(acc, tz), x0, y0, tl);
     }
     x0 = x1;
     y0 = y1;

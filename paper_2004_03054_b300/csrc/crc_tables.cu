@@ -107,7 +107,7 @@ bool make_crc_tables(uint32_t* slice, uint32_t* shift) {
     to_tables(z, shift + size_t(j) * 1024);
     z = mul(z, z);
   }
-  to_tables(power(z1, 31 * kLaneSpan), shift + size_t(kShiftSkip) * 1024);
+  to_tables(power(z1, 992), shift + size_t(kShift992) * 1024);
   Mat inv;
   if (!invert(z1, &inv)) return false;
   Mat zp = inv;

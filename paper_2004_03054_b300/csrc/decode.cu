@@ -148,16 +148,17 @@ __global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs
 // 16-byte window (two aligned 8-byte loads; tables are readable up to 16 bytes past any
 // entry, since at least the trailer and footer follow every data block).
 constexpr int kVerifyWarps = 32;
+constexpr uint32_t kVerifySmem = (kRepWords + 1024) * 4;
 
 __global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_block_verify(const BlockDesc* __restrict__ blocks,
                                                                        uint32_t n_blocks,
                                                                        const DInput* __restrict__ in,
                                                                        const DErr* errs, DErr* verr, CrcTabs tabs) {
-  extern __shared__ __align__(16) uint8_t s_ver[];
-  uint32_t tl, tz;
-  crc_smem_setup(s_ver, tabs, &tl, &tz);
+  extern __shared__ uint32_t s_ver[];
+  load_rep_tables992(s_ver, s_ver + kRepWords, tabs);
   __syncthreads();
   const uint32_t lane = lane_id();
+  const uint32_t tl = smem_addr(s_ver) + lane * 4u, tz = smem_addr(s_ver + kRepWords);
   const uint64_t warps = gstride() / 32;
   for (uint64_t g = gtid() / 32; g < n_blocks; g += warps) {
     const BlockDesc b = blocks[g];
@@ -567,8 +568,8 @@ void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* i
 void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const DErr* errs, DErr* verr,
                          CrcTabs tabs, cudaStream_t st) {
   if (!n_blocks) return;
-  cudaFuncSetAttribute(k_block_verify, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCrcSmem));
-  k_block_verify<<<grid_for(n_blocks, kVerifyWarps, kSms), kVerifyWarps * 32, kCrcSmem, st>>>(blocks, n_blocks,
+  cudaFuncSetAttribute(k_block_verify, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kVerifySmem));
+  k_block_verify<<<grid_for(n_blocks, kVerifyWarps, kSms), kVerifyWarps * 32, kVerifySmem, st>>>(blocks, n_blocks,
                                                                                                  in, errs, verr, tabs);
   count_launches(1);
 }

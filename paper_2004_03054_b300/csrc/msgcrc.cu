@@ -22,6 +22,7 @@ namespace {
 
 constexpr int kMsgWarps = 32;
 constexpr uint32_t kMsgMaxChunks = 64;
+constexpr uint32_t kMsgSmem = (kRepWords + 1024) * 4;
 
 __device__ __forceinline__ uint64_t msg_chunk(uint64_t n) {
   const uint64_t c = (n + kMsgMaxChunks - 1) / kMsgMaxChunks;
@@ -32,11 +33,11 @@ __device__ __forceinline__ uint64_t msg_chunk(uint64_t n) {
 __global__ void __launch_bounds__(kMsgWarps * 32, 1) k_msg_chunks(CrcMsg* __restrict__ msgs,
                                                                   const uint32_t* __restrict__ count, uint32_t mult,
                                                                   CrcTabs tabs) {
-  extern __shared__ __align__(16) uint8_t s_msg[];
-  uint32_t tl, tz;
-  crc_smem_setup(s_msg, tabs, &tl, &tz);
+  extern __shared__ uint32_t s_msg[];
+  load_rep_tables992(s_msg, s_msg + kRepWords, tabs);
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t tl = smem_addr(s_msg) + lane * 4u, tz = smem_addr(s_msg + kRepWords);
   const uint64_t n_slots = uint64_t((count ? *count : 1u) * mult) * kMsgMaxChunks;
   const uint64_t warps = gstride() / 32;
   for (uint64_t w = gtid() / 32; w < n_slots; w += warps) {
@@ -73,8 +74,8 @@ __global__ void k_msg_finish(const CrcMsg* __restrict__ msgs, const uint32_t* __
 void launch_msg_crc(CrcMsg* msgs, const uint32_t* count, uint32_t mult, uint32_t max_msgs, DErr* errs, CrcTabs tabs,
                     cudaStream_t st) {
   if (!max_msgs) return;
-  cudaFuncSetAttribute(k_msg_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCrcSmem));
-  k_msg_chunks<<<kSms, kMsgWarps * 32, kCrcSmem, st>>>(msgs, count, mult, tabs);
+  cudaFuncSetAttribute(k_msg_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMsgSmem));
+  k_msg_chunks<<<kSms, kMsgWarps * 32, kMsgSmem, st>>>(msgs, count, mult, tabs);
   k_msg_finish<<<grid_for(max_msgs, 128, kSms), 128, 0, st>>>(msgs, count, mult, errs, tabs);
   count_launches(2);
 }

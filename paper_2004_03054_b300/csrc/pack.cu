@@ -957,6 +957,7 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(Counts* __restrict__
 // Masked CRC-32C trailers of the blocks k_encode wrote (done[b] = 1): one warp per block,
 // the block re-read from global memory (mostly L2).
 constexpr int kCrcWarps = 32;
+constexpr uint32_t kCrcSmem = (kRepWords + 1024) * 4;
 
 __global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(const Counts* __restrict__ cnt,
                                                                   const uint32_t* __restrict__ blk_file,
@@ -965,11 +966,11 @@ __global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(const Counts* _
                                                                   const uint64_t* __restrict__ bsz,
                                                                   uint8_t* __restrict__ out, uint64_t out_cap,
                                                                   const uint8_t* __restrict__ done, CrcTabs tabs) {
-  extern __shared__ __align__(16) uint8_t s_crc[];
-  uint32_t tl, tz;
-  crc_smem_setup(s_crc, tabs, &tl, &tz);
+  extern __shared__ uint32_t s_crc[];
+  load_rep_tables992(s_crc, s_crc + kRepWords, tabs);
   __syncthreads();
   const uint32_t lane = lane_id();
+  const uint32_t tl = smem_addr(s_crc) + lane * 4u, tz = smem_addr(s_crc + kRepWords);
   const uint32_t nb = cnt->nb;
   const uint64_t warps = gstride() / 32;
   for (uint64_t b = gtid() / 32; b < nb; b += warps) {
