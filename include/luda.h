@@ -84,7 +84,9 @@ typedef struct {
                                    as fit) */
   uint32_t elem_threads;        /* threads per CTA of the per-record and per-block kernels of the drop rule,
                                    cut and layout stages: 64..1024, multiple of 32 (default 256) */
-  uint32_t reserved[2];         /* must be 0 */
+  uint32_t crc_ctas;            /* CTAs (one per SM) of the data-block checksum kernels, which run beside the
+                                   other stages on a second stream: 1..148 (default 100) */
+  uint32_t reserved;            /* must be 0 */
 } luda_tuning;
 
 /* Fills the defaults (all fields 0). */

@@ -2,8 +2,9 @@
 
 A tuning decides how the pipeline's kernels split their work over CTAs: records per merge
 tile, merge CTAs per SM, decoder warps per CTA, block-walk CTA size, staged-encoder CTAs per
-SM and the CTA size of the per-record kernels. No tuning changes an output byte, so the
-tuner is free to pick whichever is fastest for a batch.
+SM, the CTA size of the per-record kernels and the SMs given to the checksum kernels (which
+run beside the other stages). No tuning changes an output byte, so the tuner is free to
+pick whichever is fastest for a batch.
 
 The search is coordinate descent over a small grid (one knob at a time, the others held at
 the best values so far): every candidate of one knob is timed by the library itself
@@ -33,10 +34,11 @@ SPACE: dict[str, tuple[int, ...]] = {
     "walk_threads": (64, 128, 256),
     "encode_ctas_per_sm": (1, 2, 0),
     "elem_threads": (128, 256, 512),
+    "crc_ctas": (148, 120, 100, 74),
 }
 # The library's defaults, resolved.
 DEFAULT = {"merge_tile": 1024, "merge_ctas_per_sm": 8, "decode_warps": 8, "walk_threads": 256,
-           "encode_ctas_per_sm": 0, "elem_threads": 256}
+           "encode_ctas_per_sm": 0, "elem_threads": 256, "crc_ctas": 100}
 
 
 @dataclass

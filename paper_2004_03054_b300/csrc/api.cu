@@ -63,7 +63,8 @@ bool luda::tuning_valid(const luda_tuning* t) {
   else if (t->encode_ctas_per_sm > 8) bad = "encode_ctas_per_sm";
   else if (t->elem_threads && (t->elem_threads < 64 || t->elem_threads > 1024 || t->elem_threads % 32))
     bad = "elem_threads";
-  else if (t->reserved[0] || t->reserved[1]) bad = "reserved";
+  else if (t->crc_ctas > kSms) bad = "crc_ctas";
+  else if (t->reserved) bad = "reserved";
   if (bad) set_detail("invalid tuning: %s", bad);
   return bad == nullptr;
 }
@@ -76,6 +77,7 @@ luda::TuningScope::TuningScope(const luda_tuning* t) : saved_(t_tuning) {
   if (t->walk_threads) t_tuning.walk_threads = t->walk_threads;
   if (t->encode_ctas_per_sm) t_tuning.encode_ctas_per_sm = t->encode_ctas_per_sm;
   if (t->elem_threads) t_tuning.elem_threads = t->elem_threads;
+  if (t->crc_ctas) t_tuning.crc_ctas = t->crc_ctas;
 }
 
 luda::TuningScope::~TuningScope() { t_tuning = saved_; }

@@ -569,8 +569,8 @@ void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInpu
                          CrcTabs tabs, cudaStream_t st) {
   if (!n_blocks) return;
   cudaFuncSetAttribute(k_block_verify, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kVerifySmem));
-  k_block_verify<<<grid_for(n_blocks, kVerifyWarps, kSms), kVerifyWarps * 32, kVerifySmem, st>>>(blocks, n_blocks,
-                                                                                                 in, errs, verr, tabs);
+  const unsigned g = grid_for(n_blocks, kVerifyWarps, tuning().crc_ctas);
+  k_block_verify<<<g, kVerifyWarps * 32, kVerifySmem, st>>>(blocks, n_blocks, in, errs, verr, tabs);
   count_launches(1);
 }
 

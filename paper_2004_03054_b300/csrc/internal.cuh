@@ -154,6 +154,7 @@ struct Tuning {
   uint32_t walk_threads = 256;
   uint32_t encode_ctas_per_sm = 0;  // 0: as many as shared memory allows
   uint32_t elem_threads = 256;
+  uint32_t crc_ctas = 100;  // about two thirds of the SMs: the other stages run beside the checksums
 };
 const Tuning& tuning();
 // Range check of a luda_tuning (0 = default); sets the error detail on failure.

@@ -1375,7 +1375,7 @@ void launch_block_crc(const Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                       CrcTabs tabs, cudaStream_t st) {
   if (!cap) return;
   cudaFuncSetAttribute(k_block_crc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCrcSmem));
-  k_block_crc<<<kSms, kCrcWarps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done, tabs);
+  k_block_crc<<<tuning().crc_ctas, kCrcWarps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done, tabs);
   count_launches(1);
 }
 
