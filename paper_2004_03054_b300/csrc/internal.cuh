@@ -104,7 +104,7 @@ struct CrcMsg {
 
 // Merge key of a record: the first 32 bytes of its user key as four big-endian words
 // (zero-padded).
-struct MKey {
+struct __align__(16) MKey {
   uint64_t h[4];
 };
 

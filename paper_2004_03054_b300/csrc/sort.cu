@@ -154,10 +154,27 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const MergeSpan* __rest
     const uint32_t i1 = d1 == total ? sp.a_len : corank_cta(d1, A, Ak, sp.a_len, B, Bk, sp.b_len, recs, arena);
     const uint32_t j0 = d0 - i0, j1 = d1 - i1;
     const uint32_t na = i1 - i0, nb = j1 - j0;
-    for (uint32_t x = threadIdx.x; x < na + nb; x += blockDim.x) {
-      const uint32_t src = x < na ? i0 + x : sp.a_len + j0 + (x - na);
-      s_ord[x] = A[src];
-      s_key[x] = Ak[src];
+    {
+      // all of a thread's loads first, then the shared stores (one memory latency per tile)
+      uint32_t ro[kItems];
+      MKey rk[kItems];
+#pragma unroll
+      for (uint32_t k = 0; k < kItems; ++k) {
+        const uint32_t x = threadIdx.x + k * kMergeThreads;
+        if (x < na + nb) {
+          const uint32_t src = x < na ? i0 + x : sp.a_len + j0 + (x - na);
+          ro[k] = A[src];
+          rk[k] = Ak[src];
+        }
+      }
+#pragma unroll
+      for (uint32_t k = 0; k < kItems; ++k) {
+        const uint32_t x = threadIdx.x + k * kMergeThreads;
+        if (x < na + nb) {
+          s_ord[x] = ro[k];
+          s_key[x] = rk[k];
+        }
+      }
     }
     __syncthreads();
     const uint32_t dd = threadIdx.x * kItems;
