@@ -108,6 +108,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) of one k_encode_stg launch on the full-size large job, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass), and the SHA-256 of
+# csrc/pack.cu at the time: once the encoder's source changes the number no longer
+# describes it and the bench reports null.
+_ENCODE_TRAFFIC = (2042097408, "09a8da99d185c93f285206b2ac0dfc8049a1961a38aa937cfe640c2d8d6752ac")
+
+
+def _recorded_traffic(scale):
+    import hashlib
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2004_03054_b300", "csrc", "pack.cu")
+    try:
+        digest = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return _ENCODE_TRAFFIC[0] if digest == _ENCODE_TRAFFIC[1] and scale == 1.0 else None
+
+
 # ---- our arm ------------------------------------------------------------------------------
 def run_ours(args, ws, rank, local):
     import torch
@@ -183,17 +200,21 @@ def run_ours(args, ws, rank, local):
         ms = float(t.item())
     value = ws * in_bytes / MiB / (ms / 1e3)
 
-    # dominant kernel: block scan [1] (CRC verify and walk of every input block) vs encode [5]
+    # dominant kernel: the encoder [5], the largest share of the job's kernel time and on the
+    # critical path; the input checksum kernel [1] runs on a second stream on part of the
+    # SMs beside the later stages, so its duration there is not its own speed (reported beside)
     peak, peak_kind = _peaks()
     avg = [statistics.mean(s[i] for s in stages) for i in range(8)]
-    cand = {1: "block scan (k_block_verify + k_block_walk)", 5: "k_encode_stg"}
-    dom = max(cand, key=lambda i: avg[i])
+    dom = 5
     dom_bytes = sbytes[-1][dom]
     achieved = dom_bytes / (avg[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": cand[dom], "achieved": round(achieved, 1), "peak": peak,
+    roofline = {"bound": "hbm", "kernel": "k_encode_stg", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
                 "bytes_per_launch": dom_bytes, "ms_per_launch": round(avg[dom], 4),
-                "traffic": args.traffic}
+                "traffic": args.traffic if args.traffic is not None else _recorded_traffic(args.scale),
+                "input_checksums": {"kernel": "k_block_verify (second stream, beside decode, sort and cut)",
+                                    "bytes_per_launch": sbytes[-1][1], "ms_per_launch": round(avg[1], 4),
+                                    "achieved": round(sbytes[-1][1] / (avg[1] / 1e3) / 1e9, 1)}}
     path_gbs = (in_bytes + out_bytes) / (ms / 1e3) / 1e9
     stage_names = ["sizing", "block_scan", "decode", "sort", "gc_cut_layout", "encode", "meta", "device_span"]
 
@@ -547,7 +568,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--batch-warmup", type=int, default=3)
     ap.add_argument("--traffic", type=float, default=None,
-                    help="dram bytes per launch of the dominant kernel from an ncu capture (reported as is)")
+                    help="dram bytes per launch of the dominant kernel from an ncu capture (default: the "
+                         "recorded capture while the encoder's source is unchanged)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

@@ -137,8 +137,8 @@ typedef struct {
   double ms_h2d, ms_device, ms_d2h;
   /* With LUDA_F_TRACE, CUDA-event times on the call's stream (ms) and algorithmic bytes:
    *  [0] sizing (footers, index, block scan, prefix sums; includes host round trips)
-   *  [1] block-scan kernel alone: CRC-32C verify + structure of every input data block;
-   *      bytes = input data blocks with trailers (read once)
+   *  [1] input checksum kernel alone (CRC-32C of every input data block; it runs on a
+   *      second stream beside the later stages); bytes = input data blocks with trailers
    *  [2] decode kernel alone      [3] order check + merge sort
    *  [4] drop rule, entry sizes, block and file cut, layout
    *  [5] encode kernel alone (block images without their CRC): bytes = output data

@@ -963,7 +963,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   if (ms_d2h) *ms_d2h = d2h;
   if (tr.on) {
     stage_ms[0] = tr.span(0, 3);
-    stage_ms[1] = tr.span(11, 12) + tr.span(1, 2);  // checksum kernel (side stream) + walk
+    stage_ms[1] = tr.span(11, 12);  // input checksum kernel (side stream, beside the later stages)
     stage_ms[2] = tr.span(4, 5);
     stage_ms[3] = tr.span(5, 6);
     stage_ms[4] = tr.span(6, 7);
