@@ -397,7 +397,7 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   trace_mark(tr, 8, st);
   // data block trailers on the side stream (joined by the caller through event slot 3)
   CK(fork_join(side, 2, st, side->s));
-  launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, side->s);
+  launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, false, side->s);
   CK(cudaEventRecord(side->ev[3], side->s));
   launch_encode_big(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
                     fmt, out, out_cap, b.big, tabs, st);
@@ -408,6 +408,8 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   launch_key_lens(b.meta, cnt, cap, b.klens, st);
   CK((exclusive_scan<uint64_t, uint64_t>(b.klens, b.koff, cap, &cnt->nf, b.scan_tmp, st)));
   launch_key_gather(b.meta, cnt, cap, b.koff, b.files, b.surv, recs, arena, b.keybuf, st);
+  // the SMs the trailer kernel left join it for the blocks still to do
+  launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, true, st);
   CK(cudaGetLastError());
   return LUDA_OK;
 }
@@ -784,7 +786,8 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   if ((rc = get_side(&side))) return rc;
   CK(fork_join(side, 0, st, side->s));
   tr.mark(11, side->s);
-  launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, side->s);
+  launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, false,
+                      side->s);
   tr.mark(12, side->s);
   CK(cudaEventRecord(side->ev[1], side->s));
   tr.mark(1, st);
@@ -914,6 +917,8 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
   launch_gc_compact(src_o, d_keep, d_pos, n_rec, pb.surv, st);
   launch_job_surv(d_jobs, n_jobs, d_pos, n_rec, d_cnt, st);
+  // the SMs the input checksum kernel left join it for the blocks still to do
+  launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, true, st);
   CK(cudaGetLastError());
   if ((rc = run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap, tabs, st,
                      side, tr.on ? &tr : nullptr)))
@@ -1412,7 +1417,8 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     launch_plan_checks(d_in, N, d_plan_nblk, d_errs, st);
     launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
     CK(fork_join(side, 0, st, side->s));
-    launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, side->s);
+    launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, false,
+                      side->s);
     CK(cudaEventRecord(side->ev[1], side->s));
     launch_block_walk(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, st);
     launch_plan_check_recs(d_blocks, NB, d_nrec, d_kbytes, d_plan_nrec, d_plan_kbytes, d_in, d_errs, st);
@@ -1431,6 +1437,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
     launch_gc_compact(src_o, d_keep, d_pos, n_rec, pb.surv, st);
     launch_job_surv(d_jobs, n_jobs, d_pos, n_rec, d_cnt, st);
+    launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, true, st);
     luda_status prc = run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap,
                                tabs, st, side);
     if (prc) return prc;

@@ -153,14 +153,22 @@ constexpr uint32_t kVerifySmem = (kRepWords + 1024) * 4;
 __global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_block_verify(const BlockDesc* __restrict__ blocks,
                                                                        uint32_t n_blocks,
                                                                        const DInput* __restrict__ in,
-                                                                       const DErr* errs, DErr* verr, CrcTabs tabs) {
+                                                                       const DErr* errs, DErr* verr, CrcTabs tabs,
+                                                                       uint32_t* __restrict__ next) {
   extern __shared__ uint32_t s_ver[];
+  __shared__ uint32_t s_go;  // one decision for the whole CTA
+  if (threadIdx.x == 0) s_go = *(volatile uint32_t*)next < n_blocks;
+  __syncthreads();
+  if (!s_go) return;  // a helper launch with nothing left
   load_rep_tables992(s_ver, s_ver + kRepWords, tabs);
   __syncthreads();
   const uint32_t lane = lane_id();
   const uint32_t tl = smem_addr(s_ver) + lane * 4u, tz = smem_addr(s_ver + kRepWords);
-  const uint64_t warps = gstride() / 32;
-  for (uint64_t g = gtid() / 32; g < n_blocks; g += warps) {
+  for (;;) {
+    uint32_t g = 0;
+    if (lane == 0) g = atomicAdd(next, 1u);
+    g = __shfl_sync(0xFFFFFFFFu, g, 0);
+    if (g >= n_blocks) break;
     const BlockDesc b = blocks[g];
     DErr* e = verr + b.job;
     if (b.ptr == nullptr || *(volatile const int32_t*)&errs[b.job].code != 0 || *(volatile int32_t*)&e->code != 0)
@@ -566,11 +574,12 @@ void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* i
 }
 
 void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const DErr* errs, DErr* verr,
-                         CrcTabs tabs, cudaStream_t st) {
-  if (!n_blocks) return;
+                         CrcTabs tabs, uint32_t* next, bool helper, cudaStream_t st) {
+  const uint32_t ctas = helper ? kSms - tuning().crc_ctas : tuning().crc_ctas;
+  if (!n_blocks || !ctas) return;
   cudaFuncSetAttribute(k_block_verify, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kVerifySmem));
-  const unsigned g = grid_for(n_blocks, kVerifyWarps, tuning().crc_ctas);
-  k_block_verify<<<g, kVerifyWarps * 32, kVerifySmem, st>>>(blocks, n_blocks, in, errs, verr, tabs);
+  const unsigned g = grid_for(n_blocks, kVerifyWarps, ctas);
+  k_block_verify<<<g, kVerifyWarps * 32, kVerifySmem, st>>>(blocks, n_blocks, in, errs, verr, tabs, next);
   count_launches(1);
 }
 
@@ -584,7 +593,8 @@ void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput*
 
 void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
                        uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, CrcTabs tabs, cudaStream_t st) {
-  launch_block_verify(blocks, n_blocks, in, errs, errs, tabs, st);
+  launch_block_verify(blocks, n_blocks, in, errs, errs, tabs, &cnt->crc_next_in, false, st);
+  launch_block_verify(blocks, n_blocks, in, errs, errs, tabs, &cnt->crc_next_in, true, st);
   launch_block_walk(blocks, n_blocks, in, nrec, kbytes, errs, cnt, hdr_tab, st);
 }
 

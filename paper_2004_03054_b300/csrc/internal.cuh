@@ -87,6 +87,8 @@ struct Counts {
   uint32_t gap_blk;         // largest next(b) - b of the file cut
   uint32_t big_blocks;      // data blocks left to the CTA-per-block encoder
   uint32_t max_kv;          // largest internal key + value length in the inputs (block walk)
+  uint32_t crc_next_in;     // next input data block for the checksum kernels' warps
+  uint32_t crc_next_out;    // next output data block for the trailer kernels' warps
 };
 
 // One message for the multi-warp CRC (index and filter blocks): n bytes at p (contents and
@@ -192,8 +194,11 @@ void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput*
 // The two halves of launch_block_scan, for callers that run them on different streams:
 // checksum and type byte (errors into verr; blocks of jobs failed in errs or verr are
 // skipped), and the structure walk with entry counts.
+// Input checksums. Warps take blocks from the counter *next (zero before the first
+// launch); a helper launch (helper = true) on another stream adds the SMs the first launch
+// left (148 - crc_ctas) and ends at once if no block is left.
 void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const DErr* errs, DErr* verr,
-                         CrcTabs tabs, cudaStream_t st);
+                         CrcTabs tabs, uint32_t* next, bool helper, cudaStream_t st);
 void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
                        uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st);
 // After decode: every data block's index key equals its last internal key.
@@ -279,9 +284,10 @@ void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const u
                    const uint8_t* arena, Fmt fmt, uint32_t max_kv, uint8_t* out, uint64_t out_cap, uint8_t* done,
                    uint32_t* big, DErr* errs, CrcTabs tabs, cudaStream_t st);
 // CRC trailers of the staged encoder's blocks (done[b] = 1).
-void launch_block_crc(const Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,
+// Output block trailers; blocks taken from cnt->crc_next_out, helper launches as above.
+void launch_block_crc(Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,
                       const uint64_t* C, const uint64_t* bsz, uint8_t* out, uint64_t out_cap, const uint8_t* done,
-                      CrcTabs tabs, cudaStream_t st);
+                      CrcTabs tabs, bool helper, cudaStream_t st);
 // The blocks the staged encoder left, one CTA per block (bytes and CRC trailer).
 void launch_encode_big(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
                        const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,

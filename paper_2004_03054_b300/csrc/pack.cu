@@ -959,7 +959,7 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(Counts* __restrict__
 constexpr int kCrcWarps = 32;
 constexpr uint32_t kCrcSmem = (kRepWords + 1024) * 4;
 
-__global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(const Counts* __restrict__ cnt,
+__global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(Counts* __restrict__ cnt,
                                                                   const uint32_t* __restrict__ blk_file,
                                                                   const FileDesc* __restrict__ files,
                                                                   const uint64_t* __restrict__ C,
@@ -967,13 +967,21 @@ __global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(const Counts* _
                                                                   uint8_t* __restrict__ out, uint64_t out_cap,
                                                                   const uint8_t* __restrict__ done, CrcTabs tabs) {
   extern __shared__ uint32_t s_crc[];
+  __shared__ uint32_t s_go;  // one decision for the whole CTA
+  const uint32_t nb = cnt->nb;
+  uint32_t* next = &cnt->crc_next_out;
+  if (threadIdx.x == 0) s_go = *(volatile uint32_t*)next < nb;
+  __syncthreads();
+  if (!s_go) return;  // a helper launch with nothing left
   load_rep_tables992(s_crc, s_crc + kRepWords, tabs);
   __syncthreads();
   const uint32_t lane = lane_id();
   const uint32_t tl = smem_addr(s_crc) + lane * 4u, tz = smem_addr(s_crc + kRepWords);
-  const uint32_t nb = cnt->nb;
-  const uint64_t warps = gstride() / 32;
-  for (uint64_t b = gtid() / 32; b < nb; b += warps) {
+  for (;;) {
+    uint32_t b = 0;
+    if (lane == 0) b = atomicAdd(next, 1u);
+    b = __shfl_sync(0xFFFFFFFFu, b, 0);
+    if (b >= nb) break;
     if (!done[b]) continue;
     const FileDesc F = files[blk_file[b]];
     if (F.off + F.size > out_cap) continue;
@@ -1370,12 +1378,13 @@ void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const u
   count_launches(2);
 }
 
-void launch_block_crc(const Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,
+void launch_block_crc(Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,
                       const uint64_t* C, const uint64_t* bsz, uint8_t* out, uint64_t out_cap, const uint8_t* done,
-                      CrcTabs tabs, cudaStream_t st) {
-  if (!cap) return;
+                      CrcTabs tabs, bool helper, cudaStream_t st) {
+  const uint32_t ctas = helper ? kSms - tuning().crc_ctas : tuning().crc_ctas;
+  if (!cap || !ctas) return;
   cudaFuncSetAttribute(k_block_crc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCrcSmem));
-  k_block_crc<<<tuning().crc_ctas, kCrcWarps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done, tabs);
+  k_block_crc<<<ctas, kCrcWarps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done, tabs);
   count_launches(1);
 }
 
