@@ -306,6 +306,47 @@ luda_status err_status(const DErr& e, uint32_t job, uint32_t n_jobs) {
   return luda_status(e.code);
 }
 
+// ---- pinned staging for the small host<->device transfers of one call --------------------
+// Copies from and to pageable memory are staged by the driver synchronously; these go
+// through one pinned buffer per host thread instead, so that a round trip is a few
+// asynchronous copies and one synchronisation. take() hands out 16-byte aligned pieces
+// until reset(); a request that does not fit returns NULL (the caller then uses its own
+// memory) and the buffer grows at the next reset.
+class HostStage {
+ public:
+  ~HostStage() {
+    if (p_) cudaFreeHost(p_);
+  }
+  // Call only when no copy from or to the buffer is pending (after a synchronisation).
+  void reset() {
+    off_ = 0;
+    if (want_ > cap_) {
+      if (p_) cudaFreeHost(p_);
+      p_ = nullptr;
+      cap_ = 0;
+      void* q = nullptr;
+      if (cudaHostAlloc(&q, want_, cudaHostAllocDefault) == cudaSuccess) {
+        p_ = static_cast<uint8_t*>(q);
+        cap_ = want_;
+      }
+    }
+  }
+  void* take(size_t n) {
+    const size_t o = (off_ + 15) & ~size_t(15);
+    if (!p_ || o + n > cap_) {
+      want_ = std::max(want_, std::max<size_t>(1u << 20, 2 * (o + n)));
+      return nullptr;
+    }
+    off_ = o + n;
+    return p_ + o;
+  }
+
+ private:
+  uint8_t* p_ = nullptr;
+  size_t cap_ = 0, off_ = 0, want_ = 1u << 20;
+};
+thread_local HostStage t_stage;
+
 // ---- the pack stages, shared by compaction and build --------------------------------------
 struct PackBufs {
   uint32_t *surv, *lcp, *sd, *dr, *next, *bpos, *blk_start, *fnext, *fpos, *file_start, *blk_file, *ie;
@@ -320,9 +361,13 @@ struct PackBufs {
   uint32_t* bitmap;
   uint8_t* keybuf;
   void *scan_tmp, *stitch_tmp;
+  uint32_t meta_cap;  // entries of meta
+  uint64_t key_cap;   // bytes of keybuf
 };
 
 void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t key_cap) {
+  b.meta_cap = cap + 1;
+  b.key_cap = key_cap + 1;
   b.surv = L.take<uint32_t>(cap + 1);
   b.lcp = L.take<uint32_t>(cap + 1);
   b.sd = L.take<uint32_t>(cap + 1);
@@ -438,23 +483,55 @@ struct Collected {
 // d_errs holds 2 * (n_jobs + 1) entries: the main chain's errors, then the input checksum
 // errors; a checksum error takes precedence (the inputs are verified before anything is
 // read from them in the method's order).
+// The counts, job records and error words come back in one round trip, together with the
+// first kSpecMeta table records and kSpecKeys boundary-key bytes; only a result with more
+// tables or key bytes than that needs a second one.
+constexpr uint32_t kSpecMeta = 256;
+constexpr uint64_t kSpecKeys = 64 * 1024;
+
 luda_status collect(const Counts* d_cnt, const JobDev* d_jobs, const DErr* d_errs, const PackBufs& b, uint32_t n_jobs,
                     Collected* c, cudaStream_t st) {
+  const size_t ne = 2 * size_t(n_jobs + 1);
+  const uint32_t spec_m = std::min(kSpecMeta, b.meta_cap);
+  const uint64_t spec_k = std::min(kSpecKeys, b.key_cap);
+  HostStage& hs = t_stage;  // reset by the caller at the start of its call
+  Counts* h_cnt = static_cast<Counts*>(hs.take(sizeof(Counts)));
+  JobDev* h_jobs = static_cast<JobDev*>(hs.take(sizeof(JobDev) * n_jobs));
+  DErr* h_errs = static_cast<DErr*>(hs.take(sizeof(DErr) * ne));
+  FileMeta* h_meta = static_cast<FileMeta*>(hs.take(sizeof(FileMeta) * spec_m));
+  uint8_t* h_keys = static_cast<uint8_t*>(hs.take(spec_k));
+  const bool staged = h_cnt && h_jobs && h_errs && h_meta && h_keys;
   c->jobs.resize(n_jobs);
-  c->errs.resize(2 * (n_jobs + 1));
-  CK(cudaMemcpyAsync(&c->cnt, d_cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(c->jobs.data(), d_jobs, sizeof(JobDev) * n_jobs, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(c->errs.data(), d_errs, sizeof(DErr) * 2 * (n_jobs + 1), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  c->errs.resize(ne);
+  if (staged) {
+    CK(cudaMemcpyAsync(h_cnt, d_cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_jobs, d_jobs, sizeof(JobDev) * n_jobs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_errs, d_errs, sizeof(DErr) * ne, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_meta, b.meta, sizeof(FileMeta) * spec_m, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_keys, b.keybuf, spec_k, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c->cnt = *h_cnt;
+    memcpy(c->jobs.data(), h_jobs, sizeof(JobDev) * n_jobs);
+    memcpy(c->errs.data(), h_errs, sizeof(DErr) * ne);
+  } else {
+    CK(cudaMemcpyAsync(&c->cnt, d_cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->jobs.data(), d_jobs, sizeof(JobDev) * n_jobs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->errs.data(), d_errs, sizeof(DErr) * ne, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
   for (uint32_t j = 0; j < n_jobs; ++j)
     if (c->errs[n_jobs + 1 + j].code) c->errs[j] = c->errs[n_jobs + 1 + j];
   c->errs.resize(n_jobs);
   c->meta.resize(c->cnt.nf);
   c->keys.resize(c->cnt.key_bytes + 1);
-  if (c->cnt.nf) {
-    CK(cudaMemcpyAsync(c->meta.data(), b.meta, sizeof(FileMeta) * c->cnt.nf, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(c->keys.data(), b.keybuf, c->cnt.key_bytes, cudaMemcpyDeviceToHost, st));
+  if (!c->cnt.nf) return LUDA_OK;
+  if (staged && c->cnt.nf <= spec_m && c->cnt.key_bytes <= spec_k) {
+    memcpy(c->meta.data(), h_meta, sizeof(FileMeta) * c->cnt.nf);
+    memcpy(c->keys.data(), h_keys, c->cnt.key_bytes);
+    return LUDA_OK;
   }
+  CK(cudaMemcpyAsync(c->meta.data(), b.meta, sizeof(FileMeta) * c->cnt.nf, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(c->keys.data(), b.keybuf, c->cnt.key_bytes, cudaMemcpyDeviceToHost, st));
   return LUDA_OK;
 }
 
@@ -728,13 +805,25 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     }
   } guard{mem, {bufA}};
 
+  HostStage& hs = t_stage;
+  hs.reset();
+  // a pinned copy of a host array for an asynchronous copy (the array itself if none is left)
+  auto pin = [&](const void* src, size_t n) -> const void* {
+    void* q = hs.take(n);
+    if (!q) return src;
+    memcpy(q, src, n);
+    return q;
+  };
   CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * 2 * (n_jobs + 1), st));
   CK(cudaMemsetAsync(d_cnt, 0, sizeof(Counts), st));
-  if (N) CK(cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
+  DInput* hin_pin = static_cast<DInput*>(hs.take(sizeof(DInput) * (N + 1)));
+  if (N)
+    CK(cudaMemcpyAsync(d_in, pin(hin.data(), sizeof(DInput) * N), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
   launch_footers(d_in, N, d_errs, d_msgs, tabs, st);
   CK(cudaGetLastError());
-  if (N) CK(cudaMemcpyAsync(hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
+  if (N) CK(cudaMemcpyAsync(hin_pin ? hin_pin : hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (N && hin_pin) memcpy(hin.data(), hin_pin, sizeof(DInput) * N);
   std::vector<uint32_t> in_blk_first(N + 1, 0);
   uint64_t NB64 = 0;
   for (uint32_t i = 0; i < N; ++i) {
@@ -749,8 +838,9 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   }
   const uint32_t NB = uint32_t(NB64);
   if (N) {
-    CK(cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_in_blk_first, in_blk_first.data(), sizeof(uint32_t) * (N + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_in, pin(hin.data(), sizeof(DInput) * N), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_in_blk_first, pin(in_blk_first.data(), sizeof(uint32_t) * (N + 1)),
+                       sizeof(uint32_t) * (N + 1), cudaMemcpyHostToDevice, st));
   }
 
   // ---- sizing: block scan ------------------------------------------------------------------
@@ -803,13 +893,36 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   std::vector<uint64_t> in_key(N + 1);
   std::vector<DErr> herr(n_jobs + 1);
   std::vector<uint8_t> link(N + 1, 0);
-  CK(cudaMemcpyAsync(in_rec.data(), d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(in_key.data(), d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(herr.data(), d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&fmt.max_kv, &d_cnt->max_kv, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  if (N) CK(cudaMemcpyAsync(link.data(), d_link, N, cudaMemcpyDeviceToHost, st));
-  tr.mark(3, st);
-  CK(cudaStreamSynchronize(st));
+  {
+    // one pinned piece for the five results (pageable vectors if the stage is full)
+    uint32_t* p_rec = static_cast<uint32_t*>(hs.take(sizeof(uint32_t) * (N + 1)));
+    uint64_t* p_key = static_cast<uint64_t*>(hs.take(sizeof(uint64_t) * (N + 1)));
+    DErr* p_err = static_cast<DErr*>(hs.take(sizeof(DErr) * n_jobs));
+    uint32_t* p_kv = static_cast<uint32_t*>(hs.take(sizeof(uint32_t)));
+    uint8_t* p_link = static_cast<uint8_t*>(hs.take(N + 1));
+    const bool pinned = p_rec && p_key && p_err && p_kv && p_link;
+    if (!pinned) {
+      p_rec = in_rec.data();
+      p_key = in_key.data();
+      p_err = herr.data();
+      p_kv = &fmt.max_kv;
+      p_link = link.data();
+    }
+    CK(cudaMemcpyAsync(p_rec, d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(p_key, d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+    if (n_jobs) CK(cudaMemcpyAsync(p_err, d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(p_kv, &d_cnt->max_kv, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (N) CK(cudaMemcpyAsync(p_link, d_link, N, cudaMemcpyDeviceToHost, st));
+    tr.mark(3, st);
+    CK(cudaStreamSynchronize(st));
+    if (pinned) {
+      memcpy(in_rec.data(), p_rec, sizeof(uint32_t) * (N + 1));
+      memcpy(in_key.data(), p_key, sizeof(uint64_t) * (N + 1));
+      if (n_jobs) memcpy(herr.data(), p_err, sizeof(DErr) * n_jobs);
+      fmt.max_kv = *p_kv;
+      if (N) memcpy(link.data(), p_link, N);
+    }
+  }
 
   const uint32_t n_rec = in_rec[N];
   const uint64_t K = in_key[N];
@@ -897,10 +1010,12 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     }
   } out_guard{mem, d_out, &out_owned};
 
-  CK(cudaMemcpyAsync(&d_cnt->n_rec, &n_rec, sizeof n_rec, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_jobs, hjobs.data(), sizeof(JobDev) * n_jobs, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(&d_cnt->n_rec, pin(&n_rec, sizeof n_rec), sizeof n_rec, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_jobs, pin(hjobs.data(), sizeof(JobDev) * n_jobs), sizeof(JobDev) * n_jobs,
+                     cudaMemcpyHostToDevice, st));
   if (!spans.empty())
-    CK(cudaMemcpyAsync(d_spans, spans.data(), sizeof(MergeSpan) * spans.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_spans, pin(spans.data(), sizeof(MergeSpan) * spans.size()), sizeof(MergeSpan) * spans.size(),
+                       cudaMemcpyHostToDevice, st));
 
   tr.mark(4, st);
   launch_decode(d_blocks, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
@@ -1125,6 +1240,7 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
   CK(cudaStreamWaitEvent(st, side->ev[3], 0));
   td.stop(st);
   Collected col;
+  t_stage.reset();  // nothing of this call was staged before (its copies are synchronous)
   if ((rc = collect(d_cnt, d_job, d_err, pb, 1, &col, st))) return rc;
   Holder* h = new Holder();
   uint8_t* base = d_out;
@@ -1719,6 +1835,7 @@ luda_status luda_plan_outputs(luda_plan* plan, luda_outputs* outs) {
   cudaError_t e = cudaEventSynchronize(P->done);
   if (e != cudaSuccess) return cuda_fail(e, "waiting for the plan");
   Collected col;
+  t_stage.reset();
   luda_status rc = collect(P->d_cnt, P->d_jobs, P->d_errs, P->pb, P->n_jobs, &col, P->st);
   if (rc) return rc;
   if ((e = cudaStreamSynchronize(P->st)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
