@@ -75,8 +75,8 @@ typedef void (*luda_free_fn)(void* ptr, void* ctx, void* stream);
  * field means the built-in default. luda_autotune measures candidates; a caller passes
  * the winner through luda_options.tuning. */
 typedef struct {
-  uint32_t merge_tile;          /* records per merge CTA: 512, 1024 or 2048 (default 1024) */
-  uint32_t merge_ctas_per_sm;   /* grid of each merge pass, CTAs per SM: 1..32 (default 8) */
+  uint32_t merge_tile;          /* records per merge CTA: 512, 1024 or 2048 (default 512) */
+  uint32_t merge_ctas_per_sm;   /* grid of each merge pass, CTAs per SM: 1..32 (default 16) */
   uint32_t decode_warps;        /* warps per CTA of the decoder, one data block each: 1..16 (default 8) */
   uint32_t walk_threads;        /* threads per CTA of the block walk, one block each: 32..256, multiple of 32
                                    (default 256) */
@@ -86,7 +86,8 @@ typedef struct {
                                    cut and layout stages: 64..1024, multiple of 32 (default 256) */
   uint32_t crc_ctas;            /* CTAs (one per SM) of the data-block checksum kernels, which run beside the
                                    other stages on a second stream: 1..148 (default 100) */
-  uint32_t reserved;            /* must be 0 */
+  uint32_t crc_warps;           /* warps per CTA of the checksum kernels: 8, 16, 24 or 32 (default 32); fewer
+                                   leave room on their SMs for the other stages' CTAs */
 } luda_tuning;
 
 /* Fills the defaults (all fields 0). */

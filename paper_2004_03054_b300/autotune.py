@@ -35,10 +35,11 @@ SPACE: dict[str, tuple[int, ...]] = {
     "encode_ctas_per_sm": (1, 2, 0),
     "elem_threads": (128, 256, 512),
     "crc_ctas": (148, 120, 100, 74),
+    "crc_warps": (32, 16),
 }
 # The library's defaults, resolved.
-DEFAULT = {"merge_tile": 1024, "merge_ctas_per_sm": 8, "decode_warps": 8, "walk_threads": 256,
-           "encode_ctas_per_sm": 0, "elem_threads": 256, "crc_ctas": 100}
+DEFAULT = {"merge_tile": 512, "merge_ctas_per_sm": 16, "decode_warps": 8, "walk_threads": 256,
+           "encode_ctas_per_sm": 0, "elem_threads": 256, "crc_ctas": 100, "crc_warps": 32}
 
 
 @dataclass

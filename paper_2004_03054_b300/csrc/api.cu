@@ -46,6 +46,30 @@ void set_detail(const char* fmt, ...) {
 
 void luda::set_error_detail(const char* text) { snprintf(t_detail, sizeof t_detail, "%s", text); }
 
+void luda::smem_optin_raw(const void* kernel, int bytes) {
+  // The attribute belongs to the kernel on the device, not to a thread: one table for the
+  // process, and the size only grows (a smaller value set by one thread would make another
+  // thread's larger launch fail).
+  struct Entry {
+    const void* k;
+    int dev, bytes;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  for (Entry& e : done)
+    if (e.k == kernel && e.dev == dev) {
+      if (bytes <= e.bytes) return;
+      if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+        e.bytes = bytes;
+      return;
+    }
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+    done.push_back(Entry{kernel, dev, bytes});
+}
+
 // ---- launch shapes ----------------------------------------------------------------------------
 namespace {
 thread_local Tuning t_tuning;
@@ -64,7 +88,7 @@ bool luda::tuning_valid(const luda_tuning* t) {
   else if (t->elem_threads && (t->elem_threads < 64 || t->elem_threads > 1024 || t->elem_threads % 32))
     bad = "elem_threads";
   else if (t->crc_ctas > kSms) bad = "crc_ctas";
-  else if (t->reserved) bad = "reserved";
+  else if (t->crc_warps && (t->crc_warps < 8 || t->crc_warps > 32 || t->crc_warps % 8)) bad = "crc_warps";
   if (bad) set_detail("invalid tuning: %s", bad);
   return bad == nullptr;
 }
@@ -78,6 +102,7 @@ luda::TuningScope::TuningScope(const luda_tuning* t) : saved_(t_tuning) {
   if (t->encode_ctas_per_sm) t_tuning.encode_ctas_per_sm = t->encode_ctas_per_sm;
   if (t->elem_threads) t_tuning.elem_threads = t->elem_threads;
   if (t->crc_ctas) t_tuning.crc_ctas = t->crc_ctas;
+  if (t->crc_warps) t_tuning.crc_warps = t->crc_warps;
 }
 
 luda::TuningScope::~TuningScope() { t_tuning = saved_; }

@@ -577,9 +577,10 @@ void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInpu
                          CrcTabs tabs, uint32_t* next, bool helper, cudaStream_t st) {
   const uint32_t ctas = helper ? kSms - tuning().crc_ctas : tuning().crc_ctas;
   if (!n_blocks || !ctas) return;
-  cudaFuncSetAttribute(k_block_verify, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kVerifySmem));
-  const unsigned g = grid_for(n_blocks, kVerifyWarps, ctas);
-  k_block_verify<<<g, kVerifyWarps * 32, kVerifySmem, st>>>(blocks, n_blocks, in, errs, verr, tabs, next);
+  smem_optin(k_block_verify, kVerifySmem);
+  const unsigned w = tuning().crc_warps;
+  const unsigned g = grid_for(n_blocks, w, ctas);
+  k_block_verify<<<g, w * 32, kVerifySmem, st>>>(blocks, n_blocks, in, errs, verr, tabs, next);
   count_launches(1);
 }
 

@@ -150,13 +150,14 @@ inline unsigned grid_for(uint64_t work, unsigned per_cta, unsigned max_ctas = kS
 // The launchers read the calling thread's current tuning; an entry point installs the
 // caller's (luda_options.tuning) for its duration with a TuningScope. Defaults resolved:
 struct Tuning {
-  uint32_t merge_tile = 1024;
-  uint32_t merge_ctas_per_sm = 8;
+  uint32_t merge_tile = 512;
+  uint32_t merge_ctas_per_sm = 16;
   uint32_t decode_warps = 8;
   uint32_t walk_threads = 256;
   uint32_t encode_ctas_per_sm = 0;  // 0: as many as shared memory allows
   uint32_t elem_threads = 256;
   uint32_t crc_ctas = 100;  // about two thirds of the SMs: the other stages run beside the checksums
+  uint32_t crc_warps = 32;
 };
 const Tuning& tuning();
 // Range check of a luda_tuning (0 = default); sets the error detail on failure.
@@ -173,6 +174,15 @@ class TuningScope {
 };
 // CTA size of the per-record and per-block kernels of the drop rule, cut and layout stages.
 inline unsigned elem_threads() { return tuning().elem_threads; }
+
+// Lets `kernel` use `bytes` of dynamic shared memory on the current device. The attribute
+// call takes a driver lock and costs more than a small launch, so each thread remembers
+// the largest size it has set per kernel and device.
+void smem_optin_raw(const void* kernel, int bytes);
+template <class K>
+inline void smem_optin(K* kernel, uint32_t bytes) {
+  smem_optin_raw(reinterpret_cast<const void*>(kernel), int(bytes));
+}
 
 // ---- scan.cu ----------------------------------------------------------------------------
 uint64_t scan_temp_bytes(uint64_t n);

@@ -74,7 +74,7 @@ __global__ void k_msg_finish(const CrcMsg* __restrict__ msgs, const uint32_t* __
 void launch_msg_crc(CrcMsg* msgs, const uint32_t* count, uint32_t mult, uint32_t max_msgs, DErr* errs, CrcTabs tabs,
                     cudaStream_t st) {
   if (!max_msgs) return;
-  cudaFuncSetAttribute(k_msg_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMsgSmem));
+  smem_optin(k_msg_chunks, kMsgSmem);
   k_msg_chunks<<<kSms, kMsgWarps * 32, kMsgSmem, st>>>(msgs, count, mult, tabs);
   k_msg_finish<<<grid_for(max_msgs, 128, kSms), 128, 0, st>>>(msgs, count, mult, errs, tabs);
   count_launches(2);

@@ -1282,7 +1282,7 @@ void launch_stitch(const uint32_t* next, const uint32_t* n_dev, uint32_t cap, ui
   k_max_gap<<<grid_for(cap, 256, kSms * 2), 256, 0, st>>>(next, n_dev, gap); count_launches(1);
   cudaMemsetAsync(flags, 0, cap + 1, st);  // the walk path sets only the chain's flags
   k_stitch_win<<<grid_for(tiles, 1, kSms * 8), 256, 0, st>>>(next, n_dev, gap, exitw); count_launches(1);
-  cudaFuncSetAttribute(k_stitch_compose, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCombSmem));
+  smem_optin(k_stitch_compose, kCombSmem);
   k_stitch_compose<<<1, 1024, kCombSmem, st>>>(exitw, n_dev, gap, entry, done);
   k_stitch_combine<<<1, 256, 0, st>>>(exitw, n_dev, gap, entry, done); count_launches(2);
   k_stitch_mark<<<grid_for(tiles, 1, kSms * 8), 128, 0, st>>>(next, n_dev, gap, entry, flags); count_launches(1);
@@ -1372,7 +1372,7 @@ void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const u
   uint32_t per_sm = (227u * 1024u) / (smem + 1024u);
   per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
   if (tuning().encode_ctas_per_sm && tuning().encode_ctas_per_sm < per_sm) per_sm = tuning().encode_ctas_per_sm;
-  cudaFuncSetAttribute(k_encode_stg, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  smem_optin(k_encode_stg, smem);
   k_block_enc<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(blk_start, cnt, blk_file, files, C, bsz, out_cap, bd);
   k_encode_stg<<<kSms * per_sm, kStgThreads, smem, st>>>(cnt, bd, lcp, ed, fmt, out, out_cap, done, big, errs, S, I);
   count_launches(2);
@@ -1383,8 +1383,9 @@ void launch_block_crc(Counts* cnt, uint32_t cap, const uint32_t* blk_file, const
                       CrcTabs tabs, bool helper, cudaStream_t st) {
   const uint32_t ctas = helper ? kSms - tuning().crc_ctas : tuning().crc_ctas;
   if (!cap || !ctas) return;
-  cudaFuncSetAttribute(k_block_crc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kCrcSmem));
-  k_block_crc<<<ctas, kCrcWarps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done, tabs);
+  smem_optin(k_block_crc, kCrcSmem);
+  k_block_crc<<<ctas, tuning().crc_warps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done,
+                                                                tabs);
   count_launches(1);
 }
 
@@ -1393,7 +1394,7 @@ void launch_encode_big(const uint32_t* blk_start, Counts* cnt, uint32_t cap, con
                        const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
                        Fmt fmt, uint8_t* out, uint64_t out_cap, const uint32_t* big, CrcTabs tabs, cudaStream_t st) {
   if (!cap) return;
-  cudaFuncSetAttribute(k_encode_big, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kEncBuf));
+  smem_optin(k_encode_big, kEncBuf);
   k_encode_big<<<kSms, kEncThreads, kEncBuf, st>>>(blk_start, cnt, blk_file, files, C, bsz, surv, lcp, sd, dr, recs,
                                                    arena, fmt, out, out_cap, big, tabs);
   count_launches(1);

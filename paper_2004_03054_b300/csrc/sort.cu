@@ -290,7 +290,7 @@ template <uint32_t kTile>
 void merge_pass_t(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t* ord0, MKey* key0,
                   uint32_t* ord1, MKey* key1, Recs recs, const uint8_t* arena, cudaStream_t st) {
   constexpr uint32_t smem = kTile * (sizeof(MKey) + sizeof(uint32_t));
-  if (smem > 48u * 1024u) cudaFuncSetAttribute(k_merge<kTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (smem > 48u * 1024u) smem_optin(k_merge<kTile>, smem);
   k_merge<kTile><<<grid_for(n_tiles, 1, kSms * tuning().merge_ctas_per_sm), kMergeThreads, smem, st>>>(
       spans, n_spans, n_tiles, ord0, key0, ord1, key1, recs, arena);
 }

@@ -13,7 +13,7 @@ from paper_2004_03054_b300 import luda
 def _cost(t):
     """A separable cost with a known minimum per knob (in ms)."""
     best = {"merge_tile": 2048, "merge_ctas_per_sm": 4, "decode_warps": 16, "walk_threads": 128,
-            "encode_ctas_per_sm": 1, "elem_threads": 512, "crc_ctas": 74}
+            "encode_ctas_per_sm": 1, "elem_threads": 512, "crc_ctas": 74, "crc_warps": 16}
     return 10.0 + sum(abs(AT.SPACE[k].index(t[k]) - AT.SPACE[k].index(best[k])) for k in AT.SPACE), best
 
 
@@ -88,10 +88,8 @@ def test_library_checks_tuning_ranges():
     assert L.luda_tuning_check(C.byref(t0)) == luda.OK
     for bad in ({"merge_tile": 768}, {"merge_tile": 4096}, {"merge_ctas_per_sm": 33}, {"decode_warps": 17},
                 {"walk_threads": 48}, {"walk_threads": 512}, {"encode_ctas_per_sm": 9}, {"elem_threads": 32},
-                {"elem_threads": 100}, {"elem_threads": 2048}, {"crc_ctas": 149}):
+                {"elem_threads": 100}, {"elem_threads": 2048}, {"crc_ctas": 149},
+                {"crc_warps": 4}, {"crc_warps": 20}, {"crc_warps": 40}):
         assert L.luda_tuning_check(C.byref(luda.Tuning.of(bad))) == luda.ERR_INVALID_ARG, bad
         assert list(bad)[0] in luda.last_error_detail()
-    t = luda.Tuning()
-    t.reserved = 1
-    assert L.luda_tuning_check(C.byref(t)) == luda.ERR_INVALID_ARG
     assert L.luda_tuning_check(None) == luda.ERR_INVALID_ARG

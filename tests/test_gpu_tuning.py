@@ -28,6 +28,9 @@ TUNINGS = [
     {"elem_threads": 1024},
     {"merge_tile": 512, "merge_ctas_per_sm": 2, "decode_warps": 2, "walk_threads": 96, "encode_ctas_per_sm": 2,
      "elem_threads": 160},
+    {"crc_warps": 16, "crc_ctas": 148},
+    {"crc_warps": 8, "crc_ctas": 20},
+    {"crc_ctas": 1},
 ]
 
 
