@@ -18,10 +18,22 @@ Policy (LevelDB's, with concurrent jobs on disjoint tables):
   * a job is bottommost when no deeper level holds a table overlapping its key range;
     there are no snapshots (smallest snapshot = newest sequence number).
   * writes stall while L0 holds 12 tables (LevelDB's stop trigger).
+
+Failures: a job is all-or-nothing (its outputs depend only on its inputs and options), so
+a failed job leaves its input tables in the tree untouched and the policy simply starts it
+again; the same tables failing three times in a row is an error. For tests, `fault`
+injects failures on the host: a job it selects gets one extra, corrupted input table.
+
+Checkpoint: snapshot() writes the tree (every table's bytes plus a JSON manifest of levels,
+key ranges, table numbers and compaction pointers) to a directory; restore() rebuilds the
+tree on the device from it. A compaction in flight is not part of a snapshot (it would be
+redone).
 """
 from __future__ import annotations
 
 import ctypes as C
+import json
+import os
 import time
 from dataclasses import dataclass, field
 
@@ -75,6 +87,7 @@ class JobRecord:
     stats: object = None
     in_bytes: int = 0
     out_bytes: int = 0
+    extra: object = None     # an injected corrupt input (kept alive until the job ends)
 
 
 @dataclass
@@ -93,6 +106,7 @@ class ServeReport:
     stall_s: float = 0.0
     level_bytes: list = field(default_factory=list)
     flushes: int = 0
+    retried: int = 0         # jobs started again after a failure
 
     def pct(self, p: float) -> float:
         if not self.latencies_ms:
@@ -109,9 +123,12 @@ class LSM:
     def __init__(self, server: luda.Server, memtable_bytes: int = 64 * MiB, l0_trigger: int = 4,
                  l0_stop: int = 12, fanout: int = 10, target_file: int = 64 * MiB, block_size: int = 4096,
                  restart_interval: int = 16, bloom_bits_per_key: int = 10, value_pool_bytes: int = 256 * MiB,
-                 seed: int = 5, on_complete=None):
+                 seed: int = 5, on_complete=None, fault=None):
         import torch
         self.server = server
+        self.fault = fault            # fault(job_index, level) -> True: corrupt that job
+        self.submitted = 0
+        self.fail_count = {}          # table numbers of a failed job -> failures in a row
         self.l0_trigger, self.l0_stop, self.fanout = l0_trigger, l0_stop, fanout
         self.l1_target = fanout * memtable_bytes
         self.levels = [[] for _ in range(N_LEVELS)]
@@ -189,8 +206,15 @@ class LSM:
         for t in lower:
             t.busy = "lower"
         bottom = self._bottommost(level + 1, lo, hi)
-        ticket = self.server.submit([(t.ptr, t.size) for t in inputs], W.MAX_SEQ, bottom, level + 1)
-        rec = JobRecord(ticket, level, inputs, bottom, time.perf_counter(), in_bytes=sum(t.size for t in inputs))
+        extra = None
+        if self.fault is not None and self.fault(self.submitted, level):
+            extra = luda.device_bytes(inputs[0].ptr, inputs[0].size)
+            extra[min(10, extra.numel() - 1)] ^= 0x40  # inside the first data block: its checksum fails
+        self.submitted += 1
+        pairs = ([(extra.data_ptr(), extra.numel())] if extra is not None else []) + [(t.ptr, t.size) for t in inputs]
+        ticket = self.server.submit(pairs, W.MAX_SEQ, bottom, level + 1)
+        rec = JobRecord(ticket, level, inputs, bottom, time.perf_counter(), in_bytes=sum(t.size for t in inputs),
+                        extra=extra)
         self.jobs[ticket] = rec
         return rec
 
@@ -238,11 +262,20 @@ class LSM:
         r.run_ms.append(stats.run_ms)
         r.admit_wait_ms.append(stats.admit_wait_ms)
         r.compaction_in_bytes += rec.in_bytes
+        rec.extra = None
         if out.status != 0:
+            # all or nothing: the inputs stay in the tree and the policy starts the job again
             r.failed += 1
             for t in rec.inputs:
                 t.busy = ""
-            raise RuntimeError(f"compaction job failed: {luda.strerror(out.status)}")
+            key = frozenset(t.number for t in rec.inputs)
+            n = self.fail_count.get(key, 0) + 1
+            self.fail_count[key] = n
+            if n >= 3:
+                raise RuntimeError(f"compaction job failed three times: {luda.strerror(out.status)}")
+            r.retried += 1
+            return
+        self.fail_count.pop(frozenset(t.number for t in rec.inputs), None)
         if self.on_complete is not None:
             self.on_complete(rec, out)
         owner = _Owner(out, out.n_tables) if out.n_tables else None
@@ -269,9 +302,54 @@ class LSM:
                 t.release()
             lv.clear()
 
+    # ---- checkpoint ------------------------------------------------------------------------
+    def snapshot(self, path: str) -> dict:
+        """Write every table (its bytes, <number>.sst) and manifest.json to directory
+        `path`; returns the manifest. Call with no job running."""
+        if self.jobs:
+            raise RuntimeError("snapshot with compaction jobs running")
+        os.makedirs(path, exist_ok=True)
+        levels = []
+        for lv in self.levels:
+            entries = []
+            for t in lv:
+                name = f"{t.number:06d}.sst"
+                luda.device_bytes(t.ptr, t.size).cpu().numpy().tofile(os.path.join(path, name))
+                entries.append({"number": t.number, "file": name, "size": t.size, "smallest": t.smallest.hex(),
+                                "largest": t.largest.hex(), "n_entries": t.n_entries})
+            levels.append(entries)
+        manifest = {"levels": levels, "pointer": [p.hex() for p in self.pointer], "next_number": self.next_number,
+                    "format": list(self.fmt), "l0_trigger": self.l0_trigger, "l0_stop": self.l0_stop,
+                    "fanout": self.fanout, "l1_target": self.l1_target}
+        tmp = os.path.join(path, "manifest.json.tmp")
+        with open(tmp, "w") as f:
+            json.dump(manifest, f, indent=1)
+        os.replace(tmp, os.path.join(path, "manifest.json"))
+        return manifest
+
+    def restore(self, path: str) -> None:
+        """Replace this (empty) tree with the one snapshot() wrote to `path`."""
+        import torch
+        if any(self.levels) or self.jobs:
+            raise RuntimeError("restore into a tree that is not empty")
+        with open(os.path.join(path, "manifest.json")) as f:
+            m = json.load(f)
+        if tuple(m["format"]) != tuple(self.fmt):
+            raise ValueError(f"snapshot format {m['format']} differs from this tree's {list(self.fmt)}")
+        for lv, entries in enumerate(m["levels"]):
+            for e in entries:
+                data = np.fromfile(os.path.join(path, e["file"]), dtype=np.uint8)
+                if data.size != e["size"]:
+                    raise ValueError(f"{e['file']}: {data.size} bytes, manifest says {e['size']}")
+                dev = torch.from_numpy(data).cuda()
+                self.levels[lv].append(SST(e["number"], dev.data_ptr(), int(e["size"]), bytes.fromhex(e["smallest"]),
+                                           bytes.fromhex(e["largest"]), int(e["n_entries"]), dev))
+        self.pointer = [bytes.fromhex(p) for p in m["pointer"]]
+        self.next_number = int(m["next_number"])
+
 
 def serve(stream, n_slots: int = 4, hbm_budget: int = 40 * 10**9, pace: bool = True, on_complete=None,
-          lsm_kw: dict | None = None) -> ServeReport:
+          lsm_kw: dict | None = None, before_close=None) -> ServeReport:
     """Feed a write stream (workloads.config5_stream) into a simulated LSM tree served by a
     luda.Server with `n_slots` slots: memtables are flushed when the stream time says they
     are full (wall clock, if `pace`), compactions start as soon as the policy allows and
@@ -317,6 +395,8 @@ def serve(stream, n_slots: int = 4, hbm_budget: int = 40 * 10**9, pace: bool = T
         st = server.stats()
         rep.running_peak, rep.budget_peak = int(st.running_peak), int(st.budget_peak)
         rep.level_bytes = [lsm.level_bytes(i) for i in range(N_LEVELS)]
+        if before_close is not None:
+            before_close(lsm)
         return rep
     finally:
         lsm.close()
