@@ -1132,6 +1132,8 @@ int ora_read_table(const uint8_t* f, uint64_t fsize, ora_read** out) {
   free(key.p);
   free(ri.lastkeys.p);
   free(ri.lkoff);
+  free(ri.ic.keys.p);
+  free(ri.ic.kend);
   if (rc != ORA_OK) {
     free(ri.ic.off);
     free(ri.ic.size);
