@@ -150,20 +150,35 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 // Tables in shared memory, addressed with 32-bit shared-window addresses so that every
 // lookup is one byte extract, one address multiply-add and one ld.shared with the table's
 // offset as an immediate. tl = address of this lane's column of the lane-replicated slicing
-// tables (word (t * 256 + v) * 32 + lane holds slice[t][v]); tz = address of Z_992's four
-// byte tables.
-// One global load per table word, then its 32 lane copies stored in rotated order, so that
+// tables (word (t * 256 + v) * 32 + lane holds slice[t][v]); tz = address of this lane's
+// copy of Z_992's four byte tables: kZCopies interleaved copies (word (t * 256 + v) *
+// kZCopies + c holds copy c), lane l reading copy l mod kZCopies, so that lanes sharing a
+// bank are the 32 / kZCopies lanes of one copy and conflicts stay few.
+constexpr uint32_t kZCopies = 16;
+constexpr uint32_t kZWords = 1024 * kZCopies;
+constexpr uint32_t kRepSmem = (kRepWords + kZWords) * 4;  // bytes of shared memory for both
+
+// One global load per table word, then its lane copies stored in rotated order, so that
 // the 32 threads of a warp (consecutive words) hit 32 different banks. blockDim must be a
 // multiple of 32.
 __device__ __forceinline__ void load_rep_tables992(uint32_t* sTr, uint32_t* sZ, const CrcTabs tabs) {
   const uint32_t rot = threadIdx.x & 31u;
   for (uint32_t w = threadIdx.x; w < 1024; w += blockDim.x) {
     const uint32_t val = __ldg(tabs.slice + w);
-    sZ[w] = __ldg(tabs.shift + size_t(kShift992) * 1024 + w);
+    const uint32_t zv = __ldg(tabs.shift + size_t(kShift992) * 1024 + w);
     uint32_t* row = sTr + w * 32u;
 #pragma unroll 8
     for (uint32_t l = 0; l < 32; ++l) row[(l + rot) & 31u] = val;
+    uint32_t* zrow = sZ + w * kZCopies;
+    const uint32_t zrot = (w >> 1) & (kZCopies - 1);
+#pragma unroll
+    for (uint32_t c = 0; c < kZCopies; ++c) zrow[(c + zrot) & (kZCopies - 1)] = zv;
   }
+}
+
+// Address of lane `lane`'s copy of the skip tables that start at sZ.
+__device__ __forceinline__ uint32_t zcopy_addr(const uint32_t* sZ, uint32_t lane) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(sZ)) + (lane & (kZCopies - 1)) * 4u;
 }
 
 template <uint32_t kOff>
@@ -183,8 +198,10 @@ __device__ __forceinline__ uint32_t crc_word_rep(uint32_t c, uint32_t w, uint32_
 }
 
 __device__ __forceinline__ uint32_t crc_z992(uint32_t v, uint32_t tz) {
-  return lds_off<0u>(tz + __byte_perm(v, 0, 0x4440) * 4u) ^ lds_off<1024u>(tz + __byte_perm(v, 0, 0x4441) * 4u) ^
-         lds_off<2048u>(tz + __byte_perm(v, 0, 0x4442) * 4u) ^ lds_off<3072u>(tz + __byte_perm(v, 0, 0x4443) * 4u);
+  constexpr uint32_t kRow = kZCopies * 4u, kTab = 256u * kRow;
+  return lds_off<0u>(tz + __byte_perm(v, 0, 0x4440) * kRow) ^ lds_off<kTab>(tz + __byte_perm(v, 0, 0x4441) * kRow) ^
+         lds_off<2u * kTab>(tz + __byte_perm(v, 0, 0x4442) * kRow) ^
+         lds_off<3u * kTab>(tz + __byte_perm(v, 0, 0x4443) * kRow);
 }
 
 __device__ __forceinline__ uint32_t crc_unit32(uint32_t acc, const uint4& x, const uint4& y, uint32_t tl) {

@@ -148,7 +148,7 @@ __global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs
 // 16-byte window (two aligned 8-byte loads; tables are readable up to 16 bytes past any
 // entry, since at least the trailer and footer follow every data block).
 constexpr int kVerifyWarps = 32;
-constexpr uint32_t kVerifySmem = (kRepWords + 1024) * 4;
+constexpr uint32_t kVerifySmem = kRepSmem;
 
 __global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_block_verify(const BlockDesc* __restrict__ blocks,
                                                                        uint32_t n_blocks,
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_block_verify(const Blo
   load_rep_tables992(s_ver, s_ver + kRepWords, tabs);
   __syncthreads();
   const uint32_t lane = lane_id();
-  const uint32_t tl = smem_addr(s_ver) + lane * 4u, tz = smem_addr(s_ver + kRepWords);
+  const uint32_t tl = smem_addr(s_ver) + lane * 4u, tz = zcopy_addr(s_ver + kRepWords, lane);
   for (;;) {
     uint32_t g = 0;
     if (lane == 0) g = atomicAdd(next, 1u);

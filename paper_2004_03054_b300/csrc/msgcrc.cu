@@ -22,7 +22,7 @@ namespace {
 
 constexpr int kMsgWarps = 32;
 constexpr uint32_t kMsgMaxChunks = 64;
-constexpr uint32_t kMsgSmem = (kRepWords + 1024) * 4;
+constexpr uint32_t kMsgSmem = kRepSmem;
 
 __device__ __forceinline__ uint64_t msg_chunk(uint64_t n) {
   const uint64_t c = (n + kMsgMaxChunks - 1) / kMsgMaxChunks;
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kMsgWarps * 32, 1) k_msg_chunks(CrcMsg* __rest
   load_rep_tables992(s_msg, s_msg + kRepWords, tabs);
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t tl = smem_addr(s_msg) + lane * 4u, tz = smem_addr(s_msg + kRepWords);
+  const uint32_t tl = smem_addr(s_msg) + lane * 4u, tz = zcopy_addr(s_msg + kRepWords, lane);
   const uint64_t n_slots = uint64_t((count ? *count : 1u) * mult) * kMsgMaxChunks;
   const uint64_t warps = gstride() / 32;
   for (uint64_t w = gtid() / 32; w < n_slots; w += warps) {

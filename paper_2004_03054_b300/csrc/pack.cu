@@ -957,7 +957,7 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(Counts* __restrict__
 // Masked CRC-32C trailers of the blocks k_encode wrote (done[b] = 1): one warp per block,
 // the block re-read from global memory (mostly L2).
 constexpr int kCrcWarps = 32;
-constexpr uint32_t kCrcSmem = (kRepWords + 1024) * 4;
+constexpr uint32_t kCrcSmem = kRepSmem;
 
 __global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(Counts* __restrict__ cnt,
                                                                   const uint32_t* __restrict__ blk_file,
@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(Counts* __restr
   load_rep_tables992(s_crc, s_crc + kRepWords, tabs);
   __syncthreads();
   const uint32_t lane = lane_id();
-  const uint32_t tl = smem_addr(s_crc) + lane * 4u, tz = smem_addr(s_crc + kRepWords);
+  const uint32_t tl = smem_addr(s_crc) + lane * 4u, tz = zcopy_addr(s_crc + kRepWords, lane);
   for (;;) {
     uint32_t b = 0;
     if (lane == 0) b = atomicAdd(next, 1u);
