@@ -775,6 +775,13 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(Counts* __restrict__
       D.m = __shfl_sync(0xFFFFFFFFu, pre.m, src_lane);
       D.contents = __shfl_sync(0xFFFFFFFFu, pre.contents, src_lane);
       D.job = __shfl_sync(0xFFFFFFFFu, pre.job, src_lane);
+      // the block's first 32 entry descriptors start loading before the slot is free
+      EncDesc pd{};
+      uint32_t plcp = 0;
+      if ((D.job & 0x80000000u) == 0 && D.m <= kStgMaxEnt && lane < D.m) {
+        pd = ed[D.s0 + lane];
+        plcp = lcp[D.s0 + lane];
+      }
       if (j >= 2 && !mbar_wait(empty(sl), ((j >> 1) - 1) & 1u)) {
         if (lane == 0) report(errs + (D.job & 0x7FFFFFFFu), E_TIMEOUT, 0, b);
         break;
@@ -798,8 +805,8 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(Counts* __restrict__
         uint32_t esz = 0, ssz = 0, shr = 0, nsh = 0, vlen = 0, kc = 0;
         uint64_t kp = 0, vp = 0;
         if (k < m) {
-          const EncDesc d = ed[s0 + k];
-          shr = (k % R) == 0 ? 0u : lcp[s0 + k];
+          const EncDesc d = k0 == 0 ? pd : ed[s0 + k];
+          shr = (k % R) == 0 ? 0u : (k0 == 0 ? plcp : lcp[s0 + k]);
           nsh = d.klen - shr;
           vlen = d.vlen;
           kp = d.kptr + shr;
