@@ -28,6 +28,7 @@ ERR_NOT_SUPPORTED = -3
 ERR_OOM = -4
 ERR_DUPLICATE_KEY = -7
 F_STRICT_DUP = 1
+F_SHORT_INDEX = 4  # index keys shortened (format variant of R9)
 MAX_SEQ = (1 << 56) - 1
 
 
@@ -56,7 +57,7 @@ class _Read(C.Structure):
                 ("vals", C.POINTER(C.c_uint8)), ("voff", C.POINTER(C.c_uint64)), ("n", C.c_uint64),
                 ("n_blocks", C.c_uint64), ("blk_off", C.POINTER(C.c_uint64)),
                 ("blk_size", C.POINTER(C.c_uint64)), ("blk_last", C.POINTER(C.c_uint64)),
-                ("index_keys_ok", C.c_uint32), ("layout_ok", C.c_uint32),
+                ("index_keys_ok", C.c_uint32), ("index_keys_exact", C.c_uint32), ("layout_ok", C.c_uint32),
                 ("filter_off", C.c_uint64), ("filter_size", C.c_uint64)]
 
 
@@ -90,7 +91,7 @@ def lib():
                                   C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(C.POINTER(_Result))]
         L.ora_build.restype = C.c_int
         L.ora_build.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
+                                C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32,
                                 C.POINTER(C.POINTER(_Result))]
         L.ora_free_result.argtypes = [C.POINTER(_Result)]
         L.ora_read_table.restype = C.c_int
@@ -226,7 +227,7 @@ def compact(inputs, smallest_snapshot: int = MAX_SEQ, bottommost: bool = False, 
 
 
 def build_tables(run, block_size: int = 4096, restart_interval: int = 16, bloom_bits_per_key: int = 10,
-                 target_file_size: int = (1 << 64) - 1) -> Result:
+                 target_file_size: int = (1 << 64) - 1, flags: int = 0) -> Result:
     """Build tables from one sorted run (a ``workloads.Run``): the memtable-flush path."""
     ukeys = np.ascontiguousarray(run.ukeys, np.uint8)
     ukoff = np.ascontiguousarray(run.ukoff, np.uint64)
@@ -237,7 +238,7 @@ def build_tables(run, block_size: int = 4096, restart_interval: int = 16, bloom_
     res = C.POINTER(_Result)()
     rc = lib().ora_build(ukeys.ctypes.data, ukoff.ctypes.data, seqs.ctypes.data, types.ctypes.data,
                          vals.ctypes.data, voff.ctypes.data, len(seqs), block_size, restart_interval,
-                         bloom_bits_per_key, target_file_size, C.byref(res))
+                         bloom_bits_per_key, target_file_size, flags, C.byref(res))
     return _take(rc, res)
 
 
@@ -249,7 +250,8 @@ class ReadTable:
     blk_off: list
     blk_size: list
     blk_last: list
-    index_keys_ok: bool
+    index_keys_ok: bool       # every index key in [its block's last key, the next block's first key)
+    index_keys_exact: bool    # every index key equals its block's last key
     layout_ok: bool
     filter: bytes       # filter block contents (bitmap || k)
 
@@ -276,7 +278,7 @@ def read_table(data: bytes):
         blk_off=[int(t.blk_off[i]) for i in range(nb)],
         blk_size=[int(t.blk_size[i]) for i in range(nb)],
         blk_last=[int(t.blk_last[i]) for i in range(nb)],
-        index_keys_ok=bool(t.index_keys_ok), layout_ok=bool(t.layout_ok),
+        index_keys_ok=bool(t.index_keys_ok), index_keys_exact=bool(t.index_keys_exact), layout_ok=bool(t.layout_ok),
         filter=bytes(a[int(t.filter_off): int(t.filter_off) + int(t.filter_size)]),
     )
     L.ora_free_read(r)

@@ -41,6 +41,7 @@
 #define ORA_ERR_DUPLICATE_KEY (-7)
 
 #define ORA_F_STRICT_DUP 1u
+#define ORA_F_SHORT_INDEX 4u /* R9 variant: shortened index keys */
 
 #define ORA_MAGIC 0x4C55444153535431ull
 #define ORA_FOOTER 48
@@ -382,6 +383,10 @@ typedef struct {
   uint64_t fkcap;
   uint64_t n_entries;
   buf_t smallest, largest;
+  /* R9 variant: a flushed block's index entry waits for the next block's first key */
+  int short_index, pending;
+  buf_t pend_key;
+  uint64_t pend_off, pend_size;
   /* finished tables */
   ora_table* tables;
   uint32_t n_tables, cap_tables;
@@ -404,16 +409,65 @@ static int put_handle(buf_t* b, uint64_t off, uint64_t size) {
   return buf_put_varint(b, off) || buf_put_varint(b, size);
 }
 
+/* R9 with short index keys. For the last internal key `last` of a block (user key a) and,
+ * when another block of the same table follows, that block's first internal key `next`
+ * (user key b): let d be the first byte position where a and b differ (next == NULL: the
+ * first byte of a that is not 0xFF). If such a position exists, a[d] can be raised by one
+ * (below 0xFF; with a next key also still below b[d]) and d + 1 is shorter than a, the
+ * index key is a[0..d) || (a[d] + 1) followed by the trailer of the largest sequence
+ * number with type 1; otherwise it is `last` itself. Either way last <= key < next in the
+ * internal key order. */
+static int index_key(const uint8_t* last, uint64_t llen, const uint8_t* next, uint64_t nlen, buf_t* out) {
+  const uint64_t ua = llen - 8;
+  uint64_t d = 0;
+  int shorten = 0;
+  if (next) {
+    const uint64_t ub = nlen - 8, m = ua < ub ? ua : ub;
+    while (d < m && last[d] == next[d]) d++;
+    shorten = d < m && last[d] < 0xFF && last[d] + 1 < next[d] && d + 1 < ua;
+  } else {
+    while (d < ua && last[d] == 0xFF) d++;
+    shorten = d < ua && d + 1 < ua;
+  }
+  out->n = 0;
+  if (!shorten) return buf_put(out, last, llen);
+  const uint8_t up = (uint8_t)(last[d] + 1);
+  return buf_put(out, last, d) || buf_put(out, &up, 1) || buf_put_u64(out, ORA_MAX_SEQ << 8 | 1u);
+}
+
+static int tb_add_index(tb_t* tb, const uint8_t* key, uint64_t klen, uint64_t off, uint64_t size) {
+  buf_t h = {0};
+  int rc = put_handle(&h, off, size) || bb_add(&tb->index, key, klen, h.p, h.n);
+  free(h.p);
+  return rc;
+}
+
+/* The pending index entry, now that the next block's first key (or the end of the table,
+ * next == NULL) is known. */
+static int tb_resolve_index(tb_t* tb, const uint8_t* next, uint64_t nlen) {
+  if (!tb->pending) return 0;
+  tb->pending = 0;
+  buf_t k = {0};
+  int rc = index_key(tb->pend_key.p, tb->pend_key.n, next, nlen, &k) ||
+           tb_add_index(tb, k.p, k.n, tb->pend_off, tb->pend_size);
+  free(k.p);
+  return rc;
+}
+
 static int tb_flush_block(tb_t* tb) {
   uint64_t off, size;
   if (bb_finish(&tb->data)) return -1;
   if (write_block(&tb->file, tb->data.buf.p, tb->data.buf.n, &off, &size)) return -1;
-  /* Index entry: the block's last internal key, unshortened, and the block's handle. */
-  buf_t h = {0};
-  int rc = put_handle(&h, off, size) ||
-           bb_add(&tb->index, tb->data.last_key.p, tb->data.last_key.n, h.p, h.n);
-  free(h.p);
-  if (rc) return -1;
+  if (tb->short_index) {
+    tb->pending = 1;
+    tb->pend_key.n = 0;
+    tb->pend_off = off;
+    tb->pend_size = size;
+    if (buf_put(&tb->pend_key, tb->data.last_key.p, tb->data.last_key.n)) return -1;
+  } else if (tb_add_index(tb, tb->data.last_key.p, tb->data.last_key.n, off, size)) {
+    /* Index entry: the block's last internal key, unshortened, and the block's handle. */
+    return -1;
+  }
   return bb_reset(&tb->data);
 }
 
@@ -448,6 +502,7 @@ static int build_filter(tb_t* tb, buf_t* out) {
 
 static int tb_finish_file(tb_t* tb) {
   if (tb->data.n > 0 && tb_flush_block(tb)) return -1;
+  if (tb_resolve_index(tb, NULL, 0)) return -1;
   uint64_t foff, fsize, moff, msize, ioff, isize;
   buf_t f = {0};
   int rc = build_filter(tb, &f) || write_block(&tb->file, f.p, f.n, &foff, &fsize);
@@ -512,6 +567,7 @@ static int tb_add(tb_t* tb, const uint8_t* key, uint64_t klen, const uint8_t* va
     if (bb_reset(&tb->data) || bb_reset(&tb->index)) return -1;
     if (buf_put(&tb->smallest, key, klen)) return -1;
   }
+  if (tb_resolve_index(tb, key, klen)) return -1;
   if (bb_add(&tb->data, key, klen, val, vlen)) return -1;
   if (tb->n_entries + 2 > tb->fkcap) {
     uint64_t cap = tb->fkcap ? tb->fkcap * 2 : 1024;
@@ -539,6 +595,7 @@ static void tb_free(tb_t* tb) {
   free(tb->fkoff);
   free(tb->smallest.p);
   free(tb->largest.p);
+  free(tb->pend_key.p);
 }
 
 void ora_free_result(ora_result* r) {
@@ -561,8 +618,9 @@ static int check_opts(uint64_t T, uint32_t R, uint32_t bpk, uint64_t target) {
   return ORA_OK;
 }
 
-static void tb_init(tb_t* tb, uint64_t T, uint32_t R, uint32_t bpk, uint64_t target) {
+static void tb_init(tb_t* tb, uint64_t T, uint32_t R, uint32_t bpk, uint64_t target, uint32_t flags) {
   memset(tb, 0, sizeof *tb);
+  tb->short_index = (flags & ORA_F_SHORT_INDEX) != 0;
   tb->T = T;
   tb->R = R;
   tb->bpk = bpk;
@@ -796,13 +854,22 @@ static int decode_input(const uint8_t* f, uint64_t fsize, uint32_t input, ents_t
     const uint64_t before = es->n;
     rc = read_block(f, fsize, ic.off[b], ic.size[b], "data", input);
     if (rc == ORA_OK) rc = walk_block(f + ic.off[b], ic.size[b], &key, data_cb, &dc, "data", input, ic.off[b]);
-    /* R9: the index key of a data block is that block's last internal key */
+    /* R9: a data block's index key is at or above its last internal key, and the previous
+     * block's index key is below this block's first internal key */
     if (rc == ORA_OK) {
       const uint64_t k0 = b ? ic.kend[b - 1] : 0, kl = ic.kend[b] - k0;
       const ent_t* last = es->n > before ? &es->e[es->n - 1] : NULL;
-      if (!last || last->klen != kl || memcmp(es->keys.p + last->koff, ic.keys.p + k0, kl) != 0) {
-        detail("input %u: index key of data block %llu is not its last key", input, (unsigned long long)b);
+      if (!last || kl < 8 || cmp_internal(es->keys.p + last->koff, last->klen, ic.keys.p + k0, kl) > 0) {
+        detail("input %u: index key of data block %llu is below its last key", input, (unsigned long long)b);
         rc = ORA_ERR_CORRUPTION;
+      } else if (b > 0) {
+        const uint64_t p0 = b > 1 ? ic.kend[b - 2] : 0, pl = ic.kend[b - 1] - p0;
+        const ent_t* first = &es->e[before];
+        if (cmp_internal(ic.keys.p + p0, pl, es->keys.p + first->koff, first->klen) >= 0) {
+          detail("input %u: index key of data block %llu is not below the next block's first key", input,
+                 (unsigned long long)(b - 1));
+          rc = ORA_ERR_CORRUPTION;
+        }
       }
     }
   }
@@ -870,7 +937,7 @@ int ora_compact(const uint8_t* const* datas, const uint64_t* sizes, uint32_t n_i
     }
   }
   tb_t tb;
-  tb_init(&tb, block_size, restart_interval, bloom_bits_per_key, target_file_size);
+  tb_init(&tb, block_size, restart_interval, bloom_bits_per_key, target_file_size, flags);
   uint64_t dropped = 0;
   if (rc == ORA_OK) {
     const uint64_t INF = ~0ull;
@@ -925,7 +992,7 @@ int ora_compact(const uint8_t* const* datas, const uint64_t* sizes, uint32_t n_i
  * a type other than 0/1 is an invalid argument. */
 int ora_build(const uint8_t* ukeys, const uint64_t* ukoff, const uint64_t* seqs, const uint8_t* types,
               const uint8_t* vals, const uint64_t* voff, uint64_t n, uint64_t block_size, uint32_t restart_interval,
-              uint32_t bloom_bits_per_key, uint64_t target_file_size, ora_result** out) {
+              uint32_t bloom_bits_per_key, uint64_t target_file_size, uint32_t flags, ora_result** out) {
   g_detail[0] = 0;
   *out = NULL;
   int rc = check_opts(block_size, restart_interval, bloom_bits_per_key, target_file_size);
@@ -933,7 +1000,7 @@ int ora_build(const uint8_t* ukeys, const uint64_t* ukoff, const uint64_t* seqs,
   ora_result* res = (ora_result*)calloc(1, sizeof(ora_result));
   if (!res) return ORA_ERR_OOM;
   tb_t tb;
-  tb_init(&tb, block_size, restart_interval, bloom_bits_per_key, target_file_size);
+  tb_init(&tb, block_size, restart_interval, bloom_bits_per_key, target_file_size, flags);
   buf_t prev = {0}, cur = {0};
   for (uint64_t i = 0; rc == ORA_OK && i < n; i++) {
     if (seqs[i] > ORA_MAX_SEQ || types[i] > 1) {
@@ -990,7 +1057,8 @@ typedef struct {
   uint64_t* blk_off;   /* data block handles */
   uint64_t* blk_size;
   uint64_t* blk_last;  /* entry index of each block's last entry */
-  uint32_t index_keys_ok;   /* every index key equals its block's last key */
+  uint32_t index_keys_ok;   /* every index key lies in [its block's last key, the next block's first key) */
+  uint32_t index_keys_exact; /* every index key equals its block's last key */
   uint32_t layout_ok;       /* data blocks tile [0, filter) and the blocks follow in order */
   uint64_t filter_off, filter_size;
 } ora_read;
@@ -1102,7 +1170,7 @@ int ora_read_table(const uint8_t* f, uint64_t fsize, ora_read** out) {
   memset(&dc, 0, sizeof dc);
   uint64_t* blk_last = (uint64_t*)calloc(ri.ic.n + 1, sizeof(uint64_t));
   if (!r || !blk_last) rc = rc ? rc : ORA_ERR_OOM;
-  uint32_t keys_ok = 1, layout_ok = 1;
+  uint32_t keys_ok = 1, keys_exact = 1, layout_ok = 1;
   uint64_t expect = 0;
   for (uint64_t b = 0; rc == ORA_OK && b < ri.ic.n; b++) {
     if (ri.ic.off[b] != expect) layout_ok = 0;
@@ -1114,11 +1182,18 @@ int ora_read_table(const uint8_t* f, uint64_t fsize, ora_read** out) {
         rc = ORA_ERR_CORRUPTION;
         break;
       }
+      const uint64_t first = b ? blk_last[b - 1] + 1 : 0;
       blk_last[b] = dc.n - 1;
-      uint64_t lk = dc.koff[dc.n] - dc.koff[dc.n - 1];
-      if (lk != ri.lkoff[b + 1] - ri.lkoff[b] ||
-          memcmp(dc.keys.p + dc.koff[dc.n - 1], ri.lastkeys.p + ri.lkoff[b], lk) != 0)
-        keys_ok = 0;
+      const uint64_t lk = dc.koff[dc.n] - dc.koff[dc.n - 1], ik = ri.lkoff[b + 1] - ri.lkoff[b];
+      const uint8_t* ikey = ri.lastkeys.p + ri.lkoff[b];
+      if (lk != ik || memcmp(dc.keys.p + dc.koff[dc.n - 1], ikey, lk) != 0) keys_exact = 0;
+      if (ik < 8 || cmp_internal(dc.keys.p + dc.koff[dc.n - 1], lk, ikey, ik) > 0) keys_ok = 0;
+      if (b > 0) {
+        const uint64_t pk = ri.lkoff[b] - ri.lkoff[b - 1];
+        if (pk < 8 || cmp_internal(ri.lastkeys.p + ri.lkoff[b - 1], pk, dc.keys.p + dc.koff[first],
+                                   dc.koff[first + 1] - dc.koff[first]) >= 0)
+          keys_ok = 0;
+      }
     }
   }
   if (rc == ORA_OK) {
@@ -1159,6 +1234,7 @@ int ora_read_table(const uint8_t* f, uint64_t fsize, ora_read** out) {
   r->blk_size = ri.ic.size;
   r->blk_last = blk_last;
   r->index_keys_ok = keys_ok;
+  r->index_keys_exact = keys_exact;
   r->layout_ok = layout_ok;
   r->filter_off = mc.off;
   r->filter_size = mc.size;

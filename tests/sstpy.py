@@ -97,15 +97,24 @@ def read(buf: bytes):
     filt = block(buf, foff, fsize)
     blocks = []
     allents = []
-    for k, v, _ in index:
+    for i, (k, v, _) in enumerate(index):
         off, size, _ = handle(v)
         ents = entries(block(buf, off, size))
-        if ents[-1][0] != k:
-            raise ValueError("index key is not the block's last key")
+        # R9: last key <= index key < the next block's first key (internal key order)
+        if len(k) < 8 or _order(ents[-1][0]) > _order(k):
+            raise ValueError("index key is below its block's last key")
+        if blocks and _order(index[i - 1][0]) >= _order(ents[0][0]):
+            raise ValueError("index key is not below the next block's first key")
         blocks.append((off, size, ents))
         allents.extend((e[0], e[1]) for e in ents)
-    return dict(entries=allents, blocks=blocks, filter=filt,
+    return dict(entries=allents, blocks=blocks, filter=filt, index_keys=[k for k, _, _ in index],
                 handles=dict(filter=(foff, fsize), meta=(moff, msize), index=(ioff, isize)))
+
+
+def _order(ikey: bytes):
+    """Sort key of an internal key: user key ascending, then the trailer descending."""
+    (tr,) = struct.unpack("<Q", ikey[-8:])
+    return (ikey[:-8], -tr)
 
 
 def split_internal(ikey: bytes):

@@ -156,25 +156,37 @@ def test_out_of_order_input_is_corruption():
     assert res.status == oracle.ERR_CORRUPTION and "out of order" in res.detail
 
 
-def _single_block_table(contents, index_key):
-    """A minimal table around one data block's contents (filter empty-ish, valid CRCs);
-    index_key is the block's index entry key (the format wants its last internal key)."""
+def _table(blocks):
+    """A minimal table around data blocks [(contents, index_key)] (filter empty-ish, valid
+    CRCs); index_key is the block's index entry key."""
     def blk(c):
         return c + b"\x00" + struct.pack("<I", oracle.mask(oracle.crc32c(c + b"\x00")))
-    data = blk(contents)
+    data, handles = b"", []
+    for contents, _ in blocks:
+        handles.append(oracle.put_varint(len(data)) + oracle.put_varint(len(contents)))
+        data += blk(contents)
     filt_c = bytes(8) + b"\x06"
     filt_off = len(data)
     data += blk(filt_c)
     meta_c = oracle.encode_block([(b"filter.luda.bloom", oracle.put_varint(filt_off) + oracle.put_varint(len(filt_c)))], 1)
     meta_off = len(data)
     data += blk(meta_c)
-    idx_c = oracle.encode_block([(index_key, oracle.put_varint(0) + oracle.put_varint(len(contents)))], 1)
+    idx_c = oracle.encode_block([(k, h) for (_, k), h in zip(blocks, handles)], 1)
     idx_off = len(data)
     data += blk(idx_c)
     ft = (oracle.put_varint(meta_off) + oracle.put_varint(len(meta_c)) + oracle.put_varint(idx_off)
           + oracle.put_varint(len(idx_c)))
     ft = ft + bytes(40 - len(ft)) + struct.pack("<Q", 0x4C55444153535431)
     return data + ft
+
+
+def _single_block_table(contents, index_key):
+    """A minimal table around one data block's contents; index_key is its index entry key."""
+    return _table([(contents, index_key)])
+
+
+def _ik(user, seq=1, typ=1):
+    return user + struct.pack("<Q", seq << 8 | typ)
 
 
 def test_hand_made_table_is_valid():
@@ -186,14 +198,42 @@ def test_hand_made_table_is_valid():
     assert res.tables[0].n_entries == 2
 
 
-@pytest.mark.parametrize("index_key", [b"z" * 9, b"b" + struct.pack("<Q", 2 << 8 | 1), b"a" * 9, b"b" * 9])
-def test_index_key_must_be_last_key(index_key):
-    """R9: an index entry whose key is not its block's last internal key (checksums intact)
-    makes the table corrupt."""
-    contents = oracle.encode_block([(b"a" + struct.pack("<Q", 2 << 8 | 1), b"y"),
-                                    (b"b" + struct.pack("<Q", 1 << 8 | 1), b"x")], 16)
+@pytest.mark.parametrize("index_key", [_ik(b"b", 2), b"a" * 9, b"b" * 9, b"a", b""])
+def test_index_key_below_last_key_is_corrupt(index_key):
+    """R9: an index key below its block's last internal key (or not an internal key at all)
+    makes the table corrupt, checksums intact."""
+    contents = oracle.encode_block([(_ik(b"a", 2), b"y"), (_ik(b"b", 1), b"x")], 16)
     res = oracle.compact([_single_block_table(contents, index_key)])
     assert res.status == oracle.ERR_CORRUPTION and "index key" in res.detail
+
+
+@pytest.mark.parametrize("index_key", [_ik(b"b", 1), b"z" * 9, _ik(b"c", oracle.MAX_SEQ), _ik(b"b\x00", 9)])
+def test_index_key_at_or_above_last_key_is_valid(index_key):
+    """R9: any index key at or above the block's last key is valid for the table's last
+    block (shortened index keys are such keys)."""
+    contents = oracle.encode_block([(_ik(b"a", 2), b"y"), (_ik(b"b", 1), b"x")], 16)
+    res = oracle.compact([_single_block_table(contents, index_key)])
+    assert res.status == 0 and res.n_in_entries == 2
+    st, rt, _ = oracle.read_table(_single_block_table(contents, index_key))
+    assert st == 0 and rt.index_keys_ok and rt.index_keys_exact == (index_key == _ik(b"b", 1))
+
+
+@pytest.mark.parametrize("key0,ok", [(_ik(b"b", 1), True), (_ik(b"c", oracle.MAX_SEQ), True),
+                                     (_ik(b"d", oracle.MAX_SEQ), True), (_ik(b"d", 1), False),
+                                     (_ik(b"d", 0), False), (_ik(b"e", 5), False)])
+def test_index_key_must_stay_below_next_blocks_first_key(key0, ok):
+    """R9: the index key of a block that another block follows must lie below that block's
+    first internal key (d@1 here; d@MAX sorts before it, d@1 and d@0 do not)."""
+    b0 = oracle.encode_block([(_ik(b"a", 2), b"y"), (_ik(b"b", 1), b"x")], 16)
+    b1 = oracle.encode_block([(_ik(b"d", 1), b"u"), (_ik(b"e", 1), b"v")], 16)
+    img = _table([(b0, key0), (b1, _ik(b"e", 1))])
+    res = oracle.compact([img])
+    if ok:
+        assert res.status == 0 and res.n_in_entries == 4
+    else:
+        assert res.status == oracle.ERR_CORRUPTION and "index key" in res.detail
+    st, rt, _ = oracle.read_table(img)
+    assert st == 0 and rt.index_keys_ok == ok
 
 
 def test_duplicate_internal_key_across_inputs():
