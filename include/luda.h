@@ -55,6 +55,8 @@ typedef enum {
 
 /* options.flags */
 #define LUDA_F_STRICT_DUP 1u /* identical internal keys across inputs are an error */
+#define LUDA_F_SHORT_INDEX 4u /* write shortened index keys (format variant R9s: LevelDB's bytewise separator
+                                 and short successor); decoders accept either kind */
 #define LUDA_F_TRACE 2u      /* record per-stage device times (luda_outputs.stage_ms); LUDA_TRACE=1 in the
                                 environment does the same for every call. Stage boundaries always open
                                 NVTX ranges "luda/<stage>" on the calling thread. */

@@ -307,7 +307,7 @@ luda_status opts_check(const luda_options* o, Fmt* fmt) {
   uint32_t k = o->bloom_bits_per_key * 69 / 100;
   if (k < 1) k = 1;
   if (k > 30) k = 30;
-  *fmt = Fmt{o->block_size, o->restart_interval, o->bloom_bits_per_key, k, o->target_file_size};
+  *fmt = Fmt{o->block_size, o->restart_interval, o->bloom_bits_per_key, k, o->target_file_size, 0, o->flags};
   return LUDA_OK;
 }
 
@@ -455,7 +455,8 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   launch_compact_flags(b.fflags, b.fpos, &cnt->nb, cap, b.file_start, &cnt->nf, st);
   launch_job_files(jobs, n_jobs, b.fpos, st);
   launch_block_file(b.fpos, cnt, cap, b.blk_file, st);
-  launch_index_sizes(b.blk_start, b.bsz, b.C, b.blk_file, b.file_start, cnt, cap, b.surv, recs, b.ie, st);
+  launch_index_sizes(b.blk_start, b.bsz, b.C, b.blk_file, b.file_start, cnt, cap, b.surv, recs, arena, fmt, b.ie,
+                     st);
   CK((exclusive_scan<uint32_t, uint64_t>(b.ie, b.IX, cap, &cnt->nb, b.scan_tmp, st)));
   launch_file_layout(b.file_start, cnt, cap, b.blk_start, b.C, b.IX, fmt, jobs, n_jobs, b.files, b.fsize, b.bmw, st);
   CK((exclusive_scan<uint64_t, uint64_t>(b.fsize, b.foff, cap, &cnt->nf, b.scan_tmp, st)));
@@ -474,8 +475,8 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   launch_encode_big(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
                     fmt, out, out_cap, b.big, tabs, st);
   launch_bloom(b.ed, cnt, cap, b.files, fmt, b.bitmap, out_cap, bm_cap, st);
-  launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, out, out_cap,
-                     st);
+  launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, fmt, out,
+                     out_cap, st);
   launch_file_finish(b.files, cnt, cap, b.bitmap, b.surv, recs, fmt, out, out_cap, tabs, b.fmsg, b.meta, st);
   launch_key_lens(b.meta, cnt, cap, b.klens, st);
   CK((exclusive_scan<uint64_t, uint64_t>(b.klens, b.koff, cap, &cnt->nf, b.scan_tmp, st)));

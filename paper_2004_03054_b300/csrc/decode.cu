@@ -428,26 +428,6 @@ __global__ void __launch_bounds__(512) k_decode(const BlockDesc* __restrict__ bl
   }
 }
 
-// One thread per data block, after decode: the block's index key must equal its last
-// internal key (R9 of the format).
-__global__ void k_check_index(const BlockDesc* __restrict__ blocks, uint32_t n_blocks, const DInput* __restrict__ in,
-                              const uint32_t* __restrict__ nrec, const uint32_t* __restrict__ rec_first, Recs recs,
-                              const uint8_t* __restrict__ arena, DErr* errs) {
-  for (uint64_t g = gtid(); g < n_blocks; g += gstride()) {
-    const BlockDesc b = blocks[g];
-    if (b.ptr == nullptr || nrec[g] == 0 || *(volatile int32_t*)&errs[b.job].code != 0) continue;
-    const uint32_t last = rec_first[g] + nrec[g] - 1;
-    const uint32_t kl = recs.klen[last];
-    bool ok = kl == b.ilen;
-    const uint8_t* k = arena + recs.koff[last];
-    for (uint32_t i = 0; ok && i < kl; i += 8) {
-      const uint32_t avail = kl - i < 8 ? kl - i : 8u;
-      ok = key_word(k + i, avail) == key_word(b.ikey + i, avail);
-    }
-    if (!ok) report(errs + b.job, E_CORRUPT, in[b.input].local, b.off);
-  }
-}
-
 // Internal-key order of two full internal keys (user key bytes, proper prefix first, then
 // the trailer descending).
 __device__ int cmp_ikey_bytes(const uint8_t* a, uint32_t la, const uint8_t* b, uint32_t lb) {
@@ -462,9 +442,27 @@ __device__ int cmp_ikey_bytes(const uint8_t* a, uint32_t la, const uint8_t* b, u
   return ta == tb ? 0 : (ta > tb ? -1 : 1);
 }
 
+// R9: a data block's index key is an internal key at or above the block's last key, and
+// below the first key of the next data block of the same table.
+__global__ void k_check_index(const BlockDesc* __restrict__ blocks, uint32_t n_blocks, const DInput* __restrict__ in,
+                              const uint32_t* __restrict__ nrec, const uint32_t* __restrict__ rec_first, Recs recs,
+                              const uint8_t* __restrict__ arena, DErr* errs) {
+  for (uint64_t g = gtid(); g < n_blocks; g += gstride()) {
+    const BlockDesc b = blocks[g];
+    if (b.ptr == nullptr || nrec[g] == 0 || *(volatile int32_t*)&errs[b.job].code != 0) continue;
+    const uint32_t last = rec_first[g] + nrec[g] - 1;
+    bool ok = b.ilen >= 8 && cmp_ikey_bytes(arena + recs.koff[last], recs.klen[last], b.ikey, b.ilen) <= 0;
+    if (ok && g + 1 < n_blocks && blocks[g + 1].input == b.input && nrec[g + 1] > 0) {
+      const uint32_t first = rec_first[g + 1];
+      ok = cmp_ikey_bytes(b.ikey, b.ilen, arena + recs.koff[first], recs.klen[first]) < 0;
+    }
+    if (!ok) report(errs + b.job, E_CORRUPT, in[b.input].local, b.off);
+  }
+}
+
 // One thread per input: link[i] = 1 when input i + 1 belongs to the same job and all its
 // keys follow all of input i's (its first key, read from its first data block, is above
-// input i's last key, read from input i's last index entry). Linked inputs form one sorted
+// input i's last index key, which is at or above its last key). Linked inputs form one sorted
 // run for the merge. The index keys are checked against the data after decode, and each
 // input's own order by the order check, so a link never rests on an unchecked key.
 __global__ void k_run_links(const DInput* __restrict__ in, uint32_t n_inputs, const BlockDesc* __restrict__ blocks,

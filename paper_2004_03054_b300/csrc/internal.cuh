@@ -69,7 +69,7 @@ struct Fmt {
   uint32_t k;       // bloom probes
   uint64_t target;  // target file size
   uint32_t max_kv;  // largest internal key + value length of the inputs (0: unknown)
-  uint32_t pad;
+  uint32_t flags;   // luda_options.flags
 };
 
 // Device-side counts of the stages whose sizes only the device knows.
@@ -279,7 +279,7 @@ void launch_job_files(JobDev* jobs, uint32_t n_jobs, const uint32_t* fpos, cudaS
 void launch_block_file(const uint32_t* fpos, const Counts* cnt, uint32_t cap, uint32_t* blk_file, cudaStream_t st);
 void launch_index_sizes(const uint32_t* blk_start, const uint64_t* bsz, const uint64_t* C, const uint32_t* blk_file,
                         const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* surv, Recs recs,
-                        uint32_t* ie, cudaStream_t st);
+                        const uint8_t* arena, Fmt fmt, uint32_t* ie, cudaStream_t st);
 void launch_file_layout(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_start,
                         const uint64_t* C, const uint64_t* IX, Fmt fmt, const JobDev* jobs, uint32_t n_jobs,
                         FileDesc* files, uint64_t* fsize, uint64_t* bmwords, cudaStream_t st);
@@ -307,8 +307,8 @@ void launch_bloom(const EncDesc* ed, const Counts* cnt, uint32_t cap, const File
                   uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st);
 void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* bsz,
                         const uint64_t* C, const uint64_t* IX, const uint32_t* blk_file, const FileDesc* files,
-                        const uint32_t* surv, Recs recs, const uint8_t* arena, uint8_t* out, uint64_t out_cap,
-                        cudaStream_t st);
+                        const uint32_t* surv, Recs recs, const uint8_t* arena, Fmt fmt, uint8_t* out,
+                        uint64_t out_cap, cudaStream_t st);
 void launch_file_finish(const FileDesc* files, const Counts* cnt, uint32_t cap, const uint32_t* bitmap,
                         const uint32_t* surv, Recs recs, Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs,
                         CrcMsg* msgs, FileMeta* meta, cudaStream_t st);

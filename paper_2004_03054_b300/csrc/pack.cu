@@ -381,15 +381,73 @@ __global__ void k_block_file(const uint32_t* __restrict__ fpos, const Counts* __
   for (uint64_t b = gtid(); b < nb; b += gstride()) blk_file[b] = fpos[b + 1] - 1;
 }
 
+// R9s: the length L of block b's shortened index user key (its bytes are a[0..L-1) and
+// a[L-1] + 1, then the trailer of the largest sequence number with type put), or 0 when
+// the block keeps its full last key. a = user key of the block's last key (ua bytes); nb =
+// user key of the next block's first key in the same table (ub bytes), or nullptr for the
+// table's last block. The first differing byte is found 8 bytes at a time.
+__device__ uint32_t short_index_len(const uint8_t* a, uint32_t ua, const uint8_t* nb, uint32_t ub) {
+  if (nb) {
+    const uint32_t m = ua < ub ? ua : ub;
+    uint32_t d = m;
+    for (uint32_t i = 0; i < m; i += 8) {
+      const uint32_t avail = m - i < 8 ? m - i : 8u;
+      const uint64_t x = key_word(a + i, avail) ^ key_word(nb + i, avail);
+      if (x) {
+        d = i + (uint32_t(__clzll(x)) >> 3);
+        break;
+      }
+    }
+    return d < m && uint32_t(a[d]) + 1 < uint32_t(nb[d]) && d + 1 < ua ? d + 1 : 0u;
+  }
+  uint32_t d = 0;
+  while (d < ua && a[d] == 0xFF) ++d;
+  return d + 1 < ua ? d + 1 : 0u;
+}
+
+// Index key of block b: its length, and (with dst) its bytes.
+__device__ __forceinline__ uint32_t index_key_of(uint64_t b, uint32_t fb1, const uint32_t* __restrict__ start,
+                                                 const uint32_t* __restrict__ surv, const Recs& recs,
+                                                 const uint8_t* __restrict__ arena, uint32_t flags, uint8_t* dst) {
+  const uint32_t x = surv[start[b + 1] - 1];
+  const uint32_t klen = recs.klen[x];
+  const uint8_t* k = arena + recs.koff[x];
+  uint32_t L = 0;
+  if (flags & LUDA_F_SHORT_INDEX) {
+    const uint8_t* nk = nullptr;
+    uint32_t nl = 0;
+    if (b + 1 < fb1) {
+      const uint32_t y = surv[start[b + 1]];
+      nk = arena + recs.koff[y];
+      nl = recs.klen[y] - 8;
+    }
+    L = short_index_len(k, klen - 8, nk, nl);
+  }
+  if (!L) {
+    if (dst)
+      for (uint32_t t = 0; t < klen; ++t) dst[t] = k[t];
+    return klen;
+  }
+  if (dst) {
+    for (uint32_t t = 0; t + 1 < L; ++t) dst[t] = k[t];
+    dst[L - 1] = uint8_t(k[L - 1] + 1);
+    dst[L] = 1;  // trailer (2^56 - 1) << 8 | 1, little-endian
+    for (uint32_t t = 1; t < 8; ++t) dst[L + t] = 0xFF;
+  }
+  return L + 8;
+}
+
 __global__ void k_index_sizes(const uint32_t* __restrict__ start, const uint64_t* __restrict__ bsz,
                               const uint64_t* __restrict__ C, const uint32_t* __restrict__ blk_file,
                               const uint32_t* __restrict__ file_start, const Counts* __restrict__ cnt,
-                              const uint32_t* __restrict__ surv, Recs recs, uint32_t* __restrict__ ie) {
+                              const uint32_t* __restrict__ surv, Recs recs, const uint8_t* __restrict__ arena,
+                              uint32_t flags, uint32_t* __restrict__ ie) {
   const uint32_t nb = cnt->nb;
   for (uint64_t b = gtid(); b < nb; b += gstride()) {
-    const uint32_t fb0 = file_start[blk_file[b]];
+    const uint32_t f = blk_file[b];
+    const uint32_t fb0 = file_start[f], fb1 = file_start[f + 1];
     const uint64_t off = C[b] - C[fb0];
-    const uint32_t klen = recs.klen[surv[start[b + 1] - 1]];
+    const uint32_t klen = index_key_of(b, fb1, start, surv, recs, arena, flags, nullptr);
     const uint32_t hlen = varint_size(off) + varint_size(bsz[b]);
     ie[b] = 1 + varint_size(klen) + varint_size(hlen) + klen + hlen;
   }
@@ -1066,7 +1124,7 @@ __global__ void k_index_write(const uint32_t* __restrict__ start, const Counts* 
                               const uint64_t* __restrict__ C, const uint64_t* __restrict__ IX,
                               const uint32_t* __restrict__ blk_file, const FileDesc* __restrict__ files,
                               const uint32_t* __restrict__ surv, Recs recs, const uint8_t* __restrict__ arena,
-                              uint8_t* __restrict__ out, uint64_t out_cap) {
+                              uint32_t flags, uint8_t* __restrict__ out, uint64_t out_cap) {
   const uint32_t nb = cnt->nb;
   for (uint64_t b = gtid(); b < nb; b += gstride()) {
     const FileDesc F = files[blk_file[b]];
@@ -1074,16 +1132,14 @@ __global__ void k_index_write(const uint32_t* __restrict__ start, const Counts* 
     uint8_t* ib = out + F.off + F.index_off;
     const uint32_t fb0 = F.blk_begin, fb1 = F.blk_end;
     const uint64_t eoff = IX[b] - IX[fb0];
-    const uint32_t x = surv[start[b + 1] - 1];
-    const uint32_t klen = recs.klen[x];
+    const uint32_t klen = index_key_of(b, fb1, start, surv, recs, arena, flags, nullptr);
     const uint64_t off = C[b] - C[fb0], size = bsz[b];
     const uint32_t hlen = varint_size(off) + varint_size(size);
     uint8_t* p = ib + eoff;
     *p++ = 0;
     p += put_varint(p, klen);
     p += put_varint(p, hlen);
-    const uint8_t* k = arena + recs.koff[x];
-    for (uint32_t t = 0; t < klen; ++t) p[t] = k[t];
+    index_key_of(b, fb1, start, surv, recs, arena, flags, p);
     p += klen;
     p += put_varint(p, off);
     put_varint(p, size);
@@ -1329,9 +1385,11 @@ void launch_block_file(const uint32_t* fpos, const Counts* cnt, uint32_t cap, ui
 
 void launch_index_sizes(const uint32_t* blk_start, const uint64_t* bsz, const uint64_t* C, const uint32_t* blk_file,
                         const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* surv, Recs recs,
-                        uint32_t* ie, cudaStream_t st) {
+                        const uint8_t* arena, Fmt fmt, uint32_t* ie, cudaStream_t st) {
   if (!cap) return;
-  k_index_sizes<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(blk_start, bsz, C, blk_file, file_start, cnt, surv, recs, ie); count_launches(1);
+  k_index_sizes<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(blk_start, bsz, C, blk_file, file_start,
+                                                                           cnt, surv, recs, arena, fmt.flags, ie);
+  count_launches(1);
 }
 
 void launch_file_layout(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_start,
@@ -1416,11 +1474,12 @@ void launch_bloom(const EncDesc* ed, const Counts* cnt, uint32_t cap, const File
 
 void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* bsz,
                         const uint64_t* C, const uint64_t* IX, const uint32_t* blk_file, const FileDesc* files,
-                        const uint32_t* surv, Recs recs, const uint8_t* arena, uint8_t* out, uint64_t out_cap,
-                        cudaStream_t st) {
+                        const uint32_t* surv, Recs recs, const uint8_t* arena, Fmt fmt, uint8_t* out,
+                        uint64_t out_cap, cudaStream_t st) {
   if (!cap) return;
   k_index_write<<<grid_for(cap, 128), 128, 0, st>>>(blk_start, cnt, bsz, C, IX, blk_file, files, surv, recs, arena,
-                                                    out, out_cap); count_launches(1);
+                                                    fmt.flags, out, out_cap);
+  count_launches(1);
 }
 
 void launch_file_finish(const FileDesc* files, const Counts* cnt, uint32_t cap, const uint32_t* bitmap,

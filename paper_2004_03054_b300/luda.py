@@ -25,6 +25,7 @@ ERR_DUPLICATE_KEY = -7
 ERR_PLAN_MISMATCH = -8
 F_STRICT_DUP = 1
 F_TRACE = 2
+F_SHORT_INDEX = 4  # shortened index keys (format variant R9s)
 MAX_SEQ = (1 << 56) - 1
 
 

@@ -239,3 +239,51 @@ def test_skewed_runs(seed):
                                 level))
     job = W.Job(f"skew{seed}", seed, runs, W.MAX_SEQ, False, 4096, 16, 10, 1 << 20)
     check_job(job)
+
+
+# ---- format variant R9s: shortened index keys ------------------------------------------------
+@pytest.mark.parametrize("cfg,scale", [(1, 1 / 16), (2, 1 / 16), (3, 1 / 128)])
+def test_short_index_configs(cfg, scale):
+    job = W.make(cfg, scale=scale)
+    check_job(job, flags=luda.F_SHORT_INDEX)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_short_index_small_jobs(seed):
+    rng = np.random.default_rng(8000 + seed)
+    job = W.tiny_job(rng, n_keys=int(rng.integers(5, 400)), max_versions=4, n_inputs=int(rng.integers(1, 6)),
+                     key_len=(0, 20), val_len=(0, 300))
+    job.block_size = int(rng.choice([1, 64, 512, 4096]))
+    job.target_file_size = int(rng.choice([1, 3000, 1 << 20]))
+    check_job(job, flags=luda.F_SHORT_INDEX)
+
+
+def test_short_index_inputs_and_builder():
+    """Inputs whose index keys are shortened decode like any others; the device builder
+    writes R9s keys as the oracle's builder does."""
+    job = W.config1(seed=12, scale=1 / 32)
+    short = []
+    for r in job.inputs:
+        res = oracle.build_tables(r, job.block_size, job.restart_interval, job.bloom_bits_per_key, U64MAX,
+                                  flags=oracle.F_SHORT_INDEX)
+        short.append(res.tables[0].data)
+        got = luda.build_device(r, luda.options(job.block_size, job.restart_interval, job.bloom_bits_per_key,
+                                                U64MAX, flags=luda.F_SHORT_INDEX))
+        assert got.status == 0 and [t.cpu().numpy().tobytes() for t in got.tables] == [res.tables[0].data]
+    check_job(job, short)
+    check_job(job, short, flags=luda.F_SHORT_INDEX)
+
+
+@pytest.mark.parametrize("key0", [b"b" + struct.pack("<Q", 1 << 8 | 1), b"c" + struct.pack("<Q", (1 << 64) - 255),
+                                  b"d" + struct.pack("<Q", 1 << 8 | 1), b"d" + struct.pack("<Q", 1 << 8 | 0),
+                                  b"e" + struct.pack("<Q", 5 << 8 | 1), b"a" * 9, b"a"])
+def test_index_key_interval_check(key0):
+    from test_oracle_invariants import _table
+    b0 = oracle.encode_block([(b"a" + struct.pack("<Q", 2 << 8 | 1), b"y"), (b"b" + struct.pack("<Q", 1 << 8 | 1), b"x")],
+                             16)
+    b1 = oracle.encode_block([(b"d" + struct.pack("<Q", 1 << 8 | 1), b"u"), (b"e" + struct.pack("<Q", 1 << 8 | 1), b"v")],
+                             16)
+    img = _table([(b0, key0), (b1, b"e" + struct.pack("<Q", 1 << 8 | 1))])
+    job = W.Job("ikey2", 0, [], W.MAX_SEQ, False)
+    check_job(job, [img])
+    check_job(job, oracle_inputs(W.config1(seed=4, scale=1 / 128)) + [img])
