@@ -165,7 +165,8 @@ luda_status get_tabs(CrcTabs* out) {
 struct Side {
   int dev = -1;
   cudaStream_t s = nullptr;
-  cudaEvent_t ev[4] = {};
+  cudaEvent_t ev[5] = {};  // forks and joins: 0 input checksums, 1 their end, 2 trailers, 3 their end,
+                           // 4 index block checksums
 };
 thread_local Side t_side;
 
@@ -867,7 +868,14 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   DInput* hin_pin = static_cast<DInput*>(hs.take(sizeof(DInput) * (N + 1)));
   if (N)
     CK(cudaMemcpyAsync(d_in, pin(hin.data(), sizeof(DInput) * N), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
-  launch_footers(d_in, N, d_errs, d_msgs, tabs, st);
+  // the index blocks' checksums run on the side stream (their errors, like the data blocks',
+  // take precedence when the results are collected) while the host sizes the job
+  Side* side = nullptr;
+  if ((rc = get_side(&side))) return rc;
+  launch_footers_read(d_in, N, d_errs, d_msgs, st);
+  CK(fork_join(side, 4, st, side->s));
+  launch_index_crc(d_msgs, N, d_errs + n_jobs + 1, tabs, side->s);
+  launch_footers_finish(d_in, N, d_errs, st);
   CK(cudaGetLastError());
   if (N) CK(cudaMemcpyAsync(hin_pin ? hin_pin : hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -920,8 +928,6 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
 
   launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
   // input checksums on the side stream, joined before the results are collected
-  Side* side = nullptr;
-  if ((rc = get_side(&side))) return rc;
   CK(fork_join(side, 0, st, side->s));
   tr.mark(11, side->s);
   launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, false,
@@ -1577,7 +1583,10 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * 2 * (n_jobs + 1), st));
     CK(cudaMemsetAsync(d_cnt, 0, sizeof(Counts), st));
     CK(cudaMemcpyAsync(&d_cnt->n_rec, d_nrec_const, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
-    launch_footers(d_in, N, d_errs, d_msgs, tabs, st);
+    launch_footers_read(d_in, N, d_errs, d_msgs, st);
+    CK(fork_join(side, 4, st, side->s));
+    launch_index_crc(d_msgs, N, d_errs + n_jobs + 1, tabs, side->s);
+    launch_footers_finish(d_in, N, d_errs, st);
     launch_plan_checks(d_in, N, d_plan_nblk, d_errs, st);
     launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
     CK(fork_join(side, 0, st, side->s));

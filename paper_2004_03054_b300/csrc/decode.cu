@@ -556,13 +556,27 @@ void launch_plan_check_recs(const BlockDesc* blocks, uint32_t n_blocks, const ui
   count_launches(1);
 }
 
-void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs, CrcTabs tabs, cudaStream_t st) {
+void launch_footers_read(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs, cudaStream_t st) {
   if (!n_inputs) return;
   k_footers<<<grid_for(n_inputs, 128), 128, 0, st>>>(in, n_inputs, errs, msgs);
   count_launches(1);
+}
+
+void launch_index_crc(CrcMsg* msgs, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cudaStream_t st) {
+  if (!n_inputs) return;
   launch_msg_crc(msgs, nullptr, n_inputs, n_inputs, errs, tabs, st);
+}
+
+void launch_footers_finish(DInput* in, uint32_t n_inputs, DErr* errs, cudaStream_t st) {
+  if (!n_inputs) return;
   k_footers_finish<<<grid_for(n_inputs, 128), 128, 0, st>>>(in, n_inputs, errs);
   count_launches(1);
+}
+
+void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs, CrcTabs tabs, cudaStream_t st) {
+  launch_footers_read(in, n_inputs, errs, msgs, st);
+  launch_index_crc(msgs, n_inputs, errs, tabs, st);
+  launch_footers_finish(in, n_inputs, errs, st);
 }
 
 void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,

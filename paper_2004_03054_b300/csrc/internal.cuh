@@ -196,6 +196,12 @@ bool make_crc_tables(uint32_t* slice, uint32_t* shift);
 // ---- decode.cu ---------------------------------------------------------------------------
 // Footers and index block checksums of n_inputs tables; msgs: n_inputs entries of scratch.
 void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs, CrcTabs tabs, cudaStream_t st);
+// launch_footers in three parts, so that the index blocks' checksums can run on another
+// stream: the footers (queueing one checksum message per index block), the checksums,
+// and the index block counts.
+void launch_footers_read(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs, cudaStream_t st);
+void launch_index_crc(CrcMsg* msgs, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cudaStream_t st);
+void launch_footers_finish(DInput* in, uint32_t n_inputs, DErr* errs, cudaStream_t st);
 void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
                           BlockDesc* blocks, DErr* errs, cudaStream_t st);
 constexpr uint32_t kHdrMax = 64;  // entry offsets recorded per block for the decoder
