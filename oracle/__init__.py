@@ -62,6 +62,7 @@ class _Read(C.Structure):
 
 
 _lib = None
+_EMPTY = np.zeros(1, np.uint8)  # a valid address for an empty bound key
 
 
 def lib():
@@ -89,6 +90,10 @@ def lib():
         L.ora_compact.restype = C.c_int
         L.ora_compact.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32, C.c_uint64,
                                   C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(C.POINTER(_Result))]
+        L.ora_compact_range.restype = C.c_int
+        L.ora_compact_range.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32, C.c_uint64,
+                                        C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32, C.c_void_p, C.c_uint64,
+                                        C.c_void_p, C.c_uint64, C.POINTER(C.POINTER(_Result))]
         L.ora_build.restype = C.c_int
         L.ora_build.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32,
@@ -210,17 +215,24 @@ def _take(rc, res_p) -> Result:
 
 def compact(inputs, smallest_snapshot: int = MAX_SEQ, bottommost: bool = False, block_size: int = 4096,
             restart_interval: int = 16, bloom_bits_per_key: int = 10, target_file_size: int = 2 << 20,
-            flags: int = 0, timing: dict | None = None) -> Result:
+            flags: int = 0, timing: dict | None = None, lo: bytes | None = None, hi: bytes | None = None) -> Result:
     """Compact input tables (listed newest first) into new tables. When `timing` is a
-    dict, timing["seconds"] receives the wall time of the C call alone."""
+    dict, timing["seconds"] receives the wall time of the C call alone. lo / hi restrict
+    the compaction to the user keys [lo, hi) (R13; None = unbounded)."""
     arrs = [_u8(x) for x in inputs]
     ptrs = (C.c_void_p * max(1, len(arrs)))(*[a.ctypes.data for a in arrs])
     sizes = (C.c_uint64 * max(1, len(arrs)))(*[len(a) for a in arrs])
     res = C.POINTER(_Result)()
     L = lib()
     t0 = time.perf_counter()
-    rc = L.ora_compact(ptrs, sizes, len(arrs), smallest_snapshot, int(bool(bottommost)), block_size,
-                       restart_interval, bloom_bits_per_key, target_file_size, flags, C.byref(res))
+    lo_a = _u8(lo) if lo is not None else None
+    hi_a = _u8(hi) if hi is not None else None
+    rc = L.ora_compact_range(ptrs, sizes, len(arrs), smallest_snapshot, int(bool(bottommost)), block_size,
+                             restart_interval, bloom_bits_per_key, target_file_size, flags,
+                             (lo_a.ctypes.data if len(lo_a) else _EMPTY.ctypes.data) if lo_a is not None else None,
+                             len(lo_a) if lo_a is not None else 0,
+                             (hi_a.ctypes.data if len(hi_a) else _EMPTY.ctypes.data) if hi_a is not None else None,
+                             len(hi_a) if hi_a is not None else 0, C.byref(res))
     if timing is not None:
         timing["seconds"] = time.perf_counter() - t0
     return _take(rc, res)
@@ -289,3 +301,22 @@ def bloom_may_contain(filter_contents: bytes, ukey: bytes) -> bool:
     f = _u8(filter_contents)
     k = _u8(ukey)
     return bool(lib().ora_bloom_may_contain(f.ctypes.data, len(f), k.ctypes.data, len(k)))
+
+
+def subcompact(inputs, bounds, smallest_snapshot: int = MAX_SEQ, bottommost: bool = False, block_size: int = 4096,
+               restart_interval: int = 16, bloom_bits_per_key: int = 10, target_file_size: int = 2 << 20,
+               flags: int = 0) -> Result:
+    """R13 subcompactions: the job split at the strictly increasing user keys `bounds` into
+    len(bounds) + 1 ranged compactions, whose tables are concatenated in key order (entry
+    counts summed; the first failing range's status)."""
+    edges = [None] + list(bounds) + [None]
+    out = Result(0, [])
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        r = compact(inputs, smallest_snapshot, bottommost, block_size, restart_interval, bloom_bits_per_key,
+                    target_file_size, flags, lo=lo, hi=hi)
+        if r.status != 0:
+            return r
+        out.tables.extend(r.tables)
+        out.n_in_entries += r.n_in_entries
+        out.n_dropped += r.n_dropped
+    return out

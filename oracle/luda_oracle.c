@@ -840,7 +840,22 @@ bad:
 }
 
 /* Decode one input table into `es`, entries in file order; check strict key order. */
-static int decode_input(const uint8_t* f, uint64_t fsize, uint32_t input, ents_t* es) {
+/* A user-key range [lo, hi) of a ranged compaction (R13); a NULL bound is unbounded. */
+typedef struct {
+  const uint8_t* lo;
+  uint64_t lo_len;
+  const uint8_t* hi;
+  uint64_t hi_len;
+} range_t;
+
+static int in_range(const range_t* rg, const uint8_t* u, uint64_t n) {
+  if (!rg) return 1;
+  if (rg->lo && cmp_user(u, n, rg->lo, rg->lo_len) < 0) return 0;
+  if (rg->hi && cmp_user(u, n, rg->hi, rg->hi_len) >= 0) return 0;
+  return 1;
+}
+
+static int decode_input(const uint8_t* f, uint64_t fsize, uint32_t input, ents_t* es, const range_t* rg) {
   uint64_t moff, msize, ioff, isize;
   int rc = read_footer(f, fsize, input, &moff, &msize, &ioff, &isize);
   if (rc) return rc;
@@ -850,8 +865,24 @@ static int decode_input(const uint8_t* f, uint64_t fsize, uint32_t input, ents_t
   rc = walk_block(f + ioff, isize, &key, index_cb, &ic, "index", input, ioff);
   uint64_t first = es->n;
   data_ctx dc = {es, input, 0};
+  int prev_read = 0;
   for (uint64_t b = 0; rc == ORA_OK && b < ic.n; b++) {
     const uint64_t before = es->n;
+    /* R13: a ranged compaction reads block b only when it can hold keys of [lo, hi): its
+     * index key's user key is not below lo, and the previous block's is below hi */
+    if (rg) {
+      const uint64_t k0 = b ? ic.kend[b - 1] : 0, kl = ic.kend[b] - k0;
+      int rd = 1;
+      if (rg->lo && kl >= 8 && cmp_user(ic.keys.p + k0, kl - 8, rg->lo, rg->lo_len) < 0) rd = 0;
+      if (rd && b > 0 && rg->hi) {
+        const uint64_t p0 = b > 1 ? ic.kend[b - 2] : 0, pl = ic.kend[b - 1] - p0;
+        if (pl >= 8 && cmp_user(ic.keys.p + p0, pl - 8, rg->hi, rg->hi_len) >= 0) rd = 0;
+      }
+      if (!rd) {
+        prev_read = 0;
+        continue;
+      }
+    }
     rc = read_block(f, fsize, ic.off[b], ic.size[b], "data", input);
     if (rc == ORA_OK) rc = walk_block(f + ic.off[b], ic.size[b], &key, data_cb, &dc, "data", input, ic.off[b]);
     /* R9: a data block's index key is at or above its last internal key, and the previous
@@ -862,7 +893,7 @@ static int decode_input(const uint8_t* f, uint64_t fsize, uint32_t input, ents_t
       if (!last || kl < 8 || cmp_internal(es->keys.p + last->koff, last->klen, ic.keys.p + k0, kl) > 0) {
         detail("input %u: index key of data block %llu is below its last key", input, (unsigned long long)b);
         rc = ORA_ERR_CORRUPTION;
-      } else if (b > 0) {
+      } else if (b > 0 && prev_read) {
         const uint64_t p0 = b > 1 ? ic.kend[b - 2] : 0, pl = ic.kend[b - 1] - p0;
         const ent_t* first = &es->e[before];
         if (cmp_internal(ic.keys.p + p0, pl, es->keys.p + first->koff, first->klen) >= 0) {
@@ -872,6 +903,7 @@ static int decode_input(const uint8_t* f, uint64_t fsize, uint32_t input, ents_t
         }
       }
     }
+    prev_read = 1;
   }
   free(ic.off);
   free(ic.size);
@@ -905,9 +937,12 @@ static int cmp_entry(const void* va, const void* vb) {
   return a->pos < b->pos ? -1 : (a->pos > b->pos ? 1 : 0);
 }
 
-int ora_compact(const uint8_t* const* datas, const uint64_t* sizes, uint32_t n_inputs, uint64_t smallest_snapshot,
-                int32_t bottommost, uint64_t block_size, uint32_t restart_interval, uint32_t bloom_bits_per_key,
-                uint64_t target_file_size, uint32_t flags, ora_result** out) {
+int ora_compact_range(const uint8_t* const* datas, const uint64_t* sizes, uint32_t n_inputs,
+                      uint64_t smallest_snapshot, int32_t bottommost, uint64_t block_size, uint32_t restart_interval,
+                      uint32_t bloom_bits_per_key, uint64_t target_file_size, uint32_t flags, const uint8_t* lo,
+                      uint64_t lo_len, const uint8_t* hi, uint64_t hi_len, ora_result** out) {
+  range_t range = {lo, lo_len, hi, hi_len};
+  const range_t* rg = (lo || hi) ? &range : NULL;
   g_detail[0] = 0;
   *out = NULL;
   int rc = check_opts(block_size, restart_interval, bloom_bits_per_key, target_file_size);
@@ -916,7 +951,7 @@ int ora_compact(const uint8_t* const* datas, const uint64_t* sizes, uint32_t n_i
   ents_t es;
   memset(&es, 0, sizeof es);
   /* Phase 1: unpack every input. */
-  for (uint32_t i = 0; rc == ORA_OK && i < n_inputs; i++) rc = decode_input(datas[i], sizes[i], i, &es);
+  for (uint32_t i = 0; rc == ORA_OK && i < n_inputs; i++) rc = decode_input(datas[i], sizes[i], i, &es, rg);
   ora_result* res = (ora_result*)calloc(1, sizeof(ora_result));
   if (!res && rc == ORA_OK) rc = ORA_ERR_OOM;
   /* Phase 2: sort all pairs in the total order, then drop stale versions and, at the
@@ -953,7 +988,8 @@ int ora_compact(const uint8_t* const* datas, const uint64_t* sizes, uint32_t n_i
       uint64_t seq = tr >> 8;
       int is_del = (tr & 0xFF) == 0;
       int drop = 0;
-      if (last_seq != INF && last_seq <= smallest_snapshot) drop = 1;
+      if (!in_range(rg, k, e->klen - 8)) drop = 1; /* R13: only keys of the range are written */
+      else if (last_seq != INF && last_seq <= smallest_snapshot) drop = 1;
       else if (is_del && seq <= smallest_snapshot && bottommost) drop = 1;
       last_seq = seq;
       if (drop) {
@@ -984,6 +1020,13 @@ int ora_compact(const uint8_t* const* datas, const uint64_t* sizes, uint32_t n_i
   }
   *out = res;
   return ORA_OK;
+}
+
+int ora_compact(const uint8_t* const* datas, const uint64_t* sizes, uint32_t n_inputs, uint64_t smallest_snapshot,
+                int32_t bottommost, uint64_t block_size, uint32_t restart_interval, uint32_t bloom_bits_per_key,
+                uint64_t target_file_size, uint32_t flags, ora_result** out) {
+  return ora_compact_range(datas, sizes, n_inputs, smallest_snapshot, bottommost, block_size, restart_interval,
+                           bloom_bits_per_key, target_file_size, flags, NULL, 0, NULL, 0, out);
 }
 
 /* Build tables from entries the caller already sorted (a memtable flush): user keys,
