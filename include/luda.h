@@ -175,7 +175,20 @@ typedef struct {
   int32_t level;
   uint64_t smallest_snapshot;
   int32_t bottommost;
+  /* Optional user-key range [range_lo, range_hi) (format rule R13; host pointers, NULL =
+   * unbounded): the job reads only the data blocks that can hold keys of the range and
+   * writes only those keys. Not supported by plans (luda_plan_create rejects it). */
+  const uint8_t* range_lo;
+  uint32_t range_lo_len;
+  const uint8_t* range_hi;
+  uint32_t range_hi_len;
 } luda_job;
+
+/* A user key (host memory). */
+typedef struct {
+  const uint8_t* data;
+  uint32_t len;
+} luda_key;
 
 /* Compacts n_jobs jobs together: every kernel of the pipeline runs once over all jobs'
  * work. outs[j] receives job j's tables (device pointers) and status; a corrupt job fails
@@ -183,6 +196,16 @@ typedef struct {
  * that stopped the whole batch. */
 LUDA_API luda_status luda_batch_compact_device(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts,
                                       luda_outputs* outs);
+
+/* ---- subcompactions (format rule R13) --------------------------------------------------
+ * One job split at the strictly increasing user keys bounds[0..n_bounds) into n_bounds + 1
+ * ranged jobs, run together as one batch; *out receives their tables concatenated in key
+ * order (device pointers, as luda_compact_device), n_in_entries and n_dropped summed, and
+ * the first failing range's status. The entries written are exactly those of the whole
+ * job; only the file cut differs (each range starts its own tables). */
+LUDA_API luda_status luda_subcompact_device(const luda_input* inputs, uint32_t n_inputs, int32_t level,
+                                            uint64_t smallest_snapshot, const luda_key* bounds, uint32_t n_bounds,
+                                            const luda_options* opts, luda_outputs* out);
 
 /* ---- plans: a batch sized once, captured in a CUDA graph, replayed --------------------
  * luda_plan_create runs the sizing pass on the jobs' device inputs, allocates every

@@ -90,7 +90,7 @@ def coordinate_search(measure, space: dict | None = None, start: dict | None = N
 def signature(jobs, opts: luda.Options) -> str:
     """What the cached tuning depends on: the format options and the batch's rough size."""
     n_jobs = max(1, len(jobs))
-    nbytes = max(1, sum(int(t.numel()) for inputs, _, _ in jobs for t in inputs))
+    nbytes = max(1, sum(int(t.numel()) for job in jobs for t in job[0]))
     return (f"T{opts.block_size}-R{opts.restart_interval}-bpk{opts.bloom_bits_per_key}-"
             f"tgt{opts.target_file_size}-jobs2^{round(math.log2(n_jobs))}-bytes2^{round(math.log2(nbytes))}")
 

@@ -647,7 +647,20 @@ struct HostJob {
   uint32_t n_inputs;
   uint64_t snapshot;
   int32_t bottommost;
+  const uint8_t* lo = nullptr;  // user-key range [lo, hi) (R13), host memory; null = unbounded
+  uint32_t lo_len = 0;
+  const uint8_t* hi = nullptr;
+  uint32_t hi_len = 0;
 };
+
+HostJob host_job(const luda_job& j) {
+  HostJob h{j.inputs, j.n_inputs, j.smallest_snapshot, j.bottommost};
+  h.lo = j.range_lo;
+  h.lo_len = j.range_lo ? j.range_lo_len : 0;
+  h.hi = j.range_hi;
+  h.hi_len = j.range_hi ? j.range_hi_len : 0;
+  return h;
+}
 
 struct Timer {
   cudaEvent_t a = nullptr, b = nullptr;
@@ -823,29 +836,56 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   job_in_first[n_jobs] = uint32_t(hin.size());
   const uint32_t N = uint32_t(hin.size());
 
+  // ranged jobs (R13): one JobRange per job and the bound keys back to back
+  std::vector<JobRange> hranges;
+  std::vector<uint8_t> hbounds;
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    JobRange r{};
+    if (jobs[j].lo) {
+      r.flags |= 1u;
+      r.lo_off = uint32_t(hbounds.size());
+      r.lo_len = jobs[j].lo_len;
+      hbounds.insert(hbounds.end(), jobs[j].lo, jobs[j].lo + jobs[j].lo_len);
+    }
+    if (jobs[j].hi) {
+      r.flags |= 2u;
+      r.hi_off = uint32_t(hbounds.size());
+      r.hi_len = jobs[j].hi_len;
+      hbounds.insert(hbounds.end(), jobs[j].hi, jobs[j].hi + jobs[j].hi_len);
+    }
+    hranges.push_back(r);
+  }
+  const bool ranged = !hbounds.empty() || std::any_of(hranges.begin(), hranges.end(),
+                                                      [](const JobRange& r) { return r.flags != 0; });
   Layout LA;
-  DInput* d_in = LA.take<DInput>(N + 1);
-  DErr* d_errs = LA.take<DErr>(2 * (n_jobs + 1));  // main chain, then input checksums
-  JobDev* d_jobs = LA.take<JobDev>(n_jobs + 1);
-  uint32_t* d_in_blk_first = LA.take<uint32_t>(N + 1);
-  Counts* d_cnt = LA.take<Counts>(1);
-  CrcMsg* d_msgs = LA.take<CrcMsg>(N + 1);
-  uint8_t* d_link = LA.take<uint8_t>(N + 1);
+  DInput* d_in;
+  DErr* d_errs;
+  JobDev* d_jobs;
+  uint32_t* d_in_blk_first;
+  Counts* d_cnt;
+  CrcMsg* d_msgs;
+  uint8_t* d_link;
+  JobRange* d_ranges = nullptr;
+  uint8_t* d_bounds = nullptr;
+  auto layA = [&](Layout& L) {
+    d_in = L.take<DInput>(N + 1);
+    d_errs = L.take<DErr>(2 * (n_jobs + 1));  // main chain, then input checksums
+    d_jobs = L.take<JobDev>(n_jobs + 1);
+    d_in_blk_first = L.take<uint32_t>(N + 1);
+    d_cnt = L.take<Counts>(1);
+    d_msgs = L.take<CrcMsg>(N + 1);
+    d_link = L.take<uint8_t>(N + 1);
+    if (ranged) {
+      d_ranges = L.take<JobRange>(n_jobs + 1);
+      d_bounds = L.take<uint8_t>(hbounds.size() + 32);  // word reads may pass the last key
+    }
+  };
+  layA(LA);
   uint8_t* bufA = static_cast<uint8_t*>(mem.get(LA.off));
   if (!bufA) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
-  {
-    const size_t used = LA.off;
-    LA = Layout{};
-    LA.base = bufA;
-    d_in = LA.take<DInput>(N + 1);
-    d_errs = LA.take<DErr>(2 * (n_jobs + 1));
-    d_jobs = LA.take<JobDev>(n_jobs + 1);
-    d_in_blk_first = LA.take<uint32_t>(N + 1);
-    d_cnt = LA.take<Counts>(1);
-    d_msgs = LA.take<CrcMsg>(N + 1);
-    d_link = LA.take<uint8_t>(N + 1);
-    (void)used;
-  }
+  LA = Layout{};
+  LA.base = bufA;
+  layA(LA);
   struct Guard {
     const DevMem& m;
     std::vector<void*> ps;
@@ -865,6 +905,12 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   };
   CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * 2 * (n_jobs + 1), st));
   CK(cudaMemsetAsync(d_cnt, 0, sizeof(Counts), st));
+  if (ranged) {
+    CK(cudaMemcpyAsync(d_ranges, pin(hranges.data(), sizeof(JobRange) * n_jobs), sizeof(JobRange) * n_jobs,
+                       cudaMemcpyHostToDevice, st));
+    if (!hbounds.empty())
+      CK(cudaMemcpyAsync(d_bounds, pin(hbounds.data(), hbounds.size()), hbounds.size(), cudaMemcpyHostToDevice, st));
+  }
   DInput* hin_pin = static_cast<DInput*>(hs.take(sizeof(DInput) * (N + 1)));
   if (N)
     CK(cudaMemcpyAsync(d_in, pin(hin.data(), sizeof(DInput) * N), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
@@ -926,7 +972,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   LB.base = bufB;
   layoutB(LB, d_blocks, d_nrec, d_kbytes, d_rec_first, d_key_first, d_in_rec, d_in_key, d_tmpB);
 
-  launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
+  launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st, d_ranges, d_bounds);
   // input checksums on the side stream, joined before the results are collected
   CK(fork_join(side, 0, st, side->s));
   tr.mark(11, side->s);
@@ -1082,7 +1128,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
                       d_pfx1, recs, d_arena, st);
   uint32_t* src_o = ms.final_buf ? d_ord1 : d_ord0;
   tr.mark(6, st);
-  launch_gc_flags(src_o, n_rec, d_jobs, n_jobs, recs, d_arena, d_keep, d_errs, st);
+  launch_gc_flags(src_o, n_rec, d_jobs, n_jobs, recs, d_arena, d_keep, d_errs, st, d_ranges, d_bounds);
   CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
   launch_gc_compact(src_o, d_keep, d_pos, n_rec, pb.surv, st);
   launch_job_surv(d_jobs, n_jobs, d_pos, n_rec, d_cnt, st);
@@ -1370,6 +1416,11 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   Fmt fmt;
   luda_status rc = opts_check(o, &fmt);
   if (rc) return rc;
+  for (uint32_t j = 0; j < n_jobs; ++j)
+    if (jobs[j].range_lo || jobs[j].range_hi) {
+      set_detail("job %u: ranged jobs are not supported in plans", j);
+      return LUDA_ERR_INVALID_ARG;
+    }
   const TuningScope tuned(o->tuning);
   CrcTabs tabs;
   if ((rc = get_tabs(&tabs))) return rc;
@@ -1684,7 +1735,8 @@ luda_status luda::compact_job_host(const luda_job& job, const luda_options* opts
     cudaStreamSynchronize(st);
     gate->copy_end(0);
   }
-  HostJob hj{din.data(), n_inputs, job.smallest_snapshot, job.bottommost};
+  HostJob hj = host_job(job);
+  hj.inputs = din.data();
   double ms = 0, d2h = 0;
   double sms[LUDA_N_STAGES] = {};
   uint64_t sbytes[LUDA_N_STAGES] = {};
@@ -1718,7 +1770,7 @@ luda_status luda::compact_job_device(const luda_job& job, const luda_options* op
     set_detail("NULL argument");
     return LUDA_ERR_INVALID_ARG;
   }
-  HostJob hj{job.inputs, job.n_inputs, job.smallest_snapshot, job.bottommost};
+  HostJob hj = host_job(job);
   const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
   double ms = 0;
   luda_status rc = run_compaction(&hj, 1, opts, st, out, false, &ms, nullptr, out->stage_ms, out->stage_bytes, gate);
@@ -1789,8 +1841,7 @@ luda_status luda_batch_compact_device(const luda_job* jobs, uint32_t n_jobs, con
     return LUDA_ERR_INVALID_ARG;
   }
   std::vector<HostJob> hj(n_jobs);
-  for (uint32_t j = 0; j < n_jobs; ++j) hj[j] = HostJob{jobs[j].inputs, jobs[j].n_inputs, jobs[j].smallest_snapshot,
-                                                        jobs[j].bottommost};
+  for (uint32_t j = 0; j < n_jobs; ++j) hj[j] = host_job(jobs[j]);
   const cudaStream_t st = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
   double ms = 0;
   luda_status rc = run_compaction(hj.data(), n_jobs, opts, st, outs, false, &ms, nullptr);
@@ -1799,6 +1850,103 @@ luda_status luda_batch_compact_device(const luda_job* jobs, uint32_t n_jobs, con
     outs[j].ms_device = ms;
   }
   return rc;
+}
+
+luda_status luda_subcompact_device(const luda_input* inputs, uint32_t n_inputs, int32_t level,
+                                   uint64_t smallest_snapshot, const luda_key* bounds, uint32_t n_bounds,
+                                   const luda_options* opts, luda_outputs* out) {
+  (void)level;
+  t_detail[0] = 0;
+  if (!out || (!inputs && n_inputs) || (!bounds && n_bounds) || !opts) {
+    set_detail("NULL argument");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  memset(out, 0, sizeof *out);
+  for (uint32_t b = 0; b < n_bounds; ++b) {
+    if (!bounds[b].data && bounds[b].len) {
+      set_detail("bound %u: data is NULL", b);
+      return LUDA_ERR_INVALID_ARG;
+    }
+    if (b > 0) {
+      const luda_key& x = bounds[b - 1];
+      const luda_key& y = bounds[b];
+      const uint32_t m = std::min(x.len, y.len);
+      const int c = m ? memcmp(x.data, y.data, m) : 0;
+      if (c > 0 || (c == 0 && x.len >= y.len)) {
+        set_detail("bounds %u and %u are not strictly increasing", b - 1, b);
+        return LUDA_ERR_INVALID_ARG;
+      }
+    }
+  }
+  static const uint8_t kEmpty = 0;
+  const uint32_t K = n_bounds + 1;
+  std::vector<HostJob> hj(K);
+  for (uint32_t r = 0; r < K; ++r) {
+    hj[r] = HostJob{inputs, n_inputs, smallest_snapshot, opts->bottommost};
+    if (r > 0) {
+      hj[r].lo = bounds[r - 1].len ? bounds[r - 1].data : &kEmpty;
+      hj[r].lo_len = bounds[r - 1].len;
+    }
+    if (r + 1 < K) {
+      hj[r].hi = bounds[r].len ? bounds[r].data : &kEmpty;
+      hj[r].hi_len = bounds[r].len;
+    }
+  }
+  std::vector<luda_outputs> outs(K);
+  const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+  double ms = 0;
+  luda_status rc = run_compaction(hj.data(), K, opts, st, outs.data(), false, &ms, nullptr);
+  if (rc) {
+    out->status = rc;
+    return rc;
+  }
+  // one result: the ranges' tables in key order; their keys are copied into one buffer and
+  // the device tables stay owned by the ranges' shared holder
+  luda_status first = LUDA_OK;
+  uint32_t nt = 0;
+  uint64_t kb = 0;
+  for (const luda_outputs& o : outs) {
+    if (o.status && !first) first = luda_status(o.status);
+    out->n_in_entries += o.n_in_entries;
+    out->n_dropped += o.n_dropped;
+    nt += o.n_tables;
+    for (uint32_t t = 0; t < o.n_tables; ++t) kb += o.tables[t].smallest_len + o.tables[t].largest_len;
+  }
+  if (first) {
+    for (luda_outputs& o : outs) luda_outputs_free(&o);
+    memset(out, 0, sizeof *out);
+    out->status = first;
+    return first;
+  }
+  out->tables = static_cast<luda_table*>(calloc(nt ? nt : 1, sizeof(luda_table)));
+  uint8_t* keys = static_cast<uint8_t*>(malloc(kb ? kb : 1));
+  Holder* holder = nullptr;
+  uint64_t kp = 0;
+  for (luda_outputs& o : outs) {
+    OutPriv* p = static_cast<OutPriv*>(o._priv);
+    if (p && !holder) {
+      holder = p->holder;
+      ++holder->refs;
+    }
+    for (uint32_t t = 0; t < o.n_tables; ++t) {
+      luda_table tb = o.tables[t];
+      memcpy(keys + kp, tb.smallest, tb.smallest_len);
+      tb.smallest = keys + kp;
+      kp += tb.smallest_len;
+      memcpy(keys + kp, tb.largest, tb.largest_len);
+      tb.largest = keys + kp;
+      kp += tb.largest_len;
+      out->tables[out->n_tables++] = tb;
+    }
+    luda_outputs_free(&o);
+  }
+  if (holder) {
+    out->_priv = new OutPriv{holder, keys};
+  } else {
+    free(keys);
+  }
+  out->ms_device = ms;
+  return LUDA_OK;
 }
 
 luda_status luda_compact_device(const luda_input* inputs, uint32_t n_inputs, int32_t level, uint64_t smallest_snapshot,

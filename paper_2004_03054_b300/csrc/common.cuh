@@ -153,6 +153,18 @@ __device__ __forceinline__ uint64_t le_word(const uint8_t* p) {
   return sh ? (w >> sh) | (q[1] << (64 - sh)) : w;
 }
 
+// Order of two user keys (memcmp over the common length, a proper prefix first); reads
+// whole aligned 8-byte words around the keys (both buffers readable to 16 bytes past).
+__device__ __forceinline__ int cmp_user_keys(const uint8_t* a, uint32_t la, const uint8_t* b, uint32_t lb) {
+  const uint32_t m = la < lb ? la : lb;
+  for (uint32_t i = 0; i < m; i += 8) {
+    const uint32_t avail = m - i < 8 ? m - i : 8u;
+    const uint64_t wa = key_word(a + i, avail), wb = key_word(b + i, avail);
+    if (wa != wb) return wa < wb ? -1 : 1;
+  }
+  return la == lb ? 0 : (la < lb ? -1 : 1);
+}
+
 // Internal key order from byte `from` of the user keys on, given that the bytes before it
 // are equal (zero-padded): user key bytes (8 at a time), proper prefix first, then trailer
 // descending, then record id ascending (input index, then position; 0 for a == b).

@@ -79,11 +79,40 @@ __global__ void k_footers_finish(DInput* in, uint32_t n_inputs, DErr* errs) {
   }
 }
 
-// One thread per data block: its index entry (restart interval 1, so every entry starts
-// a restart segment and all decode independently) gives the block handle.
+// Index entry k of input d (restart interval 1, so every entry starts a restart segment
+// and all decode independently): its key and block handle; false when malformed.
+__device__ bool index_entry(const DInput& d, uint32_t k, const uint8_t** key, uint32_t* klen, uint64_t* off,
+                            uint64_t* size) {
+  const uint8_t* ib = d.data + d.idx_off;
+  const uint64_t rstart = d.idx_size - 4 - 4ull * d.nblk;
+  const uint64_t s = ld_u32(ib + rstart + 4ull * k);
+  const uint64_t e = k + 1 < d.nblk ? ld_u32(ib + rstart + 4ull * (k + 1)) : rstart;
+  if ((k == 0 && s != 0) || s >= e || e > rstart) return false;
+  const uint8_t* p = ib + s;
+  const uint8_t* end = ib + e;
+  uint64_t shared = 0, nonshared = 0, vlen = 0;
+  uint32_t a = get_varint<32>(p, end, &shared);
+  if (a) a = (p += a, get_varint<32>(p, end, &nonshared));
+  if (a) a = (p += a, get_varint<32>(p, end, &vlen));
+  if (a) p += a;
+  if (!(a && shared == 0 && nonshared <= uint64_t(end - p) && vlen <= uint64_t(end - p) - nonshared)) return false;
+  *key = p;
+  *klen = uint32_t(nonshared);
+  p += nonshared;
+  if (p + vlen != end) return false;
+  const uint8_t* vend = p + vlen;
+  uint32_t b = get_varint<64>(p, vend, off);
+  if (b) b = (p += b, get_varint<64>(p, vend, size));
+  return b && p + b == vend && handle_ok(*off, *size, d.size - kFooter);
+}
+
+// One thread per data block: its index entry gives the block handle. A block of a ranged
+// job (R13) that cannot hold keys of the range (its index key's user key is below lo, or
+// the previous block's is at or above hi) is left unread (null ptr).
 __global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs,
                                 const uint32_t* __restrict__ in_blk_first, uint32_t n_blocks,
-                                BlockDesc* __restrict__ blocks, DErr* errs) {
+                                BlockDesc* __restrict__ blocks, DErr* errs, const JobRange* __restrict__ ranges,
+                                const uint8_t* __restrict__ bounds) {
   for (uint64_t g = gtid(); g < n_blocks; g += gstride()) {
     uint32_t lo = 0, hi = n_inputs;  // last input with blk_first <= g
     while (hi - lo > 1) {
@@ -99,41 +128,33 @@ __global__ void k_index_entries(const DInput* __restrict__ in, uint32_t n_inputs
       blocks[g] = out;
       continue;
     }
-    const uint8_t* ib = d.data + d.idx_off;
-    const uint64_t rstart = d.idx_size - 4 - 4ull * d.nblk;
-    const uint64_t s = ld_u32(ib + rstart + 4ull * k);
-    const uint64_t e = k + 1 < d.nblk ? ld_u32(ib + rstart + 4ull * (k + 1)) : rstart;
-    bool ok = !(k == 0 && s != 0) && s < e && e <= rstart;
-    if (ok) {
-      const uint8_t* p = ib + s;
-      const uint8_t* end = ib + e;
-      uint64_t shared = 0, nonshared = 0, vlen = 0;
-      uint32_t a = get_varint<32>(p, end, &shared);
-      if (a) a = (p += a, get_varint<32>(p, end, &nonshared));
-      if (a) a = (p += a, get_varint<32>(p, end, &vlen));
-      if (a) p += a;
-      ok = a && shared == 0 && nonshared <= uint64_t(end - p) && vlen <= uint64_t(end - p) - nonshared;
-      const uint8_t* ikey = p;
-      if (ok) {
-        p += nonshared;
-        ok = p + vlen == end;
+    const uint8_t* ikey = nullptr;
+    uint32_t ilen = 0;
+    uint64_t off = 0, size = 0;
+    if (index_entry(d, k, &ikey, &ilen, &off, &size)) {
+      bool read = true;
+      if (ranges && ranges[d.job].flags) {
+        const JobRange r = ranges[d.job];
+        if ((r.flags & 1u) && ilen >= 8 && cmp_user_keys(ikey, ilen - 8, bounds + r.lo_off, r.lo_len) < 0)
+          read = false;
+        const uint8_t* pk;
+        uint32_t pl;
+        uint64_t po, ps;
+        if (read && k > 0 && (r.flags & 2u) && index_entry(d, k - 1, &pk, &pl, &po, &ps) && pl >= 8 &&
+            cmp_user_keys(pk, pl - 8, bounds + r.hi_off, r.hi_len) >= 0)
+          read = false;
       }
-      uint64_t off = 0, size = 0;
-      if (ok) {
-        const uint8_t* vend = p + vlen;
-        uint32_t b = get_varint<64>(p, vend, &off);
-        if (b) b = (p += b, get_varint<64>(p, vend, &size));
-        ok = b && p + b == vend && handle_ok(off, size, d.size - kFooter);
-      }
-      if (ok) {
+      if (read) {
         out.ptr = d.data + off;
         out.size = size;
         out.off = off;
         out.ikey = ikey;
-        out.ilen = uint32_t(nonshared);
+        out.ilen = ilen;
       }
+    } else {
+      const uint64_t rstart = d.idx_size - 4 - 4ull * d.nblk;
+      report(errs + d.job, E_CORRUPT, d.local, d.idx_off + rstart + 4ull * k);
     }
-    if (!ok) report(errs + d.job, E_CORRUPT, d.local, d.idx_off + rstart + 4ull * k);
     blocks[g] = out;
   }
 }
@@ -488,7 +509,7 @@ __global__ void k_run_links(const DInput* __restrict__ in, uint32_t n_inputs, co
 __global__ void k_zero_failed(const BlockDesc* __restrict__ blocks, uint32_t n_blocks, const DErr* __restrict__ errs,
                               uint32_t* __restrict__ nrec, uint64_t* __restrict__ kbytes) {
   for (uint64_t g = gtid(); g < n_blocks; g += gstride())
-    if (errs[blocks[g].job].code != 0) {
+    if (errs[blocks[g].job].code != 0 || blocks[g].ptr == nullptr) {
       nrec[g] = 0;
       kbytes[g] = 0;
     }
@@ -580,9 +601,12 @@ void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs, Crc
 }
 
 void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
-                          BlockDesc* blocks, DErr* errs, cudaStream_t st) {
+                          BlockDesc* blocks, DErr* errs, cudaStream_t st, const JobRange* ranges,
+                          const uint8_t* bounds) {
   if (!n_blocks) return;
-  k_index_entries<<<grid_for(n_blocks, 256), 256, 0, st>>>(in, n_inputs, in_blk_first, n_blocks, blocks, errs); count_launches(1);
+  k_index_entries<<<grid_for(n_blocks, 256), 256, 0, st>>>(in, n_inputs, in_blk_first, n_blocks, blocks, errs,
+                                                           ranges, bounds);
+  count_launches(1);
 }
 
 void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const DErr* errs, DErr* verr,

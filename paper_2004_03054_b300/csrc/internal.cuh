@@ -33,6 +33,19 @@ struct BlockDesc {
   uint32_t pad;
 };
 
+// A job's user-key range (R13): bounds are bytes of the call's bound buffer.
+struct JobRange {
+  uint32_t lo_off, lo_len, hi_off, hi_len;
+  uint32_t flags;  // 1: lo present, 2: hi present
+};
+
+// R13: is the user key u inside its job's range [lo, hi)?
+__device__ __forceinline__ bool key_in_range(const JobRange& r, const uint8_t* bounds, const uint8_t* u, uint32_t n) {
+  if ((r.flags & 1u) && cmp_user_keys(u, n, bounds + r.lo_off, r.lo_len) < 0) return false;
+  if ((r.flags & 2u) && cmp_user_keys(u, n, bounds + r.hi_off, r.hi_len) >= 0) return false;
+  return true;
+}
+
 struct JobDev {
   uint64_t snapshot;
   uint32_t bottommost;
@@ -202,8 +215,11 @@ void launch_footers(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs, Crc
 void launch_footers_read(DInput* in, uint32_t n_inputs, DErr* errs, CrcMsg* msgs, cudaStream_t st);
 void launch_index_crc(CrcMsg* msgs, uint32_t n_inputs, DErr* errs, CrcTabs tabs, cudaStream_t st);
 void launch_footers_finish(DInput* in, uint32_t n_inputs, DErr* errs, cudaStream_t st);
+// With ranges (one JobRange per job, bound bytes in `bounds`), a block no key of its job's
+// range can be in gets a null ptr (it is neither checked nor decoded).
 void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
-                          BlockDesc* blocks, DErr* errs, cudaStream_t st);
+                          BlockDesc* blocks, DErr* errs, cudaStream_t st, const JobRange* ranges = nullptr,
+                          const uint8_t* bounds = nullptr);
 constexpr uint32_t kHdrMax = 64;  // entry offsets recorded per block for the decoder
 void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
                        uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, CrcTabs tabs, cudaStream_t st);
@@ -224,6 +240,7 @@ void launch_check_index(const BlockDesc* blocks, uint32_t n_blocks, const DInput
 // order); needs the block descriptors and the inputs' blk_first.
 void launch_run_links(const DInput* in, uint32_t n_inputs, const BlockDesc* blocks, const DErr* errs, uint8_t* link,
                       cudaStream_t st);
+// Blocks of failed jobs and blocks not read (null ptr) hold no records.
 void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,
                         uint64_t* kbytes, cudaStream_t st);
 void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,
@@ -258,8 +275,10 @@ void launch_sort_init(uint32_t* ord, MKey* okey, Recs recs, const uint8_t* arena
 // One pass of merges; ord[b] / key[b] are the two buffers, each span names its source.
 void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tiles, uint32_t tile, uint32_t* ord0,
                        MKey* key0, uint32_t* ord1, MKey* key1, Recs recs, const uint8_t* arena, cudaStream_t st);
+// With ranges, records whose user key is outside their job's range are dropped first.
 void launch_gc_flags(const uint32_t* ord, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, Recs recs,
-                     const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st);
+                     const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st,
+                     const JobRange* ranges = nullptr, const uint8_t* bounds = nullptr);
 void launch_gc_compact(const uint32_t* ord, const uint32_t* keep, const uint32_t* pos, uint32_t n_rec,
                        uint32_t* surv, cudaStream_t st);
 void launch_job_surv(JobDev* jobs, uint32_t n_jobs, const uint32_t* pos, uint32_t n_rec, Counts* cnt,

@@ -42,6 +42,7 @@ struct Ticket {
   uint64_t id = 0;
   luda_job job{};
   std::vector<luda_input> inputs;
+  std::vector<uint8_t> range_lo, range_hi;  // copies of the job's range keys
   TState state = TState::kQueued;
   luda_status rc = LUDA_OK;
   luda_outputs out{};
@@ -201,6 +202,16 @@ static luda_status submit(luda_server* s, const luda_job* job, uint64_t* ticket,
   t->inputs.assign(job->inputs, job->inputs + job->n_inputs);
   t->job = *job;
   t->job.inputs = t->inputs.data();
+  if (job->range_lo) {
+    t->range_lo.assign(job->range_lo, job->range_lo + job->range_lo_len);
+    t->range_lo.push_back(0);  // never empty, so data() is a valid pointer
+    t->job.range_lo = t->range_lo.data();
+  }
+  if (job->range_hi) {
+    t->range_hi.assign(job->range_hi, job->range_hi + job->range_hi_len);
+    t->range_hi.push_back(0);
+    t->job.range_hi = t->range_hi.data();
+  }
   for (const luda_input& in : t->inputs) t->stats.input_bytes += in.size;
   t->t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(s->mu);

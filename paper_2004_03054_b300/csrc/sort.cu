@@ -209,7 +209,7 @@ __device__ __forceinline__ uint32_t find_job(const JobDev* jobs, uint32_t n_jobs
 
 __global__ void k_gc_flags(const uint32_t* __restrict__ ord, uint32_t n_rec, const JobDev* __restrict__ jobs,
                            uint32_t n_jobs, Recs recs, const uint8_t* __restrict__ arena, uint32_t* __restrict__ keep,
-                           DErr* errs) {
+                           DErr* errs, const JobRange* __restrict__ ranges, const uint8_t* __restrict__ bounds) {
   for (uint64_t p = gtid(); p < n_rec; p += gstride()) {
     const uint32_t j = find_job(jobs, n_jobs, uint32_t(p), false);
     const JobDev job = jobs[j];
@@ -221,6 +221,10 @@ __global__ void k_gc_flags(const uint32_t* __restrict__ ord, uint32_t n_rec, con
     const uint64_t tr = recs.tr[x];
     const uint64_t S = job.snapshot;
     bool drop = false;
+    if (ranges && ranges[j].flags && !key_in_range(ranges[j], bounds, arena + recs.koff[x], recs.klen[x] - 8)) {
+      keep[p] = 0;  // R13: only keys of the job's range are written
+      continue;
+    }
     if (p > job.rec_begin) {
       const uint32_t y = ord[p - 1];
       if (same_user_key(recs, arena, y, x)) {
@@ -307,9 +311,12 @@ void launch_merge_pass(const MergeSpan* spans, uint32_t n_spans, uint32_t n_tile
 }
 
 void launch_gc_flags(const uint32_t* ord, uint32_t n_rec, const JobDev* jobs, uint32_t n_jobs, Recs recs,
-                     const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st) {
+                     const uint8_t* arena, uint32_t* keep, DErr* errs, cudaStream_t st, const JobRange* ranges,
+                     const uint8_t* bounds) {
   if (!n_rec) return;
-  k_gc_flags<<<grid_for(n_rec, elem_threads()), elem_threads(), 0, st>>>(ord, n_rec, jobs, n_jobs, recs, arena, keep, errs); count_launches(1);
+  k_gc_flags<<<grid_for(n_rec, elem_threads()), elem_threads(), 0, st>>>(ord, n_rec, jobs, n_jobs, recs, arena, keep,
+                                                                         errs, ranges, bounds);
+  count_launches(1);
 }
 
 void launch_gc_compact(const uint32_t* ord, const uint32_t* keep, const uint32_t* pos, uint32_t n_rec,

@@ -83,7 +83,13 @@ class Outputs(C.Structure):
 
 class Job(C.Structure):
     _fields_ = [("inputs", C.POINTER(Input)), ("n_inputs", C.c_uint32), ("level", C.c_int32),
-                ("smallest_snapshot", C.c_uint64), ("bottommost", C.c_int32)]
+                ("smallest_snapshot", C.c_uint64), ("bottommost", C.c_int32),
+                ("range_lo", C.c_void_p), ("range_lo_len", C.c_uint32),
+                ("range_hi", C.c_void_p), ("range_hi_len", C.c_uint32)]
+
+
+class Key(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("len", C.c_uint32)]
 
 
 class ServerConfig(C.Structure):
@@ -156,6 +162,9 @@ def lib():
         L.luda_autotune.argtypes = [C.POINTER(Job), C.c_uint32, C.POINTER(Options), C.POINTER(Tuning), C.c_uint32,
                                     C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_uint32)]
         L.luda_autotune.restype = st
+        L.luda_subcompact_device.restype = st
+        L.luda_subcompact_device.argtypes = [C.POINTER(Input), C.c_uint32, C.c_int32, C.c_uint64, C.POINTER(Key),
+                                             C.c_uint32, C.POINTER(Options), C.POINTER(Outputs)]
         L.luda_server_create.restype = st
         L.luda_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]
         L.luda_server_submit.restype = st
@@ -314,17 +323,48 @@ def batch_compact_device(jobs, opts: Options | None = None, copy_out: bool = Tru
     return rc, [_take(rc, outs[j], device=True) for j in range(len(jobs))]
 
 
+def subcompact_device(inputs, bounds, smallest_snapshot: int = MAX_SEQ, level: int = 1,
+                      opts: Options | None = None, copy_out: bool = True):
+    """R13 subcompactions of one job (inputs: torch uint8 CUDA tensors) at the strictly
+    increasing user keys `bounds`: one Result with the ranges' tables in key order."""
+    ins = (Input * max(1, len(inputs)))()
+    for i, t in enumerate(inputs):
+        ins[i].data, ins[i].size = t.data_ptr(), t.numel()
+    bufs = [C.create_string_buffer(bytes(b), max(1, len(b))) for b in bounds]
+    keys = (Key * max(1, len(bounds)))()
+    for i, (b, buf) in enumerate(zip(bounds, bufs)):
+        keys[i].data, keys[i].len = C.cast(buf, C.c_void_p), len(b)
+    o = Options.from_buffer_copy(opts or options())
+    if o.stream is None:
+        o.stream = current_stream()
+    out = Outputs()
+    rc = lib().luda_subcompact_device(ins, len(inputs), level, smallest_snapshot, keys, len(bounds), C.byref(o),
+                                      C.byref(out))
+    if not copy_out:
+        return rc, out
+    return _take(rc, out, device=True)
+
+
 def _jobs_array(jobs):
-    """jobs: list of (inputs: [torch CUDA uint8 tensors], smallest_snapshot, bottommost)."""
+    """jobs: list of (inputs: [torch CUDA uint8 tensors], smallest_snapshot, bottommost), or
+    of (inputs, smallest_snapshot, bottommost, lo, hi) for ranged jobs (R13; bytes or None)."""
     keep = []
     js = (Job * max(1, len(jobs)))()
-    for j, (inputs, snap, bottom) in enumerate(jobs):
+    for j, job in enumerate(jobs):
+        inputs, snap, bottom = job[:3]
+        lo, hi = (job[3], job[4]) if len(job) > 3 else (None, None)
         ins = (Input * max(1, len(inputs)))()
         for i, t in enumerate(inputs):
             ins[i].data, ins[i].size = t.data_ptr(), t.numel()
         keep.append(ins)
         js[j].inputs = C.cast(ins, C.POINTER(Input))
         js[j].n_inputs, js[j].smallest_snapshot, js[j].bottommost = len(inputs), snap, int(bool(bottom))
+        for name, key in (("lo", lo), ("hi", hi)):
+            if key is not None:
+                buf = C.create_string_buffer(bytes(key), max(1, len(key)))
+                keep.append(buf)
+                setattr(js[j], "range_" + name, C.cast(buf, C.c_void_p))
+                setattr(js[j], "range_" + name + "_len", len(key))
     return js, keep
 
 
@@ -334,7 +374,7 @@ class Plan:
 
     def __init__(self, jobs, opts: Options | None = None):
         self._js, self._keep = _jobs_array(jobs)
-        self._inputs = [t for inputs, _, _ in jobs for t in inputs]
+        self._inputs = [t for job in jobs for t in job[0]]
         self.n_jobs = len(jobs)
         self.opts = opts or options()
         self.handle = C.c_void_p()

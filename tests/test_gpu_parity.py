@@ -287,3 +287,68 @@ def test_index_key_interval_check(key0):
     job = W.Job("ikey2", 0, [], W.MAX_SEQ, False)
     check_job(job, [img])
     check_job(job, oracle_inputs(W.config1(seed=4, scale=1 / 128)) + [img])
+
+
+# ---- R13: ranged jobs and subcompactions -------------------------------------------------------
+def _user_keys(job):
+    return sorted({bytes(r.ukeys[r.ukoff[i]:r.ukoff[i + 1]]) for r in job.inputs for i in range(len(r.seqs))})
+
+
+def _oracle_opts(job, flags=0):
+    return dict(smallest_snapshot=job.smallest_snapshot, bottommost=job.bottommost, block_size=job.block_size,
+                restart_interval=job.restart_interval, bloom_bits_per_key=job.bloom_bits_per_key,
+                target_file_size=job.target_file_size, flags=flags)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_subcompaction_matches_oracle(seed):
+    rng = np.random.default_rng(4400 + seed)
+    job = W.tiny_job(rng, n_keys=int(rng.integers(10, 500)), max_versions=5, n_inputs=int(rng.integers(1, 6)),
+                     key_len=(0, 16), val_len=(0, 300), p_del=0.1)
+    job.block_size, job.target_file_size = int(rng.choice([64, 512, 4096])), int(rng.choice([1500, 1 << 20]))
+    job.bottommost = bool(rng.integers(0, 2))
+    ins = oracle_inputs(job)
+    keys = _user_keys(job)
+    bounds = sorted(set([keys[int(i)] for i in rng.integers(0, len(keys), size=int(rng.integers(1, 5)))]
+                        + [rng.bytes(int(rng.integers(0, 5)))]))
+    flags = int(rng.choice([0, luda.F_SHORT_INDEX]))
+    want = oracle.subcompact(ins, bounds, **_oracle_opts(job, flags))
+    got = luda.subcompact_device([dev(x) for x in ins], bounds, job.smallest_snapshot,
+                                 opts=luda.job_options(job, flags=flags))
+    assert got.status == want.status == 0, (got.status, got.detail)
+    assert [t.cpu().numpy().tobytes() for t in got.tables] == [t.data for t in want.tables]
+    assert got.n_in_entries == want.n_in_entries and got.n_dropped == want.n_dropped
+    assert [(s, l) for s, l in zip(got.smallest, got.largest)] == [(t.smallest, t.largest) for t in want.tables]
+
+
+def test_ranged_jobs_in_a_batch_and_corrupt_blocks_outside_the_range():
+    job = W.config1(seed=9, scale=1 / 32)
+    ins = oracle_inputs(job)
+    st, rt, _ = oracle.read_table(ins[1])
+    last = [rt.keys[rt.blk_last[b]][:-8] for b in range(rt.n_blocks)]
+    lo, hi = last[5] + b"\x00", last[8] + b"\x00"
+    bad_out = bytearray(ins[1])
+    bad_out[rt.blk_off[2] + 3] ^= 0x20   # below the range: not read
+    bad_in = bytearray(ins[1])
+    bad_in[rt.blk_off[7] + 3] ^= 0x20    # inside the range
+    cases = [(ins, lo, hi), ([ins[0], bytes(bad_out)] + ins[2:], lo, hi), ([ins[0], bytes(bad_in)] + ins[2:], lo, hi),
+             (ins, None, lo), (ins, hi, None), (ins, lo, lo)]
+    batch = [([dev(x) for x in c], job.smallest_snapshot, job.bottommost, a, b) for c, a, b in cases]
+    rc, got = luda.batch_compact_device(batch, luda.job_options(job))
+    assert rc == 0
+    for (c, a, b), g in zip(cases, got):
+        w = oracle.compact(c, **_oracle_opts(job), lo=a, hi=b)
+        assert g.status == w.status, (g.status, w.status, g.detail)
+        if w.status == 0:
+            assert [t.cpu().numpy().tobytes() for t in g.tables] == [t.data for t in w.tables]
+            assert g.n_in_entries == w.n_in_entries and g.n_dropped == w.n_dropped
+    assert got[1].status == 0 and got[2].status == luda.ERR_CORRUPTION
+
+
+def test_subcompaction_bad_bounds_and_plans_reject_ranges():
+    job = W.config1(seed=2, scale=1 / 128)
+    ins = [dev(x) for x in oracle_inputs(job)]
+    assert luda.subcompact_device(ins, [b"b", b"a"]).status == luda.ERR_INVALID_ARG
+    assert luda.subcompact_device(ins, [b"a", b"a"]).status == luda.ERR_INVALID_ARG
+    with pytest.raises(RuntimeError):
+        luda.Plan([(ins, job.smallest_snapshot, job.bottommost, b"a", None)], luda.job_options(job))
