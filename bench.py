@@ -463,7 +463,7 @@ def served(args):
                        "L0 trigger 4, fanout 10, 64 MiB tables, 40 GB budget"}
     for name, slots in (("continuous", args.serve_slots), ("per_job_fifo", 1)):
         stream = W.config5_stream(seed=5, n_memtables=args.serve_memtables, write_rate=args.serve_rate)
-        rep = L.serve(stream, n_slots=slots, hbm_budget=40 * 10**9, pace=True)
+        rep = L.serve(stream, n_slots=slots, hbm_budget=40 * 10**9, pace=True, prewarm_bytes=16 << 30)
         out[name] = {"slots": slots, "jobs": rep.jobs, "failed": rep.failed,
                      "value": round(rep.compaction_in_bytes / MiB / rep.wall_s, 1), "unit": "MiB/s",
                      "wall_s": round(rep.wall_s, 3), "compaction_in_bytes": rep.compaction_in_bytes,

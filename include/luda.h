@@ -266,6 +266,10 @@ typedef struct {
   uint64_t hbm_budget;     /* device bytes the admitted jobs may hold at once (> 0) */
   luda_options opts;       /* format options of every job; opts.stream is ignored and
                               opts.bottommost is replaced by each job's own flag */
+  uint64_t prewarm_bytes;  /* device bytes allocated and freed at creation (opts.dev_alloc NULL: the
+                              stream-ordered pool keeps them), so that early jobs do not wait for the
+                              driver to map memory; 0 = none. Each slot also sets up its per-thread
+                              state (second stream, pinned staging) before taking jobs. */
 } luda_server_config;
 
 typedef struct {

@@ -1690,6 +1690,17 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
 
 }  // namespace
 
+luda_status luda::warm_thread() {
+  Side* side = nullptr;
+  luda_status rc = get_side(&side);
+  if (rc) return rc;
+  CrcTabs tabs;
+  if ((rc = get_tabs(&tabs))) return rc;
+  t_stage.take(1);  // notes the size the stage wants
+  t_stage.reset();  // allocates it
+  return LUDA_OK;
+}
+
 luda_status luda::compact_job_host(const luda_job& job, const luda_options* opts, luda_outputs* out,
                                    AdmitGate* gate) {
   t_detail[0] = 0;

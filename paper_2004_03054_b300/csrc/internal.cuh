@@ -371,6 +371,9 @@ struct AdmitGate {
 luda_status compact_job_device(const luda_job& job, const luda_options* opts, luda_outputs* out, AdmitGate* gate);
 // One job with host inputs: copied to the device, compacted, new tables copied back into
 // library-owned pinned host memory (luda_compact plus an admission gate).
+// Sets up the calling thread's per-thread state (second stream and its events, the CRC
+// tables of the device, the pinned staging buffer) ahead of its first job.
+luda_status warm_thread();
 luda_status compact_job_host(const luda_job& job, const luda_options* opts, luda_outputs* out, AdmitGate* gate);
 
 }  // namespace luda

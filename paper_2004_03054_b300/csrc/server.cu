@@ -107,6 +107,7 @@ struct SlotGate final : AdmitGate {
 
 void slot_main(luda_server* s, uint32_t slot) {
   cudaSetDevice(s->device);
+  luda::warm_thread();  // best effort: a job sets up whatever is still missing itself
   for (;;) {
     Ticket* t = nullptr;
     {
@@ -189,6 +190,12 @@ luda_status luda_server_create(const luda_server_config* cfg, luda_server** serv
       return LUDA_ERR_CUDA;
     }
     s->streams.push_back(st);
+  }
+  if (cfg->prewarm_bytes && !cfg->opts.dev_alloc) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, cfg->prewarm_bytes, s->streams[0]) == cudaSuccess) cudaFreeAsync(p, s->streams[0]);
+    cudaStreamSynchronize(s->streams[0]);
+    cudaGetLastError();  // a prewarm that does not fit is not an error
   }
   for (uint32_t i = 0; i < cfg->n_slots; ++i) s->slots.emplace_back(slot_main, s.get(), i);
   *server = s.release();

@@ -349,7 +349,7 @@ class LSM:
 
 
 def serve(stream, n_slots: int = 4, hbm_budget: int = 40 * 10**9, pace: bool = True, on_complete=None,
-          lsm_kw: dict | None = None, before_close=None) -> ServeReport:
+          lsm_kw: dict | None = None, before_close=None, prewarm_bytes: int = 0) -> ServeReport:
     """Feed a write stream (workloads.config5_stream) into a simulated LSM tree served by a
     luda.Server with `n_slots` slots: memtables are flushed when the stream time says they
     are full (wall clock, if `pace`), compactions start as soon as the policy allows and
@@ -359,7 +359,7 @@ def serve(stream, n_slots: int = 4, hbm_budget: int = 40 * 10**9, pace: bool = T
     kw = dict(lsm_kw or {})
     opts = luda.options(kw.get("block_size", 4096), kw.get("restart_interval", 16), kw.get("bloom_bits_per_key", 10),
                         kw.get("target_file", 64 * MiB))
-    server = luda.Server(n_slots, hbm_budget, opts)
+    server = luda.Server(n_slots, hbm_budget, opts, prewarm_bytes=prewarm_bytes)
     lsm = LSM(server, on_complete=on_complete, **kw)
     torch.cuda.synchronize()
     mts = list(stream)

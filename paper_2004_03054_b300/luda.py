@@ -93,7 +93,8 @@ class Key(C.Structure):
 
 
 class ServerConfig(C.Structure):
-    _fields_ = [("n_slots", C.c_uint32), ("hbm_budget", C.c_uint64), ("opts", Options)]
+    _fields_ = [("n_slots", C.c_uint32), ("hbm_budget", C.c_uint64), ("opts", Options),
+                ("prewarm_bytes", C.c_uint64)]
 
 
 class JobStats(C.Structure):
@@ -414,9 +415,9 @@ class Server:
     uint8 tensors (or (device pointer, size) pairs) that must stay alive until their job
     completes; the server keeps a reference to tensors until the job is collected."""
 
-    def __init__(self, n_slots: int, hbm_budget: int, opts: Options | None = None):
+    def __init__(self, n_slots: int, hbm_budget: int, opts: Options | None = None, prewarm_bytes: int = 0):
         cfg = ServerConfig()
-        cfg.n_slots, cfg.hbm_budget = n_slots, hbm_budget
+        cfg.n_slots, cfg.hbm_budget, cfg.prewarm_bytes = n_slots, hbm_budget, prewarm_bytes
         cfg.opts = opts or options()
         self.handle = C.c_void_p()
         rc = lib().luda_server_create(C.byref(cfg), C.byref(self.handle))

@@ -39,14 +39,15 @@ def _tables(res):
     return [t.cpu().numpy().tobytes() for t in res.tables]
 
 
-@pytest.mark.parametrize("n_slots,budget", [(4, 1 << 40), (4, 24 << 20), (1, 1 << 40), (8, 1)])
-def test_server_mix_equals_alone_and_oracle(n_slots, budget):
+@pytest.mark.parametrize("n_slots,budget,prewarm", [(4, 1 << 40, 0), (4, 24 << 20, 0), (1, 1 << 40, 0), (8, 1, 0),
+                                                    (3, 1 << 40, 1 << 30)])
+def test_server_mix_equals_alone_and_oracle(n_slots, budget, prewarm):
     jobs = _jobs(15, seed=11)
     ins = [oracle_inputs(j) for j in jobs]
     want = [oracle_compact(j, x) for j, x in zip(jobs, ins)]
     dev = [[_dev(b) for b in x] for x in ins]
     torch.cuda.synchronize()
-    srv = luda.Server(n_slots, budget, luda.options(T, R, BPK, TARGET))
+    srv = luda.Server(n_slots, budget, luda.options(T, R, BPK, TARGET), prewarm_bytes=prewarm)
     tickets = [srv.submit(d, j.smallest_snapshot, j.bottommost) for d, j in zip(dev, jobs)]
     seen = set()
     for _ in tickets:
