@@ -29,6 +29,7 @@ ERR_OOM = -4
 ERR_DUPLICATE_KEY = -7
 F_STRICT_DUP = 1
 F_SHORT_INDEX = 4  # index keys shortened (format variant of R9)
+F_FILTER_ARRAY = 8  # one filter per 2 KiB of data block offsets (format variant of R10)
 MAX_SEQ = (1 << 56) - 1
 
 
@@ -58,7 +59,7 @@ class _Read(C.Structure):
                 ("n_blocks", C.c_uint64), ("blk_off", C.POINTER(C.c_uint64)),
                 ("blk_size", C.POINTER(C.c_uint64)), ("blk_last", C.POINTER(C.c_uint64)),
                 ("index_keys_ok", C.c_uint32), ("index_keys_exact", C.c_uint32), ("layout_ok", C.c_uint32),
-                ("filter_off", C.c_uint64), ("filter_size", C.c_uint64)]
+                ("filter_off", C.c_uint64), ("filter_size", C.c_uint64), ("filter_array", C.c_uint32)]
 
 
 _lib = None
@@ -104,6 +105,8 @@ def lib():
         L.ora_free_read.argtypes = [C.POINTER(_Read)]
         L.ora_bloom_may_contain.restype = C.c_int
         L.ora_bloom_may_contain.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64]
+        L.ora_filter_array_may_contain.restype = C.c_int
+        L.ora_filter_array_may_contain.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_uint64]
         L.ora_last_detail.restype = C.c_char_p
         del u8p
         _lib = L
@@ -265,7 +268,8 @@ class ReadTable:
     index_keys_ok: bool       # every index key in [its block's last key, the next block's first key)
     index_keys_exact: bool    # every index key equals its block's last key
     layout_ok: bool
-    filter: bytes       # filter block contents (bitmap || k)
+    filter: bytes       # filter block contents (bitmap || k, or a filter array)
+    filter_array: bool = False  # the metaindex names a filter array
 
 
 def read_table(data: bytes):
@@ -292,6 +296,7 @@ def read_table(data: bytes):
         blk_last=[int(t.blk_last[i]) for i in range(nb)],
         index_keys_ok=bool(t.index_keys_ok), index_keys_exact=bool(t.index_keys_exact), layout_ok=bool(t.layout_ok),
         filter=bytes(a[int(t.filter_off): int(t.filter_off) + int(t.filter_size)]),
+        filter_array=bool(t.filter_array),
     )
     L.ora_free_read(r)
     return OK, out, ""
@@ -301,6 +306,13 @@ def bloom_may_contain(filter_contents: bytes, ukey: bytes) -> bool:
     f = _u8(filter_contents)
     k = _u8(ukey)
     return bool(lib().ora_bloom_may_contain(f.ctypes.data, len(f), k.ctypes.data, len(k)))
+
+
+def filter_array_may_contain(filter_contents: bytes, block_off: int, ukey: bytes) -> bool:
+    """Query of a filter array for a key of the data block at table offset block_off."""
+    f = _u8(filter_contents)
+    k = _u8(ukey)
+    return bool(lib().ora_filter_array_may_contain(f.ctypes.data, len(f), block_off, k.ctypes.data, len(k)))
 
 
 def subcompact(inputs, bounds, smallest_snapshot: int = MAX_SEQ, bottommost: bool = False, block_size: int = 4096,

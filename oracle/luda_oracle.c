@@ -20,12 +20,17 @@
  *   4. re-encode with the sequential, one-entry-at-a-time table builder loop (flush a
  *      block when its size estimate reaches the block size, finish a file when its
  *      flushed size reaches the target).
+ * Format variants, each behind a flag: shortened index keys, ranged compactions, and
+ * LevelDB's filter array (one filter per 2 KiB of data block offsets; the paper's
+ * prototype is built on LevelDB 1.22, §IV-A, whose tables carry a bloom filter block,
+ * §II-A) built by the same loop's block-start steps.
  *
  * Parity pins (tests/test_oracle_*.py): published CRC-32C check values, a bit-at-a-time
  * CRC from the polynomial, MurmurHash3 published values, a hand-worked block example,
  * a brute-force dictionary replay of the generated writes, an independent pure-Python
  * table reader, bloom false-positive rate against its closed form, and structural
- * invariants of every produced table.
+ * invariants of every produced table; the filter array against the independent reader's
+ * own construction and a hand-worked layout.
  */
 #include <stdarg.h>
 #include <stdint.h>
@@ -42,12 +47,15 @@
 
 #define ORA_F_STRICT_DUP 1u
 #define ORA_F_SHORT_INDEX 4u /* R9 variant: shortened index keys */
+#define ORA_F_FILTER_ARRAY 8u /* R10 variant: one filter per 2 KiB of data block offsets */
 
 #define ORA_MAGIC 0x4C55444153535431ull
 #define ORA_FOOTER 48
 #define ORA_TRAILER 5
 #define ORA_MAX_SEQ ((1ull << 56) - 1)
 static const char ORA_FILTER_NAME[] = "filter.luda.bloom";
+static const char ORA_FILTER_ARRAY_NAME[] = "filter.luda.bloom2k";
+#define ORA_FILTER_BASE_LG 11u
 
 static char g_detail[512];
 
@@ -387,6 +395,12 @@ typedef struct {
   int short_index, pending;
   buf_t pend_key;
   uint64_t pend_off, pend_size;
+  /* R10 variant: the filters generated so far (concatenated), their offsets, and the first
+   * entry not yet in a filter */
+  int filter_array;
+  buf_t farr;
+  uint32_t* foffs;
+  uint64_t nfilt, capfilt, fgen;
   /* finished tables */
   ora_table* tables;
   uint32_t n_tables, cap_tables;
@@ -454,10 +468,13 @@ static int tb_resolve_index(tb_t* tb, const uint8_t* next, uint64_t nlen) {
   return rc;
 }
 
+static int fa_start_block(tb_t* tb, uint64_t off);
+
 static int tb_flush_block(tb_t* tb) {
   uint64_t off, size;
   if (bb_finish(&tb->data)) return -1;
   if (write_block(&tb->file, tb->data.buf.p, tb->data.buf.n, &off, &size)) return -1;
+  if (tb->filter_array && fa_start_block(tb, tb->file.n)) return -1;
   if (tb->short_index) {
     tb->pending = 1;
     tb->pend_key.n = 0;
@@ -471,11 +488,12 @@ static int tb_flush_block(tb_t* tb) {
   return bb_reset(&tb->data);
 }
 
-/* Bloom filter over the table's user keys: m = max(64, n*bpk) bits rounded up to whole
- * bytes, k = clamp(bpk*69/100, 1, 30) probes by double hashing h, h+d, h+2d, ... with
- * h = MurmurHash3_x86_32(key, 0) and d = h rotated right by 17. */
-static int build_filter(tb_t* tb, buf_t* out) {
-  uint64_t n = tb->n_entries;
+/* Bloom filter over the user keys of the open table's entries [first, last), appended to
+ * out: m = max(64, n*bpk) bits rounded up to whole bytes, k = clamp(bpk*69/100, 1, 30)
+ * probes by double hashing h, h+d, h+2d, ... with h = MurmurHash3_x86_32(key, 0) and d = h
+ * rotated right by 17; then the byte k. */
+static int bloom_append(tb_t* tb, uint64_t first, uint64_t last, buf_t* out) {
+  uint64_t n = last - first;
   uint64_t bits = n * tb->bpk;
   if (bits < 64) bits = 64;
   uint64_t bytes = (bits + 7) / 8;
@@ -483,16 +501,17 @@ static int build_filter(tb_t* tb, buf_t* out) {
   uint32_t k = tb->bpk * 69 / 100;
   if (k < 1) k = 1;
   if (k > 30) k = 30;
-  out->n = 0;
+  const uint64_t at = out->n;
   if (buf_reserve(out, bytes + 1)) return -1;
-  memset(out->p, 0, bytes);
-  out->n = bytes;
-  for (uint64_t i = 0; i < n; i++) {
+  memset(out->p + at, 0, bytes);
+  out->n = at + bytes;
+  uint8_t* bm = out->p + at;
+  for (uint64_t i = first; i < last; i++) {
     uint32_t h = ora_murmur3_32(tb->fkeys.p + tb->fkoff[i], tb->fkoff[i + 1] - tb->fkoff[i], 0);
     uint32_t d = (h >> 17) | (h << 15);
     for (uint32_t j = 0; j < k; j++) {
       uint64_t b = h % bits;
-      out->p[b >> 3] |= (uint8_t)(1u << (b & 7));
+      bm[b >> 3] |= (uint8_t)(1u << (b & 7));
       h += d;
     }
   }
@@ -500,21 +519,66 @@ static int build_filter(tb_t* tb, buf_t* out) {
   return buf_put(out, &kb, 1);
 }
 
+/* R10 filter block: one bloom filter over every entry of the table. */
+static int build_filter(tb_t* tb, buf_t* out) {
+  out->n = 0;
+  return bloom_append(tb, 0, tb->n_entries, out);
+}
+
+/* R10 variant, filter array (LevelDB's filter block builder): filter i covers the data
+ * blocks whose offset in the table lies in [i * 2 KiB, (i + 1) * 2 KiB). The next filter
+ * takes the entries added since the previous one; with none it is empty. */
+static int fa_generate(tb_t* tb) {
+  if (tb->nfilt == tb->capfilt) {
+    uint64_t cap = tb->capfilt ? tb->capfilt * 2 : 64;
+    uint32_t* q = (uint32_t*)realloc(tb->foffs, cap * sizeof(uint32_t));
+    if (!q) return -1;
+    tb->foffs = q;
+    tb->capfilt = cap;
+  }
+  tb->foffs[tb->nfilt++] = (uint32_t)tb->farr.n;
+  if (tb->fgen < tb->n_entries && bloom_append(tb, tb->fgen, tb->n_entries, &tb->farr)) return -1;
+  tb->fgen = tb->n_entries;
+  return 0;
+}
+
+/* A data block starts at offset `off` of the table: every filter index below off / 2 KiB
+ * is generated (the first of them holds the entries added so far). */
+static int fa_start_block(tb_t* tb, uint64_t off) {
+  while (tb->nfilt < (off >> ORA_FILTER_BASE_LG))
+    if (fa_generate(tb)) return -1;
+  return 0;
+}
+
+/* Filter array contents: the filters, u32 offset of each, u32 offset of that array, the
+ * byte base_lg = 11. The entries of the last block, if no filter holds them yet, get one. */
+static int build_filter_array(tb_t* tb, buf_t* out) {
+  if (tb->fgen < tb->n_entries && fa_generate(tb)) return -1;
+  out->n = 0;
+  if (buf_put(out, tb->farr.p, tb->farr.n)) return -1;
+  for (uint64_t i = 0; i < tb->nfilt; i++)
+    if (buf_put_u32(out, tb->foffs[i])) return -1;
+  uint8_t lg = (uint8_t)ORA_FILTER_BASE_LG;
+  return buf_put_u32(out, (uint32_t)tb->farr.n) || buf_put(out, &lg, 1);
+}
+
 static int tb_finish_file(tb_t* tb) {
   if (tb->data.n > 0 && tb_flush_block(tb)) return -1;
   if (tb_resolve_index(tb, NULL, 0)) return -1;
   uint64_t foff, fsize, moff, msize, ioff, isize;
   buf_t f = {0};
-  int rc = build_filter(tb, &f) || write_block(&tb->file, f.p, f.n, &foff, &fsize);
+  int rc = (tb->filter_array ? build_filter_array(tb, &f) : build_filter(tb, &f)) ||
+           write_block(&tb->file, f.p, f.n, &foff, &fsize);
   free(f.p);
   if (rc) return -1;
+  const char* fname = tb->filter_array ? ORA_FILTER_ARRAY_NAME : ORA_FILTER_NAME;
   /* Metaindex: one entry naming the filter block. */
   bb_t meta;
   memset(&meta, 0, sizeof meta);
   meta.R = 1;
   buf_t h = {0};
   rc = bb_reset(&meta) || put_handle(&h, foff, fsize) ||
-       bb_add(&meta, (const uint8_t*)ORA_FILTER_NAME, sizeof ORA_FILTER_NAME - 1, h.p, h.n) ||
+       bb_add(&meta, (const uint8_t*)fname, strlen(fname), h.p, h.n) ||
        bb_finish(&meta) || write_block(&tb->file, meta.buf.p, meta.buf.n, &moff, &msize);
   free(h.p);
   bb_free(&meta);
@@ -564,6 +628,8 @@ static int tb_add(tb_t* tb, const uint8_t* key, uint64_t klen, const uint8_t* va
     tb->file.n = 0;
     tb->fkeys.n = 0;
     tb->n_entries = 0;
+    tb->farr.n = 0;
+    tb->nfilt = tb->fgen = 0;
     if (bb_reset(&tb->data) || bb_reset(&tb->index)) return -1;
     if (buf_put(&tb->smallest, key, klen)) return -1;
   }
@@ -596,6 +662,8 @@ static void tb_free(tb_t* tb) {
   free(tb->smallest.p);
   free(tb->largest.p);
   free(tb->pend_key.p);
+  free(tb->farr.p);
+  free(tb->foffs);
 }
 
 void ora_free_result(ora_result* r) {
@@ -621,6 +689,7 @@ static int check_opts(uint64_t T, uint32_t R, uint32_t bpk, uint64_t target) {
 static void tb_init(tb_t* tb, uint64_t T, uint32_t R, uint32_t bpk, uint64_t target, uint32_t flags) {
   memset(tb, 0, sizeof *tb);
   tb->short_index = (flags & ORA_F_SHORT_INDEX) != 0;
+  tb->filter_array = (flags & ORA_F_FILTER_ARRAY) != 0;
   tb->T = T;
   tb->R = R;
   tb->bpk = bpk;
@@ -1104,6 +1173,7 @@ typedef struct {
   uint32_t index_keys_exact; /* every index key equals its block's last key */
   uint32_t layout_ok;       /* data blocks tile [0, filter) and the blocks follow in order */
   uint64_t filter_off, filter_size;
+  uint32_t filter_array;    /* the filter block is a filter array (R10 variant) */
 } ora_read;
 
 typedef struct {
@@ -1138,13 +1208,17 @@ static int rd_cb(void* vctx, const uint8_t* key, uint64_t klen, const uint8_t* v
 typedef struct {
   buf_t name;
   uint64_t off, size;
-  int found;
+  int found, array;
 } meta_ctx;
 
 static int meta_cb(void* vctx, const uint8_t* key, uint64_t klen, const uint8_t* val, uint64_t vlen, int at_restart) {
   meta_ctx* c = (meta_ctx*)vctx;
   (void)at_restart;
-  if (klen == sizeof ORA_FILTER_NAME - 1 && memcmp(key, ORA_FILTER_NAME, klen) == 0) {
+  const int plain = klen == sizeof ORA_FILTER_NAME - 1 && memcmp(key, ORA_FILTER_NAME, klen) == 0;
+  const int array = klen == sizeof ORA_FILTER_ARRAY_NAME - 1 && memcmp(key, ORA_FILTER_ARRAY_NAME, klen) == 0;
+  if (plain || array) {
+    if (c->found) return ORA_ERR_CORRUPTION;
+    c->array = array;
     uint32_t a = get_varint(val, val + vlen, 64, &c->off);
     if (!a) return ORA_ERR_CORRUPTION;
     uint32_t b = get_varint(val + a, val + vlen, 64, &c->size);
@@ -1281,8 +1355,28 @@ int ora_read_table(const uint8_t* f, uint64_t fsize, ora_read** out) {
   r->layout_ok = layout_ok;
   r->filter_off = mc.off;
   r->filter_size = mc.size;
+  r->filter_array = (uint32_t)mc.array;
   *out = r;
   return ORA_OK;
+}
+
+/* Membership query against a filter array's contents for a key of the data block at
+ * offset block_off: the filter of index block_off >> base_lg decides; an empty one holds
+ * nothing; a malformed array answers "may contain". */
+int ora_bloom_may_contain(const uint8_t* filter, uint64_t len, const uint8_t* ukey, uint64_t ulen);
+int ora_filter_array_may_contain(const uint8_t* fa, uint64_t len, uint64_t block_off, const uint8_t* ukey,
+                                 uint64_t ulen) {
+  if (len < 5) return 1;
+  const uint32_t lg = fa[len - 1];
+  const uint64_t arr = rd_u32(fa + len - 5);
+  if (arr > len - 5 || lg > 63) return 1;
+  const uint64_t num = (len - 5 - arr) / 4, i = block_off >> lg;
+  if (i >= num) return 1;
+  const uint64_t start = rd_u32(fa + arr + 4 * i);
+  const uint64_t limit = i + 1 < num ? rd_u32(fa + arr + 4 * (i + 1)) : arr;
+  if (start == limit) return 0;
+  if (start > limit || limit > arr) return 1;
+  return ora_bloom_may_contain(fa + start, limit - start, ukey, ulen);
 }
 
 /* Bloom membership query against a filter block's contents (bitmap || k). */

@@ -92,8 +92,11 @@ def read(buf: bytes):
     ioff, isize, _ = handle(ft, p)
     index = entries(block(buf, ioff, isize))
     meta = entries(block(buf, moff, msize))
-    fh = [v for k, v, _ in meta if k == b"filter.luda.bloom"]
-    foff, fsize, _ = handle(fh[0])
+    fh = [(k, v) for k, v, _ in meta if k in (b"filter.luda.bloom", b"filter.luda.bloom2k")]
+    if len(fh) != 1:
+        raise ValueError("metaindex must name exactly one filter")
+    fname = fh[0][0].decode()
+    foff, fsize, _ = handle(fh[0][1])
     filt = block(buf, foff, fsize)
     blocks = []
     allents = []
@@ -107,7 +110,7 @@ def read(buf: bytes):
             raise ValueError("index key is not below the next block's first key")
         blocks.append((off, size, ents))
         allents.extend((e[0], e[1]) for e in ents)
-    return dict(entries=allents, blocks=blocks, filter=filt, index_keys=[k for k, _, _ in index],
+    return dict(entries=allents, blocks=blocks, filter=filt, filter_name=fname, index_keys=[k for k, _, _ in index],
                 handles=dict(filter=(foff, fsize), meta=(moff, msize), index=(ioff, isize)))
 
 
@@ -120,3 +123,65 @@ def _order(ikey: bytes):
 def split_internal(ikey: bytes):
     (tr,) = struct.unpack("<Q", ikey[-8:])
     return ikey[:-8], tr >> 8, tr & 0xFF
+
+
+def murmur3_32(data: bytes, seed: int = 0) -> int:
+    """MurmurHash3 x86_32, written from its published definition (4-byte little-endian
+    blocks mixed with c1 = 0xcc9e2d51, c2 = 0x1b873593, rotations 15 and 13, then the
+    tail, the length and the fmix32 finaliser)."""
+    M = 0xFFFFFFFF
+    h = seed & M
+    n = len(data)
+    c1, c2 = 0xCC9E2D51, 0x1B873593
+
+    def rotl(x, r):
+        return ((x << r) | (x >> (32 - r))) & M
+
+    for i in range(0, n - n % 4, 4):
+        k = int.from_bytes(data[i:i + 4], "little")
+        k = rotl((k * c1) & M, 15) * c2 & M
+        h = (rotl(h ^ k, 13) * 5 + 0xE6546B64) & M
+    t = data[n - n % 4:]
+    if t:
+        k = int.from_bytes(t, "little")
+        h ^= rotl((k * c1) & M, 15) * c2 & M
+    h ^= n
+    h ^= h >> 16
+    h = (h * 0x85EBCA6B) & M
+    h ^= h >> 13
+    h = (h * 0xC2B2AE35) & M
+    return h ^ (h >> 16)
+
+
+def bloom(ukeys, bpk: int) -> bytes:
+    """One R10 bloom filter (bitmap || k) over the user keys, bit by bit."""
+    bits = max(64, len(ukeys) * bpk)
+    nbytes = (bits + 7) // 8
+    bits = nbytes * 8
+    k = min(30, max(1, bpk * 69 // 100))
+    bm = bytearray(nbytes)
+    for u in ukeys:
+        h = murmur3_32(u)
+        d = ((h >> 17) | (h << 15)) & 0xFFFFFFFF
+        for _ in range(k):
+            b = h % bits
+            bm[b >> 3] |= 1 << (b & 7)
+            h = (h + d) & 0xFFFFFFFF
+    return bytes(bm) + bytes([k])
+
+
+def filter_array(blocks, data_end: int, bpk: int, base_lg: int = 11) -> bytes:
+    """The R10 variant's filter block, from a table's data blocks [(off, size, entries)]
+    and the offset where its data blocks end: filter i holds the user keys of the blocks
+    with off >> base_lg == i; there are max(data_end >> base_lg, (last off >> base_lg) + 1)
+    filters, the ones without keys empty."""
+    n = max(data_end >> base_lg, (blocks[-1][0] >> base_lg) + 1) if blocks else 0
+    keys = [[] for _ in range(n)]
+    for off, _, ents in blocks:
+        keys[off >> base_lg].extend(e[0][:-8] for e in ents)
+    body, offs = b"", []
+    for ks in keys:
+        offs.append(len(body))
+        if ks:
+            body += bloom(ks, bpk)
+    return body + b"".join(struct.pack("<I", o) for o in offs) + struct.pack("<I", len(body)) + bytes([base_lg])
