@@ -57,6 +57,10 @@ typedef enum {
 #define LUDA_F_STRICT_DUP 1u /* identical internal keys across inputs are an error */
 #define LUDA_F_SHORT_INDEX 4u /* write shortened index keys (format variant R9s: LevelDB's bytewise separator
                                  and short successor); decoders accept either kind */
+#define LUDA_F_FILTER_ARRAY 8u /* write LevelDB's filter array (format variant R10a, after the bloom filter
+                                  block of an SST in LUDA §II-A and LevelDB 1.22 of §IV-A): one bloom filter
+                                  per 2 KiB of data block offsets, metaindex key "filter.luda.bloom2k";
+                                  compactions do not read filter blocks, so inputs may carry either kind */
 #define LUDA_F_TRACE 2u      /* record per-stage device times (luda_outputs.stage_ms); LUDA_TRACE=1 in the
                                 environment does the same for every call. Stage boundaries always open
                                 NVTX ranges "luda/<stage>" on the calling thread. */

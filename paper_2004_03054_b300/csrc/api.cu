@@ -391,11 +391,36 @@ struct PackBufs {
   void *scan_tmp, *stitch_tmp;
   uint32_t meta_cap;  // entries of meta
   uint64_t key_cap;   // bytes of keybuf
+  // filter arrays (LUDA_F_FILTER_ARRAY): per table, then per filter
+  uint64_t *fcount, *fbase, *fbytes, *fwords, *fboff, *fwoff;
+  uint64_t slot_cap;  // filters the buffers hold (0 without filter arrays)
 };
 
-void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t key_cap) {
+// Capacity of the filter arrays: a table has at most (data bytes >> 11) + 1 filters, and
+// out_cap bounds all tables' bytes.
+static uint64_t filter_slot_cap(const Fmt& fmt, uint64_t out_cap, uint64_t max_tables) {
+  return (fmt.flags & LUDA_F_FILTER_ARRAY) ? (out_cap >> kFilterBaseLg) + max_tables + 2 : 0;
+}
+
+// Output bytes a filter array can add over one filter per table, for a job of n entries
+// whose data blocks hold at most `data` bytes: a non-empty filter of m entries takes at most
+// m * bpk / 8 + 10 bytes, every filter a 4-byte offset (at most data / 512 + 1 per table of
+// them), and a table 6 more bytes of array offset and metaindex name.
+static uint64_t filter_array_extra(const Fmt& fmt, uint64_t data, uint64_t n) {
+  return (fmt.flags & LUDA_F_FILTER_ARRAY) ? (data >> (kFilterBaseLg - 3)) + 24 * n + 64 : 0;
+}
+
+void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t key_cap, uint64_t slot_cap) {
   b.meta_cap = cap + 1;
   b.key_cap = key_cap + 1;
+  b.slot_cap = slot_cap;
+  const uint64_t nfa = slot_cap ? cap + 1 : 1;
+  b.fcount = L.take<uint64_t>(nfa);
+  b.fbase = L.take<uint64_t>(nfa);
+  b.fbytes = L.take<uint64_t>(slot_cap + 1);
+  b.fwords = L.take<uint64_t>(slot_cap + 1);
+  b.fboff = L.take<uint64_t>(slot_cap + 1);
+  b.fwoff = L.take<uint64_t>(slot_cap + 1);
   b.surv = L.take<uint32_t>(cap + 1);
   b.lcp = L.take<uint32_t>(cap + 1);
   b.sd = L.take<uint32_t>(cap + 1);
@@ -430,7 +455,7 @@ void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t
   b.meta = L.take<FileMeta>(cap + 1);
   b.bitmap = L.take<uint32_t>(bm_cap + 1);
   b.keybuf = L.take<uint8_t>(key_cap + 1);
-  b.scan_tmp = L.take<uint8_t>(scan_temp_bytes(cap + 1));
+  b.scan_tmp = L.take<uint8_t>(scan_temp_bytes((slot_cap > cap ? slot_cap : cap) + 1));
   b.stitch_tmp = L.take<uint8_t>(stitch_temp_bytes(cap + 1));
 }
 
@@ -459,10 +484,21 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   launch_index_sizes(b.blk_start, b.bsz, b.C, b.blk_file, b.file_start, cnt, cap, b.surv, recs, arena, fmt, b.ie,
                      st);
   CK((exclusive_scan<uint32_t, uint64_t>(b.ie, b.IX, cap, &cnt->nb, b.scan_tmp, st)));
-  launch_file_layout(b.file_start, cnt, cap, b.blk_start, b.C, b.IX, fmt, jobs, n_jobs, b.files, b.fsize, b.bmw, st);
+  FiltArr fa{};
+  if (b.slot_cap) {
+    // filter arrays: filters per table, each filter's bytes and bitmap words, their sums
+    launch_filter_count(b.file_start, cnt, cap, b.C, b.fcount, st);
+    CK((exclusive_scan<uint64_t, uint64_t>(b.fcount, b.fbase, cap, &cnt->nf, b.scan_tmp, st)));
+    launch_filter_sizes(b.fbase, b.file_start, b.blk_start, b.C, cnt, b.slot_cap, fmt, b.fbytes, b.fwords, st);
+    CK((exclusive_scan<uint64_t, uint64_t>(b.fbytes, b.fboff, b.slot_cap, &cnt->n_filt, b.scan_tmp, st)));
+    CK((exclusive_scan<uint64_t, uint64_t>(b.fwords, b.fwoff, b.slot_cap, &cnt->n_filt, b.scan_tmp, st)));
+    fa = FiltArr{b.fbase, b.fboff, b.fwoff, b.fbytes, b.slot_cap};
+  }
+  launch_file_layout(b.file_start, cnt, cap, b.blk_start, b.C, b.IX, fmt, fa, jobs, n_jobs, b.files, b.fsize, b.bmw,
+                     st);
   CK((exclusive_scan<uint64_t, uint64_t>(b.fsize, b.foff, cap, &cnt->nf, b.scan_tmp, st)));
   CK((exclusive_scan<uint64_t, uint64_t>(b.bmw, b.bmoff, cap, &cnt->nf, b.scan_tmp, st)));
-  launch_file_offsets(b.files, cnt, cap, b.foff, b.bmoff, jobs, n_jobs, out_cap, bm_cap, errs, st);
+  launch_file_offsets(b.files, cnt, cap, b.foff, b.bmoff, fa, jobs, n_jobs, out_cap, bm_cap, errs, st);
   launch_zero_bitmap(b.bitmap, cnt, bm_cap, st);
   trace_mark(tr, 7, st);
   launch_encode(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, b.ed, b.bd, recs,
@@ -475,10 +511,10 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   CK(cudaEventRecord(side->ev[3], side->s));
   launch_encode_big(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
                     fmt, out, out_cap, b.big, tabs, st);
-  launch_bloom(b.ed, cnt, cap, b.files, fmt, b.bitmap, out_cap, bm_cap, st);
+  launch_bloom(b.ed, cnt, cap, b.files, fmt, b.blk_start, b.C, fa, b.bitmap, out_cap, bm_cap, st);
   launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, fmt, out,
                      out_cap, st);
-  launch_file_finish(b.files, cnt, cap, b.bitmap, b.surv, recs, fmt, out, out_cap, tabs, b.fmsg, b.meta, st);
+  launch_file_finish(b.files, cnt, cap, b.bitmap, b.surv, recs, fmt, fa, out, out_cap, tabs, b.fmsg, b.meta, st);
   launch_key_lens(b.meta, cnt, cap, b.klens, st);
   CK((exclusive_scan<uint64_t, uint64_t>(b.klens, b.koff, cap, &cnt->nf, b.scan_tmp, st)));
   launch_key_gather(b.meta, cnt, cap, b.koff, b.files, b.surv, recs, arena, b.keybuf, st);
@@ -1042,6 +1078,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     // Output bound: data <= K + V + 24n; index <= K + 31n + 9 per table; filter, metaindex and
     // footer <= n*bpk/8 + 116 per table; tables <= n.
     out_cap += 2 * kj + job_in_bytes[j] + 200 * nj + 256;
+    out_cap += filter_array_extra(fmt, 2 * kj + job_in_bytes[j] + 24 * nj, nj);
     bm_cap += nj * fmt.bpk / 32 + 5 * nj + 8;
   }
   // merge schedule: linked inputs form one sorted run
@@ -1085,7 +1122,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     d_pos = L.take<uint32_t>(n_rec + 1);
     d_co = L.take<uint32_t>(max_tiles + 1);
     d_spans = L.take<MergeSpan>(spans.size() + 1);
-    pack_layout(L, pb, cap, bm_cap, key_cap);
+    pack_layout(L, pb, cap, bm_cap, key_cap, filter_slot_cap(fmt, out_cap, cap));
   };
   layoutC(LC);
   if (gate && !gate->admit(LA.off + LB.off + LC.off + out_cap + gate->extra)) {
@@ -1250,7 +1287,7 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
     CK(cudaStreamSynchronize(st));
   }
   const uint64_t K = ku + 8ull * n;
-  const uint64_t out_cap = 2 * K + vb + 200ull * n + 4096;
+  const uint64_t out_cap = 2 * K + vb + 200ull * n + 4096 + filter_array_extra(fmt, 2 * K + vb + 24ull * n, n);
   const uint64_t bm_cap = uint64_t(n) * fmt.bpk / 32 + 5ull * n + 64;
   Layout L;
   Recs recs;
@@ -1266,7 +1303,7 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
     d_err = l.take<DErr>(4);  // main chain and input checksums (collect's layout)
     d_job = l.take<JobDev>(1);
     d_cnt = l.take<Counts>(1);
-    pack_layout(l, pb, n, bm_cap, 2 * K + 64);
+    pack_layout(l, pb, n, bm_cap, 2 * K + 64, filter_slot_cap(fmt, out_cap, n));
     if (host_in) {
       h_ukeys = l.take<uint8_t>(ku + 16);
       h_ukoff = l.take<uint64_t>(n + 1);
@@ -1571,6 +1608,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     const uint64_t nj = jd.rec_end - jd.rec_begin;
     const uint64_t kj = in_key[job_in_first[j + 1]] - in_key[job_in_first[j]];
     out_cap += 2 * kj + job_in_bytes[j] + 200 * nj + 256;
+    out_cap += filter_array_extra(fmt, 2 * kj + job_in_bytes[j] + 24 * nj, nj);
     bm_cap += nj * fmt.bpk / 32 + 5 * nj + 8;
   }
   // merge schedule (as in run_compaction); replays check that the links still hold
@@ -1611,7 +1649,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     d_pos = L.take<uint32_t>(n_rec + 1);
     d_co = L.take<uint32_t>(max_tiles + 1);
     d_spans = L.take<MergeSpan>(spans.size() + 1);
-    pack_layout(L, pb, cap, bm_cap, 2 * K + 64);
+    pack_layout(L, pb, cap, bm_cap, 2 * K + 64, filter_slot_cap(fmt, out_cap, cap));
   };
   layC(LC);
   LC.base = alloc(LC.off);

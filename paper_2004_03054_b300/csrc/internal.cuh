@@ -71,8 +71,8 @@ struct FileDesc {
   uint32_t blk_begin, blk_end;  // output data blocks
   uint32_t ent_begin, ent_end;  // survivor positions
   uint32_t job;
-  uint32_t pad;
-  uint64_t bm_bits;      // filter bits
+  uint32_t n_filt;       // filters of the filter array (LUDA_F_FILTER_ARRAY)
+  uint64_t bm_bits;      // filter bits (one filter per table)
 };
 
 struct Fmt {
@@ -102,6 +102,21 @@ struct Counts {
   uint32_t max_kv;          // largest internal key + value length in the inputs (block walk)
   uint32_t crc_next_in;     // next input data block for the checksum kernels' warps
   uint32_t crc_next_out;    // next output data block for the trailer kernels' warps
+  uint32_t n_filt;          // filters of all tables' filter arrays (LUDA_F_FILTER_ARRAY)
+};
+
+// The filter arrays of a batch (LUDA_F_FILTER_ARRAY; base == nullptr otherwise). Filter s
+// of all tables: table f owns filters [base[f], base[f + 1]); its filter i covers the data
+// blocks starting in [i, i + 1) * 2 KiB of the table. boff / woff: exclusive sums of the
+// filters' bytes (bitmap and k, zero when empty) and of their bitmap words; bytes: each
+// filter's bytes. cap: filters the buffers hold.
+constexpr uint32_t kFilterBaseLg = 11;
+struct FiltArr {
+  const uint64_t* base;
+  const uint64_t* boff;
+  const uint64_t* woff;
+  const uint64_t* bytes;
+  uint64_t cap;
 };
 
 // One message for the multi-warp CRC (index and filter blocks): n bytes at p (contents and
@@ -305,11 +320,18 @@ void launch_block_file(const uint32_t* fpos, const Counts* cnt, uint32_t cap, ui
 void launch_index_sizes(const uint32_t* blk_start, const uint64_t* bsz, const uint64_t* C, const uint32_t* blk_file,
                         const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* surv, Recs recs,
                         const uint8_t* arena, Fmt fmt, uint32_t* ie, cudaStream_t st);
+// Filter array sizes: filters per table, then (after their scan into fa.base) each
+// filter's bytes and bitmap words; sets cnt->n_filt.
+void launch_filter_count(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint64_t* C,
+                         uint64_t* nfilt, cudaStream_t st);
+void launch_filter_sizes(const uint64_t* fbase, const uint32_t* file_start, const uint32_t* blk_start,
+                         const uint64_t* C, Counts* cnt, uint64_t slot_cap, Fmt fmt, uint64_t* fbytes,
+                         uint64_t* fwords, cudaStream_t st);
 void launch_file_layout(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_start,
-                        const uint64_t* C, const uint64_t* IX, Fmt fmt, const JobDev* jobs, uint32_t n_jobs,
-                        FileDesc* files, uint64_t* fsize, uint64_t* bmwords, cudaStream_t st);
+                        const uint64_t* C, const uint64_t* IX, Fmt fmt, FiltArr fa, const JobDev* jobs,
+                        uint32_t n_jobs, FileDesc* files, uint64_t* fsize, uint64_t* bmwords, cudaStream_t st);
 void launch_file_offsets(FileDesc* files, Counts* cnt, uint32_t cap, const uint64_t* foff, const uint64_t* bmoff,
-                         JobDev* jobs, uint32_t n_jobs, uint64_t out_cap, uint64_t bm_cap, DErr* errs,
+                         FiltArr fa, JobDev* jobs, uint32_t n_jobs, uint64_t out_cap, uint64_t bm_cap, DErr* errs,
                          cudaStream_t st);
 void launch_zero_bitmap(uint32_t* bitmap, const Counts* cnt, uint64_t cap_words, cudaStream_t st);
 void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const uint32_t* blk_file,
@@ -329,14 +351,15 @@ void launch_encode_big(const uint32_t* blk_start, Counts* cnt, uint32_t cap, con
                        const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, Recs recs, const uint8_t* arena,
                        Fmt fmt, uint8_t* out, uint64_t out_cap, const uint32_t* big, CrcTabs tabs, cudaStream_t st);
 void launch_bloom(const EncDesc* ed, const Counts* cnt, uint32_t cap, const FileDesc* files, Fmt fmt,
-                  uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st);
+                  const uint32_t* blk_start, const uint64_t* C, FiltArr fa, uint32_t* bitmap, uint64_t out_cap,
+                  uint64_t bm_cap, cudaStream_t st);
 void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t cap, const uint64_t* bsz,
                         const uint64_t* C, const uint64_t* IX, const uint32_t* blk_file, const FileDesc* files,
                         const uint32_t* surv, Recs recs, const uint8_t* arena, Fmt fmt, uint8_t* out,
                         uint64_t out_cap, cudaStream_t st);
 void launch_file_finish(const FileDesc* files, const Counts* cnt, uint32_t cap, const uint32_t* bitmap,
-                        const uint32_t* surv, Recs recs, Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs,
-                        CrcMsg* msgs, FileMeta* meta, cudaStream_t st);
+                        const uint32_t* surv, Recs recs, Fmt fmt, FiltArr fa, uint8_t* out, uint64_t out_cap,
+                        CrcTabs tabs, CrcMsg* msgs, FileMeta* meta, cudaStream_t st);
 void launch_key_lens(const FileMeta* meta, const Counts* cnt, uint32_t cap, uint64_t* lens, cudaStream_t st);
 void launch_key_gather(FileMeta* meta, Counts* cnt, uint32_t cap, const uint64_t* koff, const FileDesc* files,
                        const uint32_t* surv, Recs recs, const uint8_t* arena, uint8_t* keybuf, cudaStream_t st);

@@ -453,12 +453,75 @@ __global__ void k_index_sizes(const uint32_t* __restrict__ start, const uint64_t
   }
 }
 
+// Largest i in [0, n) with a[i] <= v (a ascending, a[0] <= v).
+template <typename T>
+__device__ __forceinline__ uint32_t last_le(const T* __restrict__ a, uint32_t n, T v) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---- filter array (R10a) ----------------------------------------------------------------
+// Filters of table f: max(D >> 11, (o_last >> 11) + 1), D = end of its data blocks, o_last =
+// offset of its last data block.
+__global__ void k_filter_count(const uint32_t* __restrict__ file_start, const Counts* __restrict__ cnt,
+                               const uint64_t* __restrict__ C, uint64_t* __restrict__ nfilt) {
+  const uint32_t nf = cnt->nf;
+  for (uint64_t f = gtid(); f < nf; f += gstride()) {
+    const uint32_t fb0 = file_start[f], fb1 = file_start[f + 1];
+    const uint64_t a = (C[fb1] - C[fb0]) >> kFilterBaseLg, b = ((C[fb1 - 1] - C[fb0]) >> kFilterBaseLg) + 1;
+    nfilt[f] = a > b ? a : b;
+  }
+}
+
+// One thread per filter: the entries of the table's blocks that start in the filter's
+// window (blocks are in offset order, so a range found by two binary searches), its bytes
+// (bitmap and k; none when empty) and bitmap words. Filters past slot_cap are left to the
+// capacity check of k_file_offsets.
+__global__ void k_filter_sizes(const uint64_t* __restrict__ fbase, const uint32_t* __restrict__ file_start,
+                               const uint32_t* __restrict__ start, const uint64_t* __restrict__ C, Counts* cnt,
+                               uint64_t slot_cap, Fmt fmt, uint64_t* __restrict__ fbytes,
+                               uint64_t* __restrict__ fwords) {
+  const uint32_t nf = cnt->nf;
+  const uint64_t total = fbase[nf], n = total < slot_cap ? total : slot_cap;
+  if (gtid() == 0) cnt->n_filt = uint32_t(n);
+  for (uint64_t s = gtid(); s < n; s += gstride()) {
+    const uint32_t f = last_le<uint64_t>(fbase, nf, s);
+    const uint32_t fb0 = file_start[f], fb1 = file_start[f + 1];
+    const uint64_t w0 = C[fb0] + ((s - fbase[f]) << kFilterBaseLg), w1 = w0 + (1ull << kFilterBaseLg);
+    uint32_t lo = fb0, hi = fb1;  // first block at or after w0
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (C[mid] < w0) lo = mid + 1;
+      else hi = mid;
+    }
+    uint32_t lo2 = lo, hi2 = fb1;  // first block at or after w1
+    while (lo2 < hi2) {
+      const uint32_t mid = (lo2 + hi2) >> 1;
+      if (C[mid] < w1) lo2 = mid + 1;
+      else hi2 = mid;
+    }
+    const uint64_t keys = start[lo2] - start[lo];
+    uint64_t bits = keys * fmt.bpk;
+    if (bits < 64) bits = 64;
+    const uint64_t bytes = keys ? (bits + 7) / 8 : 0;
+    fbytes[s] = keys ? bytes + 1 : 0;
+    fwords[s] = (bytes + 3) / 4;
+  }
+}
+
 __global__ void k_file_layout(const uint32_t* __restrict__ file_start, const Counts* __restrict__ cnt,
                               const uint32_t* __restrict__ start,
                               const uint64_t* __restrict__ C, const uint64_t* __restrict__ IX, Fmt fmt,
-                              const JobDev* __restrict__ jobs, uint32_t n_jobs, FileDesc* __restrict__ files,
-                              uint64_t* __restrict__ fsize, uint64_t* __restrict__ bmwords) {
+                              FiltArr fa, const JobDev* __restrict__ jobs, uint32_t n_jobs,
+                              FileDesc* __restrict__ files, uint64_t* __restrict__ fsize,
+                              uint64_t* __restrict__ bmwords) {
   const uint32_t nf = cnt->nf;
+  const bool fits = fa.base && fa.base[nf] <= fa.cap;
   for (uint64_t f = gtid(); f < nf; f += gstride()) {
     const uint32_t fb0 = file_start[f], fb1 = file_start[f + 1];
     const uint32_t e0 = start[fb0], e1 = start[fb1];
@@ -469,26 +532,36 @@ __global__ void k_file_layout(const uint32_t* __restrict__ file_start, const Cou
     d.ent_end = e1;
     d.job = job_of_block(jobs, n_jobs, fb0);
     d.data_size = C[fb1] - C[fb0];
-    uint64_t bits = uint64_t(e1 - e0) * fmt.bpk;
-    if (bits < 64) bits = 64;
-    const uint64_t bytes = (bits + 7) / 8;
-    d.bm_bits = bytes * 8;
-    d.filter_size = bytes + 1;
+    uint64_t words;
+    if (fa.base) {
+      // filter array: the filters, their u32 offsets, the array's offset, base_lg
+      const uint64_t s0 = fits ? fa.base[f] : 0, s1 = fits ? fa.base[f + 1] : 0;
+      d.n_filt = uint32_t(s1 - s0);
+      d.filter_size = (fa.boff[s1] - fa.boff[s0]) + 4 * (s1 - s0) + 5;
+      words = fa.woff[s1] - fa.woff[s0];
+    } else {
+      uint64_t bits = uint64_t(e1 - e0) * fmt.bpk;
+      if (bits < 64) bits = 64;
+      const uint64_t bytes = (bits + 7) / 8;
+      d.bm_bits = bytes * 8;
+      d.filter_size = bytes + 1;
+      words = (bytes + 3) / 4;
+    }
     const uint32_t hf = varint_size(d.data_size) + varint_size(d.filter_size);
-    d.meta_size = 3 + 17 + hf + 8;
+    d.meta_size = 3 + (fa.base ? 19 : 17) + hf + 8;
     d.meta_off = d.data_size + d.filter_size + kTrailer;
     d.index_size = (IX[fb1] - IX[fb0]) + 4ull * (fb1 - fb0) + 4;
     d.index_off = d.meta_off + d.meta_size + kTrailer;
     d.size = d.index_off + d.index_size + kTrailer + kFooter;
     files[f] = d;
     fsize[f] = d.size;
-    bmwords[f] = (bytes + 3) / 4;
+    bmwords[f] = words;
   }
 }
 
 __global__ void k_file_offsets(FileDesc* files, Counts* cnt, const uint64_t* __restrict__ foff,
-                               const uint64_t* __restrict__ bmoff, JobDev* jobs, uint32_t n_jobs, uint64_t out_cap,
-                               uint64_t bm_cap, DErr* errs) {
+                               const uint64_t* __restrict__ bmoff, FiltArr fa, JobDev* jobs, uint32_t n_jobs,
+                               uint64_t out_cap, uint64_t bm_cap, DErr* errs) {
   const uint32_t nf = cnt->nf;
   for (uint64_t f = gtid(); f < nf; f += gstride()) {
     files[f].off = foff[f];
@@ -496,7 +569,8 @@ __global__ void k_file_offsets(FileDesc* files, Counts* cnt, const uint64_t* __r
   }
   for (uint64_t j = gtid(); j < n_jobs; j += gstride()) {
     jobs[j].out_bytes = foff[jobs[j].file_end] - foff[jobs[j].file_begin];
-    if (foff[nf] > out_cap || bmoff[nf] > bm_cap) report(errs + j, E_OOM, ~0u, foff[nf]);
+    if (foff[nf] > out_cap || bmoff[nf] > bm_cap || (fa.base && fa.base[nf] > fa.cap))
+      report(errs + j, E_OOM, ~0u, foff[nf]);
   }
   if (gtid() == 0) {
     cnt->out_bytes = foff[nf];
@@ -1095,10 +1169,12 @@ __device__ uint32_t murmur3_32(const uint8_t* p, uint32_t n, uint32_t seed) {
 }
 
 __global__ void k_bloom(const EncDesc* __restrict__ ed, const Counts* __restrict__ cnt,
-                        const FileDesc* __restrict__ files, Fmt fmt, uint32_t* __restrict__ bitmap,
+                        const FileDesc* __restrict__ files, Fmt fmt, const uint32_t* __restrict__ start,
+                        const uint64_t* __restrict__ C, FiltArr fa, uint32_t* __restrict__ bitmap,
                         uint64_t out_cap, uint64_t bm_cap) {
   const uint32_t n = cnt->n_surv, nf = cnt->nf;
   if (cnt->out_bytes > out_cap || cnt->bm_words > bm_cap) return;
+  if (fa.base && fa.base[nf] > fa.cap) return;
   for (uint64_t s = gtid(); s < n; s += gstride()) {
     uint32_t lo = 0, hi = nf;  // the table holding survivor s
     while (hi - lo > 1) {
@@ -1111,8 +1187,15 @@ __global__ void k_bloom(const EncDesc* __restrict__ ed, const Counts* __restrict
     uint32_t h = murmur3_32(reinterpret_cast<const uint8_t*>(e.kptr), e.klen - 8, 0);
     const uint32_t d = (h >> 17) | (h << 15);
     uint32_t* bm = bitmap + F.bm_word;
+    uint64_t nbits = F.bm_bits;
+    if (fa.base) {  // the filter of the 2 KiB window the entry's block starts in
+      const uint32_t b = F.blk_begin + last_le<uint32_t>(start + F.blk_begin, F.blk_end - F.blk_begin, uint32_t(s));
+      const uint64_t slot = fa.base[lo] + ((C[b] - C[F.blk_begin]) >> kFilterBaseLg);
+      bm = bitmap + fa.woff[slot];
+      nbits = (fa.bytes[slot] - 1) * 8;
+    }
     for (uint32_t j = 0; j < fmt.k; ++j) {
-      const uint64_t bit = h % F.bm_bits;
+      const uint64_t bit = h % nbits;
       atomicOr(bm + (bit >> 5), 1u << (bit & 31));
       h += d;
     }
@@ -1148,10 +1231,29 @@ __global__ void k_index_write(const uint32_t* __restrict__ start, const Counts* 
 }
 
 // Filter bitmaps into the tables: one thread per 32-bit bitmap word of all tables.
-__global__ void k_filter_copy(const FileDesc* __restrict__ files, const Counts* __restrict__ cnt,
+__global__ void k_filter_copy(const FileDesc* __restrict__ files, const Counts* __restrict__ cnt, FiltArr fa,
                               const uint32_t* __restrict__ bitmap, uint8_t* __restrict__ out, uint64_t out_cap) {
   const uint32_t nf = cnt->nf;
   const uint64_t nw = cnt->bm_words;
+  if (fa.base) {
+    // filter array: word w of filter s, at the filter's offset in its table's filter block
+    const uint32_t ns = cnt->n_filt;
+    if (fa.base[nf] > fa.cap) return;
+    for (uint64_t w = gtid(); w < nw; w += gstride()) {
+      const uint32_t s = last_le<uint64_t>(fa.woff, ns, w);
+      const uint32_t f = last_le<uint64_t>(fa.base, nf, s);
+      const FileDesc F = files[f];
+      if (F.off + F.size > out_cap) continue;
+      const uint64_t i = 4 * (w - fa.woff[s]), bytes = fa.bytes[s] - 1;
+      if (fa.bytes[s] == 0 || i >= bytes) continue;
+      const uint32_t v = bitmap[w];
+      uint8_t* fp = out + F.off + F.data_size + (fa.boff[s] - fa.boff[fa.base[f]]) + i;
+#pragma unroll
+      for (uint32_t k = 0; k < 4; ++k)
+        if (i + k < bytes) fp[k] = uint8_t(v >> (8 * k));
+    }
+    return;
+  }
   for (uint64_t w = gtid(); w < nw; w += gstride()) {
     uint32_t lo = 0, hi = nf;  // last table whose bitmap starts at or before w
     while (hi - lo > 1) {
@@ -1171,6 +1273,23 @@ __global__ void k_filter_copy(const FileDesc* __restrict__ files, const Counts* 
   }
 }
 
+// Filter array, one thread per filter: its probe count byte (when not empty) and its entry
+// in the table's offset array.
+__global__ void k_filter_tail(const FileDesc* __restrict__ files, const Counts* __restrict__ cnt, FiltArr fa, Fmt fmt,
+                              uint8_t* __restrict__ out, uint64_t out_cap) {
+  const uint32_t nf = cnt->nf, ns = cnt->n_filt;
+  if (fa.base[nf] > fa.cap) return;
+  for (uint64_t s = gtid(); s < ns; s += gstride()) {
+    const uint32_t f = last_le<uint64_t>(fa.base, nf, s);
+    const FileDesc F = files[f];
+    if (F.off + F.size > out_cap) continue;
+    const uint64_t s0 = fa.base[f], rel = fa.boff[s] - fa.boff[s0];
+    uint8_t* fp = out + F.off + F.data_size;
+    if (fa.bytes[s]) fp[rel + fa.bytes[s] - 1] = uint8_t(fmt.k);
+    st_u32(fp + (fa.boff[fa.base[f + 1]] - fa.boff[s0]) + 4 * (s - s0), uint32_t(rel));
+  }
+}
+
 // One thread per table: probe count byte, metaindex, index restart count, footer, the three
 // block checksums queued for the multi-warp CRC, and the table's summary.
 __global__ void k_file_finish(const FileDesc* __restrict__ files, const Counts* __restrict__ cnt,
@@ -1185,20 +1304,27 @@ __global__ void k_file_finish(const FileDesc* __restrict__ files, const Counts* 
     }
     uint8_t* base = out + F.off;
     uint8_t* fp = base + F.data_size;
-    const uint64_t bytes = F.filter_size - 1;
-    fp[bytes] = uint8_t(fmt.k);
-    fp[bytes + 1] = 0;
-    // metaindex: one entry "filter.luda.bloom" -> filter handle, restart interval 1
+    const bool array = (fmt.flags & LUDA_F_FILTER_ARRAY) != 0;
+    if (array) {  // the offset array's position, then base_lg
+      st_u32(fp + F.filter_size - 5, uint32_t(F.filter_size - 5 - 4ull * F.n_filt));
+      fp[F.filter_size - 1] = uint8_t(kFilterBaseLg);
+    } else {
+      fp[F.filter_size - 1] = uint8_t(fmt.k);
+    }
+    fp[F.filter_size] = 0;
+    // metaindex: one entry "filter.luda.bloom" (or "filter.luda.bloom2k" for a filter
+    // array) -> filter handle, restart interval 1
     uint8_t* mp = base + F.meta_off;
     uint8_t hbuf[20];
     uint32_t hl = put_varint(hbuf, F.data_size);
     hl += put_varint(hbuf + hl, F.filter_size);
     uint32_t q = 0;
+    const char name[] = "filter.luda.bloom2k";
+    const uint32_t name_len = array ? 19 : 17;
     mp[q++] = 0;
-    mp[q++] = 17;
+    mp[q++] = uint8_t(name_len);
     mp[q++] = uint8_t(hl);
-    const char name[] = "filter.luda.bloom";
-    for (int i = 0; i < 17; ++i) mp[q++] = uint8_t(name[i]);
+    for (uint32_t i = 0; i < name_len; ++i) mp[q++] = uint8_t(name[i]);
     for (uint32_t i = 0; i < hl; ++i) mp[q++] = hbuf[i];
     st_u32(mp + q, 0);
     st_u32(mp + q + 4, 1);
@@ -1392,19 +1518,34 @@ void launch_index_sizes(const uint32_t* blk_start, const uint64_t* bsz, const ui
   count_launches(1);
 }
 
-void launch_file_layout(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_start,
-                        const uint64_t* C, const uint64_t* IX, Fmt fmt, const JobDev* jobs, uint32_t n_jobs,
-                        FileDesc* files, uint64_t* fsize, uint64_t* bmwords, cudaStream_t st) {
+void launch_filter_count(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint64_t* C,
+                         uint64_t* nfilt, cudaStream_t st) {
   if (!cap) return;
-  k_file_layout<<<grid_for(cap, 128), 128, 0, st>>>(file_start, cnt, blk_start, C, IX, fmt, jobs, n_jobs, files,
+  k_filter_count<<<grid_for(cap, 128), 128, 0, st>>>(file_start, cnt, C, nfilt); count_launches(1);
+}
+
+void launch_filter_sizes(const uint64_t* fbase, const uint32_t* file_start, const uint32_t* blk_start,
+                         const uint64_t* C, Counts* cnt, uint64_t slot_cap, Fmt fmt, uint64_t* fbytes,
+                         uint64_t* fwords, cudaStream_t st) {
+  k_filter_sizes<<<grid_for(slot_cap ? slot_cap : 1, 256), 256, 0, st>>>(fbase, file_start, blk_start, C, cnt,
+                                                                        slot_cap, fmt, fbytes, fwords);
+  count_launches(1);
+}
+
+void launch_file_layout(const uint32_t* file_start, const Counts* cnt, uint32_t cap, const uint32_t* blk_start,
+                        const uint64_t* C, const uint64_t* IX, Fmt fmt, FiltArr fa, const JobDev* jobs,
+                        uint32_t n_jobs, FileDesc* files, uint64_t* fsize, uint64_t* bmwords, cudaStream_t st) {
+  if (!cap) return;
+  k_file_layout<<<grid_for(cap, 128), 128, 0, st>>>(file_start, cnt, blk_start, C, IX, fmt, fa, jobs, n_jobs, files,
                                                     fsize, bmwords); count_launches(1);
 }
 
 void launch_file_offsets(FileDesc* files, Counts* cnt, uint32_t cap, const uint64_t* foff, const uint64_t* bmoff,
-                         JobDev* jobs, uint32_t n_jobs, uint64_t out_cap, uint64_t bm_cap, DErr* errs,
+                         FiltArr fa, JobDev* jobs, uint32_t n_jobs, uint64_t out_cap, uint64_t bm_cap, DErr* errs,
                          cudaStream_t st) {
-  k_file_offsets<<<grid_for(cap > n_jobs ? cap : n_jobs, 128), 128, 0, st>>>(files, cnt, foff, bmoff, jobs, n_jobs,
-                                                                             out_cap, bm_cap, errs); count_launches(1);
+  k_file_offsets<<<grid_for(cap > n_jobs ? cap : n_jobs, 128), 128, 0, st>>>(files, cnt, foff, bmoff, fa, jobs,
+                                                                             n_jobs, out_cap, bm_cap, errs);
+  count_launches(1);
 }
 
 void launch_zero_bitmap(uint32_t* bitmap, const Counts* cnt, uint64_t cap_words, cudaStream_t st) {
@@ -1466,9 +1607,11 @@ void launch_encode_big(const uint32_t* blk_start, Counts* cnt, uint32_t cap, con
 }
 
 void launch_bloom(const EncDesc* ed, const Counts* cnt, uint32_t cap, const FileDesc* files, Fmt fmt,
-                  uint32_t* bitmap, uint64_t out_cap, uint64_t bm_cap, cudaStream_t st) {
+                  const uint32_t* blk_start, const uint64_t* C, FiltArr fa, uint32_t* bitmap, uint64_t out_cap,
+                  uint64_t bm_cap, cudaStream_t st) {
   if (!cap) return;
-  k_bloom<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(ed, cnt, files, fmt, bitmap, out_cap, bm_cap);
+  k_bloom<<<grid_for(cap, elem_threads()), elem_threads(), 0, st>>>(ed, cnt, files, fmt, blk_start, C, fa, bitmap,
+                                                                     out_cap, bm_cap);
   count_launches(1);
 }
 
@@ -1483,10 +1626,14 @@ void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t c
 }
 
 void launch_file_finish(const FileDesc* files, const Counts* cnt, uint32_t cap, const uint32_t* bitmap,
-                        const uint32_t* surv, Recs recs, Fmt fmt, uint8_t* out, uint64_t out_cap, CrcTabs tabs,
-                        CrcMsg* msgs, FileMeta* meta, cudaStream_t st) {
+                        const uint32_t* surv, Recs recs, Fmt fmt, FiltArr fa, uint8_t* out, uint64_t out_cap,
+                        CrcTabs tabs, CrcMsg* msgs, FileMeta* meta, cudaStream_t st) {
   if (!cap) return;
-  k_filter_copy<<<kSms * 4, 256, 0, st>>>(files, cnt, bitmap, out, out_cap);
+  k_filter_copy<<<kSms * 4, 256, 0, st>>>(files, cnt, fa, bitmap, out, out_cap);
+  if (fa.base) {
+    k_filter_tail<<<grid_for(fa.cap ? fa.cap : 1, 256), 256, 0, st>>>(files, cnt, fa, fmt, out, out_cap);
+    count_launches(1);
+  }
   k_file_finish<<<grid_for(cap, 128, kSms), 128, 0, st>>>(files, cnt, surv, recs, fmt, out, out_cap, msgs, meta);
   count_launches(2);
   launch_msg_crc(msgs, &cnt->nf, 3, 3 * cap, nullptr, tabs, st);

@@ -26,6 +26,7 @@ ERR_PLAN_MISMATCH = -8
 F_STRICT_DUP = 1
 F_TRACE = 2
 F_SHORT_INDEX = 4  # shortened index keys (format variant R9s)
+F_FILTER_ARRAY = 8  # one bloom filter per 2 KiB of data block offsets (format variant R10a)
 MAX_SEQ = (1 << 56) - 1
 
 
@@ -493,13 +494,16 @@ class Server:
 
 
 def _run_arrays(run, device: bool):
+    # an empty array (no key or value bytes at all) still gets a buffer: the C ABI wants
+    # every array of a non-empty run non-NULL, and reads none of its bytes
+    arrs = [np.ascontiguousarray(a) if np.asarray(a).size else np.zeros(1, np.asarray(a).dtype)
+            for a in (run.ukeys, run.ukoff, run.seqs, run.types, run.vals, run.voff)]
     if device:
         import torch
-        keep = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
-                (run.ukeys, run.ukoff, run.seqs, run.types, run.vals, run.voff)]
+        keep = [torch.from_numpy(a).cuda() for a in arrs]
         ptrs = [t.data_ptr() for t in keep]
     else:
-        keep = [np.ascontiguousarray(a) for a in (run.ukeys, run.ukoff, run.seqs, run.types, run.vals, run.voff)]
+        keep = arrs
         ptrs = [a.ctypes.data for a in keep]
     ra = RunArrays(*ptrs, run.n)
     return ra, keep
