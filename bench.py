@@ -309,6 +309,8 @@ def run_ours(args, ws, rank, local):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if not args.no_variants:
+        line["variants"] = variants(job, inputs, in_bytes, stream)
     if not args.no_batched:
         line["batched"] = batched(args, stream)
     if not args.no_served:
@@ -316,6 +318,62 @@ def run_ours(args, ws, rank, local):
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
+
+
+def variants(job, inputs, in_bytes, stream, steps=5):
+    """The same large job with the format variants (shortened index keys R9s, the 2 KiB
+    filter array R10a, both) and as four range subcompactions (R13, split at the first
+    user keys of the lower level's tables at its quartiles): device ms per call (CUDA
+    events around `steps` calls after two warm-up calls) and input MiB/s."""
+    import torch
+    from paper_2004_03054_b300 import luda
+
+    L = luda.lib()
+    ins = (luda.Input * len(inputs))()
+    for i, t in enumerate(inputs):
+        ins[i].data, ins[i].size = t.data_ptr(), t.numel()
+    lower = [r for r in job.inputs if r.level == max(x.level for x in job.inputs)]
+    picks = sorted({len(lower) * k // 4 for k in (1, 2, 3)} - {0})
+    bounds = [bytes(lower[i].ukeys[int(lower[i].ukoff[0]):int(lower[i].ukoff[1])]) for i in picks]
+    bufs = [C.create_string_buffer(b, max(1, len(b))) for b in bounds]
+    keys = (luda.Key * len(bounds))()
+    for i, (b, buf) in enumerate(zip(bounds, bufs)):
+        keys[i].data, keys[i].len = C.cast(buf, C.c_void_p), len(b)
+
+    def timed(call):
+        def once():
+            out = luda.Outputs()
+            rc = call(out)
+            if rc != 0:
+                raise RuntimeError(f"variant failed: {rc} {luda.last_error_detail()}")
+            n = sum(out.tables[i].size for i in range(out.n_tables))
+            L.luda_outputs_free(C.byref(out))
+            return n
+        for _ in range(2):
+            once()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            nout = once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        return {"ms_per_step": round(ms, 4), "value": round(in_bytes / MiB / (ms / 1e3), 1), "unit": "MiB/s",
+                "output_bytes": nout}
+
+    res = {}
+    for name, flags in (("default", 0), ("short_index", luda.F_SHORT_INDEX), ("filter_array", luda.F_FILTER_ARRAY),
+                        ("short_index+filter_array", luda.F_SHORT_INDEX | luda.F_FILTER_ARRAY)):
+        o = luda.job_options(job, flags=flags, stream=C.c_void_p(stream.cuda_stream))
+        res[name] = timed(lambda out, o=o: L.luda_compact_device(ins, len(inputs), job.level, job.smallest_snapshot,
+                                                                 C.byref(o), C.byref(out)))
+    o = luda.job_options(job, stream=C.c_void_p(stream.cuda_stream))
+    res["subcompactions_4"] = timed(lambda out: L.luda_subcompact_device(ins, len(inputs), job.level,
+                                                                         job.smallest_snapshot, keys, len(bounds),
+                                                                         C.byref(o), C.byref(out)))
+    res["subcompactions_4"]["bounds"] = "first user keys of the lower level's tables at its quartiles"
+    return res
 
 
 def batched(args, stream):
@@ -560,6 +618,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batched leg: plan with the default launch shapes")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the format-variant and subcompaction timings")
     ap.add_argument("--serve-memtables", type=int, default=40)
     ap.add_argument("--serve-rate", type=float, default=8e6, help="writes per second of the served stream")
     ap.add_argument("--serve-slots", type=int, default=6)
