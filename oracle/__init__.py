@@ -30,6 +30,7 @@ ERR_DUPLICATE_KEY = -7
 F_STRICT_DUP = 1
 F_SHORT_INDEX = 4  # index keys shortened (format variant of R9)
 F_FILTER_ARRAY = 8  # one filter per 2 KiB of data block offsets (format variant of R10)
+F_COMPRESS = 16  # data blocks stored Snappy-compressed when that saves an eighth (R4c)
 MAX_SEQ = (1 << 56) - 1
 
 
@@ -105,6 +106,10 @@ def lib():
         L.ora_free_read.argtypes = [C.POINTER(_Read)]
         L.ora_bloom_may_contain.restype = C.c_int
         L.ora_bloom_may_contain.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64]
+        for name in ("ora_snappy_compress", "ora_snappy_uncompress"):
+            f = getattr(L, name)
+            f.restype = C.c_int
+            f.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p), C.POINTER(C.c_uint64)]
         L.ora_filter_array_may_contain.restype = C.c_int
         L.ora_filter_array_may_contain.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_uint64]
         L.ora_last_detail.restype = C.c_char_p
@@ -306,6 +311,30 @@ def bloom_may_contain(filter_contents: bytes, ukey: bytes) -> bool:
     f = _u8(filter_contents)
     k = _u8(ukey)
     return bool(lib().ora_bloom_may_contain(f.ctypes.data, len(f), k.ctypes.data, len(k)))
+
+
+def _codec(name, data: bytes):
+    a = _u8(data)
+    p = C.c_void_p()
+    n = C.c_uint64()
+    rc = getattr(lib(), name)(a.ctypes.data, len(a), C.byref(p), C.byref(n))
+    if rc != OK:
+        return rc, None
+    out = C.string_at(p, n.value) if n.value else b""
+    C.CDLL(None).free(p)
+    return OK, out
+
+
+def snappy_compress(data: bytes) -> bytes:
+    """This format's compressor (R4c): a Snappy-format stream."""
+    rc, out = _codec("ora_snappy_compress", data)
+    assert rc == OK
+    return out
+
+
+def snappy_uncompress(stream: bytes):
+    """(status, bytes | None) of a Snappy-format stream."""
+    return _codec("ora_snappy_uncompress", stream)
 
 
 def filter_array_may_contain(filter_contents: bytes, block_off: int, ukey: bytes) -> bool:

@@ -48,6 +48,7 @@
 #define ORA_F_STRICT_DUP 1u
 #define ORA_F_SHORT_INDEX 4u /* R9 variant: shortened index keys */
 #define ORA_F_FILTER_ARRAY 8u /* R10 variant: one filter per 2 KiB of data block offsets */
+#define ORA_F_COMPRESS 16u    /* R4c: data blocks stored Snappy-compressed when that saves 1/8 */
 
 #define ORA_MAGIC 0x4C55444153535431ull
 #define ORA_FOOTER 48
@@ -398,6 +399,7 @@ typedef struct {
   /* R10 variant: the filters generated so far (concatenated), their offsets, and the first
    * entry not yet in a filter */
   int filter_array;
+  int compress;     /* R4c */
   buf_t farr;
   uint32_t* foffs;
   uint64_t nfilt, capfilt, fgen;
@@ -406,17 +408,162 @@ typedef struct {
   uint32_t n_tables, cap_tables;
 } tb_t;
 
-/* Write a block: contents, then the trailer (type 0x00, masked CRC32C over contents and
- * type). Returns the handle of the block. */
-static int write_block(buf_t* file, const uint8_t* contents, uint64_t n, uint64_t* off, uint64_t* size) {
+/* Write a block: its stored bytes, then the trailer (type byte, masked CRC32C over the
+ * stored bytes and the type). Returns the handle of the block. */
+static int write_block_t(buf_t* file, const uint8_t* contents, uint64_t n, uint8_t type, uint64_t* off,
+                         uint64_t* size) {
   crc_init();
   *off = file->n;
   *size = n;
-  uint8_t type = 0;
   uint32_t c = crc_extend(0xFFFFFFFFu, contents, n);
   c = crc_extend(c, &type, 1) ^ 0xFFFFFFFFu;
   if (buf_put(file, contents, n) || buf_put(file, &type, 1) || buf_put_u32(file, ora_mask(c))) return -1;
   return 0;
+}
+
+static int write_block(buf_t* file, const uint8_t* contents, uint64_t n, uint64_t* off, uint64_t* size) {
+  return write_block_t(file, contents, n, 0, off, size);
+}
+
+/* ------------------------------------------------------------------------------------
+ * R4c block compression. The paper leaves Snappy compression to future work (§IV-A);
+ * LevelDB, which it builds on, stores a data block compressed (trailer type 1) when
+ * that saves at least an eighth of its bytes. The stream is the public Snappy format:
+ * varint32 uncompressed length, then elements whose tag's low two bits give the kind:
+ *   0 literal: length - 1 in the tag's upper six bits when below 60, else in the next
+ *     1..4 bytes (little-endian) for the values 60..63; then the literal bytes;
+ *   1 copy: length 4 + bits 2..4, offset = bits 5..7 << 8 | next byte;
+ *   2 copy: length 1 + bits 2..7, offset = next 2 bytes (little-endian);
+ *   3 copy: length 1 + bits 2..7, offset = next 4 bytes;
+ * a copy repeats `length` bytes from `offset` bytes back (1 <= offset <= bytes so far;
+ * overlapping copies repeat a pattern).
+ * ------------------------------------------------------------------------------------ */
+int ora_snappy_uncompress(const uint8_t* in, uint64_t n, uint8_t** out, uint64_t* out_len) {
+  *out = NULL;
+  *out_len = 0;
+  const uint8_t* p = in;
+  const uint8_t* end = in + n;
+  uint64_t ulen;
+  uint32_t a = get_varint(p, end, 32, &ulen);
+  if (!a) return ORA_ERR_CORRUPTION;
+  p += a;
+  uint8_t* o = (uint8_t*)malloc(ulen ? ulen : 1);
+  if (!o) return ORA_ERR_OOM;
+  uint64_t w = 0;
+  while (p < end) {
+    const uint8_t tag = *p++;
+    const uint32_t kind = tag & 3u;
+    uint64_t len, off = 0;
+    if (kind == 0) {
+      len = tag >> 2;
+      if (len >= 60) {
+        const uint32_t nb = (uint32_t)len - 59;
+        if ((uint64_t)(end - p) < nb) goto bad;
+        len = 0;
+        for (uint32_t i = 0; i < nb; i++) len |= (uint64_t)p[i] << (8 * i);
+        p += nb;
+      }
+      len += 1;
+      if ((uint64_t)(end - p) < len || ulen - w < len) goto bad;
+      memcpy(o + w, p, len);
+      p += len;
+      w += len;
+      continue;
+    }
+    const uint32_t nb = kind == 1 ? 1 : (kind == 2 ? 2 : 4);
+    if ((uint64_t)(end - p) < nb) goto bad;
+    if (kind == 1) {
+      len = 4 + ((tag >> 2) & 7u);
+      off = ((uint64_t)(tag >> 5) << 8) | p[0];
+    } else {
+      len = 1 + (tag >> 2);
+      for (uint32_t i = 0; i < nb; i++) off |= (uint64_t)p[i] << (8 * i);
+    }
+    p += nb;
+    if (off == 0 || off > w || ulen - w < len) goto bad;
+    for (uint64_t i = 0; i < len; i++, w++) o[w] = o[w - off];
+  }
+  if (w != ulen) goto bad;
+  *out = o;
+  *out_len = ulen;
+  return ORA_OK;
+bad:
+  free(o);
+  return ORA_ERR_CORRUPTION;
+}
+
+/* One literal element of len >= 1 bytes (shortest length form). */
+static int sn_literal(buf_t* out, const uint8_t* p, uint64_t len) {
+  const uint64_t v = len - 1;
+  uint8_t hdr[5];
+  uint32_t h = 0;
+  if (v < 60) {
+    hdr[h++] = (uint8_t)(v << 2);
+  } else {
+    const uint32_t nb = v < (1u << 8) ? 1 : v < (1u << 16) ? 2 : v < (1u << 24) ? 3 : 4;
+    hdr[h++] = (uint8_t)((59 + nb) << 2);
+    for (uint32_t i = 0; i < nb; i++) hdr[h++] = (uint8_t)(v >> (8 * i));
+  }
+  return buf_put(out, hdr, h) || buf_put(out, p, len);
+}
+
+static int sn_copy(buf_t* out, uint64_t off, uint64_t len) {
+  uint8_t e[3];
+  if (len <= 11 && off < 2048) {
+    e[0] = (uint8_t)(1u | (uint32_t)(len - 4) << 2 | (uint32_t)(off >> 8) << 5);
+    e[1] = (uint8_t)off;
+    return buf_put(out, e, 2);
+  }
+  e[0] = (uint8_t)(2u | (uint32_t)(len - 1) << 2);
+  e[1] = (uint8_t)off;
+  e[2] = (uint8_t)(off >> 8);
+  return buf_put(out, e, 3);
+}
+
+/* This format's compressor (the stream format admits many encodings of one block; this
+ * one is fixed so that every implementation writes the same bytes). Let H(i) be the
+ * 12-bit hash (x * 2654435761 mod 2^32) >> 20 of the little-endian 32-bit word x at
+ * position i (defined for i + 4 <= n), and cand(i) the largest j < i with H(j) = H(i).
+ * Scanning greedily from i = 0: if cand(i) exists, i - cand(i) < 65536 and the four bytes
+ * at cand(i) equal those at i, a copy of offset i - cand(i) and length L = the common
+ * length of the two positions' suffixes, at most 64 and at most n - i, is emitted and i
+ * moves by L; otherwise byte i joins the pending literal and i moves by one. Pending
+ * literal bytes are emitted as one literal element before each copy and at the end. A
+ * copy takes the 2-byte form (kind 1) when L <= 11 and the offset is below 2048, else the
+ * 3-byte form (kind 2). */
+int ora_snappy_compress(const uint8_t* in, uint64_t n, uint8_t** out, uint64_t* out_len) {
+  buf_t o = {0};
+  int64_t last[4096];
+  for (int i = 0; i < 4096; i++) last[i] = -1;
+  int rc = buf_put_varint(&o, n);
+  uint64_t i = 0, lit = 0, scanned = 0;
+  while (rc == 0 && i + 4 <= n) {
+    /* cand(i): every position below i has been entered into the table, in order */
+    while (scanned < i) {
+      last[(uint32_t)(rd_u32(in + scanned) * 2654435761u) >> 20] = (int64_t)scanned;
+      scanned++;
+    }
+    const uint32_t h = (uint32_t)(rd_u32(in + i) * 2654435761u) >> 20;
+    const int64_t j = last[h];
+    if (j >= 0 && i - (uint64_t)j < 65536 && memcmp(in + j, in + i, 4) == 0) {
+      uint64_t L = 4;
+      while (L < 64 && i + L < n && in[j + L] == in[i + L]) L++;
+      rc = (i > lit ? sn_literal(&o, in + lit, i - lit) : 0) || sn_copy(&o, i - (uint64_t)j, L);
+      i += L;
+      lit = i;
+    } else {
+      i++;
+    }
+  }
+  if (rc == 0 && n > lit) rc = sn_literal(&o, in + lit, n - lit);
+  if (rc) {
+    free(o.p);
+    *out = NULL;
+    return ORA_ERR_OOM;
+  }
+  *out = o.p;
+  *out_len = o.n;
+  return ORA_OK;
 }
 
 static int put_handle(buf_t* b, uint64_t off, uint64_t size) {
@@ -473,7 +620,23 @@ static int fa_start_block(tb_t* tb, uint64_t off);
 static int tb_flush_block(tb_t* tb) {
   uint64_t off, size;
   if (bb_finish(&tb->data)) return -1;
-  if (write_block(&tb->file, tb->data.buf.p, tb->data.buf.n, &off, &size)) return -1;
+  int stored = 0;
+  if (tb->compress) {
+    /* R4c: kept compressed when that saves at least an eighth of the raw bytes */
+    uint8_t* c;
+    uint64_t cn;
+    const uint64_t raw = tb->data.buf.n;
+    if (ora_snappy_compress(tb->data.buf.p, raw, &c, &cn)) return -1;
+    if (cn < raw - raw / 8) {
+      stored = 1;
+      if (write_block_t(&tb->file, c, cn, 1, &off, &size)) {
+        free(c);
+        return -1;
+      }
+    }
+    free(c);
+  }
+  if (!stored && write_block(&tb->file, tb->data.buf.p, tb->data.buf.n, &off, &size)) return -1;
   if (tb->filter_array && fa_start_block(tb, tb->file.n)) return -1;
   if (tb->short_index) {
     tb->pending = 1;
@@ -690,6 +853,7 @@ static void tb_init(tb_t* tb, uint64_t T, uint32_t R, uint32_t bpk, uint64_t tar
   memset(tb, 0, sizeof *tb);
   tb->short_index = (flags & ORA_F_SHORT_INDEX) != 0;
   tb->filter_array = (flags & ORA_F_FILTER_ARRAY) != 0;
+  tb->compress = (flags & ORA_F_COMPRESS) != 0;
   tb->T = T;
   tb->R = R;
   tb->bpk = bpk;
@@ -724,7 +888,32 @@ typedef struct {
   buf_t keys;
   ent_t* e;
   uint64_t n, cap;
+  uint8_t** owned;  /* decompressed blocks the entries' values point into */
+  uint64_t n_owned, cap_owned;
 } ents_t;
+
+static int ents_own(ents_t* es, uint8_t* p) {
+  if (!p) return 0;
+  if (es->n_owned == es->cap_owned) {
+    uint64_t cap = es->cap_owned ? es->cap_owned * 2 : 64;
+    uint8_t** q = (uint8_t**)realloc(es->owned, cap * sizeof(uint8_t*));
+    if (!q) {
+      free(p);
+      return -1;
+    }
+    es->owned = q;
+    es->cap_owned = cap;
+  }
+  es->owned[es->n_owned++] = p;
+  return 0;
+}
+
+static void ents_free(ents_t* es) {
+  for (uint64_t i = 0; i < es->n_owned; i++) free(es->owned[i]);
+  free(es->owned);
+  free(es->e);
+  free(es->keys.p);
+}
 
 static int ents_push(ents_t* es, const uint8_t* key, uint64_t klen, const uint8_t* val, uint64_t vlen,
                      uint32_t input, uint64_t pos) {
@@ -745,10 +934,11 @@ static int ents_push(ents_t* es, const uint8_t* key, uint64_t klen, const uint8_
   return buf_put(&es->keys, key, klen);
 }
 
-/* Read the block at handle (off, size) of a file: check bounds, the CRC over contents and
- * type, then the type byte. */
-static int read_block(const uint8_t* f, uint64_t fsize, uint64_t off, uint64_t size, const char* what,
-                      uint32_t input) {
+/* Read the block at handle (off, size) of a file: check bounds, the CRC over the stored
+ * bytes and type, then the type byte: 0, or with `type` given also 1 (R4c, compressed),
+ * returned there. */
+static int read_block_t(const uint8_t* f, uint64_t fsize, uint64_t off, uint64_t size, const char* what,
+                        uint32_t input, uint8_t* type) {
   uint64_t limit = fsize - ORA_FOOTER;
   if (off > limit || size > limit - off || ORA_TRAILER > limit - off - size) {
     detail("input %u: %s block handle (%llu,%llu) outside the file", input, what,
@@ -762,10 +952,36 @@ static int read_block(const uint8_t* f, uint64_t fsize, uint64_t off, uint64_t s
     detail("input %u: %s block at %llu: checksum mismatch", input, what, (unsigned long long)off);
     return ORA_ERR_CORRUPTION;
   }
-  if (f[off + size] != 0) {
+  if (f[off + size] != 0 && !(type && f[off + size] == 1)) {
     detail("input %u: %s block at %llu: compression type %u not supported", input, what,
            (unsigned long long)off, f[off + size]);
     return ORA_ERR_NOT_SUPPORTED;
+  }
+  if (type) *type = f[off + size];
+  return ORA_OK;
+}
+
+static int read_block(const uint8_t* f, uint64_t fsize, uint64_t off, uint64_t size, const char* what,
+                      uint32_t input) {
+  return read_block_t(f, fsize, off, size, what, input, NULL);
+}
+
+/* A data block's contents: the stored bytes, or for type 1 their decompression (a new
+ * buffer in *owned, which the caller frees). */
+static int load_data_block(const uint8_t* f, uint64_t fsize, uint64_t off, uint64_t size, uint32_t input,
+                           const uint8_t** contents, uint64_t* csize, uint8_t** owned) {
+  uint8_t type = 0;
+  *owned = NULL;
+  int rc = read_block_t(f, fsize, off, size, "data", input, &type);
+  if (rc) return rc;
+  *contents = f + off;
+  *csize = size;
+  if (type == 1) {
+    rc = ora_snappy_uncompress(f + off, size, owned, csize);
+    if (rc == ORA_ERR_CORRUPTION)
+      detail("input %u: data block at %llu: malformed compressed stream", input, (unsigned long long)off);
+    if (rc) return rc;
+    *contents = *owned;
   }
   return ORA_OK;
 }
@@ -952,8 +1168,12 @@ static int decode_input(const uint8_t* f, uint64_t fsize, uint32_t input, ents_t
         continue;
       }
     }
-    rc = read_block(f, fsize, ic.off[b], ic.size[b], "data", input);
-    if (rc == ORA_OK) rc = walk_block(f + ic.off[b], ic.size[b], &key, data_cb, &dc, "data", input, ic.off[b]);
+    const uint8_t* contents = NULL;
+    uint64_t csize = 0;
+    uint8_t* owned = NULL;
+    rc = load_data_block(f, fsize, ic.off[b], ic.size[b], input, &contents, &csize, &owned);
+    if (rc == ORA_OK && ents_own(es, owned)) rc = ORA_ERR_OOM;
+    if (rc == ORA_OK) rc = walk_block(contents, csize, &key, data_cb, &dc, "data", input, ic.off[b]);
     /* R9: a data block's index key is at or above its last internal key, and the previous
      * block's index key is below this block's first internal key */
     if (rc == ORA_OK) {
@@ -1081,8 +1301,7 @@ int ora_compact_range(const uint8_t* const* datas, const uint64_t* sizes, uint32
     free(tb.tables[i].largest);
   }
   free(tb.tables);
-  free(es.e);
-  free(es.keys.p);
+  ents_free(&es);
   if (rc != ORA_OK) {
     ora_free_result(res);
     return rc;
@@ -1292,8 +1511,12 @@ int ora_read_table(const uint8_t* f, uint64_t fsize, ora_read** out) {
   for (uint64_t b = 0; rc == ORA_OK && b < ri.ic.n; b++) {
     if (ri.ic.off[b] != expect) layout_ok = 0;
     expect = ri.ic.off[b] + ri.ic.size[b] + ORA_TRAILER;
-    rc = read_block(f, fsize, ri.ic.off[b], ri.ic.size[b], "data", 0);
-    if (rc == ORA_OK) rc = walk_block(f + ri.ic.off[b], ri.ic.size[b], &key, rd_cb, &dc, "data", 0, ri.ic.off[b]);
+    const uint8_t* contents = NULL;
+    uint64_t csize = 0;
+    uint8_t* owned = NULL;
+    rc = load_data_block(f, fsize, ri.ic.off[b], ri.ic.size[b], 0, &contents, &csize, &owned);
+    if (rc == ORA_OK) rc = walk_block(contents, csize, &key, rd_cb, &dc, "data", 0, ri.ic.off[b]);
+    free(owned);
     if (rc == ORA_OK) {
       if (dc.n == 0) {
         rc = ORA_ERR_CORRUPTION;

@@ -41,15 +41,62 @@ def varint(buf: bytes, pos: int, limit: int):
         shift += 7
 
 
-def block(buf: bytes, off: int, size: int) -> bytes:
+def block(buf: bytes, off: int, size: int, data: bool = False) -> bytes:
+    """A block's contents after its checksum check; a data block may be stored compressed
+    (type 1, R4c)."""
     contents = buf[off:off + size]
     typ = buf[off + size]
     (m,) = struct.unpack_from("<I", buf, off + size + 1)
     if crc32c(buf[off:off + size + 1]) != unmask(m):
         raise ValueError("crc")
+    if typ == 1 and data:
+        return snappy_uncompress(contents)
     if typ != 0:
         raise ValueError("compressed")
     return contents
+
+
+def snappy_uncompress(b: bytes) -> bytes:
+    """A Snappy-format stream, decoded element by element from the format's published
+    description (varint length; literal, 1-, 2- and 4-byte-offset copy elements)."""
+    ulen, p = varint(b, 0, len(b))
+    out = bytearray()
+    while p < len(b):
+        tag = b[p]
+        p += 1
+        kind = tag & 3
+        if kind == 0:
+            n = tag >> 2
+            if n >= 60:
+                nb = n - 59
+                if p + nb > len(b):
+                    raise ValueError("truncated literal length")
+                n = int.from_bytes(b[p:p + nb], "little")
+                p += nb
+            n += 1
+            if p + n > len(b):
+                raise ValueError("truncated literal")
+            out += b[p:p + n]
+            p += n
+            continue
+        if kind == 1:
+            if p + 1 > len(b):
+                raise ValueError("truncated copy")
+            n, off = 4 + ((tag >> 2) & 7), ((tag >> 5) << 8) | b[p]
+            p += 1
+        else:
+            nb = 2 if kind == 2 else 4
+            if p + nb > len(b):
+                raise ValueError("truncated copy")
+            n, off = 1 + (tag >> 2), int.from_bytes(b[p:p + nb], "little")
+            p += nb
+        if off == 0 or off > len(out):
+            raise ValueError("copy offset")
+        for _ in range(n):
+            out.append(out[-off])
+    if len(out) != ulen:
+        raise ValueError("length")
+    return bytes(out)
 
 
 def entries(contents: bytes):
@@ -99,10 +146,12 @@ def read(buf: bytes):
     foff, fsize, _ = handle(fh[0][1])
     filt = block(buf, foff, fsize)
     blocks = []
+    types = []
     allents = []
     for i, (k, v, _) in enumerate(index):
         off, size, _ = handle(v)
-        ents = entries(block(buf, off, size))
+        ents = entries(block(buf, off, size, data=True))
+        types.append(buf[off + size])
         # R9: last key <= index key < the next block's first key (internal key order)
         if len(k) < 8 or _order(ents[-1][0]) > _order(k):
             raise ValueError("index key is below its block's last key")
@@ -110,7 +159,8 @@ def read(buf: bytes):
             raise ValueError("index key is not below the next block's first key")
         blocks.append((off, size, ents))
         allents.extend((e[0], e[1]) for e in ents)
-    return dict(entries=allents, blocks=blocks, filter=filt, filter_name=fname, index_keys=[k for k, _, _ in index],
+    return dict(entries=allents, blocks=blocks, types=types, filter=filt, filter_name=fname,
+                index_keys=[k for k, _, _ in index],
                 handles=dict(filter=(foff, fsize), meta=(moff, msize), index=(ioff, isize)))
 
 

@@ -125,15 +125,19 @@ def test_crc_flip_is_corruption():
     assert res.status == oracle.ERR_CORRUPTION and res.tables == []
 
 
-def test_compressed_block_not_supported():
+@pytest.mark.parametrize("typ,status", [(1, oracle.ERR_CORRUPTION), (2, oracle.ERR_NOT_SUPPORTED),
+                                        (0xFF, oracle.ERR_NOT_SUPPORTED)])
+def test_block_types(typ, status):
+    """Type 1 (R4c, Snappy in LevelDB) is read as a compressed stream: raw contents under
+    that type do not decode to their announced length. Other types are not supported."""
     job, ins = _job_and_inputs()
     off, size = _first_data_block(ins[0])
     bad = bytearray(ins[0])
-    bad[off + size] = 1                                  # snappy in LevelDB
+    bad[off + size] = typ
     crc = oracle.mask(oracle.crc32c(bytes(bad[off: off + size + 1])))
     bad[off + size + 1: off + size + 5] = struct.pack("<I", crc)
     res = oracle_compact(job, [bytes(bad)] + ins[1:])
-    assert res.status == oracle.ERR_NOT_SUPPORTED
+    assert res.status == status
 
 
 @pytest.mark.parametrize("cut", [1, 8, 47, 48])
