@@ -45,7 +45,9 @@ typedef enum {
   LUDA_OK = 0,
   LUDA_ERR_INVALID_ARG = -1,   /* bad option, NULL pointer, unsorted run given to luda_build */
   LUDA_ERR_CORRUPTION = -2,    /* checksum, varint, offsets, footer, magic or key order */
-  LUDA_ERR_NOT_SUPPORTED = -3, /* a block whose type byte is not 0 (compressed) */
+  LUDA_ERR_NOT_SUPPORTED = -3, /* a block type other than 0 (raw) and 1 (compressed data block, R4c),
+                                  a compressed index block, or a compressed data block where the entry
+                                  point does not decompress (plans, the allocation-free check) */
   LUDA_ERR_OOM = -4,           /* device or pinned host allocation failed */
   LUDA_ERR_CUDA = -5,          /* a CUDA runtime call failed (no GPU, launch error) */
   LUDA_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
@@ -61,6 +63,9 @@ typedef enum {
                                   block of an SST in LUDA §II-A and LevelDB 1.22 of §IV-A): one bloom filter
                                   per 2 KiB of data block offsets, metaindex key "filter.luda.bloom2k";
                                   compactions do not read filter blocks, so inputs may carry either kind */
+#define LUDA_F_COMPRESS 16u   /* write compressed data blocks (format variant R4c): not built on the device,
+                                 whose entry points return LUDA_ERR_NOT_SUPPORTED for it; compressed INPUT
+                                 blocks are read without any flag. Other unknown flags: INVALID_ARG */
 #define LUDA_F_TRACE 2u      /* record per-stage device times (luda_outputs.stage_ms); LUDA_TRACE=1 in the
                                 environment does the same for every call. Stage boundaries always open
                                 NVTX ranges "luda/<stage>" on the calling thread. */
@@ -166,7 +171,14 @@ typedef struct {
  * luda_compact_device: inputs[].data are device pointers on opts->stream; the new tables
  *   stay on the device in one library-owned allocation.
  * `level` is the output level (recorded only); `smallest_snapshot` is the oldest sequence
- *   number any reader may still see ((1<<56)-1 when there are no snapshots). */
+ *   number any reader may still see ((1<<56)-1 when there are no snapshots).
+ * Input data blocks may be stored compressed (type 1, format rule R4c, the public Snappy
+ *   stream format; the Snappy compression the paper leaves to future work, §IV-A): their
+ *   checksums are verified on the stored bytes, then they are decompressed on the device
+ *   into a scratch arena (one warp per block) and sized a second time from their contents
+ *   (one more host round trip, only when such blocks are present). A stream that does not
+ *   decode to its announced length is LUDA_ERR_CORRUPTION. Output blocks are written
+ *   uncompressed (LUDA_F_COMPRESS output is not built on the device). */
 LUDA_API luda_status luda_compact(const luda_input* inputs, uint32_t n_inputs, int32_t level, uint64_t smallest_snapshot,
                          const luda_options* opts, luda_outputs* out);
 LUDA_API luda_status luda_compact_device(const luda_input* inputs, uint32_t n_inputs, int32_t level,
@@ -218,7 +230,9 @@ LUDA_API luda_status luda_subcompact_device(const luda_input* inputs, uint32_t n
  * input bytes and checks on the device that the sizes still match the plan
  * (LUDA_ERR_PLAN_MISMATCH otherwise). The inputs must stay valid and unchanged in size
  * for the plan's life. luda_plan_outputs gives each job's tables from the last run
- * (device pointers into the plan, valid until the next run or destroy). */
+ * (device pointers into the plan, valid until the next run or destroy). A job whose
+ * inputs hold compressed data blocks (R4c) reports LUDA_ERR_NOT_SUPPORTED in its outputs:
+ * a plan is sized from the stored blocks and does not decompress. */
 typedef struct luda_plan luda_plan;
 LUDA_API luda_status luda_plan_create(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts, luda_plan** plan);
 LUDA_API luda_status luda_plan_run(luda_plan* plan, void* stream);
@@ -347,7 +361,9 @@ LUDA_API luda_status luda_build_device(const luda_run* run, const luda_options* 
  * serialise them. The first call on a device (with that device current) looks up the
  * scratch with cudaGetSymbolAddress and uploads CRC tables with cudaMemcpyToSymbol;
  * make that first call before any stream capture. Returns the table's status (also in
- * out->status); on a corrupt table out->bad_offset is the byte offset of the fault. */
+ * out->status); on a corrupt table out->bad_offset is the byte offset of the fault. A
+ * compressed data block (type 1, R4c) is checked up to its checksum and then reported as
+ * LUDA_ERR_NOT_SUPPORTED: its structure is behind a decompression, which needs memory. */
 #define LUDA_NOALLOC_MAX_BLOCKS 16384u
 
 typedef struct {

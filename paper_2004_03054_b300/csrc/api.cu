@@ -305,6 +305,14 @@ luda_status opts_check(const luda_options* o, Fmt* fmt) {
     return LUDA_ERR_INVALID_ARG;
   }
   if (!tuning_valid(o->tuning)) return LUDA_ERR_INVALID_ARG;
+  if (o->flags & LUDA_F_COMPRESS) {
+    set_detail("LUDA_F_COMPRESS: compressed output blocks are not written on the device");
+    return LUDA_ERR_NOT_SUPPORTED;
+  }
+  if (o->flags & ~(LUDA_F_STRICT_DUP | LUDA_F_TRACE | LUDA_F_SHORT_INDEX | LUDA_F_FILTER_ARRAY)) {
+    set_detail("unknown option flags 0x%x", o->flags);
+    return LUDA_ERR_INVALID_ARG;
+  }
   uint32_t k = o->bloom_bits_per_key * 69 / 100;
   if (k < 1) k = 1;
   if (k > 30) k = 30;
@@ -984,9 +992,12 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   // ---- sizing: block scan ------------------------------------------------------------------
   Layout LB;
   uint16_t* d_hdr;
+  uint64_t *d_ulen, *d_ures;  // R4c: decompressed length and arena share of each block
   auto layoutB = [&](Layout& L, BlockDesc*& blocks, uint32_t*& nrec, uint64_t*& kbytes, uint32_t*& rec_first,
                      uint64_t*& key_first, uint32_t*& in_rec, uint64_t*& in_key, void*& tmp) {
     blocks = L.take<BlockDesc>(NB + 1);
+    d_ulen = L.take<uint64_t>(NB + 1);
+    d_ures = L.take<uint64_t>(NB + 1);
     d_hdr = L.take<uint16_t>(uint64_t(NB) * kHdrMax + 1);
     nrec = L.take<uint32_t>(NB + 1);
     kbytes = L.take<uint64_t>(NB + 1);
@@ -1016,40 +1027,50 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
                       side->s);
   tr.mark(12, side->s);
   CK(cudaEventRecord(side->ev[1], side->s));
-  tr.mark(1, st);
-  launch_block_walk(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, st);
-  tr.mark(2, st);
-  launch_zero_failed(d_blocks, NB, d_errs, d_nrec, d_kbytes, st);
-  launch_run_links(d_in, N, d_blocks, d_errs, d_link, st);
-  CK((exclusive_scan<uint32_t, uint32_t>(d_nrec, d_rec_first, NB, nullptr, d_tmpB, st)));
-  CK((exclusive_scan<uint64_t, uint64_t>(d_kbytes, d_key_first, NB, nullptr, d_tmpB, st)));
-  launch_input_ranges(d_in, N, d_rec_first, d_key_first, d_in_rec, d_in_key, st);
-  CK(cudaGetLastError());
+  // block contents: the stored blocks, or copies pointing at their decompressed contents
+  BlockDesc* d_cb = d_blocks;
   std::vector<uint32_t> in_rec(N + 1);
   std::vector<uint64_t> in_key(N + 1);
   std::vector<DErr> herr(n_jobs + 1);
   std::vector<uint8_t> link(N + 1, 0);
-  {
-    // one pinned piece for the five results (pageable vectors if the stage is full)
+  uint32_t comp_blocks = 0;
+  uint64_t comp_bytes = 0;
+  // entry counts and key bytes of every block, the inputs' record ranges and links; with
+  // `contents` the blocks are contents already (the second pass after decompression)
+  auto size_pass = [&](bool contents) -> luda_status {
+    launch_block_walk(d_cb, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, st, d_ulen, d_ures, contents);
+    if (!contents) tr.mark(2, st);
+    launch_zero_failed(d_cb, NB, d_errs, d_nrec, d_kbytes, st);
+    launch_run_links(d_in, N, d_cb, d_errs, d_link, st);
+    CK((exclusive_scan<uint32_t, uint32_t>(d_nrec, d_rec_first, NB, nullptr, d_tmpB, st)));
+    CK((exclusive_scan<uint64_t, uint64_t>(d_kbytes, d_key_first, NB, nullptr, d_tmpB, st)));
+    launch_input_ranges(d_in, N, d_rec_first, d_key_first, d_in_rec, d_in_key, st);
+    CK(cudaGetLastError());
+    // one pinned piece for the results (pageable vectors if the stage is full)
     uint32_t* p_rec = static_cast<uint32_t*>(hs.take(sizeof(uint32_t) * (N + 1)));
     uint64_t* p_key = static_cast<uint64_t*>(hs.take(sizeof(uint64_t) * (N + 1)));
     DErr* p_err = static_cast<DErr*>(hs.take(sizeof(DErr) * n_jobs));
     uint32_t* p_kv = static_cast<uint32_t*>(hs.take(sizeof(uint32_t)));
     uint8_t* p_link = static_cast<uint8_t*>(hs.take(N + 1));
-    const bool pinned = p_rec && p_key && p_err && p_kv && p_link;
+    uint64_t* p_comp = static_cast<uint64_t*>(hs.take(2 * sizeof(uint64_t)));
+    const bool pinned = p_rec && p_key && p_err && p_kv && p_link && p_comp;
+    uint64_t comp[2] = {0, 0};
     if (!pinned) {
       p_rec = in_rec.data();
       p_key = in_key.data();
       p_err = herr.data();
       p_kv = &fmt.max_kv;
       p_link = link.data();
+      p_comp = comp;
     }
     CK(cudaMemcpyAsync(p_rec, d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(p_key, d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
     if (n_jobs) CK(cudaMemcpyAsync(p_err, d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(p_kv, &d_cnt->max_kv, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     if (N) CK(cudaMemcpyAsync(p_link, d_link, N, cudaMemcpyDeviceToHost, st));
-    tr.mark(3, st);
+    CK(cudaMemcpyAsync(p_comp, &d_cnt->comp_blocks, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(p_comp + 1, &d_cnt->comp_bytes, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    if (!contents) tr.mark(3, st);
     CK(cudaStreamSynchronize(st));
     if (pinned) {
       memcpy(in_rec.data(), p_rec, sizeof(uint32_t) * (N + 1));
@@ -1057,7 +1078,39 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
       if (n_jobs) memcpy(herr.data(), p_err, sizeof(DErr) * n_jobs);
       fmt.max_kv = *p_kv;
       if (N) memcpy(link.data(), p_link, N);
+      comp[0] = p_comp[0];
+      comp[1] = p_comp[1];
     }
+    comp_blocks = uint32_t(comp[0]);
+    comp_bytes = comp[1];
+    return LUDA_OK;
+  };
+  tr.mark(1, st);
+  if ((rc = size_pass(false))) return rc;
+  if (comp_blocks) {
+    // R4c: the compressed blocks decompressed into one arena (each at a 16-byte multiple),
+    // then the job sized again from the contents
+    Layout LD;
+    uint64_t* d_uoff;
+    BlockDesc* d_cblocks;
+    uint8_t* d_dec;
+    auto layoutD = [&](Layout& L) {
+      d_uoff = L.take<uint64_t>(NB + 1);
+      d_cblocks = L.take<BlockDesc>(NB + 1);
+      d_dec = L.take<uint8_t>(comp_bytes + 64);
+    };
+    layoutD(LD);
+    uint8_t* bufD = static_cast<uint8_t*>(mem.get(LD.off));
+    if (!bufD) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
+    guard.ps.push_back(bufD);
+    LD = Layout{};
+    LD.base = bufD;
+    layoutD(LD);
+    CK((exclusive_scan<uint64_t, uint64_t>(d_ures, d_uoff, NB, nullptr, d_tmpB, st)));
+    CK(cudaMemcpyAsync(d_cblocks, d_blocks, sizeof(BlockDesc) * NB, cudaMemcpyDeviceToDevice, st));
+    launch_decompress(d_blocks, NB, d_ulen, d_uoff, d_dec, comp_bytes, d_cblocks, d_in, d_errs, st);
+    d_cb = d_cblocks;
+    if ((rc = size_pass(true))) return rc;
   }
 
   const uint32_t n_rec = in_rec[N];
@@ -1081,6 +1134,8 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     out_cap += filter_array_extra(fmt, 2 * kj + job_in_bytes[j] + 24 * nj, nj);
     bm_cap += nj * fmt.bpk / 32 + 5 * nj + 8;
   }
+  // compressed inputs (R4c): their values take up to their decompressed bytes in the output
+  out_cap += comp_bytes + (fmt.flags & LUDA_F_FILTER_ARRAY ? comp_bytes >> (kFilterBaseLg - 3) : 0);
   // merge schedule: linked inputs form one sorted run
   MergeSched ms;
   ms.tile = tuning().merge_tile;
@@ -1155,9 +1210,9 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
                        cudaMemcpyHostToDevice, st));
 
   tr.mark(4, st);
-  launch_decode(d_blocks, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
+  launch_decode(d_cb, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
   tr.mark(5, st);
-  launch_check_index(d_blocks, NB, d_in, d_nrec, d_rec_first, recs, d_arena, d_errs, st);
+  launch_check_index(d_cb, NB, d_in, d_nrec, d_rec_first, recs, d_arena, d_errs, st);
   launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
   launch_sort_init(d_ord0, d_pfx0, recs, d_arena, n_rec, st);
   for (size_t p = 0; p < pass_span0.size(); ++p)
@@ -1854,7 +1909,7 @@ const char* luda_strerror(luda_status s) {
     case LUDA_OK: return "ok";
     case LUDA_ERR_INVALID_ARG: return "invalid argument";
     case LUDA_ERR_CORRUPTION: return "corrupt input table";
-    case LUDA_ERR_NOT_SUPPORTED: return "not supported (compressed block)";
+    case LUDA_ERR_NOT_SUPPORTED: return "not supported (block type or compressed block on this path)";
     case LUDA_ERR_OOM: return "out of memory";
     case LUDA_ERR_CUDA: return "CUDA error";
     case LUDA_ERR_TIMEOUT: return "device wait timed out";

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_block_verify(const Blo
     if (lane == 0) {
       const uint32_t want = crc_unmask(ld_u32(b.ptr + b.size + 1));
       if (got != want) report(e, E_CORRUPT, in[b.input].local, b.off);
-      else if (b.ptr[b.size] != 0) report(e, E_NOTSUP, in[b.input].local, b.off);
+      else if (b.ptr[b.size] > 1) report(e, E_NOTSUP, in[b.input].local, b.off);  // 1: compressed (R4c)
     }
   }
 }
@@ -236,19 +236,57 @@ __device__ __forceinline__ uint32_t read_header(const uint8_t* p, const uint8_t*
   return pos;
 }
 
+// Stored blocks: a compressed one (type 1, R4c) is not walked here; with ulen given its
+// decompressed length goes to ulen[g] and its arena share (16-byte multiple) to ures[g]
+// (kRawBlock and 0 for the others), without ulen it is not supported. With `contents` the
+// blocks are contents (decompressed or raw), the type byte is not read, and the stored
+// bytes were counted already.
 __global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
                                                     const DInput* __restrict__ in, uint32_t* __restrict__ nrec,
                                                     uint64_t* __restrict__ kbytes, DErr* errs, Counts* counts,
-                                                    uint16_t* __restrict__ hdr_tab) {
-  unsigned long long data_bytes = 0;
-  uint32_t max_kv = 0;
+                                                    uint16_t* __restrict__ hdr_tab, uint64_t* __restrict__ ulen,
+                                                    uint64_t* __restrict__ ures, bool contents) {
+  unsigned long long data_bytes = 0, comp_bytes = 0;
+  uint32_t max_kv = 0, comp = 0;
   for (uint64_t g = gtid(); g < n_blocks; g += gstride()) {
     const BlockDesc b = blocks[g];
     DErr* e = errs + b.job;
     uint32_t cnt = 0;
     uint64_t kb = 0;
+    if (!contents && ulen) {
+      ulen[g] = kRawBlock;
+      ures[g] = 0;
+    }
     if (b.ptr != nullptr && *(volatile int32_t*)&e->code == 0) {
-      data_bytes += b.size + kTrailer;
+      if (!contents) data_bytes += b.size + kTrailer;
+      if (!contents && b.ptr[b.size] == 1) {
+        // the stream's length header: a varint32 inside the stored bytes
+        uint64_t n = 0;
+        uint32_t sh = 0, k = 0;
+        bool ok = false;
+        for (; k < 5 && k < b.size; ++k) {
+          const uint8_t c = b.ptr[k];
+          n |= uint64_t(c & 0x7Fu) << sh;
+          sh += 7;
+          if (!(c & 0x80u)) {
+            ok = n <= 0xFFFFFFFFull;
+            break;
+          }
+        }
+        if (!ulen) {
+          report(e, E_NOTSUP, in[b.input].local, b.off);
+        } else if (!ok) {
+          report(e, E_CORRUPT, in[b.input].local, b.off);
+        } else {
+          ulen[g] = n;
+          ures[g] = ((n + 15) & ~15ull) + 16;
+          comp_bytes += ures[g];
+          comp += 1;
+        }
+        nrec[g] = 0;
+        kbytes[g] = 0;
+        continue;
+      }
       const uint64_t nr = b.size >= 4 ? ld_u32(b.ptr + b.size - 4) : 0;
       bool bad = !(nr >= 1 && nr <= (b.size - 4) / 4);
       if (!bad) {
@@ -302,9 +340,17 @@ __global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict_
     kbytes[g] = kb;
   }
 #pragma unroll
-  for (int d = 16; d; d >>= 1) data_bytes += __shfl_xor_sync(0xFFFFFFFFu, data_bytes, d);
+  for (int d = 16; d; d >>= 1) {
+    data_bytes += __shfl_xor_sync(0xFFFFFFFFu, data_bytes, d);
+    comp_bytes += __shfl_xor_sync(0xFFFFFFFFu, comp_bytes, d);
+    comp += __shfl_xor_sync(0xFFFFFFFFu, comp, d);
+  }
   if ((threadIdx.x & 31u) == 0 && data_bytes)
     atomicAdd(reinterpret_cast<unsigned long long*>(&counts->in_data_bytes), data_bytes);
+  if ((threadIdx.x & 31u) == 0 && comp) {
+    atomicAdd(&counts->comp_blocks, comp);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&counts->comp_bytes), comp_bytes);
+  }
   max_kv = __reduce_max_sync(0xFFFFFFFFu, max_kv);
   if ((threadIdx.x & 31u) == 0 && max_kv) atomicMax(&counts->max_kv, max_kv);
 }
@@ -621,10 +667,124 @@ void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInpu
 }
 
 void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st) {
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st,
+                       uint64_t* ulen, uint64_t* ures, bool contents) {
   if (!n_blocks) return;
   const unsigned t = tuning().walk_threads;
-  k_block_walk<<<grid_for(n_blocks, t), t, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, cnt, hdr_tab);
+  k_block_walk<<<grid_for(n_blocks, t), t, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, cnt, hdr_tab, ulen,
+                                                    ures, contents);
+  count_launches(1);
+}
+
+// R4c, one warp per compressed block: lane 0 reads each element's tag and extra bytes
+// (every read inside the stored bytes), the warp writes its bytes. A copy of offset d
+// and length L writes out[w + i] = out[w - d + i mod d] for i < L: the copy's own output
+// repeats with period d, so every byte comes from the d bytes before w, already written
+// (elements are separated by __syncwarp). Any element that runs past the stream, copies
+// from before the output or writes past the announced length, or a total other than it,
+// is CORRUPTION; the block's contents pointer stays null then.
+__global__ void __launch_bounds__(256) k_decompress(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
+                                                    const uint64_t* __restrict__ ulen,
+                                                    const uint64_t* __restrict__ uoff, uint8_t* __restrict__ dst,
+                                                    uint64_t dst_cap, BlockDesc* __restrict__ cblocks,
+                                                    const DInput* __restrict__ in, DErr* errs) {
+  const uint32_t lane = lane_id();
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t g = gtid() / 32; g < n_blocks; g += warps) {
+    const uint64_t n = ulen[g];
+    if (n == kRawBlock) continue;
+    const BlockDesc b = blocks[g];
+    DErr* e = errs + b.job;
+    if (b.ptr == nullptr || *(volatile int32_t*)&e->code != 0) continue;
+    bool ok = uoff[g] + n <= dst_cap;
+    uint8_t* out = dst + uoff[g];
+    const uint8_t* src = b.ptr;
+    uint64_t p = 0;  // stream position (lane 0's view, broadcast)
+    while (p < b.size && (src[p] & 0x80u)) ++p;  // the length header (checked by the walk)
+    ++p;
+    uint64_t w = 0;
+    while (ok) {
+      // lane 0: the next element as (kind, length, offset or source position, its bytes)
+      uint32_t kind = 0, good = 1, done = 0;
+      uint64_t len = 0, arg = 0, used = 0;
+      if (lane == 0) {
+        if (p >= b.size) {
+          done = 1;
+        } else {
+          const uint32_t tag = src[p];
+          kind = tag & 3u;
+          if (kind == 0) {
+            len = tag >> 2;
+            uint32_t nb = 0;
+            if (len >= 60) {
+              nb = uint32_t(len) - 59;
+              if (b.size - p - 1 < nb) {
+                good = 0;
+              } else {
+                len = 0;
+                for (uint32_t i = 0; i < nb; ++i) len |= uint64_t(src[p + 1 + i]) << (8 * i);
+              }
+            }
+            len += 1;
+            used = 1 + nb;
+            arg = p + used;  // literal bytes
+            if (good && (b.size - arg < len || n - w < len)) good = 0;
+            used += len;
+          } else {
+            const uint32_t nb = kind == 1 ? 1u : (kind == 2 ? 2u : 4u);
+            if (b.size - p - 1 < nb) {
+              good = 0;
+            } else if (kind == 1) {
+              len = 4 + ((tag >> 2) & 7u);
+              arg = (uint64_t(tag >> 5) << 8) | src[p + 1];
+            } else {
+              len = 1 + (tag >> 2);
+              for (uint32_t i = 0; i < nb; ++i) arg |= uint64_t(src[p + 1 + i]) << (8 * i);
+            }
+            used = 1 + nb;
+            if (good && (arg == 0 || arg > w || n - w < len)) good = 0;
+          }
+        }
+      }
+      done = __shfl_sync(0xFFFFFFFFu, done, 0);
+      good = __shfl_sync(0xFFFFFFFFu, good, 0);
+      if (done) break;
+      if (!good) {
+        ok = false;
+        break;
+      }
+      kind = __shfl_sync(0xFFFFFFFFu, kind, 0);
+      len = __shfl_sync(0xFFFFFFFFu, len, 0);
+      arg = __shfl_sync(0xFFFFFFFFu, arg, 0);
+      used = __shfl_sync(0xFFFFFFFFu, used, 0);
+      if (kind == 0) {
+        for (uint64_t i = lane; i < len; i += 32) out[w + i] = src[arg + i];
+      } else {
+        for (uint64_t i = lane; i < len; i += 32) out[w + i] = out[w - arg + i % arg];
+      }
+      __syncwarp();
+      w += len;
+      p += used;
+    }
+    if (ok && w != n) ok = false;
+    if (lane == 0) {
+      if (ok) {
+        cblocks[g].ptr = out;
+        cblocks[g].size = n;
+      } else {
+        cblocks[g].ptr = nullptr;
+        report(e, E_CORRUPT, in[b.input].local, b.off);
+      }
+    }
+  }
+}
+
+void launch_decompress(const BlockDesc* blocks, uint32_t n_blocks, const uint64_t* ulen, const uint64_t* uoff,
+                       uint8_t* dst, uint64_t dst_cap, BlockDesc* cblocks, const DInput* in, DErr* errs,
+                       cudaStream_t st) {
+  if (!n_blocks) return;
+  k_decompress<<<grid_for(uint64_t(n_blocks) * 32, 256), 256, 0, st>>>(blocks, n_blocks, ulen, uoff, dst, dst_cap,
+                                                                      cblocks, in, errs);
   count_launches(1);
 }
 

@@ -103,6 +103,8 @@ struct Counts {
   uint32_t crc_next_in;     // next input data block for the checksum kernels' warps
   uint32_t crc_next_out;    // next output data block for the trailer kernels' warps
   uint32_t n_filt;          // filters of all tables' filter arrays (LUDA_F_FILTER_ARRAY)
+  uint32_t comp_blocks;     // compressed input data blocks (R4c) seen by the block walk
+  uint64_t comp_bytes;      // arena bytes their contents take once decompressed
 };
 
 // The filter arrays of a batch (LUDA_F_FILTER_ARRAY; base == nullptr otherwise). Filter s
@@ -247,7 +249,14 @@ void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput*
 void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const DErr* errs, DErr* verr,
                          CrcTabs tabs, uint32_t* next, bool helper, cudaStream_t st);
 void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st);
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st,
+                       uint64_t* ulen = nullptr, uint64_t* ures = nullptr, bool contents = false);
+// R4c: compressed data blocks (ulen[g] != kRawBlock) decompressed into dst + uoff[g], one
+// warp per block; cblocks[g] (a copy of blocks[g]) then points at the contents.
+constexpr uint64_t kRawBlock = ~0ull;
+void launch_decompress(const BlockDesc* blocks, uint32_t n_blocks, const uint64_t* ulen, const uint64_t* uoff,
+                       uint8_t* dst, uint64_t dst_cap, BlockDesc* cblocks, const DInput* in, DErr* errs,
+                       cudaStream_t st);
 // After decode: every data block's index key equals its last internal key.
 void launch_check_index(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,
                         const uint32_t* rec_first, Recs recs, const uint8_t* arena, DErr* errs, cudaStream_t st);

@@ -40,6 +40,11 @@ def test_noalloc_check_matches_compaction_two_calls_in_a_row():
         for _ in range(2):
             got = luda.check_table_noalloc(t)
             torch.cuda.synchronize()
+            if x is not inputs[-1] and x == bytes(comp):
+                # a type-1 block: the compaction reads it as a compressed stream (raw contents
+                # do not decode), the allocation-free check does not decompress
+                assert (got.status, ref.status) == (luda.ERR_NOT_SUPPORTED, luda.ERR_CORRUPTION)
+                continue
             assert got.status == ref.status, (got.status, ref.status)
             if ref.status == 0:
                 assert got.n_entries == ref.n_in_entries
