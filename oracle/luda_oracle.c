@@ -523,39 +523,50 @@ static int sn_copy(buf_t* out, uint64_t off, uint64_t len) {
 /* This format's compressor (the stream format admits many encodings of one block; this
  * one is fixed so that every implementation writes the same bytes). Let H(i) be the
  * 12-bit hash (x * 2654435761 mod 2^32) >> 20 of the little-endian 32-bit word x at
- * position i (defined for i + 4 <= n), and cand(i) the largest j < i with H(j) = H(i).
- * Scanning greedily from i = 0: if cand(i) exists, i - cand(i) < 65536 and the four bytes
- * at cand(i) equal those at i, a copy of offset i - cand(i) and length L = the common
- * length of the two positions' suffixes, at most 64 and at most n - i, is emitted and i
- * moves by L; otherwise byte i joins the pending literal and i moves by one. Pending
- * literal bytes are emitted as one literal element before each copy and at the end. A
- * copy takes the 2-byte form (kind 1) when L <= 11 and the offset is below 2048, else the
- * 3-byte form (kind 2). */
+ * position i (defined for i + 4 <= n), and cand(i) the largest j < i with H(j) = H(i),
+ * over every position of the block. The block is cut into 64-byte segments [64s, e),
+ * e = min(64s + 64, n), each parsed greedily from its start on its own: at position i,
+ * if e - i >= 4, cand(i) exists, i - cand(i) < 65536 and the four bytes at cand(i) equal
+ * those at i, a copy of offset i - cand(i) and length L = the common length of the two
+ * positions' suffixes, at most e - i, is emitted and i moves by L; otherwise byte i joins
+ * the pending literal and i moves by one. Pending literal bytes are emitted as one literal
+ * element before each copy and at the segment's end. A copy takes the 2-byte form (kind 1)
+ * when L <= 11 and the offset is below 2048, else the 3-byte form (kind 2). Segments make
+ * the parses independent of each other (a parallel compressor gives each its own thread)
+ * and keep every copy within 64 bytes. */
 int ora_snappy_compress(const uint8_t* in, uint64_t n, uint8_t** out, uint64_t* out_len) {
   buf_t o = {0};
   int64_t last[4096];
-  for (int i = 0; i < 4096; i++) last[i] = -1;
-  int rc = buf_put_varint(&o, n);
-  uint64_t i = 0, lit = 0, scanned = 0;
-  while (rc == 0 && i + 4 <= n) {
-    /* cand(i): every position below i has been entered into the table, in order */
-    while (scanned < i) {
-      last[(uint32_t)(rd_u32(in + scanned) * 2654435761u) >> 20] = (int64_t)scanned;
-      scanned++;
-    }
-    const uint32_t h = (uint32_t)(rd_u32(in + i) * 2654435761u) >> 20;
-    const int64_t j = last[h];
-    if (j >= 0 && i - (uint64_t)j < 65536 && memcmp(in + j, in + i, 4) == 0) {
-      uint64_t L = 4;
-      while (L < 64 && i + L < n && in[j + L] == in[i + L]) L++;
-      rc = (i > lit ? sn_literal(&o, in + lit, i - lit) : 0) || sn_copy(&o, i - (uint64_t)j, L);
-      i += L;
-      lit = i;
-    } else {
-      i++;
-    }
+  for (int k = 0; k < 4096; k++) last[k] = -1;
+  /* cand of every position, entered in position order */
+  int64_t* cand = (int64_t*)malloc((n ? n : 1) * sizeof(int64_t));
+  if (!cand) return ORA_ERR_OOM;
+  for (uint64_t p = 0; p < n; p++) {
+    cand[p] = -1;
+    if (p + 4 > n) continue;
+    const uint32_t h = (uint32_t)(rd_u32(in + p) * 2654435761u) >> 20;
+    cand[p] = last[h];
+    last[h] = (int64_t)p;
   }
-  if (rc == 0 && n > lit) rc = sn_literal(&o, in + lit, n - lit);
+  int rc = buf_put_varint(&o, n);
+  for (uint64_t s0 = 0; rc == 0 && s0 < n; s0 += 64) {
+    const uint64_t e = s0 + 64 < n ? s0 + 64 : n;
+    uint64_t i = s0, lit = s0;
+    while (rc == 0 && i < e) {
+      const int64_t j = cand[i];
+      if (e - i >= 4 && j >= 0 && i - (uint64_t)j < 65536 && memcmp(in + j, in + i, 4) == 0) {
+        uint64_t L = 4;
+        while (i + L < e && in[j + L] == in[i + L]) L++;
+        rc = (i > lit ? sn_literal(&o, in + lit, i - lit) : 0) || sn_copy(&o, i - (uint64_t)j, L);
+        i += L;
+        lit = i;
+      } else {
+        i++;
+      }
+    }
+    if (rc == 0 && e > lit) rc = sn_literal(&o, in + lit, e - lit);
+  }
+  free(cand);
   if (rc) {
     free(o.p);
     *out = NULL;

@@ -59,8 +59,14 @@ def test_decode_rejects(stream):
 #     10 -> literal "ab" (tag 04), kind-1 copy 1 | 6 << 2 = 0x19, offset 02;
 #   "abcdefgh" * 4: the eight 4-grams of the first period hash apart (0x630 0x637 0x63d
 #     0x643 0x649 0xdcf 0x0fd 0x546); position 8 finds 0 with length 24 > 11 -> literal
-#     of 8 (tag 0x1c), kind-2 copy 2 | 23 << 2 = 0x5e, offset 08 00.
+#     of 8 (tag 0x1c), kind-2 copy 2 | 23 << 2 = 0x5e, offset 08 00;
+#   100 zero bytes: segment [0, 64): literal 00, then position 1 finds 0 and copies to the
+#     segment's end (length 63 > 11: kind 2, 2 | 62 << 2 = 0xfa, offset 01 00); segment
+#     [64, 100) starts its own parse: position 64 finds 63, copy of length 36 (0x8e 01 00);
+#   66 zero bytes: as above, then segment [64, 66) has fewer than 4 bytes: literal 00 00.
 @pytest.mark.parametrize("data,stream", [
+    (bytes(100), "64" "0000" "fa0100" "8e0100"),
+    (bytes(66), "42" "0000" "fa0100" "040000"),
     (b"a" * 10, "0a" "0061" "1501"),
     (b"ab" * 6, "0c" "046162" "1902"),
     (b"abcdefgh" * 4, "20" "1c" + b"abcdefgh".hex() + "5e0800"),
@@ -89,7 +95,7 @@ def test_round_trip(seed):
         c = oracle.snappy_compress(data)
         assert sstpy.snappy_uncompress(c) == data
         assert oracle.snappy_uncompress(c) == (0, data)
-    # a long run of zeros: copies of the maximum length 64 at offset 1 after one literal byte
+    # a long run of zeros: one literal byte, then one copy of offset 1 per 64-byte segment
     z = oracle.snappy_compress(bytes(1000))
     assert len(z) < 60 and sstpy.snappy_uncompress(z) == bytes(1000)
 
