@@ -63,9 +63,12 @@ typedef enum {
                                   block of an SST in LUDA §II-A and LevelDB 1.22 of §IV-A): one bloom filter
                                   per 2 KiB of data block offsets, metaindex key "filter.luda.bloom2k";
                                   compactions do not read filter blocks, so inputs may carry either kind */
-#define LUDA_F_COMPRESS 16u   /* write compressed data blocks (format variant R4c): not built on the device,
-                                 whose entry points return LUDA_ERR_NOT_SUPPORTED for it; compressed INPUT
-                                 blocks are read without any flag. Other unknown flags: INVALID_ARG */
+#define LUDA_F_COMPRESS 16u   /* write data blocks compressed (format variant R4c, LevelDB's Snappy type in the
+                                 public stream format; the paper's future work, §IV-A) when that saves an
+                                 eighth: the raw blocks go to scratch, one warp per block compresses them
+                                 (64-byte segments parsed one per lane), the file cut and layout use the
+                                 stored sizes. Compressed INPUT blocks are read without any flag. Unknown
+                                 flags are LUDA_ERR_INVALID_ARG */
 #define LUDA_F_TRACE 2u      /* record per-stage device times (luda_outputs.stage_ms); LUDA_TRACE=1 in the
                                 environment does the same for every call. Stage boundaries always open
                                 NVTX ranges "luda/<stage>" on the calling thread. */
@@ -178,7 +181,7 @@ typedef struct {
  *   into a scratch arena (one warp per block) and sized a second time from their contents
  *   (one more host round trip, only when such blocks are present). A stream that does not
  *   decode to its announced length is LUDA_ERR_CORRUPTION. Output blocks are written
- *   uncompressed (LUDA_F_COMPRESS output is not built on the device). */
+ *   compressed with LUDA_F_COMPRESS, else raw. */
 LUDA_API luda_status luda_compact(const luda_input* inputs, uint32_t n_inputs, int32_t level, uint64_t smallest_snapshot,
                          const luda_options* opts, luda_outputs* out);
 LUDA_API luda_status luda_compact_device(const luda_input* inputs, uint32_t n_inputs, int32_t level,

@@ -305,11 +305,7 @@ luda_status opts_check(const luda_options* o, Fmt* fmt) {
     return LUDA_ERR_INVALID_ARG;
   }
   if (!tuning_valid(o->tuning)) return LUDA_ERR_INVALID_ARG;
-  if (o->flags & LUDA_F_COMPRESS) {
-    set_detail("LUDA_F_COMPRESS: compressed output blocks are not written on the device");
-    return LUDA_ERR_NOT_SUPPORTED;
-  }
-  if (o->flags & ~(LUDA_F_STRICT_DUP | LUDA_F_TRACE | LUDA_F_SHORT_INDEX | LUDA_F_FILTER_ARRAY)) {
+  if (o->flags & ~(LUDA_F_STRICT_DUP | LUDA_F_TRACE | LUDA_F_SHORT_INDEX | LUDA_F_FILTER_ARRAY | LUDA_F_COMPRESS)) {
     set_detail("unknown option flags 0x%x", o->flags);
     return LUDA_ERR_INVALID_ARG;
   }
@@ -402,7 +398,18 @@ struct PackBufs {
   // filter arrays (LUDA_F_FILTER_ARRAY): per table, then per filter
   uint64_t *fcount, *fbase, *fbytes, *fwords, *fboff, *fwoff;
   uint64_t slot_cap;  // filters the buffers hold (0 without filter arrays)
+  PackCz cz;          // compressed blocks (raw_cap == 0 without LUDA_F_COMPRESS)
 };
+
+// Scratch of the compressed-block pass for an output bound of out_cap bytes and at most
+// cap blocks: raw blocks (each rounded to 16 bytes with a trailer's room) and their streams
+// (n + n / 32 + 16 rounded, plus 16, per block).
+static uint64_t cz_raw_cap(const Fmt& fmt, uint64_t out_cap, uint64_t cap) {
+  return (fmt.flags & LUDA_F_COMPRESS) ? out_cap + 32 * (cap + 1) : 0;
+}
+static uint64_t cz_stream_cap(const Fmt& fmt, uint64_t out_cap, uint64_t cap) {
+  return (fmt.flags & LUDA_F_COMPRESS) ? out_cap + out_cap / 32 + 48 * (cap + 1) : 0;
+}
 
 // Capacity of the filter arrays: a table has at most (data bytes >> 11) + 1 filters, and
 // out_cap bounds all tables' bytes.
@@ -418,8 +425,23 @@ static uint64_t filter_array_extra(const Fmt& fmt, uint64_t data, uint64_t n) {
   return (fmt.flags & LUDA_F_FILTER_ARRAY) ? (data >> (kFilterBaseLg - 3)) + 24 * n + 64 : 0;
 }
 
-void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t key_cap, uint64_t slot_cap) {
+void pack_layout(Layout& L, PackBufs& b, uint32_t cap, uint64_t bm_cap, uint64_t key_cap, uint64_t slot_cap,
+                 uint64_t raw_cap = 0, uint64_t c_cap = 0, uint32_t n_jobs = 1) {
   b.meta_cap = cap + 1;
+  b.cz = PackCz{};
+  b.cz.raw_cap = raw_cap;
+  b.cz.c_cap = c_cap;
+  if (raw_cap) {
+    b.cz.rawsz = L.take<uint64_t>(cap + 1);
+    b.cz.czsz = L.take<uint64_t>(cap + 1);
+    b.cz.Craw = L.take<uint64_t>(cap + 1);
+    b.cz.Cc = L.take<uint64_t>(cap + 1);
+    b.cz.ctype = L.take<uint8_t>(cap + 1);
+    b.cz.rfiles = L.take<FileDesc>(uint64_t(n_jobs) + 1);
+    b.cz.rbf = L.take<uint32_t>(cap + 1);
+    b.cz.raw = L.take<uint8_t>(raw_cap + 64);
+    b.cz.cz = L.take<uint8_t>(c_cap + 64);
+  }
   b.key_cap = key_cap + 1;
   b.slot_cap = slot_cap;
   const uint64_t nfa = slot_cap ? cap + 1 : 1;
@@ -482,6 +504,17 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   launch_compact_flags(b.sflags, b.bpos, &cnt->n_surv, cap, b.blk_start, &cnt->nb, st);
   launch_job_blocks(jobs, n_jobs, b.bpos, st);
   launch_block_sizes(b.blk_start, cnt, cap, b.P, b.dr, fmt, b.bsz, b.disk, st);
+  if (b.cz.raw_cap) {
+    // R4c: the raw blocks into scratch (the block cut used their sizes), then each block
+    // compressed and its stored size taken for the file cut and the layout
+    launch_compress_blocks(b.cz, jobs, n_jobs, cnt, cap, b.bsz, b.disk, b.scan_tmp, st);
+    launch_encode(b.blk_start, cnt, cap, b.cz.rbf, b.cz.rfiles, b.cz.Craw, b.bsz, b.surv, b.lcp, b.sd, b.dr, b.ed,
+                  b.bd, recs, arena, fmt, fmt.max_kv, b.cz.raw, b.cz.raw_cap, b.enc_done, b.big, errs, tabs, st);
+    launch_encode_big(b.blk_start, cnt, cap, b.cz.rbf, b.cz.rfiles, b.cz.Craw, b.bsz, b.surv, b.lcp, b.sd, b.dr,
+                      recs, arena, fmt, b.cz.raw, b.cz.raw_cap, b.big, tabs, st);
+    launch_compress(b.cz, cnt, cap, b.bsz, b.disk, st);
+    CK(cudaGetLastError());
+  }
   CK((exclusive_scan<uint64_t, uint64_t>(b.disk, b.C, cap, &cnt->nb, b.scan_tmp, st)));
   launch_file_next(b.C, cnt, cap, jobs, n_jobs, fmt, b.fnext, st);
   launch_stitch(b.fnext, &cnt->nb, cap, &cnt->gap_blk, jobs, n_jobs, true, b.fflags, b.stitch_tmp, st);
@@ -509,16 +542,20 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   launch_file_offsets(b.files, cnt, cap, b.foff, b.bmoff, fa, jobs, n_jobs, out_cap, bm_cap, errs, st);
   launch_zero_bitmap(b.bitmap, cnt, bm_cap, st);
   trace_mark(tr, 7, st);
-  launch_encode(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, b.ed, b.bd, recs,
-                arena,
-                fmt, fmt.max_kv, out, out_cap, b.enc_done, b.big, errs, tabs, st);
+  if (b.cz.raw_cap) {
+    launch_place(b.cz, cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, st);
+  } else {
+    launch_encode(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, b.ed, b.bd, recs,
+                  arena, fmt, fmt.max_kv, out, out_cap, b.enc_done, b.big, errs, tabs, st);
+  }
   trace_mark(tr, 8, st);
   // data block trailers on the side stream (joined by the caller through event slot 3)
   CK(fork_join(side, 2, st, side->s));
   launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, false, side->s);
   CK(cudaEventRecord(side->ev[3], side->s));
-  launch_encode_big(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
-                    fmt, out, out_cap, b.big, tabs, st);
+  if (!b.cz.raw_cap)
+    launch_encode_big(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
+                      fmt, out, out_cap, b.big, tabs, st);
   launch_bloom(b.ed, cnt, cap, b.files, fmt, b.blk_start, b.C, fa, b.bitmap, out_cap, bm_cap, st);
   launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, fmt, out,
                      out_cap, st);
@@ -1177,7 +1214,8 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     d_pos = L.take<uint32_t>(n_rec + 1);
     d_co = L.take<uint32_t>(max_tiles + 1);
     d_spans = L.take<MergeSpan>(spans.size() + 1);
-    pack_layout(L, pb, cap, bm_cap, key_cap, filter_slot_cap(fmt, out_cap, cap));
+    pack_layout(L, pb, cap, bm_cap, key_cap, filter_slot_cap(fmt, out_cap, cap), cz_raw_cap(fmt, out_cap, cap),
+                cz_stream_cap(fmt, out_cap, cap), n_jobs);
   };
   layoutC(LC);
   if (gate && !gate->admit(LA.off + LB.off + LC.off + out_cap + gate->extra)) {
@@ -1358,7 +1396,8 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
     d_err = l.take<DErr>(4);  // main chain and input checksums (collect's layout)
     d_job = l.take<JobDev>(1);
     d_cnt = l.take<Counts>(1);
-    pack_layout(l, pb, n, bm_cap, 2 * K + 64, filter_slot_cap(fmt, out_cap, n));
+    pack_layout(l, pb, n, bm_cap, 2 * K + 64, filter_slot_cap(fmt, out_cap, n), cz_raw_cap(fmt, out_cap, n),
+                cz_stream_cap(fmt, out_cap, n), 1);
     if (host_in) {
       h_ukeys = l.take<uint8_t>(ku + 16);
       h_ukoff = l.take<uint64_t>(n + 1);
@@ -1704,7 +1743,8 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     d_pos = L.take<uint32_t>(n_rec + 1);
     d_co = L.take<uint32_t>(max_tiles + 1);
     d_spans = L.take<MergeSpan>(spans.size() + 1);
-    pack_layout(L, pb, cap, bm_cap, 2 * K + 64, filter_slot_cap(fmt, out_cap, cap));
+    pack_layout(L, pb, cap, bm_cap, 2 * K + 64, filter_slot_cap(fmt, out_cap, cap), cz_raw_cap(fmt, out_cap, cap),
+                cz_stream_cap(fmt, out_cap, cap), n_jobs);
   };
   layC(LC);
   LC.base = alloc(LC.off);

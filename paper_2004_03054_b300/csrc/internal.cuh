@@ -369,6 +369,25 @@ void launch_index_write(const uint32_t* blk_start, const Counts* cnt, uint32_t c
 void launch_file_finish(const FileDesc* files, const Counts* cnt, uint32_t cap, const uint32_t* bitmap,
                         const uint32_t* surv, Recs recs, Fmt fmt, FiltArr fa, uint8_t* out, uint64_t out_cap,
                         CrcTabs tabs, CrcMsg* msgs, FileMeta* meta, cudaStream_t st);
+// Compressed data blocks (R4c, LUDA_F_COMPRESS): scratch for the raw blocks and their
+// streams, per-block offsets into both, pseudo-tables (one per job) for the raw pass.
+struct PackCz {
+  uint64_t *rawsz, *czsz, *Craw, *Cc;
+  uint8_t* ctype;
+  FileDesc* rfiles;
+  uint32_t* rbf;
+  uint8_t *raw, *cz;
+  uint64_t raw_cap, c_cap;
+};
+// Raw and stream offsets of every block and the pseudo-tables (after the block sizes).
+void launch_compress_blocks(PackCz z, JobDev* jobs, uint32_t n_jobs, Counts* cnt, uint32_t cap, uint64_t* bsz,
+                            uint64_t* disk, void* scan_tmp, cudaStream_t st);
+// After the raw pass: every block compressed, bsz/disk turned into the stored sizes.
+void launch_compress(PackCz z, Counts* cnt, uint32_t cap, uint64_t* bsz, uint64_t* disk, cudaStream_t st);
+// After the layout: stored bytes and type bytes into the tables; done[b] = 1 for all.
+void launch_place(PackCz z, Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,
+                  const uint64_t* C, const uint64_t* bsz, uint8_t* out, uint64_t out_cap, uint8_t* done,
+                  cudaStream_t st);
 void launch_key_lens(const FileMeta* meta, const Counts* cnt, uint32_t cap, uint64_t* lens, cudaStream_t st);
 void launch_key_gather(FileMeta* meta, Counts* cnt, uint32_t cap, const uint64_t* koff, const FileDesc* files,
                        const uint32_t* surv, Recs recs, const uint8_t* arena, uint8_t* keybuf, cudaStream_t st);

@@ -1131,6 +1131,200 @@ __global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(Counts* __restr
   }
 }
 
+// ---- compressed data blocks (R4c) ------------------------------------------------------------
+// With LUDA_F_COMPRESS the encoders first write every block's raw contents into a scratch
+// arena (block b at Craw[b], one pseudo-table per job), k_compress compresses each block
+// into a second scratch (block b at Cc[b]) and turns bsz/disk into the stored sizes (the
+// block cut used the raw ones), the file cut and layout run on the stored sizes, and
+// k_place copies each block's stored bytes and type byte into its table; the trailer
+// checksums then cover the stored bytes.
+
+// Scratch shares: raw block with room for a trailer, and the compressor's bound (a 64-byte
+// segment of literals takes at most 66 bytes; a copy never takes more than it covers; the
+// length header at most 5), both 16-byte multiples.
+__global__ void k_raw_sizes(const Counts* __restrict__ cnt, const uint64_t* __restrict__ bsz,
+                            uint64_t* __restrict__ rawsz, uint64_t* __restrict__ czsz) {
+  const uint32_t nb = cnt->nb;
+  for (uint64_t b = gtid(); b < nb; b += gstride()) {
+    const uint64_t n = bsz[b];
+    rawsz[b] = (n + kTrailer + 15) & ~15ull;
+    czsz[b] = ((n + n / 32 + 16 + 15) & ~15ull) + 16;
+  }
+}
+
+__global__ void k_raw_files(const JobDev* __restrict__ jobs, uint32_t n_jobs, const Counts* __restrict__ cnt,
+                            const uint64_t* __restrict__ Craw, FileDesc* __restrict__ rfiles,
+                            uint32_t* __restrict__ rbf) {
+  for (uint64_t j = gtid(); j < n_jobs; j += gstride()) {
+    FileDesc F{};
+    F.blk_begin = jobs[j].blk_begin;
+    F.blk_end = jobs[j].blk_end;
+    F.off = Craw[F.blk_begin];
+    F.size = Craw[F.blk_end] - F.off;
+    F.job = uint32_t(j);
+    rfiles[j] = F;
+  }
+  const uint32_t nb = cnt->nb;
+  for (uint64_t b = gtid(); b < nb; b += gstride()) rbf[b] = job_of_block(jobs, n_jobs, uint32_t(b));
+}
+
+constexpr uint32_t kCzWarps = 4;
+constexpr uint32_t kCzTab = 4096;      // hash table entries (12-bit hash)
+constexpr uint32_t kCzWin = 32 * 64;   // positions per window: one 64-byte segment per lane
+constexpr uint32_t kCzStage = 72;      // staging bytes per lane (a segment's elements: at most 66)
+constexpr uint32_t kCzNone = 0xFFFFFFFFu;
+constexpr uint32_t kCzWarpSmem = (kCzTab + kCzWin) * 4 + 32 * kCzStage;
+constexpr uint32_t kCzSmem = kCzWarps * kCzWarpSmem;
+
+__device__ __forceinline__ uint32_t ld4_bytes(const uint8_t* p) {
+  return uint32_t(p[0]) | uint32_t(p[1]) << 8 | uint32_t(p[2]) << 16 | uint32_t(p[3]) << 24;
+}
+
+// One warp per block. Per window of 2048 positions: the warp steps through it 32
+// positions at a time (lane = position) to find cand(i), the latest earlier position with
+// the same 12-bit hash (within the step by matching hashes across lanes, else from the
+// table of earlier steps, which the last lane of each hash then updates); then each lane
+// parses its own 64-byte segment from the window's candidates into its staging bytes, and
+// the segments are written out in order after a warp scan of their sizes. The block is
+// kept compressed (type 1) when the stream is shorter than raw - raw / 8.
+__global__ void __launch_bounds__(kCzWarps * 32) k_compress(const Counts* __restrict__ cnt,
+                                                            const uint64_t* __restrict__ Craw,
+                                                            const uint64_t* __restrict__ Cc,
+                                                            uint64_t* __restrict__ bsz, uint64_t* __restrict__ disk,
+                                                            const uint8_t* __restrict__ raw, uint64_t raw_cap,
+                                                            uint8_t* __restrict__ cz, uint64_t c_cap,
+                                                            uint8_t* __restrict__ ctype) {
+  extern __shared__ __align__(16) uint8_t s_cz[];
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t* tab = reinterpret_cast<uint32_t*>(s_cz + warp * kCzWarpSmem);
+  uint32_t* cw = tab + kCzTab;
+  uint8_t* stage = reinterpret_cast<uint8_t*>(cw + kCzWin) + lane * kCzStage;
+  const uint32_t nb = cnt->nb;
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t b = gtid() / 32; b < nb; b += warps) {
+    const uint64_t n = bsz[b];
+    const uint64_t cbound = n + n / 32 + 16;
+    if (Craw[b] + n > raw_cap || Cc[b] + cbound > c_cap) {
+      if (lane == 0) ctype[b] = 0;
+      continue;
+    }
+    const uint8_t* in = raw + Craw[b];
+    uint8_t* o = cz + Cc[b];
+    for (uint32_t k = lane; k < kCzTab; k += 32) tab[k] = kCzNone;
+    uint32_t total = 0;  // stream bytes so far: the length header, then the segments
+    {
+      uint64_t v = n;
+      while (v >= 0x80) {
+        if (lane == 0) o[total] = uint8_t(v | 0x80);
+        v >>= 7;
+        ++total;
+      }
+      if (lane == 0) o[total] = uint8_t(v);
+      ++total;
+    }
+    __syncwarp();
+    for (uint64_t wb = 0; wb < n; wb += kCzWin) {
+      const uint64_t we = wb + kCzWin < n ? wb + kCzWin : n;
+      for (uint64_t base = wb; base < we; base += 32) {
+        const uint64_t p = base + lane;
+        const bool valid = p + 4 <= n;
+        const uint32_t h = valid ? (ld4_bytes(in + p) * 2654435761u) >> 20 : kCzTab + lane;
+        const uint32_t m = __match_any_sync(0xFFFFFFFFu, h);
+        const uint32_t lower = m & ((1u << lane) - 1u);
+        uint32_t c = kCzNone;
+        if (valid) c = lower ? uint32_t(base) + (31u - __clz(lower)) : tab[h];
+        __syncwarp();
+        if (valid && (m >> lane) == 1u) tab[h] = uint32_t(p);
+        __syncwarp();
+        if (p < we) cw[p - wb] = c;
+      }
+      __syncwarp();
+      // this lane's segment [s0, e)
+      const uint64_t s0 = wb + 64ull * lane;
+      uint32_t sz = 0;
+      if (s0 < n) {
+        const uint64_t e = s0 + 64 < n ? s0 + 64 : n;
+        uint64_t i = s0, lit = s0;
+        auto literal = [&](uint64_t from, uint64_t to) {
+          const uint32_t len = uint32_t(to - from), v = len - 1;
+          if (v < 60) {
+            stage[sz++] = uint8_t(v << 2);
+          } else {
+            stage[sz++] = uint8_t(60u << 2);
+            stage[sz++] = uint8_t(v);
+          }
+          for (uint64_t k = from; k < to; ++k) stage[sz++] = in[k];
+        };
+        while (i < e) {
+          const uint32_t c = cw[i - wb];
+          bool ok = e - i >= 4 && c != kCzNone && i - c < 65536;
+          if (ok) ok = ld4_bytes(in + c) == ld4_bytes(in + i);
+          if (ok) {
+            uint64_t L = 4;
+            while (i + L < e && in[c + L] == in[i + L]) ++L;
+            if (i > lit) literal(lit, i);
+            const uint64_t off = i - c;
+            if (L <= 11 && off < 2048) {
+              stage[sz++] = uint8_t(1u | uint32_t(L - 4) << 2 | uint32_t(off >> 8) << 5);
+              stage[sz++] = uint8_t(off);
+            } else {
+              stage[sz++] = uint8_t(2u | uint32_t(L - 1) << 2);
+              stage[sz++] = uint8_t(off);
+              stage[sz++] = uint8_t(off >> 8);
+            }
+            i += L;
+            lit = i;
+          } else {
+            ++i;
+          }
+        }
+        if (e > lit) literal(lit, e);
+      }
+      // segments in order
+      uint32_t x = sz;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= uint32_t(d)) x += y;
+      }
+      const uint32_t at = total + x - sz;
+      for (uint32_t k = 0; k < sz; ++k) o[at + k] = stage[k];
+      total += __shfl_sync(0xFFFFFFFFu, x, 31);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      const bool keep = total < n - n / 8;
+      ctype[b] = keep ? 1 : 0;
+      bsz[b] = keep ? total : n;
+      disk[b] = bsz[b] + kTrailer;
+    }
+  }
+}
+
+// One warp per block: its stored bytes (compressed or raw) and type byte into its table.
+__global__ void k_place(const Counts* __restrict__ cnt, const uint32_t* __restrict__ blk_file,
+                        const FileDesc* __restrict__ files, const uint64_t* __restrict__ C,
+                        const uint64_t* __restrict__ bsz, const uint64_t* __restrict__ Craw,
+                        const uint64_t* __restrict__ Cc, const uint8_t* __restrict__ raw,
+                        const uint8_t* __restrict__ cz, const uint8_t* __restrict__ ctype,
+                        uint8_t* __restrict__ out, uint64_t out_cap, uint8_t* __restrict__ done) {
+  const uint32_t lane = lane_id(), nb = cnt->nb;
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t b = gtid() / 32; b < nb; b += warps) {
+    const FileDesc F = files[blk_file[b]];
+    if (F.off + F.size > out_cap) continue;
+    uint8_t* dst = out + F.off + (C[b] - C[F.blk_begin]);
+    const uint8_t t = ctype[b];
+    const uint8_t* src = t ? cz + Cc[b] : raw + Craw[b];
+    const uint64_t n = bsz[b];
+    for (uint64_t k = lane; k < n; k += 32) dst[k] = src[k];
+    if (lane == 0) {
+      dst[n] = t;
+      done[b] = 1;
+    }
+  }
+}
+
 // MurmurHash3 x86_32 (Appleby, public domain), from its published description.
 __device__ __forceinline__ uint32_t rotl(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }
 
@@ -1659,6 +1853,34 @@ void launch_build_records(const uint8_t* ukeys, const uint64_t* ukoff, const uin
 void launch_build_check(Recs recs, const uint8_t* arena, uint32_t n, DErr* err, cudaStream_t st) {
   if (n < 2) return;
   k_build_check<<<grid_for(n, 256), 256, 0, st>>>(recs, arena, n, err); count_launches(1);
+}
+
+void launch_compress_blocks(PackCz z, JobDev* jobs, uint32_t n_jobs, Counts* cnt, uint32_t cap, uint64_t* bsz,
+                            uint64_t* disk, void* scan_tmp, cudaStream_t st) {
+  if (!cap) return;
+  k_raw_sizes<<<grid_for(cap, 256), 256, 0, st>>>(cnt, bsz, z.rawsz, z.czsz);
+  count_launches(1);
+  exclusive_scan<uint64_t, uint64_t>(z.rawsz, z.Craw, cap, &cnt->nb, scan_tmp, st);
+  exclusive_scan<uint64_t, uint64_t>(z.czsz, z.Cc, cap, &cnt->nb, scan_tmp, st);
+  k_raw_files<<<grid_for(cap > n_jobs ? cap : n_jobs, 256), 256, 0, st>>>(jobs, n_jobs, cnt, z.Craw, z.rfiles, z.rbf);
+  count_launches(1);
+}
+
+void launch_compress(PackCz z, Counts* cnt, uint32_t cap, uint64_t* bsz, uint64_t* disk, cudaStream_t st) {
+  if (!cap) return;
+  smem_optin(k_compress, kCzSmem);
+  k_compress<<<grid_for(uint64_t(cap) * 32, kCzWarps * 32), kCzWarps * 32, kCzSmem, st>>>(
+      cnt, z.Craw, z.Cc, bsz, disk, z.raw, z.raw_cap, z.cz, z.c_cap, z.ctype);
+  count_launches(1);
+}
+
+void launch_place(PackCz z, Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,
+                  const uint64_t* C, const uint64_t* bsz, uint8_t* out, uint64_t out_cap, uint8_t* done,
+                  cudaStream_t st) {
+  if (!cap) return;
+  k_place<<<grid_for(uint64_t(cap) * 32, 256), 256, 0, st>>>(cnt, blk_file, files, C, bsz, z.Craw, z.Cc, z.raw,
+                                                             z.cz, z.ctype, out, out_cap, done);
+  count_launches(1);
 }
 
 }  // namespace luda

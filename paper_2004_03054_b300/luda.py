@@ -27,7 +27,7 @@ F_STRICT_DUP = 1
 F_TRACE = 2
 F_SHORT_INDEX = 4  # shortened index keys (format variant R9s)
 F_FILTER_ARRAY = 8  # one bloom filter per 2 KiB of data block offsets (format variant R10a)
-F_COMPRESS = 16  # compressed output blocks (R4c): not supported on the device
+F_COMPRESS = 16  # data blocks written compressed when that saves an eighth (format variant R4c)
 MAX_SEQ = (1 << 56) - 1
 
 

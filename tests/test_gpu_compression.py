@@ -140,9 +140,75 @@ def test_plan_reports_compressed_inputs_not_supported():
     plan.close()
 
 
-def test_compressed_output_and_unknown_flags_are_refused():
+def test_unknown_flags_are_refused():
     ins = _inputs(1, 50, 100, 4096, seed=51)
-    res = luda.compact_device([dev(ins[0])], oracle.MAX_SEQ, opts=luda.options(flags=luda.F_COMPRESS))
-    assert res.status == luda.ERR_NOT_SUPPORTED and res.tables == []
     res = luda.compact_device([dev(ins[0])], oracle.MAX_SEQ, opts=luda.options(flags=64))
     assert res.status == luda.ERR_INVALID_ARG
+
+
+# ---- compressed output (LUDA_F_COMPRESS) ---------------------------------------------------
+CZ = luda.F_COMPRESS
+
+
+@pytest.mark.parametrize("n_in,n,vlen,T,target", [(1, 300, 200, 4096, 64 << 10), (3, 200, 100, 4096, 32 << 10),
+                                                  (4, 150, 40, 256, 8 << 10), (2, 60, 3000, 1, 64 << 10),
+                                                  (3, 100, 1000, 16384, 1 << 20), (5, 400, 0, 512, 16 << 10),
+                                                  (2, 300, 5000, 65536, 1 << 20)])
+def test_compressed_output(n_in, n, vlen, T, target):
+    ins = _inputs(n_in, n, vlen, T, seed=7 * n + vlen + T, compress=(True, False))
+    got = _both(ins, T=T, target=target, flags=CZ)
+    if vlen >= 100:
+        assert any(t == 1 for x in got.tables for t in sstpy.read(x)["types"])
+
+
+@pytest.mark.parametrize("flags", [CZ | luda.F_SHORT_INDEX, CZ | luda.F_FILTER_ARRAY,
+                                   CZ | luda.F_SHORT_INDEX | luda.F_FILTER_ARRAY])
+def test_compressed_output_with_other_variants(flags):
+    ins = _inputs(3, 250, 150, 2048, seed=61)
+    _both(ins, T=2048, target=24 << 10, flags=flags)
+
+
+def test_compressed_output_of_incompressible_and_tiny_jobs():
+    job = W.config1(seed=8, scale=1 / 32)
+    ins = [oracle.build_tables(r, job.block_size, job.restart_interval, job.bloom_bits_per_key, U64MAX).tables[0].data
+           for r in job.inputs]
+    got = _both(ins, T=job.block_size, target=job.target_file_size, flags=CZ, snapshot=job.smallest_snapshot,
+                bottommost=job.bottommost)
+    assert all(t == 0 for x in got.tables for t in sstpy.read(x)["types"])   # random values: kept raw
+    for seed in range(12):
+        rng = np.random.default_rng(700 + seed)
+        j = W.tiny_job(rng, n_keys=int(rng.integers(1, 200)), max_versions=3, n_inputs=int(rng.integers(1, 5)),
+                       key_len=(0, 20), val_len=(0, 400))
+        tins = [oracle.build_tables(r, 256, 4, 10, U64MAX, flags=oracle.F_COMPRESS).tables[0].data
+                for r in j.inputs]
+        _both(tins, T=int(rng.choice([1, 64, 256, 4096])), target=int(rng.choice([1, 3000, 1 << 20])), flags=CZ,
+              snapshot=j.smallest_snapshot, bottommost=j.bottommost)
+
+
+def test_compressed_builder_batch_and_plan():
+    run = _run(500, 300, seed=71)
+    want = oracle.build_tables(run, 4096, 16, 10, 64 << 10, flags=oracle.F_COMPRESS)
+    got = luda.build_device(run, luda.options(4096, 16, 10, 64 << 10, flags=CZ))
+    assert got.status == 0, got.detail
+    assert [t.cpu().numpy().tobytes() for t in got.tables] == [t.data for t in want.tables]
+    ins = [_inputs(2, 200, 150, 4096, seed=s) for s in (81, 82)]
+    wants = [oracle.compact(x, oracle.MAX_SEQ, False, 4096, 16, 10, 32 << 10, oracle.F_COMPRESS) for x in ins]
+    batch = [([dev(b) for b in x], oracle.MAX_SEQ, False) for x in ins]
+    opts = luda.options(4096, 16, 10, 32 << 10, flags=CZ)
+    rc, outs = luda.batch_compact_device(batch, opts)
+    assert rc == 0
+    for g, w in zip(outs, wants):
+        g.tables = [t.cpu().numpy().tobytes() for t in g.tables]
+        assert_same(g, w)
+    raw_ins = [[oracle.build_tables(_run(200, 150, seed=s + k), 4096, 16, 10, U64MAX).tables[0].data for k in (0, 1)]
+               for s in (91, 93)]
+    # plans take uncompressed inputs; their output may be compressed
+    pw = [oracle.compact(x, oracle.MAX_SEQ, False, 4096, 16, 10, 32 << 10, oracle.F_COMPRESS) for x in raw_ins]
+    plan = luda.Plan([([dev(b) for b in x], oracle.MAX_SEQ, False) for x in raw_ins], opts)
+    for _ in range(2):
+        plan.run()
+        torch.cuda.synchronize()
+        for g, w in zip(plan.outputs(), pw):
+            g.tables = [t.cpu().numpy().tobytes() for t in g.tables]
+            assert_same(g, w)
+    plan.close()
