@@ -310,7 +310,7 @@ def run_ours(args, ws, rank, local):
         "e2e": e2e,
     }
     if not args.no_variants:
-        line["variants"] = variants(job, inputs, in_bytes, stream)
+        line["variants"] = variants(job, inputs, in_bytes, stream, scale=args.scale)
     if not args.no_batched:
         line["batched"] = batched(args, stream)
     if not args.no_served:
@@ -320,13 +320,16 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def variants(job, inputs, in_bytes, stream, steps=5):
+def variants(job, inputs, in_bytes, stream, scale=1.0, steps=5):
     """The same large job with the format variants (shortened index keys R9s, the 2 KiB
-    filter array R10a, both) and as four range subcompactions (R13, split at the first
-    user keys of the lower level's tables at its quartiles): device ms per call (CUDA
-    events around `steps` calls after two warm-up calls) and input MiB/s."""
+    filter array R10a, both, compressed output R4c) and as four range subcompactions (R13,
+    split at the first user keys of the lower level's tables at its quartiles), and the
+    same job shape with compressible values whose inputs are stored compressed (read, and
+    read + written compressed): device ms per call (CUDA events around `steps` calls after
+    two warm-up calls) and input MiB/s (stored input bytes)."""
     import torch
     from paper_2004_03054_b300 import luda
+    from paper_2004_03054_b300 import workloads as W
 
     L = luda.lib()
     ins = (luda.Input * len(inputs))()
@@ -364,7 +367,8 @@ def variants(job, inputs, in_bytes, stream, steps=5):
 
     res = {}
     for name, flags in (("default", 0), ("short_index", luda.F_SHORT_INDEX), ("filter_array", luda.F_FILTER_ARRAY),
-                        ("short_index+filter_array", luda.F_SHORT_INDEX | luda.F_FILTER_ARRAY)):
+                        ("short_index+filter_array", luda.F_SHORT_INDEX | luda.F_FILTER_ARRAY),
+                        ("compress_output", luda.F_COMPRESS)):
         o = luda.job_options(job, flags=flags, stream=C.c_void_p(stream.cuda_stream))
         res[name] = timed(lambda out, o=o: L.luda_compact_device(ins, len(inputs), job.level, job.smallest_snapshot,
                                                                  C.byref(o), C.byref(out)))
@@ -373,6 +377,31 @@ def variants(job, inputs, in_bytes, stream, steps=5):
                                                                          job.smallest_snapshot, keys, len(bounds),
                                                                          C.byref(o), C.byref(out)))
     res["subcompactions_4"]["bounds"] = "first user keys of the lower level's tables at its quartiles"
+    res["compress_output"]["note"] = "random values: blocks are compressed, then kept raw (no eighth saved)"
+
+    # R4c on compressible data: the same job shape with values drawn from a word vocabulary
+    # (about half compressible), its input tables built compressed on the device
+    cjob = W.with_compressible_values(W.config3(seed=3, scale=scale))
+    cins = []
+    for r in cjob.inputs:
+        b = luda.build_device(r, luda.options(cjob.block_size, cjob.restart_interval, cjob.bloom_bits_per_key,
+                                              (1 << 64) - 1, flags=luda.F_COMPRESS))
+        if b.status != 0 or len(b.tables) != 1:
+            raise RuntimeError(f"compressed input build failed: {b.status} {b.detail}")
+        cins.append(b.tables[0])
+    del cjob
+    cin = (luda.Input * len(cins))()
+    for i, t in enumerate(cins):
+        cin[i].data, cin[i].size = t.data_ptr(), t.numel()
+    stored = sum(t.numel() for t in cins)
+    for name, flags in (("compressed_inputs", 0), ("compressed_inputs+compress_output", luda.F_COMPRESS)):
+        o = luda.job_options(job, flags=flags, stream=C.c_void_p(stream.cuda_stream))
+        r = timed(lambda out, o=o: L.luda_compact_device(cin, len(cins), job.level, job.smallest_snapshot,
+                                                         C.byref(o), C.byref(out)))
+        r["value"] = round(stored / MiB / (r["ms_per_step"] / 1e3), 1)
+        r["input_bytes_stored"] = stored
+        r["workload"] = "cfg3_large shape, values from a 256-word vocabulary of 8-byte words, inputs stored compressed"
+        res[name] = r
     return res
 
 

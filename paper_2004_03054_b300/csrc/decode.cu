@@ -676,13 +676,15 @@ void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput*
   count_launches(1);
 }
 
-// R4c, one warp per compressed block: lane 0 reads each element's tag and extra bytes
-// (every read inside the stored bytes), the warp writes its bytes. A copy of offset d
-// and length L writes out[w + i] = out[w - d + i mod d] for i < L: the copy's own output
-// repeats with period d, so every byte comes from the d bytes before w, already written
-// (elements are separated by __syncwarp). Any element that runs past the stream, copies
-// from before the output or writes past the announced length, or a total other than it,
-// is CORRUPTION; the block's contents pointer stays null then.
+// R4c, one warp per compressed block. Every lane parses the same elements in step from a
+// 128-byte window of the stream held in registers (lane l keeps its bytes 4l..4l+3; a
+// byte is one shuffle away; the window moves when an element's header could leave it),
+// so no parse step waits on memory; then the warp writes the element's bytes. A copy of
+// offset d and length L writes out[w + i] = out[w - d + i mod d] for i < L: the copy's
+// own output repeats with period d, so every byte comes from the d bytes before w, already
+// written (elements are separated by __syncwarp). Any element that runs past the stream,
+// copies from before the output or writes past the announced length, or a total other
+// than it, is CORRUPTION; the block's contents pointer stays null then.
 __global__ void __launch_bounds__(256) k_decompress(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
                                                     const uint64_t* __restrict__ ulen,
                                                     const uint64_t* __restrict__ uoff, uint8_t* __restrict__ dst,
@@ -699,68 +701,78 @@ __global__ void __launch_bounds__(256) k_decompress(const BlockDesc* __restrict_
     bool ok = uoff[g] + n <= dst_cap;
     uint8_t* out = dst + uoff[g];
     const uint8_t* src = b.ptr;
-    uint64_t p = 0;  // stream position (lane 0's view, broadcast)
-    while (p < b.size && (src[p] & 0x80u)) ++p;  // the length header (checked by the walk)
+    const uint64_t S = b.size;
+    uint64_t p = 0;
+    while (p < S && (src[p] & 0x80u)) ++p;  // the length header (checked by the block walk)
     ++p;
+    uint64_t wb = 0;
+    uint32_t word = 0;
+    bool have = false;
+    auto refill = [&](uint64_t at) {
+      wb = at;
+      word = 0;
+#pragma unroll
+      for (uint32_t k = 0; k < 4; ++k) {
+        const uint64_t q = at + 4 * lane + k;
+        if (q < S) word |= uint32_t(src[q]) << (8 * k);
+      }
+      have = true;
+    };
+    auto byte_at = [&](uint64_t q) -> uint32_t {
+      const uint32_t r = uint32_t(q - wb);
+      return (__shfl_sync(0xFFFFFFFFu, word, r >> 2) >> ((r & 3u) * 8)) & 0xFFu;
+    };
     uint64_t w = 0;
-    while (ok) {
-      // lane 0: the next element as (kind, length, offset or source position, its bytes)
-      uint32_t kind = 0, good = 1, done = 0;
+    while (ok && p < S) {
+      if (!have || p + 5 > wb + 128) refill(p);
+      const uint32_t tag = byte_at(p);
+      const uint32_t kind = tag & 3u;
       uint64_t len = 0, arg = 0, used = 0;
-      if (lane == 0) {
-        if (p >= b.size) {
-          done = 1;
-        } else {
-          const uint32_t tag = src[p];
-          kind = tag & 3u;
-          if (kind == 0) {
-            len = tag >> 2;
-            uint32_t nb = 0;
-            if (len >= 60) {
-              nb = uint32_t(len) - 59;
-              if (b.size - p - 1 < nb) {
-                good = 0;
-              } else {
-                len = 0;
-                for (uint32_t i = 0; i < nb; ++i) len |= uint64_t(src[p + 1 + i]) << (8 * i);
-              }
-            }
-            len += 1;
-            used = 1 + nb;
-            arg = p + used;  // literal bytes
-            if (good && (b.size - arg < len || n - w < len)) good = 0;
-            used += len;
-          } else {
-            const uint32_t nb = kind == 1 ? 1u : (kind == 2 ? 2u : 4u);
-            if (b.size - p - 1 < nb) {
-              good = 0;
-            } else if (kind == 1) {
-              len = 4 + ((tag >> 2) & 7u);
-              arg = (uint64_t(tag >> 5) << 8) | src[p + 1];
-            } else {
-              len = 1 + (tag >> 2);
-              for (uint32_t i = 0; i < nb; ++i) arg |= uint64_t(src[p + 1 + i]) << (8 * i);
-            }
-            used = 1 + nb;
-            if (good && (arg == 0 || arg > w || n - w < len)) good = 0;
-          }
-        }
-      }
-      done = __shfl_sync(0xFFFFFFFFu, done, 0);
-      good = __shfl_sync(0xFFFFFFFFu, good, 0);
-      if (done) break;
-      if (!good) {
-        ok = false;
-        break;
-      }
-      kind = __shfl_sync(0xFFFFFFFFu, kind, 0);
-      len = __shfl_sync(0xFFFFFFFFu, len, 0);
-      arg = __shfl_sync(0xFFFFFFFFu, arg, 0);
-      used = __shfl_sync(0xFFFFFFFFu, used, 0);
       if (kind == 0) {
-        for (uint64_t i = lane; i < len; i += 32) out[w + i] = src[arg + i];
+        len = tag >> 2;
+        uint32_t nb = 0;
+        if (len >= 60) {
+          nb = uint32_t(len) - 59;
+          if (S - p - 1 < nb) {
+            ok = false;
+            break;
+          }
+          len = 0;
+          for (uint32_t k = 0; k < nb; ++k) len |= uint64_t(byte_at(p + 1 + k)) << (8 * k);
+        }
+        len += 1;
+        used = 1 + nb;
+        arg = p + used;  // literal bytes
+        if (S - arg < len || n - w < len) {
+          ok = false;
+          break;
+        }
+        used += len;
+        for (uint64_t k = lane; k < len; k += 32) out[w + k] = src[arg + k];
       } else {
-        for (uint64_t i = lane; i < len; i += 32) out[w + i] = out[w - arg + i % arg];
+        const uint32_t nb = kind == 1 ? 1u : (kind == 2 ? 2u : 4u);
+        if (S - p - 1 < nb) {
+          ok = false;
+          break;
+        }
+        if (kind == 1) {
+          len = 4 + ((tag >> 2) & 7u);
+          arg = (uint64_t(tag >> 5) << 8) | byte_at(p + 1);
+        } else {
+          len = 1 + (tag >> 2);
+          for (uint32_t k = 0; k < nb; ++k) arg |= uint64_t(byte_at(p + 1 + k)) << (8 * k);
+        }
+        used = 1 + nb;
+        if (arg == 0 || arg > w || n - w < len) {
+          ok = false;
+          break;
+        }
+        if (arg >= len) {
+          for (uint64_t k = lane; k < len; k += 32) out[w + k] = out[w - arg + k];
+        } else {  // overlapping: a pattern of arg < len <= 64 bytes
+          const uint32_t d = uint32_t(arg);
+          for (uint32_t k = lane; k < uint32_t(len); k += 32) out[w + k] = out[w - d + k % d];
+        }
       }
       __syncwarp();
       w += len;

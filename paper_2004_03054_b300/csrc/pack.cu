@@ -1258,7 +1258,7 @@ __global__ void __launch_bounds__(kCzWarps * 32) k_compress(const Counts* __rest
         while (i < e) {
           const uint32_t c = cw[i - wb];
           bool ok = e - i >= 4 && c != kCzNone && i - c < 65536;
-          if (ok) ok = ld4_bytes(in + c) == ld4_bytes(in + i);
+          if (ok) ok = in[c] == in[i] && ld4_bytes(in + c) == ld4_bytes(in + i);
           if (ok) {
             uint64_t L = 4;
             while (i + L < e && in[c + L] == in[i + L]) ++L;

@@ -222,6 +222,22 @@ def _prefix_keys(rng, count, pool, lo, hi, seen):
     return out
 
 
+def with_compressible_values(job: Job, seed: int = 17, vocab: int = 256, word: int = 8) -> Job:
+    """The job with every value rewritten (same lengths) as a stream of `word`-byte words
+    drawn uniformly from a vocabulary of `vocab` random words, so that blocks compress
+    (format variant R4c): most words recur within a block at distances below 2 KiB. The
+    paper's YCSB values are random; this stands in for the text-like values of LevelDB's
+    own benchmark, which compress to about half."""
+    rng = np.random.default_rng(seed)
+    words = np.frombuffer(rng.bytes(vocab * word), np.uint8).reshape(vocab, word)
+    for r in job.inputs:
+        total = int(r.voff[-1])
+        if total:
+            idx = rng.integers(0, vocab, size=(total + word - 1) // word)
+            r.vals = np.ascontiguousarray(words[idx].reshape(-1)[:total])
+    return job
+
+
 def config3(seed: int = 3, scale: float = 1.0) -> Job:
     rng = np.random.default_rng(seed)
     per = max(8, int(round(64 * MiB * scale / 1076.0)))
