@@ -693,62 +693,63 @@ __global__ void __launch_bounds__(256) k_decompress(const BlockDesc* __restrict_
   const uint32_t lane = lane_id();
   const uint64_t warps = gstride() / 32;
   for (uint64_t g = gtid() / 32; g < n_blocks; g += warps) {
-    const uint64_t n = ulen[g];
-    if (n == kRawBlock) continue;
+    const uint64_t n64 = ulen[g];
+    if (n64 == kRawBlock) continue;
     const BlockDesc b = blocks[g];
     DErr* e = errs + b.job;
     if (b.ptr == nullptr || *(volatile int32_t*)&e->code != 0) continue;
-    bool ok = uoff[g] + n <= dst_cap;
+    // positions fit 32 bits: the length header is a varint32, a block's stored size too
+    bool ok = uoff[g] + n64 <= dst_cap && b.size < 0xFFFFFFFFull;
+    const uint32_t n = uint32_t(n64), S = uint32_t(b.size);
     uint8_t* out = dst + uoff[g];
     const uint8_t* src = b.ptr;
-    const uint64_t S = b.size;
-    uint64_t p = 0;
+    uint32_t p = 0;
     while (p < S && (src[p] & 0x80u)) ++p;  // the length header (checked by the block walk)
     ++p;
-    uint64_t wb = 0;
-    uint32_t word = 0;
+    uint32_t wb = 0, word = 0;
     bool have = false;
-    auto refill = [&](uint64_t at) {
+    auto refill = [&](uint32_t at) {
       wb = at;
       word = 0;
 #pragma unroll
       for (uint32_t k = 0; k < 4; ++k) {
-        const uint64_t q = at + 4 * lane + k;
+        const uint32_t q = at + 4 * lane + k;
         if (q < S) word |= uint32_t(src[q]) << (8 * k);
       }
       have = true;
     };
-    auto byte_at = [&](uint64_t q) -> uint32_t {
-      const uint32_t r = uint32_t(q - wb);
+    auto byte_at = [&](uint32_t q) -> uint32_t {
+      const uint32_t r = q - wb;
       return (__shfl_sync(0xFFFFFFFFu, word, r >> 2) >> ((r & 3u) * 8)) & 0xFFu;
     };
-    uint64_t w = 0;
+    uint32_t w = 0;
     while (ok && p < S) {
       if (!have || p + 5 > wb + 128) refill(p);
       const uint32_t tag = byte_at(p);
       const uint32_t kind = tag & 3u;
-      uint64_t len = 0, arg = 0, used = 0;
+      uint32_t len = 0, arg = 0, used = 0;
       if (kind == 0) {
-        len = tag >> 2;
+        uint64_t l = tag >> 2;
         uint32_t nb = 0;
-        if (len >= 60) {
-          nb = uint32_t(len) - 59;
+        if (l >= 60) {
+          nb = uint32_t(l) - 59;
           if (S - p - 1 < nb) {
             ok = false;
             break;
           }
-          len = 0;
-          for (uint32_t k = 0; k < nb; ++k) len |= uint64_t(byte_at(p + 1 + k)) << (8 * k);
+          l = 0;
+          for (uint32_t k = 0; k < nb; ++k) l |= uint64_t(byte_at(p + 1 + k)) << (8 * k);
         }
-        len += 1;
+        l += 1;
         used = 1 + nb;
         arg = p + used;  // literal bytes
-        if (S - arg < len || n - w < len) {
+        if (uint64_t(S - arg) < l || uint64_t(n - w) < l) {
           ok = false;
           break;
         }
+        len = uint32_t(l);
         used += len;
-        for (uint64_t k = lane; k < len; k += 32) out[w + k] = src[arg + k];
+        for (uint32_t k = lane; k < len; k += 32) out[w + k] = src[arg + k];
       } else {
         const uint32_t nb = kind == 1 ? 1u : (kind == 2 ? 2u : 4u);
         if (S - p - 1 < nb) {
@@ -757,10 +758,10 @@ __global__ void __launch_bounds__(256) k_decompress(const BlockDesc* __restrict_
         }
         if (kind == 1) {
           len = 4 + ((tag >> 2) & 7u);
-          arg = (uint64_t(tag >> 5) << 8) | byte_at(p + 1);
+          arg = ((tag >> 5) << 8) | byte_at(p + 1);
         } else {
           len = 1 + (tag >> 2);
-          for (uint32_t k = 0; k < nb; ++k) arg |= uint64_t(byte_at(p + 1 + k)) << (8 * k);
+          for (uint32_t k = 0; k < nb; ++k) arg |= byte_at(p + 1 + k) << (8 * k);
         }
         used = 1 + nb;
         if (arg == 0 || arg > w || n - w < len) {
@@ -768,10 +769,11 @@ __global__ void __launch_bounds__(256) k_decompress(const BlockDesc* __restrict_
           break;
         }
         if (arg >= len) {
-          for (uint64_t k = lane; k < len; k += 32) out[w + k] = out[w - arg + k];
+          if (lane < len) out[w + lane] = out[w - arg + lane];
+          if (lane + 32 < len) out[w + lane + 32] = out[w - arg + lane + 32];
         } else {  // overlapping: a pattern of arg < len <= 64 bytes
-          const uint32_t d = uint32_t(arg);
-          for (uint32_t k = lane; k < uint32_t(len); k += 32) out[w + k] = out[w - d + k % d];
+          if (lane < len) out[w + lane] = out[w - arg + lane % arg];
+          if (lane + 32 < len) out[w + lane + 32] = out[w - arg + (lane + 32) % arg];
         }
       }
       __syncwarp();
