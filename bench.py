@@ -45,6 +45,18 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(values, ws):
+    """Element-wise maximum of `values` over all ranks (an all-reduce on the process group
+    the replicas share), or `values` themselves on one rank."""
+    if ws <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -194,10 +206,7 @@ def run_ours(args, ws, rank, local):
     time.sleep(0.2)
     sampler.stop()
     clocks = sampler.summary(t0, t1)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks([ms], ws)[0]
     value = ws * in_bytes / MiB / (ms / 1e3)
 
     # dominant kernel: the encoder [5], the largest share of the job's kernel time and on the
@@ -279,10 +288,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         te = (time.perf_counter() - ts) / ke
         srv.close()
-        if ws > 1:
-            t = torch.tensor([te, te_single], dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te, te_single = float(t[0].item()), float(t[1].item())
+        te, te_single = _max_over_ranks([te, te_single], ws)
         e2e = {"value": round(ws * in_bytes / MiB / te, 1), "unit": "MiB/s", "h2d_bytes_per_step": in_bytes,
                "d2h_bytes_per_step": d2h, "ms_per_step": round(te * 1e3, 3), "steps": ke,
                "api": f"luda_server_submit_host, {depth} slots, {depth} jobs in flight (copies in and out overlap)",
