@@ -21,17 +21,6 @@ namespace luda {
 
 namespace {
 
-__device__ __forceinline__ uint32_t find_last_le(const uint32_t* a, uint32_t n, uint32_t v) {
-  // largest i in [0, n) with a[i] <= v (a non-decreasing, a[0] <= v)
-  uint32_t lo = 0, hi = n;
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (a[mid] <= v) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
 __device__ __forceinline__ uint32_t job_of_surv(const JobDev* jobs, uint32_t n_jobs, uint32_t s) {
   uint32_t lo = 0, hi = n_jobs;
   while (hi - lo > 1) {
@@ -1168,16 +1157,23 @@ __global__ void k_raw_files(const JobDev* __restrict__ jobs, uint32_t n_jobs, co
   for (uint64_t b = gtid(); b < nb; b += gstride()) rbf[b] = job_of_block(jobs, n_jobs, uint32_t(b));
 }
 
-constexpr uint32_t kCzWarps = 4;
 constexpr uint32_t kCzTab = 4096;      // hash table entries (12-bit hash)
 constexpr uint32_t kCzWin = 32 * 64;   // positions per window: one 64-byte segment per lane
 constexpr uint32_t kCzStage = 72;      // staging bytes per lane (a segment's elements: at most 66)
-constexpr uint32_t kCzNone = 0xFFFFFFFFu;
-constexpr uint32_t kCzWarpSmem = (kCzTab + kCzWin) * 4 + 32 * kCzStage;
-constexpr uint32_t kCzSmem = kCzWarps * kCzWarpSmem;
+// Positions as Pos (16 bits for blocks below 65535 bytes: smaller tables, more warps per
+// SM; 32 bits for larger blocks), kWarps warps per CTA.
+template <typename Pos>
+__host__ __device__ constexpr uint32_t cz_warp_smem() {
+  return (kCzTab + kCzWin) * uint32_t(sizeof(Pos)) + 32 * kCzStage;
+}
+constexpr uint32_t kCzSmallMax = 65534;  // largest block for 16-bit positions (65535: none)
+constexpr uint32_t kCzWarps16 = 2, kCzWarps32 = 4;
 
-__device__ __forceinline__ uint32_t ld4_bytes(const uint8_t* p) {
-  return uint32_t(p[0]) | uint32_t(p[1]) << 8 | uint32_t(p[2]) << 16 | uint32_t(p[3]) << 24;
+// The little-endian word at in + q, from the two aligned words around it (`in` is 16-byte
+// aligned and its block's scratch share extends at least 4 bytes past any word read).
+__device__ __forceinline__ uint32_t ld4_at(const uint8_t* __restrict__ in, uint64_t q) {
+  const uint32_t* a = reinterpret_cast<const uint32_t*>(in + (q & ~uint64_t(3)));
+  return __funnelshift_r(__ldg(a), __ldg(a + 1), uint32_t(q & 3u) * 8u);
 }
 
 // One warp per block. Per window of 2048 positions: the warp steps through it 32
@@ -1187,7 +1183,8 @@ __device__ __forceinline__ uint32_t ld4_bytes(const uint8_t* p) {
 // parses its own 64-byte segment from the window's candidates into its staging bytes, and
 // the segments are written out in order after a warp scan of their sizes. The block is
 // kept compressed (type 1) when the stream is shorter than raw - raw / 8.
-__global__ void __launch_bounds__(kCzWarps * 32) k_compress(const Counts* __restrict__ cnt,
+template <typename Pos, uint32_t kWarps>
+__global__ void __launch_bounds__(kWarps * 32) k_compress(const Counts* __restrict__ cnt,
                                                             const uint64_t* __restrict__ Craw,
                                                             const uint64_t* __restrict__ Cc,
                                                             uint64_t* __restrict__ bsz, uint64_t* __restrict__ disk,
@@ -1195,14 +1192,17 @@ __global__ void __launch_bounds__(kCzWarps * 32) k_compress(const Counts* __rest
                                                             uint8_t* __restrict__ cz, uint64_t c_cap,
                                                             uint8_t* __restrict__ ctype) {
   extern __shared__ __align__(16) uint8_t s_cz[];
+  constexpr bool kSmall = sizeof(Pos) == 2;
+  constexpr uint32_t kCzNone = kSmall ? 0xFFFFu : 0xFFFFFFFFu;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  uint32_t* tab = reinterpret_cast<uint32_t*>(s_cz + warp * kCzWarpSmem);
-  uint32_t* cw = tab + kCzTab;
+  Pos* tab = reinterpret_cast<Pos*>(s_cz + warp * cz_warp_smem<Pos>());
+  Pos* cw = tab + kCzTab;
   uint8_t* stage = reinterpret_cast<uint8_t*>(cw + kCzWin) + lane * kCzStage;
   const uint32_t nb = cnt->nb;
   const uint64_t warps = gstride() / 32;
   for (uint64_t b = gtid() / 32; b < nb; b += warps) {
     const uint64_t n = bsz[b];
+    if (kSmall != (n <= kCzSmallMax)) continue;  // the other instance takes this block
     const uint64_t cbound = n + n / 32 + 16;
     if (Craw[b] + n > raw_cap || Cc[b] + cbound > c_cap) {
       if (lane == 0) ctype[b] = 0;
@@ -1210,7 +1210,7 @@ __global__ void __launch_bounds__(kCzWarps * 32) k_compress(const Counts* __rest
     }
     const uint8_t* in = raw + Craw[b];
     uint8_t* o = cz + Cc[b];
-    for (uint32_t k = lane; k < kCzTab; k += 32) tab[k] = kCzNone;
+    for (uint32_t k = lane; k < kCzTab; k += 32) tab[k] = Pos(kCzNone);
     uint32_t total = 0;  // stream bytes so far: the length header, then the segments
     {
       uint64_t v = n;
@@ -1228,15 +1228,15 @@ __global__ void __launch_bounds__(kCzWarps * 32) k_compress(const Counts* __rest
       for (uint64_t base = wb; base < we; base += 32) {
         const uint64_t p = base + lane;
         const bool valid = p + 4 <= n;
-        const uint32_t h = valid ? (ld4_bytes(in + p) * 2654435761u) >> 20 : kCzTab + lane;
+        const uint32_t h = valid ? (ld4_at(in, p) * 2654435761u) >> 20 : kCzTab + lane;
         const uint32_t m = __match_any_sync(0xFFFFFFFFu, h);
         const uint32_t lower = m & ((1u << lane) - 1u);
         uint32_t c = kCzNone;
-        if (valid) c = lower ? uint32_t(base) + (31u - __clz(lower)) : tab[h];
+        if (valid) c = lower ? uint32_t(base) + (31u - __clz(lower)) : uint32_t(tab[h]);
         __syncwarp();
-        if (valid && (m >> lane) == 1u) tab[h] = uint32_t(p);
+        if (valid && (m >> lane) == 1u) tab[h] = Pos(p);
         __syncwarp();
-        if (p < we) cw[p - wb] = c;
+        if (p < we) cw[p - wb] = Pos(c);
       }
       __syncwarp();
       // this lane's segment [s0, e)
@@ -1256,9 +1256,9 @@ __global__ void __launch_bounds__(kCzWarps * 32) k_compress(const Counts* __rest
           for (uint64_t k = from; k < to; ++k) stage[sz++] = in[k];
         };
         while (i < e) {
-          const uint32_t c = cw[i - wb];
+          const uint32_t c = uint32_t(cw[i - wb]);
           bool ok = e - i >= 4 && c != kCzNone && i - c < 65536;
-          if (ok) ok = in[c] == in[i] && ld4_bytes(in + c) == ld4_bytes(in + i);
+          if (ok) ok = ld4_at(in, c) == ld4_at(in, i);
           if (ok) {
             uint64_t L = 4;
             while (i + L < e && in[c + L] == in[i + L]) ++L;
@@ -1868,10 +1868,15 @@ void launch_compress_blocks(PackCz z, JobDev* jobs, uint32_t n_jobs, Counts* cnt
 
 void launch_compress(PackCz z, Counts* cnt, uint32_t cap, uint64_t* bsz, uint64_t* disk, cudaStream_t st) {
   if (!cap) return;
-  smem_optin(k_compress, kCzSmem);
-  k_compress<<<grid_for(uint64_t(cap) * 32, kCzWarps * 32), kCzWarps * 32, kCzSmem, st>>>(
+  // blocks below 64 KiB (nearly all) with 16-bit positions, the others with 32-bit ones
+  constexpr uint32_t s16 = kCzWarps16 * cz_warp_smem<uint16_t>(), s32 = kCzWarps32 * cz_warp_smem<uint32_t>();
+  smem_optin(k_compress<uint16_t, kCzWarps16>, s16);
+  smem_optin(k_compress<uint32_t, kCzWarps32>, s32);
+  k_compress<uint16_t, kCzWarps16><<<grid_for(uint64_t(cap) * 32, kCzWarps16 * 32), kCzWarps16 * 32, s16, st>>>(
       cnt, z.Craw, z.Cc, bsz, disk, z.raw, z.raw_cap, z.cz, z.c_cap, z.ctype);
-  count_launches(1);
+  k_compress<uint32_t, kCzWarps32><<<grid_for(uint64_t(cap) * 32, kCzWarps32 * 32), kCzWarps32 * 32, s32, st>>>(
+      cnt, z.Craw, z.Cc, bsz, disk, z.raw, z.raw_cap, z.cz, z.c_cap, z.ctype);
+  count_launches(2);
 }
 
 void launch_place(PackCz z, Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,
