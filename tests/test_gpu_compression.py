@@ -212,3 +212,20 @@ def test_compressed_builder_batch_and_plan():
             g.tables = [t.cpu().numpy().tobytes() for t in g.tables]
             assert_same(g, w)
     plan.close()
+
+
+def test_host_entry_point_and_server_host_jobs_with_compression():
+    """luda_compact (host inputs, host outputs) and the server's host-buffer jobs take the
+    same decompression and compression paths."""
+    ins = _inputs(3, 200, 200, 4096, seed=101, compress=(True, False))
+    want = oracle.compact(ins, oracle.MAX_SEQ, False, 4096, 16, 10, 32 << 10, oracle.F_COMPRESS)
+    got = luda.compact(ins, oracle.MAX_SEQ, opts=luda.options(4096, 16, 10, 32 << 10, flags=CZ))
+    assert got.status == 0, got.detail
+    assert [bytes(t) for t in got.tables] == [t.data for t in want.tables]
+    host = [torch.frombuffer(bytearray(x), dtype=torch.uint8).pin_memory() for x in ins]
+    srv = luda.Server(2, 1 << 40, luda.options(4096, 16, 10, 32 << 10, flags=CZ))
+    t = srv.submit(host, oracle.MAX_SEQ, False, host=True)
+    res, _ = srv.wait(t, timeout_ms=60_000)
+    srv.close()
+    assert res.status == 0
+    assert [bytes(x) for x in res.tables] == [x.data for x in want.tables]
