@@ -1160,11 +1160,12 @@ __global__ void k_raw_files(const JobDev* __restrict__ jobs, uint32_t n_jobs, co
 constexpr uint32_t kCzTab = 4096;      // hash table entries (12-bit hash)
 constexpr uint32_t kCzWin = 32 * 64;   // positions per window: one 64-byte segment per lane
 constexpr uint32_t kCzStage = 72;      // staging bytes per lane (a segment's elements: at most 66)
+constexpr uint32_t kCzWinOut = 32 * 66 + 64;  // a window's stream, joined before its coalesced store
 // Positions as Pos (16 bits for blocks below 65535 bytes: smaller tables, more warps per
 // SM; 32 bits for larger blocks), kWarps warps per CTA.
 template <typename Pos>
 __host__ __device__ constexpr uint32_t cz_warp_smem() {
-  return (kCzTab + kCzWin) * uint32_t(sizeof(Pos)) + 32 * kCzStage;
+  return (kCzTab + kCzWin) * uint32_t(sizeof(Pos)) + 32 * kCzStage + kCzWinOut;
 }
 constexpr uint32_t kCzSmallMax = 65534;  // largest block for 16-bit positions (65535: none)
 constexpr uint32_t kCzWarps16 = 2, kCzWarps32 = 4;
@@ -1197,7 +1198,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_compress(const Counts* __restri
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   Pos* tab = reinterpret_cast<Pos*>(s_cz + warp * cz_warp_smem<Pos>());
   Pos* cw = tab + kCzTab;
-  uint8_t* stage = reinterpret_cast<uint8_t*>(cw + kCzWin) + lane * kCzStage;
+  uint8_t* const stage0 = reinterpret_cast<uint8_t*>(cw + kCzWin);
+  uint8_t* stage = stage0 + lane * kCzStage;
+  uint8_t* const wout = stage0 + 32 * kCzStage;
   const uint32_t nb = cnt->nb;
   const uint64_t warps = gstride() / 32;
   for (uint64_t b = gtid() / 32; b < nb; b += warps) {
@@ -1287,9 +1290,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_compress(const Counts* __restri
         const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
         if (lane >= uint32_t(d)) x += y;
       }
-      const uint32_t at = total + x - sz;
-      for (uint32_t k = 0; k < sz; ++k) o[at + k] = stage[k];
-      total += __shfl_sync(0xFFFFFFFFu, x, 31);
+      // the segments joined in shared memory, then stored by consecutive lanes
+      const uint32_t at = x - sz, wsum = __shfl_sync(0xFFFFFFFFu, x, 31);
+      for (uint32_t k = 0; k < sz; ++k) wout[at + k] = stage[k];
+      __syncwarp();
+      for (uint32_t k = lane; k < wsum; k += 32) o[total + k] = wout[k];
+      total += wsum;
       __syncwarp();
     }
     if (lane == 0) {
