@@ -676,15 +676,19 @@ void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput*
   count_launches(1);
 }
 
-// R4c, one warp per compressed block. Every lane parses the same elements in step from a
-// 128-byte window of the stream held in registers (lane l keeps its bytes 4l..4l+3; a
-// byte is one shuffle away; the window moves when an element's header could leave it),
-// so no parse step waits on memory; then the warp writes the element's bytes. A copy of
-// offset d and length L writes out[w + i] = out[w - d + i mod d] for i < L: the copy's
-// own output repeats with period d, so every byte comes from the d bytes before w, already
-// written (elements are separated by __syncwarp). Any element that runs past the stream,
-// copies from before the output or writes past the announced length, or a total other
-// than it, is CORRUPTION; the block's contents pointer stays null then.
+// R4c, one warp per compressed block, several elements per step. The stream's next 128
+// bytes sit in registers (lane l holds bytes 4l..4l+3 of the window; a byte is one
+// shuffle away). Each step, lane l reads the element header that would start at p + l and
+// where the element after it would start; the true element starts are the chain from p
+// (one shuffle per element), their output positions a warp scan of their lengths. The
+// marked elements of at most 64 bytes whose source lies wholly before the step's first
+// output byte (literals, and copies reaching back past it) are then written at once, each
+// by its own lane; the others (long literals, copies of bytes this step writes) follow in
+// order, the warp's lanes covering an element's bytes. A copy of offset d and length L
+// writes out[w + i] = out[w - d + i mod d] for i < L (its own output repeats with period
+// d, so every byte comes from the d bytes before w). Any element that runs past the
+// stream, copies from before the output or writes past the announced length, or a total
+// other than it, is CORRUPTION; the block's contents pointer stays null then.
 __global__ void __launch_bounds__(256) k_decompress(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
                                                     const uint64_t* __restrict__ ulen,
                                                     const uint64_t* __restrict__ uoff, uint8_t* __restrict__ dst,
@@ -708,77 +712,129 @@ __global__ void __launch_bounds__(256) k_decompress(const BlockDesc* __restrict_
     ++p;
     uint32_t wb = 0, word = 0;
     bool have = false;
-    auto refill = [&](uint32_t at) {
-      wb = at;
-      word = 0;
-#pragma unroll
-      for (uint32_t k = 0; k < 4; ++k) {
-        const uint32_t q = at + 4 * lane + k;
-        if (q < S) word |= uint32_t(src[q]) << (8 * k);
-      }
-      have = true;
-    };
-    auto byte_at = [&](uint32_t q) -> uint32_t {
+    auto byte_at = [&](uint32_t q) -> uint32_t {  // q in [wb, wb + 128)
       const uint32_t r = q - wb;
       return (__shfl_sync(0xFFFFFFFFu, word, r >> 2) >> ((r & 3u) * 8)) & 0xFFu;
     };
     uint32_t w = 0;
     while (ok && p < S) {
-      if (!have || p + 5 > wb + 128) refill(p);
-      const uint32_t tag = byte_at(p);
+      if (!have || p + 37 > wb + 128) {  // the window covers every header starting below p + 32
+        wb = p;
+        word = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+          const uint32_t q = wb + 4 * lane + k;
+          if (q < S) word |= uint32_t(src[q]) << (8 * k);
+        }
+        have = true;
+      }
+      // the element that would start at q = p + lane
+      const uint32_t q = p + lane;
+      const uint32_t tag = byte_at(q < S ? q : p);
       const uint32_t kind = tag & 3u;
-      uint32_t len = 0, arg = 0, used = 0;
+      uint32_t hl = kind == 0 ? 1u : (kind == 1 ? 2u : (kind == 2 ? 3u : 5u));
+      uint32_t nb = 0;
+      if (kind == 0 && (tag >> 2) >= 60) {
+        nb = (tag >> 2) - 59;
+        hl = 1 + nb;
+      }
+      uint32_t x[4];
+#pragma unroll
+      for (uint32_t k = 0; k < 4; ++k) x[k] = byte_at(q + 1 + k);  // q + 4 < p + 36: in the window
+      uint64_t len = 0;
+      uint32_t arg = 0;
       if (kind == 0) {
-        uint64_t l = tag >> 2;
-        uint32_t nb = 0;
-        if (l >= 60) {
-          nb = uint32_t(l) - 59;
-          if (S - p - 1 < nb) {
-            ok = false;
-            break;
-          }
-          l = 0;
-          for (uint32_t k = 0; k < nb; ++k) l |= uint64_t(byte_at(p + 1 + k)) << (8 * k);
+        len = tag >> 2;
+        if (nb) {
+          len = 0;
+#pragma unroll
+          for (uint32_t k = 0; k < 4; ++k)
+            if (k < nb) len |= uint64_t(x[k]) << (8 * k);
         }
-        l += 1;
-        used = 1 + nb;
-        arg = p + used;  // literal bytes
-        if (uint64_t(S - arg) < l || uint64_t(n - w) < l) {
-          ok = false;
-          break;
-        }
-        len = uint32_t(l);
-        used += len;
-        for (uint32_t k = lane; k < len; k += 32) out[w + k] = src[arg + k];
+        len += 1;
+      } else if (kind == 1) {
+        len = 4 + ((tag >> 2) & 7u);
+        arg = ((tag >> 5) << 8) | x[0];
       } else {
-        const uint32_t nb = kind == 1 ? 1u : (kind == 2 ? 2u : 4u);
-        if (S - p - 1 < nb) {
-          ok = false;
+        len = 1 + (tag >> 2);
+        arg = x[0] | x[1] << 8;
+        if (kind == 3) arg |= x[2] << 16 | x[3] << 24;
+      }
+      // header and literal bytes inside the stream; where the next element would start
+      const bool fits = q < S && hl <= S - q && (kind != 0 || len <= uint64_t(S - q - hl));
+      const uint64_t nx = uint64_t(q) + hl + (kind == 0 ? len : 0);
+      const uint32_t nxt = fits && nx < uint64_t(p) + 32 ? uint32_t(nx - p) : 32u;
+      // the chain of true element starts from p
+      uint32_t marks = 0, cur = 0, last = 0;
+      bool broken = false;
+      while (cur < 32 && p + cur < S) {
+        marks |= 1u << cur;
+        last = cur;
+        if (!__shfl_sync(0xFFFFFFFFu, fits ? 1u : 0u, cur)) {
+          broken = true;
           break;
         }
-        if (kind == 1) {
-          len = 4 + ((tag >> 2) & 7u);
-          arg = ((tag >> 5) << 8) | byte_at(p + 1);
+        cur = __shfl_sync(0xFFFFFFFFu, nxt, cur);
+      }
+      if (broken) {
+        ok = false;
+        break;
+      }
+      const bool mine = (marks >> lane) & 1u;
+      // output positions of the marked elements
+      const uint64_t ml = mine ? len : 0;
+      uint64_t xs = ml;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, xs, d);
+        if (lane >= uint32_t(d)) xs += y;
+      }
+      const uint64_t total = __shfl_sync(0xFFFFFFFFu, xs, 31);
+      const uint64_t wl = uint64_t(w) + xs - ml;
+      const bool bad = mine && (wl + len > n || (kind != 0 && (arg == 0 || arg > wl)));
+      if (__any_sync(0xFFFFFFFFu, bad)) {
+        ok = false;
+        break;
+      }
+      // elements that read nothing this step writes, at most 64 bytes: each lane its own
+      const uint32_t ew = uint32_t(wl), el = uint32_t(len);
+      const bool solo = mine && el <= 64 && (kind == 0 || (arg >= el ? ew - arg + el <= w : ew - arg + arg <= w));
+      if (solo) {
+        if (kind == 0) {
+          const uint32_t from = q + hl;
+          for (uint32_t k = 0; k < el; ++k) out[ew + k] = src[from + k];
+        } else if (arg >= el) {
+          for (uint32_t k = 0; k < el; ++k) out[ew + k] = out[ew - arg + k];
         } else {
-          len = 1 + (tag >> 2);
-          for (uint32_t k = 0; k < nb; ++k) arg |= byte_at(p + 1 + k) << (8 * k);
-        }
-        used = 1 + nb;
-        if (arg == 0 || arg > w || n - w < len) {
-          ok = false;
-          break;
-        }
-        if (arg >= len) {
-          if (lane < len) out[w + lane] = out[w - arg + lane];
-          if (lane + 32 < len) out[w + lane + 32] = out[w - arg + lane + 32];
-        } else {  // overlapping: a pattern of arg < len <= 64 bytes
-          if (lane < len) out[w + lane] = out[w - arg + lane % arg];
-          if (lane + 32 < len) out[w + lane + 32] = out[w - arg + (lane + 32) % arg];
+          for (uint32_t k = 0; k < el; ++k) out[ew + k] = out[ew - arg + k % arg];
         }
       }
       __syncwarp();
-      w += len;
-      p += used;
+      // the rest, in order
+      uint32_t todo = marks & ~__ballot_sync(0xFFFFFFFFu, solo);
+      while (todo) {
+        const uint32_t l = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t ek = __shfl_sync(0xFFFFFFFFu, kind, l);
+        const uint32_t tl = __shfl_sync(0xFFFFFFFFu, el, l);
+        const uint32_t tw = __shfl_sync(0xFFFFFFFFu, ew, l);
+        if (ek == 0) {
+          const uint32_t from = p + l + __shfl_sync(0xFFFFFFFFu, hl, l);
+          for (uint32_t k = lane; k < tl; k += 32) out[tw + k] = src[from + k];
+        } else {
+          const uint32_t d = __shfl_sync(0xFFFFFFFFu, arg, l);
+          if (d >= tl) {
+            if (lane < tl) out[tw + lane] = out[tw - d + lane];
+            if (lane + 32 < tl) out[tw + lane + 32] = out[tw - d + lane + 32];
+          } else {  // overlapping: a pattern of d < tl <= 64 bytes
+            if (lane < tl) out[tw + lane] = out[tw - d + lane % d];
+            if (lane + 32 < tl) out[tw + lane + 32] = out[tw - d + (lane + 32) % d];
+          }
+        }
+        __syncwarp();
+      }
+      w += uint32_t(total);
+      p = uint32_t(__shfl_sync(0xFFFFFFFFu, nx, last));
     }
     if (ok && w != n) ok = false;
     if (lane == 0) {
