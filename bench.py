@@ -220,10 +220,7 @@ def run_ours(args, ws, rank, local):
     roofline = {"bound": "hbm", "kernel": "k_encode_stg", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
                 "bytes_per_launch": dom_bytes, "ms_per_launch": round(avg[dom], 4),
-                "traffic": args.traffic if args.traffic is not None else _recorded_traffic(args.scale),
-                "input_checksums": {"kernel": "k_block_verify (second stream, beside decode, sort and cut)",
-                                    "bytes_per_launch": sbytes[-1][1], "ms_per_launch": round(avg[1], 4),
-                                    "achieved": round(sbytes[-1][1] / (avg[1] / 1e3) / 1e9, 1)}}
+                "traffic": args.traffic if args.traffic is not None else _recorded_traffic(args.scale)}
     path_gbs = (in_bytes + out_bytes) / (ms / 1e3) / 1e9
     stage_names = ["sizing", "block_scan", "decode", "sort", "gc_cut_layout", "encode", "meta", "device_span"]
 

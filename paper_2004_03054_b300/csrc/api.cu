@@ -115,6 +115,7 @@ namespace {
 struct DevTables {
   uint32_t* slice = nullptr;
   uint32_t* shift = nullptr;
+  uint32_t* chunk = nullptr;
 };
 std::mutex g_mu;
 DevTables g_tabs[128];
@@ -128,22 +129,26 @@ luda_status get_tabs(CrcTabs* out) {
   std::lock_guard<std::mutex> lk(g_mu);
   DevTables& t = g_tabs[dev];
   if (!t.slice) {
-    std::vector<uint32_t> slice(1024), shift(size_t(kShiftTables) * 1024);
-    if (!make_crc_tables(slice.data(), shift.data())) {
+    std::vector<uint32_t> slice(1024), shift(size_t(kShiftTables) * 1024), chunk(size_t(kChunkTables) * 1024);
+    if (!make_crc_tables(slice.data(), shift.data()) || !make_chunk_tables(chunk.data())) {
       set_detail("crc table generation failed");
       return LUDA_ERR_CUDA;
     }
-    uint32_t *ds = nullptr, *dh = nullptr;
+    uint32_t *ds = nullptr, *dh = nullptr, *dc = nullptr;
     if (cudaMalloc(&ds, slice.size() * 4) != cudaSuccess || cudaMalloc(&dh, shift.size() * 4) != cudaSuccess ||
+        cudaMalloc(&dc, chunk.size() * 4) != cudaSuccess ||
         cudaMemcpy(ds, slice.data(), slice.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(dh, shift.data(), shift.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(dh, shift.data(), shift.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dc, chunk.data(), chunk.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaFree(ds);
       cudaFree(dh);
+      cudaFree(dc);
       set_detail("could not upload crc tables: %s", cudaGetErrorString(cudaGetLastError()));
       return LUDA_ERR_CUDA;
     }
     t.slice = ds;
     t.shift = dh;
+    t.chunk = dc;
     // Keep freed stream-ordered allocations cached in the device's default pool instead of
     // returning them to the driver at every synchronisation (a process-local setting).
     cudaMemPool_t pool;
@@ -154,6 +159,7 @@ luda_status get_tabs(CrcTabs* out) {
   }
   out->slice = t.slice;
   out->shift = t.shift;
+  out->chunk = t.chunk;
   return LUDA_OK;
 }
 
@@ -549,9 +555,13 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
                   arena, fmt, fmt.max_kv, out, out_cap, b.enc_done, b.big, errs, tabs, st);
   }
   trace_mark(tr, 8, st);
-  // data block trailers on the side stream (joined by the caller through event slot 3)
+  // data block trailers on the side stream (joined by the caller through event slot 3):
+  // assembled from the pieces' registers, or (compressed blocks) computed from the bytes
   CK(fork_join(side, 2, st, side->s));
-  launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, false, side->s);
+  if (b.cz.raw_cap)
+    launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, false, side->s);
+  else
+    launch_block_trailer(cnt, cap, b.bd, b.sd, b.dr, b.ed, fmt, out, b.enc_done, tabs, side->s);
   CK(cudaEventRecord(side->ev[3], side->s));
   if (!b.cz.raw_cap)
     launch_encode_big(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
@@ -563,8 +573,9 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   launch_key_lens(b.meta, cnt, cap, b.klens, st);
   CK((exclusive_scan<uint64_t, uint64_t>(b.klens, b.koff, cap, &cnt->nf, b.scan_tmp, st)));
   launch_key_gather(b.meta, cnt, cap, b.koff, b.files, b.surv, recs, arena, b.keybuf, st);
-  // the SMs the trailer kernel left join it for the blocks still to do
-  launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, true, st);
+  // the SMs the trailer kernel of compressed blocks left join it for the blocks still to do
+  if (b.cz.raw_cap)
+    launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, true, st);
   CK(cudaGetLastError());
   return LUDA_OK;
 }
@@ -578,6 +589,7 @@ Recs recs_layout(Layout& L, uint32_t n) {
   r.vptr = L.take<uint64_t>(n + 1);
   r.vlen = L.take<uint32_t>(n + 1);
   r.src = L.take<uint32_t>(n + 1);
+  r.vcrc = L.take<uint32_t>(n + 1);
   return r;
 }
 
@@ -1028,14 +1040,17 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
 
   // ---- sizing: block scan ------------------------------------------------------------------
   Layout LB;
-  uint16_t* d_hdr;
+  uint2* d_hdr;  // the walk's entry table
+  uint32_t *d_nch, *d_chunk_first;  // the unpack's chunks per block and their offsets
   uint64_t *d_ulen, *d_ures;  // R4c: decompressed length and arena share of each block
   auto layoutB = [&](Layout& L, BlockDesc*& blocks, uint32_t*& nrec, uint64_t*& kbytes, uint32_t*& rec_first,
                      uint64_t*& key_first, uint32_t*& in_rec, uint64_t*& in_key, void*& tmp) {
     blocks = L.take<BlockDesc>(NB + 1);
     d_ulen = L.take<uint64_t>(NB + 1);
     d_ures = L.take<uint64_t>(NB + 1);
-    d_hdr = L.take<uint16_t>(uint64_t(NB) * kHdrMax + 1);
+    d_hdr = L.take<uint2>(uint64_t(NB) * kHdrMax + 1);
+    d_nch = L.take<uint32_t>(NB + 1);
+    d_chunk_first = L.take<uint32_t>(NB + 1);
     nrec = L.take<uint32_t>(NB + 1);
     kbytes = L.take<uint64_t>(NB + 1);
     rec_first = L.take<uint32_t>(NB + 1);
@@ -1057,13 +1072,6 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   layoutB(LB, d_blocks, d_nrec, d_kbytes, d_rec_first, d_key_first, d_in_rec, d_in_key, d_tmpB);
 
   launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st, d_ranges, d_bounds);
-  // input checksums on the side stream, joined before the results are collected
-  CK(fork_join(side, 0, st, side->s));
-  tr.mark(11, side->s);
-  launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, false,
-                      side->s);
-  tr.mark(12, side->s);
-  CK(cudaEventRecord(side->ev[1], side->s));
   // block contents: the stored blocks, or copies pointing at their decompressed contents
   BlockDesc* d_cb = d_blocks;
   std::vector<uint32_t> in_rec(N + 1);
@@ -1072,13 +1080,15 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   std::vector<uint8_t> link(N + 1, 0);
   uint32_t comp_blocks = 0;
   uint64_t comp_bytes = 0;
+  uint32_t n_chunks = 0;  // the unpack's chunk registers (the walk's counts summed)
   // entry counts and key bytes of every block, the inputs' record ranges and links; with
   // `contents` the blocks are contents already (the second pass after decompression)
   auto size_pass = [&](bool contents) -> luda_status {
-    launch_block_walk(d_cb, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, st, d_ulen, d_ures, contents);
+    launch_block_walk(d_cb, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, st, d_ulen, d_ures, contents, d_nch);
     if (!contents) tr.mark(2, st);
     launch_zero_failed(d_cb, NB, d_errs, d_nrec, d_kbytes, st);
     launch_run_links(d_in, N, d_cb, d_errs, d_link, st);
+    CK((exclusive_scan<uint32_t, uint32_t>(d_nch, d_chunk_first, NB, nullptr, d_tmpB, st)));
     CK((exclusive_scan<uint32_t, uint32_t>(d_nrec, d_rec_first, NB, nullptr, d_tmpB, st)));
     CK((exclusive_scan<uint64_t, uint64_t>(d_kbytes, d_key_first, NB, nullptr, d_tmpB, st)));
     launch_input_ranges(d_in, N, d_rec_first, d_key_first, d_in_rec, d_in_key, st);
@@ -1090,7 +1100,8 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     uint32_t* p_kv = static_cast<uint32_t*>(hs.take(sizeof(uint32_t)));
     uint8_t* p_link = static_cast<uint8_t*>(hs.take(N + 1));
     uint64_t* p_comp = static_cast<uint64_t*>(hs.take(2 * sizeof(uint64_t)));
-    const bool pinned = p_rec && p_key && p_err && p_kv && p_link && p_comp;
+    uint32_t* p_nch = static_cast<uint32_t*>(hs.take(sizeof(uint32_t)));
+    const bool pinned = p_rec && p_key && p_err && p_kv && p_link && p_comp && p_nch;
     uint64_t comp[2] = {0, 0};
     if (!pinned) {
       p_rec = in_rec.data();
@@ -1099,6 +1110,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
       p_kv = &fmt.max_kv;
       p_link = link.data();
       p_comp = comp;
+      p_nch = &n_chunks;
     }
     CK(cudaMemcpyAsync(p_rec, d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(p_key, d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
@@ -1107,6 +1119,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     if (N) CK(cudaMemcpyAsync(p_link, d_link, N, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(p_comp, &d_cnt->comp_blocks, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(p_comp + 1, &d_cnt->comp_bytes, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(p_nch, d_chunk_first + NB, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     if (!contents) tr.mark(3, st);
     CK(cudaStreamSynchronize(st));
     if (pinned) {
@@ -1117,6 +1130,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
       if (N) memcpy(link.data(), p_link, N);
       comp[0] = p_comp[0];
       comp[1] = p_comp[1];
+      n_chunks = *p_nch;
     }
     comp_blocks = uint32_t(comp[0]);
     comp_bytes = comp[1];
@@ -1143,6 +1157,14 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     LD = Layout{};
     LD.base = bufD;
     layoutD(LD);
+    // the stored blocks' checksums on the side stream (the unpack reads the contents),
+    // joined before the results are collected
+    CK(fork_join(side, 0, st, side->s));
+    tr.mark(11, side->s);
+    launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, false,
+                        side->s);
+    tr.mark(12, side->s);
+    CK(cudaEventRecord(side->ev[1], side->s));
     CK((exclusive_scan<uint64_t, uint64_t>(d_ures, d_uoff, NB, nullptr, d_tmpB, st)));
     CK(cudaMemcpyAsync(d_cblocks, d_blocks, sizeof(BlockDesc) * NB, cudaMemcpyDeviceToDevice, st));
     launch_decompress(d_blocks, NB, d_ulen, d_uoff, d_dec, comp_bytes, d_cblocks, d_in, d_errs, st);
@@ -1199,13 +1221,16 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   Layout LC;
   Recs recs;
   uint8_t* d_arena;
-  uint32_t *d_ord0, *d_ord1, *d_keep, *d_pos, *d_co;
+  uint32_t *d_ord0, *d_ord1, *d_keep, *d_pos, *d_co, *d_chunkF, *d_snap;
   MKey *d_pfx0, *d_pfx1;
   MergeSpan* d_spans;
   PackBufs pb;
+  const uint64_t chunk_cap = uint64_t(n_chunks) + 16;
   auto layoutC = [&](Layout& L) {
     recs = recs_layout(L, n_rec);
     d_arena = L.take<uint8_t>(K + 64);
+    d_chunkF = L.take<uint32_t>(chunk_cap);
+    d_snap = L.take<uint32_t>(2ull * n_rec + 2ull * NB + 2);
     d_ord0 = L.take<uint32_t>(n_rec + 1);
     d_ord1 = L.take<uint32_t>(n_rec + 1);
     d_pfx0 = L.take<MKey>(n_rec + 1);
@@ -1248,7 +1273,14 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
                        cudaMemcpyHostToDevice, st));
 
   tr.mark(4, st);
-  launch_decode(d_cb, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
+  // one read of every data block: checksum (stored blocks; compressed ones were verified on
+  // their stored bytes above), records, keys and value registers
+  {
+    UnpArgs ua{d_cb,          NB,    d_in,       d_nrec,   d_kbytes, nullptr, nullptr,
+               d_hdr,         d_rec_first, d_key_first, d_chunk_first, d_chunkF, d_snap, recs,
+               d_arena,       d_errs, d_errs + n_jobs + 1, comp_blocks == 0};
+    launch_unpack(ua, tabs, st);
+  }
   tr.mark(5, st);
   launch_check_index(d_cb, NB, d_in, d_nrec, d_rec_first, recs, d_arena, d_errs, st);
   launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
@@ -1262,13 +1294,14 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
   launch_gc_compact(src_o, d_keep, d_pos, n_rec, pb.surv, st);
   launch_job_surv(d_jobs, n_jobs, d_pos, n_rec, d_cnt, st);
-  // the SMs the input checksum kernel left join it for the blocks still to do
-  launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, true, st);
+  // the SMs the stored blocks' checksum kernel left join it for the blocks still to do
+  if (comp_blocks)
+    launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, true, st);
   CK(cudaGetLastError());
   if ((rc = run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap, tabs, st,
                      side, &tr)))
     return rc;
-  CK(cudaStreamWaitEvent(st, side->ev[1], 0));
+  if (comp_blocks) CK(cudaStreamWaitEvent(st, side->ev[1], 0));
   CK(cudaStreamWaitEvent(st, side->ev[3], 0));
   tr.mark(10, st);
   tdev.stop(st);
@@ -1313,7 +1346,8 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   if (ms_d2h) *ms_d2h = d2h;
   if (tr.on) {
     stage_ms[0] = tr.span(0, 3);
-    stage_ms[1] = tr.span(11, 12);  // input checksum kernel (side stream, beside the later stages)
+    // stored blocks' checksums (compressed inputs only: side stream, beside the later stages)
+    stage_ms[1] = comp_blocks ? tr.span(11, 12) : 0.0;
     stage_ms[2] = tr.span(4, 5);
     stage_ms[3] = tr.span(5, 6);
     stage_ms[4] = tr.span(6, 7);
@@ -1463,6 +1497,7 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
   CK(cudaMemcpyAsync(d_cnt, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
   launch_build_records(ukeys, ukoff, seqs, types, vals, voff, n, recs, arena, pb.surv, d_err, st);
   launch_build_check(recs, arena, n, d_err, st);
+  launch_value_crc(recs, nullptr, n, tabs, st);
   CK(cudaGetLastError());
   Side* side = nullptr;
   if ((rc = get_side(&side))) return rc;
@@ -1643,12 +1678,15 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   BlockDesc* d_blocks;
   uint32_t *d_nrec, *d_rec_first, *d_in_rec, *d_plan_nrec;
   uint64_t *d_kbytes, *d_key_first, *d_in_key, *d_plan_kbytes;
-  uint16_t* d_hdr;
+  uint2* d_hdr;  // the walk's entry table
+  uint32_t *d_nch, *d_chunk_first;  // the unpack's chunks per block and their offsets
   void* d_tmpB;
   uint8_t *d_link, *d_plan_link;
   auto layB = [&](Layout& L) {
     d_blocks = L.take<BlockDesc>(NB + 1);
-    d_hdr = L.take<uint16_t>(uint64_t(NB) * kHdrMax + 1);
+    d_hdr = L.take<uint2>(uint64_t(NB) * kHdrMax + 1);
+    d_nch = L.take<uint32_t>(NB + 1);
+    d_chunk_first = L.take<uint32_t>(NB + 1);
     d_nrec = L.take<uint32_t>(NB + 1);
     d_kbytes = L.take<uint64_t>(NB + 1);
     d_plan_nrec = L.take<uint32_t>(NB + 1);
@@ -1667,7 +1705,8 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   LB.off = 0;
   layB(LB);
   launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
-  launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, tabs, st);
+  launch_block_scan(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, tabs, st, d_nch);
+  CK((exclusive_scan<uint32_t, uint32_t>(d_nch, d_chunk_first, NB, nullptr, d_tmpB, st)));
   launch_zero_failed(d_blocks, NB, d_errs, d_nrec, d_kbytes, st);
   launch_run_links(d_in, N, d_blocks, d_errs, d_plan_link, st);
   if (NB) {
@@ -1684,6 +1723,8 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   CK(cudaMemcpyAsync(in_rec.data(), d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(in_key.data(), d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&fmt.max_kv, &d_cnt->max_kv, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  uint32_t n_chunks = 0;
+  CK(cudaMemcpyAsync(&n_chunks, d_chunk_first + NB, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   if (N) CK(cudaMemcpyAsync(link.data(), d_plan_link, N, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const uint32_t n_rec = in_rec[N];
@@ -1728,13 +1769,16 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
   Layout LC;
   Recs recs;
   uint8_t* d_arena;
-  uint32_t *d_ord0, *d_ord1, *d_keep, *d_pos, *d_co;
+  uint32_t *d_ord0, *d_ord1, *d_keep, *d_pos, *d_co, *d_chunkF, *d_snap;
   MKey *d_pfx0, *d_pfx1;
   MergeSpan* d_spans;
   PackBufs pb;
+  const uint64_t chunk_cap = uint64_t(n_chunks) + 16;
   auto layC = [&](Layout& L) {
     recs = recs_layout(L, n_rec);
     d_arena = L.take<uint8_t>(K + 64);
+    d_chunkF = L.take<uint32_t>(chunk_cap);
+    d_snap = L.take<uint32_t>(2ull * n_rec + 2ull * NB + 2);
     d_ord0 = L.take<uint32_t>(n_rec + 1);
     d_ord1 = L.take<uint32_t>(n_rec + 1);
     d_pfx0 = L.take<MKey>(n_rec + 1);
@@ -1773,15 +1817,18 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     launch_footers_finish(d_in, N, d_errs, st);
     launch_plan_checks(d_in, N, d_plan_nblk, d_errs, st);
     launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st);
-    CK(fork_join(side, 0, st, side->s));
-    launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, false,
-                      side->s);
-    CK(cudaEventRecord(side->ev[1], side->s));
     launch_block_walk(d_blocks, NB, d_in, d_nrec, d_kbytes, d_errs, d_cnt, d_hdr, st);
     launch_plan_check_recs(d_blocks, NB, d_nrec, d_kbytes, d_plan_nrec, d_plan_kbytes, d_in, d_errs, st);
     launch_run_links(d_in, N, d_blocks, d_errs, d_link, st);
     launch_plan_check_links(d_link, d_plan_link, N, d_in, d_errs, st);
-    launch_decode(d_blocks, NB, d_in, d_nrec, d_hdr, d_rec_first, d_key_first, recs, d_arena, d_errs, st);
+    {
+      // the chunk offsets are the plan's (a block with more chunks than planned takes the
+      // path without boundaries)
+      UnpArgs ua{d_blocks,      NB,     d_in,       d_nrec,   d_kbytes, d_plan_nrec, d_plan_kbytes,
+                 d_hdr,         d_rec_first, d_key_first, d_chunk_first, d_chunkF, d_snap, recs,
+                 d_arena,       d_errs, d_errs + n_jobs + 1, true};
+      launch_unpack(ua, tabs, st);
+    }
     launch_plan_sanitize(recs, n_rec, d_jobs, n_jobs, d_errs, d_arena, st);
     launch_check_index(d_blocks, NB, d_in, d_nrec, d_rec_first, recs, d_arena, d_errs, st);
     launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
@@ -1794,11 +1841,9 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
     CK((exclusive_scan<uint32_t, uint32_t>(d_keep, d_pos, n_rec, nullptr, pb.scan_tmp, st)));
     launch_gc_compact(src_o, d_keep, d_pos, n_rec, pb.surv, st);
     launch_job_surv(d_jobs, n_jobs, d_pos, n_rec, d_cnt, st);
-    launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, true, st);
     luda_status prc = run_pack(pb, d_cnt, d_jobs, n_jobs, d_errs, cap, recs, d_arena, fmt, d_out, out_cap, bm_cap,
                                tabs, st, side);
     if (prc) return prc;
-    CK(cudaStreamWaitEvent(st, side->ev[1], 0));
     CK(cudaStreamWaitEvent(st, side->ev[3], 0));
     return LUDA_OK;
   };

@@ -129,6 +129,7 @@ struct Recs {
   uint64_t* vptr;   // device address of the value bytes (inside an input table)
   uint32_t* vlen;
   uint32_t* src;    // batch-global input index (order check)
+  uint32_t* vcrc;   // F(value): CRC-32C register after the value bytes from a zero register
 };
 
 // 8 key bytes at p as a big-endian word; bytes at index >= avail read as 0. p may have any

@@ -35,9 +35,17 @@ constexpr int kShiftInv = 15;
 constexpr int kShift992 = kShiftPow + kShiftInv;  // "feed 992 zero bytes" (32-byte lane spans)
 constexpr int kShiftTables = kShift992 + 1;
 
+// Shift matrices of the unpack's 144-byte chunks (each 4 x 256 words), Z_L for L = 16, 32,
+// 64, 128 (the byte-table steps of a shift below 144), 80 (the second of a chunk's two
+// chains), 144 * 2^k for k < 5 (one chunk, and the lane butterfly) and 144 * 32 (the
+// other lanes' chunks of a round).
+constexpr uint32_t kChunk = 144;
+enum : int { kCZ16, kCZ32, kCZ64, kCZ128, kCZ80, kCZ144, kCZ288, kCZ576, kCZ1152, kCZ2304, kCZ4608, kChunkTables };
+
 struct CrcTabs {
   const uint32_t* slice;  // 4 x 256: slice[k*256 + v] = register after k+1 byte steps of v
   const uint32_t* shift;  // kShiftTables x 4 x 256
+  const uint32_t* chunk;  // kChunkTables x 4 x 256 (the unpack kernel's matrices)
 };
 
 // One 4-byte step with slicing-by-4 tables in shared memory.
@@ -311,6 +319,33 @@ __device__ __forceinline__ uint32_t crc_zeros(uint32_t v, uint64_t L, const CrcT
   uint64_t q = L >> 4;
   for (uint32_t j = 0; q; ++j, q >>= 1)
     if (q & 1u) v = crc_shift(tabs.shift + size_t(j) * 1024, v);
+  return v;
+}
+
+// ---- CRCs assembled from pieces --------------------------------------------------------------
+// A data block's checksum is assembled from the registers of its pieces: with F(M) the
+// register after feeding M into a zero register, F(A || B) = Z_|B|(F(A)) xor F(B), and the
+// standard CRC of a message M of n bytes is ~(Z_n(0xFFFFFFFF) xor F(M)). The value of every
+// record carries F(value) from the pass that read it, so the encoder's blocks need only
+// the few header and key bytes fed directly plus one shift per piece.
+
+// One byte step of the register (T0: the first 256 words of the slicing table).
+__device__ __forceinline__ uint32_t crc_byte(uint32_t c, uint32_t b, const uint32_t* T0) {
+  return T0[(c ^ b) & 0xFFu] ^ (c >> 8);
+}
+
+// One matrix of four byte tables (1024 words) applied to v.
+__device__ __forceinline__ uint32_t crc_mat(const uint32_t* t, uint32_t v) {
+  return t[v & 0xFFu] ^ t[256 + ((v >> 8) & 0xFFu)] ^ t[512 + ((v >> 16) & 0xFFu)] ^ t[768 + (v >> 24)];
+}
+
+// Z_L(v) from tables in shared memory: L mod 16 zero-byte steps with T0, then for every
+// set bit j of L / 16 the matrix Z_{16 * 2^j} stored at sZ + j * 1024 (2^nz > L / 16).
+__device__ __forceinline__ uint32_t crc_zeros_s(uint32_t v, uint32_t L, const uint32_t* T0, const uint32_t* sZ) {
+  for (uint32_t r = L & 15u; r; --r) v = T0[v & 0xFFu] ^ (v >> 8);
+  uint32_t q = L >> 4;
+  for (uint32_t j = 0; q; ++j, q >>= 1)
+    if (q & 1u) v = crc_mat(sZ + j * 1024u, v);
   return v;
 }
 

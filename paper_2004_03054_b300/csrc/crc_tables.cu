@@ -118,4 +118,23 @@ bool make_crc_tables(uint32_t* slice, uint32_t* shift) {
   return true;
 }
 
+// Fills `out` (kChunkTables * 1024 words) with the matrices Z_L listed at kCZ16 ... kCZ4608.
+bool make_chunk_tables(uint32_t* out) {
+  uint32_t slice[256];
+  for (uint32_t v = 0; v < 256; ++v) {
+    uint32_t c = v;
+    for (int b = 0; b < 8; ++b) c = (c & 1u) ? (c >> 1) ^ kPoly : (c >> 1);
+    slice[v] = c;
+  }
+  Mat z1;
+  for (int i = 0; i < 32; ++i) {
+    const uint32_t r = 1u << i;
+    z1.col[i] = slice[r & 0xFFu] ^ (r >> 8);
+  }
+  static const uint32_t kLen[kChunkTables] = {16, 32, 64, 128, 80, kChunk, 2 * kChunk, 4 * kChunk,
+                                              8 * kChunk, 16 * kChunk, 32 * kChunk};
+  for (int t = 0; t < kChunkTables; ++t) to_tables(power(z1, kLen[t]), out + size_t(t) * 1024);
+  return true;
+}
+
 }  // namespace luda

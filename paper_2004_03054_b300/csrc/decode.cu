@@ -244,8 +244,9 @@ __device__ __forceinline__ uint32_t read_header(const uint8_t* p, const uint8_t*
 __global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
                                                     const DInput* __restrict__ in, uint32_t* __restrict__ nrec,
                                                     uint64_t* __restrict__ kbytes, DErr* errs, Counts* counts,
-                                                    uint16_t* __restrict__ hdr_tab, uint64_t* __restrict__ ulen,
-                                                    uint64_t* __restrict__ ures, bool contents) {
+                                                    uint2* __restrict__ ent_tab, uint64_t* __restrict__ ulen,
+                                                    uint64_t* __restrict__ ures, bool contents,
+                                                    uint32_t* __restrict__ nch) {
   unsigned long long data_bytes = 0, comp_bytes = 0;
   uint32_t max_kv = 0, comp = 0;
   for (uint64_t g = gtid(); g < n_blocks; g += gstride()) {
@@ -285,6 +286,7 @@ __global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict_
         }
         nrec[g] = 0;
         kbytes[g] = 0;
+        if (nch) nch[g] = 0;
         continue;
       }
       const uint64_t nr = b.size >= 4 ? ld_u32(b.ptr + b.size - 4) : 0;
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict_
       if (!bad) {
         const uint64_t rstart = b.size - 4 - 4 * nr;
         const uint8_t* rs = b.ptr + rstart;
-        uint16_t* offs = b.size < 65536 ? hdr_tab + g * kHdrMax : nullptr;
+        uint2* ents = ent_tab && b.size < 65536 ? ent_tab + g * kHdrMax : nullptr;
         uint64_t s = ld_u32(rs);
         bad = s != 0;
         for (uint64_t k = 0; k < nr && !bad; ++k) {
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict_
           uint64_t prev = 0;
           bool first = true;
           while (p < end) {
-            if (offs && cnt < kHdrMax) offs[cnt] = uint16_t(p - b.ptr);
+            const uint32_t off = uint32_t(p - b.ptr);
             uint32_t f[3];
             const uint32_t hl = read_header(p, end, f);
             if (!hl) {
@@ -319,6 +321,13 @@ __global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict_
                 vlen > uint64_t(end - p) - nonshared || shared + nonshared < 8) {
               bad = true;
               break;
+            }
+            if (ents && cnt < kHdrMax) {
+              // entry start, value start and end; shared and non-shared key bytes (at most 255
+              // each here: longer keys are rebuilt by the sequential walk anyway)
+              const uint32_t vs = uint32_t(p - b.ptr) + uint32_t(nonshared);
+              ents[cnt] = make_uint2(off | (vs << 16), (vs + uint32_t(vlen)) | (min(uint32_t(shared), 255u) << 16) |
+                                                           (min(uint32_t(nonshared), 255u) << 24));
             }
             p += nonshared + vlen;
             prev = shared + nonshared;
@@ -338,6 +347,13 @@ __global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict_
     }
     nrec[g] = cnt;
     kbytes[g] = kb;
+    if (nch) {
+      // chunks of the unpack's boundary path: the message (contents and type byte) widened
+      // to 16-byte words, in kChunk-byte chunks
+      const uintptr_t ps = reinterpret_cast<uintptr_t>(b.ptr), a1 = (ps + b.size + 1 + 15) & ~uintptr_t(15);
+      const uint64_t U = (a1 - (ps & ~uintptr_t(15)) + kChunk - 1) / kChunk;
+      nch[g] = cnt > 0 && cnt <= kHdrMax && b.size < 65536 && U <= kUnpChunkMax ? uint32_t(U) : 0u;
+    }
   }
 #pragma unroll
   for (int d = 16; d; d >>= 1) {
@@ -355,15 +371,12 @@ __global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict_
   if ((threadIdx.x & 31u) == 0 && max_kv) atomicMax(&counts->max_kv, max_kv);
 }
 
-// One warp per data block. With the block's entry offsets from the scan (at most kHdrMax
-// entries, keys of at most 128 bytes), all headers are parsed at once (lane per entry)
-// and the keys are rebuilt entry by entry with lanes as byte positions: lane t keeps byte
-// t (t + 32, ...) of the current key in registers, takes the new bytes from the entry's
-// key delta, and stores the whole key with coalesced byte stores. Other blocks are
-// decoded by lane 0 alone, walking the segments in order.
+// Keys of at most 32 * kDecSlots = 128 bytes are rebuilt with lanes as byte positions; a
+// block with longer keys (or too many entries for the walk's table) is decoded by one lane
+// walking its restart segments in order (decode_walk).
 constexpr uint32_t kDecSlots = 4;  // key bytes per lane: 128-byte keys
 
-__device__ void decode_walk(const BlockDesc& b, uint64_t rec, uint64_t kpos, Recs& recs, uint8_t* arena, bool* bad) {
+__device__ void decode_walk(const BlockDesc& b, uint64_t rec, uint64_t kpos, const Recs& recs, uint8_t* arena, bool* bad) {
   const uint64_t nr = ld_u32(b.ptr + b.size - 4);
   const uint64_t rstart = b.size - 4 - 4 * nr;
   const uint8_t* rs = b.ptr + rstart;
@@ -398,54 +411,433 @@ __device__ void decode_walk(const BlockDesc& b, uint64_t rec, uint64_t kpos, Rec
   }
 }
 
-__global__ void __launch_bounds__(512) k_decode(const BlockDesc* __restrict__ blocks, uint32_t n_blocks,
-                                                const DInput* __restrict__ in, const uint32_t* __restrict__ nrec,
-                                                const uint16_t* __restrict__ hdr_tab,
-                                                const uint32_t* __restrict__ rec_first,
-                                                const uint64_t* __restrict__ key_first, Recs recs,
-                                                uint8_t* __restrict__ arena, DErr* errs) {
+// F(value) of every record: one warp per record, 32-byte lane spans over the value from a
+// zero register, without the final complement (the piece the encoder's trailers reuse).
+__global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_value_crc(Recs recs, const uint32_t* __restrict__ n_dev,
+                                                                    uint32_t n_max, CrcTabs tabs) {
+  extern __shared__ uint32_t s_vc[];
+  load_rep_tables992(s_vc, s_vc + kRepWords, tabs);
+  __syncthreads();
+  const uint32_t n = n_dev ? *n_dev : n_max;
   const uint32_t lane = lane_id();
+  const uint32_t tl = smem_addr(s_vc) + lane * 4u, tz = zcopy_addr(s_vc + kRepWords, lane);
   const uint64_t warps = gstride() / 32;
-  for (uint64_t g = gtid() / 32; g < n_blocks; g += warps) {
-    const BlockDesc b = blocks[g];
-    DErr* e = errs + b.job;
-    if (b.ptr == nullptr || *(volatile int32_t*)&e->code != 0) continue;
-    const uint32_t nent = nrec[g];
-    const uint64_t rec0 = rec_first[g], key0 = key_first[g];
-    bool bad = false;
-    bool tab = nent <= kHdrMax && b.size < 65536;
-    // lane-per-entry header parse (entries lane and lane + 32)
-    uint32_t sh[2] = {0, 0}, ns[2] = {0, 0}, kl[2] = {0, 0}, dp[2] = {0, 0};
-    if (tab) {
-      bool long_key = false;
+  for (uint64_t r = gtid() / 32; r < n; r += warps) {
+    const uint32_t c = warp_crc32c_u32<false, false>(reinterpret_cast<const uint8_t*>(recs.vptr[r]), recs.vlen[r],
+                                                      tl, tz, tabs);
+    if (lane == 0) recs.vcrc[r] = c;
+  }
+}
+
+// ---- unpack: checksum, value registers and decode from one read of each block ---------------
+// Two kernels, one warp per data block in each (§III-C "unpack": blocks are independent).
+//
+// k_unpack (checksum pass). The block's message (contents and type byte, n bytes) is cut
+// into chunks of kChunk = 144 bytes that end at the 16-byte boundary after its end (bytes
+// outside the message read as zero); in round r lane l folds chunk U - 32 * (rounds - r) + l
+// with two independent registers (the chunk's first 64 bytes and its last 80, joined by
+// Z_80), and keeps Z_{32 * kChunk}-weighted sums of its chunks; a butterfly joins the lanes
+// (Z_{kChunk * 2^k}). With the first four message bytes complemented (the register's
+// initial value), the result equals Z_pad of the complemented stored CRC when the block is
+// intact. For a block with at most kHdrMax entries the walk's entry table gives the pieces
+// of the message (each entry's header with key delta, its value, and the restart array
+// with num_restarts and the type byte), and the pass stores, per chunk, its register
+// (chunkF) and, per piece boundary, the register of its chunk's bytes before the
+// boundary's 16-byte word (snap). Other blocks are decoded here by the sequential walk,
+// each value's register computed by the whole warp.
+//
+// k_unpack_post (value registers and keys, blocks with boundaries). Lane per entry: the
+// prefix register at a boundary is its word's register advanced by the word's bytes before
+// it; F(value) = S(end) xor Z_len(S(start)) inside one chunk, the chunks in between joined
+// by Z_kChunk (Horner). The keys are rebuilt with lanes as byte positions (the shared
+// prefix carried in registers, the delta read from the block, which the checksum pass left
+// in L2) into a per-warp buffer in shared memory and the key arena.
+constexpr uint32_t kUnpWarps = 16;
+constexpr uint32_t kUnpBndMax = 2 * kHdrMax + 2;  // piece boundaries: two per entry, the tail, the end
+constexpr uint8_t kNoBnd = 0xFF;
+struct UnpWarp {
+  uint32_t bnd[kUnpBndMax];      // piece boundaries (message offsets, ascending)
+  uint8_t bfirst[kUnpChunkMax];  // first boundary inside each chunk (kNoBnd: none)
+};
+constexpr uint32_t kUnpSmem = kRepWords * 4 + kChunkTables * 4096 + kUnpWarps * uint32_t(sizeof(UnpWarp));
+static_assert(kUnpSmem <= 227u * 1024u, "unpack shared memory");
+
+// Byte step with this lane's column of the lane-replicated slicing tables.
+__device__ __forceinline__ uint32_t crc_byte_rep(uint32_t c, uint32_t b, uint32_t tl) {
+  return lds_off<0u>(tl + ((c ^ b) & 0xFFu) * 128u) ^ (c >> 8);
+}
+
+// Z_L(v) for L < 256: L mod 16 byte steps, then Z_16, Z_32, Z_64, Z_128 (sC: the chunk
+// matrices in shared memory).
+__device__ __forceinline__ uint32_t unp_zeros(uint32_t v, uint32_t L, uint32_t tl, const uint32_t* sC) {
+  for (uint32_t r = L & 15u; r; --r) v = crc_byte_rep(v, 0u, tl);
+  const uint32_t q = L >> 4;
+#pragma unroll
+  for (uint32_t j = 0; j < 4; ++j)
+    if (q & (1u << j)) v = crc_mat(sC + (kCZ16 + j) * 1024u, v);
+  return v;
+}
+
+// Message geometry: chunks of kChunk bytes ending at a1 = end rounded up to 16.
+struct UnpGeo {
+  uintptr_t ps, pe, a1, lo16;
+  uint32_t U, rounds, pad;
+  int32_t x0;  // message offset of chunk 0's first byte (<= 0)
+};
+
+__device__ __forceinline__ UnpGeo unp_geo(const uint8_t* p, uint32_t n) {
+  UnpGeo G;
+  G.ps = reinterpret_cast<uintptr_t>(p);
+  G.pe = G.ps + n;
+  G.a1 = (G.pe + 15) & ~uintptr_t(15);
+  G.lo16 = G.ps & ~uintptr_t(15);
+  G.pad = uint32_t(G.a1 - G.pe);
+  G.U = uint32_t((G.a1 - G.lo16 + kChunk - 1) / kChunk);
+  G.rounds = (G.U + 31) >> 5;
+  G.x0 = int32_t(int64_t(G.a1) - int64_t(kChunk) * int64_t(G.U) - int64_t(G.ps));
+  return G;
+}
+
+// Bytes of the little-endian word at address q outside [ps, pe) become 0.
+__device__ __forceinline__ uint32_t unp_mask(uint32_t w, uintptr_t q, uintptr_t ps, uintptr_t pe) {
+  uint32_t keep = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+    if (q + b >= ps && q + b < pe) keep |= 0xFFu << (8 * b);
+  return w & keep;
+}
+
+__device__ __forceinline__ uint4 unp_mask4(uint4 x, uintptr_t q, uintptr_t ps, uintptr_t pe) {
+  if (q < ps || q + 16 > pe) {
+    x.x = unp_mask(x.x, q, ps, pe);
+    x.y = unp_mask(x.y, q + 4, ps, pe);
+    x.z = unp_mask(x.z, q + 8, ps, pe);
+    x.w = unp_mask(x.w, q + 12, ps, pe);
+  }
+  return x;
+}
+
+constexpr int kChunkW = int(kChunk / 16);  // 16-byte words of a chunk
+
+// The words of chunk c (c < 0: zeros); only 16-byte words holding message bytes are read,
+// and bytes outside the message read as 0.
+__device__ __forceinline__ void unp_load(const UnpGeo G, int32_t c, uint4 (&w)[kChunkW]) {
+  const uintptr_t base = G.a1 - uintptr_t(kChunk) * uintptr_t(int64_t(G.U) - c);
+  if (c >= 0 && base >= G.ps && base + kChunk <= G.pe) {
+    const uint4* q = reinterpret_cast<const uint4*>(base);
+#pragma unroll
+    for (int t = 0; t < kChunkW; ++t) w[t] = q[t];
+    return;
+  }
+#pragma unroll
+  for (int t = 0; t < kChunkW; ++t) {
+    const uintptr_t q = base + 16u * t;
+    w[t] = make_uint4(0, 0, 0, 0);
+    if (c >= 0 && q >= G.lo16) w[t] = unp_mask4(*reinterpret_cast<const uint4*>(q), q, G.ps, G.pe);
+  }
+}
+
+__device__ __forceinline__ uint32_t crc_quad_rep(uint32_t S, const uint4 v, uint32_t tl) {
+  S = crc_word_rep(S, v.x, tl);
+  S = crc_word_rep(S, v.y, tl);
+  S = crc_word_rep(S, v.z, tl);
+  return crc_word_rep(S, v.w, tl);
+}
+
+// Folds every chunk of the message: returns this lane's Z_{32 * kChunk}-weighted sum of its
+// chunks' registers. With nb > 0 boundaries (W->bnd, W->bfirst set), each chunk's register
+// goes to chF[c] and, for each boundary inside the chunk, the register of the chunk's bytes
+// before the boundary's 16-byte word to snap[i]. With `init`, the sum is that of the message
+// with its first four bytes complemented (the standard register's initial value
+// 0xFFFFFFFF). The next round's chunks are prefetched into L2 while a round is folded.
+__device__ __forceinline__ uint32_t unp_fold(const UnpGeo G, const UnpWarp* W, uint32_t nb, uint32_t* chF,
+                                             uint32_t* snap, uint32_t tl, const uint32_t* sC, bool init) {
+  const uint32_t lane = lane_id();
+  uint32_t acc = 0;
+  for (uint32_t r = 0; r < G.rounds; ++r) {
+    const int32_t c = int32_t(G.U) - int32_t(32 * (G.rounds - r)) + int32_t(lane);
+    if (lane == 0 && r + 1 < G.rounds) {
+      const uintptr_t lo = G.a1 - uintptr_t(kChunk) * uintptr_t(32 * (G.rounds - r - 1));
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(32u * kChunk) : "memory");
+    }
+    uint4 cur[kChunkW];
+    unp_load(G, c, cur);
+    if (c >= 0) {
+      // two chains: words 0..3 (64 bytes) and 4..8 (80 bytes); Sk[j]: register before word j
+      uint32_t SA = 0, SB = 0, Sk[kChunkW];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        if (j < 4) {
+          Sk[j] = SA;
+          SA = crc_quad_rep(SA, cur[j], tl);
+        }
+        Sk[4 + j] = SB;
+        SB = crc_quad_rep(SB, cur[4 + j], tl);
+      }
+      uint32_t S = crc_mat(sC + kCZ80 * 1024u, SA) ^ SB;
+      const int32_t xc = G.x0 + int32_t(kChunk) * c;  // message offset of the chunk
+      if (nb) {
+        chF[c] = S;
+        for (uint32_t bi = W->bfirst[c]; bi < nb; ++bi) {
+          const int32_t rr = int32_t(W->bnd[bi]) - xc;
+          if (rr >= int32_t(kChunk)) break;
+          const uint32_t k = uint32_t(rr) >> 4;
+          uint32_t sv = Sk[0];
+#pragma unroll
+          for (uint32_t j = 1; j < uint32_t(kChunkW); ++j) sv = k == j ? Sk[j] : sv;
+          // a word of the second chain: its register follows the first chain's bytes
+          if (k >= 4) sv ^= unp_zeros(SA, 16u * (k - 4), tl, sC);
+          snap[bi] = sv;
+        }
+      }
+      if (init && xc < 4) {
+        // bytes 0..3 of the message complemented: F(0xFFFFFFFF) shifted to the end of the
+        // chunk, or (bytes split between chunks) Z_{kChunk - 1 - r}(F(0xFF)) per byte at offset r
+        const int32_t r0 = -xc;
+        if (r0 >= 0 && r0 + 4 <= int32_t(kChunk)) {
+          S ^= unp_zeros(crc_word_rep(0u, 0xFFFFFFFFu, tl), uint32_t(int32_t(kChunk) - 4 - r0), tl, sC);
+        } else {
+          const uint32_t ff = crc_byte_rep(0u, 0xFFu, tl);
+          for (int32_t q = 0; q < 4; ++q) {
+            const int32_t rr = q - xc;
+            if (rr >= 0 && rr < int32_t(kChunk)) S ^= unp_zeros(ff, uint32_t(int32_t(kChunk) - 1 - rr), tl, sC);
+          }
+        }
+      }
+      acc = crc_mat(sC + kCZ4608 * 1024u, acc) ^ S;  // the other lanes' chunks of the round
+    }
+  }
+  return acc;
+}
+
+// Z_pad(F(message)) from the lanes' sums (every lane gets it): a butterfly with Z_{kChunk * 2^k}.
+__device__ __forceinline__ uint32_t unp_join(uint32_t acc, const uint32_t* sC) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const uint32_t other = __shfl_xor_sync(0xFFFFFFFFu, acc, 1u << k);
+    const uint32_t* tab = sC + (kCZ144 + k) * 1024u;
+    acc = (lane & (1u << k)) ? (crc_mat(tab, other) ^ acc) : (crc_mat(tab, acc) ^ other);
+  }
+  return acc;
+}
+
+// F(p[0 .. n)) by the whole warp (no boundaries; the pad removed with Z_{-pad}).
+__device__ __noinline__ uint32_t unp_range(const uint8_t* p, uint32_t n, uint32_t tl, const uint32_t* sC,
+                                           const CrcTabs tabs) {
+  if (n == 0) return 0;
+  const UnpGeo G = unp_geo(p, n);
+  uint32_t acc = unp_join(unp_fold(G, nullptr, 0, nullptr, nullptr, tl, sC, false), sC);
+  if (G.pad) acc = crc_shift(tabs.shift + size_t(kShiftPow + G.pad - 1) * 1024, acc);
+  return acc;
+}
+
+// Entry count of block g as the unpack takes it: zero when a replayed plan's counts differ.
+__device__ __forceinline__ uint32_t unp_entries(const UnpArgs& A, uint64_t g) {
+  const uint32_t nent = A.nrec[g];
+  if (A.plan_nrec && (nent != A.plan_nrec[g] || A.kbytes[g] != A.plan_kbytes[g])) return 0;
+  return nent;
+}
+
+// Whether block g takes the boundary path (both kernels decide alike).
+__device__ __forceinline__ bool unp_fast(const UnpArgs& A, const BlockDesc& b, uint64_t g, uint32_t nent,
+                                         const UnpGeo& G) {
+  return nent > 0 && nent <= kHdrMax && b.size < 65536 && G.U <= A.chunk_first[g + 1] - A.chunk_first[g];
+}
+
+__global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, CrcTabs tabs) {
+  extern __shared__ __align__(16) uint32_t s_unp[];
+  uint32_t* sTr = s_unp;
+  uint32_t* sC = s_unp + kRepWords;
+  UnpWarp* Wall = reinterpret_cast<UnpWarp*>(sC + kChunkTables * 1024);
+  {
+    const uint32_t rot = threadIdx.x & 31u;
+    for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) {
+      const uint32_t val = __ldg(tabs.slice + i);
+      uint32_t* row = sTr + i * 32u;
+#pragma unroll 8
+      for (uint32_t l = 0; l < 32; ++l) row[(l + rot) & 31u] = val;
+    }
+    for (uint32_t i = threadIdx.x; i < kChunkTables * 1024; i += blockDim.x) sC[i] = __ldg(tabs.chunk + i);
+  }
+  __syncthreads();
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  UnpWarp* W = Wall + warp;
+  const uint32_t tl = smem_addr(sTr) + lane * 4u;
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t g = gtid() / 32; g < A.n_blocks; g += warps) {
+    const BlockDesc b = A.blocks[g];
+    if (b.ptr == nullptr) continue;
+    const uint32_t nent = unp_entries(A, g);
+    if (!A.verify && nent == 0) continue;
+    const uint64_t rec0 = A.rec_first[g];
+    const uint32_t n = uint32_t(b.size) + 1;  // contents and type byte
+    const UnpGeo G = unp_geo(b.ptr, n);
+    const bool fast = unp_fast(A, b, g, nent, G);
+    const uint32_t nb = fast ? 2 * nent + 2 : 0;
+    if (fast) {
+      // piece boundaries from the walk's entry table, then the first boundary of every chunk
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const uint32_t k = lane + 32 * h;
         if (k < nent) {
-          // the walk already validated this header (16-byte window read)
-          const uint8_t* p = b.ptr + hdr_tab[g * kHdrMax + k];
-          uint32_t f[3] = {0, 0, 0};
-          p += read_header(p, b.ptr + b.size, f);
-          sh[h] = f[0];
-          ns[h] = f[1];
-          kl[h] = f[0] + f[1];
-          dp[h] = uint32_t(p - b.ptr);
-          long_key |= kl[h] > 32 * kDecSlots;
-          recs.vptr[rec0 + k] = reinterpret_cast<uint64_t>(p + f[1]);
-          recs.vlen[rec0 + k] = f[2];
-          recs.klen[rec0 + k] = kl[h];
-          recs.src[rec0 + k] = b.input;
+          const uint2 t = A.ent_tab[g * kHdrMax + k];
+          W->bnd[2 * k] = t.x & 0xFFFFu;
+          W->bnd[2 * k + 1] = t.x >> 16;
+          if (k == nent - 1) {
+            W->bnd[2 * nent] = t.y & 0xFFFFu;  // the restart array
+            W->bnd[2 * nent + 1] = n;
+          }
         }
       }
-      tab = !__any_sync(0xFFFFFFFFu, long_key);
+      for (uint32_t c = lane; c < G.U; c += 32) W->bfirst[c] = kNoBnd;
+      __syncwarp();
+      for (uint32_t i = lane; i < nb; i += 32) {
+        const uint32_t c = uint32_t(int32_t(W->bnd[i]) - G.x0) / kChunk;
+        if (c < G.U && (i == 0 || uint32_t(int32_t(W->bnd[i - 1]) - G.x0) / kChunk != c)) W->bfirst[c] = uint8_t(i);
+      }
+      __syncwarp();
     }
-    if (!tab) {
-      if (lane == 0) decode_walk(b, rec0, key0, recs, arena, &bad);
-      bad = __any_sync(0xFFFFFFFFu, bad);
-      if (bad && lane == 0) report(e, E_CORRUPT, in[b.input].local, b.off);
+    uint32_t acc = 0;
+    if (fast || A.verify)
+      acc = unp_fold(G, W, nb, A.chunkF + A.chunk_first[g], A.snap + 2 * (rec0 + g), tl, sC, A.verify);
+    if (A.verify) {
+      const uint32_t got = unp_join(acc, sC);
+      if (lane == 0) {
+        const uint32_t want = unp_zeros(~crc_unmask(ld_u32(b.ptr + b.size + 1)), G.pad, tl, sC);
+        DErr* ve = A.verr + b.job;
+        if (got != want) report(ve, E_CORRUPT, A.in[b.input].local, b.off);
+        else if (b.ptr[b.size] > 1) report(ve, E_NOTSUP, A.in[b.input].local, b.off);  // 1: compressed (R4c)
+      }
+    }
+    if (nent == 0 || fast) {
+      __syncwarp();  // the warp's shared arrays are reused by its next block
       continue;
     }
-    // key offsets: exclusive scan of key lengths over the (up to 64) entries
+    // a block without boundaries: the sequential walk, then each value's register
+    bool bad = false;
+    if (lane == 0) decode_walk(b, rec0, A.key_first[g], A.recs, A.arena, &bad);
+    bad = __any_sync(0xFFFFFFFFu, bad);
+    if (bad && lane == 0) report(A.errs + b.job, E_CORRUPT, A.in[b.input].local, b.off);
+    for (uint32_t k = 0; k < nent; ++k) {
+      const uint32_t v = unp_range(reinterpret_cast<const uint8_t*>(A.recs.vptr[rec0 + k]), A.recs.vlen[rec0 + k], tl,
+                                   sC, tabs);
+      if (lane == 0) A.recs.vcrc[rec0 + k] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// ---- k_unpack_post ------------------------------------------------------------------------------
+constexpr uint32_t kPostWarps = 8;
+constexpr uint32_t kPostKeyBuf = 1024;  // key bytes of a block rebuilt in shared memory
+constexpr uint32_t kPostZ = kCZ144 + 1;  // the chunk matrices kCZ16 .. kCZ144
+constexpr uint32_t kPostSmem = (1024 + kPostZ * 1024) * 4 + kPostWarps * kPostKeyBuf;
+
+// Z_L(v) for L < 256 with the slicing table sT and the matrices sZ (Z_16 .. Z_128) in shared
+// memory: whole zero words, single zero bytes, then the matrices.
+__device__ __forceinline__ uint32_t post_zeros(uint32_t v, uint32_t L, const uint32_t* sT, const uint32_t* sZ) {
+  uint32_t r = L & 15u;
+  for (; r >= 4; r -= 4) v = crc_step4(v, 0u, sT);
+  for (; r; --r) v = sT[v & 0xFFu] ^ (v >> 8);
+  const uint32_t q = L >> 4;
+#pragma unroll
+  for (uint32_t j = 0; j < 4; ++j)
+    if (q & (1u << j)) v = crc_mat(sZ + (kCZ16 + j) * 1024u, v);
+  return v;
+}
+
+// Register v advanced by the first q (< 16) bytes of the 16-byte word at address w (bytes
+// outside the message as 0): whole 4-byte words, then single bytes.
+__device__ __forceinline__ uint32_t post_feed(uint32_t v, const UnpGeo& G, uintptr_t w, uint32_t q,
+                                              const uint32_t* sT) {
+  if (q == 0) return v;
+  const uint4 x = unp_mask4(*reinterpret_cast<const uint4*>(w), w, G.ps, G.pe);
+  const uint32_t words[4] = {x.x, x.y, x.z, x.w};
+  uint32_t t = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < 3; ++j)
+    if (t + 4 <= q) {
+      v = crc_step4(v, words[j], sT);
+      t += 4;
+    }
+  const uint32_t last = t == 0 ? words[0] : t == 4 ? words[1] : t == 8 ? words[2] : words[3];
+  for (uint32_t i = 0; t + i < q; ++i) v = sT[(v ^ (last >> (8 * i))) & 0xFFu] ^ (v >> 8);
+  return v;
+}
+
+// Eight bytes of shared memory at p (any alignment) as a little-endian word; big-endian when
+// `be`, with bytes at index >= avail as 0.
+__device__ __forceinline__ uint64_t smem_word(const uint8_t* p, uint32_t avail, bool be) {
+  uint64_t v = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < 8; ++i) {
+    const uint64_t byte = i < avail ? p[i] : 0u;
+    v |= be ? byte << (56 - 8 * i) : byte << (8 * i);
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kPostWarps * 32) k_unpack_post(const UnpArgs A, CrcTabs tabs) {
+  extern __shared__ __align__(16) uint32_t s_post[];
+  uint32_t* sT = s_post;
+  uint32_t* sZ = s_post + 1024;
+  for (uint32_t i = threadIdx.x; i < 1024; i += blockDim.x) sT[i] = __ldg(tabs.slice + i);
+  for (uint32_t i = threadIdx.x; i < kPostZ * 1024; i += blockDim.x) sZ[i] = __ldg(tabs.chunk + i);
+  __syncthreads();
+  const uint32_t* sZ144 = sZ + kCZ144 * 1024u;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  uint8_t* keys = reinterpret_cast<uint8_t*>(sZ + kPostZ * 1024) + warp * kPostKeyBuf;
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t g = gtid() / 32; g < A.n_blocks; g += warps) {
+    const BlockDesc b = A.blocks[g];
+    if (b.ptr == nullptr) continue;
+    const uint32_t nent = unp_entries(A, g);
+    const UnpGeo G = unp_geo(b.ptr, uint32_t(b.size) + 1);
+    if (!unp_fast(A, b, g, nent, G)) continue;
+    const uint64_t rec0 = A.rec_first[g], key0 = A.key_first[g];
+    const uint32_t* chF = A.chunkF + A.chunk_first[g];
+    const uint32_t* snap = A.snap + 2 * (rec0 + g);
+    const uintptr_t base0 = G.a1 - uintptr_t(kChunk) * uintptr_t(G.U);  // chunk 0's first byte
+    // lane per entry (entries lane and lane + 32): record fields and the value's register
+    uint32_t sh[2] = {0, 0}, kl[2] = {0, 0}, dp[2] = {0, 0};
+    bool long_key = false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t k = lane + 32 * h;
+      if (k < nent) {
+        const uint2 t = A.ent_tab[g * kHdrMax + k];
+        const uint32_t vs = t.x >> 16, ve = t.y & 0xFFFFu, ns = t.y >> 24;
+        sh[h] = (t.y >> 16) & 0xFFu;
+        kl[h] = sh[h] + ns;
+        dp[h] = vs - ns;
+        long_key |= kl[h] > 32 * kDecSlots;
+        A.recs.vptr[rec0 + k] = reinterpret_cast<uint64_t>(b.ptr + vs);
+        A.recs.vlen[rec0 + k] = ve - vs;
+        A.recs.klen[rec0 + k] = kl[h];
+        A.recs.src[rec0 + k] = b.input;
+        uint32_t F = 0;
+        if (vs < ve) {
+          // prefix registers at the value's start (boundary 2k + 1) and end (boundary 2k + 2)
+          const uint32_t ao = uint32_t(int32_t(vs) - G.x0), zo = uint32_t(int32_t(ve) - G.x0);
+          const uint32_t ca = ao / kChunk, ra = ao - kChunk * ca;
+          const uint32_t cb = (zo - 1) / kChunk, rb = zo - kChunk * cb;
+          const uint32_t Pa = post_feed(snap[2 * k + 1], G, base0 + (ao & ~15u), ao & 15u, sT);
+          const uint32_t Pb = rb == kChunk ? chF[cb] : post_feed(snap[2 * k + 2], G, base0 + (zo & ~15u), zo & 15u, sT);
+          if (ca == cb) {
+            F = Pb ^ post_zeros(Pa, rb - ra, sT, sZ);
+          } else {
+            uint32_t x = chF[ca] ^ post_zeros(Pa, kChunk - ra, sT, sZ);
+            for (uint32_t c = ca + 1; c < cb; ++c) x = crc_mat(sZ144, x) ^ chF[c];
+            F = post_zeros(x, rb, sT, sZ) ^ Pb;
+          }
+        }
+        A.recs.vcrc[rec0 + k] = F;
+      }
+    }
+    long_key = __any_sync(0xFFFFFFFFu, long_key);
+    // keys
+    bool bad = false;
     uint32_t x0 = kl[0], x1 = kl[1];
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -456,42 +848,49 @@ __global__ void __launch_bounds__(512) k_decode(const BlockDesc* __restrict__ bl
       }
     }
     const uint32_t tot0 = __shfl_sync(0xFFFFFFFFu, x0, 31);
-    const uint32_t ko[2] = {x0 - kl[0], tot0 + x1 - kl[1]};
-    uint8_t cur[kDecSlots] = {0, 0, 0, 0};
-    for (uint32_t k = 0; k < nent; ++k) {
-      const uint32_t src = k & 31u, h = k >> 5;
-      const uint32_t shared = __shfl_sync(0xFFFFFFFFu, h ? sh[1] : sh[0], src);
-      const uint32_t klen = __shfl_sync(0xFFFFFFFFu, h ? kl[1] : kl[0], src);
-      const uint32_t dpos = __shfl_sync(0xFFFFFFFFu, h ? dp[1] : dp[0], src);
-      const uint32_t kof = __shfl_sync(0xFFFFFFFFu, h ? ko[1] : ko[0], src);
-      uint8_t* kd = arena + key0 + kof;
+    const uint32_t ko[2] = {x0 - kl[0], tot0 + x1 - kl[1]};  // key offsets (exclusive scan of lengths)
+    const uint32_t ktot = tot0 + __shfl_sync(0xFFFFFFFFu, x1, 31);
+    if (long_key || ktot > kPostKeyBuf) {
+      if (lane == 0) decode_walk(b, rec0, key0, A.recs, A.arena, &bad);
+    } else {
+      // lane t keeps byte t (t + 32, ...) of the current key: the shared prefix carried from
+      // the previous key, the rest read from the key delta (four entries' reads in flight)
+      uint8_t cur[kDecSlots] = {0, 0, 0, 0};
+#pragma unroll 4
+      for (uint32_t k = 0; k < nent; ++k) {
+        const uint32_t src = k & 31u, h = k >> 5;
+        const uint32_t shared = __shfl_sync(0xFFFFFFFFu, h ? sh[1] : sh[0], src);
+        const uint32_t klen = __shfl_sync(0xFFFFFFFFu, h ? kl[1] : kl[0], src);
+        const uint32_t dpos = __shfl_sync(0xFFFFFFFFu, h ? dp[1] : dp[0], src);
+        const uint32_t kof = __shfl_sync(0xFFFFFFFFu, h ? ko[1] : ko[0], src);
 #pragma unroll
-      for (uint32_t s = 0; s < kDecSlots; ++s) {
-        const uint32_t t = lane + 32 * s;
-        if (t < klen) {
-          if (t >= shared) cur[s] = b.ptr[dpos + t - shared];
-          kd[t] = cur[s];
+        for (uint32_t s = 0; s < kDecSlots; ++s) {
+          const uint32_t t = lane + 32 * s;
+          if (t < klen) {
+            if (t >= shared) cur[s] = __ldg(b.ptr + dpos + t - shared);
+            keys[kof + t] = cur[s];
+            A.arena[key0 + kof + t] = cur[s];
+          }
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t k = lane + 32 * h;
+        if (k < nent) {
+          const uint8_t* kd = keys + ko[h];
+          const uint32_t ul = kl[h] - 8;
+          const uint64_t tr = smem_word(kd + ul, 8u, false);
+          if ((tr & 0xFF) > 1) bad = true;
+          A.recs.pfx[rec0 + k] = smem_word(kd, ul < 8 ? ul : 8u, true);
+          A.recs.tr[rec0 + k] = tr;
+          A.recs.koff[rec0 + k] = key0 + ko[h];
         }
       }
     }
-    __syncwarp();  // the warp's key bytes are visible to all its lanes
-    // per entry (lane): user-key prefix and trailer read back from the rebuilt key
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t k = lane + 32 * h;
-      if (k < nent) {
-        const uint8_t* kd = arena + key0 + ko[h];
-        const uint32_t ul = kl[h] - 8;
-        const uint64_t pf = key_word(kd, ul < 8 ? ul : 8u);
-        const uint64_t tr = le_word(kd + ul);
-        if ((tr & 0xFF) > 1) bad = true;
-        recs.pfx[rec0 + k] = pf;
-        recs.tr[rec0 + k] = tr;
-        recs.koff[rec0 + k] = key0 + ko[h];
-      }
-    }
     bad = __any_sync(0xFFFFFFFFu, bad);
-    if (bad && lane == 0) report(e, E_CORRUPT, in[b.input].local, b.off);
+    if (bad && lane == 0) report(A.errs + b.job, E_CORRUPT, A.in[b.input].local, b.off);
+    __syncwarp();  // the key buffer is reused by the warp's next block
   }
 }
 
@@ -667,12 +1066,12 @@ void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInpu
 }
 
 void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st,
-                       uint64_t* ulen, uint64_t* ures, bool contents) {
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint2* ent_tab, cudaStream_t st,
+                       uint64_t* ulen, uint64_t* ures, bool contents, uint32_t* nch) {
   if (!n_blocks) return;
   const unsigned t = tuning().walk_threads;
-  k_block_walk<<<grid_for(n_blocks, t), t, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, cnt, hdr_tab, ulen,
-                                                    ures, contents);
+  k_block_walk<<<grid_for(n_blocks, t), t, 0, st>>>(blocks, n_blocks, in, nrec, kbytes, errs, cnt, ent_tab, ulen,
+                                                    ures, contents, nch);
   count_launches(1);
 }
 
@@ -859,20 +1258,27 @@ void launch_decompress(const BlockDesc* blocks, uint32_t n_blocks, const uint64_
 }
 
 void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, CrcTabs tabs, cudaStream_t st) {
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint2* ent_tab, CrcTabs tabs, cudaStream_t st,
+                       uint32_t* nch) {
   launch_block_verify(blocks, n_blocks, in, errs, errs, tabs, &cnt->crc_next_in, false, st);
   launch_block_verify(blocks, n_blocks, in, errs, errs, tabs, &cnt->crc_next_in, true, st);
-  launch_block_walk(blocks, n_blocks, in, nrec, kbytes, errs, cnt, hdr_tab, st);
+  launch_block_walk(blocks, n_blocks, in, nrec, kbytes, errs, cnt, ent_tab, st, nullptr, nullptr, false, nch);
 }
 
-void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,
-                   const uint16_t* hdr_tab, const uint32_t* rec_first, const uint64_t* key_first, Recs recs,
-                   uint8_t* arena, DErr* errs, cudaStream_t st) {
-  if (!n_blocks) return;
-  const unsigned w = tuning().decode_warps;
-  k_decode<<<grid_for(n_blocks, w), w * 32, 0, st>>>(blocks, n_blocks, in, nrec, hdr_tab, rec_first, key_first, recs,
-                                                  arena, errs);
+void launch_value_crc(Recs recs, const uint32_t* n, uint32_t n_max, CrcTabs tabs, cudaStream_t st) {
+  if (!n_max) return;
+  smem_optin(k_value_crc, kVerifySmem);
+  k_value_crc<<<kSms, kVerifyWarps * 32, kVerifySmem, st>>>(recs, n, n_max, tabs);
   count_launches(1);
+}
+
+void launch_unpack(const UnpArgs& a, CrcTabs tabs, cudaStream_t st) {
+  if (!a.n_blocks) return;
+  smem_optin(k_unpack, kUnpSmem);
+  k_unpack<<<kSms, kUnpWarps * 32, kUnpSmem, st>>>(a, tabs);
+  smem_optin(k_unpack_post, kPostSmem);
+  k_unpack_post<<<grid_for(a.n_blocks, kPostWarps, kSms * 8), kPostWarps * 32, kPostSmem, st>>>(a, tabs);
+  count_launches(2);
 }
 
 void launch_check_index(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,

@@ -22,6 +22,10 @@ struct DInput {
   uint32_t blk_first;   // first global data-block id, set by the host
 };
 
+// Unpack: chunks of kChunk bytes (crc.cuh) per data block with piece boundaries; the walk
+// records each block's chunk count when the block takes that path (kUnpChunkMax at most).
+constexpr uint32_t kUnpChunkMax = 240;
+
 struct BlockDesc {
   const uint8_t* ptr;   // block contents
   uint64_t size;        // contents size (trailer excluded)
@@ -153,6 +157,8 @@ struct EncDesc {
   uint64_t kptr;  // device address of the full internal key (key arena)
   uint64_t vptr;  // device address of the value (input table)
   uint32_t klen, vlen;
+  uint32_t vcrc;  // F(value) (the record's vcrc)
+  uint32_t pad;
 };
 
 // Per-output-table summary copied to the host at the end.
@@ -222,6 +228,7 @@ cudaError_t exclusive_scan(const In* in, Out* out, uint64_t cap, const uint32_t*
 
 // ---- crc_tables.cu ------------------------------------------------------------------------
 bool make_crc_tables(uint32_t* slice, uint32_t* shift);
+bool make_chunk_tables(uint32_t* out);
 
 // ---- decode.cu ---------------------------------------------------------------------------
 // Footers and index block checksums of n_inputs tables; msgs: n_inputs entries of scratch.
@@ -237,9 +244,13 @@ void launch_footers_finish(DInput* in, uint32_t n_inputs, DErr* errs, cudaStream
 void launch_index_entries(const DInput* in, uint32_t n_inputs, const uint32_t* in_blk_first, uint32_t n_blocks,
                           BlockDesc* blocks, DErr* errs, cudaStream_t st, const JobRange* ranges = nullptr,
                           const uint8_t* bounds = nullptr);
-constexpr uint32_t kHdrMax = 64;  // entry offsets recorded per block for the decoder
+// The block walk's entry table: for the first kHdrMax entries of a block (blocks below
+// 64 KiB), x = entry offset | value offset << 16, y = value end | shared << 16 | non-shared
+// << 24 (key lengths clamped to 255; keys over 128 bytes are rebuilt by the sequential walk).
+constexpr uint32_t kHdrMax = 64;
 void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, CrcTabs tabs, cudaStream_t st);
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint2* ent_tab, CrcTabs tabs, cudaStream_t st,
+                       uint32_t* nch = nullptr);
 // The two halves of launch_block_scan, for callers that run them on different streams:
 // checksum and type byte (errors into verr; blocks of jobs failed in errs or verr are
 // skipped), and the structure walk with entry counts.
@@ -248,9 +259,12 @@ void launch_block_scan(const BlockDesc* blocks, uint32_t n_blocks, const DInput*
 // left (148 - crc_ctas) and ends at once if no block is left.
 void launch_block_verify(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const DErr* errs, DErr* verr,
                          CrcTabs tabs, uint32_t* next, bool helper, cudaStream_t st);
+// With nch given, nch[g] = the block's chunk count when the unpack takes it with piece
+// boundaries (at most kHdrMax entries, below 64 KiB, at most kUnpChunkMax chunks), else 0.
 void launch_block_walk(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, uint32_t* nrec,
-                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint16_t* hdr_tab, cudaStream_t st,
-                       uint64_t* ulen = nullptr, uint64_t* ures = nullptr, bool contents = false);
+                       uint64_t* kbytes, DErr* errs, Counts* cnt, uint2* ent_tab, cudaStream_t st,
+                       uint64_t* ulen = nullptr, uint64_t* ures = nullptr, bool contents = false,
+                       uint32_t* nch = nullptr);
 // R4c: compressed data blocks (ulen[g] != kRawBlock) decompressed into dst + uoff[g], one
 // warp per block; cblocks[g] (a copy of blocks[g]) then points at the contents.
 constexpr uint64_t kRawBlock = ~0ull;
@@ -267,9 +281,36 @@ void launch_run_links(const DInput* in, uint32_t n_inputs, const BlockDesc* bloc
 // Blocks of failed jobs and blocks not read (null ptr) hold no records.
 void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,
                         uint64_t* kbytes, cudaStream_t st);
-void launch_decode(const BlockDesc* blocks, uint32_t n_blocks, const DInput* in, const uint32_t* nrec,
-                   const uint16_t* hdr_tab, const uint32_t* rec_first, const uint64_t* key_first, Recs recs,
-                   uint8_t* arena, DErr* errs, cudaStream_t st);
+// The unpack of every data block from one read of its bytes, in two kernels (one warp per
+// block in each): with `verify` the block checksum and type byte (errors into verr); for
+// every block with entries (nrec[g] > 0; with plan_nrec given, only when the entry and key
+// counts match the plan) the records, the rebuilt keys and each value's CRC register
+// (recs.vcrc). chunk_first: exclusive scan of the walk's chunk counts (n_blocks + 1);
+// chunkF: chunk_first[n_blocks] words; snap: 2 * (records + n_blocks) words.
+struct UnpArgs {
+  const BlockDesc* blocks;
+  uint32_t n_blocks;
+  const DInput* in;
+  const uint32_t* nrec;
+  const uint64_t* kbytes;
+  const uint32_t* plan_nrec;
+  const uint64_t* plan_kbytes;
+  const uint2* ent_tab;
+  const uint32_t* rec_first;
+  const uint64_t* key_first;
+  const uint32_t* chunk_first;
+  uint32_t* chunkF;
+  uint32_t* snap;
+  Recs recs;
+  uint8_t* arena;
+  DErr* errs;
+  DErr* verr;
+  bool verify;
+};
+void launch_unpack(const UnpArgs& a, CrcTabs tabs, cudaStream_t st);
+// recs.vcrc[r] = F(value of record r) for r < *n (or n_max when n is NULL), one warp per
+// record (decoded records and the build path's records).
+void launch_value_crc(Recs recs, const uint32_t* n, uint32_t n_max, CrcTabs tabs, cudaStream_t st);
 void launch_input_ranges(const DInput* in, uint32_t n_inputs, const uint32_t* rec_first,
                          const uint64_t* key_first, uint32_t* in_rec, uint64_t* in_key, cudaStream_t st);
 
@@ -349,6 +390,12 @@ void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const u
                    Recs recs,
                    const uint8_t* arena, Fmt fmt, uint32_t max_kv, uint8_t* out, uint64_t out_cap, uint8_t* done,
                    uint32_t* big, DErr* errs, CrcTabs tabs, cudaStream_t st);
+// Masked CRC trailers of the staged encoder's blocks (done[b] = 1), assembled from each
+// entry's header and key delta (read back from the block) and the survivors' value
+// registers (EncDesc.vcrc).
+void launch_block_trailer(const Counts* cnt, uint32_t cap, const BlkEnc* bd, const uint32_t* sd, const uint32_t* dr,
+                          const EncDesc* ed, Fmt fmt, uint8_t* out, const uint8_t* done, CrcTabs tabs,
+                          cudaStream_t st);
 // CRC trailers of the staged encoder's blocks (done[b] = 1).
 // Output block trailers; blocks taken from cnt->crc_next_out, helper launches as above.
 void launch_block_crc(Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,

@@ -43,7 +43,6 @@ struct NaScratch {
   BlockDesc blocks[kNaMaxBlocks];
   uint32_t nrec[kNaMaxBlocks];
   uint64_t kbytes[kNaMaxBlocks];
-  uint16_t hdr[uint64_t(kNaMaxBlocks) * kHdrMax];
 };
 
 static __device__ __align__(256) NaScratch g_na_scratch;
@@ -154,7 +153,7 @@ luda_status luda_check_table_noalloc(const uint8_t* table, uint64_t size, void* 
     const uint32_t first[2] = {0, nblk};
     NA_CK(cudaMemcpyAsync(S->blk_first, first, sizeof first, cudaMemcpyHostToDevice, st));
     launch_index_entries(&S->in, 1, S->blk_first, nblk, S->blocks, &S->err, st);
-    launch_block_scan(S->blocks, nblk, &S->in, S->nrec, S->kbytes, &S->err, &S->cnt, S->hdr, dev->tabs, st);
+    launch_block_scan(S->blocks, nblk, &S->in, S->nrec, S->kbytes, &S->err, &S->cnt, nullptr, dev->tabs, st);
     k_na_sum<<<grid_for(nblk, 256, kSms), 256, 0, st>>>(S->nrec, nblk, &S->entries);
     count_launches(1);
     NA_CK(cudaGetLastError());

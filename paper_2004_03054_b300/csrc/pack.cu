@@ -73,7 +73,7 @@ __global__ void k_sizes(const uint32_t* __restrict__ surv, const Counts* __restr
     lcp[s] = l;
     sd[s] = d;
     dr[s] = r - d;
-    ed[s] = EncDesc{reinterpret_cast<uint64_t>(arena + recs.koff[x]), recs.vptr[x], klen, vlen};
+    ed[s] = EncDesc{reinterpret_cast<uint64_t>(arena + recs.koff[x]), recs.vptr[x], klen, vlen, recs.vcrc[x], 0u};
     kv += klen + vlen;
   }
 #pragma unroll
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(kEncThreads) k_encode_big(const uint32_t* __re
 //     shifts (one warp per entry). The aligned middle of the image leaves in one bulk
 //     store (cp.async.bulk shared -> global); the ragged ends with byte stores.
 // Blocks with more than kStgMaxEnt entries or larger than the buffers go to k_encode_big.
-// The CRC trailer is written afterwards by k_block_crc.
+// The CRC trailer is assembled afterwards by k_block_trailer.
 constexpr uint32_t kStgConsumers = 8;
 constexpr uint32_t kStgThreads = 32 * (kStgConsumers + 1);
 constexpr uint32_t kStgCons = 32 * kStgConsumers;  // consumer threads
@@ -1117,6 +1117,80 @@ __global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(Counts* __restr
     const uint64_t contents = bsz[b];
     const uint32_t crc = warp_crc32c_u32(dst, contents + 1, tl, tz, tabs);
     if (lane == 0) st_u32(dst + contents + 1, crc_mask(crc));
+  }
+}
+
+// ---- data block trailers ----------------------------------------------------------------------
+// Masked CRC-32C trailer of every block the staged encoder wrote (done[b] = 1), assembled
+// from pieces (F linear, F(A || B) = Z_|B|(F(A)) xor F(B)): entry k contributes
+// Z_{n - end_k}(Z_{vlen_k}(h_k) xor F(value_k)), with h_k the register of the entry's
+// header and key delta read back from the block, restart word r (the offset of entry r * R)
+// Z_{n - end of the word}(F(word)), num_restarts and the type byte Z_1(F(num_restarts)), and
+// the register's initial value Z_n(0xFFFFFFFF), where n = contents + 1 is the message
+// length and end_k the end offset of entry k. One warp per block, one lane per entry; the
+// entry offsets come from a warp scan of the entry sizes. The shift matrices Z_{16 * 2^j}
+// and the slicing table sit in shared memory.
+constexpr uint32_t kTrlZ = 13;  // Z_{16 * 2^j} for j < 13: messages of at most 64 KiB
+constexpr uint32_t kTrlSmem = (1024 + kTrlZ * 1024) * 4;
+constexpr uint32_t kTrlThreads = 1024;
+
+__global__ void __launch_bounds__(kTrlThreads) k_block_trailer(const Counts* __restrict__ cnt,
+                                                               const BlkEnc* __restrict__ bd,
+                                                               const uint32_t* __restrict__ sd,
+                                                               const uint32_t* __restrict__ dr,
+                                                               const EncDesc* __restrict__ ed, Fmt fmt,
+                                                               uint8_t* __restrict__ out,
+                                                               const uint8_t* __restrict__ done, CrcTabs tabs) {
+  extern __shared__ uint32_t s_trl[];
+  for (uint32_t i = threadIdx.x; i < 1024 + kTrlZ * 1024; i += blockDim.x)
+    s_trl[i] = i < 1024 ? __ldg(tabs.slice + i) : __ldg(tabs.shift + (i - 1024));
+  __syncthreads();
+  const uint32_t* sT = s_trl;
+  const uint32_t* sZ = s_trl + 1024;
+  const uint32_t lane = lane_id(), R = fmt.R, nb = cnt->nb;
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t b = gtid() / 32; b < nb; b += warps) {
+    if (!done[b]) continue;
+    const BlkEnc D = bd[b];
+    if (D.job & 0x80000000u) continue;  // outside the output arena (never staged)
+    const uint32_t m = D.m, msg = D.contents + 1, nr = (m + R - 1) / R, rbase = D.contents - 4 - 4 * nr;
+    uint32_t acc = 0, carry = 0;
+    for (uint32_t k0 = 0; k0 < m; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      const bool restart = k % R == 0;
+      uint32_t esz = 0;
+      if (k < m) esz = sd[D.s0 + k] + (restart ? dr[D.s0 + k] : 0u);
+      uint32_t x = esz;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= uint32_t(d)) x += o;
+      }
+      if (k < m) {
+        const uint32_t eoff = carry + x - esz;
+        const EncDesc e = ed[D.s0 + k];
+        // header and key delta: bytes [a, z) of the output, aligned words (the bytes before
+        // a zeroed: leading zeros leave a zero register unchanged), then single bytes
+        const uint64_t a = D.dst + eoff, z = a + esz - e.vlen;
+        uint32_t h = 0;
+        uint64_t q = a & ~uint64_t(3);
+#pragma unroll 4
+        for (; q + 4 <= z; q += 4) {
+          uint32_t w = *reinterpret_cast<const uint32_t*>(out + q);
+          if (q < a) w &= ~0u << (8 * uint32_t(a - q));
+          h = crc_step4(h, w, sT);
+        }
+        for (q = q > a ? q : a; q < z; ++q) h = crc_byte(h, out[q], sT);
+        const uint32_t g = crc_zeros_s(h, e.vlen, sT, sZ) ^ e.vcrc;
+        acc ^= crc_zeros_s(g, msg - (eoff + esz), sT, sZ);
+        if (restart) acc ^= crc_zeros_s(crc_step4(0u, eoff, sT), msg - (rbase + 4 * (k / R) + 4), sT, sZ);
+      }
+      carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+    }
+    if (lane == 0) acc ^= crc_zeros_s(crc_step4(0u, nr, sT), 1, sT, sZ) ^ crc_zeros_s(0xFFFFFFFFu, msg, sT, sZ);
+#pragma unroll
+    for (int d = 16; d; d >>= 1) acc ^= __shfl_xor_sync(0xFFFFFFFFu, acc, d);
+    if (lane < 4) out[D.dst + D.contents + 1 + lane] = uint8_t(crc_mask(acc ^ 0xFFFFFFFFu) >> (8 * lane));
   }
 }
 
@@ -1594,12 +1668,21 @@ __global__ void k_build_records(const uint8_t* __restrict__ ukeys, const uint64_
                                 const uint64_t* __restrict__ seqs, const uint8_t* __restrict__ types,
                                 const uint8_t* __restrict__ vals, const uint64_t* __restrict__ voff, uint32_t n,
                                 Recs recs, uint8_t* __restrict__ arena, uint32_t* __restrict__ surv, DErr* err) {
+  const uint64_t uend = ukoff[n], vend = voff[n];
   for (uint64_t i = gtid(); i < n; i += gstride()) {
-    const uint64_t u0 = ukoff[i], ulen = ukoff[i + 1] - u0;
-    const uint64_t kpos = u0 + 8 * i;
+    uint64_t u0 = ukoff[i], ulen = ukoff[i + 1] - u0;
+    uint64_t v0 = voff[i], vlen = voff[i + 1] - v0;
     const uint64_t seq = seqs[i];
     const uint32_t ty = types[i];
     if (seq >= (1ull << 56) || ty > 1) report(err, E_INVALID, ~0u, i);
+    // offsets that are not ascending inside [0, total] fail the call; the record then
+    // stays inside the buffers (empty user key and value)
+    if (ukoff[i + 1] < u0 || ukoff[i + 1] > uend || voff[i + 1] < v0 || voff[i + 1] > vend ||
+        ulen > 0xFFFFFF00ull || vlen > 0xFFFFFFFFull) {
+      report(err, E_INVALID, ~0u, i);
+      u0 = ulen = v0 = vlen = 0;
+    }
+    const uint64_t kpos = u0 + 8 * i;
     const uint64_t tr = (seq << 8) | (ty & 0xFFu);
     uint8_t* kd = arena + kpos;
     for (uint64_t t = 0; t < ulen; ++t) kd[t] = ukeys[u0 + t];
@@ -1608,8 +1691,8 @@ __global__ void k_build_records(const uint8_t* __restrict__ ukeys, const uint64_
     recs.koff[i] = kpos;
     recs.klen[i] = uint32_t(ulen + 8);
     recs.tr[i] = tr;
-    recs.vptr[i] = reinterpret_cast<uint64_t>(vals + voff[i]);
-    recs.vlen[i] = uint32_t(voff[i + 1] - voff[i]);
+    recs.vptr[i] = reinterpret_cast<uint64_t>(vals + v0);
+    recs.vlen[i] = uint32_t(vlen);
     recs.src[i] = 0;
     surv[i] = uint32_t(i);
   }
@@ -1769,8 +1852,7 @@ void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const u
                    const FileDesc* files, const uint64_t* C, const uint64_t* bsz, const uint32_t* surv,
                    const uint32_t* lcp, const uint32_t* sd, const uint32_t* dr, const EncDesc* ed, BlkEnc* bd,
                    Recs recs, const uint8_t* arena, Fmt fmt, uint32_t max_kv, uint8_t* out, uint64_t out_cap,
-                   uint8_t* done,
-                   uint32_t* big, DErr* errs, CrcTabs tabs, cudaStream_t st) {
+                   uint8_t* done, uint32_t* big, DErr* errs, CrcTabs tabs, cudaStream_t st) {
   if (!cap) return;
   uint32_t S, I;
   stg_sizes(fmt.T, max_kv, &S, &I);
@@ -1792,6 +1874,15 @@ void launch_block_crc(Counts* cnt, uint32_t cap, const uint32_t* blk_file, const
   smem_optin(k_block_crc, kCrcSmem);
   k_block_crc<<<ctas, tuning().crc_warps * 32, kCrcSmem, st>>>(cnt, blk_file, files, C, bsz, out, out_cap, done,
                                                                 tabs);
+  count_launches(1);
+}
+
+void launch_block_trailer(const Counts* cnt, uint32_t cap, const BlkEnc* bd, const uint32_t* sd, const uint32_t* dr,
+                          const EncDesc* ed, Fmt fmt, uint8_t* out, const uint8_t* done, CrcTabs tabs,
+                          cudaStream_t st) {
+  if (!cap) return;
+  smem_optin(k_block_trailer, kTrlSmem);
+  k_block_trailer<<<kSms, kTrlThreads, kTrlSmem, st>>>(cnt, bd, sd, dr, ed, fmt, out, done, tabs);
   count_launches(1);
 }
 
