@@ -561,7 +561,7 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   if (b.cz.raw_cap)
     launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, false, side->s);
   else
-    launch_block_trailer(cnt, cap, b.bd, b.sd, b.dr, b.ed, fmt, out, b.enc_done, tabs, side->s);
+    launch_block_trailer(cnt, cap, b.bd, b.sd, b.dr, b.ed, recs.vcrc, fmt, out, b.enc_done, tabs, side->s);
   CK(cudaEventRecord(side->ev[3], side->s));
   if (!b.cz.raw_cap)
     launch_encode_big(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
@@ -1276,10 +1276,15 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   // one read of every data block: checksum (stored blocks; compressed ones were verified on
   // their stored bytes above), records, keys and value registers
   {
+    // records and keys here; the checksums (stored blocks; compressed ones were verified on
+    // their stored bytes above) and the value registers on the side stream, beside the
+    // merge, drop rule and cuts (joined with the data block trailers)
     UnpArgs ua{d_cb,          NB,    d_in,       d_nrec,   d_kbytes, nullptr, nullptr,
                d_hdr,         d_rec_first, d_key_first, d_chunk_first, d_chunkF, d_snap, recs,
-               d_arena,       d_errs, d_errs + n_jobs + 1, comp_blocks == 0};
-    launch_unpack(ua, tabs, st);
+               d_arena,       d_errs, d_errs + n_jobs + 1, comp_blocks == 0, &d_cnt->unp_next};
+    CK(fork_join(side, 0, st, side->s));
+    launch_unpack_crc(ua, tabs, tuning().crc_ctas, side->s);
+    launch_unpack_keys(ua, st);
   }
   tr.mark(5, st);
   launch_check_index(d_cb, NB, d_in, d_nrec, d_rec_first, recs, d_arena, d_errs, st);
@@ -1826,8 +1831,10 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
       // path without boundaries)
       UnpArgs ua{d_blocks,      NB,     d_in,       d_nrec,   d_kbytes, d_plan_nrec, d_plan_kbytes,
                  d_hdr,         d_rec_first, d_key_first, d_chunk_first, d_chunkF, d_snap, recs,
-                 d_arena,       d_errs, d_errs + n_jobs + 1, true};
-      launch_unpack(ua, tabs, st);
+                 d_arena,       d_errs, d_errs + n_jobs + 1, true, &d_cnt->unp_next};
+      CK(fork_join(side, 0, st, side->s));
+      launch_unpack_crc(ua, tabs, tuning().crc_ctas, side->s);
+      launch_unpack_keys(ua, st);
     }
     launch_plan_sanitize(recs, n_rec, d_jobs, n_jobs, d_errs, d_arena, st);
     launch_check_index(d_blocks, NB, d_in, d_nrec, d_rec_first, recs, d_arena, d_errs, st);

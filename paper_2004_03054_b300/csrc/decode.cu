@@ -429,29 +429,33 @@ __global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_value_crc(Recs recs, c
   }
 }
 
-// ---- unpack: checksum, value registers and decode from one read of each block ---------------
-// Two kernels, one warp per data block in each (§III-C "unpack": blocks are independent).
+// ---- unpack: records and keys; checksums and value registers from one read of each block ----
+// One warp per data block in every kernel (§III-C "unpack": blocks are independent).
 //
-// k_unpack (checksum pass). The block's message (contents and type byte, n bytes) is cut
-// into chunks of kChunk = 144 bytes that end at the 16-byte boundary after its end (bytes
-// outside the message read as zero); in round r lane l folds chunk U - 32 * (rounds - r) + l
-// with two independent registers (the chunk's first 64 bytes and its last 80, joined by
-// Z_80), and keeps Z_{32 * kChunk}-weighted sums of its chunks; a butterfly joins the lanes
+// k_keys (main stream). Lane per entry from the walk's entry table: the records' value and
+// key fields; the keys are rebuilt with lanes as byte positions (the shared prefix carried
+// in registers, the delta read from the block) into a per-warp buffer in shared memory and
+// the key arena. Blocks the table does not cover are decoded by one lane walking them.
+//
+// k_unpack (second stream, beside the merge, drop rule and cuts; a work counter hands out
+// blocks). The block's message (contents and type byte, n bytes) is cut into chunks of
+// kChunk = 144 bytes that end at the 16-byte boundary after its end (bytes outside the
+// message read as zero); in round r lane l folds chunk U - 32 * (rounds - r) + l with two
+// independent registers (the chunk's first 64 bytes and its last 80, joined by Z_80), and
+// keeps Z_{32 * kChunk}-weighted sums of its chunks; a butterfly joins the lanes
 // (Z_{kChunk * 2^k}). With the first four message bytes complemented (the register's
 // initial value), the result equals Z_pad of the complemented stored CRC when the block is
 // intact. For a block with at most kHdrMax entries the walk's entry table gives the pieces
 // of the message (each entry's header with key delta, its value, and the restart array
 // with num_restarts and the type byte), and the pass stores, per chunk, its register
 // (chunkF) and, per piece boundary, the register of its chunk's bytes before the
-// boundary's 16-byte word (snap). Other blocks are decoded here by the sequential walk,
-// each value's register computed by the whole warp.
+// boundary's 16-byte word (snap). For other blocks each value's register is computed by
+// the whole warp on its own.
 //
-// k_unpack_post (value registers and keys, blocks with boundaries). Lane per entry: the
+// k_vcrc (second stream, after k_unpack; blocks with boundaries). Lane per entry: the
 // prefix register at a boundary is its word's register advanced by the word's bytes before
 // it; F(value) = S(end) xor Z_len(S(start)) inside one chunk, the chunks in between joined
-// by Z_kChunk (Horner). The keys are rebuilt with lanes as byte positions (the shared
-// prefix carried in registers, the delta read from the block, which the checksum pass left
-// in L2) into a per-warp buffer in shared memory and the key arena.
+// by Z_kChunk (Horner). Only the trailers of the new data blocks read the value registers.
 constexpr uint32_t kUnpWarps = 16;
 constexpr uint32_t kUnpBndMax = 2 * kHdrMax + 2;  // piece boundaries: two per entry, the tail, the end
 constexpr uint8_t kNoBnd = 0xFF;
@@ -664,8 +668,11 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   UnpWarp* W = Wall + warp;
   const uint32_t tl = smem_addr(sTr) + lane * 4u;
-  const uint64_t warps = gstride() / 32;
-  for (uint64_t g = gtid() / 32; g < A.n_blocks; g += warps) {
+  for (;;) {
+    uint32_t gg = 0;
+    if (lane == 0) gg = atomicAdd(A.next, 1u);
+    const uint64_t g = __shfl_sync(0xFFFFFFFFu, gg, 0);
+    if (g >= A.n_blocks) break;
     const BlockDesc b = A.blocks[g];
     if (b.ptr == nullptr) continue;
     const uint32_t nent = unp_entries(A, g);
@@ -714,25 +721,50 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
       __syncwarp();  // the warp's shared arrays are reused by its next block
       continue;
     }
-    // a block without boundaries: the sequential walk, then each value's register
-    bool bad = false;
-    if (lane == 0) decode_walk(b, rec0, A.key_first[g], A.recs, A.arena, &bad);
-    bad = __any_sync(0xFFFFFFFFu, bad);
-    if (bad && lane == 0) report(A.errs + b.job, E_CORRUPT, A.in[b.input].local, b.off);
+    // a block without boundaries: each value's register on its own; the values from the
+    // entry table, or (blocks the table does not cover) from lane 0 walking the block
+    const bool tab = nent <= kHdrMax && b.size < 65536;
+    const uint64_t nr = ld_u32(b.ptr + b.size - 4);
+    const uint64_t rstart = b.size - 4 - 4 * nr;
+    const uint8_t *p = nullptr, *end = nullptr;  // lane 0's walk position
+    uint64_t seg = 0;
     for (uint32_t k = 0; k < nent; ++k) {
-      const uint32_t v = unp_range(reinterpret_cast<const uint8_t*>(A.recs.vptr[rec0 + k]), A.recs.vlen[rec0 + k], tl,
-                                   sC, tabs);
+      uint64_t vp = 0;
+      uint32_t vl = 0;
+      if (tab) {
+        const uint2 t = A.ent_tab[g * kHdrMax + k];
+        vp = reinterpret_cast<uint64_t>(b.ptr + (t.x >> 16));
+        vl = (t.y & 0xFFFFu) - (t.x >> 16);
+      } else if (lane == 0) {
+        // the walk validated the block: next entry, crossing into the next restart segment
+        while (p >= end) {
+          p = b.ptr + ld_u32(b.ptr + rstart + 4 * seg);
+          end = b.ptr + (seg + 1 < nr ? ld_u32(b.ptr + rstart + 4 * (seg + 1)) : rstart);
+          ++seg;
+        }
+        uint64_t shared, nonshared, vlen;
+        p += get_varint<32>(p, end, &shared);
+        p += get_varint<32>(p, end, &nonshared);
+        p += get_varint<32>(p, end, &vlen);
+        p += nonshared;
+        vp = reinterpret_cast<uint64_t>(p);
+        vl = uint32_t(vlen);
+        p += vlen;
+      }
+      vp = __shfl_sync(0xFFFFFFFFu, vp, 0);
+      vl = __shfl_sync(0xFFFFFFFFu, vl, 0);
+      const uint32_t v = unp_range(reinterpret_cast<const uint8_t*>(vp), vl, tl, sC, tabs);
       if (lane == 0) A.recs.vcrc[rec0 + k] = v;
     }
     __syncwarp();
   }
 }
 
-// ---- k_unpack_post ------------------------------------------------------------------------------
+// ---- k_vcrc and k_keys ----------------------------------------------------------------------------
 constexpr uint32_t kPostWarps = 8;
-constexpr uint32_t kPostKeyBuf = 1024;  // key bytes of a block rebuilt in shared memory
 constexpr uint32_t kPostZ = kCZ144 + 1;  // the chunk matrices kCZ16 .. kCZ144
-constexpr uint32_t kPostSmem = (1024 + kPostZ * 1024) * 4 + kPostWarps * kPostKeyBuf;
+constexpr uint32_t kPostSmem = (1024 + kPostZ * 1024) * 4;
+constexpr uint32_t kKeysWarps = 16;
 
 // Z_L(v) for L < 256 with the slicing table sT and the matrices sZ (Z_16 .. Z_128) in shared
 // memory: whole zero words, single zero bytes, then the matrices.
@@ -766,19 +798,7 @@ __device__ __forceinline__ uint32_t post_feed(uint32_t v, const UnpGeo& G, uintp
   return v;
 }
 
-// Eight bytes of shared memory at p (any alignment) as a little-endian word; big-endian when
-// `be`, with bytes at index >= avail as 0.
-__device__ __forceinline__ uint64_t smem_word(const uint8_t* p, uint32_t avail, bool be) {
-  uint64_t v = 0;
-#pragma unroll
-  for (uint32_t i = 0; i < 8; ++i) {
-    const uint64_t byte = i < avail ? p[i] : 0u;
-    v |= be ? byte << (56 - 8 * i) : byte << (8 * i);
-  }
-  return v;
-}
-
-__global__ void __launch_bounds__(kPostWarps * 32) k_unpack_post(const UnpArgs A, CrcTabs tabs) {
+__global__ void __launch_bounds__(kPostWarps * 32) k_vcrc(const UnpArgs A, CrcTabs tabs) {
   extern __shared__ __align__(16) uint32_t s_post[];
   uint32_t* sT = s_post;
   uint32_t* sZ = s_post + 1024;
@@ -786,8 +806,7 @@ __global__ void __launch_bounds__(kPostWarps * 32) k_unpack_post(const UnpArgs A
   for (uint32_t i = threadIdx.x; i < kPostZ * 1024; i += blockDim.x) sZ[i] = __ldg(tabs.chunk + i);
   __syncthreads();
   const uint32_t* sZ144 = sZ + kCZ144 * 1024u;
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  uint8_t* keys = reinterpret_cast<uint8_t*>(sZ + kPostZ * 1024) + warp * kPostKeyBuf;
+  const uint32_t lane = lane_id();
   const uint64_t warps = gstride() / 32;
   for (uint64_t g = gtid() / 32; g < A.n_blocks; g += warps) {
     const BlockDesc b = A.blocks[g];
@@ -795,94 +814,112 @@ __global__ void __launch_bounds__(kPostWarps * 32) k_unpack_post(const UnpArgs A
     const uint32_t nent = unp_entries(A, g);
     const UnpGeo G = unp_geo(b.ptr, uint32_t(b.size) + 1);
     if (!unp_fast(A, b, g, nent, G)) continue;
-    const uint64_t rec0 = A.rec_first[g], key0 = A.key_first[g];
+    const uint64_t rec0 = A.rec_first[g];
     const uint32_t* chF = A.chunkF + A.chunk_first[g];
     const uint32_t* snap = A.snap + 2 * (rec0 + g);
     const uintptr_t base0 = G.a1 - uintptr_t(kChunk) * uintptr_t(G.U);  // chunk 0's first byte
-    // lane per entry (entries lane and lane + 32): record fields and the value's register
-    uint32_t sh[2] = {0, 0}, kl[2] = {0, 0}, dp[2] = {0, 0};
-    bool long_key = false;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t k = lane + 32 * h;
-      if (k < nent) {
-        const uint2 t = A.ent_tab[g * kHdrMax + k];
-        const uint32_t vs = t.x >> 16, ve = t.y & 0xFFFFu, ns = t.y >> 24;
-        sh[h] = (t.y >> 16) & 0xFFu;
-        kl[h] = sh[h] + ns;
-        dp[h] = vs - ns;
-        long_key |= kl[h] > 32 * kDecSlots;
-        A.recs.vptr[rec0 + k] = reinterpret_cast<uint64_t>(b.ptr + vs);
-        A.recs.vlen[rec0 + k] = ve - vs;
-        A.recs.klen[rec0 + k] = kl[h];
-        A.recs.src[rec0 + k] = b.input;
-        uint32_t F = 0;
-        if (vs < ve) {
-          // prefix registers at the value's start (boundary 2k + 1) and end (boundary 2k + 2)
-          const uint32_t ao = uint32_t(int32_t(vs) - G.x0), zo = uint32_t(int32_t(ve) - G.x0);
-          const uint32_t ca = ao / kChunk, ra = ao - kChunk * ca;
-          const uint32_t cb = (zo - 1) / kChunk, rb = zo - kChunk * cb;
-          const uint32_t Pa = post_feed(snap[2 * k + 1], G, base0 + (ao & ~15u), ao & 15u, sT);
-          const uint32_t Pb = rb == kChunk ? chF[cb] : post_feed(snap[2 * k + 2], G, base0 + (zo & ~15u), zo & 15u, sT);
-          if (ca == cb) {
-            F = Pb ^ post_zeros(Pa, rb - ra, sT, sZ);
-          } else {
-            uint32_t x = chF[ca] ^ post_zeros(Pa, kChunk - ra, sT, sZ);
-            for (uint32_t c = ca + 1; c < cb; ++c) x = crc_mat(sZ144, x) ^ chF[c];
-            F = post_zeros(x, rb, sT, sZ) ^ Pb;
-          }
+    for (uint32_t k = lane; k < nent; k += 32) {
+      const uint2 t = A.ent_tab[g * kHdrMax + k];
+      const uint32_t vs = t.x >> 16, ve = t.y & 0xFFFFu;
+      uint32_t F = 0;
+      if (vs < ve) {
+        // prefix registers at the value's start (boundary 2k + 1) and end (boundary 2k + 2)
+        const uint32_t ao = uint32_t(int32_t(vs) - G.x0), zo = uint32_t(int32_t(ve) - G.x0);
+        const uint32_t ca = ao / kChunk, ra = ao - kChunk * ca;
+        const uint32_t cb = (zo - 1) / kChunk, rb = zo - kChunk * cb;
+        const uint32_t Pa = post_feed(snap[2 * k + 1], G, base0 + (ao & ~15u), ao & 15u, sT);
+        const uint32_t Pb = rb == kChunk ? chF[cb] : post_feed(snap[2 * k + 2], G, base0 + (zo & ~15u), zo & 15u, sT);
+        if (ca == cb) {
+          F = Pb ^ post_zeros(Pa, rb - ra, sT, sZ);
+        } else {
+          uint32_t x = chF[ca] ^ post_zeros(Pa, kChunk - ra, sT, sZ);
+          for (uint32_t c = ca + 1; c < cb; ++c) x = crc_mat(sZ144, x) ^ chF[c];
+          F = post_zeros(x, rb, sT, sZ) ^ Pb;
         }
-        A.recs.vcrc[rec0 + k] = F;
       }
+      A.recs.vcrc[rec0 + k] = F;
     }
-    long_key = __any_sync(0xFFFFFFFFu, long_key);
-    // keys
-    bool bad = false;
-    uint32_t x0 = kl[0], x1 = kl[1];
+  }
+}
+
+__global__ void __launch_bounds__(kKeysWarps * 32) k_keys(const UnpArgs A) {
+  const uint32_t lane = lane_id();
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t g = gtid() / 32; g < A.n_blocks; g += warps) {
+    const BlockDesc b = A.blocks[g];
+    if (b.ptr == nullptr) continue;
+    const uint32_t nent = unp_entries(A, g);
+    if (nent == 0) continue;
+    const uint64_t rec0 = A.rec_first[g], key0 = A.key_first[g];
+    bool tab = nent <= kHdrMax && b.size < 65536;
+    // lane per entry (entries lane and lane + 32): record fields
+    uint32_t sh[2] = {0, 0}, kl[2] = {0, 0}, dp[2] = {0, 0};
+    if (tab) {
+      bool long_key = false;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t o0 = __shfl_up_sync(0xFFFFFFFFu, x0, d), o1 = __shfl_up_sync(0xFFFFFFFFu, x1, d);
-      if (lane >= uint32_t(d)) {
-        x0 += o0;
-        x1 += o1;
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t k = lane + 32 * h;
+        if (k < nent) {
+          const uint2 t = A.ent_tab[g * kHdrMax + k];
+          const uint32_t vs = t.x >> 16, ve = t.y & 0xFFFFu, ns = t.y >> 24;
+          sh[h] = (t.y >> 16) & 0xFFu;
+          kl[h] = sh[h] + ns;
+          dp[h] = vs - ns;
+          long_key |= kl[h] > 32 * kDecSlots;
+          A.recs.vptr[rec0 + k] = reinterpret_cast<uint64_t>(b.ptr + vs);
+          A.recs.vlen[rec0 + k] = ve - vs;
+          A.recs.klen[rec0 + k] = kl[h];
+          A.recs.src[rec0 + k] = b.input;
+        }
       }
+      tab = !__any_sync(0xFFFFFFFFu, long_key);
     }
-    const uint32_t tot0 = __shfl_sync(0xFFFFFFFFu, x0, 31);
-    const uint32_t ko[2] = {x0 - kl[0], tot0 + x1 - kl[1]};  // key offsets (exclusive scan of lengths)
-    const uint32_t ktot = tot0 + __shfl_sync(0xFFFFFFFFu, x1, 31);
-    if (long_key || ktot > kPostKeyBuf) {
+    bool bad = false;
+    if (!tab) {
       if (lane == 0) decode_walk(b, rec0, key0, A.recs, A.arena, &bad);
     } else {
+      // key offsets: exclusive scan of key lengths over the (up to 64) entries
+      uint32_t x0 = kl[0], x1 = kl[1];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o0 = __shfl_up_sync(0xFFFFFFFFu, x0, d), o1 = __shfl_up_sync(0xFFFFFFFFu, x1, d);
+        if (lane >= uint32_t(d)) {
+          x0 += o0;
+          x1 += o1;
+        }
+      }
+      const uint32_t tot0 = __shfl_sync(0xFFFFFFFFu, x0, 31);
+      const uint32_t ko[2] = {x0 - kl[0], tot0 + x1 - kl[1]};
       // lane t keeps byte t (t + 32, ...) of the current key: the shared prefix carried from
-      // the previous key, the rest read from the key delta (four entries' reads in flight)
+      // the previous key, the rest read from the key delta
       uint8_t cur[kDecSlots] = {0, 0, 0, 0};
-#pragma unroll 4
       for (uint32_t k = 0; k < nent; ++k) {
         const uint32_t src = k & 31u, h = k >> 5;
         const uint32_t shared = __shfl_sync(0xFFFFFFFFu, h ? sh[1] : sh[0], src);
         const uint32_t klen = __shfl_sync(0xFFFFFFFFu, h ? kl[1] : kl[0], src);
         const uint32_t dpos = __shfl_sync(0xFFFFFFFFu, h ? dp[1] : dp[0], src);
         const uint32_t kof = __shfl_sync(0xFFFFFFFFu, h ? ko[1] : ko[0], src);
+        uint8_t* kd = A.arena + key0 + kof;
 #pragma unroll
         for (uint32_t s = 0; s < kDecSlots; ++s) {
           const uint32_t t = lane + 32 * s;
           if (t < klen) {
             if (t >= shared) cur[s] = __ldg(b.ptr + dpos + t - shared);
-            keys[kof + t] = cur[s];
-            A.arena[key0 + kof + t] = cur[s];
+            kd[t] = cur[s];
           }
         }
       }
-      __syncwarp();
+      __syncwarp();  // the warp's key bytes are visible to all its lanes
+      // per entry (lane): user-key prefix and trailer read back from the rebuilt key
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const uint32_t k = lane + 32 * h;
         if (k < nent) {
-          const uint8_t* kd = keys + ko[h];
+          const uint8_t* kd = A.arena + key0 + ko[h];
           const uint32_t ul = kl[h] - 8;
-          const uint64_t tr = smem_word(kd + ul, 8u, false);
+          const uint64_t tr = le_word(kd + ul);
           if ((tr & 0xFF) > 1) bad = true;
-          A.recs.pfx[rec0 + k] = smem_word(kd, ul < 8 ? ul : 8u, true);
+          A.recs.pfx[rec0 + k] = key_word(kd, ul < 8 ? ul : 8u);
           A.recs.tr[rec0 + k] = tr;
           A.recs.koff[rec0 + k] = key0 + ko[h];
         }
@@ -890,7 +927,6 @@ __global__ void __launch_bounds__(kPostWarps * 32) k_unpack_post(const UnpArgs A
     }
     bad = __any_sync(0xFFFFFFFFu, bad);
     if (bad && lane == 0) report(A.errs + b.job, E_CORRUPT, A.in[b.input].local, b.off);
-    __syncwarp();  // the key buffer is reused by the warp's next block
   }
 }
 
@@ -1272,12 +1308,18 @@ void launch_value_crc(Recs recs, const uint32_t* n, uint32_t n_max, CrcTabs tabs
   count_launches(1);
 }
 
-void launch_unpack(const UnpArgs& a, CrcTabs tabs, cudaStream_t st) {
+void launch_unpack_keys(const UnpArgs& a, cudaStream_t st) {
+  if (!a.n_blocks) return;
+  k_keys<<<grid_for(a.n_blocks, kKeysWarps), kKeysWarps * 32, 0, st>>>(a);
+  count_launches(1);
+}
+
+void launch_unpack_crc(const UnpArgs& a, CrcTabs tabs, uint32_t ctas, cudaStream_t st) {
   if (!a.n_blocks) return;
   smem_optin(k_unpack, kUnpSmem);
-  k_unpack<<<kSms, kUnpWarps * 32, kUnpSmem, st>>>(a, tabs);
-  smem_optin(k_unpack_post, kPostSmem);
-  k_unpack_post<<<grid_for(a.n_blocks, kPostWarps, kSms * 8), kPostWarps * 32, kPostSmem, st>>>(a, tabs);
+  k_unpack<<<ctas, kUnpWarps * 32, kUnpSmem, st>>>(a, tabs);
+  smem_optin(k_vcrc, kPostSmem);
+  k_vcrc<<<grid_for(a.n_blocks, kPostWarps, kSms * 8), kPostWarps * 32, kPostSmem, st>>>(a, tabs);
   count_launches(2);
 }
 

@@ -106,6 +106,7 @@ struct Counts {
   uint32_t max_kv;          // largest internal key + value length in the inputs (block walk)
   uint32_t crc_next_in;     // next input data block for the checksum kernels' warps
   uint32_t crc_next_out;    // next output data block for the trailer kernels' warps
+  uint32_t unp_next;        // next data block for the unpack's checksum pass
   uint32_t n_filt;          // filters of all tables' filter arrays (LUDA_F_FILTER_ARRAY)
   uint32_t comp_blocks;     // compressed input data blocks (R4c) seen by the block walk
   uint64_t comp_bytes;      // arena bytes their contents take once decompressed
@@ -157,7 +158,7 @@ struct EncDesc {
   uint64_t kptr;  // device address of the full internal key (key arena)
   uint64_t vptr;  // device address of the value (input table)
   uint32_t klen, vlen;
-  uint32_t vcrc;  // F(value) (the record's vcrc)
+  uint32_t rec;   // the survivor's record
   uint32_t pad;
 };
 
@@ -281,11 +282,10 @@ void launch_run_links(const DInput* in, uint32_t n_inputs, const BlockDesc* bloc
 // Blocks of failed jobs and blocks not read (null ptr) hold no records.
 void launch_zero_failed(const BlockDesc* blocks, uint32_t n_blocks, const DErr* errs, uint32_t* nrec,
                         uint64_t* kbytes, cudaStream_t st);
-// The unpack of every data block from one read of its bytes, in two kernels (one warp per
-// block in each): with `verify` the block checksum and type byte (errors into verr); for
-// every block with entries (nrec[g] > 0; with plan_nrec given, only when the entry and key
-// counts match the plan) the records, the rebuilt keys and each value's CRC register
-// (recs.vcrc). chunk_first: exclusive scan of the walk's chunk counts (n_blocks + 1);
+// The unpack of every data block: records and rebuilt keys, and from one read of the
+// block's bytes with `verify` the block checksum and type byte (errors into verr) and each
+// value's CRC register (recs.vcrc); only blocks with entries (nrec[g] > 0; with plan_nrec
+// given, only when the entry and key counts match the plan) have records. chunk_first: exclusive scan of the walk's chunk counts (n_blocks + 1);
 // chunkF: chunk_first[n_blocks] words; snap: 2 * (records + n_blocks) words.
 struct UnpArgs {
   const BlockDesc* blocks;
@@ -306,8 +306,12 @@ struct UnpArgs {
   DErr* errs;
   DErr* verr;
   bool verify;
+  uint32_t* next;  // block counter of the checksum pass (zero before it)
 };
-void launch_unpack(const UnpArgs& a, CrcTabs tabs, cudaStream_t st);
+// Records and keys (every field but vcrc).
+void launch_unpack_keys(const UnpArgs& a, cudaStream_t st);
+// Checksums (with `verify`) and the value registers (vcrc), on `ctas` CTAs of one SM each.
+void launch_unpack_crc(const UnpArgs& a, CrcTabs tabs, uint32_t ctas, cudaStream_t st);
 // recs.vcrc[r] = F(value of record r) for r < *n (or n_max when n is NULL), one warp per
 // record (decoded records and the build path's records).
 void launch_value_crc(Recs recs, const uint32_t* n, uint32_t n_max, CrcTabs tabs, cudaStream_t st);
@@ -392,10 +396,10 @@ void launch_encode(const uint32_t* blk_start, Counts* cnt, uint32_t cap, const u
                    uint32_t* big, DErr* errs, CrcTabs tabs, cudaStream_t st);
 // Masked CRC trailers of the staged encoder's blocks (done[b] = 1), assembled from each
 // entry's header and key delta (read back from the block) and the survivors' value
-// registers (EncDesc.vcrc).
+// registers (vcrc of the records).
 void launch_block_trailer(const Counts* cnt, uint32_t cap, const BlkEnc* bd, const uint32_t* sd, const uint32_t* dr,
-                          const EncDesc* ed, Fmt fmt, uint8_t* out, const uint8_t* done, CrcTabs tabs,
-                          cudaStream_t st);
+                          const EncDesc* ed, const uint32_t* vcrc, Fmt fmt, uint8_t* out, const uint8_t* done,
+                          CrcTabs tabs, cudaStream_t st);
 // CRC trailers of the staged encoder's blocks (done[b] = 1).
 // Output block trailers; blocks taken from cnt->crc_next_out, helper launches as above.
 void launch_block_crc(Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,

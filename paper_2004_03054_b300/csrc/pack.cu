@@ -73,7 +73,7 @@ __global__ void k_sizes(const uint32_t* __restrict__ surv, const Counts* __restr
     lcp[s] = l;
     sd[s] = d;
     dr[s] = r - d;
-    ed[s] = EncDesc{reinterpret_cast<uint64_t>(arena + recs.koff[x]), recs.vptr[x], klen, vlen, recs.vcrc[x], 0u};
+    ed[s] = EncDesc{reinterpret_cast<uint64_t>(arena + recs.koff[x]), recs.vptr[x], klen, vlen, x, 0u};
     kv += klen + vlen;
   }
 #pragma unroll
@@ -1138,7 +1138,8 @@ __global__ void __launch_bounds__(kTrlThreads) k_block_trailer(const Counts* __r
                                                                const BlkEnc* __restrict__ bd,
                                                                const uint32_t* __restrict__ sd,
                                                                const uint32_t* __restrict__ dr,
-                                                               const EncDesc* __restrict__ ed, Fmt fmt,
+                                                               const EncDesc* __restrict__ ed,
+                                                               const uint32_t* __restrict__ vcrc, Fmt fmt,
                                                                uint8_t* __restrict__ out,
                                                                const uint8_t* __restrict__ done, CrcTabs tabs) {
   extern __shared__ uint32_t s_trl[];
@@ -1181,7 +1182,7 @@ __global__ void __launch_bounds__(kTrlThreads) k_block_trailer(const Counts* __r
           h = crc_step4(h, w, sT);
         }
         for (q = q > a ? q : a; q < z; ++q) h = crc_byte(h, out[q], sT);
-        const uint32_t g = crc_zeros_s(h, e.vlen, sT, sZ) ^ e.vcrc;
+        const uint32_t g = crc_zeros_s(h, e.vlen, sT, sZ) ^ vcrc[e.rec];
         acc ^= crc_zeros_s(g, msg - (eoff + esz), sT, sZ);
         if (restart) acc ^= crc_zeros_s(crc_step4(0u, eoff, sT), msg - (rbase + 4 * (k / R) + 4), sT, sZ);
       }
@@ -1878,11 +1879,11 @@ void launch_block_crc(Counts* cnt, uint32_t cap, const uint32_t* blk_file, const
 }
 
 void launch_block_trailer(const Counts* cnt, uint32_t cap, const BlkEnc* bd, const uint32_t* sd, const uint32_t* dr,
-                          const EncDesc* ed, Fmt fmt, uint8_t* out, const uint8_t* done, CrcTabs tabs,
-                          cudaStream_t st) {
+                          const EncDesc* ed, const uint32_t* vcrc, Fmt fmt, uint8_t* out, const uint8_t* done,
+                          CrcTabs tabs, cudaStream_t st) {
   if (!cap) return;
   smem_optin(k_block_trailer, kTrlSmem);
-  k_block_trailer<<<kSms, kTrlThreads, kTrlSmem, st>>>(cnt, bd, sd, dr, ed, fmt, out, done, tabs);
+  k_block_trailer<<<kSms, kTrlThreads, kTrlSmem, st>>>(cnt, bd, sd, dr, ed, vcrc, fmt, out, done, tabs);
   count_launches(1);
 }
 

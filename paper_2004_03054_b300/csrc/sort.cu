@@ -266,7 +266,6 @@ __global__ void k_plan_sanitize(Recs recs, uint32_t n_rec, const JobDev* __restr
     recs.tr[p] = 0;
     recs.vptr[p] = reinterpret_cast<uint64_t>(arena);
     recs.vlen[p] = 0;
-    recs.vcrc[p] = 0;
     recs.src[p] = jobs[j].in_first;
   }
 }
