@@ -163,6 +163,11 @@ luda_status get_tabs(CrcTabs* out) {
   return LUDA_OK;
 }
 
+// SMs of the unpack's checksum pass on the side stream: the other half runs the records,
+// merge, drop rule and cuts beside it (74 of 148 measured best on the large job, against
+// 50, 100, 120 and 148).
+constexpr uint32_t kUnpCtas = kSms / 2;
+
 // ---- side stream --------------------------------------------------------------------------
 // Work that does not feed the main chain of a compaction runs on a second stream of the
 // calling thread: the checksums of the input data blocks (overlapping decode, merge, drop
@@ -171,8 +176,9 @@ luda_status get_tabs(CrcTabs* out) {
 struct Side {
   int dev = -1;
   cudaStream_t s = nullptr;
-  cudaEvent_t ev[5] = {};  // forks and joins: 0 input checksums, 1 their end, 2 trailers, 3 their end,
-                           // 4 index block checksums
+  cudaStream_t s2 = nullptr;  // a third stream: the tables' filter, index and footer beside the encoder
+  cudaEvent_t ev[7] = {};  // forks and joins: 0 input checksums, 1 their end, 2 trailers, 3 their end,
+                           // 4 index block checksums, 5 filter/index/footer fork, 6 their end
 };
 thread_local Side t_side;
 
@@ -186,10 +192,12 @@ luda_status get_side(Side** out) {
   if (sd.dev != dev) {
     if (sd.s) {
       cudaStreamDestroy(sd.s);
+      if (sd.s2) cudaStreamDestroy(sd.s2);
       for (cudaEvent_t& e : sd.ev) cudaEventDestroy(e);
     }
     sd = Side{};
-    if (cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sd.s2, cudaStreamNonBlocking) != cudaSuccess) {
       set_detail("cudaStreamCreateWithFlags failed");
       return LUDA_ERR_CUDA;
     }
@@ -547,6 +555,18 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   CK((exclusive_scan<uint64_t, uint64_t>(b.bmw, b.bmoff, cap, &cnt->nf, b.scan_tmp, st)));
   launch_file_offsets(b.files, cnt, cap, b.foff, b.bmoff, fa, jobs, n_jobs, out_cap, bm_cap, errs, st);
   launch_zero_bitmap(b.bitmap, cnt, bm_cap, st);
+  // filter, index block, metaindex, footer and table keys on the third stream, beside the
+  // encoder (they read the survivors and the layout, not the data blocks)
+  CK(fork_join(side, 5, st, side->s2));
+  launch_bloom(b.ed, cnt, cap, b.files, fmt, b.blk_start, b.C, fa, b.bitmap, out_cap, bm_cap, side->s2);
+  launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, fmt, out,
+                     out_cap, side->s2);
+  launch_file_finish(b.files, cnt, cap, b.bitmap, b.surv, recs, fmt, fa, out, out_cap, tabs, b.fmsg, b.meta,
+                     side->s2);
+  launch_key_lens(b.meta, cnt, cap, b.klens, side->s2);
+  CK((exclusive_scan<uint64_t, uint64_t>(b.klens, b.koff, cap, &cnt->nf, b.scan_tmp, side->s2)));
+  launch_key_gather(b.meta, cnt, cap, b.koff, b.files, b.surv, recs, arena, b.keybuf, side->s2);
+  CK(cudaEventRecord(side->ev[6], side->s2));
   trace_mark(tr, 7, st);
   if (b.cz.raw_cap) {
     launch_place(b.cz, cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, st);
@@ -566,13 +586,7 @@ luda_status run_pack(PackBufs& b, Counts* cnt, JobDev* jobs, uint32_t n_jobs, DE
   if (!b.cz.raw_cap)
     launch_encode_big(b.blk_start, cnt, cap, b.blk_file, b.files, b.C, b.bsz, b.surv, b.lcp, b.sd, b.dr, recs, arena,
                       fmt, out, out_cap, b.big, tabs, st);
-  launch_bloom(b.ed, cnt, cap, b.files, fmt, b.blk_start, b.C, fa, b.bitmap, out_cap, bm_cap, st);
-  launch_index_write(b.blk_start, cnt, cap, b.bsz, b.C, b.IX, b.blk_file, b.files, b.surv, recs, arena, fmt, out,
-                     out_cap, st);
-  launch_file_finish(b.files, cnt, cap, b.bitmap, b.surv, recs, fmt, fa, out, out_cap, tabs, b.fmsg, b.meta, st);
-  launch_key_lens(b.meta, cnt, cap, b.klens, st);
-  CK((exclusive_scan<uint64_t, uint64_t>(b.klens, b.koff, cap, &cnt->nf, b.scan_tmp, st)));
-  launch_key_gather(b.meta, cnt, cap, b.koff, b.files, b.surv, recs, arena, b.keybuf, st);
+  CK(cudaStreamWaitEvent(st, side->ev[6], 0));
   // the SMs the trailer kernel of compressed blocks left join it for the blocks still to do
   if (b.cz.raw_cap)
     launch_block_crc(cnt, cap, b.blk_file, b.files, b.C, b.bsz, out, out_cap, b.enc_done, tabs, true, st);
@@ -1283,7 +1297,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
                d_hdr,         d_rec_first, d_key_first, d_chunk_first, d_chunkF, d_snap, recs,
                d_arena,       d_errs, d_errs + n_jobs + 1, comp_blocks == 0, &d_cnt->unp_next};
     CK(fork_join(side, 0, st, side->s));
-    launch_unpack_crc(ua, tabs, tuning().crc_ctas, side->s);
+    launch_unpack_crc(ua, tabs, kUnpCtas, side->s);
     launch_unpack_keys(ua, st);
   }
   tr.mark(5, st);
@@ -1833,7 +1847,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
                  d_hdr,         d_rec_first, d_key_first, d_chunk_first, d_chunkF, d_snap, recs,
                  d_arena,       d_errs, d_errs + n_jobs + 1, true, &d_cnt->unp_next};
       CK(fork_join(side, 0, st, side->s));
-      launch_unpack_crc(ua, tabs, tuning().crc_ctas, side->s);
+      launch_unpack_crc(ua, tabs, kUnpCtas, side->s);
       launch_unpack_keys(ua, st);
     }
     launch_plan_sanitize(recs, n_rec, d_jobs, n_jobs, d_errs, d_arena, st);

@@ -1133,6 +1133,7 @@ __global__ void __launch_bounds__(kCrcWarps * 32, 1) k_block_crc(Counts* __restr
 constexpr uint32_t kTrlZ = 13;  // Z_{16 * 2^j} for j < 13: messages of at most 64 KiB
 constexpr uint32_t kTrlSmem = (1024 + kTrlZ * 1024) * 4;
 constexpr uint32_t kTrlThreads = 1024;
+constexpr uint32_t kTrlWords = 24;  // header and key-delta words loaded at once (keys up to about 80 bytes)
 
 __global__ void __launch_bounds__(kTrlThreads) k_block_trailer(const Counts* __restrict__ cnt,
                                                                const BlkEnc* __restrict__ bd,
@@ -1171,15 +1172,28 @@ __global__ void __launch_bounds__(kTrlThreads) k_block_trailer(const Counts* __r
         const uint32_t eoff = carry + x - esz;
         const EncDesc e = ed[D.s0 + k];
         // header and key delta: bytes [a, z) of the output, aligned words (the bytes before
-        // a zeroed: leading zeros leave a zero register unchanged), then single bytes
+        // a zeroed: leading zeros leave a zero register unchanged), then single bytes; the
+        // words of up to kTrlWords are all loaded before the register is advanced
         const uint64_t a = D.dst + eoff, z = a + esz - e.vlen;
         uint32_t h = 0;
         uint64_t q = a & ~uint64_t(3);
-#pragma unroll 4
-        for (; q + 4 <= z; q += 4) {
-          uint32_t w = *reinterpret_cast<const uint32_t*>(out + q);
-          if (q < a) w &= ~0u << (8 * uint32_t(a - q));
-          h = crc_step4(h, w, sT);
+        const uint32_t nw = uint32_t((z - q) >> 2);
+        if (nw <= kTrlWords) {
+          uint32_t wv[kTrlWords];
+#pragma unroll
+          for (uint32_t i = 0; i < kTrlWords; ++i)
+            wv[i] = i < nw ? *reinterpret_cast<const uint32_t*>(out + q + 4 * i) : 0u;
+          if (nw) wv[0] &= ~0u << (8 * uint32_t(a - q));
+#pragma unroll
+          for (uint32_t i = 0; i < kTrlWords; ++i)
+            if (i < nw) h = crc_step4(h, wv[i], sT);
+          q += 4ull * nw;
+        } else {
+          for (; q + 4 <= z; q += 4) {
+            uint32_t w = *reinterpret_cast<const uint32_t*>(out + q);
+            if (q < a) w &= ~0u << (8 * uint32_t(a - q));
+            h = crc_step4(h, w, sT);
+          }
         }
         for (q = q > a ? q : a; q < z; ++q) h = crc_byte(h, out[q], sT);
         const uint32_t g = crc_zeros_s(h, e.vlen, sT, sZ) ^ vcrc[e.rec];
