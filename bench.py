@@ -18,7 +18,7 @@ device-to-host copy of the new tables inside the timed region). Multi-GPU is rep
 only: each rank compacts its own copy of the job; nothing is exchanged.
 
 `--impl reference` times the CPU oracle (the plain single-threaded C compactor used by
-the tests) on a bounded sample of the same workload; it is the baseline arm.
+the tests, pinned to one host core) on the same workload; it is the baseline arm.
 """
 from __future__ import annotations
 
@@ -26,6 +26,7 @@ import argparse
 import ctypes as C
 import json
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -120,21 +121,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) of one k_encode_stg launch on the full-size large job, from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass), and the SHA-256 of
-# csrc/pack.cu at the time: once the encoder's source changes the number no longer
-# describes it and the bench reports null.
-_ENCODE_TRAFFIC = (2043730688, "2f7c1fd04934e011961f109a20e4f7899d09ae59ddf0f19d82b66fb5142ae1d6")
+# DRAM bytes (read + write) of all kernels of one compaction call on the large job, from an
+# ncu capture of one call (dram__bytes_read.sum + dram__bytes_write.sum per launch, summed;
+# the capture's job and its scale factor are in profiles/), with the SHA-256 of the CUDA
+# sources at the time: once a kernel's source changes the number no longer describes the
+# call and the bench reports null.
+_CALL_TRAFFIC = (None, "")
+
+
+def _sources_digest():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2004_03054_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(src, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
 
 
 def _recorded_traffic(scale):
-    import hashlib
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2004_03054_b300", "csrc", "pack.cu")
     try:
-        digest = hashlib.sha256(open(path, "rb").read()).hexdigest()
+        digest = _sources_digest()
     except OSError:
         return None
-    return _ENCODE_TRAFFIC[0] if digest == _ENCODE_TRAFFIC[1] and scale == 1.0 else None
+    return _CALL_TRAFFIC[0] if digest == _CALL_TRAFFIC[1] and scale == 1.0 else None
 
 
 # ---- our arm ------------------------------------------------------------------------------
@@ -148,6 +159,13 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("gloo")
     L = luda.lib()
+    # the clock sampler starts before the inputs are built, so that the GPU goes from the
+    # input build straight into the warm-up steps (an idle GPU takes a while to come back
+    # to full speed)
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else str(local))
+    sampler.start()
     job = W.config3(seed=3, scale=args.scale)
     # inputs: the library's own builder packs each run into one table, kept on the device
     inputs = []
@@ -180,11 +198,6 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    props = torch.cuda.get_device_properties(local)
-    uuid = getattr(props, "uuid", None)
-    sampler = ClockSampler(f"GPU-{uuid}" if uuid else str(local))
-    sampler.start()
-    time.sleep(0.3)
     l0 = luda.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.time()
@@ -203,26 +216,35 @@ def run_ours(args, ws, rank, local):
         torch.distributed.barrier()
     launches = luda.launch_count() - l0
     ms = e0.elapsed_time(e1) / args.steps
-    time.sleep(0.2)
-    sampler.stop()
-    clocks = sampler.summary(t0, t1)
     ms = _max_over_ranks([ms], ws)[0]
     value = ws * in_bytes / MiB / (ms / 1e3)
 
-    # dominant kernel: the encoder [5], the largest share of the job's kernel time and on the
-    # critical path; the input checksum kernel [1] runs on a second stream on part of the
-    # SMs beside the later stages, so its duration there is not its own speed (reported beside)
+    # roofline of the whole call: algorithmic bytes (every input table read once, every new
+    # table written once) over the time per call; the kernels that take more than a tenth of
+    # the call beside it, each with its own algorithmic bytes and its CUDA-event time (stage
+    # events on the stream it runs on)
     peak, peak_kind = _peaks()
     avg = [statistics.mean(s[i] for s in stages) for i in range(8)]
-    dom = 5
-    dom_bytes = sbytes[-1][dom]
-    achieved = dom_bytes / (avg[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_encode_stg", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
-                "bytes_per_launch": dom_bytes, "ms_per_launch": round(avg[dom], 4),
-                "traffic": args.traffic if args.traffic is not None else _recorded_traffic(args.scale)}
-    path_gbs = (in_bytes + out_bytes) / (ms / 1e3) / 1e9
-    stage_names = ["sizing", "block_scan", "decode", "sort", "gc_cut_layout", "encode", "meta", "device_span"]
+    path_bytes = in_bytes + out_bytes
+    path_gbs = path_bytes / (ms / 1e3) / 1e9
+    kernels = []
+    for name, idx, what in (("k_encode_stg", 5, "data blocks written + survivors' keys and values read"),
+                            ("k_unpack (checksum pass, second stream, 74 SMs)", 1, "input data blocks read"),
+                            ("k_keys", 2, "records and keys (latency-bound; key deltas and entry tables read)")):
+        if avg[idx] <= 0 or avg[idx] < 0.1 * ms:
+            continue
+        b = sbytes[-1][idx]
+        k = {"kernel": name, "ms_per_launch": round(avg[idx], 4), "share_of_call": round(avg[idx] / ms, 3)}
+        if b:
+            k.update({"bytes_per_launch": b, "algorithmic_bytes": what,
+                      "achieved": round(b / (avg[idx] / 1e3) / 1e9, 1), "frac": round(b / (avg[idx] / 1e3) / 1e9 / peak, 4)})
+        kernels.append(k)
+    roofline = {"bound": "hbm", "scope": "whole compaction call (all kernels; input + output table bytes)",
+                "achieved": round(path_gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(path_gbs / peak, 4),
+                "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_call": path_bytes, "ms_per_call": round(ms, 4),
+                "traffic": args.traffic if args.traffic is not None else _recorded_traffic(args.scale),
+                "kernels": kernels}
+    stage_names = ["sizing", "unpack_checksums", "keys", "sort", "gc_cut_layout", "encode", "meta", "device_span"]
 
     # end to end: luda_compact with pinned host inputs, new tables back in pinned host memory
     e2e = None
@@ -286,11 +308,15 @@ def run_ours(args, ws, rank, local):
         te = (time.perf_counter() - ts) / ke
         srv.close()
         te, te_single = _max_over_ranks([te, te_single], ws)
-        e2e = {"value": round(ws * in_bytes / MiB / te, 1), "unit": "MiB/s", "h2d_bytes_per_step": in_bytes,
-               "d2h_bytes_per_step": d2h, "ms_per_step": round(te * 1e3, 3), "steps": ke,
-               "api": f"luda_server_submit_host, {depth} slots, {depth} jobs in flight (copies in and out overlap)",
-               "single_call": {"value": round(ws * in_bytes / MiB / te_single, 1), "unit": "MiB/s",
-                               "ms_per_step": round(te_single * 1e3, 3), "api": "luda_compact"}}
+        e2e = {"value": round(ws * in_bytes / MiB / te_single, 1), "unit": "MiB/s", "h2d_bytes_per_step": in_bytes,
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(te_single * 1e3, 3), "steps": ke,
+               "api": "luda_compact (pinned host inputs in, new tables out to pinned host memory, one call at a time)",
+               "pipelined": {"value": round(ws * in_bytes / MiB / te, 1), "unit": "MiB/s",
+                             "ms_per_step": round(te * 1e3, 3), "steps": ke,
+                             "api": f"luda_server_submit_host, {depth} slots, {depth} jobs in flight "
+                                    "(one job's copies in and another's copies out overlap)"}}
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
 
     if rank != 0:
         return
@@ -305,8 +331,6 @@ def run_ours(args, ws, rank, local):
                    "entries_in": n_in, "entries_dropped": n_drop,
                    "l2": "inputs (1 GiB) larger than the 126 MB L2; no flush", "parallelism": f"replicas x{ws}"},
         "roofline": roofline,
-        "path": {"bytes_in_plus_out": in_bytes + out_bytes, "achieved_gbs": round(path_gbs, 1),
-                 "frac_of_peak": round(path_gbs / peak, 4)},
         "stage_ms": {n: round(v, 4) for n, v in zip(stage_names, avg)},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -571,23 +595,44 @@ def served(args):
 
 
 def cpu_baseline(args):
-    """The oracle as it stands, single-threaded, on the same job (one full run)."""
+    """The oracle as it stands on the same job: three runs in a child process pinned to one
+    host core (taskset -c 0, else sched_setaffinity), median of the three compaction times."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--cpu-scale", str(args.cpu_scale)]
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    if shutil.which("taskset"):
+        cmd = ["taskset", "-c", "0"] + cmd
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(f"cpu baseline failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _cpu_baseline_child(args):
     import oracle
     from paper_2004_03054_b300 import workloads as W
+    try:
+        os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    except (AttributeError, OSError):
+        pass
     scale = args.cpu_scale
     job = W.config3(seed=3, scale=scale)
     ins = [oracle.build_tables(r, job.block_size, job.restart_interval, job.bloom_bits_per_key,
                                (1 << 64) - 1).tables[0].data for r in job.inputs]
     nbytes = sum(len(x) for x in ins)
-    timing = {}
-    res = oracle.compact(ins, job.smallest_snapshot, job.bottommost, job.block_size, job.restart_interval,
-                         job.bloom_bits_per_key, job.target_file_size, timing=timing)
-    if res.status != 0:
-        raise RuntimeError("oracle failed")
-    sec = timing["seconds"]
-    return {"value": round(nbytes / MiB / sec, 2), "unit": "MiB/s", "cores": 1, "kind": "oracle",
-            "sample": f"cfg3 job at scale {scale} ({nbytes / MiB:.0f} MiB of input), one run, {sec:.2f} s",
-            "cpu": _cpu_model(), "host_cores": os.cpu_count()}
+    secs = []
+    for _ in range(3):
+        timing = {}
+        res = oracle.compact(ins, job.smallest_snapshot, job.bottommost, job.block_size, job.restart_interval,
+                             job.bloom_bits_per_key, job.target_file_size, timing=timing)
+        if res.status != 0:
+            raise RuntimeError("oracle failed")
+        secs.append(timing["seconds"])
+    sec = statistics.median(secs)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else 1
+    print(json.dumps({"value": round(nbytes / MiB / sec, 2), "unit": "MiB/s", "cores": cores, "kind": "oracle",
+                      "sample": f"cfg3 job at scale {scale} ({nbytes / MiB:.0f} MiB of input), median of 3 runs "
+                                f"({', '.join(f'{x:.2f}' for x in secs)} s) on one pinned core",
+                      "cpu": _cpu_model(), "host_cores": os.cpu_count()}), flush=True)
 
 
 def _oracle_job_seconds(job):
@@ -640,6 +685,10 @@ def run_reference(args, ws, rank):
         return
     import oracle
     from paper_2004_03054_b300 import workloads as W
+    try:  # one host core, like the cpu baseline
+        os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    except (AttributeError, OSError):
+        pass
     scale = args.ref_scale
     job = W.config3(seed=3, scale=scale)
     ins = [oracle.build_tables(r, job.block_size, job.restart_interval, job.bloom_bits_per_key,
@@ -664,7 +713,10 @@ def run_reference(args, ws, rank):
             "value": round(value, 2), "unit": "MiB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(sec * 1e3, 2), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u8", "data": "synthetic (seeded, shaped like the paper's workloads)",
-            "config": {"workload": "cfg3_large (bounded sample)", "scale": scale, "input_bytes": nbytes},
+            "config": {"workload": "cfg3_large: 4 L0 + 12 L1 tables of 64 MiB, 8-64 B keys (0-24 B shared prefixes), "
+                                   "1 KiB values, 10% overwrites, 3% deletes, 16 KiB blocks, R=16, bpk=10, 64 MiB files"
+                                   + ("" if scale == 1.0 else f" (bounded sample at scale {scale})"),
+                       "scale": scale, "input_bytes": nbytes},
             "cpu_baseline": {"value": round(value, 2), "unit": "MiB/s", "cores": 1, "kind": "oracle",
                              "sample": sample, "cpu": _cpu_model()},
             "e2e": {"value": round(value, 2), "unit": "MiB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -674,12 +726,12 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--cpu-scale", type=float, default=1.0)
-    ap.add_argument("--ref-scale", type=float, default=1 / 16)
+    ap.add_argument("--ref-scale", type=float, default=1.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -696,7 +748,11 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture (default: the "
                          "recorded capture while the encoder's source is unchanged)")
+    ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_baseline_child:
+        _cpu_baseline_child(args)
+        return
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -154,13 +154,16 @@ typedef struct {
   double ms_h2d, ms_device, ms_d2h;
   /* With LUDA_F_TRACE, CUDA-event times on the call's stream (ms) and algorithmic bytes:
    *  [0] sizing (footers, index, block scan, prefix sums; includes host round trips)
-   *  [1] input checksum kernel alone (CRC-32C of every input data block; it runs on a
-   *      second stream beside the later stages); bytes = input data blocks with trailers
-   *  [2] decode kernel alone      [3] order check + merge sort
+   *  [1] the unpack's checksum pass (CRC-32C of every input data block and the values'
+   *      CRC registers; it runs on a second stream beside stages 2-4); bytes = input data
+   *      blocks with trailers
+   *  [2] records and keys kernel alone      [3] order check + merge sort
    *  [4] drop rule, entry sizes, block and file cut, layout
    *  [5] encode kernel alone (block images without their CRC): bytes = output data
    *      blocks written + survivor keys and values read
-   *  [6] data block CRC trailers, bloom, index, metaindex, footer, boundary keys
+   *  [6] the rest after the encoder: data block CRC trailers (assembled from the pieces'
+   *      registers), joined with the filter, index, metaindex and footer kernels that ran
+   *      beside the encoder
    *  [7] whole device span */
   double stage_ms[LUDA_N_STAGES];
   uint64_t stage_bytes[LUDA_N_STAGES];

@@ -1174,10 +1174,8 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     // the stored blocks' checksums on the side stream (the unpack reads the contents),
     // joined before the results are collected
     CK(fork_join(side, 0, st, side->s));
-    tr.mark(11, side->s);
     launch_block_verify(d_blocks, NB, d_in, d_errs, d_errs + n_jobs + 1, tabs, &d_cnt->crc_next_in, false,
                         side->s);
-    tr.mark(12, side->s);
     CK(cudaEventRecord(side->ev[1], side->s));
     CK((exclusive_scan<uint64_t, uint64_t>(d_ures, d_uoff, NB, nullptr, d_tmpB, st)));
     CK(cudaMemcpyAsync(d_cblocks, d_blocks, sizeof(BlockDesc) * NB, cudaMemcpyDeviceToDevice, st));
@@ -1297,7 +1295,9 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
                d_hdr,         d_rec_first, d_key_first, d_chunk_first, d_chunkF, d_snap, recs,
                d_arena,       d_errs, d_errs + n_jobs + 1, comp_blocks == 0, &d_cnt->unp_next};
     CK(fork_join(side, 0, st, side->s));
+    tr.mark(11, side->s);
     launch_unpack_crc(ua, tabs, kUnpCtas, side->s);
+    tr.mark(12, side->s);
     launch_unpack_keys(ua, st);
   }
   tr.mark(5, st);
@@ -1365,8 +1365,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   if (ms_d2h) *ms_d2h = d2h;
   if (tr.on) {
     stage_ms[0] = tr.span(0, 3);
-    // stored blocks' checksums (compressed inputs only: side stream, beside the later stages)
-    stage_ms[1] = comp_blocks ? tr.span(11, 12) : 0.0;
+    stage_ms[1] = tr.span(11, 12);  // the unpack's checksum pass (side stream, beside the later stages)
     stage_ms[2] = tr.span(4, 5);
     stage_ms[3] = tr.span(5, 6);
     stage_ms[4] = tr.span(6, 7);
