@@ -69,6 +69,11 @@ typedef enum {
                                  (64-byte segments parsed one per lane), the file cut and layout use the
                                  stored sizes. Compressed INPUT blocks are read without any flag. Unknown
                                  flags are LUDA_ERR_INVALID_ARG */
+#define LUDA_F_TEST_WAIT0 32u /* test only: the staged encoder's bounded waits for its shared-memory copy slots
+                                 give up at once (limit 0 instead of one second), as a wait that runs out
+                                 would; the call then fails with LUDA_ERR_TIMEOUT and returns no tables. The
+                                 bulk copies already issued are still waited for (one second at most) before
+                                 each CTA exits, so the device stays usable */
 #define LUDA_F_TRACE 2u      /* record per-stage device times (luda_outputs.stage_ms); LUDA_TRACE=1 in the
                                 environment does the same for every call. Stage boundaries always open
                                 NVTX ranges "luda/<stage>" on the calling thread. */
@@ -218,6 +223,16 @@ typedef struct {
  * that stopped the whole batch. */
 LUDA_API luda_status luda_batch_compact_device(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts,
                                       luda_outputs* outs);
+/* The same with host buffers (§III-A: the host hands the GPU the tables of each selected
+ * job and takes the new tables back): jobs[j].inputs[].data are host pointers (pinned
+ * memory gives the fastest copies). Every job's inputs are copied into one device arena
+ * (one copy per input, on opts->stream; ms_h2d), all jobs run as one batch as above, and
+ * the new tables of all jobs come back in one copy into library-owned pinned host memory
+ * (ms_d2h): outs[j].tables[].data are host pointers. A corrupt job fails alone (its
+ * outs[j].status, no tables); an error that stops the whole batch is returned and set in
+ * every outs[j].status, with no tables anywhere. */
+LUDA_API luda_status luda_batch_compact(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts,
+                                        luda_outputs* outs);
 
 /* ---- subcompactions (format rule R13) --------------------------------------------------
  * One job split at the strictly increasing user keys bounds[0..n_bounds) into n_bounds + 1
@@ -355,13 +370,23 @@ LUDA_API luda_status luda_build_device(const luda_run* run, const luda_options* 
  * engines that reserve all device memory at start-up, and paths that cannot afford an
  * allocation's implicit synchronisation.
  *
- * luda_check_table_noalloc verifies one table on the device exactly as a compaction
- * reads it -- footer, index block, and every data block's CRC-32C, type byte and
- * structure -- and counts its entries. `table` is a device pointer to `size` bytes on
- * `stream` (a cudaStream_t, NULL = legacy default). It calls no cudaMalloc, cudaFree or
- * other allocating routine: its scratch is a static device array of about 2.7 MiB that
- * every GPU loading the library holds until the process exits, limited to tables of at
- * most LUDA_NOALLOC_MAX_BLOCKS data blocks (larger tables: LUDA_ERR_INVALID_ARG with a
+ * luda_check_table_noalloc runs the checks of a compaction's sizing pass on one table
+ * and counts its entries, without allocating. It checks: the footer (magic, block
+ * handles inside the file); the index block's CRC-32C, type byte and entry structure
+ * (varints, restart array, handles of the data blocks inside the file and in order); and
+ * every data block's CRC-32C, type byte and entry structure (varints, shared prefix no
+ * longer than the previous key, restart array, entry and key byte counts). It does NOT
+ * check what a compaction checks only after decoding the keys: the internal-key order
+ * within the table and the index-key rule (each index key at or after its block's last
+ * key and before the next block's first key). A table with valid checksums but two keys
+ * out of order passes this check and then fails a compaction with LUDA_ERR_CORRUPTION.
+ * `table` is a device pointer to `size` bytes on `stream` (a cudaStream_t, NULL = legacy
+ * default), in device or managed memory of the current device (cudaPointerGetAttributes;
+ * anything else, e.g. a host pointer, is LUDA_ERR_INVALID_ARG before any launch). It
+ * calls no cudaMalloc, cudaFree or other allocating routine: its scratch and CRC tables
+ * are static device arrays, at most LUDA_NOALLOC_STATIC_BYTES per GPU that loads the
+ * library, held until the process exits; the scratch limits it to tables of at most
+ * LUDA_NOALLOC_MAX_BLOCKS data blocks (larger tables: LUDA_ERR_INVALID_ARG with a
  * message naming the limit). The scratch is shared by all calls and keeps the last
  * call's contents; each call clears what it needs. Calls that overlap on the GPU race:
  * serialise them. The first call on a device (with that device current) looks up the
@@ -371,6 +396,7 @@ LUDA_API luda_status luda_build_device(const luda_run* run, const luda_options* 
  * compressed data block (type 1, R4c) is checked up to its checksum and then reported as
  * LUDA_ERR_NOT_SUPPORTED: its structure is behind a decompression, which needs memory. */
 #define LUDA_NOALLOC_MAX_BLOCKS 16384u
+#define LUDA_NOALLOC_STATIC_BYTES (1200u * 1024u) /* scratch (block descriptors and counts) + CRC tables */
 
 typedef struct {
   int32_t status;       /* luda_status */

@@ -20,6 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "luda_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_HDR = os.path.join(os.path.dirname(_HERE), "include", "luda_oracle.h")  # its C ABI (luda_oracle_compact)
 
 OK = 0
 ERR_INVALID_ARG = -1
@@ -36,9 +37,11 @@ MAX_SEQ = (1 << 56) - 1
 
 def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc (plain -O2, no vectorisation pragmas)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-I", os.path.dirname(_HDR),
+                               "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 

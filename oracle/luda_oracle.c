@@ -32,11 +32,15 @@
  * invariants of every produced table; the filter array against the independent reader's
  * own construction and a hand-worked layout.
  */
+#define _POSIX_C_SOURCE 199309L /* clock_gettime */
 #include <stdarg.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
+
+#include "luda_oracle.h"
 
 #define ORA_OK 0
 #define ORA_ERR_INVALID_ARG (-1)
@@ -1626,4 +1630,81 @@ int ora_bloom_may_contain(const uint8_t* filter, uint64_t len, const uint8_t* uk
     h += d;
   }
   return 1;
+}
+
+/* ------------------------------------------------------------------------------------
+ * luda_compact's C ABI (include/luda_oracle.h): the same arguments, served by
+ * ora_compact above. Only marshalling: the flags are checked, the inputs handed over,
+ * the result's tables moved into the caller's outputs.
+ * ------------------------------------------------------------------------------------ */
+int luda_oracle_compact(const luda_oracle_input* inputs, uint32_t n_inputs, int32_t level,
+                        uint64_t smallest_snapshot, const luda_oracle_options* opts, luda_oracle_outputs* out) {
+  (void)level;
+  if (!out) return ORA_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  const uint32_t known = ORA_F_STRICT_DUP | 2u /* trace: nothing to record */ | ORA_F_SHORT_INDEX |
+                         ORA_F_FILTER_ARRAY | ORA_F_COMPRESS;
+  if (!opts || (n_inputs && !inputs) || (opts->flags & ~known)) {
+    out->status = ORA_ERR_INVALID_ARG;
+    return ORA_ERR_INVALID_ARG;
+  }
+  const uint8_t** datas = (const uint8_t**)malloc(sizeof(uint8_t*) * (n_inputs ? n_inputs : 1));
+  uint64_t* sizes = (uint64_t*)malloc(sizeof(uint64_t) * (n_inputs ? n_inputs : 1));
+  if (!datas || !sizes) {
+    free(datas);
+    free(sizes);
+    out->status = ORA_ERR_OOM;
+    return ORA_ERR_OOM;
+  }
+  int rc = ORA_OK;
+  for (uint32_t i = 0; i < n_inputs; i++) {
+    datas[i] = inputs[i].data;
+    sizes[i] = inputs[i].size;
+    if (!datas[i] && sizes[i]) rc = ORA_ERR_INVALID_ARG;
+  }
+  ora_result* res = NULL;
+  struct timespec t0, t1;
+  clock_gettime(CLOCK_MONOTONIC, &t0);
+  if (rc == ORA_OK)
+    rc = ora_compact(datas, sizes, n_inputs, smallest_snapshot, opts->bottommost, opts->block_size,
+                     opts->restart_interval, opts->bloom_bits_per_key, opts->target_file_size,
+                     opts->flags & ~2u, &res);
+  clock_gettime(CLOCK_MONOTONIC, &t1);
+  free(datas);
+  free(sizes);
+  if (rc == ORA_OK) {
+    out->tables = (luda_oracle_table*)calloc(res->n_tables ? res->n_tables : 1, sizeof(luda_oracle_table));
+    if (!out->tables) {
+      ora_free_result(res);
+      rc = ORA_ERR_OOM;
+    }
+  }
+  if (rc != ORA_OK) {
+    out->status = rc;
+    return rc;
+  }
+  for (uint32_t i = 0; i < res->n_tables; i++) {
+    const ora_table* t = &res->tables[i];
+    luda_oracle_table* o = &out->tables[i];
+    o->data = t->data;
+    o->size = t->size;
+    o->n_entries = t->n_entries;
+    o->smallest = t->smallest;
+    o->smallest_len = t->smallest_len;
+    o->largest = t->largest;
+    o->largest_len = t->largest_len;
+  }
+  out->n_tables = res->n_tables;
+  out->n_in_entries = res->n_in_entries;
+  out->n_dropped = res->n_dropped;
+  out->ms_device = (double)(t1.tv_sec - t0.tv_sec) * 1e3 + (double)(t1.tv_nsec - t0.tv_nsec) * 1e-6;
+  out->_priv = res; /* owns the table bytes and keys */
+  return ORA_OK;
+}
+
+void luda_oracle_outputs_free(luda_oracle_outputs* out) {
+  if (!out) return;
+  ora_free_result((ora_result*)out->_priv);
+  free(out->tables);
+  memset(out, 0, sizeof *out);
 }

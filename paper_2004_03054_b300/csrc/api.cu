@@ -319,7 +319,8 @@ luda_status opts_check(const luda_options* o, Fmt* fmt) {
     return LUDA_ERR_INVALID_ARG;
   }
   if (!tuning_valid(o->tuning)) return LUDA_ERR_INVALID_ARG;
-  if (o->flags & ~(LUDA_F_STRICT_DUP | LUDA_F_TRACE | LUDA_F_SHORT_INDEX | LUDA_F_FILTER_ARRAY | LUDA_F_COMPRESS)) {
+  if (o->flags & ~(LUDA_F_STRICT_DUP | LUDA_F_TRACE | LUDA_F_SHORT_INDEX | LUDA_F_FILTER_ARRAY | LUDA_F_COMPRESS |
+                   LUDA_F_TEST_WAIT0)) {
     set_detail("unknown option flags 0x%x", o->flags);
     return LUDA_ERR_INVALID_ARG;
   }
@@ -2057,6 +2058,79 @@ luda_status luda_batch_compact_device(const luda_job* jobs, uint32_t n_jobs, con
   for (uint32_t j = 0; j < n_jobs; ++j) {
     if (rc) outs[j].status = rc;
     outs[j].ms_device = ms;
+  }
+  return rc;
+}
+
+luda_status luda_batch_compact(const luda_job* jobs, uint32_t n_jobs, const luda_options* opts, luda_outputs* outs) {
+  t_detail[0] = 0;
+  if ((!jobs && n_jobs) || !outs || !opts) {
+    set_detail("jobs, outs or opts is NULL");
+    return LUDA_ERR_INVALID_ARG;
+  }
+  for (uint32_t j = 0; j < n_jobs; ++j) memset(&outs[j], 0, sizeof(luda_outputs));
+  auto fail_all = [&](luda_status r) {  // an error that stops the batch, in every job's status
+    for (uint32_t j = 0; j < n_jobs; ++j) outs[j].status = r;
+    return r;
+  };
+  Fmt fmt;
+  luda_status rc = opts_check(opts, &fmt);
+  if (rc) return fail_all(rc);
+  if (n_jobs == 0) return LUDA_OK;
+  // one device arena for every job's inputs, each input at a 256-byte boundary
+  std::vector<uint32_t> first(n_jobs + 1, 0);
+  std::vector<uint64_t> off(1, 0);
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    if (jobs[j].n_inputs && !jobs[j].inputs) {
+      set_detail("job %u: inputs is NULL", j);
+      return fail_all(LUDA_ERR_INVALID_ARG);
+    }
+    first[j] = uint32_t(off.size() - 1);
+    for (uint32_t i = 0; i < jobs[j].n_inputs; ++i) {
+      const luda_input& in = jobs[j].inputs[i];
+      if (!in.data && in.size) {
+        set_detail("job %u input %u: data is NULL", j, i);
+        return fail_all(LUDA_ERR_INVALID_ARG);
+      }
+      off.push_back((off.back() + in.size + 255) & ~uint64_t(255));
+    }
+  }
+  first[n_jobs] = uint32_t(off.size() - 1);
+  const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+  const DevMem mem{opts, st};
+  CrcTabs tabs;
+  if ((rc = get_tabs(&tabs))) return fail_all(rc);
+  uint8_t* arena = static_cast<uint8_t*>(mem.get(off.back() + 256));
+  if (!arena) return fail_all(cuda_fail(cudaErrorMemoryAllocation, "device allocation"));
+  std::vector<luda_input> din(first[n_jobs] + 1);
+  std::vector<HostJob> hj(n_jobs);
+  Timer th;
+  th.start(st);
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    for (uint32_t i = 0; i < jobs[j].n_inputs; ++i) {
+      const uint32_t g = first[j] + i;
+      const luda_input& in = jobs[j].inputs[i];
+      din[g] = in;
+      din[g].data = arena + off[g];
+      if (in.size && cudaMemcpyAsync(arena + off[g], in.data, in.size, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        mem.put(arena);
+        return fail_all(cuda_fail(cudaGetLastError(), "copy of the inputs to the device"));
+      }
+    }
+    hj[j] = host_job(jobs[j]);
+    hj[j].inputs = din.data() + first[j];
+  }
+  th.stop(st);
+  double ms = 0, d2h = 0;
+  rc = run_compaction(hj.data(), n_jobs, opts, st, outs, true, &ms, &d2h);
+  const double h2d = th.ms();
+  mem.put(arena);
+  cudaStreamSynchronize(st);
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    if (rc) outs[j].status = rc;
+    outs[j].ms_h2d = h2d;
+    outs[j].ms_device = ms;
+    outs[j].ms_d2h = d2h;
   }
   return rc;
 }

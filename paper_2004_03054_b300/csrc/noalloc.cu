@@ -1,18 +1,24 @@
-// noalloc.cu -- luda_check_table_noalloc: verify one input table without allocating.
+// noalloc.cu -- luda_check_table_noalloc: check one input table without allocating.
 //
 // Some callers cannot allocate device memory at the point where they want to check a
 // table: code that runs inside a custom allocator or memory-pool callback (where a
 // nested cudaMalloc would re-enter the allocator), engines that reserve all device memory
 // at start-up and forbid later allocations, and latency-critical paths where an
 // allocation's implicit synchronisation is not acceptable. This entry point runs the
-// same footer, index and block-scan kernels as a compaction, but on scratch memory that
-// lives in this file as static device arrays, so it calls no allocator.
+// kernels of a compaction's sizing pass -- footer, index entries, data block checksums
+// and type bytes, and the block walk over every entry's varints, shared prefix and the
+// restart array -- on scratch memory that lives in this file as static device arrays, so
+// it calls no allocator. It stops there: the internal-key order and the index-key rule
+// are checked by a compaction only after it has decoded the keys into an arena, so a
+// table with valid checksums but keys out of order passes this check.
 //
-// Scratch: one NaScratch (about 2.7 MiB) per device that loads the library, held until
-// the process exits. Every call reuses it and it keeps the last call's contents: each
-// call clears what must start at zero (error word, counters) itself. Calls that overlap
-// on the GPU (two host threads, or two streams in flight) share the scratch and race;
-// callers must serialise them.
+// Scratch: one NaScratch per device that loads the library (sizeof(NaScratch), under
+// 1 MiB: LUDA_NOALLOC_MAX_BLOCKS block descriptors of 48 bytes and two per-block counts)
+// plus the CRC tables (196 KiB); LUDA_NOALLOC_STATIC_BYTES bounds the sum (checked at
+// compile time). It is held until the process exits. Every call reuses it and it keeps
+// the last call's contents: each call clears what must start at zero (error word,
+// counters) itself. Calls that overlap on the GPU (two host threads, or two streams in
+// flight) share the scratch and race; callers must serialise them.
 //
 // Set-up: the first call on a device (with that device current) fetches the device
 // addresses of the static arrays with cudaGetSymbolAddress and uploads the CRC tables
@@ -48,6 +54,8 @@ struct NaScratch {
 static __device__ __align__(256) NaScratch g_na_scratch;
 static __device__ __align__(256) uint32_t g_na_slice[1024];
 static __device__ __align__(256) uint32_t g_na_shift[kShiftTables * 1024];
+static_assert(sizeof(NaScratch) + sizeof(uint32_t) * (1024 + kShiftTables * 1024) <= LUDA_NOALLOC_STATIC_BYTES,
+              "static device memory of the no-alloc check above its documented bound");
 
 // Host copies used once to fill the device tables (static: no heap allocation).
 uint32_t h_slice[1024];
@@ -126,6 +134,22 @@ luda_status luda_check_table_noalloc(const uint8_t* table, uint64_t size, void* 
   if (!out) return na_fail(LUDA_ERR_INVALID_ARG, nullptr, "out is NULL");
   memset(out, 0, sizeof *out);
   if (!table && size) return na_fail(LUDA_ERR_INVALID_ARG, out, "table is NULL");
+  if (table) {
+    // device or managed memory of the current device only: a host pointer or another
+    // GPU's memory would be read by the kernels below (a fault, or reads across devices)
+    cudaPointerAttributes attr{};
+    int cur = -1;
+    NA_CK(cudaGetDevice(&cur));
+    if (cudaPointerGetAttributes(&attr, table) != cudaSuccess) {
+      cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+      return na_fail(LUDA_ERR_INVALID_ARG, out, "table is not a CUDA pointer");
+    }
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+      return na_fail(LUDA_ERR_INVALID_ARG, out, "table is not in device or managed memory (memory type %d)",
+                     int(attr.type));
+    if (attr.device != cur)
+      return na_fail(LUDA_ERR_INVALID_ARG, out, "table is on device %d, the current device is %d", attr.device, cur);
+  }
   NaDevice* dev = nullptr;
   luda_status rc = na_setup(&dev, out);
   if (rc) return rc;

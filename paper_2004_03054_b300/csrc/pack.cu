@@ -777,13 +777,16 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait for the phase with the given parity: false once a second has passed.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+// Bounded wait for the phase with the given parity: false once limit_ns have passed. A
+// zero limit gives up without looking at the barrier (the test-only LUDA_F_TEST_WAIT0).
+constexpr uint64_t kWaitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, uint64_t limit_ns = kWaitNs) {
+  if (limit_ns == 0) return false;
   if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
     if (mbar_try_wait(a, parity)) return true;
-    if (global_ns() - t0 > 1000000000ull) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
@@ -868,6 +871,8 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(Counts* __restrict__
   uint8_t* img = stage + 2 * size_t(S);                  // [I + 16]
   const uint32_t stage_a = smem_addr(stage), img_a = smem_addr(img);
   const uint32_t R = fmt.R;
+  // limit of the waits for a copy slot; the drain at the end always allows kWaitNs
+  const uint64_t slot_wait_ns = (fmt.flags & LUDA_F_TEST_WAIT0) ? 0 : kWaitNs;
   const uint32_t nb = cnt->nb;
   if (tid == 0) {
     mbar_init(full(0), 1);
@@ -903,7 +908,7 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(Counts* __restrict__
         pd = ed[D.s0 + lane];
         plcp = lcp[D.s0 + lane];
       }
-      if (j >= 2 && !mbar_wait(empty(sl), ((j >> 1) - 1) & 1u)) {
+      if (j >= 2 && !mbar_wait(empty(sl), ((j >> 1) - 1) & 1u, slot_wait_ns)) {
         if (lane == 0) report(errs + (D.job & 0x7FFFFFFFu), E_TIMEOUT, 0, b);
         break;
       }
@@ -1004,7 +1009,7 @@ __global__ void __launch_bounds__(kStgThreads) k_encode_stg(Counts* __restrict__
   uint32_t j = 0;
   for (uint32_t b = blockIdx.x; warp != 0 && b < nb; b += gridDim.x, ++j) {
     const uint32_t sl = j & 1u;
-    if (!consumers_all(mbar_wait(full(sl), (j >> 1) & 1u))) {
+    if (!consumers_all(mbar_wait(full(sl), (j >> 1) & 1u, slot_wait_ns))) {
       if (ct == 0) report(errs + (bd[b].job & 0x7FFFFFFFu), E_TIMEOUT, 0, b);
       break;
     }

@@ -28,6 +28,7 @@ F_TRACE = 2
 F_SHORT_INDEX = 4  # shortened index keys (format variant R9s)
 F_FILTER_ARRAY = 8  # one bloom filter per 2 KiB of data block offsets (format variant R10a)
 F_COMPRESS = 16  # data blocks written compressed when that saves an eighth (format variant R4c)
+F_TEST_WAIT0 = 32  # test only: the encoder's copy-slot waits give up at once (LUDA_ERR_TIMEOUT, no tables)
 MAX_SEQ = (1 << 56) - 1
 
 
@@ -139,6 +140,8 @@ def lib():
         L.luda_compact_device.argtypes = L.luda_compact.argtypes
         L.luda_batch_compact_device.restype = st
         L.luda_batch_compact_device.argtypes = [C.POINTER(Job), C.c_uint32, C.POINTER(Options), C.POINTER(Outputs)]
+        L.luda_batch_compact.restype = st
+        L.luda_batch_compact.argtypes = L.luda_batch_compact_device.argtypes
         L.luda_build.restype = st
         L.luda_build.argtypes = [C.POINTER(RunArrays), C.POINTER(Options), C.POINTER(Outputs)]
         L.luda_build_device.restype = st
@@ -326,6 +329,17 @@ def batch_compact_device(jobs, opts: Options | None = None, copy_out: bool = Tru
     return rc, [_take(rc, outs[j], device=True) for j in range(len(jobs))]
 
 
+def batch_compact(jobs, opts: Options | None = None):
+    """luda_batch_compact: jobs as for batch_compact_device, but each job's inputs are host
+    byte strings / uint8 arrays. Returns (rc, [Result]) with host tables."""
+    js, keep = _jobs_array(jobs)
+    o = opts or options()
+    outs = (Outputs * max(1, len(jobs)))()
+    rc = lib().luda_batch_compact(js, len(jobs), C.byref(o), outs)
+    del keep
+    return rc, [_take(rc, outs[j], device=False) for j in range(len(jobs))]
+
+
 def subcompact_device(inputs, bounds, smallest_snapshot: int = MAX_SEQ, level: int = 1,
                       opts: Options | None = None, copy_out: bool = True):
     """R13 subcompactions of one job (inputs: torch uint8 CUDA tensors) at the strictly
@@ -358,7 +372,12 @@ def _jobs_array(jobs):
         lo, hi = (job[3], job[4]) if len(job) > 3 else (None, None)
         ins = (Input * max(1, len(inputs)))()
         for i, t in enumerate(inputs):
-            ins[i].data, ins[i].size = t.data_ptr(), t.numel()
+            if hasattr(t, "data_ptr"):
+                ins[i].data, ins[i].size = t.data_ptr(), t.numel()
+            else:  # host bytes (luda_batch_compact)
+                a = _u8(t)
+                keep.append(a)
+                ins[i].data, ins[i].size = a.ctypes.data, len(a)
         keep.append(ins)
         js[j].inputs = C.cast(ins, C.POINTER(Input))
         js[j].n_inputs, js[j].smallest_snapshot, js[j].bottommost = len(inputs), snap, int(bool(bottom))
@@ -511,11 +530,18 @@ def _run_arrays(run, device: bool):
 
 
 def check_table_noalloc(table, stream=None) -> TableCheck:
-    """Verify one table (torch uint8 CUDA tensor) with the entry point that allocates no
-    device memory; returns the filled luda_table_check."""
+    """Check one table (torch uint8 CUDA tensor) with the entry point that allocates no
+    device memory; returns the filled luda_table_check. The call runs with the tensor's
+    device current (on that device's current stream unless `stream` is given)."""
+    import torch
+    if not isinstance(table, torch.Tensor) or not table.is_cuda:
+        raise TypeError("check_table_noalloc takes a CUDA tensor")
+    if table.dtype != torch.uint8 or not table.is_contiguous():
+        raise TypeError("check_table_noalloc takes a contiguous uint8 tensor")
     out = TableCheck()
-    lib().luda_check_table_noalloc(C.c_void_p(table.data_ptr()), table.numel(),
-                                   stream if stream is not None else current_stream(), C.byref(out))
+    with torch.cuda.device(table.device):
+        lib().luda_check_table_noalloc(C.c_void_p(table.data_ptr()), table.numel(),
+                                       stream if stream is not None else current_stream(), C.byref(out))
     return out
 
 

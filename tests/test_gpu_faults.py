@@ -92,3 +92,44 @@ def test_every_failing_allocation_is_clean_and_the_retry_matches(host):
     assert rc == 0 and out.n_tables == len(want)
     L.luda_outputs_free(C.byref(out))
     assert not again.live
+
+
+@pytest.mark.parametrize("host,flags", [(False, 0), (True, 0), (False, luda.F_COMPRESS)])
+def test_encoder_wait_that_runs_out_fails_cleanly_and_the_next_call_matches(host, flags):
+    """The staged encoder's bounded waits for its copy slots, made to run out at once by the
+    test-only flag: the call returns LUDA_ERR_TIMEOUT with no tables, the copies already in
+    flight are drained (the device stays usable), and the same call without the flag then
+    writes the oracle's bytes."""
+    job = W.config1(seed=62, scale=1 / 8)
+    ins = oracle_inputs(job)
+    want = [t.data for t in oracle_compact(job, ins, flags=flags).tables]
+    dev = [_dev(b) for b in ins]
+    L = luda.lib()
+
+    def run(extra):
+        arr = (luda.Input * len(ins))()
+        for i, (b, d) in enumerate(zip(ins, dev)):
+            if host:
+                arr[i].data, arr[i].size = C.cast(C.c_char_p(b), C.c_void_p).value, len(b)
+            else:
+                arr[i].data, arr[i].size = d.data_ptr(), d.numel()
+        out = luda.Outputs()
+        o = luda.job_options(job, flags=flags | extra)
+        fn = L.luda_compact if host else L.luda_compact_device
+        rc = fn(arr, len(ins), job.level, job.smallest_snapshot, C.byref(o), C.byref(out))
+        torch.cuda.synchronize()
+        return rc, out
+
+    for _ in range(2):
+        rc, out = run(luda.F_TEST_WAIT0)
+        assert rc == luda.ERR_TIMEOUT, luda.last_error_detail()
+        assert out.n_tables == 0
+        assert out.status == luda.ERR_TIMEOUT
+        L.luda_outputs_free(C.byref(out))
+    rc, out = run(0)
+    assert rc == 0, luda.last_error_detail()
+    got = [C.string_at(out.tables[i].data, out.tables[i].size) if host else
+           luda.device_bytes(out.tables[i].data, out.tables[i].size).cpu().numpy().tobytes()
+           for i in range(out.n_tables)]
+    L.luda_outputs_free(C.byref(out))
+    assert got == want

@@ -7,6 +7,13 @@
 * The 256-job batch (2.2 GB): one batch call and the autotuned plan replay (the bench's
   batched legs); every job's status and entry accounting checked, and a sample of jobs
   (every 16th, plus the largest) compared byte for byte with the oracle.
+* The single-job configurations at scale 1.0: the plain job (3 tables, 6 MiB) and the
+  LevelDB-default bottommost job (11 tables, 22 MiB), through luda_compact_device and
+  luda_compact, and three plain jobs as one luda_batch_compact call (host buffers).
+* A served run at the served workload's table size (64 MiB memtables and tables, 4 KiB
+  blocks): the write stream through the simulated LSM tree and luda_server with several
+  jobs in flight; a sample of its compaction jobs (every other job of each level, from
+  the first) re-run by the oracle on the same input bytes, byte for byte.
 """
 import numpy as np
 import pytest
@@ -65,3 +72,59 @@ def test_batch_full_size_sampled():
     torch.cuda.synchronize()
     check(plan.outputs())
     plan.close()
+
+
+@pytest.mark.parametrize("cfg,seed", [("config1", 1), ("config2", 2)])
+def test_single_job_configs_full_size(cfg, seed):
+    job = getattr(W, cfg)(seed=seed, scale=1.0)
+    ins = oracle_inputs(job)
+    want = oracle_compact(job, ins)
+    assert want.status == 0
+    assert job.bottommost == (cfg == "config2")
+    got = luda.compact_device([dev(x) for x in ins], job.smallest_snapshot, level=job.level,
+                              opts=luda.job_options(job))
+    got.tables = [t.cpu().numpy().tobytes() for t in got.tables]
+    assert_same(got, want)
+    host = luda.compact(ins, job.smallest_snapshot, level=job.level, opts=luda.job_options(job))
+    assert_same(host, want)
+    assert host.ms_h2d > 0 and host.ms_d2h > 0
+    assert sum(len(x) for x in ins) > (5 << 20 if cfg == "config1" else 20 << 20)
+
+
+def test_batch_compact_host_full_size():
+    jobs = [W.config1(seed=s, scale=1.0) for s in (1, 11, 12)]
+    ins = [oracle_inputs(j) for j in jobs]
+    rc, outs = luda.batch_compact([(x, j.smallest_snapshot, j.bottommost) for j, x in zip(jobs, ins)],
+                                  luda.job_options(jobs[0]))
+    assert rc == 0
+    for j, g in enumerate(outs):
+        assert_same(g, oracle_compact(jobs[j], ins[j]))
+        assert g.ms_h2d > 0 and g.ms_d2h > 0
+
+
+def test_served_jobs_full_table_size_sampled():
+    from paper_2004_03054_b300 import lsm
+
+    kept = []
+    per_level = {}
+
+    def on_complete(rec, out):
+        n = per_level.get(rec.level, 0)
+        per_level[rec.level] = n + 1
+        if n % 2 or len(kept) >= 4:
+            return
+        ins = [luda.device_bytes(t.ptr, t.size).cpu().numpy().tobytes() for t in rec.inputs]
+        outs = [luda.device_bytes(out.tables[i].data, out.tables[i].size).cpu().numpy().tobytes()
+                for i in range(out.n_tables)]
+        kept.append((rec.level, rec.bottommost, ins, outs, int(out.n_in_entries), int(out.n_dropped)))
+
+    stream = W.config5_stream(seed=5, n_memtables=12, write_rate=8e6)
+    rep = lsm.serve(stream, n_slots=4, hbm_budget=40 * 10**9, pace=False, on_complete=on_complete)
+    assert rep.failed == 0 and rep.jobs >= 3
+    assert len(kept) >= 2 and {k[0] for k in kept} >= {0}
+    for level, bottom, ins, outs, n_in, n_drop in kept:
+        want = oracle.compact(ins, W.MAX_SEQ, bottom, 4096, 16, 10, 64 << 20)
+        assert want.status == 0
+        assert outs == [t.data for t in want.tables], level
+        assert (n_in, n_drop) == (want.n_in_entries, want.n_dropped)
+        assert sum(len(x) for x in ins) >= 4 * (50 << 20) or level > 0

@@ -67,6 +67,8 @@ def test_server_mix_equals_alone_and_oracle(n_slots, budget, prewarm):
     srv.close()
     assert ss.submitted == ss.completed == len(jobs) and ss.failed == 0
     assert 1 <= ss.running_peak <= n_slots
+    if n_slots > 1 and budget >= 1 << 40:
+        assert ss.running_peak > 1  # jobs did run on the device together
     if budget >= 1 << 40:
         assert ss.budget_peak <= budget
     else:

@@ -21,6 +21,7 @@ def exe(tmp_path_factory):
         pytest.skip("no gcc")
     path = str(tmp_path_factory.mktemp("asan") / "oracle_asan")
     r = subprocess.run(["gcc", "-std=c11", "-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+                        "-I", os.path.join(os.path.dirname(HERE), "include"),
                         "-fno-sanitize-recover=undefined", "-o", path, os.path.join(HERE, "oracle_sanitize_main.c")],
                        capture_output=True, text=True)
     if r.returncode != 0 and "sanitize" in r.stderr:
