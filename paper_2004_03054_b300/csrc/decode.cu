@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(256) k_block_walk(const BlockDesc* __restrict_
 // block with longer keys (or too many entries for the walk's table) is decoded by one lane
 // walking its restart segments in order (decode_walk).
 constexpr uint32_t kDecSlots = 4;  // key bytes per lane: 128-byte keys
+constexpr uint32_t kKeyBatch = 4;  // entries whose key bytes k_keys loads at once
 
 __device__ void decode_walk(const BlockDesc& b, uint64_t rec, uint64_t kpos, const Recs& recs, uint8_t* arena, bool* bad) {
   const uint64_t nr = ld_u32(b.ptr + b.size - 4);
@@ -458,10 +459,11 @@ __global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_value_crc(Recs recs, c
 // by Z_kChunk (Horner). Only the trailers of the new data blocks read the value registers.
 constexpr uint32_t kUnpWarps = 16;
 constexpr uint32_t kUnpBndMax = 2 * kHdrMax + 2;  // piece boundaries: two per entry, the tail, the end
-constexpr uint8_t kNoBnd = 0xFF;
+constexpr uint32_t kSkStride = 11;                // words of a lane's slot (odd: lanes hit distinct banks)
 struct UnpWarp {
-  uint32_t bnd[kUnpBndMax];      // piece boundaries (message offsets, ascending)
-  uint8_t bfirst[kUnpChunkMax];  // first boundary inside each chunk (kNoBnd: none)
+  uint32_t bnd[kUnpBndMax];     // piece boundaries (message offsets, ascending)
+  uint32_t sk[32 * kSkStride];  // per lane of a round: its chunk's registers before each 16-byte word, then
+                                // the first chain's register
 };
 constexpr uint32_t kUnpSmem = kRepWords * 4 + kChunkTables * 4096 + kUnpWarps * uint32_t(sizeof(UnpWarp));
 static_assert(kUnpSmem <= 227u * 1024u, "unpack shared memory");
@@ -549,15 +551,18 @@ __device__ __forceinline__ uint32_t crc_quad_rep(uint32_t S, const uint4 v, uint
 }
 
 // Folds every chunk of the message: returns this lane's Z_{32 * kChunk}-weighted sum of its
-// chunks' registers. With nb > 0 boundaries (W->bnd, W->bfirst set), each chunk's register
-// goes to chF[c] and, for each boundary inside the chunk, the register of the chunk's bytes
-// before the boundary's 16-byte word to snap[i]. With `init`, the sum is that of the message
-// with its first four bytes complemented (the standard register's initial value
-// 0xFFFFFFFF). The next round's chunks are prefetched into L2 while a round is folded.
-__device__ __forceinline__ uint32_t unp_fold(const UnpGeo G, const UnpWarp* W, uint32_t nb, uint32_t* chF,
+// chunks' registers. With nb > 0 boundaries (W->bnd set), each chunk's register goes to
+// chF[c] and, for each boundary inside the chunk, the register of the chunk's bytes before
+// the boundary's 16-byte word to snap[i]: after each round the lanes leave their chunks'
+// word registers in W->sk and then take the round's boundaries one per lane. With `init`,
+// the sum is that of the message with its first four bytes complemented (the standard
+// register's initial value 0xFFFFFFFF). The next round's chunks are prefetched into L2
+// while a round is folded.
+__device__ __forceinline__ uint32_t unp_fold(const UnpGeo G, UnpWarp* W, uint32_t nb, uint32_t* chF,
                                              uint32_t* snap, uint32_t tl, const uint32_t* sC, bool init) {
   const uint32_t lane = lane_id();
-  uint32_t acc = 0;
+  uint32_t acc = 0, bnext = 0;  // bnext: the first boundary of the round (warp-uniform)
+  uint32_t* slot = W ? W->sk + lane * kSkStride : nullptr;
   for (uint32_t r = 0; r < G.rounds; ++r) {
     const int32_t c = int32_t(G.U) - int32_t(32 * (G.rounds - r)) + int32_t(lane);
     if (lane == 0 && r + 1 < G.rounds) {
@@ -582,17 +587,9 @@ __device__ __forceinline__ uint32_t unp_fold(const UnpGeo G, const UnpWarp* W, u
       const int32_t xc = G.x0 + int32_t(kChunk) * c;  // message offset of the chunk
       if (nb) {
         chF[c] = S;
-        for (uint32_t bi = W->bfirst[c]; bi < nb; ++bi) {
-          const int32_t rr = int32_t(W->bnd[bi]) - xc;
-          if (rr >= int32_t(kChunk)) break;
-          const uint32_t k = uint32_t(rr) >> 4;
-          uint32_t sv = Sk[0];
 #pragma unroll
-          for (uint32_t j = 1; j < uint32_t(kChunkW); ++j) sv = k == j ? Sk[j] : sv;
-          // a word of the second chain: its register follows the first chain's bytes
-          if (k >= 4) sv ^= unp_zeros(SA, 16u * (k - 4), tl, sC);
-          snap[bi] = sv;
-        }
+        for (int j = 0; j < kChunkW; ++j) slot[j] = Sk[j];
+        slot[kChunkW] = SA;
       }
       if (init && xc < 4) {
         // bytes 0..3 of the message complemented: F(0xFFFFFFFF) shifted to the end of the
@@ -609,6 +606,35 @@ __device__ __forceinline__ uint32_t unp_fold(const UnpGeo G, const UnpWarp* W, u
         }
       }
       acc = crc_mat(sC + kCZ4608 * 1024u, acc) ^ S;  // the other lanes' chunks of the round
+    }
+    if (nb) {
+      // the boundaries inside this round's chunks (cr0 .. cr0 + 31), one per lane; they
+      // ascend, so the lanes that find one form a prefix. A boundary at the message's
+      // padded end (chunk U) lies in no chunk and is never taken.
+      __syncwarp();
+      const int32_t cr0 = int32_t(G.U) - int32_t(32 * (G.rounds - r));
+      for (;;) {
+        const uint32_t bi = bnext + lane;
+        int32_t o = 0, cb = 0;
+        bool mine = false;
+        if (bi < nb) {
+          o = int32_t(W->bnd[bi]) - G.x0;  // offset from chunk 0's first byte
+          cb = o / int32_t(kChunk);
+          mine = cb < cr0 + 32;
+        }
+        const uint32_t took = __popc(__ballot_sync(0xFFFFFFFFu, mine));
+        if (mine) {
+          const uint32_t* sl = W->sk + uint32_t(cb - cr0) * kSkStride;
+          const uint32_t k = uint32_t(o - int32_t(kChunk) * cb) >> 4;
+          uint32_t sv = sl[k];
+          // a word of the second chain: its register follows the first chain's bytes
+          if (k >= 4) sv ^= unp_zeros(sl[kChunkW], 16u * (k - 4), tl, sC);
+          snap[bi] = sv;
+        }
+        bnext += took;
+        if (took < 32) break;
+      }
+      __syncwarp();
     }
   }
   return acc;
@@ -683,7 +709,7 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
     const bool fast = unp_fast(A, b, g, nent, G);
     const uint32_t nb = fast ? 2 * nent + 2 : 0;
     if (fast) {
-      // piece boundaries from the walk's entry table, then the first boundary of every chunk
+      // piece boundaries from the walk's entry table
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const uint32_t k = lane + 32 * h;
@@ -696,12 +722,6 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
             W->bnd[2 * nent + 1] = n;
           }
         }
-      }
-      for (uint32_t c = lane; c < G.U; c += 32) W->bfirst[c] = kNoBnd;
-      __syncwarp();
-      for (uint32_t i = lane; i < nb; i += 32) {
-        const uint32_t c = uint32_t(int32_t(W->bnd[i]) - G.x0) / kChunk;
-        if (c < G.U && (i == 0 || uint32_t(int32_t(W->bnd[i - 1]) - G.x0) / kChunk != c)) W->bfirst[c] = uint8_t(i);
       }
       __syncwarp();
     }
@@ -764,7 +784,7 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
 constexpr uint32_t kPostWarps = 8;
 constexpr uint32_t kPostZ = kCZ144 + 1;  // the chunk matrices kCZ16 .. kCZ144
 constexpr uint32_t kPostSmem = (1024 + kPostZ * 1024) * 4;
-constexpr uint32_t kKeysWarps = 16;
+constexpr uint32_t kKeysWarps = 4;
 
 // Z_L(v) for L < 256 with the slicing table sT and the matrices sZ (Z_16 .. Z_128) in shared
 // memory: whole zero words, single zero bytes, then the matrices.
@@ -891,21 +911,43 @@ __global__ void __launch_bounds__(kKeysWarps * 32) k_keys(const UnpArgs A) {
       const uint32_t tot0 = __shfl_sync(0xFFFFFFFFu, x0, 31);
       const uint32_t ko[2] = {x0 - kl[0], tot0 + x1 - kl[1]};
       // lane t keeps byte t (t + 32, ...) of the current key: the shared prefix carried from
-      // the previous key, the rest read from the key delta
-      uint8_t cur[kDecSlots] = {0, 0, 0, 0};
-      for (uint32_t k = 0; k < nent; ++k) {
-        const uint32_t src = k & 31u, h = k >> 5;
-        const uint32_t shared = __shfl_sync(0xFFFFFFFFu, h ? sh[1] : sh[0], src);
-        const uint32_t klen = __shfl_sync(0xFFFFFFFFu, h ? kl[1] : kl[0], src);
-        const uint32_t dpos = __shfl_sync(0xFFFFFFFFu, h ? dp[1] : dp[0], src);
-        const uint32_t kof = __shfl_sync(0xFFFFFFFFu, h ? ko[1] : ko[0], src);
-        uint8_t* kd = A.arena + key0 + kof;
+      // the previous key, the rest read from the key delta. The delta bytes of kKeyBatch
+      // entries are loaded together (they do not depend on one another), byte s of a lane's
+      // share of entry i in byte s of d[i]; then the keys are rebuilt in order.
+      uint32_t cur = 0;
+      for (uint32_t kb = 0; kb < nent; kb += kKeyBatch) {
+        uint32_t d[kKeyBatch];
 #pragma unroll
-        for (uint32_t s = 0; s < kDecSlots; ++s) {
-          const uint32_t t = lane + 32 * s;
-          if (t < klen) {
-            if (t >= shared) cur[s] = __ldg(b.ptr + dpos + t - shared);
-            kd[t] = cur[s];
+        for (uint32_t i = 0; i < kKeyBatch; ++i) {
+          const uint32_t k = kb + i, src = k & 31u, h = (k >> 5) & 1u;
+          const uint32_t shared = __shfl_sync(0xFFFFFFFFu, h ? sh[1] : sh[0], src);
+          const uint32_t klen = __shfl_sync(0xFFFFFFFFu, h ? kl[1] : kl[0], src);
+          const uint32_t dpos = __shfl_sync(0xFFFFFFFFu, h ? dp[1] : dp[0], src);
+          d[i] = 0;
+          if (k < nent) {
+#pragma unroll
+            for (uint32_t s = 0; s < kDecSlots; ++s) {
+              const uint32_t t = lane + 32 * s;
+              if (t < klen && t >= shared) d[i] |= uint32_t(__ldg(b.ptr + dpos + t - shared)) << (8 * s);
+            }
+          }
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kKeyBatch; ++i) {
+          const uint32_t k = kb + i, src = k & 31u, h = (k >> 5) & 1u;
+          const uint32_t shared = __shfl_sync(0xFFFFFFFFu, h ? sh[1] : sh[0], src);
+          const uint32_t klen = __shfl_sync(0xFFFFFFFFu, h ? kl[1] : kl[0], src);
+          const uint32_t kof = __shfl_sync(0xFFFFFFFFu, h ? ko[1] : ko[0], src);
+          if (k < nent) {
+            uint8_t* kd = A.arena + key0 + kof;
+#pragma unroll
+            for (uint32_t s = 0; s < kDecSlots; ++s) {
+              const uint32_t t = lane + 32 * s;
+              if (t < klen) {
+                if (t >= shared) cur = (cur & ~(0xFFu << (8 * s))) | (d[i] & (0xFFu << (8 * s)));
+                kd[t] = uint8_t(cur >> (8 * s));
+              }
+            }
           }
         }
       }
