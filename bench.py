@@ -565,32 +565,45 @@ def batched(args, stream):
 
 
 def served(args):
-    """The served workload: a simulated 7-level LSM tree (64 MiB memtables, L0 trigger 4,
-    fanout 10, 64 MiB tables, 4 KiB blocks) fed by a seeded Poisson write stream (16 B
-    keys, half uniform and half zipf(0.99), 256 B values). Compaction jobs go to a
-    luda_server with continuous batching under a 40 GB HBM budget; the same stream is then
-    served by a one-slot server (the plain per-job launch, first in first out). Reports
-    compaction input MiB/s over the run's wall time and p50/p99 job latency."""
+    """The served workload: a simulated 7-level LSM tree (L0 trigger 4, fanout 10, 4 KiB
+    blocks) fed by a seeded Poisson write stream (16 B keys, half uniform and half
+    zipf(0.99), 256 B values). Compaction jobs go to a luda_server with continuous
+    batching under a 40 GB HBM budget; the same stream is then served by a one-slot server
+    (the plain per-job launch, first in first out). Two sizes: 64 MiB memtables and tables
+    (the paper's table size, a few dozen jobs), and 4 MiB memtables and tables (hundreds of
+    jobs, so that p99 is a percentile rather than the maximum). Reports compaction input
+    MiB/s over the run's wall time and p50/p99 job latency."""
     from paper_2004_03054_b300 import lsm as L
     from paper_2004_03054_b300 import workloads as W
+
+    def run(name, slots, n_memtables, table_bytes, seed):
+        stream = W.config5_stream(seed=seed, n_memtables=n_memtables, memtable_bytes=table_bytes,
+                                  write_rate=args.serve_rate)
+        rep = L.serve(stream, n_slots=slots, hbm_budget=40 * 10**9, pace=True, prewarm_bytes=16 << 30,
+                      lsm_kw={"memtable_bytes": table_bytes, "target_file": table_bytes})
+        return {"slots": slots, "jobs": rep.jobs, "failed": rep.failed,
+                "value": round(rep.compaction_in_bytes / MiB / rep.wall_s, 1), "unit": "MiB/s",
+                "wall_s": round(rep.wall_s, 3), "compaction_in_bytes": rep.compaction_in_bytes,
+                "written_bytes": rep.written_bytes,
+                "job_latency_ms": {"p50": round(rep.pct(0.5), 3), "p99": round(rep.pct(0.99), 3),
+                                   "max": round(max(rep.latencies_ms, default=0), 3)},
+                "admit_wait_ms_p99": round(sorted(rep.admit_wait_ms)[int(0.99 * (len(rep.admit_wait_ms) - 1))]
+                                           if rep.admit_wait_ms else 0, 3),
+                "running_peak": rep.running_peak, "budget_peak_bytes": rep.budget_peak,
+                "write_stall_s": round(rep.stall_s, 3),
+                "level_bytes": rep.level_bytes}
 
     out = {"workload": f"cfg5_served: {args.serve_memtables} memtables of 64 MiB, Poisson writes at "
                        f"{args.serve_rate:.0f}/s, 16 B keys (50% uniform, 50% zipf 0.99), 256 B values, "
                        "L0 trigger 4, fanout 10, 64 MiB tables, 40 GB budget"}
     for name, slots in (("continuous", args.serve_slots), ("per_job_fifo", 1)):
-        stream = W.config5_stream(seed=5, n_memtables=args.serve_memtables, write_rate=args.serve_rate)
-        rep = L.serve(stream, n_slots=slots, hbm_budget=40 * 10**9, pace=True, prewarm_bytes=16 << 30)
-        out[name] = {"slots": slots, "jobs": rep.jobs, "failed": rep.failed,
-                     "value": round(rep.compaction_in_bytes / MiB / rep.wall_s, 1), "unit": "MiB/s",
-                     "wall_s": round(rep.wall_s, 3), "compaction_in_bytes": rep.compaction_in_bytes,
-                     "written_bytes": rep.written_bytes,
-                     "job_latency_ms": {"p50": round(rep.pct(0.5), 3), "p99": round(rep.pct(0.99), 3),
-                                        "max": round(max(rep.latencies_ms, default=0), 3)},
-                     "admit_wait_ms_p99": round(sorted(rep.admit_wait_ms)[int(0.99 * (len(rep.admit_wait_ms) - 1))]
-                                                if rep.admit_wait_ms else 0, 3),
-                     "running_peak": rep.running_peak, "budget_peak_bytes": rep.budget_peak,
-                     "write_stall_s": round(rep.stall_s, 3),
-                     "level_bytes": rep.level_bytes}
+        out[name] = run(name, slots, args.serve_memtables, 64 * (1 << 20), 5)
+    if args.serve_small_memtables:
+        small = {"workload": f"cfg5_served with 4 MiB memtables and tables: {args.serve_small_memtables} memtables, "
+                             f"the same stream shape and rate"}
+        for name, slots in (("continuous", args.serve_slots), ("per_job_fifo", 1)):
+            small[name] = run(name, slots, args.serve_small_memtables, 4 * (1 << 20), 6)
+        out["tables_4mib"] = small
     return out
 
 
@@ -741,6 +754,8 @@ def main():
     ap.add_argument("--serve-memtables", type=int, default=40)
     ap.add_argument("--serve-rate", type=float, default=8e6, help="writes per second of the served stream")
     ap.add_argument("--serve-slots", type=int, default=6)
+    ap.add_argument("--serve-small-memtables", type=int, default=400,
+                    help="memtables of the 4 MiB served run (0: skip it)")
     ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--batch-steps", type=int, default=5)

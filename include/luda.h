@@ -74,6 +74,21 @@ typedef enum {
                                  would; the call then fails with LUDA_ERR_TIMEOUT and returns no tables. The
                                  bulk copies already issued are still waited for (one second at most) before
                                  each CTA exits, so the device stays usable */
+#define LUDA_F_KEEP_DECODED 64u /* keep decoded runs on the device (§III-D: data stays in GPU memory between
+                                   jobs). A call with this flag keeps, for each new table it returns on the
+                                   device, the table's decoded run: its records (key prefix, trailer, key and
+                                   value lengths, the value's CRC-32C register, the value's address inside
+                                   the table) and full keys, in one store freed together with the tables
+                                   (luda_outputs_free). A later call with this flag whose inputs are ALL
+                                   tables with kept runs (same data pointer and size) takes its records from
+                                   the runs and runs none of the footer, index, block walk, checksum and key
+                                   kernels (§II-A Phase 1 ran when the tables were written); its tables are
+                                   byte for byte those of the same call without the flag. A kept run stands
+                                   for the table's bytes as they were written: a caller that changes a
+                                   table's bytes on the device must not pass the flag for it. Tables written
+                                   compressed (LUDA_F_COMPRESS), host outputs, ranged jobs (R13) and plans
+                                   neither keep nor use runs. The store takes about 48 bytes per entry plus
+                                   the keys */
 #define LUDA_F_TRACE 2u      /* record per-stage device times (luda_outputs.stage_ms); LUDA_TRACE=1 in the
                                 environment does the same for every call. Stage boundaries always open
                                 NVTX ranges "luda/<stage>" on the calling thread. */
@@ -419,6 +434,9 @@ LUDA_API const char* luda_last_error_detail(void);
 LUDA_API const char* luda_version(void);
 /* Number of CUDA kernels this library has launched in this process so far. */
 LUDA_API uint64_t luda_launch_count(void);
+/* Number of input tables whose records came from kept decoded runs (LUDA_F_KEEP_DECODED)
+ * in this process so far. */
+LUDA_API uint64_t luda_kept_inputs_used(void);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <iterator>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -248,6 +250,80 @@ struct Layout {
   }
 };
 
+KeptRecs kept_layout(Layout& L, uint64_t n, uint64_t key_bytes) {
+  KeptRecs K;
+  K.pfx = L.take<uint64_t>(n + 1);
+  K.tr = L.take<uint64_t>(n + 1);
+  K.koff = L.take<uint64_t>(n + 1);
+  K.vptr = L.take<uint64_t>(n + 1);
+  K.klen = L.take<uint32_t>(n + 1);
+  K.vlen = L.take<uint32_t>(n + 1);
+  K.vcrc = L.take<uint32_t>(n + 1);
+  K.arena = L.take<uint8_t>(key_bytes + 64);
+  return K;
+}
+
+// ---- kept decoded runs (LUDA_F_KEEP_DECODED) -------------------------------------------------
+// A store is one device allocation holding the kept run of one call's survivors. Each new
+// table of the call registers its slice of the run under its data pointer and size; the
+// registration ends, and the store is freed, when the outputs holding the tables are freed.
+struct KeptStore {
+  void* mem = nullptr;
+  luda_free_fn dev_free = nullptr;
+  void* ctx = nullptr;
+  KeptRecs run{};
+};
+struct KeptTable {
+  KeptStore* store = nullptr;
+  uint64_t size = 0;
+  uint64_t first = 0, count = 0, key_first = 0, kbytes = 0;
+  uint32_t max_kv = 0;
+  std::vector<uint8_t> smallest, largest;  // internal keys
+};
+std::mutex g_kept_mu;
+std::unordered_map<uintptr_t, KeptTable> g_kept;  // by the table's data pointer
+std::atomic<uint64_t> g_kept_used{0};             // inputs served from kept runs
+
+void kept_free(KeptStore* k) {
+  if (!k) return;
+  {
+    std::lock_guard<std::mutex> lk(g_kept_mu);
+    for (auto it = g_kept.begin(); it != g_kept.end();)
+      it = it->second.store == k ? g_kept.erase(it) : std::next(it);
+  }
+  if (k->mem) {
+    if (k->dev_free) k->dev_free(k->mem, k->ctx, nullptr);
+    else cudaFree(k->mem);
+  }
+  delete k;
+}
+
+// The kept runs of all n inputs (copies of their registrations), or false if one has none.
+bool kept_lookup(const std::vector<DInput>& in, std::vector<KeptTable>* out) {
+  std::lock_guard<std::mutex> lk(g_kept_mu);
+  out->clear();
+  for (const DInput& d : in) {
+    auto it = g_kept.find(reinterpret_cast<uintptr_t>(d.data));
+    if (it == g_kept.end() || it->second.size != d.size) return false;
+    out->push_back(it->second);
+  }
+  return true;
+}
+
+// Internal-key order of two internal keys held on the host (user key bytes, a proper
+// prefix first, then the trailer descending).
+int cmp_ikey_host(const std::vector<uint8_t>& a, const std::vector<uint8_t>& b) {
+  if (a.size() < 8 || b.size() < 8) return a.size() < b.size() ? -1 : (a.size() > b.size() ? 1 : 0);
+  const size_t ua = a.size() - 8, ub = b.size() - 8, m = ua < ub ? ua : ub;
+  const int c = m ? memcmp(a.data(), b.data(), m) : 0;
+  if (c) return c < 0 ? -1 : 1;
+  if (ua != ub) return ua < ub ? -1 : 1;
+  uint64_t ta = 0, tb = 0;
+  memcpy(&ta, a.data() + ua, 8);
+  memcpy(&tb, b.data() + ub, 8);
+  return ta == tb ? 0 : (ta > tb ? -1 : 1);
+}
+
 // Owner of the memory behind one or more luda_outputs (shared by the jobs of a batch).
 struct Holder {
   std::atomic<int> refs{1};
@@ -256,6 +332,7 @@ struct Holder {
   void* ctx = nullptr;
   uint8_t* pinned = nullptr;
   size_t pinned_cap = 0;
+  KeptStore* kept = nullptr;  // the kept run of the tables (LUDA_F_KEEP_DECODED)
 };
 
 // A small cache of pinned host buffers for table images (cudaHostAlloc is slow).
@@ -293,6 +370,7 @@ void pinned_put(uint8_t* p, size_t cap) {
 void holder_release(Holder* h) {
   if (!h) return;
   if (--h->refs > 0) return;
+  kept_free(h->kept);  // first: no lookup may find a table whose memory is going
   if (h->dev) {
     if (h->dev_free) h->dev_free(h->dev, h->ctx, nullptr);
     else cudaFree(h->dev);
@@ -320,7 +398,7 @@ luda_status opts_check(const luda_options* o, Fmt* fmt) {
   }
   if (!tuning_valid(o->tuning)) return LUDA_ERR_INVALID_ARG;
   if (o->flags & ~(LUDA_F_STRICT_DUP | LUDA_F_TRACE | LUDA_F_SHORT_INDEX | LUDA_F_FILTER_ARRAY | LUDA_F_COMPRESS |
-                   LUDA_F_TEST_WAIT0)) {
+                   LUDA_F_TEST_WAIT0 | LUDA_F_KEEP_DECODED)) {
     set_detail("unknown option flags 0x%x", o->flags);
     return LUDA_ERR_INVALID_ARG;
   }
@@ -890,6 +968,70 @@ void merge_schedule(const std::vector<std::vector<std::pair<uint32_t, uint32_t>>
   }
 }
 
+// LUDA_F_KEEP_DECODED, after the pack stage: a store for the survivors' run, filled on st.
+// Null when nothing is kept: the flag is off, the tables are compressed (a compressed
+// block's value has no address of its own) or go to the host, or there is no memory for
+// the store (the tables are then simply not kept).
+luda_status kept_start(const luda_options* o, const DevMem& mem, bool host_out, const PackBufs& pb,
+                       const Counts* d_cnt, uint32_t cap, uint64_t key_bytes, const Recs& recs,
+                       const uint8_t* d_out, cudaStream_t st, KeptStore** out) {
+  *out = nullptr;
+  if (!(o->flags & LUDA_F_KEEP_DECODED) || host_out || pb.cz.raw_cap || !cap) return LUDA_OK;
+  Layout LK;
+  kept_layout(LK, cap, key_bytes);
+  void* km = mem.get(LK.off);
+  if (!km) {
+    cudaGetLastError();  // an allocation that failed leaves nothing behind
+    return LUDA_OK;
+  }
+  KeptStore* k = new KeptStore();
+  k->mem = km;
+  k->dev_free = o->dev_free;
+  k->ctx = o->alloc_ctx;
+  LK = Layout{};
+  LK.base = static_cast<uint8_t*>(km);
+  k->run = kept_layout(LK, cap, key_bytes);
+  const cudaError_t e =
+      launch_keep(d_cnt, cap, pb.ed, recs, pb.files, pb.bd, pb.blk_file, d_out, pb.meta, k->run, pb.scan_tmp, st);
+  if (e != cudaSuccess) {
+    kept_free(k);
+    return cuda_fail(e, "kept run");
+  }
+  *out = k;
+  return LUDA_OK;
+}
+
+// Each new table of the finished jobs registers its slice of the store's run.
+void kept_register(KeptStore* k, const Collected& col, uint32_t n_jobs, const luda_outputs* outs,
+                   const uint8_t* base) {
+  std::lock_guard<std::mutex> lk(g_kept_mu);
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    if (outs[j].status != LUDA_OK) continue;
+    const JobDev& jd = col.jobs[j];
+    uint64_t first = jd.surv_begin;
+    for (uint32_t f = jd.file_begin; f < jd.file_end; ++f) {
+      const FileMeta& m = col.meta[f];
+      KeptTable t;
+      t.store = k;
+      t.size = m.size;
+      t.first = first;
+      t.count = m.n_entries;
+      t.key_first = m.key_first;
+      t.kbytes = m.kbytes;
+      t.max_kv = m.max_kv;
+      t.smallest.assign(col.keys.begin() + m.small_koff, col.keys.begin() + m.small_koff + m.small_len);
+      t.largest.assign(col.keys.begin() + m.large_koff, col.keys.begin() + m.large_koff + m.large_len);
+      g_kept[reinterpret_cast<uintptr_t>(base + m.off)] = std::move(t);
+      first += m.n_entries;
+    }
+  }
+}
+
+struct KeptGuard {
+  KeptStore* k = nullptr;
+  ~KeptGuard() { kept_free(k); }
+};
+
 // The whole compaction for n_jobs jobs whose inputs are device pointers. On return
 // outs[j] hold device (or, with host_out, pinned host) tables.
 luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_options* o, cudaStream_t st,
@@ -965,6 +1107,10 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   }
   const bool ranged = !hbounds.empty() || std::any_of(hranges.begin(), hranges.end(),
                                                       [](const JobRange& r) { return r.flags != 0; });
+  // inputs with kept decoded runs (LUDA_F_KEEP_DECODED): when every input has one, the
+  // records come from the runs and none of the sizing and unpack kernels runs
+  std::vector<KeptTable> kin;
+  const bool cached = (o->flags & LUDA_F_KEEP_DECODED) && !ranged && N > 0 && kept_lookup(hin, &kin);
   Layout LA;
   DInput* d_in;
   DErr* d_errs;
@@ -1026,14 +1172,16 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   // take precedence when the results are collected) while the host sizes the job
   Side* side = nullptr;
   if ((rc = get_side(&side))) return rc;
-  launch_footers_read(d_in, N, d_errs, d_msgs, st);
-  CK(fork_join(side, 4, st, side->s));
-  launch_index_crc(d_msgs, N, d_errs + n_jobs + 1, tabs, side->s);
-  launch_footers_finish(d_in, N, d_errs, st);
-  CK(cudaGetLastError());
-  if (N) CK(cudaMemcpyAsync(hin_pin ? hin_pin : hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (N && hin_pin) memcpy(hin.data(), hin_pin, sizeof(DInput) * N);
+  if (!cached) {
+    launch_footers_read(d_in, N, d_errs, d_msgs, st);
+    CK(fork_join(side, 4, st, side->s));
+    launch_index_crc(d_msgs, N, d_errs + n_jobs + 1, tabs, side->s);
+    launch_footers_finish(d_in, N, d_errs, st);
+    CK(cudaGetLastError());
+    if (N) CK(cudaMemcpyAsync(hin_pin ? hin_pin : hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (N && hin_pin) memcpy(hin.data(), hin_pin, sizeof(DInput) * N);
+  }
   std::vector<uint32_t> in_blk_first(N + 1, 0);
   uint64_t NB64 = 0;
   for (uint32_t i = 0; i < N; ++i) {
@@ -1086,7 +1234,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   LB.base = bufB;
   layoutB(LB, d_blocks, d_nrec, d_kbytes, d_rec_first, d_key_first, d_in_rec, d_in_key, d_tmpB);
 
-  launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st, d_ranges, d_bounds);
+  if (!cached) launch_index_entries(d_in, N, d_in_blk_first, NB, d_blocks, d_errs, st, d_ranges, d_bounds);
   // block contents: the stored blocks, or copies pointing at their decompressed contents
   BlockDesc* d_cb = d_blocks;
   std::vector<uint32_t> in_rec(N + 1);
@@ -1152,7 +1300,32 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     return LUDA_OK;
   };
   tr.mark(1, st);
-  if ((rc = size_pass(false))) return rc;
+  if (cached) {
+    // the runs' counts, key bytes and boundary keys stand for the blocks' (records of
+    // input i follow those of input i - 1; inputs i and i + 1 of one job form one sorted run
+    // when i's largest key is below i + 1's smallest)
+    tr.mark(2, st);
+    tr.mark(3, st);
+    in_rec[0] = 0;
+    in_key[0] = 0;
+    for (uint32_t i = 0; i < N; ++i) {
+      in_rec[i + 1] = in_rec[i] + uint32_t(kin[i].count);
+      in_key[i + 1] = in_key[i] + kin[i].kbytes;
+      fmt.max_kv = std::max(fmt.max_kv, kin[i].max_kv);
+      link[i] = i + 1 < N && hin[i].job == hin[i + 1].job && kin[i].count && kin[i + 1].count &&
+                cmp_ikey_host(kin[i].largest, kin[i + 1].smallest) < 0;
+    }
+    if (uint64_t(in_rec[N]) != [&] {
+          uint64_t t = 0;
+          for (const KeptTable& k : kin) t += k.count;
+          return t;
+        }()) {
+      set_detail("too many entries in one call");
+      return LUDA_ERR_INVALID_ARG;
+    }
+  } else if ((rc = size_pass(false))) {
+    return rc;
+  }
   if (comp_blocks) {
     // R4c: the compressed blocks decompressed into one arena (each at a 16-byte multiple),
     // then the job sized again from the contents
@@ -1237,10 +1410,12 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   uint32_t *d_ord0, *d_ord1, *d_keep, *d_pos, *d_co, *d_chunkF, *d_snap;
   MKey *d_pfx0, *d_pfx1;
   MergeSpan* d_spans;
+  KeptIn* d_kin;
   PackBufs pb;
   const uint64_t chunk_cap = uint64_t(n_chunks) + 16;
   auto layoutC = [&](Layout& L) {
     recs = recs_layout(L, n_rec);
+    d_kin = L.take<KeptIn>(cached ? N + 1 : 1);
     d_arena = L.take<uint8_t>(K + 64);
     d_chunkF = L.take<uint32_t>(chunk_cap);
     d_snap = L.take<uint32_t>(2ull * n_rec + 2ull * NB + 2);
@@ -1295,15 +1470,36 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     UnpArgs ua{d_cb,          NB,    d_in,       d_nrec,   d_kbytes, nullptr, nullptr,
                d_hdr,         d_rec_first, d_key_first, d_chunk_first, d_chunkF, d_snap, recs,
                d_arena,       d_errs, d_errs + n_jobs + 1, comp_blocks == 0, &d_cnt->unp_next};
-    CK(fork_join(side, 0, st, side->s));
-    tr.mark(11, side->s);
-    launch_unpack_crc(ua, tabs, kUnpCtas, side->s);
-    tr.mark(12, side->s);
-    launch_unpack_keys(ua, st);
+    if (cached) {
+      // records from the kept runs, each input's keys in one copy
+      tr.mark(11, st);
+      tr.mark(12, st);
+      std::vector<KeptIn> hk(N);
+      uint64_t max_count = 0;
+      for (uint32_t i = 0; i < N; ++i) {
+        hk[i] = KeptIn{kin[i].store->run, kin[i].first, kin[i].count, kin[i].key_first, in_rec[i], in_key[i]};
+        max_count = std::max(max_count, kin[i].count);
+        if (kin[i].kbytes)
+          CK(cudaMemcpyAsync(d_arena + in_key[i], kin[i].store->run.arena + kin[i].key_first, kin[i].kbytes,
+                             cudaMemcpyDeviceToDevice, st));
+      }
+      CK(cudaMemcpyAsync(d_kin, pin(hk.data(), sizeof(KeptIn) * N), sizeof(KeptIn) * N, cudaMemcpyHostToDevice, st));
+      launch_kept_gather(d_kin, N, max_count, recs, st);
+      g_kept_used += N;
+    } else {
+      CK(fork_join(side, 0, st, side->s));
+      tr.mark(11, side->s);
+      launch_unpack_crc(ua, tabs, kUnpCtas, side->s);
+      tr.mark(12, side->s);
+      launch_unpack_keys(ua, st);
+    }
   }
   tr.mark(5, st);
-  launch_check_index(d_cb, NB, d_in, d_nrec, d_rec_first, recs, d_arena, d_errs, st);
-  launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
+  if (!cached) {
+    // (a kept run was checked when its table was written)
+    launch_check_index(d_cb, NB, d_in, d_nrec, d_rec_first, recs, d_arena, d_errs, st);
+    launch_check_order(recs, d_arena, n_rec, d_in, d_errs, st);
+  }
   launch_sort_init(d_ord0, d_pfx0, recs, d_arena, n_rec, st);
   for (size_t p = 0; p < pass_span0.size(); ++p)
     launch_merge_pass(d_spans + pass_span0[p], pass_nspans[p], pass_ntiles[p], ms.tile, d_ord0, d_pfx0, d_ord1,
@@ -1323,6 +1519,9 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     return rc;
   if (comp_blocks) CK(cudaStreamWaitEvent(st, side->ev[1], 0));
   CK(cudaStreamWaitEvent(st, side->ev[3], 0));
+  // LUDA_F_KEEP_DECODED: the survivors kept as a sorted run for the new tables
+  KeptGuard kguard;
+  if ((rc = kept_start(o, mem, host_out, pb, d_cnt, cap, K, recs, d_out, st, &kguard.k))) return rc;
   tr.mark(10, st);
   tdev.stop(st);
 
@@ -1382,6 +1581,11 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   for (uint32_t j = 0; j < n_jobs; ++j) {
     outs[j].status = err_status(col.errs[j], j, n_jobs);
     if (outs[j].status && !first) first = luda_status(outs[j].status);
+  }
+  if (kguard.k) {
+    kept_register(kguard.k, col, n_jobs, outs, base);
+    h->kept = kguard.k;  // freed with the tables' memory
+    kguard.k = nullptr;
   }
   fill_outputs(col, n_jobs, base, h, outs);
   holder_release(h);
@@ -1523,6 +1727,8 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
   if ((rc = run_pack(pb, d_cnt, d_job, 1, d_err, n, recs, arena, fmt, d_out, out_cap, bm_cap, tabs, st, side)))
     return rc;
   CK(cudaStreamWaitEvent(st, side->ev[3], 0));
+  KeptGuard kguard;
+  if ((rc = kept_start(o, mem, host_out, pb, d_cnt, n, K, recs, d_out, st, &kguard.k))) return rc;
   td.stop(st);
   Collected col;
   t_stage.reset();  // nothing of this call was staged before (its copies are synchronous)
@@ -1553,6 +1759,11 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
     return cuda_fail(cudaGetLastError(), "stream synchronize");
   }
   out->status = err_status(col.errs[0], 0, 1);
+  if (kguard.k) {
+    kept_register(kguard.k, col, 1, out, base);
+    h->kept = kguard.k;
+    kguard.k = nullptr;
+  }
   fill_outputs(col, 1, base, h, out);
   holder_release(h);
   out->n_in_entries = n;
@@ -2030,6 +2241,8 @@ const char* luda_last_error_detail(void) { return t_detail; }
 const char* luda_version(void) { return "luda-b300 0.1 (sm_103a)"; }
 
 uint64_t luda_launch_count(void) { return g_launches.load(); }
+
+uint64_t luda_kept_inputs_used(void) { return g_kept_used.load(); }
 
 void luda_outputs_free(luda_outputs* out) {
   if (!out) return;

@@ -167,7 +167,26 @@ struct FileMeta {
   uint64_t off, size, n_entries, data_size;
   uint64_t small_koff, large_koff;  // in the key gather buffer
   uint32_t small_len, large_len;
-  uint32_t job, pad;
+  uint32_t job;
+  uint32_t max_kv;               // kept runs (LUDA_F_KEEP_DECODED): largest key + value length
+  uint64_t key_first, kbytes;    // kept runs: the table's keys in the store's key arena
+};
+
+// ---- keep.cu: decoded runs kept between compactions (LUDA_F_KEEP_DECODED) ------------------
+// One store per call: the survivors in output order, their full keys back to back in
+// `arena` (koff: offsets, exclusive scan of klen), each value's address inside the new
+// data blocks (vptr) and its CRC-32C register (vcrc).
+struct KeptRecs {
+  uint64_t *pfx, *tr, *koff, *vptr;
+  uint32_t *klen, *vlen, *vcrc;
+  uint8_t* arena;
+};
+// One input of a call whose records come from a kept run: survivors [first, first + count)
+// of `run`, whose keys start at key_first in the run's arena; they become records
+// [rec_base, rec_base + count) with keys from key_base in the call's arena.
+struct KeptIn {
+  KeptRecs run;
+  uint64_t first, count, key_first, rec_base, key_base;
 };
 
 // ---- launch geometry --------------------------------------------------------------------
@@ -477,5 +496,13 @@ luda_status compact_job_device(const luda_job& job, const luda_options* opts, lu
 // tables of the device, the pinned staging buffer) ahead of its first job.
 luda_status warm_thread();
 luda_status compact_job_host(const luda_job& job, const luda_options* opts, luda_outputs* out, AdmitGate* gate);
+
+// The kept run of a call's survivors (after the pack stage, on the call's stream): records,
+// keys, value addresses in `out`, and per table key_first / kbytes / max_kv in meta.
+cudaError_t launch_keep(const Counts* cnt, uint32_t cap, const EncDesc* ed, Recs recs, const FileDesc* files,
+                        const BlkEnc* bd, const uint32_t* blk_file, const uint8_t* out, FileMeta* meta, KeptRecs K,
+                        void* scan_tmp, cudaStream_t st);
+// Records of inputs taken from kept runs (max_count: the largest input's count).
+void launch_kept_gather(const KeptIn* ins, uint32_t n_inputs, uint64_t max_count, Recs recs, cudaStream_t st);
 
 }  // namespace luda

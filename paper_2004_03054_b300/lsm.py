@@ -107,6 +107,7 @@ class ServeReport:
     level_bytes: list = field(default_factory=list)
     flushes: int = 0
     retried: int = 0         # jobs started again after a failure
+    kept_inputs: int = 0     # input tables whose records came from kept decoded runs
 
     def pct(self, p: float) -> float:
         if not self.latencies_ms:
@@ -123,7 +124,7 @@ class LSM:
     def __init__(self, server: luda.Server, memtable_bytes: int = 64 * MiB, l0_trigger: int = 4,
                  l0_stop: int = 12, fanout: int = 10, target_file: int = 64 * MiB, block_size: int = 4096,
                  restart_interval: int = 16, bloom_bits_per_key: int = 10, value_pool_bytes: int = 256 * MiB,
-                 seed: int = 5, on_complete=None, fault=None):
+                 seed: int = 5, on_complete=None, fault=None, keep_decoded: bool = False):
         import torch
         self.server = server
         self.fault = fault            # fault(job_index, level) -> True: corrupt that job
@@ -137,7 +138,10 @@ class LSM:
         self.jobs = {}
         self.on_complete = on_complete
         self.fmt = (block_size, restart_interval, bloom_bits_per_key)
-        self.build_opts = luda.options(block_size, restart_interval, bloom_bits_per_key, (1 << 64) - 1)
+        # keep_decoded: flushes and compactions keep their tables' decoded runs on the device,
+        # and a compaction whose inputs all have one skips decoding them (§III-D)
+        self.build_opts = luda.options(block_size, restart_interval, bloom_bits_per_key, (1 << 64) - 1,
+                                       flags=luda.F_KEEP_DECODED if keep_decoded else 0)
         self.report = ServeReport()
         g = torch.Generator(device="cuda")
         g.manual_seed(seed)
@@ -358,11 +362,13 @@ def serve(stream, n_slots: int = 4, hbm_budget: int = 40 * 10**9, pace: bool = T
     import torch
     kw = dict(lsm_kw or {})
     opts = luda.options(kw.get("block_size", 4096), kw.get("restart_interval", 16), kw.get("bloom_bits_per_key", 10),
-                        kw.get("target_file", 64 * MiB))
+                        kw.get("target_file", 64 * MiB),
+                        flags=luda.F_KEEP_DECODED if kw.get("keep_decoded") else 0)
     server = luda.Server(n_slots, hbm_budget, opts, prewarm_bytes=prewarm_bytes)
     lsm = LSM(server, on_complete=on_complete, **kw)
     torch.cuda.synchronize()
     mts = list(stream)
+    kept0 = luda.kept_inputs_used()
     t0 = time.perf_counter()
     k = 0
     try:
@@ -392,6 +398,7 @@ def serve(stream, n_slots: int = 4, hbm_budget: int = 40 * 10**9, pace: bool = T
                 lsm.schedule()
         rep = lsm.report
         rep.wall_s = time.perf_counter() - t0
+        rep.kept_inputs = luda.kept_inputs_used() - kept0
         st = server.stats()
         rep.running_peak, rep.budget_peak = int(st.running_peak), int(st.budget_peak)
         rep.level_bytes = [lsm.level_bytes(i) for i in range(N_LEVELS)]

@@ -29,6 +29,7 @@ F_SHORT_INDEX = 4  # shortened index keys (format variant R9s)
 F_FILTER_ARRAY = 8  # one bloom filter per 2 KiB of data block offsets (format variant R10a)
 F_COMPRESS = 16  # data blocks written compressed when that saves an eighth (format variant R4c)
 F_TEST_WAIT0 = 32  # test only: the encoder's copy-slot waits give up at once (LUDA_ERR_TIMEOUT, no tables)
+F_KEEP_DECODED = 64  # keep the new tables' decoded runs on the device; take kept runs for inputs (§III-D)
 MAX_SEQ = (1 << 56) - 1
 
 
@@ -152,6 +153,7 @@ def lib():
         L.luda_last_error_detail.restype = C.c_char_p
         L.luda_version.restype = C.c_char_p
         L.luda_launch_count.restype = C.c_uint64
+        L.luda_kept_inputs_used.restype = C.c_uint64
         L.luda_check_table_noalloc.restype = st
         L.luda_check_table_noalloc.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(TableCheck)]
         for name in ("luda_plan_create", "luda_plan_run", "luda_plan_outputs"):
@@ -208,6 +210,11 @@ def job_options(job, **kw) -> Options:
 def launch_count() -> int:
     """Kernels libluda has launched in this process."""
     return int(lib().luda_launch_count())
+
+
+def kept_inputs_used() -> int:
+    """Input tables whose records came from kept decoded runs in this process."""
+    return int(lib().luda_kept_inputs_used())
 
 
 def strerror(s: int) -> str:

@@ -142,7 +142,7 @@ def test_plan_reports_compressed_inputs_not_supported():
 
 def test_unknown_flags_are_refused():
     ins = _inputs(1, 50, 100, 4096, seed=51)
-    res = luda.compact_device([dev(ins[0])], oracle.MAX_SEQ, opts=luda.options(flags=64))
+    res = luda.compact_device([dev(ins[0])], oracle.MAX_SEQ, opts=luda.options(flags=1 << 10))
     assert res.status == luda.ERR_INVALID_ARG
 
 
