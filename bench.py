@@ -408,6 +408,31 @@ def variants(job, inputs, in_bytes, stream, scale=1.0, steps=5):
     res["subcompactions_4"]["bounds"] = "first user keys of the lower level's tables at its quartiles"
     res["compress_output"]["note"] = "random values: blocks are compressed, then kept raw (no eighth saved)"
 
+    # LUDA_F_KEEP_DECODED: the job keeping its tables' decoded runs, and the same job when
+    # every input table already has a kept run (the inputs built with the flag and kept
+    # alive), which skips the footer, index, walk, checksum and key kernels
+    kf = luda.F_KEEP_DECODED
+    o = luda.job_options(job, flags=kf, stream=C.c_void_p(stream.cuda_stream))
+    res["keep_outputs"] = timed(lambda out: L.luda_compact_device(ins, len(inputs), job.level, job.smallest_snapshot,
+                                                                  C.byref(o), C.byref(out)))
+    kouts, kins = [], (luda.Input * len(job.inputs))()
+    for i, r in enumerate(job.inputs):
+        ra, keep_arrays = luda._run_arrays(r, device=True)
+        bo = luda.options(job.block_size, job.restart_interval, job.bloom_bits_per_key, (1 << 64) - 1, flags=kf,
+                          stream=C.c_void_p(stream.cuda_stream))
+        out = luda.Outputs()
+        if L.luda_build_device(C.byref(ra), C.byref(bo), C.byref(out)) != 0 or out.n_tables != 1:
+            raise RuntimeError(f"kept input build failed: {luda.last_error_detail()}")
+        del keep_arrays
+        kouts.append(out)
+        kins[i].data, kins[i].size = out.tables[0].data, out.tables[0].size
+    u0 = luda.kept_inputs_used()
+    res["kept_inputs"] = timed(lambda out: L.luda_compact_device(kins, len(kouts), job.level, job.smallest_snapshot,
+                                                                 C.byref(o), C.byref(out)))
+    res["kept_inputs"]["inputs_from_kept_runs"] = luda.kept_inputs_used() - u0
+    for out in kouts:
+        L.luda_outputs_free(C.byref(out))
+
     # R4c on compressible data: the same job shape with values drawn from a word vocabulary
     # (about half compressible), its input tables built compressed on the device
     cjob = W.with_compressible_values(W.config3(seed=3, scale=scale))
@@ -576,12 +601,12 @@ def served(args):
     from paper_2004_03054_b300 import lsm as L
     from paper_2004_03054_b300 import workloads as W
 
-    def run(name, slots, n_memtables, table_bytes, seed):
+    def run(name, slots, n_memtables, table_bytes, seed, keep=False):
         stream = W.config5_stream(seed=seed, n_memtables=n_memtables, memtable_bytes=table_bytes,
                                   write_rate=args.serve_rate)
         rep = L.serve(stream, n_slots=slots, hbm_budget=40 * 10**9, pace=True, prewarm_bytes=16 << 30,
-                      lsm_kw={"memtable_bytes": table_bytes, "target_file": table_bytes})
-        return {"slots": slots, "jobs": rep.jobs, "failed": rep.failed,
+                      lsm_kw={"memtable_bytes": table_bytes, "target_file": table_bytes, "keep_decoded": keep})
+        return {"slots": slots, "jobs": rep.jobs, "failed": rep.failed, "inputs_from_kept_runs": rep.kept_inputs,
                 "value": round(rep.compaction_in_bytes / MiB / rep.wall_s, 1), "unit": "MiB/s",
                 "wall_s": round(rep.wall_s, 3), "compaction_in_bytes": rep.compaction_in_bytes,
                 "written_bytes": rep.written_bytes,
@@ -603,6 +628,9 @@ def served(args):
                              f"the same stream shape and rate"}
         for name, slots in (("continuous", args.serve_slots), ("per_job_fifo", 1)):
             small[name] = run(name, slots, args.serve_small_memtables, 4 * (1 << 20), 6)
+        # the same, every table keeping its decoded run (flushes and compactions)
+        small["continuous_kept_runs"] = run("continuous_kept_runs", args.serve_slots, args.serve_small_memtables,
+                                            4 * (1 << 20), 6, keep=True)
         out["tables_4mib"] = small
     return out
 
