@@ -121,12 +121,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) of all kernels of one compaction call on the large job, from an
-# ncu capture of one call (dram__bytes_read.sum + dram__bytes_write.sum per launch, summed;
-# the capture's job and its scale factor are in profiles/), with the SHA-256 of the CUDA
-# sources at the time: once a kernel's source changes the number no longer describes the
-# call and the bench reports null.
-_CALL_TRAFFIC = (None, "")
+# DRAM bytes (read + write) of one compaction call on the large job: all its kernels, and
+# the kernels the roofline lists, from an ncu capture of one call of the same job at
+# quarter scale (dram__bytes_read.sum + dram__bytes_write.sum per launch) times 4 (the
+# traffic grows with the entries; profiles/dram_traffic_cfg3_quarter.md), with the SHA-256
+# of the CUDA sources at the time: once a source changes the numbers no longer describe
+# the call and the bench reports null.
+_CALL_TRAFFIC = (4 * 1.059e9, "96a1008427c5d429181c5bb0bb86a35d6c612d768fe46ef8ab35264ad09b2363")
+_KERNEL_TRAFFIC = {"k_encode_stg": 4 * 475.4e6, "k_unpack": 4 * 267.9e6, "k_keys": 4 * 45.0e6}
 
 
 def _sources_digest():
@@ -140,12 +142,14 @@ def _sources_digest():
     return h.hexdigest()
 
 
-def _recorded_traffic(scale):
+def _recorded_traffic(scale, kernel=None):
     try:
         digest = _sources_digest()
     except OSError:
         return None
-    return _CALL_TRAFFIC[0] if digest == _CALL_TRAFFIC[1] and scale == 1.0 else None
+    if digest != _CALL_TRAFFIC[1] or scale != 1.0:
+        return None
+    return _CALL_TRAFFIC[0] if kernel is None else _KERNEL_TRAFFIC.get(kernel)
 
 
 # ---- our arm ------------------------------------------------------------------------------
@@ -234,7 +238,8 @@ def run_ours(args, ws, rank, local):
         if avg[idx] <= 0 or avg[idx] < 0.1 * ms:
             continue
         b = sbytes[-1][idx]
-        k = {"kernel": name, "ms_per_launch": round(avg[idx], 4), "share_of_call": round(avg[idx] / ms, 3)}
+        k = {"kernel": name, "ms_per_launch": round(avg[idx], 4), "share_of_call": round(avg[idx] / ms, 3),
+             "traffic": _recorded_traffic(args.scale, name.split()[0])}
         if b:
             k.update({"bytes_per_launch": b, "algorithmic_bytes": what,
                       "achieved": round(b / (avg[idx] / 1e3) / 1e9, 1), "frac": round(b / (avg[idx] / 1e3) / 1e9 / peak, 4)})
