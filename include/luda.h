@@ -113,7 +113,7 @@ typedef void (*luda_free_fn)(void* ptr, void* ctx, void* stream);
 typedef struct {
   uint32_t merge_tile;          /* records per merge CTA: 512, 1024 or 2048 (default 512) */
   uint32_t merge_ctas_per_sm;   /* grid of each merge pass, CTAs per SM: 1..32 (default 16) */
-  uint32_t decode_warps;        /* warps per CTA of the decoder, one data block each: 1..16 (default 8) */
+  uint32_t decode_warps;        /* warps per CTA of the key rebuild, one data block each: 1..16 (default 4) */
   uint32_t walk_threads;        /* threads per CTA of the block walk, one block each: 32..256, multiple of 32
                                    (default 256) */
   uint32_t encode_ctas_per_sm;  /* staged encoder CTAs per SM: 1..8, capped by shared memory (default: as many
@@ -121,9 +121,11 @@ typedef struct {
   uint32_t elem_threads;        /* threads per CTA of the per-record and per-block kernels of the drop rule,
                                    cut and layout stages: 64..1024, multiple of 32 (default 256) */
   uint32_t crc_ctas;            /* CTAs (one per SM) of the data-block checksum kernels, which run beside the
-                                   other stages on a second stream: 1..148 (default 100) */
-  uint32_t crc_warps;           /* warps per CTA of the checksum kernels: 8, 16, 24 or 32 (default 32); fewer
-                                   leave room on their SMs for the other stages' CTAs */
+                                   other stages on a second stream: the unpack's checksum pass, and the
+                                   checksums of stored compressed blocks: 1..148 (default 74) */
+  uint32_t crc_warps;           /* warps per CTA of the checksum kernels of compressed blocks: 8, 16, 24 or 32
+                                   (default 32; the unpack's checksum pass always has 16); fewer leave room
+                                   on their SMs for the other stages' CTAs */
 } luda_tuning;
 
 /* Fills the defaults (all fields 0). */

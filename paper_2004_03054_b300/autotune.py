@@ -1,7 +1,7 @@
 """Autotuner for the launch shapes of the batched pipeline (luda_tuning).
 
 A tuning decides how the pipeline's kernels split their work over CTAs: records per merge
-tile, merge CTAs per SM, decoder warps per CTA, block-walk CTA size, staged-encoder CTAs per
+tile, merge CTAs per SM, key-rebuild warps per CTA, block-walk CTA size, staged-encoder CTAs per
 SM, the CTA size of the per-record kernels and the SMs given to the checksum kernels (which
 run beside the other stages). No tuning changes an output byte, so the tuner is free to
 pick whichever is fastest for a batch.
@@ -30,16 +30,16 @@ from . import luda
 SPACE: dict[str, tuple[int, ...]] = {
     "merge_tile": (512, 1024, 2048),
     "merge_ctas_per_sm": (4, 8, 16),
-    "decode_warps": (4, 8, 16),
+    "decode_warps": (2, 4, 8),
     "walk_threads": (64, 128, 256),
     "encode_ctas_per_sm": (1, 2, 0),
     "elem_threads": (128, 256, 512),
-    "crc_ctas": (148, 120, 100, 74),
+    "crc_ctas": (120, 100, 74, 48),
     "crc_warps": (32, 16),
 }
 # The library's defaults, resolved.
-DEFAULT = {"merge_tile": 512, "merge_ctas_per_sm": 16, "decode_warps": 8, "walk_threads": 256,
-           "encode_ctas_per_sm": 0, "elem_threads": 256, "crc_ctas": 100, "crc_warps": 32}
+DEFAULT = {"merge_tile": 512, "merge_ctas_per_sm": 16, "decode_warps": 4, "walk_threads": 256,
+           "encode_ctas_per_sm": 0, "elem_threads": 256, "crc_ctas": 74, "crc_warps": 32}
 
 
 @dataclass

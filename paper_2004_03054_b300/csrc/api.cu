@@ -168,7 +168,6 @@ luda_status get_tabs(CrcTabs* out) {
 // SMs of the unpack's checksum pass on the side stream: the other half runs the records,
 // merge, drop rule and cuts beside it (74 of 148 measured best on the large job, against
 // 50, 100, 120 and 148).
-constexpr uint32_t kUnpCtas = kSms / 2;
 
 // ---- side stream --------------------------------------------------------------------------
 // Work that does not feed the main chain of a compaction runs on a second stream of the
@@ -1489,7 +1488,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     } else {
       CK(fork_join(side, 0, st, side->s));
       tr.mark(11, side->s);
-      launch_unpack_crc(ua, tabs, kUnpCtas, side->s);
+      launch_unpack_crc(ua, tabs, tuning().crc_ctas, side->s);
       tr.mark(12, side->s);
       launch_unpack_keys(ua, st);
     }
@@ -2058,7 +2057,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
                  d_hdr,         d_rec_first, d_key_first, d_chunk_first, d_chunkF, d_snap, recs,
                  d_arena,       d_errs, d_errs + n_jobs + 1, true, &d_cnt->unp_next};
       CK(fork_join(side, 0, st, side->s));
-      launch_unpack_crc(ua, tabs, kUnpCtas, side->s);
+      launch_unpack_crc(ua, tabs, tuning().crc_ctas, side->s);
       launch_unpack_keys(ua, st);
     }
     launch_plan_sanitize(recs, n_rec, d_jobs, n_jobs, d_errs, d_arena, st);

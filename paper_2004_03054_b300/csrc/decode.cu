@@ -694,13 +694,21 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   UnpWarp* W = Wall + warp;
   const uint32_t tl = smem_addr(sTr) + lane * 4u;
+  uint32_t gnext = 0;
+  if (lane == 0) gnext = atomicAdd(A.next, 1u);
   for (;;) {
-    uint32_t gg = 0;
-    if (lane == 0) gg = atomicAdd(A.next, 1u);
-    const uint64_t g = __shfl_sync(0xFFFFFFFFu, gg, 0);
+    const uint64_t g = __shfl_sync(0xFFFFFFFFu, gnext, 0);
     if (g >= A.n_blocks) break;
+    // the warp's next block is claimed now, so that the claim's round trip overlaps this block
+    if (lane == 0) gnext = atomicAdd(A.next, 1u);
     const BlockDesc b = A.blocks[g];
     if (b.ptr == nullptr) continue;
+    // the stored trailer and type byte are loaded before the fold, their round trip beside it
+    uint32_t stored = 0, btype = 0;
+    if (A.verify && lane == 0) {
+      stored = ld_u32(b.ptr + b.size + 1);
+      btype = b.ptr[b.size];
+    }
     const uint32_t nent = unp_entries(A, g);
     if (!A.verify && nent == 0) continue;
     const uint64_t rec0 = A.rec_first[g];
@@ -731,10 +739,10 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
     if (A.verify) {
       const uint32_t got = unp_join(acc, sC);
       if (lane == 0) {
-        const uint32_t want = unp_zeros(~crc_unmask(ld_u32(b.ptr + b.size + 1)), G.pad, tl, sC);
+        const uint32_t want = unp_zeros(~crc_unmask(stored), G.pad, tl, sC);
         DErr* ve = A.verr + b.job;
         if (got != want) report(ve, E_CORRUPT, A.in[b.input].local, b.off);
-        else if (b.ptr[b.size] > 1) report(ve, E_NOTSUP, A.in[b.input].local, b.off);  // 1: compressed (R4c)
+        else if (btype > 1) report(ve, E_NOTSUP, A.in[b.input].local, b.off);  // 1: compressed (R4c)
       }
     }
     if (nent == 0 || fast) {
@@ -784,7 +792,7 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
 constexpr uint32_t kPostWarps = 8;
 constexpr uint32_t kPostZ = kCZ144 + 1;  // the chunk matrices kCZ16 .. kCZ144
 constexpr uint32_t kPostSmem = (1024 + kPostZ * 1024) * 4;
-constexpr uint32_t kKeysWarps = 4;
+// k_keys: luda_tuning.decode_warps warps per CTA, rounded up to 2, 4, 8 or 16
 
 // Z_L(v) for L < 256 with the slicing table sT and the matrices sZ (Z_16 .. Z_128) in shared
 // memory: whole zero words, single zero bytes, then the matrices.
@@ -862,7 +870,7 @@ __global__ void __launch_bounds__(kPostWarps * 32) k_vcrc(const UnpArgs A, CrcTa
   }
 }
 
-__global__ void __launch_bounds__(kKeysWarps * 32) k_keys(const UnpArgs A) {
+__device__ __forceinline__ void keys_body(const UnpArgs& A) {
   const uint32_t lane = lane_id();
   const uint64_t warps = gstride() / 32;
   for (uint64_t g = gtid() / 32; g < A.n_blocks; g += warps) {
@@ -970,6 +978,13 @@ __global__ void __launch_bounds__(kKeysWarps * 32) k_keys(const UnpArgs A) {
     bad = __any_sync(0xFFFFFFFFu, bad);
     if (bad && lane == 0) report(A.errs + b.job, E_CORRUPT, A.in[b.input].local, b.off);
   }
+}
+
+// k_keys with W warps per CTA, sized for about 36 resident warps per SM (it waits on memory
+// most of the time, so resident warps count more than registers).
+template <uint32_t W>
+__global__ void __launch_bounds__(W * 32, 36 / W) k_keys(const UnpArgs A) {
+  keys_body(A);
 }
 
 // Internal-key order of two full internal keys (user key bytes, proper prefix first, then
@@ -1352,7 +1367,11 @@ void launch_value_crc(Recs recs, const uint32_t* n, uint32_t n_max, CrcTabs tabs
 
 void launch_unpack_keys(const UnpArgs& a, cudaStream_t st) {
   if (!a.n_blocks) return;
-  k_keys<<<grid_for(a.n_blocks, kKeysWarps), kKeysWarps * 32, 0, st>>>(a);
+  const uint32_t w = tuning().decode_warps;
+  if (w <= 2) k_keys<2><<<grid_for(a.n_blocks, 2), 64, 0, st>>>(a);
+  else if (w <= 4) k_keys<4><<<grid_for(a.n_blocks, 4), 128, 0, st>>>(a);
+  else if (w <= 8) k_keys<8><<<grid_for(a.n_blocks, 8), 256, 0, st>>>(a);
+  else k_keys<16><<<grid_for(a.n_blocks, 16), 512, 0, st>>>(a);
   count_launches(1);
 }
 

@@ -208,11 +208,11 @@ inline unsigned grid_for(uint64_t work, unsigned per_cta, unsigned max_ctas = kS
 struct Tuning {
   uint32_t merge_tile = 512;
   uint32_t merge_ctas_per_sm = 16;
-  uint32_t decode_warps = 8;
+  uint32_t decode_warps = 4;  // warps per CTA of the key rebuild (k_keys)
   uint32_t walk_threads = 256;
   uint32_t encode_ctas_per_sm = 0;  // 0: as many as shared memory allows
   uint32_t elem_threads = 256;
-  uint32_t crc_ctas = 100;  // about two thirds of the SMs: the other stages run beside the checksums
+  uint32_t crc_ctas = 74;  // the unpack's checksum pass: half the SMs, the other stages run beside it
   uint32_t crc_warps = 32;
 };
 const Tuning& tuning();
