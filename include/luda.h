@@ -174,7 +174,8 @@ typedef struct {
   uint64_t n_in_entries;        /* entries decoded from the inputs */
   uint64_t n_dropped;           /* entries removed by the drop rule */
   double ms_h2d, ms_device, ms_d2h;
-  /* With LUDA_F_TRACE, CUDA-event times on the call's stream (ms) and algorithmic bytes:
+  /* With LUDA_F_TRACE, CUDA-event times on the call's stream (ms) and algorithmic bytes
+   * (a batch call reports its stages, which all its jobs share, in every job's outputs):
    *  [0] sizing (footers, index, block scan, prefix sums; includes host round trips)
    *  [1] the unpack's checksum pass (CRC-32C of every input data block and the values'
    *      CRC registers; it runs on a second stream beside stages 2-4); bytes = input data

@@ -2266,10 +2266,14 @@ luda_status luda_batch_compact_device(const luda_job* jobs, uint32_t n_jobs, con
   for (uint32_t j = 0; j < n_jobs; ++j) hj[j] = host_job(jobs[j]);
   const cudaStream_t st = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
   double ms = 0;
-  luda_status rc = run_compaction(hj.data(), n_jobs, opts, st, outs, false, &ms, nullptr);
+  double sms[LUDA_N_STAGES] = {};
+  uint64_t sbytes[LUDA_N_STAGES] = {};
+  luda_status rc = run_compaction(hj.data(), n_jobs, opts, st, outs, false, &ms, nullptr, sms, sbytes);
   for (uint32_t j = 0; j < n_jobs; ++j) {
     if (rc) outs[j].status = rc;
     outs[j].ms_device = ms;
+    memcpy(outs[j].stage_ms, sms, sizeof sms);  // the call's stages, shared by its jobs
+    memcpy(outs[j].stage_bytes, sbytes, sizeof sbytes);
   }
   return rc;
 }
@@ -2334,7 +2338,9 @@ luda_status luda_batch_compact(const luda_job* jobs, uint32_t n_jobs, const luda
   }
   th.stop(st);
   double ms = 0, d2h = 0;
-  rc = run_compaction(hj.data(), n_jobs, opts, st, outs, true, &ms, &d2h);
+  double sms[LUDA_N_STAGES] = {};
+  uint64_t sbytes[LUDA_N_STAGES] = {};
+  rc = run_compaction(hj.data(), n_jobs, opts, st, outs, true, &ms, &d2h, sms, sbytes);
   const double h2d = th.ms();
   mem.put(arena);
   cudaStreamSynchronize(st);
@@ -2343,6 +2349,8 @@ luda_status luda_batch_compact(const luda_job* jobs, uint32_t n_jobs, const luda
     outs[j].ms_h2d = h2d;
     outs[j].ms_device = ms;
     outs[j].ms_d2h = d2h;
+    memcpy(outs[j].stage_ms, sms, sizeof sms);
+    memcpy(outs[j].stage_bytes, sbytes, sizeof sbytes);
   }
   return rc;
 }

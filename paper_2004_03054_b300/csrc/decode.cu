@@ -473,10 +473,12 @@ __device__ __forceinline__ uint32_t crc_byte_rep(uint32_t c, uint32_t b, uint32_
   return lds_off<0u>(tl + ((c ^ b) & 0xFFu) * 128u) ^ (c >> 8);
 }
 
-// Z_L(v) for L < 256: L mod 16 byte steps, then Z_16, Z_32, Z_64, Z_128 (sC: the chunk
-// matrices in shared memory).
+// Z_L(v) for L < 256: L mod 16 zero bytes (four at a time with the slicing tables, then
+// single bytes), then Z_16, Z_32, Z_64, Z_128 (sC: the chunk matrices in shared memory).
 __device__ __forceinline__ uint32_t unp_zeros(uint32_t v, uint32_t L, uint32_t tl, const uint32_t* sC) {
-  for (uint32_t r = L & 15u; r; --r) v = crc_byte_rep(v, 0u, tl);
+  uint32_t r = L & 15u;
+  for (; r >= 4; r -= 4) v = crc_word_rep(v, 0u, tl);
+  for (; r; --r) v = crc_byte_rep(v, 0u, tl);
   const uint32_t q = L >> 4;
 #pragma unroll
   for (uint32_t j = 0; j < 4; ++j)
