@@ -233,7 +233,7 @@ def run_ours(args, ws, rank, local):
     path_gbs = path_bytes / (ms / 1e3) / 1e9
     kernels = []
     for name, idx, what in (("k_encode_stg", 5, "data blocks written + survivors' keys and values read"),
-                            ("k_unpack (checksum pass, second stream, 74 SMs)", 1, "input data blocks read"),
+                            ("k_unpack (checksum pass, second stream, 56 SMs)", 1, "input data blocks read"),
                             ("k_keys", 2, "records and keys (latency-bound; key deltas and entry tables read)")):
         if avg[idx] <= 0 or avg[idx] < 0.1 * ms:
             continue

@@ -34,12 +34,12 @@ SPACE: dict[str, tuple[int, ...]] = {
     "walk_threads": (64, 128, 256),
     "encode_ctas_per_sm": (1, 2, 0),
     "elem_threads": (128, 256, 512),
-    "crc_ctas": (120, 100, 74, 48),
+    "crc_ctas": (100, 74, 64, 56),
     "crc_warps": (32, 16),
 }
 # The library's defaults, resolved.
 DEFAULT = {"merge_tile": 512, "merge_ctas_per_sm": 16, "decode_warps": 4, "walk_threads": 256,
-           "encode_ctas_per_sm": 0, "elem_threads": 256, "crc_ctas": 74, "crc_warps": 32}
+           "encode_ctas_per_sm": 0, "elem_threads": 256, "crc_ctas": 56, "crc_warps": 32}
 
 
 @dataclass

@@ -212,7 +212,7 @@ struct Tuning {
   uint32_t walk_threads = 256;
   uint32_t encode_ctas_per_sm = 0;  // 0: as many as shared memory allows
   uint32_t elem_threads = 256;
-  uint32_t crc_ctas = 74;  // the unpack's checksum pass: half the SMs, the other stages run beside it
+  uint32_t crc_ctas = 56;  // the unpack's checksum pass: the other stages run beside it on the rest
   uint32_t crc_warps = 32;
 };
 const Tuning& tuning();

@@ -13,7 +13,7 @@ from paper_2004_03054_b300 import luda
 def _cost(t):
     """A separable cost with a known minimum per knob (in ms)."""
     best = {"merge_tile": 2048, "merge_ctas_per_sm": 4, "decode_warps": 8, "walk_threads": 128,
-            "encode_ctas_per_sm": 1, "elem_threads": 512, "crc_ctas": 48, "crc_warps": 16}
+            "encode_ctas_per_sm": 1, "elem_threads": 512, "crc_ctas": 64, "crc_warps": 16}
     return 10.0 + sum(abs(AT.SPACE[k].index(t[k]) - AT.SPACE[k].index(best[k])) for k in AT.SPACE), best
 
 
