@@ -273,7 +273,8 @@ struct KeptStore {
   KeptRecs run{};
 };
 struct KeptTable {
-  KeptStore* store = nullptr;
+  KeptStore* store = nullptr;  // identifies the store (for unregistering); never dereferenced by a lookup
+  KeptRecs run{};              // the store's device arrays
   uint64_t size = 0;
   uint64_t first = 0, count = 0, key_first = 0, kbytes = 0;
   uint32_t max_kv = 0;
@@ -1012,6 +1013,7 @@ void kept_register(KeptStore* k, const Collected& col, uint32_t n_jobs, const lu
       const FileMeta& m = col.meta[f];
       KeptTable t;
       t.store = k;
+      t.run = k->run;
       t.size = m.size;
       t.first = first;
       t.count = m.n_entries;
@@ -1476,10 +1478,10 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
       std::vector<KeptIn> hk(N);
       uint64_t max_count = 0;
       for (uint32_t i = 0; i < N; ++i) {
-        hk[i] = KeptIn{kin[i].store->run, kin[i].first, kin[i].count, kin[i].key_first, in_rec[i], in_key[i]};
+        hk[i] = KeptIn{kin[i].run, kin[i].first, kin[i].count, kin[i].key_first, in_rec[i], in_key[i]};
         max_count = std::max(max_count, kin[i].count);
         if (kin[i].kbytes)
-          CK(cudaMemcpyAsync(d_arena + in_key[i], kin[i].store->run.arena + kin[i].key_first, kin[i].kbytes,
+          CK(cudaMemcpyAsync(d_arena + in_key[i], kin[i].run.arena + kin[i].key_first, kin[i].kbytes,
                              cudaMemcpyDeviceToDevice, st));
       }
       CK(cudaMemcpyAsync(d_kin, pin(hk.data(), sizeof(KeptIn) * N), sizeof(KeptIn) * N, cudaMemcpyHostToDevice, st));

@@ -132,3 +132,72 @@ def test_served_tree_with_kept_runs_equals_the_plain_tree():
     assert lv_k == lv_p
     assert rep_p.kept_inputs == 0
     assert rep_k.kept_inputs > 0
+
+
+def test_kept_runs_edge_cases():
+    """Calls that keep no runs (compressed output, host outputs), a job whose entries are all
+    dropped (no tables), ranged jobs (which never take kept runs), and a batch call whose
+    tables keep runs that a later job takes."""
+    K = luda.F_KEEP_DECODED
+    job = W.config1(seed=86, scale=1 / 16)
+    ins = oracle_inputs(job)
+    dev = [_dev(b) for b in ins]
+    ptrs = [(t.data_ptr(), t.numel()) for t in dev]
+    # compressed output: tables written, no run kept
+    cz, cz_tabs = _compact(ptrs, job.smallest_snapshot, K | luda.F_COMPRESS)
+    assert cz_tabs == [t.data for t in oracle.compact(ins, job.smallest_snapshot, False, T, R, BPK, TARGET,
+                                                      luda.F_COMPRESS).tables]
+    u0 = luda.kept_inputs_used()
+    _, again = _compact(_ptrs(cz), W.MAX_SEQ, K)
+    assert luda.kept_inputs_used() == u0
+    assert again == [t.data for t in oracle.compact(cz_tabs, W.MAX_SEQ, False, T, R, BPK, TARGET).tables]
+    luda.free_outputs(cz)
+    # host entry point with the flag: the same bytes, nothing kept or used
+    host = luda.compact(ins, job.smallest_snapshot, opts=luda.options(T, R, BPK, TARGET, flags=K))
+    assert host.status == 0 and host.tables == [t.data for t in oracle.compact(ins, job.smallest_snapshot, False, T, R,
+                                                                                BPK, TARGET).tables]
+    # every entry dropped: a bottommost job of deletions only writes no table
+    import numpy as np
+    rng = np.random.default_rng(7)
+    keys = [i.to_bytes(4, "big") for i in range(50)]
+    run = W._make_run(keys, np.arange(1, 51, dtype=np.uint64), np.zeros(50, np.uint8), np.zeros(50, np.int64), rng, 0)
+    dels = oracle.build_tables(run, T, R, BPK, (1 << 64) - 1).tables[0].data
+    d = _dev(dels)
+    out, tabs = _compact([(d.data_ptr(), d.numel())], W.MAX_SEQ, K, bottommost=True)
+    assert out.n_tables == 0 and tabs == []
+    luda.free_outputs(out)
+    # ranged jobs never take kept runs, and write the oracle's bytes
+    kept, kept_tabs = _compact(ptrs, job.smallest_snapshot, K)
+    lo = bytes(job.inputs[1].ukeys[:16])
+    u1 = luda.kept_inputs_used()
+    class Raw:  # the kept tables themselves (their addresses are what the runs are kept under)
+        def __init__(self, p, n):
+            self.p, self.n = p, n
+
+        def data_ptr(self):
+            return self.p
+
+        def numel(self):
+            return self.n
+
+    rc, outs = luda.batch_compact_device([([Raw(p, n) for p, n in _ptrs(kept)], W.MAX_SEQ, False, lo, None)],
+                                         luda.options(T, R, BPK, TARGET, flags=K))
+    assert rc == 0 and luda.kept_inputs_used() == u1
+    want = oracle.compact(kept_tabs, W.MAX_SEQ, False, T, R, BPK, TARGET, lo=lo)
+    assert [t.cpu().numpy().tobytes() for t in outs[0].tables] == [t.data for t in want.tables]
+    luda.free_outputs(kept)
+    # a batch call keeps the runs of all its jobs' tables; a later job takes them
+    jobs2 = [W.config1(seed=s, scale=1 / 16) for s in (87, 88)]
+    ins2 = [oracle_inputs(j) for j in jobs2]
+    rc, bouts = luda.batch_compact_device([([_dev(b) for b in x], j.smallest_snapshot, False) for j, x in
+                                           zip(jobs2, ins2)], luda.options(T, R, BPK, TARGET, flags=K),
+                                          copy_out=False)
+    assert rc == 0
+    bptrs = _ptrs(bouts[1]) + _ptrs(bouts[0])
+    host_in = [luda.device_bytes(p, n).cpu().numpy().tobytes() for p, n in bptrs]
+    u2 = luda.kept_inputs_used()
+    _, got = _compact(bptrs, W.MAX_SEQ, K)
+    assert luda.kept_inputs_used() - u2 == len(bptrs)
+    assert got == [t.data for t in oracle.compact(host_in, W.MAX_SEQ, False, T, R, BPK, TARGET).tables]
+    for o in bouts:
+        luda.free_outputs(o)
