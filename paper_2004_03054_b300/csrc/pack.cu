@@ -1263,6 +1263,14 @@ __host__ __device__ constexpr uint32_t cz_warp_smem() {
 }
 constexpr uint32_t kCzSmallMax = 65534;  // largest block for 16-bit positions (65535: none)
 constexpr uint32_t kCzWarps16 = 2, kCzWarps32 = 4;
+// Blocks up to kCzCopyMax bytes go to k_compress_copy, which reads a shared-memory copy.
+constexpr uint32_t kCzCopy = 18 * 1024;
+constexpr uint32_t kCzCopyMax = kCzCopy - 16;
+constexpr uint32_t kCzCopyWarps = 1;
+__host__ __device__ constexpr uint32_t cz_copy_smem() {
+  return kCzTab * 2 + kCzWin * 2 + (kCzWin / 32) * 4 + kCzWinOut + kCzCopy;
+}
+static_assert(cz_copy_smem() % 16 == 0, "16-byte aligned shares");
 
 // The little-endian word at in + q, from the two aligned words around it (`in` is 16-byte
 // aligned and its block's scratch share extends at least 4 bytes past any word read).
@@ -1299,7 +1307,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_compress(const Counts* __restri
   const uint64_t warps = gstride() / 32;
   for (uint64_t b = gtid() / 32; b < nb; b += warps) {
     const uint64_t n = bsz[b];
-    if (kSmall != (n <= kCzSmallMax)) continue;  // the other instance takes this block
+    if (kSmall ? (n <= kCzCopyMax || n > kCzSmallMax) : n <= kCzSmallMax) continue;  // another kernel takes it
     const uint64_t cbound = n + n / 32 + 16;
     if (Craw[b] + n > raw_cap || Cc[b] + cbound > c_cap) {
       if (lane == 0) ctype[b] = 0;
@@ -1388,6 +1396,198 @@ __global__ void __launch_bounds__(kWarps * 32) k_compress(const Counts* __restri
       const uint32_t at = x - sz, wsum = __shfl_sync(0xFFFFFFFFu, x, 31);
       for (uint32_t k = 0; k < sz; ++k) wout[at + k] = stage[k];
       __syncwarp();
+      for (uint32_t k = lane; k < wsum; k += 32) o[total + k] = wout[k];
+      total += wsum;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      const bool keep = total < n - n / 8;
+      ctype[b] = keep ? 1 : 0;
+      bsz[b] = keep ? total : n;
+      disk[b] = bsz[b] + kTrailer;
+    }
+  }
+}
+
+// The little-endian word at byte q of a block copy in shared memory (the copy extends at
+// least 8 bytes past any word read).
+__device__ __forceinline__ uint32_t ld4s(const uint8_t* in, uint32_t q) {
+  const uint32_t* a = reinterpret_cast<const uint32_t*>(in + (q & ~3u));
+  return __funnelshift_r(a[0], a[1], (q & 3u) * 8u);
+}
+
+// k_compress for blocks of at most kCzCopyMax bytes, with the same output: the warp first
+// copies its block into shared memory. The candidate search also decides, for every
+// position, whether a copy can start there (a candidate, whose first four bytes equal the
+// position's, inside the position's segment), as one bit per position; each lane then
+// parses its segment by jumping from one such position to the next, once to size its
+// elements and once, after a warp scan of the sizes, to write them into the window's
+// stream. The next step's word, hash and match are taken while a step updates the table.
+__global__ void __launch_bounds__(kCzCopyWarps * 32) k_compress_copy(const Counts* __restrict__ cnt,
+                                                                    const uint64_t* __restrict__ Craw,
+                                                                    const uint64_t* __restrict__ Cc,
+                                                                    uint64_t* __restrict__ bsz, uint64_t* __restrict__ disk,
+                                                                    const uint8_t* __restrict__ raw, uint64_t raw_cap,
+                                                                    uint8_t* __restrict__ cz, uint64_t c_cap,
+                                                                    uint8_t* __restrict__ ctype) {
+  extern __shared__ __align__(16) uint8_t s_cz[];
+  constexpr uint32_t kNone = 0xFFFFu;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  uint16_t* tab = reinterpret_cast<uint16_t*>(s_cz + warp * cz_copy_smem());
+  uint16_t* cw = tab + kCzTab;
+  uint32_t* okm = reinterpret_cast<uint32_t*>(cw + kCzWin);  // bit j of word k: position wb + 32k + j
+  uint8_t* const wout = reinterpret_cast<uint8_t*>(okm + kCzWin / 32);
+  uint8_t* const in = wout + kCzWinOut;
+  const uint32_t nb = cnt->nb;
+  const uint64_t warps = gstride() / 32;
+  for (uint64_t b = gtid() / 32; b < nb; b += warps) {
+    const uint64_t n64 = bsz[b];
+    if (n64 > kCzCopyMax) continue;  // k_compress takes it
+    const uint32_t n = uint32_t(n64);
+    const uint64_t cbound = n64 + n64 / 32 + 16;
+    if (Craw[b] + n64 > raw_cap || Cc[b] + cbound > c_cap) {
+      if (lane == 0) ctype[b] = 0;
+      continue;
+    }
+    {
+      // the block into shared memory, 16 bytes per lane and step (its scratch share is a
+      // 16-byte multiple at a 16-byte boundary)
+      const uint4* src = reinterpret_cast<const uint4*>(raw + Craw[b]);
+      uint4* dst = reinterpret_cast<uint4*>(in);
+      for (uint32_t k = lane; k < (n + 15) / 16; k += 32) dst[k] = __ldg(src + k);
+    }
+    uint8_t* o = cz + Cc[b];
+    for (uint32_t k = lane; k < kCzTab; k += 32) tab[k] = uint16_t(kNone);
+    uint32_t total = 0;  // stream bytes so far: the length header, then the segments
+    {
+      uint32_t v = n;
+      while (v >= 0x80) {
+        if (lane == 0) o[total] = uint8_t(v | 0x80);
+        v >>= 7;
+        ++total;
+      }
+      if (lane == 0) o[total] = uint8_t(v);
+      ++total;
+    }
+    __syncwarp();
+    for (uint32_t wb = 0; wb < n; wb += kCzWin) {
+      const uint32_t we = wb + kCzWin < n ? wb + kCzWin : n;
+      uint32_t p = wb + lane;
+      bool valid = p + 4 <= n;
+      uint32_t w = valid ? ld4s(in, p) : 0u;
+      uint32_t h = valid ? (w * 2654435761u) >> 20 : kCzTab + lane;
+      uint32_t m = __match_any_sync(0xFFFFFFFFu, h);
+      for (uint32_t base = wb; base < we; base += 32) {
+        const uint32_t pn = p + 32;
+        const bool vn = base + 32 < we && pn + 4 <= n;
+        const uint32_t wn = vn ? ld4s(in, pn) : 0u;
+        const uint32_t hn = vn ? (wn * 2654435761u) >> 20 : kCzTab + lane;
+        const uint32_t mn = __match_any_sync(0xFFFFFFFFu, hn);
+        const uint32_t lower = m & ((1u << lane) - 1u);
+        const uint32_t src = lower ? 31u - __clz(lower) : lane;
+        const uint32_t wl = __shfl_sync(0xFFFFFFFFu, w, src);
+        uint32_t c = kNone;
+        if (valid) c = lower ? base + src : uint32_t(tab[h]);
+        __syncwarp();
+        if (valid && (m >> lane) == 1u) tab[h] = uint16_t(p);
+        __syncwarp();
+        const uint32_t send = wb + ((p - wb) & ~63u) + 64u;  // the end of p's segment
+        const bool ok = valid && p < we && c != kNone && p + 4 <= (send < n ? send : n) &&
+                        (lower ? wl : ld4s(in, c)) == w;
+        if (p < we) cw[p - wb] = uint16_t(c);
+        const uint32_t bits = __ballot_sync(0xFFFFFFFFu, ok);
+        if (lane == 0) okm[(base - wb) >> 5] = bits;
+        p = pn;
+        valid = vn;
+        w = wn;
+        h = hn;
+        m = mn;
+      }
+      __syncwarp();
+      // this lane's segment [s0, e): sized, then (after the scan) written at its offset
+      const uint32_t s0 = wb + 64u * lane;
+      const uint32_t e = s0 + 64u < n ? s0 + 64u : n;
+      uint64_t mask = 0;
+      if (s0 < n) {
+        const uint32_t k0 = (s0 - wb) >> 5;
+        mask = uint64_t(okm[k0]) | (uint64_t(okm[k0 + 1]) << 32);
+        if (e - s0 < 64) mask &= (1ull << (e - s0)) - 1;  // words past the window are stale
+      }
+      uint32_t at = 0, sz = 0;
+      for (int pass = 0; pass < 2; ++pass) {
+        uint8_t* q = wout + at;
+        uint32_t put = 0;
+        auto literal = [&](uint32_t from, uint32_t to) {
+          const uint32_t len = to - from, v = len - 1;
+          if (v < 60) {
+            if (pass) q[put] = uint8_t(v << 2);
+            put += 1;
+          } else {
+            if (pass) {
+              q[put] = uint8_t(60u << 2);
+              q[put + 1] = uint8_t(v);
+            }
+            put += 2;
+          }
+          if (pass) {
+            uint32_t k = from;
+            for (; k + 4 <= to; k += 4) {
+              const uint32_t x = ld4s(in, k);
+              q[put] = uint8_t(x);
+              q[put + 1] = uint8_t(x >> 8);
+              q[put + 2] = uint8_t(x >> 16);
+              q[put + 3] = uint8_t(x >> 24);
+              put += 4;
+            }
+            for (; k < to; ++k) q[put++] = in[k];
+          } else {
+            put += len;
+          }
+        };
+        if (s0 < n) {
+          uint32_t i = s0, lit = s0;
+          while (i < e) {
+            const uint32_t oi = i - s0;
+            const uint64_t rem = mask >> oi << oi;  // copies can start at these positions >= i
+            if (!rem) break;
+            i = s0 + uint32_t(__ffsll(static_cast<long long>(rem)) - 1);
+            const uint32_t c = cw[i - wb];
+            uint32_t L = 4;
+            while (i + L < e && in[c + L] == in[i + L]) ++L;
+            if (i > lit) literal(lit, i);
+            const uint32_t off = i - c;
+            if (L <= 11 && off < 2048) {
+              if (pass) {
+                q[put] = uint8_t(1u | (L - 4) << 2 | (off >> 8) << 5);
+                q[put + 1] = uint8_t(off);
+              }
+              put += 2;
+            } else {
+              if (pass) {
+                q[put] = uint8_t(2u | (L - 1) << 2);
+                q[put + 1] = uint8_t(off);
+                q[put + 2] = uint8_t(off >> 8);
+              }
+              put += 3;
+            }
+            i += L;
+            lit = i;
+          }
+          if (e > lit) literal(lit, e);
+        }
+        if (pass == 0) {
+          sz = put;
+          uint32_t x = sz;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= uint32_t(d)) x += y;
+          }
+          at = x - sz;
+        }
+      }
+      __syncwarp();
+      const uint32_t wsum = __shfl_sync(0xFFFFFFFFu, at + sz, 31);
       for (uint32_t k = lane; k < wsum; k += 32) o[total + k] = wout[k];
       total += wsum;
       __syncwarp();
@@ -1987,13 +2187,17 @@ void launch_compress(PackCz z, Counts* cnt, uint32_t cap, uint64_t* bsz, uint64_
   if (!cap) return;
   // blocks below 64 KiB (nearly all) with 16-bit positions, the others with 32-bit ones
   constexpr uint32_t s16 = kCzWarps16 * cz_warp_smem<uint16_t>(), s32 = kCzWarps32 * cz_warp_smem<uint32_t>();
+  constexpr uint32_t scp = kCzCopyWarps * cz_copy_smem();
+  smem_optin(k_compress_copy, scp);
   smem_optin(k_compress<uint16_t, kCzWarps16>, s16);
   smem_optin(k_compress<uint32_t, kCzWarps32>, s32);
+  k_compress_copy<<<grid_for(uint64_t(cap) * 32, kCzCopyWarps * 32), kCzCopyWarps * 32, scp, st>>>(
+      cnt, z.Craw, z.Cc, bsz, disk, z.raw, z.raw_cap, z.cz, z.c_cap, z.ctype);
   k_compress<uint16_t, kCzWarps16><<<grid_for(uint64_t(cap) * 32, kCzWarps16 * 32), kCzWarps16 * 32, s16, st>>>(
       cnt, z.Craw, z.Cc, bsz, disk, z.raw, z.raw_cap, z.cz, z.c_cap, z.ctype);
   k_compress<uint32_t, kCzWarps32><<<grid_for(uint64_t(cap) * 32, kCzWarps32 * 32), kCzWarps32 * 32, s32, st>>>(
       cnt, z.Craw, z.Cc, bsz, disk, z.raw, z.raw_cap, z.cz, z.c_cap, z.ctype);
-  count_launches(2);
+  count_launches(3);
 }
 
 void launch_place(PackCz z, Counts* cnt, uint32_t cap, const uint32_t* blk_file, const FileDesc* files,
