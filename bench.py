@@ -127,8 +127,8 @@ class ClockSampler:
 # traffic grows with the entries; profiles/dram_traffic_cfg3_quarter.md), with the SHA-256
 # of the CUDA sources at the time: once a source changes the numbers no longer describe
 # the call and the bench reports null.
-_CALL_TRAFFIC = (4 * 1.059e9, "96a1008427c5d429181c5bb0bb86a35d6c612d768fe46ef8ab35264ad09b2363")
-_KERNEL_TRAFFIC = {"k_encode_stg": 4 * 475.4e6, "k_unpack": 4 * 267.9e6, "k_keys": 4 * 45.0e6}
+_CALL_TRAFFIC = (4 * 1.059e9, "7321c67130d1a0ac9937bbf6222bd17824bea4e94cde3cba8ac3bda749e8f7a5")
+_KERNEL_TRAFFIC = {"k_encode_stg": 4 * 475.5e6, "k_unpack": 4 * 267.9e6, "k_keys": 4 * 43.8e6}
 
 
 def _sources_digest():
