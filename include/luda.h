@@ -126,6 +126,12 @@ typedef struct {
   uint32_t crc_warps;           /* warps per CTA of the checksum kernels of compressed blocks: 8, 16, 24 or 32
                                    (default 32; the unpack's checksum pass always has 16); fewer leave room
                                    on their SMs for the other stages' CTAs */
+  uint32_t h2d_ranges;          /* luda_compact (host buffers) only: key ranges the inputs are copied in, so
+                                   that the tables of the first ranges are compacted and copied back while
+                                   later ranges' input bytes are still arriving (§III-D); 1 = one copy in,
+                                   one compaction, one copy out; 2..64; default: one range per
+                                   max(96 MiB, target_file_size) of input, at most 16. The tables are
+                                   byte-identical for every value */
 } luda_tuning;
 
 /* Fills the defaults (all fields 0). */
@@ -196,7 +202,18 @@ typedef struct {
 /* ---- single compaction job ------------------------------------------------------------
  * luda_compact: inputs[].data are host pointers (pinned memory gives the fastest copies);
  *   the library copies them to the device (timed in ms_h2d), compacts, and copies the new
- *   tables back into library-owned pinned host memory (ms_d2h).
+ *   tables back into library-owned pinned host memory (ms_d2h). A job of two or more
+ *   transfer ranges (luda_tuning.h2d_ranges; by default one per 96 MiB or the target size
+ *   of input, so jobs of 192 MiB and more) overlaps the two directions (§III-D): the footers and
+ *   index blocks are copied and parsed first, the data blocks follow range by range (user
+ *   keys chosen from the index keys so that the ranges hold about equal bytes), each range
+ *   is compacted once its blocks have arrived and its finished tables are copied back
+ *   while later ranges arrive. The last table of a range, back to one that starts a new
+ *   user key, is compacted again with the next range, so the tables are byte-identical to
+ *   those of the job in one piece. ms_device then sums the ranges' device times (and
+ *   stage_ms their stages); ms_h2d and ms_d2h span each direction's copies. A job whose
+ *   footers or index blocks do not parse, or whose index keys are out of order, runs in
+ *   one piece (which reports the error).
  * luda_compact_device: inputs[].data are device pointers on opts->stream; the new tables
  *   stay on the device in one library-owned allocation.
  * `level` is the output level (recorded only); `smallest_snapshot` is the oldest sequence

@@ -93,6 +93,7 @@ bool luda::tuning_valid(const luda_tuning* t) {
     bad = "elem_threads";
   else if (t->crc_ctas > kSms) bad = "crc_ctas";
   else if (t->crc_warps && (t->crc_warps < 8 || t->crc_warps > 32 || t->crc_warps % 8)) bad = "crc_warps";
+  else if (t->h2d_ranges > 64) bad = "h2d_ranges";
   if (bad) set_detail("invalid tuning: %s", bad);
   return bad == nullptr;
 }
@@ -107,6 +108,7 @@ luda::TuningScope::TuningScope(const luda_tuning* t) : saved_(t_tuning) {
   if (t->elem_threads) t_tuning.elem_threads = t->elem_threads;
   if (t->crc_ctas) t_tuning.crc_ctas = t->crc_ctas;
   if (t->crc_warps) t_tuning.crc_warps = t->crc_warps;
+  if (t->h2d_ranges) t_tuning.h2d_ranges = t->h2d_ranges;
 }
 
 luda::TuningScope::~TuningScope() { t_tuning = saved_; }
@@ -332,6 +334,7 @@ struct Holder {
   void* ctx = nullptr;
   uint8_t* pinned = nullptr;
   size_t pinned_cap = 0;
+  std::vector<std::pair<uint8_t*, size_t>> more_pinned;  // further pinned buffers of one result
   KeptStore* kept = nullptr;  // the kept run of the tables (LUDA_F_KEEP_DECODED)
 };
 
@@ -376,6 +379,7 @@ void holder_release(Holder* h) {
     else cudaFree(h->dev);
   }
   pinned_put(h->pinned, h->pinned_cap);
+  for (auto& pr : h->more_pinned) pinned_put(pr.first, pr.second);
   delete h;
 }
 
@@ -436,7 +440,9 @@ luda_status err_status(const DErr& e, uint32_t job, uint32_t n_jobs) {
 // through one pinned buffer per host thread instead, so that a round trip is a few
 // asynchronous copies and one synchronisation. take() hands out 16-byte aligned pieces
 // until reset(); a request that does not fit returns NULL (the caller then uses its own
-// memory) and the buffer grows at the next reset.
+// memory) and the buffer grows at the next reset. The buffer is mapped into the device's
+// address space: stage_copy moves a piece with a small kernel instead of a copy engine, so
+// that a round trip does not queue behind bulk copies another stream has on the engines.
 class HostStage {
  public:
   ~HostStage() {
@@ -450,9 +456,11 @@ class HostStage {
       p_ = nullptr;
       cap_ = 0;
       void* q = nullptr;
-      if (cudaHostAlloc(&q, want_, cudaHostAllocDefault) == cudaSuccess) {
+      void* d = nullptr;
+      if (cudaHostAlloc(&q, want_, cudaHostAllocMapped | cudaHostAllocPortable) == cudaSuccess) {
         p_ = static_cast<uint8_t*>(q);
         cap_ = want_;
+        dev_ = cudaHostGetDevicePointer(&d, q, 0) == cudaSuccess ? static_cast<uint8_t*>(d) : nullptr;
       }
     }
   }
@@ -465,12 +473,50 @@ class HostStage {
     off_ = o + n;
     return p_ + o;
   }
+  // The device address of host bytes [q, q + n) when they lie in the buffer, else NULL.
+  uint8_t* dev_of(const void* q, size_t n) const {
+    const uint8_t* b = static_cast<const uint8_t*>(q);
+    if (!dev_ || !p_ || b < p_ || n > cap_ || size_t(b - p_) > cap_ - n) return nullptr;
+    return dev_ + (b - p_);
+  }
 
  private:
+  uint8_t* dev_ = nullptr;
   uint8_t* p_ = nullptr;
   size_t cap_ = 0, off_ = 0, want_ = 1u << 20;
 };
 thread_local HostStage t_stage;
+
+// A copy between the device and the host stage by one small kernel (16-, 4- or 1-byte
+// words, whichever the addresses and size allow).
+__global__ void k_stage_copy(uint8_t* __restrict__ dst, const uint8_t* __restrict__ src, uint64_t n) {
+  const uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x, step = uint64_t(gridDim.x) * blockDim.x;
+  const uintptr_t a = uintptr_t(dst) | uintptr_t(src) | uintptr_t(n);
+  if ((a & 15) == 0) {
+    for (uint64_t i = i0; i < n / 16; i += step) reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+  } else if ((a & 3) == 0) {
+    for (uint64_t i = i0; i < n / 4; i += step)
+      reinterpret_cast<uint32_t*>(dst)[i] = reinterpret_cast<const uint32_t*>(src)[i];
+  } else {
+    for (uint64_t i = i0; i < n; i += step) dst[i] = src[i];
+  }
+}
+
+// cudaMemcpyAsync, except that a host-to-device or device-to-host copy of at most 1 MiB
+// whose host side lies in this thread's stage runs as k_stage_copy on the stream.
+cudaError_t stage_copy(void* dst, const void* src, size_t n, cudaMemcpyKind kind, cudaStream_t st) {
+  uint8_t* hd = nullptr;
+  if (n && n <= (1u << 20)) {
+    if (kind == cudaMemcpyHostToDevice && (hd = t_stage.dev_of(src, n))) src = hd;
+    else if (kind == cudaMemcpyDeviceToHost && (hd = t_stage.dev_of(dst, n))) dst = hd;
+  }
+  if (!hd) return cudaMemcpyAsync(dst, src, n, kind, st);
+  const uint64_t words = (n + 15) / 16;
+  const unsigned grid = unsigned(std::min<uint64_t>(64, (words + 255) / 256));
+  k_stage_copy<<<grid, 256, 0, st>>>(static_cast<uint8_t*>(dst), static_cast<const uint8_t*>(src), n);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 // ---- the pack stages, shared by compaction and build --------------------------------------
 struct PackBufs {
@@ -719,19 +765,19 @@ luda_status collect(const Counts* d_cnt, const JobDev* d_jobs, const DErr* d_err
   c->jobs.resize(n_jobs);
   c->errs.resize(ne);
   if (staged) {
-    CK(cudaMemcpyAsync(h_cnt, d_cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h_jobs, d_jobs, sizeof(JobDev) * n_jobs, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h_errs, d_errs, sizeof(DErr) * ne, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h_meta, b.meta, sizeof(FileMeta) * spec_m, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(h_keys, b.keybuf, spec_k, cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(h_cnt, d_cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(h_jobs, d_jobs, sizeof(JobDev) * n_jobs, cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(h_errs, d_errs, sizeof(DErr) * ne, cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(h_meta, b.meta, sizeof(FileMeta) * spec_m, cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(h_keys, b.keybuf, spec_k, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     c->cnt = *h_cnt;
     memcpy(c->jobs.data(), h_jobs, sizeof(JobDev) * n_jobs);
     memcpy(c->errs.data(), h_errs, sizeof(DErr) * ne);
   } else {
-    CK(cudaMemcpyAsync(&c->cnt, d_cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(c->jobs.data(), d_jobs, sizeof(JobDev) * n_jobs, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(c->errs.data(), d_errs, sizeof(DErr) * ne, cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(&c->cnt, d_cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(c->jobs.data(), d_jobs, sizeof(JobDev) * n_jobs, cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(c->errs.data(), d_errs, sizeof(DErr) * ne, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
   for (uint32_t j = 0; j < n_jobs; ++j)
@@ -745,8 +791,8 @@ luda_status collect(const Counts* d_cnt, const JobDev* d_jobs, const DErr* d_err
     memcpy(c->keys.data(), h_keys, c->cnt.key_bytes);
     return LUDA_OK;
   }
-  CK(cudaMemcpyAsync(c->meta.data(), b.meta, sizeof(FileMeta) * c->cnt.nf, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(c->keys.data(), b.keybuf, c->cnt.key_bytes, cudaMemcpyDeviceToHost, st));
+  CK(stage_copy(c->meta.data(), b.meta, sizeof(FileMeta) * c->cnt.nf, cudaMemcpyDeviceToHost, st));
+  CK(stage_copy(c->keys.data(), b.keybuf, c->cnt.key_bytes, cudaMemcpyDeviceToHost, st));
   return LUDA_OK;
 }
 
@@ -1037,7 +1083,8 @@ struct KeptGuard {
 // outs[j] hold device (or, with host_out, pinned host) tables.
 luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_options* o, cudaStream_t st,
                            luda_outputs* outs, bool host_out, double* ms_device, double* ms_d2h,
-                           double* stage_ms = nullptr, uint64_t* stage_bytes = nullptr, AdmitGate* gate = nullptr) {
+                           double* stage_ms = nullptr, uint64_t* stage_bytes = nullptr, AdmitGate* gate = nullptr,
+                           std::vector<uint32_t>* blk_nrec = nullptr) {
   Fmt fmt;
   luda_status rc = opts_check(o, &fmt);
   if (rc) return rc;
@@ -1161,14 +1208,14 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   CK(cudaMemsetAsync(d_errs, 0, sizeof(DErr) * 2 * (n_jobs + 1), st));
   CK(cudaMemsetAsync(d_cnt, 0, sizeof(Counts), st));
   if (ranged) {
-    CK(cudaMemcpyAsync(d_ranges, pin(hranges.data(), sizeof(JobRange) * n_jobs), sizeof(JobRange) * n_jobs,
+    CK(stage_copy(d_ranges, pin(hranges.data(), sizeof(JobRange) * n_jobs), sizeof(JobRange) * n_jobs,
                        cudaMemcpyHostToDevice, st));
     if (!hbounds.empty())
-      CK(cudaMemcpyAsync(d_bounds, pin(hbounds.data(), hbounds.size()), hbounds.size(), cudaMemcpyHostToDevice, st));
+      CK(stage_copy(d_bounds, pin(hbounds.data(), hbounds.size()), hbounds.size(), cudaMemcpyHostToDevice, st));
   }
   DInput* hin_pin = static_cast<DInput*>(hs.take(sizeof(DInput) * (N + 1)));
   if (N)
-    CK(cudaMemcpyAsync(d_in, pin(hin.data(), sizeof(DInput) * N), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
+    CK(stage_copy(d_in, pin(hin.data(), sizeof(DInput) * N), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
   // the index blocks' checksums run on the side stream (their errors, like the data blocks',
   // take precedence when the results are collected) while the host sizes the job
   Side* side = nullptr;
@@ -1179,7 +1226,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     launch_index_crc(d_msgs, N, d_errs + n_jobs + 1, tabs, side->s);
     launch_footers_finish(d_in, N, d_errs, st);
     CK(cudaGetLastError());
-    if (N) CK(cudaMemcpyAsync(hin_pin ? hin_pin : hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
+    if (N) CK(stage_copy(hin_pin ? hin_pin : hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (N && hin_pin) memcpy(hin.data(), hin_pin, sizeof(DInput) * N);
   }
@@ -1197,8 +1244,8 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   }
   const uint32_t NB = uint32_t(NB64);
   if (N) {
-    CK(cudaMemcpyAsync(d_in, pin(hin.data(), sizeof(DInput) * N), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(d_in_blk_first, pin(in_blk_first.data(), sizeof(uint32_t) * (N + 1)),
+    CK(stage_copy(d_in, pin(hin.data(), sizeof(DInput) * N), sizeof(DInput) * N, cudaMemcpyHostToDevice, st));
+    CK(stage_copy(d_in_blk_first, pin(in_blk_first.data(), sizeof(uint32_t) * (N + 1)),
                        sizeof(uint32_t) * (N + 1), cudaMemcpyHostToDevice, st));
   }
 
@@ -1276,16 +1323,23 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
       p_comp = comp;
       p_nch = &n_chunks;
     }
-    CK(cudaMemcpyAsync(p_rec, d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(p_key, d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
-    if (n_jobs) CK(cudaMemcpyAsync(p_err, d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(p_kv, &d_cnt->max_kv, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    if (N) CK(cudaMemcpyAsync(p_link, d_link, N, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(p_comp, &d_cnt->comp_blocks, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(p_comp + 1, &d_cnt->comp_bytes, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(p_nch, d_chunk_first + NB, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(p_rec, d_in_rec, sizeof(uint32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(p_key, d_in_key, sizeof(uint64_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+    if (n_jobs) CK(stage_copy(p_err, d_errs, sizeof(DErr) * n_jobs, cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(p_kv, &d_cnt->max_kv, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (N) CK(stage_copy(p_link, d_link, N, cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(p_comp, &d_cnt->comp_blocks, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(p_comp + 1, &d_cnt->comp_bytes, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(stage_copy(p_nch, d_chunk_first + NB, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    uint32_t* p_nrec = nullptr;
+    if (blk_nrec) {  // every block's entry count (0 for blocks a ranged job leaves unread)
+      blk_nrec->resize(NB);
+      p_nrec = static_cast<uint32_t*>(hs.take(sizeof(uint32_t) * NB));
+      if (NB) CK(stage_copy(p_nrec ? p_nrec : blk_nrec->data(), d_nrec, sizeof(uint32_t) * NB, cudaMemcpyDeviceToHost, st));
+    }
     if (!contents) tr.mark(3, st);
     CK(cudaStreamSynchronize(st));
+    if (p_nrec && NB) memcpy(blk_nrec->data(), p_nrec, sizeof(uint32_t) * NB);
     if (pinned) {
       memcpy(in_rec.data(), p_rec, sizeof(uint32_t) * (N + 1));
       memcpy(in_key.data(), p_key, sizeof(uint64_t) * (N + 1));
@@ -1353,7 +1407,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
                         side->s);
     CK(cudaEventRecord(side->ev[1], side->s));
     CK((exclusive_scan<uint64_t, uint64_t>(d_ures, d_uoff, NB, nullptr, d_tmpB, st)));
-    CK(cudaMemcpyAsync(d_cblocks, d_blocks, sizeof(BlockDesc) * NB, cudaMemcpyDeviceToDevice, st));
+    CK(stage_copy(d_cblocks, d_blocks, sizeof(BlockDesc) * NB, cudaMemcpyDeviceToDevice, st));
     launch_decompress(d_blocks, NB, d_ulen, d_uoff, d_dec, comp_bytes, d_cblocks, d_in, d_errs, st);
     d_cb = d_cblocks;
     if ((rc = size_pass(true))) return rc;
@@ -1454,11 +1508,11 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     }
   } out_guard{mem, d_out, &out_owned};
 
-  CK(cudaMemcpyAsync(&d_cnt->n_rec, pin(&n_rec, sizeof n_rec), sizeof n_rec, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_jobs, pin(hjobs.data(), sizeof(JobDev) * n_jobs), sizeof(JobDev) * n_jobs,
+  CK(stage_copy(&d_cnt->n_rec, pin(&n_rec, sizeof n_rec), sizeof n_rec, cudaMemcpyHostToDevice, st));
+  CK(stage_copy(d_jobs, pin(hjobs.data(), sizeof(JobDev) * n_jobs), sizeof(JobDev) * n_jobs,
                      cudaMemcpyHostToDevice, st));
   if (!spans.empty())
-    CK(cudaMemcpyAsync(d_spans, pin(spans.data(), sizeof(MergeSpan) * spans.size()), sizeof(MergeSpan) * spans.size(),
+    CK(stage_copy(d_spans, pin(spans.data(), sizeof(MergeSpan) * spans.size()), sizeof(MergeSpan) * spans.size(),
                        cudaMemcpyHostToDevice, st));
 
   tr.mark(4, st);
@@ -1481,10 +1535,10 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
         hk[i] = KeptIn{kin[i].run, kin[i].first, kin[i].count, kin[i].key_first, in_rec[i], in_key[i]};
         max_count = std::max(max_count, kin[i].count);
         if (kin[i].kbytes)
-          CK(cudaMemcpyAsync(d_arena + in_key[i], kin[i].run.arena + kin[i].key_first, kin[i].kbytes,
+          CK(stage_copy(d_arena + in_key[i], kin[i].run.arena + kin[i].key_first, kin[i].kbytes,
                              cudaMemcpyDeviceToDevice, st));
       }
-      CK(cudaMemcpyAsync(d_kin, pin(hk.data(), sizeof(KeptIn) * N), sizeof(KeptIn) * N, cudaMemcpyHostToDevice, st));
+      CK(stage_copy(d_kin, pin(hk.data(), sizeof(KeptIn) * N), sizeof(KeptIn) * N, cudaMemcpyHostToDevice, st));
       launch_kept_gather(d_kin, N, max_count, recs, st);
       g_kept_used += N;
     } else {
@@ -1542,7 +1596,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
     if (gate) gate->copy_begin(1);
     t.start(st);
     if (col.cnt.out_bytes)
-      if (cudaMemcpyAsync(h->pinned, d_out, col.cnt.out_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+      if (stage_copy(h->pinned, d_out, col.cnt.out_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
         if (gate) gate->copy_end(1);
         holder_release(h);
         return cuda_fail(cudaGetLastError(), "copy of the new tables to the host");
@@ -2112,6 +2166,468 @@ luda_status luda::warm_thread() {
   return LUDA_OK;
 }
 
+namespace {
+
+// ---- luda_compact with the inputs copied in key ranges (§III-D) ---------------------------
+// The job is cut at user keys into ranges whose input bytes are about equal. The inputs'
+// footers and index blocks are copied first and parsed on the device (the same kernels as
+// the sizing stage); every input's data blocks are then copied range after range on one
+// copy stream. Range r is compacted as a ranged job (R13) as soon as its blocks are on the
+// device, and its finished tables go back to the host on a second copy stream while later
+// ranges' input bytes still arrive. A table is finished when it was cut at the target
+// size: the last table of a range (and every table back to a table that starts a new user
+// key) is held back and compacted again with the next range, whose lower bound becomes
+// that table's first user key. A compaction cuts its tables greedily from its first
+// survivor and the drop rule works per user key, so every emitted table is byte for byte
+// the table the whole compaction writes at that place.
+struct Xfer {
+  int dev = -1;
+  cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t ev_in[65] = {};  // range r's input bytes have arrived
+  cudaEvent_t ev_run = nullptr;  // a range's tables are written (call stream)
+  cudaEvent_t t[4] = {};  // timing: copies in start / end, copies out start / end
+};
+thread_local Xfer t_xfer;
+
+luda_status get_xfer(Xfer** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    set_detail("no usable CUDA device");
+    return LUDA_ERR_CUDA;
+  }
+  Xfer& x = t_xfer;
+  if (x.dev != dev) {
+    if (x.in) {
+      cudaStreamDestroy(x.in);
+      cudaStreamDestroy(x.out);
+      for (cudaEvent_t& e : x.ev_in) cudaEventDestroy(e);
+      cudaEventDestroy(x.ev_run);
+      for (cudaEvent_t& e : x.t) cudaEventDestroy(e);
+    }
+    x = Xfer{};
+    if (cudaStreamCreateWithFlags(&x.in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&x.out, cudaStreamNonBlocking) != cudaSuccess) {
+      set_detail("cudaStreamCreateWithFlags failed");
+      return LUDA_ERR_CUDA;
+    }
+    bool ok = cudaEventCreateWithFlags(&x.ev_run, cudaEventDisableTiming) == cudaSuccess;
+    for (cudaEvent_t& e : x.ev_in) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    for (cudaEvent_t& e : x.t) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    if (!ok) {
+      set_detail("cudaEventCreateWithFlags failed");
+      return LUDA_ERR_CUDA;
+    }
+    x.dev = dev;
+  }
+  *out = &x;
+  return LUDA_OK;
+}
+
+// Bytewise order of two user keys (a proper prefix first), as cmp_user_keys on the device.
+int cmp_user_host(const uint8_t* a, uint64_t na, const uint8_t* b, uint64_t nb) {
+  const uint64_t m = na < nb ? na : nb;
+  const int c = m ? memcmp(a, b, m) : 0;
+  if (c) return c < 0 ? -1 : 1;
+  return na == nb ? 0 : (na < nb ? -1 : 1);
+}
+
+// Bulk copies go in pieces of this size, so that the compaction's own small copies (its
+// sizing round trip, the results) wait behind one piece at most, not behind a whole table.
+constexpr uint64_t kXferPiece = 4ull << 20;
+
+bool copy_pieces(void* dst, const void* src, uint64_t n, cudaMemcpyKind kind, cudaStream_t s) {
+  for (uint64_t o = 0; o < n; o += kXferPiece)
+    if (cudaMemcpyAsync(static_cast<uint8_t*>(dst) + o, static_cast<const uint8_t*>(src) + o,
+                        std::min(kXferPiece, n - o), kind, s) != cudaSuccess)
+      return false;
+  return true;
+}
+
+// One data block of an input as its index lists it: handle and index key (in the caller's
+// host copy of the input).
+struct PlanBlock {
+  uint64_t off, size;
+  const uint8_t* ukey;  // the index key's user key
+  uint32_t ulen;
+};
+
+// The inputs' footers and index blocks copied to their places in the arena and parsed on
+// the device; on return blocks[i] lists input i's data blocks and idx_off[i] its index
+// block's offset. False (and nothing reported) when a footer, an index block or a handle
+// is not as a well-formed table has it, or the index keys are not in order: the caller
+// then runs the whole job in one piece, which reports the error.
+bool plan_inputs(const luda_input* inputs, uint32_t N, uint8_t* const* dptr, cudaStream_t st, const DevMem& mem,
+                 const CrcTabs& tabs, std::vector<std::vector<PlanBlock>>* blocks, std::vector<uint64_t>* idx_off) {
+  std::vector<DInput> hin(N);
+  for (uint32_t i = 0; i < N; ++i) {
+    if (inputs[i].size < kFooter) return false;
+    hin[i] = DInput{};
+    hin[i].data = dptr[i];
+    hin[i].size = inputs[i].size;
+    hin[i].local = i;
+  }
+  Layout L;
+  DInput* d_in;
+  DErr* d_errs;
+  CrcMsg* d_msgs;
+  uint32_t* d_first;
+  auto lay = [&](Layout& l) {
+    d_in = l.take<DInput>(N + 1);
+    d_errs = l.take<DErr>(4);
+    d_msgs = l.take<CrcMsg>(N + 1);
+    d_first = l.take<uint32_t>(N + 1);
+  };
+  lay(L);
+  uint8_t* buf = static_cast<uint8_t*>(mem.get(L.off));
+  if (!buf) return false;
+  L = Layout{};
+  L.base = buf;
+  lay(L);
+  struct Put {
+    const DevMem& m;
+    std::vector<void*> ps;
+    ~Put() {
+      for (void* p : ps) m.put(p);
+    }
+  } put{mem, {buf}};
+  DErr herr[4];
+  bool ok = cudaMemsetAsync(d_errs, 0, sizeof(DErr) * 4, st) == cudaSuccess;
+  for (uint32_t i = 0; ok && i < N; ++i)
+    ok = cudaMemcpyAsync(dptr[i] + inputs[i].size - kFooter, inputs[i].data + inputs[i].size - kFooter, kFooter,
+                         cudaMemcpyHostToDevice, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  if (!ok) return false;
+  launch_footers_read(d_in, N, d_errs, d_msgs, st);
+  ok = cudaMemcpyAsync(hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+       cudaMemcpyAsync(herr, d_errs, sizeof herr, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+       cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok || herr[0].code) return false;
+  // the index blocks with their trailers (checksum and type byte)
+  for (uint32_t i = 0; ok && i < N; ++i) {
+    const uint64_t n = std::min<uint64_t>(hin[i].idx_size + 5, inputs[i].size - kFooter - hin[i].idx_off);
+    ok = cudaMemcpyAsync(dptr[i] + hin[i].idx_off, inputs[i].data + hin[i].idx_off, n, cudaMemcpyHostToDevice,
+                         st) == cudaSuccess;
+  }
+  if (!ok) return false;
+  launch_index_crc(d_msgs, N, d_errs + 2, tabs, st);
+  launch_footers_finish(d_in, N, d_errs, st);
+  ok = cudaMemcpyAsync(hin.data(), d_in, sizeof(DInput) * N, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+       cudaMemcpyAsync(herr, d_errs, sizeof herr, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+       cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok || herr[0].code || herr[2].code) return false;
+  std::vector<uint32_t> first(N + 1, 0);
+  for (uint32_t i = 0; i < N; ++i) {
+    if (!hin[i].nblk) return false;
+    hin[i].blk_first = first[i];
+    first[i + 1] = first[i] + hin[i].nblk;
+  }
+  const uint32_t NB = first[N];
+  BlockDesc* d_blocks = static_cast<BlockDesc*>(mem.get(sizeof(BlockDesc) * (NB + 1)));
+  if (!d_blocks) return false;
+  put.ps.push_back(d_blocks);
+  std::vector<BlockDesc> hb(NB);
+  ok = cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+       cudaMemcpyAsync(d_first, first.data(), sizeof(uint32_t) * (N + 1), cudaMemcpyHostToDevice, st) == cudaSuccess;
+  if (!ok) return false;
+  launch_index_entries(d_in, N, d_first, NB, d_blocks, d_errs, st, nullptr, nullptr);
+  ok = cudaMemcpyAsync(hb.data(), d_blocks, sizeof(BlockDesc) * NB, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+       cudaMemcpyAsync(herr, d_errs, sizeof herr, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+       cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok || herr[0].code) return false;
+  blocks->assign(N, {});
+  idx_off->assign(N, 0);
+  for (uint32_t i = 0; i < N; ++i) {
+    (*idx_off)[i] = hin[i].idx_off;
+    std::vector<PlanBlock>& v = (*blocks)[i];
+    v.reserve(hin[i].nblk);
+    for (uint32_t k = 0; k < hin[i].nblk; ++k) {
+      const BlockDesc& b = hb[first[i] + k];
+      if (!b.ptr || b.ilen < 8) return false;
+      const uint64_t koff = uint64_t(b.ikey - dptr[i]);
+      if (koff + b.ilen > inputs[i].size) return false;
+      PlanBlock p{b.off, b.size, inputs[i].data + koff, b.ilen - 8};
+      if (!v.empty()) {  // blocks in file order, keys in order
+        const PlanBlock& q = v.back();
+        if (q.off + q.size + 5 > p.off || cmp_user_host(q.ukey, q.ulen, p.ukey, p.ulen) > 0) return false;
+      }
+      v.push_back(p);
+    }
+    if (v.back().off + v.back().size + 5 > hin[i].idx_off) return false;
+  }
+  return true;
+}
+
+// Range bounds (user keys, strictly increasing, at most K - 1) that cut the inputs' data
+// bytes into parts of about equal size, except the first and the last, which take half a
+// part each: the first range's tables start going back sooner and the last range (its
+// compaction and copy out, after all bytes are in) is short. Index keys are sampled about
+// 4096 times over all inputs, each sample weighted by the data bytes since the previous
+// sample of its input.
+std::vector<std::pair<const uint8_t*, uint32_t>> range_bounds(const std::vector<std::vector<PlanBlock>>& blocks,
+                                                               uint32_t K) {
+  struct Sample {
+    const uint8_t* k;
+    uint32_t n;
+    uint64_t w;
+  };
+  uint64_t nb = 0;
+  for (const auto& v : blocks) nb += v.size();
+  const uint64_t stride = std::max<uint64_t>(1, nb / 4096);
+  std::vector<Sample> smp;
+  uint64_t total = 0;
+  for (const auto& v : blocks) {
+    uint64_t w = 0;
+    for (size_t k = 0; k < v.size(); ++k) {
+      w += v[k].size + 5;
+      if ((k + 1) % stride == 0 || k + 1 == v.size()) {
+        smp.push_back({v[k].ukey, v[k].ulen, w});
+        total += w;
+        w = 0;
+      }
+    }
+  }
+  std::sort(smp.begin(), smp.end(),
+            [](const Sample& a, const Sample& b) { return cmp_user_host(a.k, a.n, b.k, b.n) < 0; });
+  // bound r (1 <= r < K) at the fraction (r - 1/2) / (K - 1) of the bytes
+  auto frac = [&](uint32_t r) { return (double(r) - 0.5) / double(K - 1); };
+  std::vector<std::pair<const uint8_t*, uint32_t>> out;
+  uint64_t acc = 0;
+  uint32_t r = 1;
+  for (const Sample& s : smp) {
+    acc += s.w;
+    if (r < K && double(acc) >= frac(r) * double(total)) {
+      if (out.empty() || cmp_user_host(out.back().first, out.back().second, s.k, s.n) < 0) out.push_back({s.k, s.n});
+      while (r < K && double(acc) >= frac(r) * double(total)) ++r;
+    }
+  }
+  return out;
+}
+
+// The default number of ranges: one per max(96 MiB, target) of input, 16 at most. Every
+// range costs a compaction's fixed launches and round trips, which slow down while the
+// copies fill the bus (on the 1 GiB job 6 to 16 ranges all take about 33.5 ms, 24 take 42).
+uint32_t default_ranges(uint64_t in_bytes, uint64_t target) {
+  const uint64_t per = std::max<uint64_t>(96ull << 20, target);
+  return uint32_t(std::min<uint64_t>(16, in_bytes / per));
+}
+
+// luda_compact's job with its transfers overlapped by key ranges (see above). *handled is
+// false when the job is left to the one-piece path (fewer than two ranges, a ranged job, a
+// table the plan does not take); otherwise out holds the result.
+luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, luda_outputs* out, bool* handled) {
+  *handled = false;
+  const uint32_t N = job.n_inputs;
+  if (!N || job.range_lo || job.range_hi || !tuning_valid(opts->tuning)) return LUDA_OK;
+  uint64_t in_bytes = 0;
+  for (uint32_t i = 0; i < N; ++i) in_bytes += job.inputs[i].size;
+  uint32_t K = opts->tuning && opts->tuning->h2d_ranges ? opts->tuning->h2d_ranges
+                                                         : default_ranges(in_bytes, opts->target_file_size);
+  if (K < 2) return LUDA_OK;
+  const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
+  const DevMem mem{opts, st};
+  CrcTabs tabs;
+  luda_status rc = get_tabs(&tabs);
+  if (rc) return rc;
+  Xfer* x = nullptr;
+  if ((rc = get_xfer(&x))) return rc;
+  std::vector<uint64_t> off(N + 1, 0);
+  for (uint32_t i = 0; i < N; ++i) off[i + 1] = (off[i] + job.inputs[i].size + 255) & ~uint64_t(255);
+  uint8_t* arena = static_cast<uint8_t*>(mem.get(off[N] + 256));
+  if (!arena) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
+  std::vector<uint8_t*> dptr(N);
+  for (uint32_t i = 0; i < N; ++i) dptr[i] = arena + off[i];
+  std::vector<std::vector<PlanBlock>> blocks;
+  std::vector<uint64_t> idx_off;
+  if (!plan_inputs(job.inputs, N, dptr.data(), st, mem, tabs, &blocks, &idx_off)) {
+    mem.put(arena);
+    return LUDA_OK;
+  }
+  const auto bounds = range_bounds(blocks, K);
+  if (bounds.empty()) {
+    mem.put(arena);
+    return LUDA_OK;
+  }
+  *handled = true;
+  const uint32_t R = uint32_t(bounds.size()) + 1;
+  // copies in: range r's part of every input (its blocks up to the first whose index key
+  // reaches bound r, with 16 bytes beyond for the decoders' windows), the last range the
+  // rest of the data region
+  std::vector<uint64_t> done(N, 0);
+  bool ok = cudaEventRecord(x->ev_run, st) == cudaSuccess && cudaStreamWaitEvent(x->in, x->ev_run, 0) == cudaSuccess &&
+            cudaEventRecord(x->t[0], x->in) == cudaSuccess;
+  for (uint32_t r = 0; ok && r < R; ++r) {
+    for (uint32_t i = 0; ok && i < N; ++i) {
+      const std::vector<PlanBlock>& v = blocks[i];
+      uint64_t e = idx_off[i];
+      if (r + 1 < R) {
+        const auto& b = bounds[r];
+        const auto it = std::lower_bound(v.begin(), v.end(), b, [](const PlanBlock& p, const auto& key) {
+          return cmp_user_host(p.ukey, p.ulen, key.first, key.second) < 0;
+        });
+        const PlanBlock& last = it == v.end() ? v.back() : *it;
+        e = std::min(idx_off[i], last.off + last.size + 5 + 16);
+      }
+      if (e > done[i]) {
+        ok = copy_pieces(dptr[i] + done[i], job.inputs[i].data + done[i], e - done[i], cudaMemcpyHostToDevice, x->in);
+        done[i] = e;
+      }
+    }
+    ok = ok && cudaEventRecord(x->ev_in[r], x->in) == cudaSuccess;
+  }
+  ok = ok && cudaEventRecord(x->t[1], x->in) == cudaSuccess;
+  // the ranges: compact, emit the finished tables, copy them out on the second stream
+  std::vector<luda_outputs> routs(R);
+  for (luda_outputs& o : routs) memset(&o, 0, sizeof o);
+  std::vector<uint32_t> nrec, max_rec;
+  std::vector<luda_table> emitted;  // device tables, in key order
+  std::vector<uint8_t> lo;
+  bool has_lo = false;
+  double ms_dev = 0;
+  double sms[LUDA_N_STAGES] = {};
+  uint64_t sbytes[LUDA_N_STAGES] = {};
+  Holder* h = new Holder;
+  const uint64_t cap0 = ((in_bytes + in_bytes / 2) | ((64ull << 20) - 1)) + 1;
+  h->pinned = pinned_get(cap0, &h->pinned_cap);
+  uint8_t* pin = h->pinned;
+  uint64_t pin_left = h->pinned ? h->pinned_cap : 0, pos = 0;
+  std::vector<uint8_t*> host_at;  // host address of every emitted table
+  bool out_started = false;
+  auto finish = [&](luda_status s) {
+    cudaStreamSynchronize(x->in);
+    cudaStreamSynchronize(x->out);
+    for (luda_outputs& o : routs) luda_outputs_free(&o);
+    mem.put(arena);
+    cudaStreamSynchronize(st);
+    return s;
+  };
+  if (!ok || !h->pinned) {
+    const luda_status s = h->pinned ? cuda_fail(cudaGetLastError(), "copy of the inputs to the device")
+                                    : cuda_fail(cudaErrorMemoryAllocation, "pinned host allocation");
+    holder_release(h);
+    return finish(s);
+  }
+  for (uint32_t r = 0; r < R; ++r) {
+    HostJob hj{nullptr, N, job.smallest_snapshot, job.bottommost};
+    std::vector<luda_input> din(job.inputs, job.inputs + N);
+    for (uint32_t i = 0; i < N; ++i) din[i].data = dptr[i];
+    hj.inputs = din.data();
+    static const uint8_t kEmpty = 0;
+    if (has_lo) {
+      hj.lo = lo.empty() ? &kEmpty : lo.data();
+      hj.lo_len = uint32_t(lo.size());
+    }
+    if (r + 1 < R) {
+      hj.hi = bounds[r].second ? bounds[r].first : &kEmpty;
+      hj.hi_len = bounds[r].second;
+    }
+    double ms = 0;
+    double rs[LUDA_N_STAGES] = {};
+    uint64_t rb[LUDA_N_STAGES] = {};
+    if (cudaStreamWaitEvent(st, x->ev_in[r], 0) != cudaSuccess) {
+      holder_release(h);
+      return finish(cuda_fail(cudaGetLastError(), "stream wait"));
+    }
+    rc = run_compaction(&hj, 1, opts, st, &routs[r], false, &ms, nullptr, rs, rb, nullptr, &nrec);
+    if (!rc && routs[r].status) rc = luda_status(routs[r].status);
+    if (rc) {
+      holder_release(h);
+      return finish(rc);
+    }
+    ms_dev += ms;
+    for (int k = 0; k < LUDA_N_STAGES; ++k) {
+      sms[k] += rs[k];
+      sbytes[k] += rb[k];
+    }
+    if (max_rec.size() < nrec.size()) max_rec.resize(nrec.size(), 0);
+    for (size_t g = 0; g < nrec.size(); ++g) max_rec[g] = std::max(max_rec[g], nrec[g]);
+    // the tables before the last one that starts a new user key are finished
+    const luda_outputs& o = routs[r];
+    uint32_t n_emit = o.n_tables;
+    if (r + 1 < R) {
+      n_emit = 0;
+      for (uint32_t t = o.n_tables; t-- > 1;) {
+        const luda_table& a = o.tables[t - 1];
+        const luda_table& b = o.tables[t];
+        if (a.largest_len >= 8 && b.smallest_len >= 8 &&
+            cmp_user_host(a.largest, a.largest_len - 8, b.smallest, b.smallest_len - 8) != 0) {
+          n_emit = t;
+          lo.assign(b.smallest, b.smallest + b.smallest_len - 8);
+          has_lo = true;
+          break;
+        }
+      }
+    }
+    if (n_emit && !out_started) {
+      out_started = true;
+      ok = cudaEventRecord(x->t[2], x->out) == cudaSuccess;
+    }
+    ok = ok && cudaEventRecord(x->ev_run, st) == cudaSuccess && cudaStreamWaitEvent(x->out, x->ev_run, 0) == cudaSuccess;
+    for (uint32_t t = 0; ok && t < n_emit; ++t) {
+      const luda_table& tb = o.tables[t];
+      if (tb.size > pin_left) {  // another pinned buffer for the rest
+        size_t c = 0;
+        uint8_t* p = pinned_get(std::max<uint64_t>(2 * tb.size, 64ull << 20), &c);
+        if (!p) {
+          holder_release(h);
+          return finish(cuda_fail(cudaErrorMemoryAllocation, "pinned host allocation"));
+        }
+        h->more_pinned.emplace_back(p, c);
+        pin = p;
+        pin_left = c;
+        pos = 0;
+      }
+      ok = copy_pieces(pin + pos, tb.data, tb.size, cudaMemcpyDeviceToHost, x->out);
+      emitted.push_back(tb);
+      host_at.push_back(pin + pos);
+      const uint64_t adv = (tb.size + 15) & ~uint64_t(15);
+      pos += adv;
+      pin_left = adv < pin_left ? pin_left - adv : 0;
+    }
+    if (!ok) {
+      holder_release(h);
+      return finish(cuda_fail(cudaGetLastError(), "copy of the new tables to the host"));
+    }
+  }
+  // one result: the emitted tables in pinned host memory, their keys in one buffer
+  if (out_started) cudaEventRecord(x->t[3], x->out);
+  cudaStreamSynchronize(x->out);
+  const uint32_t nt = uint32_t(emitted.size());
+  uint64_t kb = 0, n_in = 0, n_out = 0;
+  for (const luda_table& t : emitted) {
+    kb += t.smallest_len + t.largest_len;
+    n_out += t.n_entries;
+  }
+  for (uint32_t v : max_rec) n_in += v;
+  out->tables = static_cast<luda_table*>(calloc(nt ? nt : 1, sizeof(luda_table)));
+  uint8_t* keys = static_cast<uint8_t*>(malloc(kb ? kb : 1));
+  uint64_t kp = 0;
+  for (uint32_t t = 0; t < nt; ++t) {
+    luda_table tb = emitted[t];
+    tb.data = host_at[t];
+    memcpy(keys + kp, emitted[t].smallest, tb.smallest_len);
+    tb.smallest = keys + kp;
+    kp += tb.smallest_len;
+    memcpy(keys + kp, emitted[t].largest, tb.largest_len);
+    tb.largest = keys + kp;
+    kp += tb.largest_len;
+    out->tables[t] = tb;
+  }
+  out->n_tables = nt;
+  out->n_in_entries = n_in;
+  out->n_dropped = n_in - n_out;
+  out->_priv = new OutPriv{h, keys};  // the result holds the holder's one reference
+  float a = 0, b = 0;
+  cudaStreamSynchronize(x->in);
+  if (cudaEventElapsedTime(&a, x->t[0], x->t[1]) == cudaSuccess) out->ms_h2d = a;
+  if (out_started && cudaEventElapsedTime(&b, x->t[2], x->t[3]) == cudaSuccess) out->ms_d2h = b;
+  out->ms_device = ms_dev;
+  memcpy(out->stage_ms, sms, sizeof sms);
+  memcpy(out->stage_bytes, sbytes, sizeof sbytes);
+  return finish(LUDA_OK);
+}
+
+}  // namespace
+
 luda_status luda::compact_job_host(const luda_job& job, const luda_options* opts, luda_outputs* out,
                                    AdmitGate* gate) {
   t_detail[0] = 0;
@@ -2122,6 +2638,26 @@ luda_status luda::compact_job_host(const luda_job& job, const luda_options* opts
     return LUDA_ERR_INVALID_ARG;
   }
   memset(out, 0, sizeof *out);
+  if (!gate) {  // a call of its own: its copies in and out overlap by key ranges
+    for (uint32_t i = 0; i < n_inputs; ++i)
+      if (!inputs[i].data && inputs[i].size) {
+        set_detail("input %u: data is NULL", i);
+        return LUDA_ERR_INVALID_ARG;
+      }
+    Fmt fmt;
+    luda_status rc = opts_check(opts, &fmt);
+    if (rc) return rc;
+    bool handled = false;
+    const TuningScope tuned(opts->tuning);
+    rc = compact_host_ranges(job, opts, out, &handled);
+    if (handled || rc) {
+      if (rc) {
+        luda_outputs_free(out);
+        out->status = rc;
+      }
+      return rc;
+    }
+  }
   const cudaStream_t st = static_cast<cudaStream_t>(opts->stream);
   const DevMem mem{opts, st};
   // one device arena for all inputs, each at a 256-byte boundary

@@ -214,6 +214,7 @@ struct Tuning {
   uint32_t elem_threads = 256;
   uint32_t crc_ctas = 56;  // the unpack's checksum pass: the other stages run beside it on the rest
   uint32_t crc_warps = 32;
+  uint32_t h2d_ranges = 0;  // luda_compact's transfer ranges (0: from the input bytes and target size)
 };
 const Tuning& tuning();
 // Range check of a luda_tuning (0 = default); sets the error detail on failure.

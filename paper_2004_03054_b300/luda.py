@@ -41,9 +41,10 @@ class Tuning(C.Structure):
     """luda_tuning: launch shapes (0 = default); they never change the output bytes."""
     _fields_ = [("merge_tile", C.c_uint32), ("merge_ctas_per_sm", C.c_uint32), ("decode_warps", C.c_uint32),
                 ("walk_threads", C.c_uint32), ("encode_ctas_per_sm", C.c_uint32), ("elem_threads", C.c_uint32),
-                ("crc_ctas", C.c_uint32), ("crc_warps", C.c_uint32)]
+                ("crc_ctas", C.c_uint32), ("crc_warps", C.c_uint32),
+                ("h2d_ranges", C.c_uint32)]
     KNOBS = ("merge_tile", "merge_ctas_per_sm", "decode_warps", "walk_threads", "encode_ctas_per_sm",
-             "elem_threads", "crc_ctas", "crc_warps")
+             "elem_threads", "crc_ctas", "crc_warps", "h2d_ranges")
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k in self.KNOBS}

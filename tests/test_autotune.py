@@ -70,7 +70,7 @@ def test_cache_round_trip_and_hit(tmp_path, monkeypatch):
 
 
 def test_tuning_struct_layout():
-    assert C.sizeof(luda.Tuning) == 32
+    assert C.sizeof(luda.Tuning) == 36  # nine uint32 fields, as luda.h declares
     assert luda.Options.tuning.offset == luda.Options.stream.offset + 8
     t = luda.Tuning.of({"merge_tile": 512, "elem_threads": 128})
     assert t.as_dict()["merge_tile"] == 512 and t.as_dict()["decode_warps"] == 0
@@ -89,7 +89,7 @@ def test_library_checks_tuning_ranges():
     for bad in ({"merge_tile": 768}, {"merge_tile": 4096}, {"merge_ctas_per_sm": 33}, {"decode_warps": 17},
                 {"walk_threads": 48}, {"walk_threads": 512}, {"encode_ctas_per_sm": 9}, {"elem_threads": 32},
                 {"elem_threads": 100}, {"elem_threads": 2048}, {"crc_ctas": 149},
-                {"crc_warps": 4}, {"crc_warps": 20}, {"crc_warps": 40}):
+                {"crc_warps": 4}, {"crc_warps": 20}, {"crc_warps": 40}, {"h2d_ranges": 65}):
         assert L.luda_tuning_check(C.byref(luda.Tuning.of(bad))) == luda.ERR_INVALID_ARG, bad
         assert list(bad)[0] in luda.last_error_detail()
     assert L.luda_tuning_check(None) == luda.ERR_INVALID_ARG

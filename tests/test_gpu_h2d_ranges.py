@@ -1,0 +1,119 @@
+"""luda_compact with its transfers overlapped by key ranges (§III-D; luda_tuning.h2d_ranges):
+the inputs' data blocks are copied range after range, each range is compacted as soon as
+its blocks are on the device and its finished tables go back while later ranges arrive.
+The tables, their keys and the entry counts equal the oracle's compaction of the whole job
+in one piece, for any number of ranges, from pageable and from pinned host memory, with
+every format variant, with user keys whose versions span tables, and on corrupt inputs."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from helpers import oracle_compact, oracle_inputs
+from paper_2004_03054_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2004_03054_b300 import luda  # noqa: E402
+from test_gpu_parity import assert_same  # noqa: E402
+
+
+def _opts(job, ranges, flags=0):
+    return luda.job_options(job, flags=flags, tuning={"h2d_ranges": ranges})
+
+
+def _pinned_compact(ins, snap, opts):
+    """luda_compact from pinned host buffers (copies truly asynchronous)."""
+    bufs = []
+    arr = (luda.Input * len(ins))()
+    for i, b in enumerate(ins):
+        t = torch.empty(len(b), dtype=torch.uint8).pin_memory()
+        t.numpy()[:] = np.frombuffer(b, dtype=np.uint8)
+        bufs.append(t)
+        arr[i].data, arr[i].size = t.data_ptr(), len(b)
+    out = luda.Outputs()
+    rc = luda.lib().luda_compact(arr, len(ins), 1, snap, C.byref(opts), C.byref(out))
+    return luda._take(rc, out, device=False)
+
+
+@pytest.mark.parametrize("cfg,scale,ranges", [("config1", 1.0, 2), ("config1", 1.0, 7), ("config2", 1 / 2, 3),
+                                              ("config2", 1 / 2, 16), ("config3", 1 / 16, 5),
+                                              ("config3", 1 / 16, 64)])
+def test_ranges_give_the_oracle_tables(cfg, scale, ranges):
+    job = getattr(W, cfg)(seed=31, scale=scale)
+    job.target_file_size = min(job.target_file_size, 256 * 1024)  # several tables per range
+    ins = oracle_inputs(job)
+    want = oracle_compact(job, ins)
+    assert want.status == 0 and len(want.tables) > 2
+    got = luda.compact(ins, job.smallest_snapshot, opts=_opts(job, ranges))
+    assert_same(got, want)
+    assert got.ms_h2d > 0 and got.ms_d2h > 0
+    pinned = _pinned_compact(ins, job.smallest_snapshot, _opts(job, ranges))
+    assert_same(pinned, want)
+
+
+@pytest.mark.parametrize("flags", [luda.F_SHORT_INDEX | luda.F_FILTER_ARRAY, luda.F_COMPRESS])
+def test_ranges_with_format_variants(flags):
+    job = W.config2(seed=32, scale=1 / 4)
+    job.target_file_size = 128 * 1024
+    ins = oracle_inputs(job)
+    want = oracle_compact(job, ins, flags)
+    assert want.status == 0
+    got = _pinned_compact(ins, job.smallest_snapshot, _opts(job, 6, flags))
+    assert_same(got, want)
+
+
+def test_ranges_with_versions_spanning_tables():
+    """Many versions per user key and tiny tables: table boundaries fall inside a user key's
+    versions, so the held-back part of a range reaches back past such boundaries."""
+    rng = np.random.default_rng(33)
+    for trial in range(12):
+        job = W.tiny_job(rng, n_keys=int(rng.integers(40, 400)), max_versions=12, n_inputs=int(rng.integers(2, 6)),
+                         key_len=(1, 6), val_len=(0, 60))
+        job.block_size = int(rng.choice([64, 256, 1024]))
+        job.target_file_size = int(rng.choice([1, 200, 700, 3000]))
+        ins = oracle_inputs(job)
+        want = oracle_compact(job, ins)
+        for ranges in (2, 5, 33):
+            got = _pinned_compact(ins, job.smallest_snapshot, _opts(job, ranges))
+            assert_same(got, want)
+
+
+def test_one_range_and_the_default_equal_the_ranges():
+    job = W.config1(seed=34, scale=1 / 2)
+    job.target_file_size = 200 * 1024
+    ins = oracle_inputs(job)
+    want = oracle_compact(job, ins)
+    for ranges in (1, 0, 4):
+        assert_same(luda.compact(ins, job.smallest_snapshot, opts=_opts(job, ranges)), want)
+
+
+def test_corrupt_inputs_fail_with_no_tables():
+    job = W.config2(seed=35, scale=1 / 4)
+    job.target_file_size = 128 * 1024
+    ins = oracle_inputs(job)
+    # a data block near the end of the largest input (a late range) and a broken footer
+    big = max(range(len(ins)), key=lambda i: len(ins[i]))
+    cases = []
+    late = bytearray(ins[big])
+    late[int(len(late) * 0.6)] ^= 0x10
+    cases.append([bytes(late) if i == big else b for i, b in enumerate(ins)])
+    foot = bytearray(ins[0])
+    foot[-1] ^= 0xFF
+    cases.append([bytes(foot)] + ins[1:])
+    for bad in cases:
+        want = oracle_compact(job, bad)
+        assert want.status != 0
+        got = _pinned_compact(bad, job.smallest_snapshot, _opts(job, 5))
+        assert got.status == want.status and got.tables == []
+    # the library is usable afterwards
+    assert_same(_pinned_compact(ins, job.smallest_snapshot, _opts(job, 5)), oracle_compact(job, ins))
+
+
+def test_range_count_is_checked():
+    job = W.config1(seed=36, scale=1 / 16)
+    ins = oracle_inputs(job)
+    got = luda.compact(ins, job.smallest_snapshot, opts=_opts(job, 65))
+    assert got.status == luda.ERR_INVALID_ARG
