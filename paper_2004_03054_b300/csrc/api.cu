@@ -502,11 +502,16 @@ __global__ void k_stage_copy(uint8_t* __restrict__ dst, const uint8_t* __restric
   }
 }
 
-// cudaMemcpyAsync, except that a host-to-device or device-to-host copy of at most 1 MiB
-// whose host side lies in this thread's stage runs as k_stage_copy on the stream.
+// Set while this thread runs a call whose bulk copies keep the copy engines busy.
+thread_local bool t_stage_by_kernel = false;
+
+// cudaMemcpyAsync, except that while t_stage_by_kernel is set a host-to-device or
+// device-to-host copy of at most 1 MiB whose host side lies in this thread's stage runs as
+// k_stage_copy on the stream. (On an idle bus the copy engine is the faster way: 0.03 ms
+// per call on the 1 GiB job.)
 cudaError_t stage_copy(void* dst, const void* src, size_t n, cudaMemcpyKind kind, cudaStream_t st) {
   uint8_t* hd = nullptr;
-  if (n && n <= (1u << 20)) {
+  if (t_stage_by_kernel && n && n <= (1u << 20)) {
     if (kind == cudaMemcpyHostToDevice && (hd = t_stage.dev_of(src, n))) src = hd;
     else if (kind == cudaMemcpyDeviceToHost && (hd = t_stage.dev_of(dst, n))) dst = hd;
   }
@@ -2476,6 +2481,10 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
   }
   ok = ok && cudaEventRecord(x->t[1], x->in) == cudaSuccess;
   // the ranges: compact, emit the finished tables, copy them out on the second stream
+  struct ByKernel {
+    ByKernel() { t_stage_by_kernel = true; }
+    ~ByKernel() { t_stage_by_kernel = false; }
+  } by_kernel;
   std::vector<luda_outputs> routs(R);
   for (luda_outputs& o : routs) memset(&o, 0, sizeof o);
   std::vector<uint32_t> nrec, max_rec;
