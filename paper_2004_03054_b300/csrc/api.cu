@@ -2248,21 +2248,46 @@ bool copy_pieces(void* dst, const void* src, uint64_t n, cudaMemcpyKind kind, cu
   return true;
 }
 
-// One data block of an input as its index lists it: handle and index key (in the caller's
-// host copy of the input).
-struct PlanBlock {
-  uint64_t off, size;
-  const uint8_t* ukey;  // the index key's user key
-  uint32_t ulen;
+// The plan of a job's copies: every data block's handle and index key as the index lists
+// them (parsed on the device; the keys are read from the caller's host copy of the
+// inputs), and each input's index block offset.
+struct Plan {
+  const luda_input* in = nullptr;
+  uint8_t* const* dptr = nullptr;
+  const BlockDesc* blk = nullptr;  // all inputs' blocks; input i's from first[i]
+  std::vector<BlockDesc> own;      // the blocks when the host stage cannot hold them
+  std::vector<uint32_t> first;
+  std::vector<uint64_t> idx_off;
+  const uint8_t* ukey(uint32_t i, uint32_t g) const { return in[i].data + (blk[g].ikey - dptr[i]); }
+  uint32_t ulen(uint32_t g) const { return blk[g].ilen - 8; }
 };
 
+// Sets *bad unless every block has a handle and an index key of at least 8 bytes, and the
+// blocks of each input follow one another in the file (trailers included, the last before
+// the index block) with index keys in order.
+__global__ void k_plan_check(const DInput* __restrict__ in, const uint32_t* __restrict__ first, uint32_t n_blocks,
+                             const BlockDesc* __restrict__ b, uint32_t* bad) {
+  for (uint64_t g = gtid(); g < n_blocks; g += gstride()) {
+    const BlockDesc x = b[g];
+    const uint32_t i = x.input;
+    bool ok = x.ptr && x.ilen >= 8;
+    if (ok && g > first[i]) {
+      const BlockDesc p = b[g - 1];
+      ok = p.ptr && p.ilen >= 8 && p.off + p.size + kTrailer <= x.off &&
+           cmp_user_keys(p.ikey, p.ilen - 8, x.ikey, x.ilen - 8) <= 0;
+    }
+    if (ok && g + 1 == first[i + 1]) ok = x.off + x.size + kTrailer <= in[i].idx_off;
+    if (!ok) atomicOr(bad, 1u);
+  }
+}
+
 // The inputs' footers and index blocks copied to their places in the arena and parsed on
-// the device; on return blocks[i] lists input i's data blocks and idx_off[i] its index
-// block's offset. False (and nothing reported) when a footer, an index block or a handle
-// is not as a well-formed table has it, or the index keys are not in order: the caller
-// then runs the whole job in one piece, which reports the error.
+// the device (the sizing stage's kernels). False (and nothing reported) when a footer, an
+// index block or a handle is not as a well-formed table has it, or the index keys or the
+// blocks are out of order: the caller then runs the whole job in one piece, which reports
+// the error.
 bool plan_inputs(const luda_input* inputs, uint32_t N, uint8_t* const* dptr, cudaStream_t st, const DevMem& mem,
-                 const CrcTabs& tabs, std::vector<std::vector<PlanBlock>>* blocks, std::vector<uint64_t>* idx_off) {
+                 const CrcTabs& tabs, Plan* plan) {
   std::vector<DInput> hin(N);
   for (uint32_t i = 0; i < N; ++i) {
     if (inputs[i].size < kFooter) return false;
@@ -2275,12 +2300,13 @@ bool plan_inputs(const luda_input* inputs, uint32_t N, uint8_t* const* dptr, cud
   DInput* d_in;
   DErr* d_errs;
   CrcMsg* d_msgs;
-  uint32_t* d_first;
+  uint32_t *d_first, *d_bad;
   auto lay = [&](Layout& l) {
     d_in = l.take<DInput>(N + 1);
     d_errs = l.take<DErr>(4);
     d_msgs = l.take<CrcMsg>(N + 1);
     d_first = l.take<uint32_t>(N + 1);
+    d_bad = l.take<uint32_t>(1);
   };
   lay(L);
   uint8_t* buf = static_cast<uint8_t*>(mem.get(L.off));
@@ -2295,8 +2321,12 @@ bool plan_inputs(const luda_input* inputs, uint32_t N, uint8_t* const* dptr, cud
       for (void* p : ps) m.put(p);
     }
   } put{mem, {buf}};
+  HostStage& hs = t_stage;
+  hs.reset();
   DErr herr[4];
-  bool ok = cudaMemsetAsync(d_errs, 0, sizeof(DErr) * 4, st) == cudaSuccess;
+  uint32_t hbad = 0;
+  bool ok = cudaMemsetAsync(d_errs, 0, sizeof(DErr) * 4, st) == cudaSuccess &&
+            cudaMemsetAsync(d_bad, 0, sizeof(uint32_t), st) == cudaSuccess;
   for (uint32_t i = 0; ok && i < N; ++i)
     ok = cudaMemcpyAsync(dptr[i] + inputs[i].size - kFooter, inputs[i].data + inputs[i].size - kFooter, kFooter,
                          cudaMemcpyHostToDevice, st) == cudaSuccess;
@@ -2320,7 +2350,8 @@ bool plan_inputs(const luda_input* inputs, uint32_t N, uint8_t* const* dptr, cud
        cudaMemcpyAsync(herr, d_errs, sizeof herr, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
        cudaStreamSynchronize(st) == cudaSuccess;
   if (!ok || herr[0].code || herr[2].code) return false;
-  std::vector<uint32_t> first(N + 1, 0);
+  std::vector<uint32_t>& first = plan->first;
+  first.assign(N + 1, 0);
   for (uint32_t i = 0; i < N; ++i) {
     if (!hin[i].nblk) return false;
     hin[i].blk_first = first[i];
@@ -2330,62 +2361,52 @@ bool plan_inputs(const luda_input* inputs, uint32_t N, uint8_t* const* dptr, cud
   BlockDesc* d_blocks = static_cast<BlockDesc*>(mem.get(sizeof(BlockDesc) * (NB + 1)));
   if (!d_blocks) return false;
   put.ps.push_back(d_blocks);
-  std::vector<BlockDesc> hb(NB);
+  BlockDesc* hb = static_cast<BlockDesc*>(hs.take(sizeof(BlockDesc) * NB));  // pinned: a fast copy
+  if (!hb) {
+    plan->own.resize(NB);
+    hb = plan->own.data();
+  }
   ok = cudaMemcpyAsync(d_in, hin.data(), sizeof(DInput) * N, cudaMemcpyHostToDevice, st) == cudaSuccess &&
        cudaMemcpyAsync(d_first, first.data(), sizeof(uint32_t) * (N + 1), cudaMemcpyHostToDevice, st) == cudaSuccess;
   if (!ok) return false;
   launch_index_entries(d_in, N, d_first, NB, d_blocks, d_errs, st, nullptr, nullptr);
-  ok = cudaMemcpyAsync(hb.data(), d_blocks, sizeof(BlockDesc) * NB, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+  k_plan_check<<<grid_for(NB, 256), 256, 0, st>>>(d_in, d_first, NB, d_blocks, d_bad);
+  count_launches(1);
+  ok = cudaMemcpyAsync(hb, d_blocks, sizeof(BlockDesc) * NB, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
        cudaMemcpyAsync(herr, d_errs, sizeof herr, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+       cudaMemcpyAsync(&hbad, d_bad, sizeof hbad, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
        cudaStreamSynchronize(st) == cudaSuccess;
-  if (!ok || herr[0].code) return false;
-  blocks->assign(N, {});
-  idx_off->assign(N, 0);
-  for (uint32_t i = 0; i < N; ++i) {
-    (*idx_off)[i] = hin[i].idx_off;
-    std::vector<PlanBlock>& v = (*blocks)[i];
-    v.reserve(hin[i].nblk);
-    for (uint32_t k = 0; k < hin[i].nblk; ++k) {
-      const BlockDesc& b = hb[first[i] + k];
-      if (!b.ptr || b.ilen < 8) return false;
-      const uint64_t koff = uint64_t(b.ikey - dptr[i]);
-      if (koff + b.ilen > inputs[i].size) return false;
-      PlanBlock p{b.off, b.size, inputs[i].data + koff, b.ilen - 8};
-      if (!v.empty()) {  // blocks in file order, keys in order
-        const PlanBlock& q = v.back();
-        if (q.off + q.size + 5 > p.off || cmp_user_host(q.ukey, q.ulen, p.ukey, p.ulen) > 0) return false;
-      }
-      v.push_back(p);
-    }
-    if (v.back().off + v.back().size + 5 > hin[i].idx_off) return false;
-  }
+  if (!ok || herr[0].code || hbad) return false;
+  plan->in = inputs;
+  plan->dptr = dptr;
+  plan->blk = hb;
+  plan->idx_off.resize(N);
+  for (uint32_t i = 0; i < N; ++i) plan->idx_off[i] = hin[i].idx_off;
   return true;
 }
 
-// Range bounds (user keys, strictly increasing, at most K - 1) that cut the inputs' data
-// bytes into parts of about equal size, except the first and the last, which take half a
-// part each: the first range's tables start going back sooner and the last range (its
-// compaction and copy out, after all bytes are in) is short. Index keys are sampled about
-// 4096 times over all inputs, each sample weighted by the data bytes since the previous
-// sample of its input.
-std::vector<std::pair<const uint8_t*, uint32_t>> range_bounds(const std::vector<std::vector<PlanBlock>>& blocks,
-                                                               uint32_t K) {
+// Range bounds (user keys in the caller's input bytes, strictly increasing, at most K - 1)
+// that cut the inputs' data bytes into parts of about equal size, except the first and the
+// last, which take half a part each: the first range's tables start going back sooner and
+// the last range (its compaction and copy out, after all bytes are in) is short. Index keys
+// are sampled about 1024 times over all inputs, each sample weighted by the data bytes
+// since the previous sample of its input.
+std::vector<std::pair<const uint8_t*, uint32_t>> range_bounds(const Plan& P, uint32_t K) {
   struct Sample {
     const uint8_t* k;
     uint32_t n;
     uint64_t w;
   };
-  uint64_t nb = 0;
-  for (const auto& v : blocks) nb += v.size();
-  const uint64_t stride = std::max<uint64_t>(1, nb / 4096);
+  const uint32_t N = uint32_t(P.first.size()) - 1;
+  const uint64_t stride = std::max<uint64_t>(1, P.first[N] / 1024);
   std::vector<Sample> smp;
   uint64_t total = 0;
-  for (const auto& v : blocks) {
+  for (uint32_t i = 0; i < N; ++i) {
     uint64_t w = 0;
-    for (size_t k = 0; k < v.size(); ++k) {
-      w += v[k].size + 5;
-      if ((k + 1) % stride == 0 || k + 1 == v.size()) {
-        smp.push_back({v[k].ukey, v[k].ulen, w});
+    for (uint32_t g = P.first[i]; g < P.first[i + 1]; ++g) {
+      w += P.blk[g].size + kTrailer;
+      if ((g - P.first[i] + 1) % stride == 0 || g + 1 == P.first[i + 1]) {
+        smp.push_back({P.ukey(i, g), P.ulen(g), w});
         total += w;
         w = 0;
       }
@@ -2406,6 +2427,20 @@ std::vector<std::pair<const uint8_t*, uint32_t>> range_bounds(const std::vector<
     }
   }
   return out;
+}
+
+// Where range r's copy of input i ends: after the first block whose index key reaches
+// the bound (all blocks when none does), 16 bytes on for the decoders' windows, at most
+// up to the index block (already on the device).
+uint64_t range_copy_end(const Plan& P, uint32_t i, const std::pair<const uint8_t*, uint32_t>& bound) {
+  uint32_t lo = P.first[i], hi = P.first[i + 1];  // first block with index key >= bound
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (cmp_user_host(P.ukey(i, mid), P.ulen(mid), bound.first, bound.second) < 0) lo = mid + 1;
+    else hi = mid;
+  }
+  const BlockDesc& b = P.blk[lo < P.first[i + 1] ? lo : P.first[i + 1] - 1];
+  return std::min(P.idx_off[i], b.off + b.size + kTrailer + 16);
 }
 
 // The default number of ranges: one per max(96 MiB, target) of input, 16 at most. Every
@@ -2441,13 +2476,13 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
   if (!arena) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
   std::vector<uint8_t*> dptr(N);
   for (uint32_t i = 0; i < N; ++i) dptr[i] = arena + off[i];
-  std::vector<std::vector<PlanBlock>> blocks;
-  std::vector<uint64_t> idx_off;
-  if (!plan_inputs(job.inputs, N, dptr.data(), st, mem, tabs, &blocks, &idx_off)) {
+  Plan plan;
+  if (!plan_inputs(job.inputs, N, dptr.data(), st, mem, tabs, &plan)) {
     mem.put(arena);
     return LUDA_OK;
   }
-  const auto bounds = range_bounds(blocks, K);
+  const std::vector<uint64_t>& idx_off = plan.idx_off;
+  const auto bounds = range_bounds(plan, K);
   if (bounds.empty()) {
     mem.put(arena);
     return LUDA_OK;
@@ -2462,16 +2497,7 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
             cudaEventRecord(x->t[0], x->in) == cudaSuccess;
   for (uint32_t r = 0; ok && r < R; ++r) {
     for (uint32_t i = 0; ok && i < N; ++i) {
-      const std::vector<PlanBlock>& v = blocks[i];
-      uint64_t e = idx_off[i];
-      if (r + 1 < R) {
-        const auto& b = bounds[r];
-        const auto it = std::lower_bound(v.begin(), v.end(), b, [](const PlanBlock& p, const auto& key) {
-          return cmp_user_host(p.ukey, p.ulen, key.first, key.second) < 0;
-        });
-        const PlanBlock& last = it == v.end() ? v.back() : *it;
-        e = std::min(idx_off[i], last.off + last.size + 5 + 16);
-      }
+      const uint64_t e = r + 1 < R ? range_copy_end(plan, i, bounds[r]) : idx_off[i];
       if (e > done[i]) {
         ok = copy_pieces(dptr[i] + done[i], job.inputs[i].data + done[i], e - done[i], cudaMemcpyHostToDevice, x->in);
         done[i] = e;
