@@ -265,13 +265,11 @@ KeptRecs kept_layout(Layout& L, uint64_t n, uint64_t key_bytes) {
 }
 
 // ---- kept decoded runs (LUDA_F_KEEP_DECODED) -------------------------------------------------
-// A store is one device allocation holding the kept run of one call's survivors. Each new
-// table of the call registers its slice of the run under its data pointer and size; the
-// registration ends, and the store is freed, when the outputs holding the tables are freed.
+// A store holds the kept run of one call's survivors, in the same device allocation as the
+// call's tables (right after them), so that both go in one release. Each new table of the
+// call registers its slice of the run under its data pointer and size; the registration
+// ends when the outputs holding the tables are freed.
 struct KeptStore {
-  void* mem = nullptr;
-  luda_free_fn dev_free = nullptr;
-  void* ctx = nullptr;
   KeptRecs run{};
 };
 struct KeptTable {
@@ -292,10 +290,6 @@ void kept_free(KeptStore* k) {
     std::lock_guard<std::mutex> lk(g_kept_mu);
     for (auto it = g_kept.begin(); it != g_kept.end();)
       it = it->second.store == k ? g_kept.erase(it) : std::next(it);
-  }
-  if (k->mem) {
-    if (k->dev_free) k->dev_free(k->mem, k->ctx, nullptr);
-    else cudaFree(k->mem);
   }
   delete k;
 }
@@ -1023,23 +1017,22 @@ void merge_schedule(const std::vector<std::vector<std::pair<uint32_t, uint32_t>>
 // Null when nothing is kept: the flag is off, the tables are compressed (a compressed
 // block's value has no address of its own) or go to the host, or there is no memory for
 // the store (the tables are then simply not kept).
-luda_status kept_start(const luda_options* o, const DevMem& mem, bool host_out, const PackBufs& pb,
+// Bytes of the store (kept_start), allocated right after the output arena so that it is
+// freed with the tables in one release (0 when the call keeps nothing).
+uint64_t kept_bytes(const luda_options* o, bool host_out, const Fmt& fmt, uint32_t cap, uint64_t key_bytes) {
+  if (!(o->flags & LUDA_F_KEEP_DECODED) || host_out || (fmt.flags & LUDA_F_COMPRESS) || !cap) return 0;
+  Layout LK;
+  kept_layout(LK, cap, key_bytes);
+  return LK.off;
+}
+
+luda_status kept_start(const luda_options* o, uint8_t* km, bool host_out, const PackBufs& pb,
                        const Counts* d_cnt, uint32_t cap, uint64_t key_bytes, const Recs& recs,
                        const uint8_t* d_out, cudaStream_t st, KeptStore** out) {
   *out = nullptr;
-  if (!(o->flags & LUDA_F_KEEP_DECODED) || host_out || pb.cz.raw_cap || !cap) return LUDA_OK;
+  if (!(o->flags & LUDA_F_KEEP_DECODED) || host_out || pb.cz.raw_cap || !cap || !km) return LUDA_OK;
+  KeptStore* k = new KeptStore();  // its memory belongs to the output allocation
   Layout LK;
-  kept_layout(LK, cap, key_bytes);
-  void* km = mem.get(LK.off);
-  if (!km) {
-    cudaGetLastError();  // an allocation that failed leaves nothing behind
-    return LUDA_OK;
-  }
-  KeptStore* k = new KeptStore();
-  k->mem = km;
-  k->dev_free = o->dev_free;
-  k->ctx = o->alloc_ctx;
-  LK = Layout{};
   LK.base = static_cast<uint8_t*>(km);
   k->run = kept_layout(LK, cap, key_bytes);
   const cudaError_t e =
@@ -1491,7 +1484,9 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
                 cz_stream_cap(fmt, out_cap, cap), n_jobs);
   };
   layoutC(LC);
-  if (gate && !gate->admit(LA.off + LB.off + LC.off + out_cap + gate->extra)) {
+  const uint64_t out_room = (out_cap + 255) & ~uint64_t(255);
+  uint64_t keep_bytes = kept_bytes(o, host_out, fmt, cap, K);
+  if (gate && !gate->admit(LA.off + LB.off + LC.off + out_room + keep_bytes + gate->extra)) {
     set_detail("the job was not admitted (server shutting down)");
     return LUDA_ERR_OOM;
   }
@@ -1501,7 +1496,12 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   LC = Layout{};
   LC.base = bufC;
   layoutC(LC);
-  uint8_t* d_out = static_cast<uint8_t*>(mem.get(out_cap));
+  uint8_t* d_out = static_cast<uint8_t*>(mem.get(out_room + keep_bytes));
+  if (!d_out && keep_bytes) {  // no room for the kept run: the tables alone
+    cudaGetLastError();
+    keep_bytes = 0;
+    d_out = static_cast<uint8_t*>(mem.get(out_cap));
+  }
   if (!d_out) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
   bool out_owned = false;
   struct OutGuard {
@@ -1581,7 +1581,9 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
   CK(cudaStreamWaitEvent(st, side->ev[3], 0));
   // LUDA_F_KEEP_DECODED: the survivors kept as a sorted run for the new tables
   KeptGuard kguard;
-  if ((rc = kept_start(o, mem, host_out, pb, d_cnt, cap, K, recs, d_out, st, &kguard.k))) return rc;
+  if ((rc = kept_start(o, keep_bytes ? d_out + out_room : nullptr, host_out, pb, d_cnt, cap, K, recs, d_out, st,
+                       &kguard.k)))
+    return rc;
   tr.mark(10, st);
   tdev.stop(st);
 
@@ -1727,7 +1729,14 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
   lay(L);
   uint8_t* buf = static_cast<uint8_t*>(mem.get(L.off));
   if (!buf) return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
-  uint8_t* d_out = static_cast<uint8_t*>(mem.get(out_cap));
+  const uint64_t out_room = (out_cap + 255) & ~uint64_t(255);
+  uint64_t keep_bytes = kept_bytes(o, host_out, fmt, n, K);
+  uint8_t* d_out = static_cast<uint8_t*>(mem.get(out_room + keep_bytes));
+  if (!d_out && keep_bytes) {  // no room for the kept run: the tables alone
+    cudaGetLastError();
+    keep_bytes = 0;
+    d_out = static_cast<uint8_t*>(mem.get(out_cap));
+  }
   if (!d_out) {
     mem.put(buf);
     return cuda_fail(cudaErrorMemoryAllocation, "device allocation");
@@ -1788,7 +1797,9 @@ luda_status run_build(const luda_run* run, bool host_in, const luda_options* o, 
     return rc;
   CK(cudaStreamWaitEvent(st, side->ev[3], 0));
   KeptGuard kguard;
-  if ((rc = kept_start(o, mem, host_out, pb, d_cnt, n, K, recs, d_out, st, &kguard.k))) return rc;
+  if ((rc = kept_start(o, keep_bytes ? d_out + out_room : nullptr, host_out, pb, d_cnt, n, K, recs, d_out, st,
+                       &kguard.k)))
+    return rc;
   td.stop(st);
   Collected col;
   t_stage.reset();  // nothing of this call was staged before (its copies are synchronous)

@@ -117,3 +117,43 @@ def test_range_count_is_checked():
     ins = oracle_inputs(job)
     got = luda.compact(ins, job.smallest_snapshot, opts=_opts(job, 65))
     assert got.status == luda.ERR_INVALID_ARG
+
+
+def _varint(n):
+    out = bytearray()
+    while n >= 0x80:
+        out.append((n & 0x7F) | 0x80)
+        n >>= 7
+    out.append(n)
+    return bytes(out)
+
+
+def test_index_out_of_order_runs_in_one_piece():
+    """Two index entries traded (index checksum recomputed): the plan finds the blocks out of
+    file order and the call runs in one piece, which rejects the table as the oracle does."""
+    import struct
+
+    import sstpy
+    job = W.config2(seed=37, scale=1 / 4)
+    job.target_file_size = 128 * 1024
+    ins = oracle_inputs(job)
+    big = max(range(len(ins)), key=lambda i: len(ins[i]))
+    t = bytearray(ins[big])
+    rd = sstpy.read(bytes(t))
+    ioff, isize = rd["handles"]["index"]
+    ents = [(k, v) for k, v, _ in sstpy.entries(bytes(t[ioff: ioff + isize]))]
+    assert len(ents) > 4
+    ents[1], ents[2] = ents[2], ents[1]
+    body, starts = bytearray(), []
+    for k, v in ents:
+        starts.append(len(body))
+        body += _varint(0) + _varint(len(k)) + _varint(len(v)) + k + v
+    body += b"".join(struct.pack("<I", s) for s in starts) + struct.pack("<I", len(starts))
+    assert len(body) == isize
+    t[ioff: ioff + isize] = body
+    t[ioff + isize + 1: ioff + isize + 5] = struct.pack("<I", oracle.mask(oracle.crc32c(bytes(body) + b"\x00")))
+    bad = [bytes(t) if i == big else b for i, b in enumerate(ins)]
+    want = oracle_compact(job, bad)
+    assert want.status == oracle.ERR_CORRUPTION
+    got = _pinned_compact(bad, job.smallest_snapshot, _opts(job, 4))
+    assert got.status == luda.ERR_CORRUPTION and got.tables == []
