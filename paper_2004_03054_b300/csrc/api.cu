@@ -2462,6 +2462,17 @@ uint32_t default_ranges(uint64_t in_bytes, uint64_t target) {
   return uint32_t(std::min<uint64_t>(16, in_bytes / per));
 }
 
+// The ranges' device memory when the caller brings no allocator: stream-ordered on the
+// stream the library names, and a range's tables (released with stream NULL) on the
+// copy-out stream, after their copy to the host.
+void* range_alloc(size_t n, void* /*ctx*/, void* stream) {
+  void* p = nullptr;
+  return cudaMallocAsync(&p, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? p : nullptr;
+}
+void range_free(void* p, void* ctx, void* stream) {
+  cudaFreeAsync(p, static_cast<cudaStream_t>(stream ? stream : ctx));
+}
+
 // luda_compact's job with its transfers overlapped by key ranges (see above). *handled is
 // false when the job is left to the one-piece path (fewer than two ranges, a ranged job, a
 // table the plan does not take); otherwise out holds the result.
@@ -2525,7 +2536,17 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
   std::vector<luda_outputs> routs(R);
   for (luda_outputs& o : routs) memset(&o, 0, sizeof o);
   std::vector<uint32_t> nrec, max_rec;
-  std::vector<luda_table> emitted;  // device tables, in key order
+  std::vector<luda_table> emitted;  // the emitted tables, in key order (keys as offsets into ekeys)
+  std::vector<uint8_t> ekeys;
+  // range runs: no kept runs (their tables go to the host); each range's tables released
+  // once their copy out is queued
+  luda_options ro = *opts;
+  ro.flags &= ~LUDA_F_KEEP_DECODED;
+  if (!ro.dev_alloc) {
+    ro.dev_alloc = range_alloc;
+    ro.dev_free = range_free;
+    ro.alloc_ctx = x->out;
+  }
   std::vector<uint8_t> lo;
   bool has_lo = false;
   double ms_dev = 0;
@@ -2573,7 +2594,7 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
       holder_release(h);
       return finish(cuda_fail(cudaGetLastError(), "stream wait"));
     }
-    rc = run_compaction(&hj, 1, opts, st, &routs[r], false, &ms, nullptr, rs, rb, nullptr, &nrec);
+    rc = run_compaction(&hj, 1, &ro, st, &routs[r], false, &ms, nullptr, rs, rb, nullptr, &nrec);
     if (!rc && routs[r].status) rc = luda_status(routs[r].status);
     if (rc) {
       holder_release(h);
@@ -2623,7 +2644,12 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
         pos = 0;
       }
       ok = copy_pieces(pin + pos, tb.data, tb.size, cudaMemcpyDeviceToHost, x->out);
-      emitted.push_back(tb);
+      luda_table e = tb;
+      e.smallest = reinterpret_cast<uint8_t*>(uintptr_t(ekeys.size()));
+      ekeys.insert(ekeys.end(), tb.smallest, tb.smallest + tb.smallest_len);
+      e.largest = reinterpret_cast<uint8_t*>(uintptr_t(ekeys.size()));
+      ekeys.insert(ekeys.end(), tb.largest, tb.largest + tb.largest_len);
+      emitted.push_back(e);
       host_at.push_back(pin + pos);
       const uint64_t adv = (tb.size + 15) & ~uint64_t(15);
       pos += adv;
@@ -2633,6 +2659,9 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
       holder_release(h);
       return finish(cuda_fail(cudaGetLastError(), "copy of the new tables to the host"));
     }
+    // with the library's allocator the tables' memory goes back on the copy-out stream, after
+    // their copies; a caller's allocator gets it back at the end
+    if (ro.dev_free == range_free) luda_outputs_free(&routs[r]);
   }
   // one result: the emitted tables in pinned host memory, their keys in one buffer
   if (out_started) cudaEventRecord(x->t[3], x->out);
@@ -2650,10 +2679,10 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
   for (uint32_t t = 0; t < nt; ++t) {
     luda_table tb = emitted[t];
     tb.data = host_at[t];
-    memcpy(keys + kp, emitted[t].smallest, tb.smallest_len);
+    memcpy(keys + kp, ekeys.data() + uintptr_t(emitted[t].smallest), tb.smallest_len);
     tb.smallest = keys + kp;
     kp += tb.smallest_len;
-    memcpy(keys + kp, emitted[t].largest, tb.largest_len);
+    memcpy(keys + kp, ekeys.data() + uintptr_t(emitted[t].largest), tb.largest_len);
     tb.largest = keys + kp;
     kp += tb.largest_len;
     out->tables[t] = tb;
