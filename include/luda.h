@@ -444,7 +444,12 @@ typedef struct {
 LUDA_API luda_status luda_check_table_noalloc(const uint8_t* table, uint64_t size, void* stream,
                                               luda_table_check* out);
 
-/* Frees everything an entry point stored in *out (host and device memory). */
+/* Frees everything an entry point stored in *out (host and device memory). Device tables
+ * the library allocated go back stream-ordered on the legacy default stream (after the work
+ * queued there and on every blocking stream; no device-wide wait): work on a non-blocking
+ * stream that still reads them must have completed, or been waited for, before this call.
+ * With a caller's allocator (luda_options.dev_free) the memory goes to dev_free(ptr, ctx,
+ * NULL). */
 LUDA_API void luda_outputs_free(luda_outputs* out);
 
 LUDA_API const char* luda_strerror(luda_status s);

@@ -369,8 +369,11 @@ void holder_release(Holder* h) {
   if (--h->refs > 0) return;
   kept_free(h->kept);  // first: no lookup may find a table whose memory is going
   if (h->dev) {
+    // stream-ordered on the legacy default stream: after the work queued there and on
+    // every blocking stream, without the device-wide wait of cudaFree (which would stall
+    // the other jobs of a server each time one releases its tables)
     if (h->dev_free) h->dev_free(h->dev, h->ctx, nullptr);
-    else cudaFree(h->dev);
+    else cudaFreeAsync(h->dev, cudaStreamLegacy);
   }
   pinned_put(h->pinned, h->pinned_cap);
   for (auto& pr : h->more_pinned) pinned_put(pr.first, pr.second);
