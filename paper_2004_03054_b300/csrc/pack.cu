@@ -1154,24 +1154,26 @@ __global__ void __launch_bounds__(kTrlThreads) k_block_trailer(const Counts* __r
   __syncthreads();
   const uint32_t* sT = s_trl;
   const uint32_t* sZ = s_trl + 1024;
-  const uint32_t lane = lane_id(), R = fmt.R, nb = cnt->nb;
-  const uint64_t warps = gstride() / 32;
-  for (uint64_t b = gtid() / 32; b < nb; b += warps) {
+  // a half warp per block: most blocks hold at most 16 entries (a lane each)
+  const uint32_t hl = lane_id() & 15u, R = fmt.R, nb = cnt->nb;
+  const uint32_t hmask = 0xFFFFu << (lane_id() & 16u);
+  const uint64_t halves = gstride() / 16;
+  for (uint64_t b = gtid() / 16; b < nb; b += halves) {
     if (!done[b]) continue;
     const BlkEnc D = bd[b];
     if (D.job & 0x80000000u) continue;  // outside the output arena (never staged)
     const uint32_t m = D.m, msg = D.contents + 1, nr = (m + R - 1) / R, rbase = D.contents - 4 - 4 * nr;
     uint32_t acc = 0, carry = 0;
-    for (uint32_t k0 = 0; k0 < m; k0 += 32) {
-      const uint32_t k = k0 + lane;
+    for (uint32_t k0 = 0; k0 < m; k0 += 16) {
+      const uint32_t k = k0 + hl;
       const bool restart = k % R == 0;
       uint32_t esz = 0;
       if (k < m) esz = sd[D.s0 + k] + (restart ? dr[D.s0 + k] : 0u);
       uint32_t x = esz;
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, x, d);
-        if (lane >= uint32_t(d)) x += o;
+      for (int d = 1; d < 16; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(hmask, x, d, 16);
+        if (hl >= uint32_t(d)) x += o;
       }
       if (k < m) {
         const uint32_t eoff = carry + x - esz;
@@ -1205,12 +1207,12 @@ __global__ void __launch_bounds__(kTrlThreads) k_block_trailer(const Counts* __r
         acc ^= crc_zeros_s(g, msg - (eoff + esz), sT, sZ);
         if (restart) acc ^= crc_zeros_s(crc_step4(0u, eoff, sT), msg - (rbase + 4 * (k / R) + 4), sT, sZ);
       }
-      carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+      carry += __shfl_sync(hmask, x, 15, 16);
     }
-    if (lane == 0) acc ^= crc_zeros_s(crc_step4(0u, nr, sT), 1, sT, sZ) ^ crc_zeros_s(0xFFFFFFFFu, msg, sT, sZ);
+    if (hl == 0) acc ^= crc_zeros_s(crc_step4(0u, nr, sT), 1, sT, sZ) ^ crc_zeros_s(0xFFFFFFFFu, msg, sT, sZ);
 #pragma unroll
-    for (int d = 16; d; d >>= 1) acc ^= __shfl_xor_sync(0xFFFFFFFFu, acc, d);
-    if (lane < 4) out[D.dst + D.contents + 1 + lane] = uint8_t(crc_mask(acc ^ 0xFFFFFFFFu) >> (8 * lane));
+    for (int d = 8; d; d >>= 1) acc ^= __shfl_xor_sync(hmask, acc, d, 16);
+    if (hl < 4) out[D.dst + D.contents + 1 + hl] = uint8_t(crc_mask(acc ^ 0xFFFFFFFFu) >> (8 * hl));
   }
 }
 
