@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kVerifyWarps * 32, 1) k_value_crc(Recs recs, c
 // boundary's 16-byte word (snap). For other blocks each value's register is computed by
 // the whole warp on its own.
 //
-// k_vcrc (second stream, after k_unpack; blocks with boundaries). Lane per entry: the
+// k_vcrc (second stream, after k_unpack; blocks with boundaries). A half warp per block, a lane per entry: the
 // prefix register at a boundary is its word's register advanced by the word's bytes before
 // it; F(value) = S(end) xor Z_len(S(start)) inside one chunk, the chunks in between joined
 // by Z_kChunk (Horner). Only the trailers of the new data blocks read the value registers.
@@ -836,9 +836,11 @@ __global__ void __launch_bounds__(kPostWarps * 32) k_vcrc(const UnpArgs A, CrcTa
   for (uint32_t i = threadIdx.x; i < kPostZ * 1024; i += blockDim.x) sZ[i] = __ldg(tabs.chunk + i);
   __syncthreads();
   const uint32_t* sZ144 = sZ + kCZ144 * 1024u;
-  const uint32_t lane = lane_id();
-  const uint64_t warps = gstride() / 32;
-  for (uint64_t g = gtid() / 32; g < A.n_blocks; g += warps) {
+  // a half warp per block (most blocks hold at most 16 entries, a lane each); the lanes
+  // work on their own, without warp-wide operations
+  const uint32_t hl = lane_id() & 15u;
+  const uint64_t halves = gstride() / 16;
+  for (uint64_t g = gtid() / 16; g < A.n_blocks; g += halves) {
     const BlockDesc b = A.blocks[g];
     if (b.ptr == nullptr) continue;
     const uint32_t nent = unp_entries(A, g);
@@ -848,7 +850,7 @@ __global__ void __launch_bounds__(kPostWarps * 32) k_vcrc(const UnpArgs A, CrcTa
     const uint32_t* chF = A.chunkF + A.chunk_first[g];
     const uint32_t* snap = A.snap + 2 * (rec0 + g);
     const uintptr_t base0 = G.a1 - uintptr_t(kChunk) * uintptr_t(G.U);  // chunk 0's first byte
-    for (uint32_t k = lane; k < nent; k += 32) {
+    for (uint32_t k = hl; k < nent; k += 16) {
       const uint2 t = A.ent_tab[g * kHdrMax + k];
       const uint32_t vs = t.x >> 16, ve = t.y & 0xFFFFu;
       uint32_t F = 0;
