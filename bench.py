@@ -127,8 +127,8 @@ class ClockSampler:
 # traffic grows with the entries; profiles/dram_traffic_cfg3_quarter.md), with the SHA-256
 # of the CUDA sources at the time: once a source changes the numbers no longer describe
 # the call and the bench reports null.
-_CALL_TRAFFIC = (4 * 1.059e9, "7321c67130d1a0ac9937bbf6222bd17824bea4e94cde3cba8ac3bda749e8f7a5")
-_KERNEL_TRAFFIC = {"k_encode_stg": 4 * 475.5e6, "k_unpack": 4 * 267.9e6, "k_keys": 4 * 43.8e6}
+_CALL_TRAFFIC = (4 * 1.0589e9, "0b6bd667ef0c6ea062cb204cdaa1e7cbe3d16ad3549c0e2a52cf14fb44c14f48")
+_KERNEL_TRAFFIC = {"k_encode_stg": 4 * 475.4e6, "k_unpack": 4 * 268.1e6, "k_keys": 4 * 43.8e6}
 
 
 def _sources_digest():
