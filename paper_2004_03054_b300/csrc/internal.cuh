@@ -213,6 +213,7 @@ struct Tuning {
   uint32_t encode_ctas_per_sm = 0;  // 0: as many as shared memory allows
   uint32_t elem_threads = 256;
   uint32_t crc_ctas = 56;  // the unpack's checksum pass: the other stages run beside it on the rest
+  bool crc_ctas_set = false;  // crc_ctas came from the caller (else it may follow the block size)
   uint32_t crc_warps = 32;
   uint32_t h2d_ranges = 0;  // luda_compact's transfer ranges (0: from the input bytes and target size)
 };
