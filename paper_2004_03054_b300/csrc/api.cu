@@ -2573,6 +2573,7 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
   Holder* h = new Holder;
   const uint64_t cap0 = ((in_bytes + in_bytes / 2) | ((64ull << 20) - 1)) + 1;
   h->pinned = pinned_get(cap0, &h->pinned_cap);
+  if (!h->pinned) h->pinned = pinned_get(256ull << 20, &h->pinned_cap);  // more buffers as tables come
   uint8_t* pin = h->pinned;
   uint64_t pin_left = h->pinned ? h->pinned_cap : 0, pos = 0;
   std::vector<uint8_t*> host_at;  // host address of every emitted table
@@ -2585,11 +2586,17 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
     cudaStreamSynchronize(st);
     return s;
   };
+  // a failed call: no copy may still write the pinned buffers when they go back to the cache
+  auto fail = [&](luda_status s) {
+    cudaStreamSynchronize(x->in);
+    cudaStreamSynchronize(x->out);
+    holder_release(h);
+    return finish(s);
+  };
   if (!ok || !h->pinned) {
     const luda_status s = h->pinned ? cuda_fail(cudaGetLastError(), "copy of the inputs to the device")
                                     : cuda_fail(cudaErrorMemoryAllocation, "pinned host allocation");
-    holder_release(h);
-    return finish(s);
+    return fail(s);
   }
   for (uint32_t r = 0; r < R; ++r) {
     HostJob hj{nullptr, N, job.smallest_snapshot, job.bottommost};
@@ -2609,14 +2616,12 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
     double rs[LUDA_N_STAGES] = {};
     uint64_t rb[LUDA_N_STAGES] = {};
     if (cudaStreamWaitEvent(st, x->ev_in[r], 0) != cudaSuccess) {
-      holder_release(h);
-      return finish(cuda_fail(cudaGetLastError(), "stream wait"));
+      return fail(cuda_fail(cudaGetLastError(), "stream wait"));
     }
     rc = run_compaction(&hj, 1, &ro, st, &routs[r], false, &ms, nullptr, rs, rb, nullptr, &nrec);
     if (!rc && routs[r].status) rc = luda_status(routs[r].status);
     if (rc) {
-      holder_release(h);
-      return finish(rc);
+      return fail(rc);
     }
     ms_dev += ms;
     for (int k = 0; k < LUDA_N_STAGES; ++k) {
@@ -2653,8 +2658,7 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
         size_t c = 0;
         uint8_t* p = pinned_get(std::max<uint64_t>(2 * tb.size, 64ull << 20), &c);
         if (!p) {
-          holder_release(h);
-          return finish(cuda_fail(cudaErrorMemoryAllocation, "pinned host allocation"));
+          return fail(cuda_fail(cudaErrorMemoryAllocation, "pinned host allocation"));
         }
         h->more_pinned.emplace_back(p, c);
         pin = p;
@@ -2674,8 +2678,7 @@ luda_status compact_host_ranges(const luda_job& job, const luda_options* opts, l
       pin_left = adv < pin_left ? pin_left - adv : 0;
     }
     if (!ok) {
-      holder_release(h);
-      return finish(cuda_fail(cudaGetLastError(), "copy of the new tables to the host"));
+      return fail(cuda_fail(cudaGetLastError(), "copy of the new tables to the host"));
     }
     // with the library's allocator the tables' memory goes back on the copy-out stream, after
     // their copies; a caller's allocator gets it back at the end
