@@ -127,8 +127,8 @@ class ClockSampler:
 # traffic grows with the entries; profiles/dram_traffic_cfg3_quarter.md), with the SHA-256
 # of the CUDA sources at the time: once a source changes the numbers no longer describe
 # the call and the bench reports null.
-_CALL_TRAFFIC = (4 * 1.0589e9, "d50fb9f925fae4b3efb6748c43668b7298fad3aa8d150b305ca09800125fa895")
-_KERNEL_TRAFFIC = {"k_encode_stg": 4 * 475.4e6, "k_unpack": 4 * 268.1e6, "k_keys": 4 * 43.8e6}
+_CALL_TRAFFIC = (4 * 1.0593e9, "f171ab9115b1b6f779606a52e994da5852aa9405bd6f4e1743bc4f254ab10a35")
+_KERNEL_TRAFFIC = {"k_encode_stg": 4 * 475.8e6, "k_unpack": 4 * 268.0e6, "k_keys": 4 * 43.8e6}
 
 
 def _sources_digest():

@@ -122,8 +122,7 @@ typedef struct {
                                    cut and layout stages: 64..1024, multiple of 32 (default 256) */
   uint32_t crc_ctas;            /* CTAs (one per SM) of the data-block checksum kernels, which run beside the
                                    other stages on a second stream: the unpack's checksum pass, and the
-                                   checksums of stored compressed blocks: 1..148 (default 56, or 74
-                                   when the data blocks average under 8 KiB) */
+                                   checksums of stored compressed blocks: 1..148 (default 56) */
   uint32_t crc_warps;           /* warps per CTA of the checksum kernels of compressed blocks: 8, 16, 24 or 32
                                    (default 32; the unpack's checksum pass always has 16); fewer leave room
                                    on their SMs for the other stages' CTAs */

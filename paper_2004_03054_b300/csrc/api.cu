@@ -106,10 +106,7 @@ luda::TuningScope::TuningScope(const luda_tuning* t) : saved_(t_tuning) {
   if (t->walk_threads) t_tuning.walk_threads = t->walk_threads;
   if (t->encode_ctas_per_sm) t_tuning.encode_ctas_per_sm = t->encode_ctas_per_sm;
   if (t->elem_threads) t_tuning.elem_threads = t->elem_threads;
-  if (t->crc_ctas) {
-    t_tuning.crc_ctas = t->crc_ctas;
-    t_tuning.crc_ctas_set = true;
-  }
+  if (t->crc_ctas) t_tuning.crc_ctas = t->crc_ctas;
   if (t->crc_warps) t_tuning.crc_warps = t->crc_warps;
   if (t->h2d_ranges) t_tuning.h2d_ranges = t->h2d_ranges;
 }
@@ -1083,13 +1080,10 @@ struct KeptGuard {
   ~KeptGuard() { kept_free(k); }
 };
 
-// SMs of the unpack's checksum pass: the caller's tuning when it sets one; else 56, or 74
-// when the data blocks average under 8 KiB (small blocks carry more fixed work per byte
-// in the pass: on the 256-job batch of 4 KiB blocks 74 take 4.70 against 4.85 ms).
-uint32_t unpack_ctas(uint64_t in_bytes, uint32_t n_blocks) {
-  if (tuning().crc_ctas_set || !n_blocks || in_bytes / n_blocks >= 8192) return tuning().crc_ctas;
-  return 74;
-}
+// Whether the unpack's lanes fold small blocks by half warps, one block each: blocks under
+// 8 KiB on average (a 5 KiB block's 36 chunks fill 64 lanes of a warp's two rounds, 48 of a
+// half warp's three).
+bool unpack_half(uint64_t in_bytes, uint32_t n_blocks) { return n_blocks && in_bytes / n_blocks < 8192; }
 
 // The whole compaction for n_jobs jobs whose inputs are device pointers. On return
 // outs[j] hold device (or, with host_out, pinned host) tables.
@@ -1565,7 +1559,7 @@ luda_status run_compaction(const HostJob* jobs, uint32_t n_jobs, const luda_opti
       tr.mark(11, side->s);
       uint64_t in_total = 0;
       for (uint64_t v : job_in_bytes) in_total += v;
-      launch_unpack_crc(ua, tabs, unpack_ctas(in_total, NB), side->s);
+      launch_unpack_crc(ua, tabs, tuning().crc_ctas, unpack_half(in_total, NB), side->s);
       tr.mark(12, side->s);
       launch_unpack_keys(ua, st);
     }
@@ -2147,7 +2141,7 @@ luda_status plan_build(const luda_job* jobs, uint32_t n_jobs, const luda_options
       CK(fork_join(side, 0, st, side->s));
       uint64_t in_total = 0;
       for (const DInput& d : hin) in_total += d.size;
-      launch_unpack_crc(ua, tabs, unpack_ctas(in_total, NB), side->s);
+      launch_unpack_crc(ua, tabs, tuning().crc_ctas, unpack_half(in_total, NB), side->s);
       launch_unpack_keys(ua, st);
     }
     launch_plan_sanitize(recs, n_rec, d_jobs, n_jobs, d_errs, d_arena, st);

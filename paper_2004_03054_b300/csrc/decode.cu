@@ -461,7 +461,8 @@ constexpr uint32_t kUnpWarps = 16;
 constexpr uint32_t kUnpBndMax = 2 * kHdrMax + 2;  // piece boundaries: two per entry, the tail, the end
 constexpr uint32_t kSkStride = 11;                // words of a lane's slot (odd: lanes hit distinct banks)
 struct UnpWarp {
-  uint32_t bnd[kUnpBndMax];     // piece boundaries (message offsets, ascending)
+  uint32_t bnd[2][kUnpBndMax];  // piece boundaries (message offsets, ascending) of the warp's block, or of
+                                // each half warp's block
   uint32_t sk[32 * kSkStride];  // per lane of a round: its chunk's registers before each 16-byte word, then
                                 // the first chain's register
 };
@@ -489,7 +490,7 @@ __device__ __forceinline__ uint32_t unp_zeros(uint32_t v, uint32_t L, uint32_t t
 // Message geometry: chunks of kChunk bytes ending at a1 = end rounded up to 16.
 struct UnpGeo {
   uintptr_t ps, pe, a1, lo16;
-  uint32_t U, rounds, pad;
+  uint32_t U, pad;
   int32_t x0;  // message offset of chunk 0's first byte (<= 0)
 };
 
@@ -501,7 +502,6 @@ __device__ __forceinline__ UnpGeo unp_geo(const uint8_t* p, uint32_t n) {
   G.lo16 = G.ps & ~uintptr_t(15);
   G.pad = uint32_t(G.a1 - G.pe);
   G.U = uint32_t((G.a1 - G.lo16 + kChunk - 1) / kChunk);
-  G.rounds = (G.U + 31) >> 5;
   G.x0 = int32_t(int64_t(G.a1) - int64_t(kChunk) * int64_t(G.U) - int64_t(G.ps));
   return G;
 }
@@ -552,7 +552,14 @@ __device__ __forceinline__ uint32_t crc_quad_rep(uint32_t S, const uint4 v, uint
   return crc_word_rep(S, v.w, tl);
 }
 
-// Folds every chunk of the message: returns this lane's Z_{32 * kChunk}-weighted sum of its
+// Lanes take a block in groups of GW: the whole warp (GW = 32), or each half warp its own
+// block (GW = 16: for small blocks, whose last round would leave most of a warp idle).
+template <uint32_t GW>
+__device__ __forceinline__ uint32_t grp_mask() {
+  return GW == 32 ? 0xFFFFFFFFu : (0xFFFFu << (lane_id() & 16u));
+}
+
+// Folds every chunk of the message: returns this lane's Z_{GW * kChunk}-weighted sum of its
 // chunks' registers. With nb > 0 boundaries (W->bnd set), each chunk's register goes to
 // chF[c] and, for each boundary inside the chunk, the register of the chunk's bytes before
 // the boundary's 16-byte word to snap[i]: after each round the lanes leave their chunks'
@@ -560,16 +567,19 @@ __device__ __forceinline__ uint32_t crc_quad_rep(uint32_t S, const uint4 v, uint
 // the sum is that of the message with its first four bytes complemented (the standard
 // register's initial value 0xFFFFFFFF). The next round's chunks are prefetched into L2
 // while a round is folded.
-__device__ __forceinline__ uint32_t unp_fold(const UnpGeo G, UnpWarp* W, uint32_t nb, uint32_t* chF,
-                                             uint32_t* snap, uint32_t tl, const uint32_t* sC, bool init) {
-  const uint32_t lane = lane_id();
-  uint32_t acc = 0, bnext = 0;  // bnext: the first boundary of the round (warp-uniform)
+template <uint32_t GW>
+__device__ __forceinline__ uint32_t unp_fold(const UnpGeo G, UnpWarp* W, const uint32_t* bnd, uint32_t nb,
+                                             uint32_t* chF, uint32_t* snap, uint32_t tl, const uint32_t* sC,
+                                             bool init) {
+  const uint32_t lane = lane_id(), gl = lane & (GW - 1), gb = lane & ~(GW - 1), gm = grp_mask<GW>();
+  const uint32_t rounds = (G.U + GW - 1) / GW;
+  uint32_t acc = 0, bnext = 0;  // bnext: the first boundary of the round (uniform in the group)
   uint32_t* slot = W ? W->sk + lane * kSkStride : nullptr;
-  for (uint32_t r = 0; r < G.rounds; ++r) {
-    const int32_t c = int32_t(G.U) - int32_t(32 * (G.rounds - r)) + int32_t(lane);
-    if (lane == 0 && r + 1 < G.rounds) {
-      const uintptr_t lo = G.a1 - uintptr_t(kChunk) * uintptr_t(32 * (G.rounds - r - 1));
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(32u * kChunk) : "memory");
+  for (uint32_t r = 0; r < rounds; ++r) {
+    const int32_t c = int32_t(G.U) - int32_t(GW * (rounds - r)) + int32_t(gl);
+    if (gl == 0 && r + 1 < rounds) {
+      const uintptr_t lo = G.a1 - uintptr_t(kChunk) * uintptr_t(GW * (rounds - r - 1));
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(GW * kChunk) : "memory");
     }
     uint4 cur[kChunkW];
     unp_load(G, c, cur);
@@ -607,26 +617,26 @@ __device__ __forceinline__ uint32_t unp_fold(const UnpGeo G, UnpWarp* W, uint32_
           }
         }
       }
-      acc = crc_mat(sC + kCZ4608 * 1024u, acc) ^ S;  // the other lanes' chunks of the round
+      acc = crc_mat(sC + (GW == 32 ? kCZ4608 : kCZ2304) * 1024u, acc) ^ S;  // the group's other chunks of the round
     }
     if (nb) {
-      // the boundaries inside this round's chunks (cr0 .. cr0 + 31), one per lane; they
+      // the boundaries inside this round's chunks (cr0 .. cr0 + GW - 1), one per lane; they
       // ascend, so the lanes that find one form a prefix. A boundary at the message's
       // padded end (chunk U) lies in no chunk and is never taken.
-      __syncwarp();
-      const int32_t cr0 = int32_t(G.U) - int32_t(32 * (G.rounds - r));
+      __syncwarp(gm);
+      const int32_t cr0 = int32_t(G.U) - int32_t(GW * (rounds - r));
       for (;;) {
-        const uint32_t bi = bnext + lane;
+        const uint32_t bi = bnext + gl;
         int32_t o = 0, cb = 0;
         bool mine = false;
         if (bi < nb) {
-          o = int32_t(W->bnd[bi]) - G.x0;  // offset from chunk 0's first byte
+          o = int32_t(bnd[bi]) - G.x0;  // offset from chunk 0's first byte
           cb = o / int32_t(kChunk);
-          mine = cb < cr0 + 32;
+          mine = cb < cr0 + int32_t(GW);
         }
-        const uint32_t took = __popc(__ballot_sync(0xFFFFFFFFu, mine));
+        const uint32_t took = __popc(__ballot_sync(gm, mine));
         if (mine) {
-          const uint32_t* sl = W->sk + uint32_t(cb - cr0) * kSkStride;
+          const uint32_t* sl = W->sk + (gb + uint32_t(cb - cr0)) * kSkStride;
           const uint32_t k = uint32_t(o - int32_t(kChunk) * cb) >> 4;
           uint32_t sv = sl[k];
           // a word of the second chain: its register follows the first chain's bytes
@@ -634,32 +644,34 @@ __device__ __forceinline__ uint32_t unp_fold(const UnpGeo G, UnpWarp* W, uint32_
           snap[bi] = sv;
         }
         bnext += took;
-        if (took < 32) break;
+        if (took < GW) break;
       }
-      __syncwarp();
+      __syncwarp(gm);
     }
   }
   return acc;
 }
 
-// Z_pad(F(message)) from the lanes' sums (every lane gets it): a butterfly with Z_{kChunk * 2^k}.
+// Z_pad(F(message)) from the group's sums (every lane gets it): a butterfly with Z_{kChunk * 2^k}.
+template <uint32_t GW>
 __device__ __forceinline__ uint32_t unp_join(uint32_t acc, const uint32_t* sC) {
-  const uint32_t lane = lane_id();
+  const uint32_t lane = lane_id(), gm = grp_mask<GW>();
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const uint32_t other = __shfl_xor_sync(0xFFFFFFFFu, acc, 1u << k);
+  for (int k = 0; k < (GW == 32 ? 5 : 4); ++k) {
+    const uint32_t other = __shfl_xor_sync(gm, acc, 1u << k);
     const uint32_t* tab = sC + (kCZ144 + k) * 1024u;
     acc = (lane & (1u << k)) ? (crc_mat(tab, other) ^ acc) : (crc_mat(tab, acc) ^ other);
   }
   return acc;
 }
 
-// F(p[0 .. n)) by the whole warp (no boundaries; the pad removed with Z_{-pad}).
+// F(p[0 .. n)) by the lane group (no boundaries; the pad removed with Z_{-pad}).
+template <uint32_t GW>
 __device__ __noinline__ uint32_t unp_range(const uint8_t* p, uint32_t n, uint32_t tl, const uint32_t* sC,
                                            const CrcTabs tabs) {
   if (n == 0) return 0;
   const UnpGeo G = unp_geo(p, n);
-  uint32_t acc = unp_join(unp_fold(G, nullptr, 0, nullptr, nullptr, tl, sC, false), sC);
+  uint32_t acc = unp_join<GW>(unp_fold<GW>(G, nullptr, nullptr, 0, nullptr, nullptr, tl, sC, false), sC);
   if (G.pad) acc = crc_shift(tabs.shift + size_t(kShiftPow + G.pad - 1) * 1024, acc);
   return acc;
 }
@@ -677,6 +689,7 @@ __device__ __forceinline__ bool unp_fast(const UnpArgs& A, const BlockDesc& b, u
   return nent > 0 && nent <= kHdrMax && b.size < 65536 && G.U <= A.chunk_first[g + 1] - A.chunk_first[g];
 }
 
+template <uint32_t GW>
 __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, CrcTabs tabs) {
   extern __shared__ __align__(16) uint32_t s_unp[];
   uint32_t* sTr = s_unp;
@@ -694,20 +707,22 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
   }
   __syncthreads();
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t gl = lane & (GW - 1), gb = lane & ~(GW - 1), gm = grp_mask<GW>();
   UnpWarp* W = Wall + warp;
+  uint32_t* bnd = W->bnd[gb ? 1 : 0];  // the group's boundary list
   const uint32_t tl = smem_addr(sTr) + lane * 4u;
   uint32_t gnext = 0;
-  if (lane == 0) gnext = atomicAdd(A.next, 1u);
+  if (gl == 0) gnext = atomicAdd(A.next, 1u);
   for (;;) {
-    const uint64_t g = __shfl_sync(0xFFFFFFFFu, gnext, 0);
+    const uint64_t g = __shfl_sync(gm, gnext, gb);
     if (g >= A.n_blocks) break;
-    // the warp's next block is claimed now, so that the claim's round trip overlaps this block
-    if (lane == 0) gnext = atomicAdd(A.next, 1u);
+    // the group's next block is claimed now, so that the claim's round trip overlaps this block
+    if (gl == 0) gnext = atomicAdd(A.next, 1u);
     const BlockDesc b = A.blocks[g];
     if (b.ptr == nullptr) continue;
     // the stored trailer and type byte are loaded before the fold, their round trip beside it
     uint32_t stored = 0, btype = 0;
-    if (A.verify && lane == 0) {
+    if (A.verify && gl == 0) {
       stored = ld_u32(b.ptr + b.size + 1);
       btype = b.ptr[b.size];
     }
@@ -721,26 +736,26 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
     if (fast) {
       // piece boundaries from the walk's entry table
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t k = lane + 32 * h;
+      for (int h = 0; h < int(kHdrMax / GW); ++h) {
+        const uint32_t k = gl + GW * h;
         if (k < nent) {
           const uint2 t = A.ent_tab[g * kHdrMax + k];
-          W->bnd[2 * k] = t.x & 0xFFFFu;
-          W->bnd[2 * k + 1] = t.x >> 16;
+          bnd[2 * k] = t.x & 0xFFFFu;
+          bnd[2 * k + 1] = t.x >> 16;
           if (k == nent - 1) {
-            W->bnd[2 * nent] = t.y & 0xFFFFu;  // the restart array
-            W->bnd[2 * nent + 1] = n;
+            bnd[2 * nent] = t.y & 0xFFFFu;  // the restart array
+            bnd[2 * nent + 1] = n;
           }
         }
       }
-      __syncwarp();
+      __syncwarp(gm);
     }
     uint32_t acc = 0;
     if (fast || A.verify)
-      acc = unp_fold(G, W, nb, A.chunkF + A.chunk_first[g], A.snap + 2 * (rec0 + g), tl, sC, A.verify);
+      acc = unp_fold<GW>(G, W, bnd, nb, A.chunkF + A.chunk_first[g], A.snap + 2 * (rec0 + g), tl, sC, A.verify);
     if (A.verify) {
-      const uint32_t got = unp_join(acc, sC);
-      if (lane == 0) {
+      const uint32_t got = unp_join<GW>(acc, sC);
+      if (gl == 0) {
         const uint32_t want = unp_zeros(~crc_unmask(stored), G.pad, tl, sC);
         DErr* ve = A.verr + b.job;
         if (got != want) report(ve, E_CORRUPT, A.in[b.input].local, b.off);
@@ -748,15 +763,16 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
       }
     }
     if (nent == 0 || fast) {
-      __syncwarp();  // the warp's shared arrays are reused by its next block
+      __syncwarp(gm);  // the group's shared arrays are reused by its next block
       continue;
     }
     // a block without boundaries: each value's register on its own; the values from the
-    // entry table, or (blocks the table does not cover) from lane 0 walking the block
+    // entry table, or (blocks the table does not cover) from the group's first lane walking
+    // the block
     const bool tab = nent <= kHdrMax && b.size < 65536;
     const uint64_t nr = ld_u32(b.ptr + b.size - 4);
     const uint64_t rstart = b.size - 4 - 4 * nr;
-    const uint8_t *p = nullptr, *end = nullptr;  // lane 0's walk position
+    const uint8_t *p = nullptr, *end = nullptr;  // the first lane's walk position
     uint64_t seg = 0;
     for (uint32_t k = 0; k < nent; ++k) {
       uint64_t vp = 0;
@@ -765,7 +781,7 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
         const uint2 t = A.ent_tab[g * kHdrMax + k];
         vp = reinterpret_cast<uint64_t>(b.ptr + (t.x >> 16));
         vl = (t.y & 0xFFFFu) - (t.x >> 16);
-      } else if (lane == 0) {
+      } else if (gl == 0) {
         // the walk validated the block: next entry, crossing into the next restart segment
         while (p >= end) {
           p = b.ptr + ld_u32(b.ptr + rstart + 4 * seg);
@@ -781,12 +797,12 @@ __global__ void __launch_bounds__(kUnpWarps * 32, 1) k_unpack(const UnpArgs A, C
         vl = uint32_t(vlen);
         p += vlen;
       }
-      vp = __shfl_sync(0xFFFFFFFFu, vp, 0);
-      vl = __shfl_sync(0xFFFFFFFFu, vl, 0);
-      const uint32_t v = unp_range(reinterpret_cast<const uint8_t*>(vp), vl, tl, sC, tabs);
-      if (lane == 0) A.recs.vcrc[rec0 + k] = v;
+      vp = __shfl_sync(gm, vp, gb);
+      vl = __shfl_sync(gm, vl, gb);
+      const uint32_t v = unp_range<GW>(reinterpret_cast<const uint8_t*>(vp), vl, tl, sC, tabs);
+      if (gl == 0) A.recs.vcrc[rec0 + k] = v;
     }
-    __syncwarp();
+    __syncwarp(gm);
   }
 }
 
@@ -1379,10 +1395,15 @@ void launch_unpack_keys(const UnpArgs& a, cudaStream_t st) {
   count_launches(1);
 }
 
-void launch_unpack_crc(const UnpArgs& a, CrcTabs tabs, uint32_t ctas, cudaStream_t st) {
+void launch_unpack_crc(const UnpArgs& a, CrcTabs tabs, uint32_t ctas, bool half_warps, cudaStream_t st) {
   if (!a.n_blocks) return;
-  smem_optin(k_unpack, kUnpSmem);
-  k_unpack<<<ctas, kUnpWarps * 32, kUnpSmem, st>>>(a, tabs);
+  if (half_warps) {
+    smem_optin(k_unpack<16>, kUnpSmem);
+    k_unpack<16><<<ctas, kUnpWarps * 32, kUnpSmem, st>>>(a, tabs);
+  } else {
+    smem_optin(k_unpack<32>, kUnpSmem);
+    k_unpack<32><<<ctas, kUnpWarps * 32, kUnpSmem, st>>>(a, tabs);
+  }
   smem_optin(k_vcrc, kPostSmem);
   k_vcrc<<<grid_for(a.n_blocks, kPostWarps, kSms * 8), kPostWarps * 32, kPostSmem, st>>>(a, tabs);
   count_launches(2);

@@ -213,7 +213,6 @@ struct Tuning {
   uint32_t encode_ctas_per_sm = 0;  // 0: as many as shared memory allows
   uint32_t elem_threads = 256;
   uint32_t crc_ctas = 56;  // the unpack's checksum pass: the other stages run beside it on the rest
-  bool crc_ctas_set = false;  // crc_ctas came from the caller (else it may follow the block size)
   uint32_t crc_warps = 32;
   uint32_t h2d_ranges = 0;  // luda_compact's transfer ranges (0: from the input bytes and target size)
 };
@@ -331,8 +330,9 @@ struct UnpArgs {
 };
 // Records and keys (every field but vcrc).
 void launch_unpack_keys(const UnpArgs& a, cudaStream_t st);
-// Checksums (with `verify`) and the value registers (vcrc), on `ctas` CTAs of one SM each.
-void launch_unpack_crc(const UnpArgs& a, CrcTabs tabs, uint32_t ctas, cudaStream_t st);
+// Checksums (with `verify`) and the value registers (vcrc), on `ctas` CTAs of one SM each;
+// with half_warps each half warp folds its own block (small blocks).
+void launch_unpack_crc(const UnpArgs& a, CrcTabs tabs, uint32_t ctas, bool half_warps, cudaStream_t st);
 // recs.vcrc[r] = F(value of record r) for r < *n (or n_max when n is NULL), one warp per
 // record (decoded records and the build path's records).
 void launch_value_crc(Recs recs, const uint32_t* n, uint32_t n_max, CrcTabs tabs, cudaStream_t st);
