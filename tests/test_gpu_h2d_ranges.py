@@ -157,3 +157,45 @@ def test_index_out_of_order_runs_in_one_piece():
     assert want.status == oracle.ERR_CORRUPTION
     got = _pinned_compact(bad, job.smallest_snapshot, _opts(job, 4))
     assert got.status == luda.ERR_CORRUPTION and got.tables == []
+
+
+def test_ranges_with_a_callers_allocator_and_failing_allocations():
+    """Through the caller's allocator hook: the key-range call gives back every byte it took,
+    and whichever allocation fails, the call either returns LUDA_ERR_OOM with no tables or
+    (a failure while planning the ranges) runs in one piece with the oracle's tables."""
+    from test_gpu_faults import Hook
+    job = W.config2(seed=38, scale=1 / 4)
+    job.target_file_size = 128 * 1024
+    ins = oracle_inputs(job)
+    want = [t.data for t in oracle_compact(job, ins).tables]
+    L = luda.lib()
+    bufs = []
+    arr = (luda.Input * len(ins))()
+    for i, b in enumerate(ins):
+        t = torch.empty(len(b), dtype=torch.uint8).pin_memory()
+        t.numpy()[:] = np.frombuffer(b, dtype=np.uint8)
+        bufs.append(t)
+        arr[i].data, arr[i].size = t.data_ptr(), len(b)
+
+    def run(hook):
+        o = hook.options(job)
+        o.tuning = C.pointer(luda.Tuning.of({"h2d_ranges": 4}))
+        out = luda.Outputs()
+        rc = L.luda_compact(arr, len(ins), job.level, job.smallest_snapshot, C.byref(o), C.byref(out))
+        torch.cuda.synchronize()
+        got = [C.string_at(out.tables[i].data, out.tables[i].size) for i in range(out.n_tables)]
+        L.luda_outputs_free(C.byref(out))
+        torch.cuda.synchronize()
+        return rc, got
+
+    ok = Hook()
+    rc, got = run(ok)
+    assert rc == 0 and got == want
+    assert not ok.live
+    n_calls = ok.calls
+    assert n_calls > 8
+    for k in range(0, n_calls, max(1, n_calls // 24)):
+        bad = Hook(fail_at=k)
+        rc, got = run(bad)
+        assert (rc == luda.ERR_OOM and got == []) or (rc == 0 and got == want), (k, rc)
+        assert not bad.live, (k, bad.live)
